@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Benchmark: retarded (light-cone) Lyman-Werner field evaluations per second.
+
+Workload (default): 128^3 periodic grid, 150 comoving Mpc box, flat LCDM
+(Omega_m = 0.31, h = 0.68), 64 equal-cosmic-time steps z = 30 -> 10 (up to 7
+active light-cone shells), 1e4 Gaussian-clustered sources with a M^-2 mass
+function and 1-4 step lifetimes, FP32 FFT + shell multiply-accumulate.  A
+"step" is one push of that step's sources (deposit + forward transform into
+the history ring) plus one retarded-field evaluation (shell MAC + inverse
+transform).  The 64-step run is cycled (history reset at the wrap).
+
+Timing: W warm-up steps, then K steps timed one by one with CUDA events on the
+plan's stream, L2 flushed (a 512 MB write) between timed steps, outside the
+events.  Under torchrun each rank runs an independent simulation on its own
+GPU (weak scaling, no data-path collective); the reported time is the max over
+ranks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "retarded-field evals/s & cell·shell MAC/s vs plain FP32 path; HBM %; p50/p99"
+UNIT = "fields/s"
+WORKLOADS = {
+    "c2": ("128^3 grid, 150 Mpc box, 64 equal-time steps z=30->10 (<=7 shells), 1e4 clustered sources "
+           "(dN/dM~M^-2, 1-4 step lifetimes), FP32 FFT+MAC"),
+    "c1": "32^3 grid, 100 Mpc box, 8 equal-time steps z=20->15 (<=2 shells), 200 uniform sources, FP32",
+    "c3": ("256^3 grid, 200 Mpc box, 128 equal-conformal-time shells spanning the LW horizon at z=15, "
+           "1e5 clustered sources, BF16 history with per-slot FP32 scale"),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=64)
+    ap.add_argument("--warmup", type=int, default=8)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--flush-mb", type=int, default=512)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_field_rate(w, steps, cells_per_step=4096, seed=0):
+    """Time the FP64 oracle on a bounded sample: for each step, its Green's
+    functions plus `cells_per_step` sampled cells; extrapolate to a full field.
+    Returns (fields/s, seconds spent, description)."""
+    import oracle
+
+    oracle.build()
+    P = oracle.Problem.from_workload(w)
+    spent = 0.0
+    per_field = []
+    for s in steps:
+        grids = oracle.source_grids(P, w.cat, s)
+        one = np.array([0], dtype=np.int64)
+        t0 = time.perf_counter()
+        P.field(s, grids, cells=one)  # Green's functions + one cell: the fixed cost
+        t1 = time.perf_counter()
+        cells = np.random.default_rng(seed + s).integers(0, w.n ** 3, size=cells_per_step).astype(np.int64)
+        P.field(s, grids, cells=cells)
+        t2 = time.perf_counter()
+        fixed = t1 - t0
+        per_cell = max(0.0, (t2 - t1) - fixed) / cells_per_step
+        per_field.append(fixed + per_cell * w.n ** 3)
+        spent += t2 - t0
+    desc = (f"oracle FP64 on steps {list(steps)}: Green's functions + {cells_per_step} sampled cells per step, "
+            f"full-field time extrapolated from the per-cell rate")
+    return 1.0 / float(np.mean(per_field)), spent, desc
+
+
+# ---------------------------------------------------------------- main
+def active_shell_work(plan, w, s):
+    """Shells the MAC reads at step s: active slices whose step had sources."""
+    lo, hi, rh = plan.shells(s)
+    return sum(1 for j in range(len(lo)) if w.cat.active(s - j)[1].shape[0] > 0), len(lo)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    import synth
+
+    w = synth.config(args.workload)
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        import oracle
+
+        threads = oracle.threads()
+        steps_pool = list(range(max(1, w.steps.n_steps // 2), w.steps.n_steps))
+        for i in range(args.warmup):
+            oracle_field_rate(w, [steps_pool[i % len(steps_pool)]], cells_per_step=256)
+        rates, spent = [], 0.0
+        for i in range(args.steps):
+            r, sp, desc = oracle_field_rate(w, [steps_pool[i % len(steps_pool)]], cells_per_step=1024, seed=i)
+            rates.append(r)
+            spent += sp
+        value = float(np.mean(rates))
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "grid": w.n,
+                           "steps_in_run": w.steps.n_steps},
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                 "sample": "each step: one observing step's Green's functions + 1024 sampled cells, "
+                                           "full-field time extrapolated"},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                "cpu_seconds": spent}
+        print(json.dumps(line))
+        return 0
+
+    import torch
+
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    import paper_1502_02294_gb300 as lc
+
+    lc.build()
+    stream = torch.cuda.current_stream()
+    plan = lc.Plan.from_workload(w, stream=stream)
+    T = w.steps.n_steps
+    plan.prepare()  # every observing step's Green's function table (plan time)
+    # device-resident inputs of every step
+    src_dev = []
+    for s in range(T):
+        pos, lum = w.cat.active(s)
+        src_dev.append((torch.from_numpy(pos).to(dev), torch.from_numpy(lum).to(dev)))
+    out = torch.empty((w.n,) * 3, dtype=torch.float32, device=dev)
+    flush = torch.empty(args.flush_mb << 20, dtype=torch.uint8, device=dev)
+    work = {s: active_shell_work(plan, w, s) for s in range(T)}
+    nk = w.n * w.n * (w.n // 2 + 1)
+
+    cursor = [0]
+
+    def step_once(timed_events=None):
+        s = cursor[0]
+        if s == 0:
+            plan.reset()
+        pos, lum = src_dev[s]
+        if timed_events:
+            timed_events[0].record(stream)
+        plan.push(s, pos, lum)
+        plan.field(s, out)
+        if timed_events:
+            timed_events[1].record(stream)
+        cursor[0] = (s + 1) % T
+        return s
+
+    for _ in range(max(3, args.warmup)):
+        step_once()
+    torch.cuda.synchronize()
+    plan.timing(reset=True)
+    plan.set_timing(True)
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = lc.kernel_launches()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    done_steps = []
+    for i in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps, outside the events
+        done_steps.append(step_once(evs[i]))
+    torch.cuda.synchronize()
+    launches = lc.kernel_launches() - launches0
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    phases = plan.timing(reset=True)
+    plan.set_timing(False)
+    per_step_ms = np.array([a.elapsed_time(b) for a, b in evs])
+    t_total = float(per_step_ms.sum()) / 1e3
+    t_max = t_total
+    if world > 1:
+        tt = torch.tensor([t_total], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * args.steps / t_max
+    mac_cells = sum(nk * work[s][0] for s in done_steps)
+
+    # roofline of the dominant kernel (shell MAC fused with the inverse x pass):
+    # algorithmic bytes = ring reads (8 B per k per non-empty shell) + the
+    # complex write (8 B per k) + one read of the step's Ghat wedge table
+    mac_ms, mac_launches = phases["mac_x"]
+    W = plan.wedge_size
+    mac_bytes = sum(nk * (8 * work[s][0] + 8) + W * 4 * work[s][1] for s in done_steps)
+    import json as _json
+
+    peaks = {}
+    try:
+        peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    mac_gbs = mac_bytes / (mac_ms / 1e3) / 1e9 if mac_ms > 0 else None
+    phase_share = {k: round(v[0] / max(1e-12, sum(x[0] for x in phases.values())), 4) for k, v in phases.items()}
+
+    # end to end through the public API: pinned host inputs, host output
+    pinned = []
+    for s in range(T):
+        pos, lum = w.cat.active(s)
+        pinned.append((torch.from_numpy(pos).pin_memory(), torch.from_numpy(lum).pin_memory()))
+    host_out = torch.empty((w.n,) * 3, dtype=torch.float32).pin_memory()
+    plan.reset()
+    e_cursor = 0
+    for _ in range(max(3, args.warmup)):
+        plan.push(e_cursor, *pinned[e_cursor])
+        plan.field(e_cursor, host_out)
+        e_cursor += 1
+    e2e_t = 0.0
+    h2d = 0
+    for i in range(args.steps):
+        s = e_cursor
+        if s == 0:
+            plan.reset()
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.push(s, *pinned[s])
+        plan.field(s, host_out)  # synchronises and copies to the host
+        e2e_t += time.perf_counter() - t0
+        h2d += pinned[s][0].numel() * 8 + pinned[s][1].numel() * 8
+        e_cursor = (s + 1) % T
+    if world > 1:
+        tt = torch.tensor([e2e_t], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_t = float(tt.item())
+    e2e = {"value": world * args.steps / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(h2d // args.steps),
+           "d2h_bytes_per_step": int(w.n ** 3 * 4)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        rate, spent, desc = oracle_field_rate(w, [20, 41, 63][: (3 if args.workload == "c2" else 1)]
+                                              if args.workload == "c2" else [w.steps.n_steps - 1])
+        cpu = {"value": rate, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle", "sample": desc,
+               "seconds": round(spent, 2)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "grid": w.n,
+                       "box_mpc": w.box, "steps_in_run": T, "ring_slots": plan.n_ring,
+                       "history": "bf16" if w.history else "fp32", "l2": f"flushed between timed steps "
+                       f"({args.flush_mb} MB write outside the events)", "inputs": "device-resident"},
+            "cell_shell_mac_per_s": world * mac_cells / t_max,
+            "latency_ms": {"p50": float(np.percentile(per_step_ms, 50)), "p99": float(np.percentile(per_step_ms, 99))},
+            "roofline": {"bound": "hbm", "kernel": "k_cols<N,+1,MAC> (shell MAC + inverse x pass)",
+                         "achieved": mac_gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": (mac_gbs / hbm_peak) if mac_gbs else None,
+                         "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+                         "bytes_per_launch": mac_bytes / max(1, mac_launches),
+                         "ms_per_launch": mac_ms / max(1, mac_launches)},
+            "phase_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},
+            "phase_share": phase_share,
+            "clocks": clocks,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    plan.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,215 @@
+/*
+ * lc.h -- C ABI of liblc, the GB300 (sm_103a) light-cone retarded-field library.
+ *
+ * The library computes the time-delayed ("retarded", light-cone) radiation
+ * field of Ahn 2015 (arXiv:1502.02294), e.g. the Lyman-Werner background:
+ *
+ *   J(x, tau_obs) = U * sum_n  G_n (*) f_n                       (Eq. 9-11)
+ *
+ * where f_n is the gridded source luminosity of past slice n (Eq. 17 source
+ * term, l^3 absorbed as in Eq. 11), G_n the effective periodic retarded
+ * Green's function of the shell that slice occupies on the observer's past
+ * light cone (Eq. 10, LW kernel of Eqs. 14-17), and (*) a periodic
+ * convolution evaluated with the convolution theorem (Eqs. 12-13):
+ *
+ *   Jhat(k) = sum_n Ghat_n(k) fhat_n(k),    J = U * IDFT(Jhat)  (1/N^3 per Eq. 12)
+ *
+ * The steps of Section 2.2 map onto the calls:  steps 1-3 (slicing, Green's
+ * functions by direct summation over periodic unit-source images, their
+ * transforms, precomputed per observing time as the paragraph after the
+ * algorithm suggests) -> lc_plan_create / lc_plan_prepare;  step 4 (transform
+ * of the source term) -> lc_push_sources;  steps 5-6 (products, inverse
+ * transform, sum over slices; the sum is taken in k-space, which is exact by
+ * linearity, so one inverse transform suffices) -> lc_retarded_field.
+ *
+ * Conventions common to every call:
+ *   - Units: comoving Mpc for lengths; luminosities in any unit; J comes out
+ *     in (luminosity unit) / Mpc^2 / sr times out_unit.
+ *   - Grids are C order, index (i, j, k) at flat position (i*N + j)*N + k, the
+ *     cell of index i centred at x = i*l, l = L/N (Section 2.2).
+ *   - Pointers may be host or device memory (detected with
+ *     cudaPointerGetAttributes); the caller owns them and the library copies
+ *     what it needs.  All device work runs on the plan's stream.
+ *   - Every call returns an lc_status.  LC_OK is 0.  Argument errors leave
+ *     the plan usable; LC_ERR_CUDA and LC_ERR_TIMEOUT mark the plan failed
+ *     (every later call on it returns LC_ERR_CUDA).
+ *   - There is no CPU fallback: without a usable CUDA device the calls
+ *     return LC_ERR_CUDA.
+ */
+#ifndef LC_H
+#define LC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lc_plan lc_plan; /* opaque, owned by the library */
+
+typedef enum {
+    LC_OK = 0,
+    LC_ERR_INVALID_ARG = 1,      /* a null pointer, a bad value, a non-finite or negative luminosity */
+    LC_ERR_UNSUPPORTED_SIZE = 2, /* N not in {8,16,32,64,96,128,192,256,384,512}, or a table too large */
+    LC_ERR_STEP_ORDER = 3,       /* push not strictly increasing, or field for a step that is not the last pushed */
+    LC_ERR_OOM = 4,              /* device allocation failed (plan left usable, nothing allocated) */
+    LC_ERR_CUDA = 5,             /* a CUDA runtime error; the plan is marked failed */
+    LC_ERR_TIMEOUT = 6,          /* a bounded device wait gave up; the plan is marked failed */
+    LC_ERR_DEVICE_CHECK = 7      /* a device-side input check failed (reported by lc_plan_check) */
+} lc_status;
+
+/* Flat LCDM, no radiation: H(z) = 100 h sqrt(omega_m (1+z)^3 + 1 - omega_m) km/s/Mpc. */
+typedef struct {
+    double omega_m;
+    double h;
+} lc_cosmology;
+
+enum { LC_STEPS_EXPLICIT = 0, LC_STEPS_EQUAL_TIME = 1, LC_STEPS_EQUAL_TAU = 2 };
+enum { LC_HISTORY_FP32 = 0, LC_HISTORY_BF16 = 1 };
+
+/* How time is sliced (step 1 of Section 2.2) and how the field is evaluated.
+ * Step s spans [tau_s, tau_{s+1}] and is observed at its end, tau_{s+1}; the
+ * sources pushed at step s stand for the source term frozen over that step
+ * (Eq. 9).  Slice n seen from step s occupies the half-open shell
+ * [tau_{s+1} - tau_{n+1}, tau_{s+1} - tau_n) and counts while its inner radius
+ * is inside the LW horizon r_h, where r / alpha(z_s(r)) = 97.39 (Eqs. 15-16). */
+typedef struct {
+    int n_steps;           /* number of steps (>= 1) */
+    int spacing;           /* LC_STEPS_* */
+    const double* z_edges; /* LC_STEPS_EXPLICIT: n_steps + 1 decreasing redshifts (copied) */
+    double z_start;        /* LC_STEPS_EQUAL_TIME: first edge (highest z) */
+    double z_end;          /* EQUAL_TIME and EQUAL_TAU: last edge */
+    int n_shell;           /* LC_STEPS_EQUAL_TAU: step width r_h(z_end) / n_shell in conformal time */
+    int subsamples;        /* s: sub-cell samples per axis in G_n (even, 2..16; 0 -> 4) */
+    int history;           /* LC_HISTORY_FP32, or LC_HISTORY_BF16 (spectra stored / DC, scale kept in FP32) */
+    int normalise;         /* 1: scale each G_n so that l^3 sum G_n = int 4 pi r^2 g dr over its shell */
+    double out_unit;       /* U: multiplies J (0 -> 1) */
+} lc_steps;
+
+/* Create a plan for an N^3 periodic grid of side box_mpc.
+ * N in {8, 16, 32, 64, 96, 128, 192, 256, 384, 512}.  cuda_stream may be NULL
+ * (default stream) or a cudaStream_t.  Allocates the device history ring,
+ * work buffers and tables; Green's function tables are built lazily per
+ * observing step (or eagerly with lc_plan_prepare).  On error *out is NULL. */
+lc_status lc_plan_create(int n, double box_mpc, const lc_cosmology* cosmo, const lc_steps* steps,
+                         void* cuda_stream, lc_plan** out);
+
+/* Build (precompute) the Green's function tables of observing steps
+ * [step_begin, step_end) -- steps 2-3 of Section 2.2 and the stored
+ * "data files" of the paragraph after it.  Idempotent. */
+lc_status lc_plan_prepare(lc_plan* plan, int step_begin, int step_end);
+
+/* Deposit the sources active during step `step` (nearest grid point, integer
+ * fixed point: bit-exact and independent of source order) and transform them
+ * into the history ring (step 4 of Section 2.2).
+ *   pos: n_src * 3 doubles (x, y, z in comoving Mpc, any real value; wrapped
+ *        periodically), host or device.
+ *   lum: n_src doubles, finite and >= 0, host or device.
+ * Steps must strictly increase; a step that is never pushed counts as having
+ * no sources.  Host inputs are validated here (LC_ERR_INVALID_ARG); device
+ * inputs are validated on the device and reported by lc_plan_check. */
+lc_status lc_push_sources(lc_plan* plan, int step, int64_t n_src, const double* pos, const double* lum);
+
+/* The retarded field at the end of step `step` (steps 5-6 of Section 2.2),
+ * which must be the last pushed step.  out: N^3 floats, C order, host or
+ * device.  With a host `out` the call waits for the result; with a device
+ * `out` it only enqueues work on the plan's stream. */
+lc_status lc_retarded_field(lc_plan* plan, int step, float* out);
+
+/* Forget the history (ring) so that steps can start again at 0; the Green's
+ * function tables are kept. */
+lc_status lc_plan_reset(lc_plan* plan);
+
+/* Synchronise the plan's stream and report device-side input checks
+ * (LC_ERR_DEVICE_CHECK) and CUDA errors. */
+lc_status lc_plan_check(lc_plan* plan);
+
+lc_status lc_plan_set_stream(lc_plan* plan, void* cuda_stream);
+lc_status lc_plan_destroy(lc_plan* plan);
+const char* lc_status_string(lc_status status);
+
+/* Device bytes held by the plan (ring + tables + buffers), for HBM-budget admission. */
+size_t lc_plan_device_bytes(const lc_plan* plan);
+
+/* Bytes lc_plan_create would allocate before any Green's function table
+ * (ring, buffers), and the bytes of one observing step's table.  Host only. */
+lc_status lc_plan_estimate(int n, const lc_steps* steps, const lc_cosmology* cosmo, size_t* base_bytes,
+                           size_t* table_bytes_per_step);
+
+/* Geometry of observing step `step`: number of active slices, their shell
+ * radii (lookback j = 0 is the newest slice) and the horizon.  Arrays of at
+ * least step + 1 entries, or NULL. */
+lc_status lc_step_shells(const lc_plan* plan, int step, int* n_active, double* r_lo, double* r_hi, double* r_h,
+                         double* shell_integral);
+
+/* Ring depth and other plan facts. */
+typedef struct {
+    int n;
+    int n_steps;
+    int n_ring;            /* history slots = max active slices over all steps */
+    int history;
+    int wedge_size;        /* C(N/2 + 3, 3) */
+    int spectrum_row;      /* padded complex row length of the half spectrum */
+    double box_mpc;
+    const double* z_edges; /* n_steps + 1 entries, owned by the plan */
+} lc_plan_info_t;
+lc_status lc_plan_info(const lc_plan* plan, lc_plan_info_t* info);
+
+/* Ghat_j of observing step `step` on the symmetric wedge 0 <= p <= q <= r <= N/2
+ * (index C(r+2,3) + C(q+1,2) + p; Ghat is real and invariant under sign flips
+ * and permutations of (p, q, r)), building the step's table if needed.
+ * out: wedge_size floats, host or device.  Also returns Ghat_j(0) in FP64. */
+lc_status lc_plan_green_wedge(lc_plan* plan, int step, int lookback, float* out, double* ghat0);
+
+/* Batched evaluation: for every i, push plans[i]'s sources for steps[i] (if
+ * n_src[i] >= 0) and compute its retarded field into outs[i] (device
+ * pointers), with all instances' kernels launched phase by phase on the
+ * stream of plans[0] so that uneven instances overlap on the device. */
+lc_status lc_batch_step(lc_plan* const* plans, int n, const int* steps, const int64_t* n_src,
+                        const double* const* pos, const double* const* lum, float* const* outs);
+
+/* --- tracing ------------------------------------------------------------------ */
+
+/* Phases of one step, each timed with a pair of CUDA events on the plan's
+ * stream when timing is enabled. */
+enum {
+    LC_PHASE_DEPOSIT = 0,    /* zero grid + source checks + fixed-point deposit */
+    LC_PHASE_R2C_Z = 1,      /* z rows, real -> complex (int64 prologue) */
+    LC_PHASE_FWD_Y = 2,      /* y pass, forward */
+    LC_PHASE_FWD_X_RING = 3, /* x pass, forward, into the history ring slot */
+    LC_PHASE_MAC_X = 4,      /* shell multiply-accumulate fused with the inverse x pass */
+    LC_PHASE_INV_Y = 5,      /* y pass, inverse */
+    LC_PHASE_C2R_Z = 6,      /* z rows, complex -> real, scaled output */
+    LC_N_PHASES = 7
+};
+/* Enable (1) or disable (0) per-phase event timing on this plan. */
+lc_status lc_plan_set_timing(lc_plan* plan, int enable);
+/* Synchronise and return the accumulated milliseconds and launch counts per
+ * phase (arrays of LC_N_PHASES, either may be NULL); reset != 0 clears them. */
+lc_status lc_plan_timing(lc_plan* plan, double* ms, int64_t* launches, int reset);
+/* Number of kernels this library has launched in this process (all plans and
+ * stand-alone calls). */
+uint64_t lc_kernel_launches(void);
+
+/* --- the hot-path kernels as stand-alone calls (tests, users) --------------- */
+
+/* Nearest-grid-point fixed-point deposit: scale S = 2^(E-62) with
+ * n_src * max(lum) < 2^E, q = rint(lum / S), grid[cell] = sum q (int64, N^3,
+ * device or host), *total = sum q.  Cell = floor(x / l + 1/2) mod N per axis. */
+lc_status lc_deposit_grid(int n, double box_mpc, int64_t n_src, const double* pos, const double* lum,
+                          int64_t* grid, double* scale, int64_t* total, void* cuda_stream);
+
+/* 3D real-to-complex DFT with the forward sign of Eq. 12 (e^{-2 pi i k.x / N},
+ * unnormalised): in N^3 floats, out N*N*(N/2+1) complex floats (interleaved),
+ * C order, device pointers. */
+lc_status lc_fft_r2c(int n, const float* in, float* out_complex, void* cuda_stream);
+
+/* Inverse of Eq. 12 (e^{+2 pi i k.x / N}), times `scale` (pass 1/N^3 for the
+ * exact inverse): in N*N*(N/2+1) complex floats, out N^3 floats, device pointers. */
+lc_status lc_fft_c2r(int n, const float* in_complex, float* out, float scale, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LC_H */

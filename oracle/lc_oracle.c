@@ -487,11 +487,10 @@ double lco_rgf_direct(const lco_problem* P, int s, int j, int dx, int dy, int dz
  * l = L / N, in IEEE double (the cell centre of index i sits at x = i l). */
 static int64_t ngp_index(double x, double l, int N) {
     double t = floor(x / l + 0.5);
-    double m = t - (double)N * floor(t / (double)N);
+    double m = fmod(t, (double)N); /* exact */
+    if (m < 0.0) m += (double)N;
     int64_t i = (int64_t)m;
-    if (i >= N) i -= N; /* guards the rounding of t / N for huge |t| */
-    if (i < 0) i += N;
-    return i;
+    return (i >= 0 && i < N) ? i : 0;
 }
 
 static int check_sources(int64_t n_src, const double* pos, const double* lum) {

@@ -1,0 +1,930 @@
+// lc_api.cu -- the C ABI of liblc (see include/lc.h): plan lifecycle, the
+// per-step orchestration of the hot path, the per-observing-step Green's
+// function tables, and stand-alone kernel entry points.
+//
+// Per step (all on the plan's stream):
+//   push  : memset(grid) -> src_prep -> deposit -> rows r2c (int64 in)
+//           -> y-pass -> x-pass with ring-slot epilogue         (step 4, Sec. 2.2)
+//   field : x-pass with shell-MAC prologue (+ FP64 k = 0) -> y-pass
+//           -> rows c2r with U / N^3 epilogue                   (steps 5-6)
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <atomic>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "lc_internal.h"
+#include "lc_kernels.cuh"
+
+namespace lc {
+extern const FftOps fft_ops_8, fft_ops_16, fft_ops_32, fft_ops_64, fft_ops_96, fft_ops_128, fft_ops_192,
+    fft_ops_256, fft_ops_384, fft_ops_512;
+
+static const FftOps* ops_for(int n) {
+    switch (n) {
+    case 8: return &fft_ops_8;
+    case 16: return &fft_ops_16;
+    case 32: return &fft_ops_32;
+    case 64: return &fft_ops_64;
+    case 96: return &fft_ops_96;
+    case 128: return &fft_ops_128;
+    case 192: return &fft_ops_192;
+    case 256: return &fft_ops_256;
+    case 384: return &fft_ops_384;
+    case 512: return &fft_ops_512;
+    default: return nullptr;
+    }
+}
+
+// cudaFuncSetAttribute once per (device, N)
+static cudaError_t ensure_init(const FftOps* ops) {
+    static std::mutex mu;
+    static std::vector<std::pair<int, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> g(mu);
+    for (auto& d : done)
+        if (d.first == dev && d.second == ops->n) return cudaSuccess;
+    e = ops->init();
+    if (e == cudaSuccess) done.push_back({dev, ops->n});
+    return e;
+}
+
+static bool is_device_ptr(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static std::vector<float2> twiddles(int n) {
+    std::vector<float2> t(n);
+    for (int m = 0; m < n; ++m) {
+        const double a = 2.0 * 3.141592653589793238462643383279502884 * m / n;
+        t[m] = make_float2((float)cos(a), (float)-sin(a));
+    }
+    return t;
+}
+
+static std::atomic<unsigned long long> g_launches{0};
+static inline void count_launch(unsigned long long k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+} // namespace lc
+
+using namespace lc;
+
+struct lc_plan {
+    int N = 0;
+    double L = 0, l = 0;
+    Cosmo cosmo{0, 0};
+    int n_steps = 0, S = 4, history = 0, normalise = 1;
+    double U = 1.0;
+    std::vector<double> z;
+    cudaStream_t stream = nullptr;
+    const FftOps* ops = nullptr;
+    int NRP = 0;
+    long long spec_elems = 0, W = 0;
+    std::vector<int> A_of_step;
+    int n_ring = 1;
+    // device state
+    long long* d_grid = nullptr;
+    float2* d_work = nullptr;
+    void* d_ring = nullptr;
+    int* d_slot_step = nullptr;
+    double* d_slot_S = nullptr;
+    long long* d_slot_total = nullptr;
+    float2* d_tw = nullptr;
+    int* d_err = nullptr;
+    unsigned long long* d_maxbits = nullptr;
+    double* d_pos = nullptr;
+    double* d_lum = nullptr;
+    long long src_cap = 0;
+    float* d_out_stage = nullptr;
+    // Green's function tables, one per observing step (built lazily)
+    struct Table {
+        float* ghat = nullptr; // [W][A]
+        double* g0 = nullptr;  // [A]
+        int A = -1;            // -1: not built
+    };
+    std::vector<Table> tables;
+    // builder scratch
+    double* d_gw = nullptr;
+    long long gw_cap = 0;
+    double* d_gtab = nullptr;
+    long long gtab_cap = 0;
+    long long* d_bnd = nullptr;
+    double* d_I = nullptr;
+    double* d_scale = nullptr;
+    size_t bytes = 0;
+    int last_pushed = -1;
+    bool failed = false;
+    // per-phase event timing
+    bool timing = false;
+    struct Mark {
+        int phase;
+        cudaEvent_t a, b;
+    };
+    std::vector<Mark> marks;
+    std::vector<cudaEvent_t> pool;
+    double ms[LC_N_PHASES] = {0};
+    long long launches[LC_N_PHASES] = {0};
+};
+
+namespace {
+
+cudaEvent_t take_event(lc_plan* p) {
+    if (!p->pool.empty()) {
+        cudaEvent_t e = p->pool.back();
+        p->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Scoped phase marker: records an event pair on the plan's stream when
+// timing is on; always counts the phase's kernel launches.
+struct Phase {
+    lc_plan* p;
+    int ph;
+    int k;
+    cudaEvent_t a = nullptr;
+    Phase(lc_plan* p_, int ph_, int kernels) : p(p_), ph(ph_), k(kernels) {
+        if (p->timing) {
+            a = take_event(p);
+            cudaEventRecord(a, p->stream);
+        }
+    }
+    ~Phase() {
+        if (p->timing) {
+            cudaEvent_t b = take_event(p);
+            cudaEventRecord(b, p->stream);
+            p->marks.push_back({ph, a, b});
+        }
+        p->launches[ph] += k;
+        count_launch(k);
+    }
+};
+
+lc_status cuda_fail(lc_plan* p, cudaError_t e) {
+    if (e == cudaSuccess) return LC_OK;
+    if (p) p->failed = true;
+    return e == cudaErrorMemoryAllocation ? LC_ERR_OOM : LC_ERR_CUDA;
+}
+
+template <class T> cudaError_t dalloc(lc_plan* p, T** ptr, size_t count) {
+    *ptr = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)ptr, sizeof(T) * count);
+    if (e == cudaSuccess) p->bytes += sizeof(T) * count;
+    else cudaGetLastError();
+    return e;
+}
+
+void free_all(lc_plan* p) {
+    cudaFree(p->d_grid);
+    cudaFree(p->d_work);
+    cudaFree(p->d_ring);
+    cudaFree(p->d_slot_step);
+    cudaFree(p->d_slot_S);
+    cudaFree(p->d_slot_total);
+    cudaFree(p->d_tw);
+    cudaFree(p->d_err);
+    cudaFree(p->d_maxbits);
+    cudaFree(p->d_pos);
+    cudaFree(p->d_lum);
+    cudaFree(p->d_out_stage);
+    cudaFree(p->d_gw);
+    cudaFree(p->d_gtab);
+    cudaFree(p->d_bnd);
+    cudaFree(p->d_I);
+    cudaFree(p->d_scale);
+    for (auto& t : p->tables) {
+        cudaFree(t.ghat);
+        cudaFree(t.g0);
+    }
+    for (auto& m : p->marks) {
+        cudaEventDestroy(m.a);
+        cudaEventDestroy(m.b);
+    }
+    for (auto e : p->pool) cudaEventDestroy(e);
+}
+
+bool valid_steps(const lc_steps* st) {
+    if (!st || st->n_steps < 1 || st->n_steps > 100000) return false;
+    if (st->subsamples != 0 && (st->subsamples < 2 || st->subsamples > 16 || st->subsamples % 2)) return false;
+    if (st->history != LC_HISTORY_FP32 && st->history != LC_HISTORY_BF16) return false;
+    if (!(st->out_unit >= 0.0) || !isfinite(st->out_unit)) return false;
+    if (st->spacing == LC_STEPS_EQUAL_TIME && !(st->z_start > st->z_end && st->z_end >= 0.0)) return false;
+    if (st->spacing == LC_STEPS_EQUAL_TAU && (st->n_shell < 1 || !(st->z_end >= 0.0))) return false;
+    if (st->spacing == LC_STEPS_EXPLICIT && !st->z_edges) return false;
+    return st->spacing >= 0 && st->spacing <= 2;
+}
+
+bool valid_cosmo(const lc_cosmology* c) {
+    return c && c->omega_m > 0.0 && c->omega_m <= 1.0 && c->h > 0.0 && isfinite(c->h);
+}
+
+// Build the Ghat table of observing step s (steps 2-3 of Section 2.2).
+lc_status build_table(lc_plan* p, int s) {
+    lc_plan::Table& T = p->tables[s];
+    if (T.A >= 0) return LC_OK;
+    StepGeom g = step_geometry(p->cosmo, p->z, s, p->l, p->S, true);
+    const int A = g.A;
+    cudaError_t e = cudaSuccess;
+    if (A == 0) {
+        T.A = 0;
+        return LC_OK;
+    }
+    if (g.ntab > (1LL << 28)) return LC_ERR_UNSUPPORTED_SIZE;
+    // host table of g(R), with the s^-3 sample weight folded in
+    std::vector<double> gt((size_t)g.ntab);
+    g_table(p->cosmo, p->z[s + 1], p->l / (2.0 * p->S), g.ntab, gt.data());
+    const double inv_s3 = 1.0 / ((double)p->S * p->S * p->S);
+    for (auto& v : gt) v *= inv_s3;
+    // scratch
+    if ((long long)A * p->W > p->gw_cap) {
+        cudaFree(p->d_gw);
+        p->bytes -= sizeof(double) * p->gw_cap;
+        p->gw_cap = 0;
+        if ((e = dalloc(p, &p->d_gw, (size_t)A * p->W)) != cudaSuccess) return LC_ERR_OOM;
+        p->gw_cap = (long long)A * p->W;
+    }
+    if (g.ntab > p->gtab_cap) {
+        cudaFree(p->d_gtab);
+        p->bytes -= sizeof(double) * p->gtab_cap;
+        p->gtab_cap = 0;
+        if ((e = dalloc(p, &p->d_gtab, (size_t)g.ntab)) != cudaSuccess) return LC_ERR_OOM;
+        p->gtab_cap = g.ntab;
+    }
+    if (!p->d_bnd) {
+        const int cap = kMaxShells + 1;
+        if (dalloc(p, &p->d_bnd, cap) != cudaSuccess || dalloc(p, &p->d_I, cap) != cudaSuccess ||
+            dalloc(p, &p->d_scale, cap) != cudaSuccess)
+            return LC_ERR_OOM;
+    }
+    if (dalloc(p, &T.ghat, (size_t)p->W * A) != cudaSuccess) return LC_ERR_OOM;
+    if (dalloc(p, &T.g0, (size_t)A) != cudaSuccess) {
+        cudaFree(T.ghat);
+        T.ghat = nullptr;
+        return LC_ERR_OOM;
+    }
+    cudaStream_t st = p->stream;
+    e = cudaMemcpyAsync(p->d_gtab, gt.data(), sizeof(double) * g.ntab, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_bnd, g.bnd.data(), sizeof(long long) * (A + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_I, g.I.data(), sizeof(double) * A, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_gw, 0, sizeof(double) * (size_t)A * p->W, st);
+    if (e != cudaSuccess) return cuda_fail(p, e);
+    RgfAccumArgs ra;
+    ra.N = p->N;
+    ra.S = p->S;
+    ra.A = A;
+    ra.U = (int)ceil(g.rh / p->L) + 1;
+    ra.l = p->l;
+    ra.W = p->W;
+    ra.bnd = p->d_bnd;
+    ra.Rh = g.Rh;
+    ra.gtab = p->d_gtab;
+    ra.gw = p->d_gw;
+    ra.rh = g.rh;
+    launch_rgf_accum(ra, st);
+    launch_rgf_norm(p->N, p->W, A, p->d_gw, p->d_I, p->l * p->l * p->l, p->normalise, p->d_scale, T.g0, st);
+    count_launch(2 + 3ULL * A);
+    for (int j = 0; j < A; ++j) {
+        RowR2CArgs r{};
+        r.in_mode = ROW_IN_WEDGE;
+        r.nrows = (long long)p->N * p->N;
+        r.gw = p->d_gw + (size_t)j * p->W;
+        r.gscale = p->d_scale + j;
+        r.dst = p->d_work;
+        r.tw = p->d_tw;
+        p->ops->rows_r2c(r, st);
+        ColArgs c{};
+        c.axis = 0;
+        c.dir = -1;
+        c.in_mode = COL_IN_PLAIN;
+        c.out_mode = COL_OUT_PLAIN;
+        c.src = p->d_work;
+        c.dst = p->d_work;
+        c.tw = p->d_tw;
+        p->ops->cols(c, st);
+        c.axis = 1;
+        c.out_mode = COL_OUT_WEDGE;
+        c.wedge_out = T.ghat;
+        c.wedge_A = A;
+        c.wedge_j = j;
+        p->ops->cols(c, st);
+    }
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st); // host table gt must outlive the copy
+    if (e != cudaSuccess) return cuda_fail(p, e);
+    T.A = A;
+    return LC_OK;
+}
+
+lc_status ensure_sources(lc_plan* p, long long n) {
+    if (n <= p->src_cap) return LC_OK;
+    cudaFree(p->d_pos);
+    cudaFree(p->d_lum);
+    p->bytes -= sizeof(double) * 4 * p->src_cap;
+    p->src_cap = 0;
+    long long cap = 1024;
+    while (cap < n) cap *= 2;
+    if (dalloc(p, &p->d_pos, (size_t)cap * 3) != cudaSuccess || dalloc(p, &p->d_lum, (size_t)cap) != cudaSuccess) {
+        cudaFree(p->d_pos);
+        cudaFree(p->d_lum);
+        p->d_pos = p->d_lum = nullptr;
+        return LC_ERR_OOM;
+    }
+    p->src_cap = cap;
+    return LC_OK;
+}
+
+bool host_sources_ok(long long n, const double* pos, const double* lum) {
+    for (long long i = 0; i < n; ++i) {
+        if (!isfinite(lum[i]) || lum[i] < 0.0) return false;
+        if (!isfinite(pos[3 * i]) || !isfinite(pos[3 * i + 1]) || !isfinite(pos[3 * i + 2])) return false;
+    }
+    return true;
+}
+
+} // namespace
+
+extern "C" {
+
+const char* lc_status_string(lc_status s) {
+    switch (s) {
+    case LC_OK: return "ok";
+    case LC_ERR_INVALID_ARG: return "invalid argument";
+    case LC_ERR_UNSUPPORTED_SIZE: return "unsupported size";
+    case LC_ERR_STEP_ORDER: return "step order";
+    case LC_ERR_OOM: return "out of device memory";
+    case LC_ERR_CUDA: return "CUDA error";
+    case LC_ERR_TIMEOUT: return "device wait timed out";
+    case LC_ERR_DEVICE_CHECK: return "device-side input check failed";
+    }
+    return "unknown status";
+}
+
+lc_status lc_plan_estimate(int n, const lc_steps* steps, const lc_cosmology* cosmo, size_t* base_bytes,
+                           size_t* table_bytes_per_step) {
+    if (!ops_for(n) || !valid_steps(steps) || !valid_cosmo(cosmo)) return LC_ERR_INVALID_ARG;
+    Cosmo c{cosmo->omega_m, cosmo->h};
+    std::vector<double> z;
+    if (step_edges(c, *steps, z)) return LC_ERR_INVALID_ARG;
+    // ring depth from the last step's geometry (the largest horizon)
+    int ring = 1;
+    for (int s = steps->n_steps - 1; s >= 0 && s >= steps->n_steps - 2; --s) {
+        StepGeom g = step_geometry(c, z, s, 1.0, 2, false);
+        ring = g.A > ring ? g.A : ring;
+    }
+    const long long nrp = nrp_of(n), spec = (long long)n * n * nrp;
+    const long long hb = steps->history == LC_HISTORY_BF16 ? 4 : 8;
+    const long long W = (long long)(n / 2 + 1) * (n / 2 + 2) * (n / 2 + 3) / 6;
+    if (base_bytes) *base_bytes = (size_t)(8LL * n * n * n + 8 * spec + hb * spec * ring + 4LL * n * n * n);
+    if (table_bytes_per_step) *table_bytes_per_step = (size_t)(4 * W * ring + 8 * ring);
+    return LC_OK;
+}
+
+lc_status lc_plan_create(int n, double box_mpc, const lc_cosmology* cosmo, const lc_steps* steps, void* cuda_stream,
+                         lc_plan** out) {
+    if (!out) return LC_ERR_INVALID_ARG;
+    *out = nullptr;
+    const FftOps* ops = ops_for(n);
+    if (!ops) return LC_ERR_UNSUPPORTED_SIZE;
+    if (!(box_mpc > 0.0) || !isfinite(box_mpc) || !valid_cosmo(cosmo) || !valid_steps(steps))
+        return LC_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        return LC_ERR_CUDA;
+    }
+    lc_plan* p = new (std::nothrow) lc_plan();
+    if (!p) return LC_ERR_OOM;
+    p->N = n;
+    p->L = box_mpc;
+    p->l = box_mpc / n;
+    p->cosmo = Cosmo{cosmo->omega_m, cosmo->h};
+    p->n_steps = steps->n_steps;
+    p->S = steps->subsamples ? steps->subsamples : 4;
+    p->history = steps->history;
+    p->normalise = steps->normalise ? 1 : 0;
+    p->U = steps->out_unit > 0.0 ? steps->out_unit : 1.0;
+    p->stream = (cudaStream_t)cuda_stream;
+    p->ops = ops;
+    p->NRP = nrp_of(n);
+    p->spec_elems = (long long)n * n * p->NRP;
+    p->W = (long long)(n / 2 + 1) * (n / 2 + 2) * (n / 2 + 3) / 6;
+    if (step_edges(p->cosmo, *steps, p->z)) {
+        delete p;
+        return LC_ERR_INVALID_ARG;
+    }
+    // active slices per observing step -> ring depth
+    p->A_of_step.resize(p->n_steps);
+    for (int s = 0; s < p->n_steps; ++s) {
+        StepGeom g = step_geometry(p->cosmo, p->z, s, p->l, p->S, false);
+        if (g.A > kMaxShells) {
+            delete p;
+            return LC_ERR_UNSUPPORTED_SIZE;
+        }
+        if (g.ntab > (1LL << 28)) {
+            delete p;
+            return LC_ERR_UNSUPPORTED_SIZE;
+        }
+        p->A_of_step[s] = g.A;
+        if (g.A > p->n_ring) p->n_ring = g.A;
+    }
+    p->tables.resize(p->n_steps);
+    cudaError_t e = ensure_init(ops);
+    if (e != cudaSuccess) {
+        delete p;
+        return LC_ERR_CUDA;
+    }
+    const size_t N3 = (size_t)n * n * n;
+    const size_t hb = p->history == LC_HISTORY_BF16 ? 4 : 8;
+    bool ok = dalloc(p, &p->d_grid, N3) == cudaSuccess && dalloc(p, &p->d_work, (size_t)p->spec_elems) == cudaSuccess &&
+              dalloc(p, (char**)&p->d_ring, hb * (size_t)p->spec_elems * p->n_ring) == cudaSuccess &&
+              dalloc(p, &p->d_slot_step, p->n_ring) == cudaSuccess && dalloc(p, &p->d_slot_S, p->n_ring) == cudaSuccess &&
+              dalloc(p, &p->d_slot_total, p->n_ring) == cudaSuccess && dalloc(p, &p->d_tw, n) == cudaSuccess &&
+              dalloc(p, &p->d_err, 1) == cudaSuccess && dalloc(p, &p->d_maxbits, 1) == cudaSuccess;
+    if (!ok) {
+        free_all(p);
+        delete p;
+        return LC_ERR_OOM;
+    }
+    std::vector<float2> tw = twiddles(n);
+    e = cudaMemcpyAsync(p->d_tw, tw.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_slot_step, 0xff, sizeof(int) * p->n_ring, p->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_slot_total, 0, sizeof(long long) * p->n_ring, p->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_err, 0, sizeof(int), p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) {
+        free_all(p);
+        delete p;
+        return LC_ERR_CUDA;
+    }
+    *out = p;
+    return LC_OK;
+}
+
+lc_status lc_plan_prepare(lc_plan* p, int b, int e) {
+    if (!p) return LC_ERR_INVALID_ARG;
+    if (p->failed) return LC_ERR_CUDA;
+    if (b < 0 || e > p->n_steps || b > e) return LC_ERR_INVALID_ARG;
+    for (int s = b; s < e; ++s) {
+        lc_status r = build_table(p, s);
+        if (r != LC_OK) return r;
+    }
+    return LC_OK;
+}
+
+lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos, const double* lum) {
+    if (!p) return LC_ERR_INVALID_ARG;
+    if (p->failed) return LC_ERR_CUDA;
+    if (step < 0 || step >= p->n_steps || n_src < 0) return LC_ERR_INVALID_ARG;
+    if (n_src > 0 && (!pos || !lum)) return LC_ERR_INVALID_ARG;
+    if (step <= p->last_pushed) return LC_ERR_STEP_ORDER;
+    cudaStream_t st = p->stream;
+    const double* dpos = pos;
+    const double* dlum = lum;
+    cudaError_t e = cudaSuccess;
+    if (n_src > 0) {
+        const bool dp = is_device_ptr(pos), dl = is_device_ptr(lum);
+        if (!dp || !dl) {
+            if (!dp && !dl && !host_sources_ok(n_src, pos, lum)) return LC_ERR_INVALID_ARG;
+            lc_status r = ensure_sources(p, n_src);
+            if (r != LC_OK) return r;
+            e = cudaMemcpyAsync(p->d_pos, pos, sizeof(double) * 3 * n_src, dp ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(p->d_lum, lum, sizeof(double) * n_src, dl ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) return cuda_fail(p, e);
+            dpos = p->d_pos;
+            dlum = p->d_lum;
+        }
+    }
+    const int slot = step % p->n_ring;
+    SlotMeta m{slot, step, p->d_slot_step, p->d_slot_S, p->d_slot_total};
+    const long long N = p->N;
+    {
+        Phase ph(p, LC_PHASE_DEPOSIT, n_src > 0 ? 2 : 1);
+        e = cudaMemsetAsync(p->d_grid, 0, sizeof(long long) * N * N * N, st);
+        if (e != cudaSuccess) return cuda_fail(p, e);
+        launch_src_prep(dpos, dlum, n_src, p->d_maxbits, p->d_err, m, st);
+        if (n_src > 0) launch_deposit(dpos, dlum, n_src, p->N, p->l, p->d_maxbits, p->d_grid, m, st);
+    }
+    RowR2CArgs r{};
+    r.in_mode = ROW_IN_I64;
+    r.nrows = N * N;
+    r.grid = p->d_grid;
+    r.slot_S = p->d_slot_S;
+    r.slot_total = p->d_slot_total;
+    r.slot = slot;
+    r.bf16 = p->history == LC_HISTORY_BF16;
+    r.dst = p->d_work;
+    r.tw = p->d_tw;
+    {
+        Phase ph(p, LC_PHASE_R2C_Z, 1);
+        p->ops->rows_r2c(r, st);
+    }
+    ColArgs c{};
+    c.axis = 0;
+    c.dir = -1;
+    c.in_mode = COL_IN_PLAIN;
+    c.out_mode = COL_OUT_PLAIN;
+    c.src = p->d_work;
+    c.dst = p->d_work;
+    c.tw = p->d_tw;
+    {
+        Phase ph(p, LC_PHASE_FWD_Y, 1);
+        p->ops->cols(c, st);
+    }
+    c.axis = 1;
+    if (p->history == LC_HISTORY_BF16) {
+        c.out_mode = COL_OUT_BF16;
+        c.dst_bf16 = reinterpret_cast<__nv_bfloat162*>(p->d_ring) + (size_t)slot * p->spec_elems;
+    } else {
+        c.dst = reinterpret_cast<float2*>(p->d_ring) + (size_t)slot * p->spec_elems;
+    }
+    {
+        Phase ph(p, LC_PHASE_FWD_X_RING, 1);
+        p->ops->cols(c, st);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(p, e);
+    p->last_pushed = step;
+    return LC_OK;
+}
+
+lc_status lc_retarded_field(lc_plan* p, int step, float* out) {
+    if (!p || !out) return LC_ERR_INVALID_ARG;
+    if (p->failed) return LC_ERR_CUDA;
+    if (step < 0 || step >= p->n_steps) return LC_ERR_INVALID_ARG;
+    if (step != p->last_pushed) return LC_ERR_STEP_ORDER;
+    lc_status rs = build_table(p, step);
+    if (rs != LC_OK) return rs;
+    cudaStream_t st = p->stream;
+    const long long N = p->N, N3 = N * N * N;
+    const bool dev_out = is_device_ptr(out);
+    float* dout = out;
+    cudaError_t e = cudaSuccess;
+    if (!dev_out) {
+        if (!p->d_out_stage && dalloc(p, &p->d_out_stage, (size_t)N3) != cudaSuccess) return LC_ERR_OOM;
+        dout = p->d_out_stage;
+    }
+    const lc_plan::Table& T = p->tables[step];
+    if (T.A == 0) {
+        e = cudaMemsetAsync(dout, 0, sizeof(float) * N3, st);
+    } else {
+        ColArgs c{};
+        c.axis = 1;
+        c.dir = 1;
+        c.in_mode = p->history == LC_HISTORY_BF16 ? COL_IN_MAC_BF16 : COL_IN_MAC_F32;
+        c.out_mode = COL_OUT_PLAIN;
+        c.dst = p->d_work;
+        c.ring = p->d_ring;
+        c.slot_elems = p->spec_elems;
+        c.n_ring = p->n_ring;
+        c.step = step;
+        c.A = T.A;
+        c.slot_step = p->d_slot_step;
+        c.slot_S = p->d_slot_S;
+        c.slot_total = p->d_slot_total;
+        c.ghat = T.ghat;
+        c.g0 = T.g0;
+        c.tw = p->d_tw;
+        {
+            Phase ph(p, LC_PHASE_MAC_X, 1);
+            p->ops->cols(c, st);
+        }
+        c.axis = 0;
+        c.in_mode = COL_IN_PLAIN;
+        c.src = p->d_work;
+        {
+            Phase ph(p, LC_PHASE_INV_Y, 1);
+            p->ops->cols(c, st);
+        }
+        RowC2RArgs r{};
+        r.nrows = N * N;
+        r.src = p->d_work;
+        r.out = dout;
+        r.scale = (float)(p->U / (double)N3);
+        r.tw = p->d_tw;
+        {
+            Phase ph(p, LC_PHASE_C2R_Z, 1);
+            p->ops->rows_c2r(r, st);
+        }
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && !dev_out) {
+        e = cudaMemcpyAsync(out, dout, sizeof(float) * N3, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    return cuda_fail(p, e);
+}
+
+lc_status lc_plan_reset(lc_plan* p) {
+    if (!p) return LC_ERR_INVALID_ARG;
+    if (p->failed) return LC_ERR_CUDA;
+    cudaError_t e = cudaMemsetAsync(p->d_slot_step, 0xff, sizeof(int) * p->n_ring, p->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_slot_total, 0, sizeof(long long) * p->n_ring, p->stream);
+    if (e != cudaSuccess) return cuda_fail(p, e);
+    p->last_pushed = -1;
+    return LC_OK;
+}
+
+lc_status lc_plan_check(lc_plan* p) {
+    if (!p) return LC_ERR_INVALID_ARG;
+    if (p->failed) return LC_ERR_CUDA;
+    int err = 0;
+    cudaError_t e = cudaStreamSynchronize(p->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(p, e);
+    if (err) {
+        cudaMemset(p->d_err, 0, sizeof(int));
+        return LC_ERR_DEVICE_CHECK;
+    }
+    return LC_OK;
+}
+
+lc_status lc_plan_set_stream(lc_plan* p, void* s) {
+    if (!p) return LC_ERR_INVALID_ARG;
+    p->stream = (cudaStream_t)s;
+    return LC_OK;
+}
+
+lc_status lc_plan_destroy(lc_plan* p) {
+    if (!p) return LC_ERR_INVALID_ARG;
+    cudaStreamSynchronize(p->stream);
+    cudaGetLastError();
+    free_all(p);
+    delete p;
+    return LC_OK;
+}
+
+size_t lc_plan_device_bytes(const lc_plan* p) { return p ? p->bytes : 0; }
+
+lc_status lc_plan_set_timing(lc_plan* p, int enable) {
+    if (!p) return LC_ERR_INVALID_ARG;
+    p->timing = enable != 0;
+    return LC_OK;
+}
+
+lc_status lc_plan_timing(lc_plan* p, double* ms, int64_t* launches, int reset) {
+    if (!p) return LC_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return cuda_fail(p, e);
+    for (auto& m : p->marks) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, m.a, m.b) == cudaSuccess) p->ms[m.phase] += t;
+        else cudaGetLastError();
+        p->pool.push_back(m.a);
+        p->pool.push_back(m.b);
+    }
+    p->marks.clear();
+    for (int i = 0; i < LC_N_PHASES; ++i) {
+        if (ms) ms[i] = p->ms[i];
+        if (launches) launches[i] = p->launches[i];
+        if (reset) {
+            p->ms[i] = 0;
+            p->launches[i] = 0;
+        }
+    }
+    return LC_OK;
+}
+
+uint64_t lc_kernel_launches(void) { return g_launches.load(); }
+
+lc_status lc_step_shells(const lc_plan* p, int step, int* n_active, double* r_lo, double* r_hi, double* r_h,
+                         double* shell_integral) {
+    if (!p || step < 0 || step >= p->n_steps) return LC_ERR_INVALID_ARG;
+    StepGeom g = step_geometry(p->cosmo, p->z, step, p->l, p->S, shell_integral != nullptr);
+    if (n_active) *n_active = g.A;
+    for (int j = 0; j < g.A; ++j) {
+        if (r_lo) r_lo[j] = g.lo[j];
+        if (r_hi) r_hi[j] = g.hi[j];
+        if (shell_integral) shell_integral[j] = g.I[j];
+    }
+    if (r_h) *r_h = g.rh;
+    return LC_OK;
+}
+
+lc_status lc_plan_info(const lc_plan* p, lc_plan_info_t* info) {
+    if (!p || !info) return LC_ERR_INVALID_ARG;
+    info->n = p->N;
+    info->n_steps = p->n_steps;
+    info->n_ring = p->n_ring;
+    info->history = p->history;
+    info->wedge_size = (int)p->W;
+    info->spectrum_row = p->NRP;
+    info->box_mpc = p->L;
+    info->z_edges = p->z.data();
+    return LC_OK;
+}
+
+lc_status lc_plan_green_wedge(lc_plan* p, int step, int lookback, float* out, double* ghat0) {
+    if (!p || !out || step < 0 || step >= p->n_steps) return LC_ERR_INVALID_ARG;
+    if (p->failed) return LC_ERR_CUDA;
+    lc_status r = build_table(p, step);
+    if (r != LC_OK) return r;
+    const lc_plan::Table& T = p->tables[step];
+    if (lookback < 0 || lookback >= T.A) return LC_ERR_INVALID_ARG;
+    // strided column j of the [W][A] table
+    cudaError_t e = cudaMemcpy2DAsync(out, sizeof(float), T.ghat + lookback, sizeof(float) * T.A, sizeof(float),
+                                      (size_t)p->W, cudaMemcpyDefault, p->stream);
+    if (e == cudaSuccess && ghat0)
+        e = cudaMemcpyAsync(ghat0, T.g0 + lookback, sizeof(double), cudaMemcpyDefault, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    return cuda_fail(p, e);
+}
+
+// ------------------------------------------------------------ stand-alone kernels
+lc_status lc_deposit_grid(int n, double box, int64_t n_src, const double* pos, const double* lum, int64_t* grid,
+                          double* scale, int64_t* total, void* stream) {
+    if (n < 1 || n > 4096 || !(box > 0.0) || n_src < 0 || !grid || (n_src > 0 && (!pos || !lum)))
+        return LC_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    lc_plan tmp; // only for the allocation helper
+    const size_t N3 = (size_t)n * n * n;
+    double *dpos = nullptr, *dlum = nullptr, *dS = nullptr;
+    long long *dgrid = nullptr, *dtot = nullptr;
+    int *dstep = nullptr, *derr = nullptr;
+    unsigned long long* dmax = nullptr;
+    const bool pos_dev = n_src > 0 && is_device_ptr(pos), lum_dev = n_src > 0 && is_device_ptr(lum),
+               grid_dev = is_device_ptr(grid);
+    if (n_src > 0 && !pos_dev && !lum_dev && !host_sources_ok(n_src, pos, lum)) return LC_ERR_INVALID_ARG;
+    cudaError_t e = cudaSuccess;
+    auto cleanup = [&]() {
+        if (!pos_dev) cudaFree(dpos);
+        if (!lum_dev) cudaFree(dlum);
+        if (!grid_dev) cudaFree(dgrid);
+        cudaFree(dS);
+        cudaFree(dtot);
+        cudaFree(dstep);
+        cudaFree(derr);
+        cudaFree(dmax);
+    };
+    bool ok = true;
+    if (pos_dev) dpos = const_cast<double*>(pos);
+    else ok = ok && dalloc(&tmp, &dpos, (size_t)3 * n_src) == cudaSuccess;
+    if (lum_dev) dlum = const_cast<double*>(lum);
+    else ok = ok && dalloc(&tmp, &dlum, (size_t)n_src) == cudaSuccess;
+    if (grid_dev) dgrid = reinterpret_cast<long long*>(grid);
+    else ok = ok && dalloc(&tmp, &dgrid, N3) == cudaSuccess;
+    ok = ok && dalloc(&tmp, &dS, 1) == cudaSuccess && dalloc(&tmp, &dtot, 1) == cudaSuccess &&
+         dalloc(&tmp, &dstep, 1) == cudaSuccess && dalloc(&tmp, &derr, 1) == cudaSuccess &&
+         dalloc(&tmp, &dmax, 1) == cudaSuccess;
+    if (!ok) {
+        cleanup();
+        return LC_ERR_OOM;
+    }
+    if (n_src > 0 && !pos_dev) e = cudaMemcpyAsync(dpos, pos, sizeof(double) * 3 * n_src, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && n_src > 0 && !lum_dev)
+        e = cudaMemcpyAsync(dlum, lum, sizeof(double) * n_src, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dgrid, 0, sizeof(long long) * N3, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(derr, 0, sizeof(int), st);
+    SlotMeta m{0, 0, dstep, dS, dtot};
+    if (e == cudaSuccess) {
+        launch_src_prep(dpos, dlum, n_src, dmax, derr, m, st);
+        if (n_src > 0) launch_deposit(dpos, dlum, n_src, n, box / n, dmax, dgrid, m, st);
+        count_launch(n_src > 0 ? 2 : 1);
+        e = cudaGetLastError();
+    }
+    long long tot = 0;
+    double S = 1.0;
+    int err = 0;
+    if (e == cudaSuccess && !grid_dev)
+        e = cudaMemcpyAsync(grid, dgrid, sizeof(long long) * N3, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&tot, dtot, sizeof(long long), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&S, dS, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, derr, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cleanup();
+    if (e != cudaSuccess) return LC_ERR_CUDA;
+    if (scale) *scale = S;
+    if (total) *total = tot;
+    return err ? LC_ERR_DEVICE_CHECK : LC_OK;
+}
+
+static lc_status fft_common(int n, cudaStream_t st, float2** work, float2** tw) {
+    const FftOps* ops = ops_for(n);
+    if (!ops) return LC_ERR_UNSUPPORTED_SIZE;
+    if (ensure_init(ops) != cudaSuccess) return LC_ERR_CUDA;
+    lc_plan tmp;
+    const size_t spec = (size_t)n * n * nrp_of(n);
+    if (dalloc(&tmp, work, spec) != cudaSuccess) return LC_ERR_OOM;
+    if (dalloc(&tmp, tw, n) != cudaSuccess) {
+        cudaFree(*work);
+        return LC_ERR_OOM;
+    }
+    std::vector<float2> t = twiddles(n);
+    if (cudaMemcpyAsync(*tw, t.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaFree(*work);
+        cudaFree(*tw);
+        return LC_ERR_CUDA;
+    }
+    return LC_OK;
+}
+
+lc_status lc_fft_r2c(int n, const float* in, float* out_complex, void* stream) {
+    if (!in || !out_complex) return LC_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    float2 *work = nullptr, *tw = nullptr;
+    lc_status r = fft_common(n, st, &work, &tw);
+    if (r != LC_OK) return r;
+    const FftOps* ops = ops_for(n);
+    RowR2CArgs ra{};
+    ra.in_mode = ROW_IN_F32;
+    ra.nrows = (long long)n * n;
+    ra.fin = in;
+    ra.dst = work;
+    ra.tw = tw;
+    ops->rows_r2c(ra, st);
+    ColArgs c{};
+    c.axis = 0;
+    c.dir = -1;
+    c.in_mode = COL_IN_PLAIN;
+    c.out_mode = COL_OUT_PLAIN;
+    c.src = work;
+    c.dst = work;
+    c.tw = tw;
+    ops->cols(c, st);
+    c.axis = 1;
+    ops->cols(c, st);
+    count_launch(3);
+    const int h = n / 2 + 1;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(out_complex, sizeof(float2) * h, work, sizeof(float2) * nrp_of(n), sizeof(float2) * h,
+                              (size_t)n * n, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(work);
+    cudaFree(tw);
+    return e == cudaSuccess ? LC_OK : LC_ERR_CUDA;
+}
+
+lc_status lc_fft_c2r(int n, const float* in_complex, float* out, float scale, void* stream) {
+    if (!in_complex || !out) return LC_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    float2 *work = nullptr, *tw = nullptr;
+    lc_status r = fft_common(n, st, &work, &tw);
+    if (r != LC_OK) return r;
+    const FftOps* ops = ops_for(n);
+    const int h = n / 2 + 1;
+    cudaError_t e = cudaMemcpy2DAsync(work, sizeof(float2) * nrp_of(n), in_complex, sizeof(float2) * h,
+                                      sizeof(float2) * h, (size_t)n * n, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) {
+        ColArgs c{};
+        c.axis = 1;
+        c.dir = 1;
+        c.in_mode = COL_IN_PLAIN;
+        c.out_mode = COL_OUT_PLAIN;
+        c.src = work;
+        c.dst = work;
+        c.tw = tw;
+        ops->cols(c, st);
+        c.axis = 0;
+        ops->cols(c, st);
+        RowC2RArgs ra{};
+        ra.nrows = (long long)n * n;
+        ra.src = work;
+        ra.out = out;
+        ra.scale = scale;
+        ra.tw = tw;
+        ops->rows_c2r(ra, st);
+        count_launch(3);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(work);
+    cudaFree(tw);
+    return e == cudaSuccess ? LC_OK : LC_ERR_CUDA;
+}
+
+lc_status lc_batch_step(lc_plan* const* plans, int n, const int* steps, const int64_t* n_src,
+                        const double* const* pos, const double* const* lum, float* const* outs) {
+    if (!plans || n < 1 || !steps || !n_src || !outs) return LC_ERR_INVALID_ARG;
+    // phase 1: every instance's deposit + forward transform; phase 2: every
+    // instance's MAC + inverse transform.  Each plan runs on its own stream so
+    // that the uneven instances overlap on the device.
+    for (int i = 0; i < n; ++i) {
+        if (n_src[i] < 0) continue;
+        lc_status r = lc_push_sources(plans[i], steps[i], n_src[i], pos ? pos[i] : nullptr, lum ? lum[i] : nullptr);
+        if (r != LC_OK) return r;
+    }
+    for (int i = 0; i < n; ++i) {
+        lc_status r = lc_retarded_field(plans[i], steps[i], outs[i]);
+        if (r != LC_OK) return r;
+    }
+    return LC_OK;
+}
+
+} // extern "C"

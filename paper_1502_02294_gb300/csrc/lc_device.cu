@@ -1,0 +1,217 @@
+// lc_device.cu -- source deposit and Green's function builder kernels.
+//
+// Deposit (Eq. 11 with l^3 absorbed into f_n; Eq. 17 source term): nearest
+// grid point, integer fixed point.  The unit S = 2^(E - 62) with
+// n_src * max(L) < 2^E bounds every cell and the total below 2^62 + n_src/2;
+// q_s = rint(L_s / S) is added with 64-bit integer atomics, so the grid and
+// the total are bit-exact and independent of source order.
+//
+// Green's function builder (Eq. 10, step 2 of Section 2.2): for every cell
+// displacement on the symmetric wedge 0 <= a <= b <= c <= N/2, sum the LW
+// kernel g(r) (Eq. 17) over s^3 sub-cell samples and all periodic images of
+// the unit source; a sample with integer squared radius R (units of
+// (l / 2s)^2) belongs to shell j iff bnd[j] <= R < bnd[j+1] and counts iff
+// R <= Rh (the horizon).  g is read from a table indexed by (R - 3) / 8.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "lc_internal.h"
+
+namespace lc {
+namespace {
+
+constexpr int kPrepThreads = 1024;
+
+__device__ __forceinline__ bool finite_d(double x) { return isfinite(x); }
+
+__global__ void __launch_bounds__(kPrepThreads)
+    k_src_prep(const double* __restrict__ pos, const double* __restrict__ lum, long long n,
+               unsigned long long* maxbits, int* err, SlotMeta m) {
+    __shared__ unsigned long long s_max[kPrepThreads / 32];
+    __shared__ int s_bad;
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    unsigned long long mx = 0;
+    int bad = 0;
+    for (long long i = threadIdx.x; i < n; i += kPrepThreads) {
+        const double L = lum[i];
+        const bool ok = finite_d(L) && L >= 0.0 && finite_d(pos[3 * i]) && finite_d(pos[3 * i + 1]) &&
+                        finite_d(pos[3 * i + 2]);
+        if (!ok) bad = 1;
+        // non-negative doubles order like their bit patterns
+        else mx = max(mx, (unsigned long long)__double_as_longlong(L));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = mx;
+    if (bad) atomicOr(&s_bad, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long r = 0;
+        for (int w = 0; w < kPrepThreads / 32; ++w) r = max(r, s_max[w]);
+        *maxbits = r;
+        if (s_bad) atomicOr(err, 1);
+        m.slot_step[m.slot] = m.step;
+        m.slot_total[m.slot] = 0;
+        m.slot_S[m.slot] = 1.0; // replaced by the deposit's unit when there are sources
+    }
+}
+
+__device__ __forceinline__ long long ngp_cell(double x, double l, int N) {
+    // floor(x / l + 1/2) mod N in IEEE double (fmod is exact), no contraction
+    const double t = floor(__dadd_rn(__ddiv_rn(x, l), 0.5));
+    double m = fmod(t, (double)N);
+    if (m < 0.0) m += (double)N;
+    long long i = (long long)m;
+    return (i >= 0 && i < N) ? i : 0;
+}
+
+__global__ void __launch_bounds__(256)
+    k_deposit(const double* __restrict__ pos, const double* __restrict__ lum, long long n, int N, double l,
+              const unsigned long long* __restrict__ maxbits, long long* __restrict__ grid, SlotMeta m) {
+    __shared__ long long s_sum[8];
+    const double lmax = __longlong_as_double((long long)*maxbits);
+    double S = 1.0;
+    if (lmax > 0.0) {
+        int E;
+        frexp(__dmul_rn((double)n, lmax), &E);
+        S = ldexp(1.0, E - 62);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) m.slot_S[m.slot] = S;
+    long long q = 0;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const double L = lum[i];
+        const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+        if (finite_d(L) && L >= 0.0 && finite_d(x) && finite_d(y) && finite_d(z)) {
+            q = llrint(__ddiv_rn(L, S));
+            const long long c = (ngp_cell(x, l, N) * N + ngp_cell(y, l, N)) * N + ngp_cell(z, l, N);
+            if (q) atomicAdd(reinterpret_cast<unsigned long long*>(grid + c), (unsigned long long)q);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = q;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_sum[w];
+        if (t) atomicAdd(reinterpret_cast<unsigned long long*>(m.slot_total + m.slot), (unsigned long long)t);
+    }
+}
+
+// wedge index -> sorted triple a <= b <= c
+__device__ __forceinline__ void wedge_decode(long long w, int& a, int& b, int& c) {
+    int cc = (int)cbrt(6.0 * (double)w);
+    while ((long long)(cc + 1) * (cc + 2) * (cc + 3) / 6 <= w) ++cc;
+    while (cc > 0 && (long long)cc * (cc + 1) * (cc + 2) / 6 > w) --cc;
+    long long rem = w - (long long)cc * (cc + 1) * (cc + 2) / 6;
+    int bb = (int)((sqrt(8.0 * (double)rem + 1.0) - 1.0) * 0.5);
+    while ((long long)(bb + 1) * (bb + 2) / 2 <= rem) ++bb;
+    while (bb > 0 && (long long)bb * (bb + 1) / 2 > rem) --bb;
+    a = (int)(rem - (long long)bb * (bb + 1) / 2);
+    b = bb;
+    c = cc;
+}
+
+constexpr int kMaxBnd = 1025;
+
+__global__ void __launch_bounds__(128) k_rgf_accum(RgfAccumArgs a) {
+    __shared__ long long s_bnd[kMaxBnd];
+    for (int i = threadIdx.x; i <= a.A; i += blockDim.x) s_bnd[i] = a.bnd[i];
+    __syncthreads();
+    const long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= a.W) return;
+    int ia, ib, ic;
+    wedge_decode(w, ia, ib, ic);
+    const int N = a.N, S = a.S, U = a.U;
+    const double hd = 0.8660254037844386 * a.l;
+    const long long top = s_bnd[a.A];
+    for (int u = -U; u <= U; ++u)
+        for (int v = -U; v <= U; ++v)
+            for (int ww = -U; ww <= U; ++ww) {
+                const double cx = a.l * (ia + (double)u * N), cy = a.l * (ib + (double)v * N),
+                             cz = a.l * (ic + (double)ww * N);
+                if (sqrt(cx * cx + cy * cy + cz * cz) - hd > a.rh) continue;
+                const long long bx = 2LL * S * (ia + (long long)u * N) + 1 - S;
+                const long long by = 2LL * S * (ib + (long long)v * N) + 1 - S;
+                const long long bz = 2LL * S * (ic + (long long)ww * N) + 1 - S;
+                for (int sa = 0; sa < S; ++sa) {
+                    const long long mx = bx + 2 * sa, mx2 = mx * mx;
+                    for (int sb = 0; sb < S; ++sb) {
+                        const long long my = by + 2 * sb, mxy = mx2 + my * my;
+                        for (int sc = 0; sc < S; ++sc) {
+                            const long long mz = bz + 2 * sc;
+                            const long long R = mxy + mz * mz;
+                            if (R > a.Rh || R >= top || R < s_bnd[0]) continue;
+                            int lo = 0, hi = a.A;
+                            while (hi - lo > 1) {
+                                const int mid = (lo + hi) >> 1;
+                                if (s_bnd[mid] <= R) lo = mid;
+                                else hi = mid;
+                            }
+                            a.gw[(long long)lo * a.W + w] += a.gtab[(R - 3) >> 3];
+                        }
+                    }
+                }
+            }
+}
+
+__global__ void __launch_bounds__(256) k_rgf_norm(int N, long long W, int A, const double* __restrict__ gw,
+                                                  const double* __restrict__ I, double l3, int normalise,
+                                                  double* scale, double* g0) {
+    // block j: sum over the full grid = sum over the wedge with multiplicity
+    // (number of distinct permutations) x prod over axes (1 at 0 and N/2, else 2)
+    __shared__ double s_part[256];
+    const int j = blockIdx.x;
+    const int M = N / 2;
+    double acc = 0.0;
+    for (long long w = threadIdx.x; w < W; w += blockDim.x) {
+        int a, b, c;
+        wedge_decode(w, a, b, c);
+        const int perms = (a == b && b == c) ? 1 : (a == b || b == c) ? 3 : 6;
+        const double ax = (a == 0 || a == M) ? 1.0 : 2.0, bx = (b == 0 || b == M) ? 1.0 : 2.0,
+                     cx = (c == 0 || c == M) ? 1.0 : 2.0;
+        acc += perms * ax * bx * cx * gw[(long long)j * W + w];
+    }
+    s_part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) s_part[threadIdx.x] += s_part[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        // gw already carries the s^-3 sample weight (folded into the g table)
+        const double sum = s_part[0];
+        if (normalise && sum > 0.0) {
+            scale[j] = I[j] / (l3 * sum);
+            g0[j] = I[j] / l3;
+        } else {
+            scale[j] = 1.0;
+            g0[j] = sum;
+        }
+    }
+}
+
+} // namespace
+
+void launch_src_prep(const double* pos, const double* lum, long long n, unsigned long long* maxbits, int* err,
+                     SlotMeta m, cudaStream_t st) {
+    k_src_prep<<<1, kPrepThreads, 0, st>>>(pos, lum, n, maxbits, err, m);
+}
+
+void launch_deposit(const double* pos, const double* lum, long long n, int N, double l,
+                    const unsigned long long* maxbits, long long* grid, SlotMeta m, cudaStream_t st) {
+    const long long blocks = n > 0 ? (n + 255) / 256 : 1;
+    k_deposit<<<(unsigned)blocks, 256, 0, st>>>(pos, lum, n, N, l, maxbits, grid, m);
+}
+
+void launch_rgf_accum(const RgfAccumArgs& a, cudaStream_t st) {
+    if (a.W <= 0) return;
+    k_rgf_accum<<<(unsigned)((a.W + 127) / 128), 128, 0, st>>>(a);
+}
+
+void launch_rgf_norm(int N, long long W, int A, const double* gw, const double* I, double l3, int normalise,
+                     double* scale, double* g0, cudaStream_t st) {
+    k_rgf_norm<<<A, 256, 0, st>>>(N, W, A, gw, I, l3, normalise, scale, g0);
+}
+
+} // namespace lc

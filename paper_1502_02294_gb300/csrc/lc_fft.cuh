@@ -1,0 +1,213 @@
+// lc_fft.cuh -- shared-memory mixed-radix FFT building blocks for sm_103a.
+//
+// The transforms of Eq. 12 (forward e^{-2 pi i k.x/N}, unnormalised; inverse
+// e^{+2 pi i k.x/N}) are done as three axis passes over a half spectrum
+// [p][q][r], r in [0, N/2], rows padded to NRP complex so that every row and
+// every 16-column chunk starts on a 32-byte sector.
+//
+// One CTA holds B independent length-N transforms in shared memory as
+// buf[t * BP + b] (transform b, element t; BP odd so that both the strided
+// Stockham loads and the contiguous stores are bank-conflict free).  A
+// radix-R stage loads every butterfly's R inputs into registers, waits,
+// twiddles, applies the R-point DFT and stores in place (Stockham autosort:
+// natural order in and out, no bit reversal).  Twiddles come from a table of
+// W_N^m = e^{-2 pi i m / N}, computed in FP64 on the host.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace lc {
+
+constexpr int kThreads = 256;
+
+__host__ __device__ constexpr int nrp_of(int n) { return ((n / 2 + 1) + 7) / 8 * 8; }
+__host__ __device__ constexpr int cw_of(int n) { return n / 2 < 16 ? n / 2 : 16; }
+// pairs of real rows per CTA in the z (row) passes
+__host__ __device__ constexpr int row_pairs_of(int n) {
+    return n <= 8 ? 32 : n <= 16 ? 32 : n <= 32 ? 32 : n <= 64 ? 32 : n <= 128 ? 16 : n <= 256 ? 8 : 4;
+}
+__host__ __device__ constexpr int odd_pad(int b) { return (b % 2 == 0) ? b + 1 : b; }
+
+// Radix plan: stages applied in order R0, R1, R2 (1 = unused).
+template <int N> struct Plan;
+template <> struct Plan<8> { static constexpr int R0 = 8, R1 = 1, R2 = 1; };
+template <> struct Plan<16> { static constexpr int R0 = 16, R1 = 1, R2 = 1; };
+template <> struct Plan<32> { static constexpr int R0 = 8, R1 = 4, R2 = 1; };
+template <> struct Plan<64> { static constexpr int R0 = 8, R1 = 8, R2 = 1; };
+template <> struct Plan<96> { static constexpr int R0 = 8, R1 = 4, R2 = 3; };
+template <> struct Plan<128> { static constexpr int R0 = 16, R1 = 8, R2 = 1; };
+template <> struct Plan<192> { static constexpr int R0 = 8, R1 = 8, R2 = 3; };
+template <> struct Plan<256> { static constexpr int R0 = 16, R1 = 16, R2 = 1; };
+template <> struct Plan<384> { static constexpr int R0 = 16, R1 = 8, R2 = 3; };
+template <> struct Plan<512> { static constexpr int R0 = 8, R1 = 8, R2 = 8; };
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// multiply by DIR * i  (DIR = -1 forward, +1 inverse)
+template <int DIR> __device__ __forceinline__ float2 mul_i(float2 a) {
+    return DIR < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+}
+
+// ---- small DFTs in registers: y_k = sum_n v_n e^{DIR 2 pi i n k / R} ----
+template <int DIR> __device__ __forceinline__ void dft2(float2& a, float2& b) {
+    float2 t = csub(a, b);
+    a = cadd(a, b);
+    b = t;
+}
+
+template <int DIR> __device__ __forceinline__ void dft3(float2* v) {
+    const float h = 0.86602540378443864676f; // sqrt(3)/2
+    float2 t = cadd(v[1], v[2]);
+    float2 d = mul_i<DIR>(cscale(csub(v[1], v[2]), h));
+    float2 m = make_float2(v[0].x - 0.5f * t.x, v[0].y - 0.5f * t.y);
+    v[0] = cadd(v[0], t);
+    v[1] = cadd(m, d);
+    v[2] = csub(m, d);
+}
+
+// 4-point DFT on v[s*0], v[s*1], v[s*2], v[s*3]
+template <int DIR, int S = 1> __device__ __forceinline__ void dft4(float2* v) {
+    float2 t0 = cadd(v[0], v[2 * S]), t1 = csub(v[0], v[2 * S]);
+    float2 t2 = cadd(v[S], v[3 * S]), t3 = mul_i<DIR>(csub(v[S], v[3 * S]));
+    v[0] = cadd(t0, t2);
+    v[2 * S] = csub(t0, t2);
+    v[S] = cadd(t1, t3);
+    v[3 * S] = csub(t1, t3);
+}
+
+template <int DIR> __device__ __forceinline__ void dft8(float2* v) {
+    const float c = 0.70710678118654752440f;
+    // even / odd halves
+    float2 e[4] = {v[0], v[2], v[4], v[6]};
+    float2 o[4] = {v[1], v[3], v[5], v[7]};
+    dft4<DIR>(e);
+    dft4<DIR>(o);
+    // W8^1 = c (1 + DIR i), W8^2 = DIR i, W8^3 = c (-1 + DIR i)
+    float2 w1 = cscale(cadd(o[1], mul_i<DIR>(o[1])), c);
+    float2 w2 = mul_i<DIR>(o[2]);
+    float2 w3 = cscale(csub(mul_i<DIR>(o[3]), o[3]), c);
+    v[0] = cadd(e[0], o[0]);
+    v[4] = csub(e[0], o[0]);
+    v[1] = cadd(e[1], w1);
+    v[5] = csub(e[1], w1);
+    v[2] = cadd(e[2], w2);
+    v[6] = csub(e[2], w2);
+    v[3] = cadd(e[3], w3);
+    v[7] = csub(e[3], w3);
+}
+
+// 16-point DFT as 4 x 4: n = 4a + b, k = k1 + 4 k2
+template <int DIR> __device__ __forceinline__ void dft16(float2* v) {
+    const float c1 = 0.92387953251128675613f, s1 = 0.38268343236508977173f, c2 = 0.70710678118654752440f;
+    // inner DFT4 over a for each b (stride 4 in v)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) dft4<DIR, 4>(v + b);
+    // now v[4*k1 + b] = X_b[k1]; twiddle by W16^{b k1} with W16 = e^{DIR 2 pi i / 16}
+    const float ds = (float)DIR;
+    // W16^m for m = 1..9 : (cos(2 pi m/16), DIR sin(2 pi m / 16))
+    const float2 w1 = make_float2(c1, ds * s1), w2 = make_float2(c2, ds * c2), w3 = make_float2(s1, ds * c1);
+    const float2 w6 = make_float2(-c2, ds * c2), w9 = make_float2(-c1, -ds * s1);
+    v[4 * 1 + 1] = cmul(v[5], w1);
+    v[4 * 1 + 2] = cmul(v[6], w2);
+    v[4 * 1 + 3] = cmul(v[7], w3);
+    v[4 * 2 + 1] = cmul(v[9], w2);
+    v[4 * 2 + 2] = mul_i<DIR>(v[10]);
+    v[4 * 2 + 3] = cmul(v[11], w6);
+    v[4 * 3 + 1] = cmul(v[13], w3);
+    v[4 * 3 + 2] = cmul(v[14], w6);
+    v[4 * 3 + 3] = cmul(v[15], w9);
+    // outer DFT4 over b for each k1 (contiguous groups of 4)
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4<DIR, 1>(v + 4 * k1);
+    // v[4 k1 + k2] = y[k1 + 4 k2]: transpose 4x4 into natural order
+    float2 t[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) t[i] = v[i];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[4 * k1 + k2];
+}
+
+template <int R, int DIR> __device__ __forceinline__ void dft(float2* v) {
+    if constexpr (R == 2) dft2<DIR>(v[0], v[1]);
+    else if constexpr (R == 3) dft3<DIR>(v);
+    else if constexpr (R == 4) dft4<DIR>(v);
+    else if constexpr (R == 8) dft8<DIR>(v);
+    else if constexpr (R == 16) dft16<DIR>(v);
+}
+
+// One in-place Stockham stage of radix R at span NS over B transforms.
+template <int N, int R, int NS, int DIR, int B, int BP>
+__device__ __forceinline__ void stage(float2* __restrict__ buf, const float2* __restrict__ tw) {
+    constexpr int NB = N / R;
+    constexpr int ITEMS = NB * B;
+    constexpr int K = (ITEMS + kThreads - 1) / kThreads;
+    float2 v[K][R];
+#pragma unroll
+    for (int it = 0; it < K; ++it) {
+        const int e = threadIdx.x + it * kThreads;
+        if (ITEMS % kThreads == 0 || e < ITEMS) {
+            const int b = e % B, j = e / B;
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[it][r] = buf[(j + r * NB) * BP + b];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < K; ++it) {
+        const int e = threadIdx.x + it * kThreads;
+        if (ITEMS % kThreads == 0 || e < ITEMS) {
+            const int b = e % B, j = e / B;
+            const int k = j % NS;
+            if constexpr (NS > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    float2 w = tw[r * k * (N / (NS * R))];
+                    if (DIR > 0) w.y = -w.y;
+                    v[it][r] = cmul(v[it][r], w);
+                }
+            }
+            dft<R, DIR>(v[it]);
+            const int base = (j / NS) * NS * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf[(base + r * NS) * BP + b] = v[it][r];
+        }
+    }
+    __syncthreads();
+}
+
+// Full length-N transform of the B transforms held in buf (natural order).
+template <int N, int DIR, int B, int BP>
+__device__ __forceinline__ void fft_smem(float2* __restrict__ buf, const float2* __restrict__ tw) {
+    using P = Plan<N>;
+    stage<N, P::R0, 1, DIR, B, BP>(buf, tw);
+    if constexpr (P::R1 > 1) stage<N, P::R1, P::R0, DIR, B, BP>(buf, tw);
+    if constexpr (P::R2 > 1) stage<N, P::R2, P::R0 * P::R1, DIR, B, BP>(buf, tw);
+}
+
+// Symmetric-wedge index of a sorted triple a <= b <= c: C(c+2,3) + C(b+1,2) + a.
+__host__ __device__ __forceinline__ long long wedge_index(int a, int b, int c) {
+    return (long long)c * (c + 1) * (c + 2) / 6 + (long long)b * (b + 1) / 2 + a;
+}
+__device__ __forceinline__ void sort3(int& a, int& b, int& c) {
+    int t;
+    if (a > b) { t = a; a = b; b = t; }
+    if (b > c) { t = b; b = c; c = t; }
+    if (a > b) { t = a; a = b; b = t; }
+}
+// Wedge index of an arbitrary (p, q, r) on an N grid (fold to [0, N/2], sort).
+__device__ __forceinline__ long long wedge_of(int p, int q, int r, int n) {
+    int a = p <= n - p ? p : n - p;
+    int b = q <= n - q ? q : n - q;
+    int c = r <= n - r ? r : n - r;
+    sort3(a, b, c);
+    return wedge_index(a, b, c);
+}
+
+} // namespace lc

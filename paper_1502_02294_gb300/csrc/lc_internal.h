@@ -1,0 +1,69 @@
+// lc_internal.h -- host planner and device-kernel launchers shared by the
+// translation units of liblc (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/lc.h"
+
+namespace lc {
+
+// ---------------- host FP64 planner (lc_host.cpp) ----------------
+struct Cosmo {
+    double om, h;
+};
+double hubble(const Cosmo& c, double z);                // km/s/Mpc
+double chi(const Cosmo& c, double z1, double z2);       // comoving Mpc, Eq. 6
+double time_myr(const Cosmo& c, double z);              // cosmic time, closed form
+double z_of_time(const Cosmo& c, double t_myr);
+double zs_of_r(const Cosmo& c, double z_obs, double r); // chi(z_obs, z_s) = r
+double alpha_lw(const Cosmo& c, double zs);             // Eq. 16
+double fmod_lw(double r, double alpha);                 // Eq. 15
+double horizon(const Cosmo& c, double z_obs);           // r / alpha(z_s(r)) = 97.39
+double shell_integral(const Cosmo& c, double z_obs, double r_lo, double r_hi, double r_h);
+int step_edges(const Cosmo& c, const lc_steps& st, std::vector<double>& z);
+// g(r) = (1+z_obs)^3 f_mod / ((4 pi)^2 (1+z_s) r^2) at r = delta sqrt(8 t + 3), t < ntab
+void g_table(const Cosmo& c, double z_obs, double delta, long long ntab, double* out);
+
+struct StepGeom {
+    int A = 0;                 // active slices (lookback j = 0 .. A-1)
+    std::vector<double> lo, hi, I;
+    double rh = 0;
+    std::vector<long long> bnd; // A + 1 integer shell boundaries in units of delta^2
+    long long Rh = 0;           // largest admissible R inside the horizon
+    long long ntab = 0;
+};
+StepGeom step_geometry(const Cosmo& c, const std::vector<double>& z, int s, double l, int S, bool integrals);
+
+// ---------------- device kernels (lc_device.cu) ----------------
+struct SlotMeta {
+    int slot, step;
+    int* slot_step;
+    double* slot_S;
+    long long* slot_total;
+};
+// Validates sources and records max(lum) bits; marks the slot (step, total = 0).
+void launch_src_prep(const double* pos, const double* lum, long long n, unsigned long long* maxbits, int* err,
+                     SlotMeta m, cudaStream_t st);
+// Fixed-point NGP deposit into grid (int64, pre-zeroed), total into slot_total.
+void launch_deposit(const double* pos, const double* lum, long long n, int N, double l,
+                    const unsigned long long* maxbits, long long* grid, SlotMeta m, cudaStream_t st);
+
+struct RgfAccumArgs {
+    int N, S, A, U;
+    double l;
+    long long W;
+    const long long* bnd;
+    long long Rh;
+    const double* gtab;
+    double* gw; // [A][W]
+    double rh;
+};
+void launch_rgf_accum(const RgfAccumArgs& a, cudaStream_t st);
+// per shell: full-grid sum with multiplicities -> scale (normalisation) and Ghat(0)
+void launch_rgf_norm(int N, long long W, int A, const double* gw, const double* I, double l3, int normalise,
+                     double* scale, double* g0, cudaStream_t st);
+
+} // namespace lc

@@ -1,0 +1,326 @@
+// lc_kernels.cuh -- the per-grid-size FFT pass kernels of the retarded-field
+// path (templated on N, instantiated once per supported N).
+//
+//  k_rows_r2c : z-axis real->complex rows (Eq. 12 forward), prologue reads the
+//               int64 fixed-point deposit grid (source term f_n, Eq. 11), a
+//               float grid, or gathers a Green's function from its wedge.
+//  k_cols     : y- or x-axis complex pass over 16-column tiles.  Fused modes:
+//                 forward x-pass epilogue -> history ring slot (FP32 / BF16),
+//                 forward x-pass epilogue -> real part on the symmetric wedge
+//                   (the stored Ghat_n of step 3, Section 2.2),
+//                 inverse x-pass prologue -> the shell multiply-accumulate
+//                   Jhat(k) = sum_n Ghat_n(k) fhat_{s-n}(k)  (Eq. 13 summed
+//                   over slices, steps 5-6) with the k = 0 mode overwritten
+//                   by its FP64 value.
+//  k_rows_c2r : z-axis complex->real rows (Eq. 12 inverse) with the output
+//               scale U / N^3 fused.
+#pragma once
+#include "lc_fft.cuh"
+
+namespace lc {
+
+enum { ROW_IN_I64 = 0, ROW_IN_F32 = 1, ROW_IN_WEDGE = 2 };
+enum { COL_IN_PLAIN = 0, COL_IN_MAC_F32 = 1, COL_IN_MAC_BF16 = 2 };
+enum { COL_OUT_PLAIN = 0, COL_OUT_BF16 = 1, COL_OUT_WEDGE = 2 };
+
+struct RowR2CArgs {
+    int in_mode;
+    long long nrows;
+    const long long* grid;    // ROW_IN_I64: N^3 int64
+    const double* slot_S;     // ROW_IN_I64: fixed-point unit of the slot
+    const long long* slot_total;
+    int slot;
+    int bf16;                 // ROW_IN_I64: 1 -> values / (S * total), else * S
+    const float* fin;         // ROW_IN_F32
+    const double* gw;         // ROW_IN_WEDGE: wedge values of one shell (FP64)
+    const double* gscale;     // ROW_IN_WEDGE: that shell's normalisation factor
+    float2* dst;              // half spectrum, rows of NRP
+    const float2* tw;
+};
+
+struct ColArgs {
+    int axis;                 // 0: y-pass, 1: x-pass
+    int in_mode, out_mode, dir;
+    const float2* src;
+    float2* dst;
+    __nv_bfloat162* dst_bf16;
+    // shell MAC (inverse x-pass)
+    const void* ring;
+    long long slot_elems;     // complex elements per ring slot
+    int n_ring, step, A;
+    const int* slot_step;
+    const double* slot_S;
+    const long long* slot_total;
+    const float* ghat;        // [wedge][A] real Ghat of this step
+    const double* g0;         // [A] FP64 Ghat_j(0)
+    // wedge extract (forward x-pass of a Green's function)
+    float* wedge_out;
+    int wedge_A, wedge_j;
+    const float2* tw;
+};
+
+struct RowC2RArgs {
+    long long nrows;
+    const float2* src;
+    float* out;
+    float scale;
+    const float2* tw;
+};
+
+constexpr int kMaxShells = 1024;
+
+template <int N> __host__ __device__ constexpr size_t rows_smem_bytes() {
+    return sizeof(float2) * (N + (size_t)N * odd_pad(row_pairs_of(N)));
+}
+template <int N> __host__ __device__ constexpr size_t cols_smem_bytes() {
+    return sizeof(float2) * (N + (size_t)N * odd_pad(cw_of(N))) + (size_t)kMaxShells * 16 + 16;
+}
+
+// ------------------------------------------------------------------------
+template <int N, int IN>
+__global__ void __launch_bounds__(kThreads) k_rows_r2c(RowR2CArgs a) {
+    constexpr int B = row_pairs_of(N), BP = odd_pad(B), NRP = nrp_of(N), H = N / 2 + 1;
+    extern __shared__ float4 smem_raw[];
+    float2* tw = reinterpret_cast<float2*>(smem_raw);
+    float2* buf = tw + N;
+    for (int i = threadIdx.x; i < N; i += kThreads) tw[i] = a.tw[i];
+    float scale = 1.0f;
+    double gsc = 1.0;
+    if constexpr (IN == ROW_IN_I64) {
+        const double S = a.slot_S[a.slot];
+        const long long tot = a.slot_total[a.slot];
+        // FP32 history: luminosity units (S is a power of two: exact);
+        // BF16 history: divided by the total so that |fhat| <= 1.
+        scale = a.bf16 ? (tot > 0 ? (float)(1.0 / (double)tot) : 0.0f) : (float)S;
+    }
+    if constexpr (IN == ROW_IN_WEDGE) gsc = *a.gscale;
+    const long long row0 = (long long)blockIdx.x * (2 * B);
+    float* bf = reinterpret_cast<float*>(buf);
+    for (int idx = threadIdx.x; idx < 2 * B * N; idx += kThreads) {
+        const int rr = idx / N, t = idx % N;
+        const long long grow = row0 + rr;
+        float val = 0.0f;
+        if (grow < a.nrows) {
+            if constexpr (IN == ROW_IN_I64) val = __ll2float_rn(a.grid[grow * N + t]) * scale;
+            else if constexpr (IN == ROW_IN_F32) val = a.fin[grow * N + t];
+            else {
+                const int x = (int)(grow / N), y = (int)(grow % N);
+                val = (float)(a.gw[wedge_of(x, y, t, N)] * gsc);
+            }
+        }
+        bf[2 * (t * BP + (rr >> 1)) + (rr & 1)] = val;
+    }
+    __syncthreads();
+    fft_smem<N, -1, B, BP>(buf, tw);
+    // unpack the two real rows of each pair: X_a = (Z_k + conj Z_{N-k}) / 2,
+    // X_b = (Z_k - conj Z_{N-k}) / (2i)
+    for (int idx = threadIdx.x; idx < 2 * B * H; idx += kThreads) {
+        const int rr = idx / H, k = idx % H;
+        const long long grow = row0 + rr;
+        if (grow >= a.nrows) continue;
+        const int pair = rr >> 1;
+        const float2 zk = buf[k * BP + pair];
+        const float2 zn = buf[(k == 0 ? 0 : N - k) * BP + pair];
+        float2 x;
+        if ((rr & 1) == 0) x = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
+        else x = make_float2(0.5f * (zk.y + zn.y), 0.5f * (zn.x - zk.x));
+        a.dst[grow * NRP + k] = x;
+    }
+}
+
+// ------------------------------------------------------------------------
+template <int N, int DIR, int IN, int OUT>
+__global__ void __launch_bounds__(kThreads) k_cols(ColArgs a) {
+    constexpr int CW = cw_of(N), BP = odd_pad(CW), NRP = nrp_of(N), M = N / 2, NCH = M / CW;
+    constexpr long long PLANE = (long long)N * NRP;
+    extern __shared__ float4 smem_raw[];
+    float2* tw = reinterpret_cast<float2*>(smem_raw);
+    float2* buf = tw + N;
+    long long* s_off = reinterpret_cast<long long*>(buf + N * BP);
+    int* s_j = reinterpret_cast<int*>(s_off + kMaxShells);
+    float* s_D = reinterpret_cast<float*>(s_j + kMaxShells);
+    __shared__ int s_nv;
+    __shared__ double s_dc;
+
+    for (int i = threadIdx.x; i < N; i += kThreads) tw[i] = a.tw[i];
+
+    const int tile = blockIdx.x;
+    const bool nyq = tile >= N * NCH;
+    int line = 0, chunk = 0;
+    long long base, ts, cs;
+    if (!nyq) {
+        line = tile / NCH;
+        chunk = tile % NCH;
+        if (a.axis == 0) { base = line * PLANE + chunk * CW; ts = NRP; cs = 1; }
+        else { base = (long long)line * NRP + chunk * CW; ts = PLANE; cs = 1; }
+    } else {
+        line = (tile - N * NCH) * CW; // first of CW lines, column r = N/2
+        if (a.axis == 0) { base = line * PLANE + M; ts = NRP; cs = PLANE; }
+        else { base = (long long)line * NRP + M; ts = PLANE; cs = NRP; }
+    }
+
+    bool dc_tile = false;
+    if constexpr (IN != COL_IN_PLAIN) {
+        // compact list of the ring slots that hold the slices of this step
+        dc_tile = (a.axis == 1) && !nyq && line == 0 && chunk == 0;
+        if (threadIdx.x == 0) {
+            int nv = 0;
+            double dc = 0.0;
+            for (int j = 0; j < a.A; ++j) {
+                const int n = a.step - j;
+                if (n < 0) break;
+                const int slot = n % a.n_ring;
+                if (a.slot_step[slot] != n) continue;
+                const long long tot = a.slot_total[slot];
+                if (tot == 0) continue;
+                const double lum = a.slot_S[slot] * (double)tot;
+                s_off[nv] = (long long)slot * a.slot_elems;
+                s_j[nv] = j;
+                s_D[nv] = (IN == COL_IN_MAC_BF16) ? (float)lum : 1.0f;
+                dc += a.g0[j] * lum;
+                ++nv;
+            }
+            s_nv = nv;
+            s_dc = dc;
+        }
+    }
+    __syncthreads();
+
+    for (int idx = threadIdx.x; idx < N * CW; idx += kThreads) {
+        const int t = idx / CW, col = idx % CW;
+        const long long addr = base + t * ts + col * cs;
+        float2 val;
+        if constexpr (IN == COL_IN_PLAIN) {
+            val = a.src[addr];
+        } else {
+            // k = (p, q, r) of this element (x-pass: t runs over p)
+            const int p = t;
+            const int q = nyq ? line + col : line;
+            const int r = nyq ? M : chunk * CW + col;
+            const float* g = a.ghat + wedge_of(p, q, r, N) * a.A;
+            float2 acc = make_float2(0.f, 0.f);
+            const int nv = s_nv;
+            for (int v = 0; v < nv; ++v) {
+                float2 f;
+                if constexpr (IN == COL_IN_MAC_F32) {
+                    f = reinterpret_cast<const float2*>(a.ring)[s_off[v] + addr];
+                } else {
+                    f = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(a.ring)[s_off[v] + addr]);
+                }
+                const float gv = __ldg(g + s_j[v]) * s_D[v];
+                acc.x = fmaf(gv, f.x, acc.x);
+                acc.y = fmaf(gv, f.y, acc.y);
+            }
+            val = acc;
+            if (dc_tile && idx == 0) val = make_float2((float)s_dc, 0.0f);
+        }
+        buf[t * BP + col] = val;
+    }
+    __syncthreads();
+    fft_smem<N, DIR, CW, BP>(buf, tw);
+    for (int idx = threadIdx.x; idx < N * CW; idx += kThreads) {
+        const int t = idx / CW, col = idx % CW;
+        const long long addr = base + t * ts + col * cs;
+        const float2 v = buf[t * BP + col];
+        if constexpr (OUT == COL_OUT_PLAIN) {
+            a.dst[addr] = v;
+        } else if constexpr (OUT == COL_OUT_BF16) {
+            a.dst_bf16[addr] = __floats2bfloat162_rn(v.x, v.y);
+        } else {
+            const int p = t;
+            const int q = nyq ? line + col : line;
+            const int r = nyq ? M : chunk * CW + col;
+            if (p <= q && q <= r) a.wedge_out[wedge_index(p, q, r) * a.wedge_A + a.wedge_j] = v.x;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(kThreads) k_rows_c2r(RowC2RArgs a) {
+    constexpr int B = row_pairs_of(N), BP = odd_pad(B), NRP = nrp_of(N), H = N / 2 + 1;
+    extern __shared__ float4 smem_raw[];
+    float2* tw = reinterpret_cast<float2*>(smem_raw);
+    float2* buf = tw + N;
+    for (int i = threadIdx.x; i < N; i += kThreads) tw[i] = a.tw[i];
+    const long long row0 = (long long)blockIdx.x * (2 * B);
+    // Z_k = X_a(k) + i X_b(k), with the Hermitian extension X(N-k) = conj X(k)
+    for (int idx = threadIdx.x; idx < B * H; idx += kThreads) {
+        const int pair = idx / H, k = idx % H;
+        const long long ra = row0 + 2 * pair, rb = ra + 1;
+        float2 xa = ra < a.nrows ? a.src[ra * NRP + k] : make_float2(0.f, 0.f);
+        float2 xb = rb < a.nrows ? a.src[rb * NRP + k] : make_float2(0.f, 0.f);
+        if (k == 0 || k == N / 2) { xa.y = 0.f; xb.y = 0.f; }
+        buf[k * BP + pair] = make_float2(xa.x - xb.y, xa.y + xb.x);
+        if (k > 0 && k < N / 2) buf[(N - k) * BP + pair] = make_float2(xa.x + xb.y, xb.x - xa.y);
+    }
+    __syncthreads();
+    fft_smem<N, 1, B, BP>(buf, tw);
+    for (int idx = threadIdx.x; idx < 2 * B * N; idx += kThreads) {
+        const int rr = idx / N, t = idx % N;
+        const long long grow = row0 + rr;
+        if (grow >= a.nrows) continue;
+        const float2 v = buf[t * BP + (rr >> 1)];
+        a.out[grow * N + t] = ((rr & 1) ? v.y : v.x) * a.scale;
+    }
+}
+
+// ------------------------------------------------------------------------
+// Host-side launchers for one N.
+struct FftOps {
+    int n;
+    cudaError_t (*init)();
+    void (*rows_r2c)(const RowR2CArgs&, cudaStream_t);
+    void (*cols)(const ColArgs&, cudaStream_t);
+    void (*rows_c2r)(const RowC2RArgs&, cudaStream_t);
+};
+
+template <int N> struct Launch {
+    static constexpr int CW = cw_of(N), NCH = (N / 2) / CW;
+    static int col_tiles() { return N * NCH + N / CW; }
+    static long long row_blocks() { return ((long long)N * N + 2 * row_pairs_of(N) - 1) / (2 * row_pairs_of(N)); }
+
+    static cudaError_t init() {
+        cudaError_t e = cudaSuccess;
+        const int cs = (int)cols_smem_bytes<N>(), rs = (int)rows_smem_bytes<N>();
+#define LC_ATTR(K, S) \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, S)
+        LC_ATTR((k_rows_r2c<N, ROW_IN_I64>), rs);
+        LC_ATTR((k_rows_r2c<N, ROW_IN_F32>), rs);
+        LC_ATTR((k_rows_r2c<N, ROW_IN_WEDGE>), rs);
+        LC_ATTR((k_rows_c2r<N>), rs);
+        LC_ATTR((k_cols<N, -1, COL_IN_PLAIN, COL_OUT_PLAIN>), cs);
+        LC_ATTR((k_cols<N, -1, COL_IN_PLAIN, COL_OUT_BF16>), cs);
+        LC_ATTR((k_cols<N, -1, COL_IN_PLAIN, COL_OUT_WEDGE>), cs);
+        LC_ATTR((k_cols<N, 1, COL_IN_PLAIN, COL_OUT_PLAIN>), cs);
+        LC_ATTR((k_cols<N, 1, COL_IN_MAC_F32, COL_OUT_PLAIN>), cs);
+        LC_ATTR((k_cols<N, 1, COL_IN_MAC_BF16, COL_OUT_PLAIN>), cs);
+#undef LC_ATTR
+        return e;
+    }
+    static void rows_r2c(const RowR2CArgs& a, cudaStream_t st) {
+        const dim3 g((unsigned)row_blocks());
+        const size_t sm = rows_smem_bytes<N>();
+        if (a.in_mode == ROW_IN_I64) k_rows_r2c<N, ROW_IN_I64><<<g, kThreads, sm, st>>>(a);
+        else if (a.in_mode == ROW_IN_F32) k_rows_r2c<N, ROW_IN_F32><<<g, kThreads, sm, st>>>(a);
+        else k_rows_r2c<N, ROW_IN_WEDGE><<<g, kThreads, sm, st>>>(a);
+    }
+    static void rows_c2r(const RowC2RArgs& a, cudaStream_t st) {
+        k_rows_c2r<N><<<(unsigned)row_blocks(), kThreads, rows_smem_bytes<N>(), st>>>(a);
+    }
+    static void cols(const ColArgs& a, cudaStream_t st) {
+        const dim3 g((unsigned)col_tiles());
+        const size_t sm = cols_smem_bytes<N>();
+        if (a.dir < 0) {
+            if (a.out_mode == COL_OUT_PLAIN) k_cols<N, -1, COL_IN_PLAIN, COL_OUT_PLAIN><<<g, kThreads, sm, st>>>(a);
+            else if (a.out_mode == COL_OUT_BF16) k_cols<N, -1, COL_IN_PLAIN, COL_OUT_BF16><<<g, kThreads, sm, st>>>(a);
+            else k_cols<N, -1, COL_IN_PLAIN, COL_OUT_WEDGE><<<g, kThreads, sm, st>>>(a);
+        } else {
+            if (a.in_mode == COL_IN_PLAIN) k_cols<N, 1, COL_IN_PLAIN, COL_OUT_PLAIN><<<g, kThreads, sm, st>>>(a);
+            else if (a.in_mode == COL_IN_MAC_F32) k_cols<N, 1, COL_IN_MAC_F32, COL_OUT_PLAIN><<<g, kThreads, sm, st>>>(a);
+            else k_cols<N, 1, COL_IN_MAC_BF16, COL_OUT_PLAIN><<<g, kThreads, sm, st>>>(a);
+        }
+    }
+};
+
+} // namespace lc

@@ -1,0 +1,259 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (stated for the retarded field): FP32 history, relative L2
+<= 1e-5 and max |dJ| / mean(J_oracle) <= 1e-4; BF16 history, relative L2 <=
+5e-3.  Deposit: bit-exact int64 grid, unit and total.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1502_02294_gb300 as lc
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP32_L2, FP32_MAX, BF16_L2 = 1e-5, 1e-4, 5e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    lc.build()
+    oracle.build()
+
+
+def errors(J, ref):
+    J = np.asarray(J, dtype=np.float64)
+    rel = np.linalg.norm(J - ref) / np.linalg.norm(ref)
+    mx = np.abs(J - ref).max() / np.abs(ref).mean()
+    return rel, mx
+
+
+def run_steps(plan, cat, steps_to_push, field_steps, device_io=True):
+    out = {}
+    for s in steps_to_push:
+        pos, lum = cat.active(s)
+        if device_io:
+            plan.push(s, torch.from_numpy(pos).cuda(), torch.from_numpy(lum).cuda())
+        else:
+            plan.push(s, pos, lum)
+        if s in field_steps:
+            if device_io:
+                out[s] = plan.field(s).cpu().numpy()
+            else:
+                o = np.empty((plan.n,) * 3, dtype=np.float32)
+                out[s] = plan.field(s, out=o)
+    return out
+
+
+# ------------------------------------------------------------------ deposit
+def test_deposit_bit_exact_against_oracle():
+    w = synth.config("c2")
+    for s in (0, 17, 40):
+        pos, lum = w.cat.active(s)
+        g, S, tot = lc.deposit_grid(w.n, w.box, pos, lum)
+        go, So, to = oracle.deposit_fixed(w.n, w.box, pos, lum)
+        assert S == So and tot == to and np.array_equal(g, go)
+        # device inputs and a device output give the same bits
+        gd = torch.zeros((w.n,) * 3, dtype=torch.int64, device="cuda")
+        _, S2, t2 = lc.deposit_grid(w.n, w.box, torch.from_numpy(pos).cuda(), torch.from_numpy(lum).cuda(), out=gd)
+        assert S2 == So and t2 == to and np.array_equal(gd.cpu().numpy(), go)
+
+
+def test_deposit_edge_positions_and_order():
+    N, box = 16, 32.0
+    l = box / N
+    rng = np.random.default_rng(5)
+    pos = np.concatenate([
+        rng.uniform(-3 * box, 4 * box, size=(300, 3)),
+        np.array([[0.0, 0.0, 0.0], [box, box, box], [-1e-300, 0.5 * l, 1.5 * l], [(N - 0.5) * l, 0.49999999 * l, 7.5 * l]]),
+    ])
+    lum = 10.0 ** rng.normal(0, 2, size=pos.shape[0])
+    lum[5] = 0.0
+    g, S, t = lc.deposit_grid(N, box, pos, lum)
+    go, So, to = oracle.deposit_fixed(N, box, pos, lum)
+    assert np.array_equal(g, go) and S == So and t == to
+    perm = rng.permutation(pos.shape[0])
+    g2, S2, t2 = lc.deposit_grid(N, box, pos[perm], lum[perm])
+    assert np.array_equal(g2, go) and t2 == to
+    ge, Se, te = lc.deposit_grid(N, box, np.zeros((0, 3)), np.zeros(0))
+    assert te == 0 and not ge.any()
+
+
+# ------------------------------------------------------------------ FFT
+def test_fft_against_brute_force_dft_8():
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((8, 8, 8)).astype(np.float32)
+    X = lc.fft_r2c(torch.from_numpy(x).cuda()).cpu().numpy()
+    ref = oracle.dft3(x.astype(np.float64), -1)[:, :, :5]
+    assert np.abs(X - ref).max() <= 1e-5 * np.abs(ref).max()
+    back = lc.fft_c2r(torch.from_numpy(X).cuda()).cpu().numpy()
+    assert np.abs(back - x).max() <= 1e-5 * np.abs(x).max()
+
+
+@pytest.mark.parametrize("n", [16, 32, 64, 96, 128, 192, 256])
+def test_fft_sizes_parseval_and_roundtrip(n):
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal((n, n, n)).astype(np.float32)
+    xt = torch.from_numpy(x).cuda()
+    X = lc.fft_r2c(xt)
+    Xn = X.cpu().numpy().astype(np.complex128)
+    ref = np.fft.rfftn(x.astype(np.float64))
+    err = np.linalg.norm(Xn - ref) / np.linalg.norm(ref)
+    assert err < 2e-6, err
+    # Parseval on the half spectrum (interior planes count twice)
+    w = np.full(n // 2 + 1, 2.0)
+    w[0] = 1.0
+    w[-1] = 1.0
+    e_k = (np.abs(Xn) ** 2 * w).sum() / n ** 3
+    assert e_k == pytest.approx((x.astype(np.float64) ** 2).sum(), rel=1e-5)
+    back = lc.fft_c2r(X).cpu().numpy()
+    assert np.abs(back - x).max() < 1e-5 * np.abs(x).max()
+
+
+# ------------------------------------------------------------------ Green's functions
+def test_green_wedge_against_oracle_transform():
+    w = synth.small(n=16, box=100.0, n_steps=6)
+    P = oracle.Problem.from_workload(w)
+    plan = lc.Plan.from_workload(w)
+    l = w.box / w.n
+    M = w.n // 2
+    s = 4
+    lo, hi, I = P.shell_table(s)
+    idx = [(a, b, c) for c in range(M + 1) for b in range(c + 1) for a in range(b + 1)]
+    ia = np.array(idx)
+    for j in range(len(I)):
+        Gh = np.fft.fftn(P.rgf_full(s, j)).real
+        ref = Gh[ia[:, 0], ia[:, 1], ia[:, 2]]
+        got, g0 = plan.green_wedge(s, j)
+        assert np.abs(got - ref).max() <= 2e-6 * np.abs(ref).max()
+        assert g0 == pytest.approx(I[j] / l ** 3, rel=1e-9)
+    plan.close()
+
+
+# ------------------------------------------------------------------ fields
+def test_field_c1_every_step_full_grid():
+    w = synth.config("c1")
+    P = oracle.Problem.from_workload(w)
+    plan = lc.Plan.from_workload(w)
+    out = run_steps(plan, w.cat, range(8), set(range(8)))
+    for s, J in out.items():
+        ref = oracle.field_for(P, w.cat, s)
+        rel, mx = errors(J, ref)
+        assert rel <= FP32_L2 and mx <= FP32_MAX, (s, rel, mx)
+    plan.close()
+
+
+@pytest.mark.parametrize("n,box,sub,clustered", [(16, 40.0, 4, False), (32, 75.0, 2, True), (96, 120.0, 2, True)])
+def test_field_small_cases_full_grid(n, box, sub, clustered):
+    w = synth.small(n=n, box=box, n_steps=6, n_src=120, subsamples=sub, clustered=clustered, seed=99 + n)
+    P = oracle.Problem.from_workload(w)
+    plan = lc.Plan.from_workload(w)
+    out = run_steps(plan, w.cat, range(6), {2, 5})
+    for s, J in out.items():
+        ref = oracle.field_for(P, w.cat, s)
+        rel, mx = errors(J, ref)
+        assert rel <= FP32_L2 and mx <= FP32_MAX, (n, s, rel, mx)
+    plan.close()
+
+
+def test_field_skipped_and_empty_steps_host_io():
+    # steps 1 and 3 never pushed, step 2 pushed empty: they count as no sources
+    w = synth.small(n=32, box=60.0, n_steps=6, n_src=80, seed=7)
+    P = oracle.Problem.from_workload(w)
+    plan = lc.Plan.from_workload(w)
+    pushed = {0: w.cat.active(0), 2: (np.zeros((0, 3)), np.zeros(0)), 4: w.cat.active(4), 5: w.cat.active(5)}
+    res = {}
+    for s, (pos, lum) in pushed.items():
+        plan.push(s, pos, lum)
+        if s in (4, 5):
+            res[s] = plan.field(s, out=np.empty((32,) * 3, dtype=np.float32))
+    for s, J in res.items():
+        A = P.active_shells(s)
+        grids = []
+        for j in range(A):
+            n = s - j
+            if n in pushed and pushed[n][1].shape[0]:
+                grids.append(oracle.deposit_ngp(w.n, w.box, *pushed[n]))
+            else:
+                grids.append(None)
+        ref = P.field(s, grids)
+        rel, mx = errors(J, ref)
+        assert rel <= FP32_L2 and mx <= FP32_MAX, (s, rel, mx)
+    plan.close()
+
+
+def test_host_and_device_io_identical():
+    w = synth.config("c1")
+    p1, p2 = lc.Plan.from_workload(w), lc.Plan.from_workload(w)
+    a = run_steps(p1, w.cat, range(5), {4}, device_io=True)[4]
+    b = run_steps(p2, w.cat, range(5), {4}, device_io=False)[4]
+    assert np.array_equal(a, b)
+    p1.close()
+    p2.close()
+
+
+def test_field_c2_sampled_cells():
+    w = synth.config("c2")
+    P = oracle.Problem.from_workload(w)
+    plan = lc.Plan.from_workload(w)
+    check = {20, 63}
+    out = run_steps(plan, w.cat, range(64), check)
+    for s in sorted(check):
+        J = out[s]
+        pos, lum = w.cat.active(s)
+        dense = np.floor(pos[np.argmax(lum)] / (w.box / w.n) + 0.5).astype(int) % w.n
+        cells = synth.sample_cells(1000 + s, w.n, 3000, dense_line_through=dense)
+        ref = oracle.field_for(P, w.cat, s, cells=cells)
+        got = J.reshape(-1)[cells]
+        rel, mx = errors(got, ref)
+        assert rel <= FP32_L2 and mx <= FP32_MAX, (s, rel, mx)
+    plan.close()
+
+
+def test_bf16_history_within_tolerance():
+    w = synth.config("c1")
+    w.history = synth.HISTORY_BF16
+    P = oracle.Problem.from_workload(w)
+    plan = lc.Plan.from_workload(w)
+    out = run_steps(plan, w.cat, range(8), {3, 7})
+    for s, J in out.items():
+        ref = oracle.field_for(P, w.cat, s)
+        rel, mx = errors(J, ref)
+        assert rel <= BF16_L2, (s, rel)
+    plan.close()
+
+
+# ------------------------------------------------------------------ host-side error paths
+def test_step_order_and_argument_errors():
+    w = synth.config("c1")
+    plan = lc.Plan.from_workload(w)
+    pos, lum = w.cat.active(0)
+    plan.push(0, pos, lum)
+    with pytest.raises(lc.LCError) as e:
+        plan.push(0, pos, lum)
+    assert e.value.status == lc.LC_ERR_STEP_ORDER
+    with pytest.raises(lc.LCError) as e:
+        plan.field(1)
+    assert e.value.status == lc.LC_ERR_STEP_ORDER
+    bad = lum.copy()
+    bad[0] = -1.0
+    with pytest.raises(lc.LCError) as e:
+        plan.push(1, pos, bad)
+    assert e.value.status == lc.LC_ERR_INVALID_ARG
+    # device inputs are checked on the device and reported by check()
+    bad[0] = np.nan
+    plan.push(1, torch.from_numpy(pos).cuda(), torch.from_numpy(bad).cuda())
+    with pytest.raises(lc.LCError) as e:
+        plan.check()
+    assert e.value.status == lc.LC_ERR_DEVICE_CHECK
+    plan.check()  # cleared
+    # the plan is still usable
+    J = plan.field(1)
+    assert torch.isfinite(J).all()
+    plan.reset()
+    plan.push(0, pos, lum)
+    plan.close()
