@@ -24,7 +24,9 @@ namespace lc {
 extern const FftOps fft_ops_8, fft_ops_16, fft_ops_32, fft_ops_64, fft_ops_96, fft_ops_128, fft_ops_192,
     fft_ops_256, fft_ops_384, fft_ops_512;
 
-static const FftOps* ops_for(int n) {
+const FftOps* fft_ops_for(int n);
+static const FftOps* ops_for(int n) { return fft_ops_for(n); }
+const FftOps* fft_ops_for(int n) {
     switch (n) {
     case 8: return &fft_ops_8;
     case 16: return &fft_ops_16;
@@ -41,7 +43,9 @@ static const FftOps* ops_for(int n) {
 }
 
 // cudaFuncSetAttribute once per (device, N)
-static cudaError_t ensure_init(const FftOps* ops) {
+cudaError_t fft_ensure_init(const FftOps* ops);
+static cudaError_t ensure_init(const FftOps* ops) { return fft_ensure_init(ops); }
+cudaError_t fft_ensure_init(const FftOps* ops) {
     static std::mutex mu;
     static std::vector<std::pair<int, int>> done;
     int dev = 0;
