@@ -209,6 +209,21 @@ lc_status lc_fft_r2c(int n, const float* in, float* out_complex, void* cuda_stre
  * exact inverse): in N*N*(N/2+1) complex floats, out N^3 floats, device pointers. */
 lc_status lc_fft_c2r(int n, const float* in_complex, float* out, float scale, void* cuda_stream);
 
+/* lc_fft_r2c without any device allocation (the paper has no counterpart:
+ * this is a library-usage variant).  For callers that cannot call cudaMalloc
+ * (a device memory pool that owns all memory, a host application that
+ * forbids allocation, or a loop that must not synchronise on one), the work
+ * spectrum and twiddle table live in one static 4 MiB device array that the
+ * library reserves on every GPU it is used on until the process exits.
+ *   n: 8, 16, 32, 64 or 96 (larger grids do not fit: LC_ERR_UNSUPPORTED_SIZE).
+ *   in, out_complex: device pointers as for lc_fft_r2c.
+ * The work is only enqueued on cuda_stream (no synchronisation).  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before capturing a stream.  All calls share the one
+ * array: calls whose work may overlap on the GPU (different streams without
+ * ordering) race and must not be issued. */
+lc_status lc_fft_r2c_static(int n, const float* in, float* out_complex, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

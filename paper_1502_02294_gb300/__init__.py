@@ -84,6 +84,7 @@ SIGNATURES = [
     ("lc_deposit_grid", _I, [_I, _D, _I64, _VP, _VP, _VP, _DP, ctypes.POINTER(_I64), _VP]),
     ("lc_fft_r2c", _I, [_I, _VP, _VP, _VP]),
     ("lc_fft_c2r", _I, [_I, _VP, _VP, ctypes.c_float, _VP]),
+    ("lc_fft_r2c_static", _I, [_I, _VP, _VP, _VP]),
 ]
 
 _L = None
@@ -335,6 +336,17 @@ def fft_r2c(x, stream=None):
     x = x.contiguous().to(torch.float32)
     out = torch.empty((n, n, n // 2 + 1), dtype=torch.complex64, device=x.device)
     _check(_lib().lc_fft_r2c(n, x.data_ptr(), out.data_ptr(), _stream_ptr(stream)), "lc_fft_r2c")
+    return out
+
+
+def fft_r2c_static(x, out=None, stream=None):
+    """fft_r2c without device allocation inside the library (N <= 96); the
+    result is enqueued on the stream, not waited for."""
+    torch = _torch()
+    n = x.shape[0]
+    if out is None:
+        out = torch.empty((n, n, n // 2 + 1), dtype=torch.complex64, device=x.device)
+    _check(_lib().lc_fft_r2c_static(n, x.data_ptr(), out.data_ptr(), _stream_ptr(stream)), "lc_fft_r2c_static")
     return out
 
 
