@@ -11,7 +11,9 @@ transform).  The 64-step run is cycled (history reset at the wrap).
 
 Timing: W warm-up steps, then K steps timed one by one with CUDA events on the
 plan's stream, L2 flushed (a 512 MB write) between timed steps, outside the
-events.  Under torchrun each rank runs an independent simulation on its own
+events.  Each step is one replay of a CUDA graph captured once per observed
+step (the library's lc_graph_create); the per-phase events captured inside
+the graphs give the shell-MAC kernel's own duration for the roofline.  Under torchrun each rank runs an independent simulation on its own
 GPU (weak scaling, no data-path collective); the reported time is the max over
 ranks.
 
@@ -193,7 +195,8 @@ def main():
     stream = torch.cuda.current_stream()
     plan = lc.Plan.from_workload(w, stream=stream)
     T = w.steps.n_steps
-    plan.prepare()  # every observing step's Green's function table (plan time)
+    t_first = 0 if w.steps.kind != synth.STEPS_EQUAL_TAU else w.steps.n_shell
+    plan.prepare(t_first, T)  # the observed steps' Green's function tables (plan time)
     # device-resident inputs of every step
     src_dev = []
     for s in range(T):
@@ -201,30 +204,50 @@ def main():
         src_dev.append((torch.from_numpy(pos).to(dev), torch.from_numpy(lum).to(dev)))
     out = torch.empty((w.n,) * 3, dtype=torch.float32, device=dev)
     flush = torch.empty(args.flush_mb << 20, dtype=torch.uint8, device=dev)
-    work = {s: active_shell_work(plan, w, s) for s in range(T)}
+    # timed window: every step for the equal-time runs; for the equal-conformal-time
+    # run the last n_shell/4 steps, after n_shell untimed fill steps (history only)
+    t0 = 0 if w.steps.kind != synth.STEPS_EQUAL_TAU else w.steps.n_shell
+    work = {s: active_shell_work(plan, w, s) for s in range(t0, T)}
     nk = w.n * w.n * (w.n // 2 + 1)
 
-    cursor = [0]
+    def refill():
+        plan.reset()
+        for s in range(t0):
+            plan.push(s, *src_dev[s])
 
-    def step_once(timed_events=None):
-        s = cursor[0]
-        if s == 0:
-            plan.reset()
-        pos, lum = src_dev[s]
-        if timed_events:
-            timed_events[0].record(stream)
-        plan.push(s, pos, lum)
-        plan.field(s, out)
-        if timed_events:
-            timed_events[1].record(stream)
-        cursor[0] = (s + 1) % T
-        return s
-
-    for _ in range(max(3, args.warmup)):
-        step_once()
-    torch.cuda.synchronize()
-    plan.timing(reset=True)
+    # one CUDA graph per observed step (push + field on device buffers).  The
+    # headline pass replays graphs without instrumentation; a second pass
+    # replays graphs captured with the per-phase events inside, which time the
+    # shell-MAC kernel on its own for the roofline.
+    window = T - t0
+    graphs = {s: plan.graph(s, *src_dev[s], out) for s in range(t0, T)}
     plan.set_timing(True)
+    graphs_timed = {s: plan.graph(s, *src_dev[s], out) for s in range(t0, T)}
+    plan.set_timing(False)
+
+    def run_pass(gs, evs=None):
+        refill()
+        steps_done = []
+        for i in range(args.steps):
+            s = t0 + i % window
+            if i and s == t0:
+                refill()  # history restarts (untimed: outside the events)
+            flush.zero_()  # L2 flush between timed steps, outside the events
+            if evs:
+                evs[i][0].record(stream)
+            gs[s].launch()
+            if evs:
+                evs[i][1].record(stream)
+            steps_done.append(s)
+        return steps_done
+
+    refill()
+    for i in range(max(3, args.warmup)):
+        s = t0 + i % window
+        if i and s == t0:
+            refill()
+        graphs[s].launch()
+    torch.cuda.synchronize()
     sampler = ClockSampler(dev.index)
     sampler.start()
     if world > 1:
@@ -232,17 +255,19 @@ def main():
     torch.cuda.synchronize()
     launches0 = lc.kernel_launches()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    done_steps = []
-    for i in range(args.steps):
-        flush.zero_()  # L2 flush between timed steps, outside the events
-        done_steps.append(step_once(evs[i]))
+    done_steps = run_pass(graphs, evs)
     torch.cuda.synchronize()
     launches = lc.kernel_launches() - launches0
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop()
+    # profiling pass (same steps, graphs with in-graph phase events)
+    plan.timing(reset=True)
+    mac_steps = run_pass(graphs_timed)
+    torch.cuda.synchronize()
     phases = plan.timing(reset=True)
-    plan.set_timing(False)
+    for g in list(graphs.values()) + list(graphs_timed.values()):
+        g.close()
     per_step_ms = np.array([a.elapsed_time(b) for a, b in evs])
     t_total = float(per_step_ms.sum()) / 1e3
     t_max = t_total
@@ -258,7 +283,8 @@ def main():
     # complex write (8 B per k) + one read of the step's Ghat wedge table
     mac_ms, mac_launches = phases["mac_x"]
     W = plan.wedge_size
-    mac_bytes = sum(nk * (8 * work[s][0] + 8) + W * 4 * work[s][1] for s in done_steps)
+    hb = 4 if w.history else 8
+    mac_bytes = sum(nk * (hb * work[s][0] + 8) + W * 4 * work[s][1] for s in mac_steps)
     import json as _json
 
     peaks = {}
@@ -276,26 +302,29 @@ def main():
         pos, lum = w.cat.active(s)
         pinned.append((torch.from_numpy(pos).pin_memory(), torch.from_numpy(lum).pin_memory()))
     host_out = torch.empty((w.n,) * 3, dtype=torch.float32).pin_memory()
-    plan.reset()
-    e_cursor = 0
+    refill()
+    e_cursor = t0
     for _ in range(max(3, args.warmup)):
         plan.push(e_cursor, *pinned[e_cursor])
         plan.field(e_cursor, host_out)
         e_cursor += 1
+        if e_cursor == T:
+            refill()
+            e_cursor = t0
     e2e_t = 0.0
     h2d = 0
     for i in range(args.steps):
         s = e_cursor
-        if s == 0:
-            plan.reset()
+        if s == t0:
+            refill()
         flush.zero_()
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        tic = time.perf_counter()
         plan.push(s, *pinned[s])
         plan.field(s, host_out)  # synchronises and copies to the host
-        e2e_t += time.perf_counter() - t0
+        e2e_t += time.perf_counter() - tic
         h2d += pinned[s][0].numel() * 8 + pinned[s][1].numel() * 8
-        e_cursor = (s + 1) % T
+        e_cursor = t0 + (s + 1 - t0) % (T - t0)
     if world > 1:
         tt = torch.tensor([e2e_t], device=dev, dtype=torch.float64)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
@@ -307,8 +336,10 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
 
-        rate, spent, desc = oracle_field_rate(w, [20, 41, 63][: (3 if args.workload == "c2" else 1)]
-                                              if args.workload == "c2" else [w.steps.n_steps - 1])
+        if args.workload == "c2":
+            rate, spent, desc = oracle_field_rate(w, [20, 41, 63], cells_per_step=16384)
+        else:
+            rate, spent, desc = oracle_field_rate(w, [w.steps.n_steps - 1], cells_per_step=2048)
         cpu = {"value": rate, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle", "sample": desc,
                "seconds": round(spent, 2)}
 
@@ -316,9 +347,9 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32" if w.history else "f32", "data": "synthetic",
             "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "grid": w.n,
-                       "box_mpc": w.box, "steps_in_run": T, "ring_slots": plan.n_ring,
+                       "box_mpc": w.box, "steps_in_run": T, "timed_window": [t0, T], "ring_slots": plan.n_ring,
                        "history": "bf16" if w.history else "fp32", "l2": f"flushed between timed steps "
                        f"({args.flush_mb} MB write outside the events)", "inputs": "device-resident"},
             "cell_shell_mac_per_s": world * mac_cells / t_max,
@@ -327,9 +358,11 @@ def main():
                          "achieved": mac_gbs, "peak": hbm_peak, "unit": "GB/s",
                          "frac": (mac_gbs / hbm_peak) if mac_gbs else None,
                          "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
-                         "bytes_per_launch": mac_bytes / max(1, mac_launches),
-                         "ms_per_launch": mac_ms / max(1, mac_launches)},
-            "phase_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},
+                         "bytes_per_launch": mac_bytes / max(1, len(mac_steps)),
+                         "ms_per_launch": mac_ms / max(1, len(mac_steps))},
+            "phase_ms_per_step": {k: v[0] / max(1, len(mac_steps)) for k, v in phases.items()},
+            "launch": "one CUDA graph replay per step (push + field captured once per observed step); "
+                      "phase times from a second pass of graphs with in-graph events",
             "phase_share": phase_share,
             "clocks": clocks,
             "e2e": e2e,

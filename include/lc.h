@@ -47,6 +47,7 @@ extern "C" {
 #endif
 
 typedef struct lc_plan lc_plan; /* opaque, owned by the library */
+typedef struct lc_step_graph lc_step_graph;
 
 typedef enum {
     LC_OK = 0,
@@ -169,6 +170,21 @@ lc_status lc_plan_green_wedge(lc_plan* plan, int step, int lookback, float* out,
 lc_status lc_batch_step(lc_plan* const* plans, int n, const int* steps, const int64_t* n_src,
                         const double* const* pos, const double* const* lum, float* const* outs);
 
+/* --- CUDA graphs of whole steps ------------------------------------------------ */
+
+/* One observing step captured as a CUDA graph: lc_push_sources(step, ...) then
+ * lc_retarded_field(step, out), replayed by lc_graph_launch with one launch
+ * call (the kernels of steps 4-6 of Section 2.2 back to back on the device).
+ * pos, lum and out are DEVICE pointers, read and written at every replay;
+ * the step's Green's function table is built before capture.  The plan must
+ * not be captured concurrently from another thread. */
+lc_status lc_graph_create(lc_plan* plan, int step, int64_t n_src, const double* pos, const double* lum, float* out,
+                          lc_step_graph** graph);
+/* Replay on the plan's stream.  Same ordering rule as lc_push_sources: the
+ * step must be later than the last pushed step; it becomes the last pushed. */
+lc_status lc_graph_launch(lc_step_graph* graph);
+lc_status lc_graph_destroy(lc_step_graph* graph);
+
 /* --- tracing ------------------------------------------------------------------ */
 
 /* Phases of one step, each timed with a pair of CUDA events on the plan's
@@ -181,7 +197,8 @@ enum {
     LC_PHASE_MAC_X = 4,      /* shell multiply-accumulate fused with the inverse x pass */
     LC_PHASE_INV_Y = 5,      /* y pass, inverse */
     LC_PHASE_C2R_Z = 6,      /* z rows, complex -> real, scaled output */
-    LC_N_PHASES = 7
+    LC_PHASE_NEAR = 7,       /* innermost shell's near cube, exact FP64 scatter + fold (FP32 history) */
+    LC_N_PHASES = 8
 };
 /* Enable (1) or disable (0) per-phase event timing on this plan. */
 lc_status lc_plan_set_timing(lc_plan* plan, int enable);

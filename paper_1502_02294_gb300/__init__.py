@@ -26,7 +26,7 @@ LC_ERR_OOM, LC_ERR_CUDA, LC_ERR_TIMEOUT, LC_ERR_DEVICE_CHECK = 4, 5, 6, 7
 STEPS_EXPLICIT, STEPS_EQUAL_TIME, STEPS_EQUAL_TAU = 0, 1, 2
 HISTORY_FP32, HISTORY_BF16 = 0, 1
 SUPPORTED_N = (8, 16, 32, 64, 96, 128, 192, 256, 384, 512)
-PHASES = ("deposit", "r2c_z", "fwd_y", "fwd_x_ring", "mac_x", "inv_y", "c2r_z")
+PHASES = ("deposit", "r2c_z", "fwd_y", "fwd_x_ring", "mac_x", "inv_y", "c2r_z", "near")
 
 
 def kernel_launches() -> int:
@@ -78,6 +78,9 @@ SIGNATURES = [
     ("lc_plan_green_wedge", _I, [_P, _I, _I, _VP, _DP]),
     ("lc_batch_step", _I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_I), ctypes.POINTER(_I64),
                            ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
+    ("lc_graph_create", _I, [_P, _I, _I64, _VP, _VP, _VP, ctypes.POINTER(_P)]),
+    ("lc_graph_launch", _I, [_P]),
+    ("lc_graph_destroy", _I, [_P]),
     ("lc_plan_set_timing", _I, [_P, _I]),
     ("lc_plan_timing", _I, [_P, _DP, ctypes.POINTER(_I64), _I]),
     ("lc_kernel_launches", ctypes.c_uint64, []),
@@ -194,7 +197,7 @@ class Plan:
     # -- lifecycle
     def close(self):
         if getattr(self, "_h", None):
-            _lib().lc_plan_destroy(self._h)
+            _lib().lc_plan_destroy(self._h)  # also destroys its step graphs
             self._h = None
 
     def __del__(self):
@@ -261,6 +264,10 @@ class Plan:
         a = A.value
         return (lo[:a], hi[:a], rh.value, I[:a]) if integrals else (lo[:a], hi[:a], rh.value)
 
+    def graph(self, step: int, pos, lum, out) -> "StepGraph":
+        """Capture push(step) + field(step) on device buffers as one CUDA graph."""
+        return StepGraph(self, step, pos, lum, out)
+
     def set_timing(self, enable: bool = True):
         _check(_lib().lc_plan_set_timing(self._h, int(bool(enable))), "lc_plan_set_timing")
 
@@ -278,6 +285,36 @@ class Plan:
         _check(_lib().lc_plan_green_wedge(self._h, int(step), int(lookback), out.ctypes.data, ctypes.byref(g0)),
                "lc_plan_green_wedge")
         return out, g0.value
+
+
+class StepGraph:
+    """A whole step (deposit, forward transform into the ring, shell MAC,
+    inverse transform) replayed with one launch; inputs/output are the device
+    tensors given at capture."""
+
+    def __init__(self, plan: Plan, step: int, pos, lum, out):
+        n = int(lum.shape[0])
+        self.plan, self.step = plan, int(step)
+        self._keep = (pos, lum, out)
+        h = ctypes.c_void_p()
+        _check(_lib().lc_graph_create(plan._h, self.step, n, pos.data_ptr() if n else None,
+                                      lum.data_ptr() if n else None, out.data_ptr(), ctypes.byref(h)),
+               "lc_graph_create")
+        self._g = h
+
+    def launch(self):
+        _check(_lib().lc_graph_launch(self._g), "lc_graph_launch")
+
+    def close(self):
+        if getattr(self, "_g", None) and self.plan._h:
+            _lib().lc_graph_destroy(self._g)
+        self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def batch_step(plans, steps, sources, outs):

@@ -17,8 +17,11 @@
 #include <new>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "lc_internal.h"
-#include "lc_kernels.cuh"
+#include "lc_mac.cuh"
 
 namespace lc {
 extern const FftOps fft_ops_8, fft_ops_16, fft_ops_32, fft_ops_64, fft_ops_96, fft_ops_128, fft_ops_192,
@@ -68,6 +71,22 @@ static bool is_device_ptr(const void* p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
 static std::vector<float2> twiddles(int n) {
     std::vector<float2> t(n);
     for (int m = 0; m < n; ++m) {
@@ -83,6 +102,9 @@ static inline void count_launch(unsigned long long k = 1) { g_launches.fetch_add
 } // namespace lc
 
 using namespace lc;
+
+// fewest active slices for which the TMA shell MAC is used
+static const int kMacTmaMinShells = 12;
 
 struct lc_plan {
     int N = 0;
@@ -112,10 +134,15 @@ struct lc_plan {
     long long src_cap = 0;
     float* d_out_stage = nullptr;
     // Green's function tables, one per observing step (built lazily)
+    // the ring as a 4-D tensor [slot][p][q][r] for the TMA shell MAC
+    alignas(64) CUtensorMap ring_map;
+    bool has_map = false;
     struct Table {
-        float* ghat = nullptr; // [W][A]
-        double* g0 = nullptr;  // [A]
-        int A = -1;            // -1: not built
+        int gstride = 0;        // row stride of ghat: A rounded up to 8
+        float* ghat = nullptr;  // [W][gstride]; shell 0 without its near cube when near_on
+        double* g0 = nullptr;   // [A] FP64 Ghat_j(0) of what the FFT path carries
+        double* gnear = nullptr; // near cube of shell 0 on the wedge prefix (near_on)
+        int A = -1;             // -1: not built
     };
     std::vector<Table> tables;
     // builder scratch
@@ -126,6 +153,12 @@ struct lc_plan {
     long long* d_bnd = nullptr;
     double* d_I = nullptr;
     double* d_scale = nullptr;
+    // near field of the innermost shell, added exactly (FP32 history)
+    bool near_on = false;
+    double* d_near = nullptr;     // N^3 FP64 accumulator, kept all-zero between steps
+    long long* d_src_cell = nullptr;
+    long long* d_src_q = nullptr;
+    long long near_cap = 0, near_n = 0;
     size_t bytes = 0;
     int last_pushed = -1;
     bool failed = false;
@@ -139,6 +172,20 @@ struct lc_plan {
     std::vector<cudaEvent_t> pool;
     double ms[LC_N_PHASES] = {0};
     long long launches[LC_N_PHASES] = {0};
+    // graph capture of a whole step (lc_graph_create)
+    bool capturing = false;
+    long long cap_kernels[LC_N_PHASES] = {0};
+    std::vector<lc_step_graph*> graphs;
+};
+
+struct lc_step_graph {
+    lc_plan* p = nullptr;
+    int step = 0;
+    long long n_src = 0;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<lc_plan::Mark> marks; // phase events inside the graph (timing on at capture)
+    long long kernels[LC_N_PHASES] = {0};
+    bool pending = false;             // replayed, events not yet read
 };
 
 namespace {
@@ -161,22 +208,44 @@ struct Phase {
     int ph;
     int k;
     cudaEvent_t a = nullptr;
+    // inside a stream capture the events must become event-record nodes
+    // (external), not capture-internal dependencies
+    void record(cudaEvent_t e) {
+        if (p->capturing) cudaEventRecordWithFlags(e, p->stream, cudaEventRecordExternal);
+        else cudaEventRecord(e, p->stream);
+    }
     Phase(lc_plan* p_, int ph_, int kernels) : p(p_), ph(ph_), k(kernels) {
         if (p->timing) {
             a = take_event(p);
-            cudaEventRecord(a, p->stream);
+            record(a);
         }
     }
     ~Phase() {
         if (p->timing) {
             cudaEvent_t b = take_event(p);
-            cudaEventRecord(b, p->stream);
+            record(b);
             p->marks.push_back({ph, a, b});
         }
-        p->launches[ph] += k;
-        count_launch(k);
+        if (p->capturing) {
+            p->cap_kernels[ph] += k; // counted when the graph is launched
+        } else {
+            p->launches[ph] += k;
+            count_launch(k);
+        }
     }
 };
+
+// read the phase events of a graph's last replay into the plan's totals
+void harvest_graph(lc_plan* p, lc_step_graph* g) {
+    if (!g->pending) return;
+    if (!g->marks.empty()) cudaEventSynchronize(g->marks.back().b);
+    for (auto& m : g->marks) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, m.a, m.b) == cudaSuccess) p->ms[m.phase] += t;
+        else cudaGetLastError();
+    }
+    g->pending = false;
+}
 
 lc_status cuda_fail(lc_plan* p, cudaError_t e) {
     if (e == cudaSuccess) return LC_OK;
@@ -194,6 +263,15 @@ template <class T> cudaError_t dalloc(lc_plan* p, T** ptr, size_t count) {
 }
 
 void free_all(lc_plan* p) {
+    for (auto* g : p->graphs) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        for (auto& m : g->marks) {
+            cudaEventDestroy(m.a);
+            cudaEventDestroy(m.b);
+        }
+        delete g;
+    }
+    p->graphs.clear();
     cudaFree(p->d_grid);
     cudaFree(p->d_work);
     cudaFree(p->d_ring);
@@ -211,9 +289,13 @@ void free_all(lc_plan* p) {
     cudaFree(p->d_bnd);
     cudaFree(p->d_I);
     cudaFree(p->d_scale);
+    cudaFree(p->d_near);
+    cudaFree(p->d_src_cell);
+    cudaFree(p->d_src_q);
     for (auto& t : p->tables) {
         cudaFree(t.ghat);
         cudaFree(t.g0);
+        cudaFree(t.gnear);
     }
     for (auto& m : p->marks) {
         cudaEventDestroy(m.a);
@@ -275,10 +357,14 @@ lc_status build_table(lc_plan* p, int s) {
             dalloc(p, &p->d_scale, cap) != cudaSuccess)
             return LC_ERR_OOM;
     }
-    if (dalloc(p, &T.ghat, (size_t)p->W * A) != cudaSuccess) return LC_ERR_OOM;
-    if (dalloc(p, &T.g0, (size_t)A) != cudaSuccess) {
+    T.gstride = (A + 7) / 8 * 8;
+    if (dalloc(p, &T.ghat, (size_t)p->W * T.gstride) != cudaSuccess) return LC_ERR_OOM;
+    if (dalloc(p, &T.g0, (size_t)A) != cudaSuccess ||
+        (p->near_on && dalloc(p, &T.gnear, (size_t)(kNearR + 1) * (kNearR + 2) * (kNearR + 3) / 6) != cudaSuccess)) {
         cudaFree(T.ghat);
+        cudaFree(T.g0);
         T.ghat = nullptr;
+        T.g0 = nullptr;
         return LC_ERR_OOM;
     }
     cudaStream_t st = p->stream;
@@ -286,6 +372,7 @@ lc_status build_table(lc_plan* p, int s) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_bnd, g.bnd.data(), sizeof(long long) * (A + 1), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_I, g.I.data(), sizeof(double) * A, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_gw, 0, sizeof(double) * (size_t)A * p->W, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(T.ghat, 0, sizeof(float) * (size_t)p->W * T.gstride, st);
     if (e != cudaSuccess) return cuda_fail(p, e);
     RgfAccumArgs ra;
     ra.N = p->N;
@@ -301,13 +388,15 @@ lc_status build_table(lc_plan* p, int s) {
     ra.rh = g.rh;
     launch_rgf_accum(ra, st);
     launch_rgf_norm(p->N, p->W, A, p->d_gw, p->d_I, p->l * p->l * p->l, p->normalise, p->d_scale, T.g0, st);
-    count_launch(2 + 3ULL * A);
+    if (p->near_on) launch_near_prep(p->d_gw, p->d_scale, T.gnear, T.g0, st);
+    count_launch(2 + 3ULL * A + (p->near_on ? 1 : 0));
     for (int j = 0; j < A; ++j) {
         RowR2CArgs r{};
         r.in_mode = ROW_IN_WEDGE;
         r.nrows = (long long)p->N * p->N;
         r.gw = p->d_gw + (size_t)j * p->W;
         r.gscale = p->d_scale + j;
+        r.near_r = (p->near_on && j == 0) ? kNearR : -1;
         r.dst = p->d_work;
         r.tw = p->d_tw;
         p->ops->rows_r2c(r, st);
@@ -323,7 +412,7 @@ lc_status build_table(lc_plan* p, int s) {
         c.axis = 1;
         c.out_mode = COL_OUT_WEDGE;
         c.wedge_out = T.ghat;
-        c.wedge_A = A;
+        c.wedge_A = T.gstride;
         c.wedge_j = j;
         p->ops->cols(c, st);
     }
@@ -464,8 +553,29 @@ lc_status lc_plan_create(int n, double box_mpc, const lc_cosmology* cosmo, const
         delete p;
         return LC_ERR_OOM;
     }
+    // ring tensor map for the TMA shell MAC: dims {r (4-B elements), q, p, slot}
+    if ((p->history == LC_HISTORY_BF16 ? ops->mac_bf16 : ops->mac_f32) && tensor_map_encoder()) {
+        const bool bf = p->history == LC_HISTORY_BF16;
+        const cuuint64_t inner = (cuuint64_t)(bf ? p->NRP : 2 * p->NRP);
+        cuuint64_t dims[4] = {inner, (cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)p->n_ring};
+        cuuint64_t strides[3] = {inner * 4, inner * 4 * n, inner * 4 * n * n};
+        cuuint32_t box[4] = {(cuuint32_t)(bf ? cw_of(n) : 2 * cw_of(n)), 1, (cuuint32_t)(n > 256 ? n / 2 : n), 1};
+        cuuint32_t es[4] = {1, 1, 1, 1};
+        CUresult r = tensor_map_encoder()(&p->ring_map, bf ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                                          4, p->d_ring, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        p->has_map = r == CUDA_SUCCESS;
+    }
+    p->near_on = p->history == LC_HISTORY_FP32;
+    if (p->near_on && dalloc(p, &p->d_near, N3) != cudaSuccess) {
+        free_all(p);
+        delete p;
+        return LC_ERR_OOM;
+    }
     std::vector<float2> tw = twiddles(n);
     e = cudaMemcpyAsync(p->d_tw, tw.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess && p->near_on) e = cudaMemsetAsync(p->d_near, 0, sizeof(double) * N3, p->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_slot_step, 0xff, sizeof(int) * p->n_ring, p->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_slot_total, 0, sizeof(long long) * p->n_ring, p->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_err, 0, sizeof(int), p->stream);
@@ -514,6 +624,21 @@ lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos
             dlum = p->d_lum;
         }
     }
+    if (p->near_on && n_src > p->near_cap) {
+        cudaFree(p->d_src_cell);
+        cudaFree(p->d_src_q);
+        p->bytes -= sizeof(long long) * 2 * p->near_cap;
+        p->near_cap = 0;
+        long long cap = 1024;
+        while (cap < n_src) cap *= 2;
+        if (dalloc(p, &p->d_src_cell, (size_t)cap) != cudaSuccess || dalloc(p, &p->d_src_q, (size_t)cap) != cudaSuccess) {
+            cudaFree(p->d_src_cell);
+            cudaFree(p->d_src_q);
+            p->d_src_cell = p->d_src_q = nullptr;
+            return LC_ERR_OOM;
+        }
+        p->near_cap = cap;
+    }
     const int slot = step % p->n_ring;
     SlotMeta m{slot, step, p->d_slot_step, p->d_slot_S, p->d_slot_total};
     const long long N = p->N;
@@ -522,8 +647,11 @@ lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos
         e = cudaMemsetAsync(p->d_grid, 0, sizeof(long long) * N * N * N, st);
         if (e != cudaSuccess) return cuda_fail(p, e);
         launch_src_prep(dpos, dlum, n_src, p->d_maxbits, p->d_err, m, st);
-        if (n_src > 0) launch_deposit(dpos, dlum, n_src, p->N, p->l, p->d_maxbits, p->d_grid, m, st);
+        if (n_src > 0)
+            launch_deposit(dpos, dlum, n_src, p->N, p->l, p->d_maxbits, p->d_grid, m, st,
+                           p->near_on ? p->d_src_cell : nullptr, p->near_on ? p->d_src_q : nullptr);
     }
+    p->near_n = p->near_on ? n_src : 0;
     RowR2CArgs r{};
     r.in_mode = ROW_IN_I64;
     r.nrows = N * N;
@@ -603,8 +731,22 @@ lc_status lc_retarded_field(lc_plan* p, int step, float* out) {
         c.slot_total = p->d_slot_total;
         c.ghat = T.ghat;
         c.g0 = T.g0;
+        c.gstride = T.gstride;
         c.tw = p->d_tw;
-        {
+        const bool bf = p->history == LC_HISTORY_BF16;
+        auto mac_fn = bf ? p->ops->mac_bf16 : p->ops->mac_f32;
+        // the TMA pipeline pays off once there are enough slices to stream;
+        // for a handful the register-gather pass is faster
+        if (mac_fn && p->has_map && T.A >= kMacTmaMinShells) {
+            // full tiles: TMA-pipelined MAC; the Nyquist column tiles: generic pass
+            Phase ph(p, LC_PHASE_MAC_X, 2);
+            MacArgs ma{step, T.A, T.gstride, p->n_ring, p->d_slot_step, p->d_slot_S, p->d_slot_total,
+                       T.ghat, T.g0, p->d_work, p->d_tw, p->d_err, bf ? 1 : 0};
+            mac_fn(&p->ring_map, ma, st);
+            c.tile0 = p->ops->full_tiles;
+            p->ops->cols(c, st);
+            c.tile0 = 0;
+        } else {
             Phase ph(p, LC_PHASE_MAC_X, 1);
             p->ops->cols(c, st);
         }
@@ -624,6 +766,14 @@ lc_status lc_retarded_field(lc_plan* p, int step, float* out) {
         {
             Phase ph(p, LC_PHASE_C2R_Z, 1);
             p->ops->rows_c2r(r, st);
+        }
+        if (p->near_on && p->near_n > 0) {
+            // innermost shell's near cube, summed exactly in FP64 and folded in
+            Phase ph(p, LC_PHASE_NEAR, 2);
+            const int slot = step % p->n_ring;
+            launch_near_scatter(p->d_src_cell, p->d_src_q, p->near_n, p->N, T.gnear, p->d_slot_S, slot, p->U,
+                                p->d_near, st);
+            launch_near_fold(p->d_src_cell, p->d_src_q, p->near_n, p->N, p->d_near, dout, st);
         }
         e = cudaGetLastError();
     }
@@ -693,6 +843,7 @@ lc_status lc_plan_timing(lc_plan* p, double* ms, int64_t* launches, int reset) {
         p->pool.push_back(m.b);
     }
     p->marks.clear();
+    for (auto* g : p->graphs) harvest_graph(p, g);
     for (int i = 0; i < LC_N_PHASES; ++i) {
         if (ms) ms[i] = p->ms[i];
         if (launches) launches[i] = p->launches[i];
@@ -741,12 +892,169 @@ lc_status lc_plan_green_wedge(lc_plan* p, int step, int lookback, float* out, do
     const lc_plan::Table& T = p->tables[step];
     if (lookback < 0 || lookback >= T.A) return LC_ERR_INVALID_ARG;
     // strided column j of the [W][A] table
-    cudaError_t e = cudaMemcpy2DAsync(out, sizeof(float), T.ghat + lookback, sizeof(float) * T.A, sizeof(float),
-                                      (size_t)p->W, cudaMemcpyDefault, p->stream);
-    if (e == cudaSuccess && ghat0)
-        e = cudaMemcpyAsync(ghat0, T.g0 + lookback, sizeof(double), cudaMemcpyDefault, p->stream);
+    std::vector<float> col((size_t)p->W);
+    double g0 = 0.0;
+    cudaError_t e = cudaMemcpy2DAsync(col.data(), sizeof(float), T.ghat + lookback, sizeof(float) * T.gstride,
+                                      sizeof(float), (size_t)p->W, cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&g0, T.g0 + lookback, sizeof(double), cudaMemcpyDeviceToHost, p->stream);
+    const int Wn = (kNearR + 1) * (kNearR + 2) * (kNearR + 3) / 6;
+    std::vector<double> gn(Wn, 0.0);
+    const bool add_near = p->near_on && lookback == 0;
+    if (e == cudaSuccess && add_near)
+        e = cudaMemcpyAsync(gn.data(), T.gnear, sizeof(double) * Wn, cudaMemcpyDeviceToHost, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
-    return cuda_fail(p, e);
+    if (e != cudaSuccess) return cuda_fail(p, e);
+    if (add_near) {
+        // the FFT path holds shell 0 without its near cube: add the cube's
+        // (real, even) transform back so that the full Ghat_0 is returned
+        const int N = p->N, M = N / 2, R = kNearR;
+        std::vector<double> cs(N);
+        for (int m = 0; m < N; ++m) cs[m] = cos(2.0 * 3.141592653589793238462643383279502884 * m / N);
+        auto wi = [](int a, int b, int c) {
+            int t;
+            if (a > b) { t = a; a = b; b = t; }
+            if (b > c) { t = b; b = c; c = t; }
+            if (a > b) { t = a; a = b; b = t; }
+            return (long long)c * (c + 1) * (c + 2) / 6 + (long long)b * (b + 1) / 2 + a;
+        };
+        double cube = 0.0;
+        for (int dx = -R; dx <= R; ++dx)
+            for (int dy = -R; dy <= R; ++dy)
+                for (int dz = -R; dz <= R; ++dz) cube += gn[wi(abs(dx), abs(dy), abs(dz))];
+        long long w = 0;
+        for (int c = 0; c <= M; ++c)
+            for (int b = 0; b <= c; ++b)
+                for (int a = 0; a <= b; ++a, ++w) {
+                    double v = 0.0;
+                    for (int dx = -R; dx <= R; ++dx)
+                        for (int dy = -R; dy <= R; ++dy)
+                            for (int dz = -R; dz <= R; ++dz) {
+                                const long long ph = ((long long)a * dx + (long long)b * dy + (long long)c * dz) % N;
+                                v += gn[wi(abs(dx), abs(dy), abs(dz))] * cs[(ph + N) % N];
+                            }
+                    col[w] = (float)((double)col[w] + v);
+                }
+        g0 += cube;
+    }
+    e = cudaMemcpy(out, col.data(), sizeof(float) * p->W, cudaMemcpyDefault);
+    if (e != cudaSuccess) return cuda_fail(p, e);
+    if (ghat0) *ghat0 = g0;
+    return LC_OK;
+}
+
+// ------------------------------------------------------------ step graphs
+lc_status lc_graph_create(lc_plan* p, int step, int64_t n_src, const double* pos, const double* lum, float* out,
+                          lc_step_graph** out_graph) {
+    if (!p || !out_graph || !out) return LC_ERR_INVALID_ARG;
+    *out_graph = nullptr;
+    if (p->failed) return LC_ERR_CUDA;
+    if (step < 0 || step >= p->n_steps || n_src < 0) return LC_ERR_INVALID_ARG;
+    if (!is_device_ptr(out) || (n_src > 0 && (!pos || !lum || !is_device_ptr(pos) || !is_device_ptr(lum))))
+        return LC_ERR_INVALID_ARG; // a graph holds device pointers only
+    lc_status r = build_table(p, step);
+    if (r != LC_OK) return r;
+    // make every buffer the step needs exist before capture
+    if (p->near_on && n_src > p->near_cap) {
+        cudaFree(p->d_src_cell);
+        cudaFree(p->d_src_q);
+        p->bytes -= sizeof(long long) * 2 * p->near_cap;
+        p->near_cap = 0;
+        long long cap = 1024;
+        while (cap < n_src) cap *= 2;
+        if (dalloc(p, &p->d_src_cell, (size_t)cap) != cudaSuccess || dalloc(p, &p->d_src_q, (size_t)cap) != cudaSuccess)
+            return LC_ERR_OOM;
+        p->near_cap = cap;
+    }
+    lc_step_graph* g = new (std::nothrow) lc_step_graph();
+    if (!g) return LC_ERR_OOM;
+    g->p = p;
+    g->step = step;
+    g->n_src = n_src;
+    cudaStream_t cap_stream = nullptr, user_stream = p->stream;
+    cudaError_t e = cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete g;
+        return cuda_fail(p, e);
+    }
+    const int saved_last = p->last_pushed;
+    const long long saved_near = p->near_n;
+    const size_t marks0 = p->marks.size();
+    for (int i = 0; i < LC_N_PHASES; ++i) p->cap_kernels[i] = 0;
+    p->stream = cap_stream;
+    p->capturing = true;
+    p->last_pushed = step - 1;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal);
+    lc_status rs = LC_OK;
+    if (e == cudaSuccess) {
+        rs = lc_push_sources(p, step, n_src, pos, lum);
+        if (rs == LC_OK) rs = lc_retarded_field(p, step, out);
+        cudaError_t e2 = cudaStreamEndCapture(cap_stream, &graph);
+        if (e == cudaSuccess) e = e2;
+    }
+    p->capturing = false;
+    p->stream = user_stream;
+    p->last_pushed = saved_last;
+    p->near_n = saved_near;
+    g->marks.assign(p->marks.begin() + marks0, p->marks.end());
+    p->marks.resize(marks0);
+    for (int i = 0; i < LC_N_PHASES; ++i) g->kernels[i] = p->cap_kernels[i];
+    if (e == cudaSuccess && rs == LC_OK) e = cudaGraphInstantiate(&g->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cap_stream);
+    if (rs != LC_OK || e != cudaSuccess) {
+        for (auto& m : g->marks) {
+            p->pool.push_back(m.a);
+            p->pool.push_back(m.b);
+        }
+        delete g;
+        cudaGetLastError();
+        if (rs != LC_OK) return rs;
+        return LC_ERR_CUDA; // capture failed: the plan itself is still usable
+    }
+    p->graphs.push_back(g);
+    *out_graph = g;
+    return LC_OK;
+}
+
+lc_status lc_graph_launch(lc_step_graph* g) {
+    if (!g || !g->p) return LC_ERR_INVALID_ARG;
+    lc_plan* p = g->p;
+    if (p->failed) return LC_ERR_CUDA;
+    if (g->step <= p->last_pushed) return LC_ERR_STEP_ORDER;
+    harvest_graph(p, g); // its previous replay, long finished in a step cycle
+    cudaError_t e = cudaGraphLaunch(g->exec, p->stream);
+    if (e != cudaSuccess) return cuda_fail(p, e);
+    p->last_pushed = g->step;
+    p->near_n = p->near_on ? g->n_src : 0;
+    long long tot = 0;
+    for (int i = 0; i < LC_N_PHASES; ++i) {
+        p->launches[i] += g->kernels[i];
+        tot += g->kernels[i];
+    }
+    count_launch((unsigned long long)tot);
+    g->pending = true;
+    return LC_OK;
+}
+
+lc_status lc_graph_destroy(lc_step_graph* g) {
+    if (!g || !g->p) return LC_ERR_INVALID_ARG;
+    lc_plan* p = g->p;
+    cudaStreamSynchronize(p->stream);
+    harvest_graph(p, g);
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    for (auto& m : g->marks) {
+        p->pool.push_back(m.a);
+        p->pool.push_back(m.b);
+    }
+    for (size_t i = 0; i < p->graphs.size(); ++i)
+        if (p->graphs[i] == g) {
+            p->graphs.erase(p->graphs.begin() + i);
+            break;
+        }
+    delete g;
+    return LC_OK;
 }
 
 // ------------------------------------------------------------ stand-alone kernels

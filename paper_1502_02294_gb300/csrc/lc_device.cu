@@ -67,7 +67,8 @@ __device__ __forceinline__ long long ngp_cell(double x, double l, int N) {
 
 __global__ void __launch_bounds__(256)
     k_deposit(const double* __restrict__ pos, const double* __restrict__ lum, long long n, int N, double l,
-              const unsigned long long* __restrict__ maxbits, long long* __restrict__ grid, SlotMeta m) {
+              const unsigned long long* __restrict__ maxbits, long long* __restrict__ grid, SlotMeta m,
+              long long* __restrict__ cell_out, long long* __restrict__ q_out) {
     __shared__ long long s_sum[8];
     const double lmax = __longlong_as_double((long long)*maxbits);
     double S = 1.0;
@@ -82,10 +83,15 @@ __global__ void __launch_bounds__(256)
     if (i < n) {
         const double L = lum[i];
         const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+        long long c = 0;
         if (finite_d(L) && L >= 0.0 && finite_d(x) && finite_d(y) && finite_d(z)) {
             q = llrint(__ddiv_rn(L, S));
-            const long long c = (ngp_cell(x, l, N) * N + ngp_cell(y, l, N)) * N + ngp_cell(z, l, N);
+            c = (ngp_cell(x, l, N) * N + ngp_cell(y, l, N)) * N + ngp_cell(z, l, N);
             if (q) atomicAdd(reinterpret_cast<unsigned long long*>(grid + c), (unsigned long long)q);
+        }
+        if (cell_out) {
+            cell_out[i] = c;
+            q_out[i] = q;
         }
     }
     for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
@@ -191,7 +197,86 @@ __global__ void __launch_bounds__(256) k_rgf_norm(int N, long long W, int A, con
     }
 }
 
+constexpr int kNearSide = 2 * kNearR + 1, kNearCube = kNearSide * kNearSide * kNearSide;
+
+__device__ __forceinline__ long long near_wedge(int dx, int dy, int dz) {
+    int a = dx < 0 ? -dx : dx, b = dy < 0 ? -dy : dy, c = dz < 0 ? -dz : dz, t;
+    if (a > b) { t = a; a = b; b = t; }
+    if (b > c) { t = b; b = c; c = t; }
+    if (a > b) { t = a; a = b; b = t; }
+    return (long long)c * (c + 1) * (c + 2) / 6 + (long long)b * (b + 1) / 2 + a;
+}
+
+__global__ void k_near_prep(const double* gw0, const double* scale0, double* gnear, double* g0_far) {
+    // one thread: the near cube is (2R+1)^3 = 125 cells
+    const int Wn = (kNearR + 1) * (kNearR + 2) * (kNearR + 3) / 6;
+    for (int w = 0; w < Wn; ++w) gnear[w] = gw0[w] * (*scale0);
+    double sum = 0.0;
+    for (int dx = -kNearR; dx <= kNearR; ++dx)
+        for (int dy = -kNearR; dy <= kNearR; ++dy)
+            for (int dz = -kNearR; dz <= kNearR; ++dz) sum += gnear[near_wedge(dx, dy, dz)];
+    *g0_far -= sum;
+}
+
+__device__ __forceinline__ long long near_target(long long c, int m, int N, int& dx, int& dy, int& dz) {
+    dx = m / (kNearSide * kNearSide) - kNearR;
+    dy = (m / kNearSide) % kNearSide - kNearR;
+    dz = m % kNearSide - kNearR;
+    const long long NN = (long long)N * N;
+    const int ix = (int)(c / NN), iy = (int)((c / N) % N), iz = (int)(c % N);
+    const int tx = (ix + dx + N) % N, ty = (iy + dy + N) % N, tz = (iz + dz + N) % N;
+    return ((long long)tx * N + ty) * N + tz;
+}
+
+__global__ void __launch_bounds__(256) k_near_scatter(const long long* __restrict__ cell, const long long* __restrict__ q,
+                                                      long long n, int N, const double* __restrict__ gnear,
+                                                      const double* __restrict__ slot_S, int slot, double U,
+                                                      double* __restrict__ acc) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * kNearCube) return;
+    const long long s = idx / kNearCube;
+    const int m = (int)(idx % kNearCube);
+    const long long qs = q[s];
+    if (qs == 0) return;
+    int dx, dy, dz;
+    const long long t = near_target(cell[s], m, N, dx, dy, dz);
+    atomicAdd(acc + t, U * slot_S[slot] * (double)qs * gnear[near_wedge(dx, dy, dz)]);
+}
+
+__global__ void __launch_bounds__(256) k_near_fold(const long long* __restrict__ cell, const long long* __restrict__ q,
+                                                   long long n, int N, double* __restrict__ acc, float* __restrict__ out) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * kNearCube) return;
+    const long long s = idx / kNearCube;
+    const int m = (int)(idx % kNearCube);
+    if (q[s] == 0) return;
+    int dx, dy, dz;
+    const long long t = near_target(cell[s], m, N, dx, dy, dz);
+    // the first thread to reach a cell takes its whole sum and clears it
+    const double v = __longlong_as_double(
+        (long long)atomicExch(reinterpret_cast<unsigned long long*>(acc + t), 0ULL));
+    if (v != 0.0) out[t] = (float)((double)out[t] + v);
+}
+
 } // namespace
+
+void launch_near_prep(const double* gw0, const double* scale0, double* gnear, double* g0_far, cudaStream_t st) {
+    k_near_prep<<<1, 1, 0, st>>>(gw0, scale0, gnear, g0_far);
+}
+
+void launch_near_scatter(const long long* cell, const long long* q, long long n, int N, const double* gnear,
+                         const double* slot_S, int slot, double U, double* acc, cudaStream_t st) {
+    const long long total = n * kNearCube;
+    if (total <= 0) return;
+    k_near_scatter<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(cell, q, n, N, gnear, slot_S, slot, U, acc);
+}
+
+void launch_near_fold(const long long* cell, const long long* q, long long n, int N, double* acc, float* out,
+                      cudaStream_t st) {
+    const long long total = n * kNearCube;
+    if (total <= 0) return;
+    k_near_fold<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(cell, q, n, N, acc, out);
+}
 
 void launch_src_prep(const double* pos, const double* lum, long long n, unsigned long long* maxbits, int* err,
                      SlotMeta m, cudaStream_t st) {
@@ -199,9 +284,10 @@ void launch_src_prep(const double* pos, const double* lum, long long n, unsigned
 }
 
 void launch_deposit(const double* pos, const double* lum, long long n, int N, double l,
-                    const unsigned long long* maxbits, long long* grid, SlotMeta m, cudaStream_t st) {
+                    const unsigned long long* maxbits, long long* grid, SlotMeta m, cudaStream_t st,
+                    long long* cell_out, long long* q_out) {
     const long long blocks = n > 0 ? (n + 255) / 256 : 1;
-    k_deposit<<<(unsigned)blocks, 256, 0, st>>>(pos, lum, n, N, l, maxbits, grid, m);
+    k_deposit<<<(unsigned)blocks, 256, 0, st>>>(pos, lum, n, N, l, maxbits, grid, m, cell_out, q_out);
 }
 
 void launch_rgf_accum(const RgfAccumArgs& a, cudaStream_t st) {

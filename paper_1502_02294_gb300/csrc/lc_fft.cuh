@@ -142,9 +142,10 @@ template <int R, int DIR> __device__ __forceinline__ void dft(float2* v) {
     else if constexpr (R == 16) dft16<DIR>(v);
 }
 
-// One in-place Stockham stage of radix R at span NS over B transforms.
-template <int N, int R, int NS, int DIR, int B, int BP>
+// One in-place Stockham stage of radix R at span NS over B transforms, NT threads.
+template <int N, int R, int NS, int DIR, int B, int BP, int NT>
 __device__ __forceinline__ void stage(float2* __restrict__ buf, const float2* __restrict__ tw) {
+    constexpr int kThreads = NT;
     constexpr int NB = N / R;
     constexpr int ITEMS = NB * B;
     constexpr int K = (ITEMS + kThreads - 1) / kThreads;
@@ -183,12 +184,17 @@ __device__ __forceinline__ void stage(float2* __restrict__ buf, const float2* __
 }
 
 // Full length-N transform of the B transforms held in buf (natural order).
-template <int N, int DIR, int B, int BP>
+template <int N, int DIR, int B, int BP, int NT = kThreads>
 __device__ __forceinline__ void fft_smem(float2* __restrict__ buf, const float2* __restrict__ tw) {
     using P = Plan<N>;
-    stage<N, P::R0, 1, DIR, B, BP>(buf, tw);
-    if constexpr (P::R1 > 1) stage<N, P::R1, P::R0, DIR, B, BP>(buf, tw);
-    if constexpr (P::R2 > 1) stage<N, P::R2, P::R0 * P::R1, DIR, B, BP>(buf, tw);
+    stage<N, P::R0, 1, DIR, B, BP, NT>(buf, tw);
+    if constexpr (P::R1 > 1) stage<N, P::R1, P::R0, DIR, B, BP, NT>(buf, tw);
+    if constexpr (P::R2 > 1) stage<N, P::R2, P::R0 * P::R1, DIR, B, BP, NT>(buf, tw);
+}
+
+// threads of a column-pass CTA: eight elements of the N x CW tile per thread (16 at N = 512)
+__host__ __device__ constexpr int col_threads_of(int n) {
+    return (n * cw_of(n)) / 8 < 64 ? 64 : ((n * cw_of(n)) / 8 > 512 ? 512 : (n * cw_of(n)) / 8);
 }
 
 // Symmetric-wedge index of a sorted triple a <= b <= c: C(c+2,3) + C(b+1,2) + a.

@@ -1,7 +1,7 @@
 // lc_fft_inst.cu -- instantiates the FFT pass kernels for one grid size.
 // Compiled once per supported N with -DLC_N=<N> (separate objects, built in
 // parallel); each object exports the launcher table lc_fft_ops_<N>.
-#include "lc_kernels.cuh"
+#include "lc_mac.cuh"
 
 #ifndef LC_N
 #error "LC_N must be defined"
@@ -10,7 +10,27 @@
 #define LC_CAT(a, b) LC_CAT2(a, b)
 
 namespace lc {
+namespace {
+cudaError_t init_all() {
+    cudaError_t e = Launch<LC_N>::init();
+    if (e == cudaSuccess) e = MacLaunch<LC_N, false>::init();
+    if (e == cudaSuccess) e = MacLaunch<LC_N, true>::init();
+    return e;
+}
+void mac_f32(const void* map, const MacArgs& a, cudaStream_t st) {
+    MacLaunch<LC_N, false>::run(static_cast<const CUtensorMap*>(map), a, st);
+}
+void mac_bf16(const void* map, const MacArgs& a, cudaStream_t st) {
+    MacLaunch<LC_N, true>::run(static_cast<const CUtensorMap*>(map), a, st);
+}
+} // namespace
 extern const FftOps LC_CAT(fft_ops_, LC_N);
-const FftOps LC_CAT(fft_ops_, LC_N) = {LC_N, &Launch<LC_N>::init, &Launch<LC_N>::rows_r2c, &Launch<LC_N>::cols,
-                                      &Launch<LC_N>::rows_c2r};
+const FftOps LC_CAT(fft_ops_, LC_N) = {LC_N,
+                                      &init_all,
+                                      &Launch<LC_N>::rows_r2c,
+                                      &Launch<LC_N>::cols,
+                                      &Launch<LC_N>::rows_c2r,
+                                      MacCfg<LC_N, false>::OK ? &mac_f32 : nullptr,
+                                      MacCfg<LC_N, true>::OK ? &mac_bf16 : nullptr,
+                                      LC_N * Launch<LC_N>::NCH};
 } // namespace lc

@@ -48,8 +48,23 @@ struct SlotMeta {
 void launch_src_prep(const double* pos, const double* lum, long long n, unsigned long long* maxbits, int* err,
                      SlotMeta m, cudaStream_t st);
 // Fixed-point NGP deposit into grid (int64, pre-zeroed), total into slot_total.
+// cell_out / q_out (may be null): each source's flat cell index and integer
+// luminosity, kept for the near-field correction of the innermost shell.
 void launch_deposit(const double* pos, const double* lum, long long n, int N, double l,
-                    const unsigned long long* maxbits, long long* grid, SlotMeta m, cudaStream_t st);
+                    const unsigned long long* maxbits, long long* grid, SlotMeta m, cudaStream_t st,
+                    long long* cell_out = nullptr, long long* q_out = nullptr);
+
+// Near field of the innermost shell (displacements |d|_inf <= R), which the
+// FFT path leaves out: gnear holds the shell's FP64 values on the wedge prefix
+// c <= R.  prep: gnear from the builder's wedge, and the far part's k = 0 value.
+constexpr int kNearR = 2;
+void launch_near_prep(const double* gw0, const double* scale0, double* gnear, double* g0_far, cudaStream_t st);
+// scatter U * S * q * G(d) into the FP64 accumulator for every source and d
+void launch_near_scatter(const long long* cell, const long long* q, long long n, int N, const double* gnear,
+                         const double* slot_S, int slot, double U, double* acc, cudaStream_t st);
+// fold the accumulator into out (one rounding per cell) and clear it
+void launch_near_fold(const long long* cell, const long long* q, long long n, int N, double* acc, float* out,
+                      cudaStream_t st);
 
 struct RgfAccumArgs {
     int N, S, A, U;

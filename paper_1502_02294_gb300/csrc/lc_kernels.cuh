@@ -34,6 +34,7 @@ struct RowR2CArgs {
     const float* fin;         // ROW_IN_F32
     const double* gw;         // ROW_IN_WEDGE: wedge values of one shell (FP64)
     const double* gscale;     // ROW_IN_WEDGE: that shell's normalisation factor
+    int near_r;               // ROW_IN_WEDGE: displacements with all |folded| <= near_r read as 0 (-1: none)
     float2* dst;              // half spectrum, rows of NRP
     const float2* tw;
 };
@@ -53,9 +54,11 @@ struct ColArgs {
     const long long* slot_total;
     const float* ghat;        // [wedge][A] real Ghat of this step
     const double* g0;         // [A] FP64 Ghat_j(0)
+    int gstride;              // row stride of the Ghat table (A rounded up to 8)
+    int tile0;                // first tile of this launch (tiles before it are skipped)
     // wedge extract (forward x-pass of a Green's function)
     float* wedge_out;
-    int wedge_A, wedge_j;
+    int wedge_A, wedge_j;     // wedge_A: row stride of the table written
     const float2* tw;
 };
 
@@ -73,17 +76,21 @@ template <int N> __host__ __device__ constexpr size_t rows_smem_bytes() {
     return sizeof(float2) * (N + (size_t)N * odd_pad(row_pairs_of(N)));
 }
 template <int N> __host__ __device__ constexpr size_t cols_smem_bytes() {
+    // twiddles + the padded tile + the compact shell list (offset, lookback, scale)
     return sizeof(float2) * (N + (size_t)N * odd_pad(cw_of(N))) + (size_t)kMaxShells * 16 + 16;
 }
 
 // ------------------------------------------------------------------------
+// z rows, real -> complex.  Every thread first issues all of its global loads
+// (compile-time count, registers), then writes them to shared memory, so a
+// CTA has its whole tile in flight at once.
 template <int N, int IN>
 __global__ void __launch_bounds__(kThreads) k_rows_r2c(RowR2CArgs a) {
     constexpr int B = row_pairs_of(N), BP = odd_pad(B), NRP = nrp_of(N), H = N / 2 + 1;
+    constexpr int TILE = 2 * B * N, PER = (TILE + kThreads - 1) / kThreads;
     extern __shared__ float4 smem_raw[];
     float2* tw = reinterpret_cast<float2*>(smem_raw);
     float2* buf = tw + N;
-    for (int i = threadIdx.x; i < N; i += kThreads) tw[i] = a.tw[i];
     float scale = 1.0f;
     double gsc = 1.0;
     if constexpr (IN == ROW_IN_I64) {
@@ -95,20 +102,33 @@ __global__ void __launch_bounds__(kThreads) k_rows_r2c(RowR2CArgs a) {
     }
     if constexpr (IN == ROW_IN_WEDGE) gsc = *a.gscale;
     const long long row0 = (long long)blockIdx.x * (2 * B);
-    float* bf = reinterpret_cast<float*>(buf);
-    for (int idx = threadIdx.x; idx < 2 * B * N; idx += kThreads) {
+    float val[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int idx = threadIdx.x + i * kThreads;
         const int rr = idx / N, t = idx % N;
         const long long grow = row0 + rr;
-        float val = 0.0f;
-        if (grow < a.nrows) {
-            if constexpr (IN == ROW_IN_I64) val = __ll2float_rn(a.grid[grow * N + t]) * scale;
-            else if constexpr (IN == ROW_IN_F32) val = a.fin[grow * N + t];
+        val[i] = 0.0f;
+        if ((TILE % kThreads == 0 || idx < TILE) && grow < a.nrows) {
+            if constexpr (IN == ROW_IN_I64) val[i] = __ll2float_rn(a.grid[grow * N + t]) * scale;
+            else if constexpr (IN == ROW_IN_F32) val[i] = a.fin[grow * N + t];
             else {
                 const int x = (int)(grow / N), y = (int)(grow % N);
-                val = (float)(a.gw[wedge_of(x, y, t, N)] * gsc);
+                const int fx = x <= N - x ? x : N - x, fy = y <= N - y ? y : N - y, fz = t <= N - t ? t : N - t;
+                const int mx = fx > fy ? (fx > fz ? fx : fz) : (fy > fz ? fy : fz);
+                val[i] = mx <= a.near_r ? 0.0f : (float)(a.gw[wedge_of(x, y, t, N)] * gsc);
             }
         }
-        bf[2 * (t * BP + (rr >> 1)) + (rr & 1)] = val;
+    }
+    for (int i = threadIdx.x; i < N; i += kThreads) tw[i] = a.tw[i];
+    float* bf = reinterpret_cast<float*>(buf);
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int idx = threadIdx.x + i * kThreads;
+        if (TILE % kThreads == 0 || idx < TILE) {
+            const int rr = idx / N, t = idx % N;
+            bf[2 * (t * BP + (rr >> 1)) + (rr & 1)] = val[i];
+        }
     }
     __syncthreads();
     fft_smem<N, -1, B, BP>(buf, tw);
@@ -129,9 +149,13 @@ __global__ void __launch_bounds__(kThreads) k_rows_r2c(RowR2CArgs a) {
 }
 
 // ------------------------------------------------------------------------
+// y or x pass over one N x CW tile (CW consecutive r-columns of one line, or
+// CW Nyquist columns of CW lines).  NT = N * CW / 8 threads, 8 elements each.
 template <int N, int DIR, int IN, int OUT>
-__global__ void __launch_bounds__(kThreads) k_cols(ColArgs a) {
+__global__ void __launch_bounds__(col_threads_of(N)) k_cols(ColArgs a) {
+    constexpr int NT = col_threads_of(N);
     constexpr int CW = cw_of(N), BP = odd_pad(CW), NRP = nrp_of(N), M = N / 2, NCH = M / CW;
+    constexpr int TILE = N * CW, PER = (TILE + NT - 1) / NT;
     constexpr long long PLANE = (long long)N * NRP;
     extern __shared__ float4 smem_raw[];
     float2* tw = reinterpret_cast<float2*>(smem_raw);
@@ -142,9 +166,7 @@ __global__ void __launch_bounds__(kThreads) k_cols(ColArgs a) {
     __shared__ int s_nv;
     __shared__ double s_dc;
 
-    for (int i = threadIdx.x; i < N; i += kThreads) tw[i] = a.tw[i];
-
-    const int tile = blockIdx.x;
+    const int tile = blockIdx.x + a.tile0;
     const bool nyq = tile >= N * NCH;
     int line = 0, chunk = 0;
     long long base, ts, cs;
@@ -158,11 +180,22 @@ __global__ void __launch_bounds__(kThreads) k_cols(ColArgs a) {
         if (a.axis == 0) { base = line * PLANE + M; ts = NRP; cs = PLANE; }
         else { base = (long long)line * NRP + M; ts = PLANE; cs = NRP; }
     }
+    long long addr[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int idx = threadIdx.x + i * NT;
+        addr[i] = base + (long long)(idx / CW) * ts + (idx % CW) * cs;
+    }
+    float2 val[PER];
 
-    bool dc_tile = false;
-    if constexpr (IN != COL_IN_PLAIN) {
+    if constexpr (IN == COL_IN_PLAIN) {
+#pragma unroll
+        for (int i = 0; i < PER; ++i)
+            if (TILE % NT == 0 || threadIdx.x + i * NT < TILE) val[i] = a.src[addr[i]];
+        for (int i = threadIdx.x; i < N; i += NT) tw[i] = a.tw[i];
+    } else {
         // compact list of the ring slots that hold the slices of this step
-        dc_tile = (a.axis == 1) && !nyq && line == 0 && chunk == 0;
+        const bool dc_tile = (a.axis == 1) && !nyq && line == 0 && chunk == 0;
         if (threadIdx.x == 0) {
             int nv = 0;
             double dc = 0.0;
@@ -183,54 +216,66 @@ __global__ void __launch_bounds__(kThreads) k_cols(ColArgs a) {
             s_nv = nv;
             s_dc = dc;
         }
-    }
-    __syncthreads();
-
-    for (int idx = threadIdx.x; idx < N * CW; idx += kThreads) {
-        const int t = idx / CW, col = idx % CW;
-        const long long addr = base + t * ts + col * cs;
-        float2 val;
-        if constexpr (IN == COL_IN_PLAIN) {
-            val = a.src[addr];
-        } else {
-            // k = (p, q, r) of this element (x-pass: t runs over p)
-            const int p = t;
+        for (int i = threadIdx.x; i < N; i += NT) tw[i] = a.tw[i];
+        // wedge rows of Ghat for this thread's elements (x pass: t runs over p)
+        const float* g[PER];
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int idx = threadIdx.x + i * NT;
+            const int t = idx / CW, col = idx % CW;
             const int q = nyq ? line + col : line;
             const int r = nyq ? M : chunk * CW + col;
-            const float* g = a.ghat + wedge_of(p, q, r, N) * a.A;
-            float2 acc = make_float2(0.f, 0.f);
-            const int nv = s_nv;
-            for (int v = 0; v < nv; ++v) {
-                float2 f;
-                if constexpr (IN == COL_IN_MAC_F32) {
-                    f = reinterpret_cast<const float2*>(a.ring)[s_off[v] + addr];
-                } else {
-                    f = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(a.ring)[s_off[v] + addr]);
-                }
-                const float gv = __ldg(g + s_j[v]) * s_D[v];
-                acc.x = fmaf(gv, f.x, acc.x);
-                acc.y = fmaf(gv, f.y, acc.y);
-            }
-            val = acc;
-            if (dc_tile && idx == 0) val = make_float2((float)s_dc, 0.0f);
+            g[i] = a.ghat + wedge_of(t, q, r, N) * a.gstride;
+            val[i] = make_float2(0.f, 0.f);
         }
-        buf[t * BP + col] = val;
+        __syncthreads();
+        const int nv = s_nv;
+        // shells outer, the tile's elements inner: PER independent ring loads
+        // (and Ghat loads) in flight per thread per shell
+        for (int v = 0; v < nv; ++v) {
+            const long long off = s_off[v];
+            const int jv = s_j[v];
+            const float D = s_D[v];
+            float2 f[PER];
+            float gv[PER];
+#pragma unroll
+            for (int i = 0; i < PER; ++i) {
+                if (TILE % NT == 0 || threadIdx.x + i * NT < TILE) {
+                    if constexpr (IN == COL_IN_MAC_F32) f[i] = reinterpret_cast<const float2*>(a.ring)[off + addr[i]];
+                    else f[i] = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(a.ring)[off + addr[i]]);
+                    gv[i] = __ldg(g[i] + jv);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < PER; ++i) {
+                const float w = gv[i] * D;
+                val[i].x = fmaf(w, f[i].x, val[i].x);
+                val[i].y = fmaf(w, f[i].y, val[i].y);
+            }
+        }
+        if (dc_tile && threadIdx.x == 0) val[0] = make_float2((float)s_dc, 0.0f);
+    }
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int idx = threadIdx.x + i * NT;
+        if (TILE % NT == 0 || idx < TILE) buf[(idx / CW) * BP + (idx % CW)] = val[i];
     }
     __syncthreads();
-    fft_smem<N, DIR, CW, BP>(buf, tw);
-    for (int idx = threadIdx.x; idx < N * CW; idx += kThreads) {
+    fft_smem<N, DIR, CW, BP, NT>(buf, tw);
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int idx = threadIdx.x + i * NT;
+        if (!(TILE % NT == 0 || idx < TILE)) continue;
         const int t = idx / CW, col = idx % CW;
-        const long long addr = base + t * ts + col * cs;
         const float2 v = buf[t * BP + col];
         if constexpr (OUT == COL_OUT_PLAIN) {
-            a.dst[addr] = v;
+            a.dst[addr[i]] = v;
         } else if constexpr (OUT == COL_OUT_BF16) {
-            a.dst_bf16[addr] = __floats2bfloat162_rn(v.x, v.y);
+            a.dst_bf16[addr[i]] = __floats2bfloat162_rn(v.x, v.y);
         } else {
-            const int p = t;
             const int q = nyq ? line + col : line;
             const int r = nyq ? M : chunk * CW + col;
-            if (p <= q && q <= r) a.wedge_out[wedge_index(p, q, r) * a.wedge_A + a.wedge_j] = v.x;
+            if (t <= q && q <= r) a.wedge_out[wedge_index(t, q, r) * a.wedge_A + a.wedge_j] = v.x;
         }
     }
 }
@@ -239,20 +284,32 @@ __global__ void __launch_bounds__(kThreads) k_cols(ColArgs a) {
 template <int N>
 __global__ void __launch_bounds__(kThreads) k_rows_c2r(RowC2RArgs a) {
     constexpr int B = row_pairs_of(N), BP = odd_pad(B), NRP = nrp_of(N), H = N / 2 + 1;
+    constexpr int TILE = B * H, PER = (TILE + kThreads - 1) / kThreads;
     extern __shared__ float4 smem_raw[];
     float2* tw = reinterpret_cast<float2*>(smem_raw);
     float2* buf = tw + N;
-    for (int i = threadIdx.x; i < N; i += kThreads) tw[i] = a.tw[i];
     const long long row0 = (long long)blockIdx.x * (2 * B);
-    // Z_k = X_a(k) + i X_b(k), with the Hermitian extension X(N-k) = conj X(k)
-    for (int idx = threadIdx.x; idx < B * H; idx += kThreads) {
+    float2 xa[PER], xb[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int idx = threadIdx.x + i * kThreads;
         const int pair = idx / H, k = idx % H;
         const long long ra = row0 + 2 * pair, rb = ra + 1;
-        float2 xa = ra < a.nrows ? a.src[ra * NRP + k] : make_float2(0.f, 0.f);
-        float2 xb = rb < a.nrows ? a.src[rb * NRP + k] : make_float2(0.f, 0.f);
-        if (k == 0 || k == N / 2) { xa.y = 0.f; xb.y = 0.f; }
-        buf[k * BP + pair] = make_float2(xa.x - xb.y, xa.y + xb.x);
-        if (k > 0 && k < N / 2) buf[(N - k) * BP + pair] = make_float2(xa.x + xb.y, xb.x - xa.y);
+        const bool ok = TILE % kThreads == 0 || idx < TILE;
+        xa[i] = (ok && ra < a.nrows) ? a.src[ra * NRP + k] : make_float2(0.f, 0.f);
+        xb[i] = (ok && rb < a.nrows) ? a.src[rb * NRP + k] : make_float2(0.f, 0.f);
+    }
+    for (int i = threadIdx.x; i < N; i += kThreads) tw[i] = a.tw[i];
+    // Z_k = X_a(k) + i X_b(k), with the Hermitian extension X(N-k) = conj X(k)
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int idx = threadIdx.x + i * kThreads;
+        if (!(TILE % kThreads == 0 || idx < TILE)) continue;
+        const int pair = idx / H, k = idx % H;
+        float2 A = xa[i], Bv = xb[i];
+        if (k == 0 || k == N / 2) { A.y = 0.f; Bv.y = 0.f; }
+        buf[k * BP + pair] = make_float2(A.x - Bv.y, A.y + Bv.x);
+        if (k > 0 && k < N / 2) buf[(N - k) * BP + pair] = make_float2(A.x + Bv.y, Bv.x - A.y);
     }
     __syncthreads();
     fft_smem<N, 1, B, BP>(buf, tw);
@@ -267,12 +324,17 @@ __global__ void __launch_bounds__(kThreads) k_rows_c2r(RowC2RArgs a) {
 
 // ------------------------------------------------------------------------
 // Host-side launchers for one N.
+struct MacArgs;
 struct FftOps {
     int n;
     cudaError_t (*init)();
     void (*rows_r2c)(const RowR2CArgs&, cudaStream_t);
     void (*cols)(const ColArgs&, cudaStream_t);
     void (*rows_c2r)(const RowC2RArgs&, cudaStream_t);
+    // fused TMA shell MAC over the full tiles (null where not built), FP32 / BF16 ring
+    void (*mac_f32)(const void* tensor_map, const MacArgs&, cudaStream_t);
+    void (*mac_bf16)(const void* tensor_map, const MacArgs&, cudaStream_t);
+    int full_tiles; // tiles of the full 16-column chunks (the Nyquist tiles follow)
 };
 
 template <int N> struct Launch {
@@ -309,8 +371,9 @@ template <int N> struct Launch {
         k_rows_c2r<N><<<(unsigned)row_blocks(), kThreads, rows_smem_bytes<N>(), st>>>(a);
     }
     static void cols(const ColArgs& a, cudaStream_t st) {
-        const dim3 g((unsigned)col_tiles());
+        const dim3 g((unsigned)(col_tiles() - a.tile0));
         const size_t sm = cols_smem_bytes<N>();
+        constexpr int kThreads = col_threads_of(N);
         if (a.dir < 0) {
             if (a.out_mode == COL_OUT_PLAIN) k_cols<N, -1, COL_IN_PLAIN, COL_OUT_PLAIN><<<g, kThreads, sm, st>>>(a);
             else if (a.out_mode == COL_OUT_BF16) k_cols<N, -1, COL_IN_PLAIN, COL_OUT_BF16><<<g, kThreads, sm, st>>>(a);

@@ -274,3 +274,23 @@ def test_step_order_and_argument_errors():
     plan.reset()
     plan.push(0, pos, lum)
     plan.close()
+
+
+def test_field_c3_bf16_full_size_sampled_cells():
+    # 256^3, 200 Mpc, 128 equal-conformal-time shells, 1e5 clustered sources,
+    # BF16 history: 128 fill steps, then fields at two observed steps
+    w = synth.config("c3")
+    P = oracle.Problem.from_workload(w)
+    plan = lc.Plan.from_workload(w)
+    T = w.steps.n_steps
+    check = {T - 17, T - 1}
+    out = run_steps(plan, w.cat, range(T), check)
+    for s in sorted(check):
+        assert plan.shells(s)[0].shape[0] == P.active_shells(s)
+        pos, lum = w.cat.active(s)
+        dense = np.floor(pos[np.argmax(lum)] / (w.box / w.n) + 0.5).astype(int) % w.n
+        cells = synth.sample_cells(7000 + s, w.n, 600, dense_line_through=dense)
+        ref = oracle.field_for(P, w.cat, s, cells=cells)
+        rel, mx, raw = errors(out[s].reshape(-1)[cells], ref)
+        assert rel <= BF16_L2, (s, rel, raw)
+    plan.close()
