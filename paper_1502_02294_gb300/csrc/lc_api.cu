@@ -389,7 +389,7 @@ lc_status build_table(lc_plan* p, int s) {
     launch_rgf_accum(ra, st);
     launch_rgf_norm(p->N, p->W, A, p->d_gw, p->d_I, p->l * p->l * p->l, p->normalise, p->d_scale, T.g0, st);
     if (p->near_on) launch_near_prep(p->d_gw, p->d_scale, T.gnear, T.g0, st);
-    count_launch(2 + 3ULL * A + (p->near_on ? 1 : 0));
+    count_launch(2 + (p->ops->plane_r2c ? 2ULL : 3ULL) * A + (p->near_on ? 1 : 0));
     for (int j = 0; j < A; ++j) {
         RowR2CArgs r{};
         r.in_mode = ROW_IN_WEDGE;
@@ -399,7 +399,6 @@ lc_status build_table(lc_plan* p, int s) {
         r.near_r = (p->near_on && j == 0) ? kNearR : -1;
         r.dst = p->d_work;
         r.tw = p->d_tw;
-        p->ops->rows_r2c(r, st);
         ColArgs c{};
         c.axis = 0;
         c.dir = -1;
@@ -408,7 +407,12 @@ lc_status build_table(lc_plan* p, int s) {
         c.src = p->d_work;
         c.dst = p->d_work;
         c.tw = p->d_tw;
-        p->ops->cols(c, st);
+        if (p->ops->plane_r2c) {
+            p->ops->plane_r2c(r, st);
+        } else {
+            p->ops->rows_r2c(r, st);
+            p->ops->cols(c, st);
+        }
         c.axis = 1;
         c.out_mode = COL_OUT_WEDGE;
         c.wedge_out = T.ghat;
@@ -662,10 +666,6 @@ lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos
     r.bf16 = p->history == LC_HISTORY_BF16;
     r.dst = p->d_work;
     r.tw = p->d_tw;
-    {
-        Phase ph(p, LC_PHASE_R2C_Z, 1);
-        p->ops->rows_r2c(r, st);
-    }
     ColArgs c{};
     c.axis = 0;
     c.dir = -1;
@@ -674,7 +674,15 @@ lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos
     c.src = p->d_work;
     c.dst = p->d_work;
     c.tw = p->d_tw;
-    {
+    if (p->ops->plane_r2c) {
+        // z and y together, one CTA per x-plane
+        Phase ph(p, LC_PHASE_R2C_Z, 1);
+        p->ops->plane_r2c(r, st);
+    } else {
+        {
+            Phase ph(p, LC_PHASE_R2C_Z, 1);
+            p->ops->rows_r2c(r, st);
+        }
         Phase ph(p, LC_PHASE_FWD_Y, 1);
         p->ops->cols(c, st);
     }
@@ -753,17 +761,21 @@ lc_status lc_retarded_field(lc_plan* p, int step, float* out) {
         c.axis = 0;
         c.in_mode = COL_IN_PLAIN;
         c.src = p->d_work;
-        {
-            Phase ph(p, LC_PHASE_INV_Y, 1);
-            p->ops->cols(c, st);
-        }
         RowC2RArgs r{};
         r.nrows = N * N;
         r.src = p->d_work;
         r.out = dout;
         r.scale = (float)(p->U / (double)N3);
         r.tw = p->d_tw;
-        {
+        if (p->ops->plane_c2r) {
+            // y and z together, one CTA per x-plane
+            Phase ph(p, LC_PHASE_C2R_Z, 1);
+            p->ops->plane_c2r(r, st);
+        } else {
+            {
+                Phase ph(p, LC_PHASE_INV_Y, 1);
+                p->ops->cols(c, st);
+            }
             Phase ph(p, LC_PHASE_C2R_Z, 1);
             p->ops->rows_c2r(r, st);
         }
@@ -1159,7 +1171,6 @@ lc_status lc_fft_r2c(int n, const float* in, float* out_complex, void* stream) {
     ra.fin = in;
     ra.dst = work;
     ra.tw = tw;
-    ops->rows_r2c(ra, st);
     ColArgs c{};
     c.axis = 0;
     c.dir = -1;
@@ -1168,10 +1179,15 @@ lc_status lc_fft_r2c(int n, const float* in, float* out_complex, void* stream) {
     c.src = work;
     c.dst = work;
     c.tw = tw;
-    ops->cols(c, st);
+    if (ops->plane_r2c) {
+        ops->plane_r2c(ra, st);
+    } else {
+        ops->rows_r2c(ra, st);
+        ops->cols(c, st);
+    }
     c.axis = 1;
     ops->cols(c, st);
-    count_launch(3);
+    count_launch(ops->plane_r2c ? 2 : 3);
     const int h = n / 2 + 1;
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
@@ -1204,15 +1220,19 @@ lc_status lc_fft_c2r(int n, const float* in_complex, float* out, float scale, vo
         c.tw = tw;
         ops->cols(c, st);
         c.axis = 0;
-        ops->cols(c, st);
         RowC2RArgs ra{};
         ra.nrows = (long long)n * n;
         ra.src = work;
         ra.out = out;
         ra.scale = scale;
         ra.tw = tw;
-        ops->rows_c2r(ra, st);
-        count_launch(3);
+        if (ops->plane_c2r) {
+            ops->plane_c2r(ra, st);
+        } else {
+            ops->cols(c, st);
+            ops->rows_c2r(ra, st);
+        }
+        count_launch(ops->plane_c2r ? 2 : 3);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -30,6 +30,8 @@ const FftOps LC_CAT(fft_ops_, LC_N) = {LC_N,
                                       &Launch<LC_N>::rows_r2c,
                                       &Launch<LC_N>::cols,
                                       &Launch<LC_N>::rows_c2r,
+                                      plane_ok<LC_N>() ? &Launch<LC_N>::plane_r2c : nullptr,
+                                      plane_ok<LC_N>() ? &Launch<LC_N>::plane_c2r : nullptr,
                                       MacCfg<LC_N, false>::OK ? &mac_f32 : nullptr,
                                       MacCfg<LC_N, true>::OK ? &mac_bf16 : nullptr,
                                       LC_N * Launch<LC_N>::NCH};

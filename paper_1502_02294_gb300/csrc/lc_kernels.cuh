@@ -72,20 +72,66 @@ struct RowC2RArgs {
 
 constexpr int kMaxShells = 1024;
 
+// The ring slots that hold the active slices of a step, compacted in
+// increasing lookback j: slot, j, scale D (the slot's luminosity total for
+// BF16 history, 1 for FP32) and the FP64 k = 0 sum  sum_j Ghat_j(0) S_j q_j.
+// Run by one whole warp: 32 slices per round trip to memory.
+__device__ __forceinline__ void mac_slot_list(int A, int step, int n_ring, const int* slot_step,
+                                              const long long* slot_total, const double* slot_S, const double* g0,
+                                              bool bf16, int* out_slot, int* out_j, float* out_D, int* nv_out,
+                                              double* dc_out) {
+    const int lane = threadIdx.x & 31;
+    int nv = 0;
+    double dc = 0.0;
+    for (int j0 = 0; j0 < A; j0 += 32) {
+        const int j = j0 + lane;
+        const int n = step - j;
+        bool valid = false;
+        int slot = 0;
+        double lum = 0.0;
+        if (j < A && n >= 0) {
+            slot = n % n_ring;
+            if (slot_step[slot] == n) {
+                const long long tot = slot_total[slot];
+                if (tot != 0) {
+                    valid = true;
+                    lum = slot_S[slot] * (double)tot;
+                }
+            }
+        }
+        const unsigned ball = __ballot_sync(0xffffffffu, valid);
+        const int pos = nv + __popc(ball & ((1u << lane) - 1u));
+        double part = 0.0;
+        if (valid) {
+            out_slot[pos] = slot;
+            out_j[pos] = j;
+            out_D[pos] = bf16 ? (float)lum : 1.0f;
+            part = g0[j] * lum;
+        }
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        dc += part;
+        nv += __popc(ball);
+    }
+    if (lane == 0) {
+        *nv_out = nv;
+        *dc_out = dc;
+    }
+}
+
 template <int N> __host__ __device__ constexpr size_t rows_smem_bytes() {
     return sizeof(float2) * (N + (size_t)N * odd_pad(row_pairs_of(N)));
 }
 template <int N> __host__ __device__ constexpr size_t cols_smem_bytes() {
-    // twiddles + the padded tile + the compact shell list (offset, lookback, scale)
-    return sizeof(float2) * (N + (size_t)N * odd_pad(cw_of(N))) + (size_t)kMaxShells * 16 + 16;
+    // twiddles + the padded tile + the compact shell list (offset, lookback, scale, slot)
+    return sizeof(float2) * (N + (size_t)N * odd_pad(cw_of(N))) + (size_t)kMaxShells * 20 + 16;
 }
 
 // ------------------------------------------------------------------------
-// z rows, real -> complex.  Every thread first issues all of its global loads
-// (compile-time count, registers), then writes them to shared memory, so a
-// CTA has its whole tile in flight at once.
+// z rows, real -> complex, persistent: a CTA owns row blocks blockIdx.x,
+// +gridDim.x, ...; every thread issues all global loads of the next block
+// (compile-time count, registers) before transforming the current one.
 template <int N, int IN>
-__global__ void __launch_bounds__(kThreads) k_rows_r2c(RowR2CArgs a) {
+__global__ void __launch_bounds__(kThreads) k_rows_r2c(RowR2CArgs a, int nblocks) {
     constexpr int B = row_pairs_of(N), BP = odd_pad(B), NRP = nrp_of(N), H = N / 2 + 1;
     constexpr int TILE = 2 * B * N, PER = (TILE + kThreads - 1) / kThreads;
     extern __shared__ float4 smem_raw[];
@@ -101,50 +147,63 @@ __global__ void __launch_bounds__(kThreads) k_rows_r2c(RowR2CArgs a) {
         scale = a.bf16 ? (tot > 0 ? (float)(1.0 / (double)tot) : 0.0f) : (float)S;
     }
     if constexpr (IN == ROW_IN_WEDGE) gsc = *a.gscale;
-    const long long row0 = (long long)blockIdx.x * (2 * B);
-    float val[PER];
+    auto fetch = [&](int blk, float* val) {
+        const long long row0 = (long long)blk * (2 * B);
 #pragma unroll
-    for (int i = 0; i < PER; ++i) {
-        const int idx = threadIdx.x + i * kThreads;
-        const int rr = idx / N, t = idx % N;
-        const long long grow = row0 + rr;
-        val[i] = 0.0f;
-        if ((TILE % kThreads == 0 || idx < TILE) && grow < a.nrows) {
-            if constexpr (IN == ROW_IN_I64) val[i] = __ll2float_rn(a.grid[grow * N + t]) * scale;
-            else if constexpr (IN == ROW_IN_F32) val[i] = a.fin[grow * N + t];
-            else {
-                const int x = (int)(grow / N), y = (int)(grow % N);
-                const int fx = x <= N - x ? x : N - x, fy = y <= N - y ? y : N - y, fz = t <= N - t ? t : N - t;
-                const int mx = fx > fy ? (fx > fz ? fx : fz) : (fy > fz ? fy : fz);
-                val[i] = mx <= a.near_r ? 0.0f : (float)(a.gw[wedge_of(x, y, t, N)] * gsc);
+        for (int i = 0; i < PER; ++i) {
+            const int idx = threadIdx.x + i * kThreads;
+            const int rr = idx / N, t = idx % N;
+            const long long grow = row0 + rr;
+            val[i] = 0.0f;
+            if ((TILE % kThreads == 0 || idx < TILE) && grow < a.nrows) {
+                if constexpr (IN == ROW_IN_I64) val[i] = __ll2float_rn(a.grid[grow * N + t]) * scale;
+                else if constexpr (IN == ROW_IN_F32) val[i] = a.fin[grow * N + t];
+                else {
+                    const int x = (int)(grow / N), y = (int)(grow % N);
+                    const int fx = x <= N - x ? x : N - x, fy = y <= N - y ? y : N - y, fz = t <= N - t ? t : N - t;
+                    const int mx = fx > fy ? (fx > fz ? fx : fz) : (fy > fz ? fy : fz);
+                    val[i] = mx <= a.near_r ? 0.0f : (float)(a.gw[wedge_of(x, y, t, N)] * gsc);
+                }
             }
         }
-    }
+    };
     for (int i = threadIdx.x; i < N; i += kThreads) tw[i] = a.tw[i];
+    float cur[PER], nxt[PER];
+    int blk = blockIdx.x;
+    if (blk < nblocks) fetch(blk, cur);
     float* bf = reinterpret_cast<float*>(buf);
+    while (blk < nblocks) {
+        const int next = blk + gridDim.x;
+        if (next < nblocks) fetch(next, nxt);
+        __syncthreads(); // the previous block has left shared memory
 #pragma unroll
-    for (int i = 0; i < PER; ++i) {
-        const int idx = threadIdx.x + i * kThreads;
-        if (TILE % kThreads == 0 || idx < TILE) {
-            const int rr = idx / N, t = idx % N;
-            bf[2 * (t * BP + (rr >> 1)) + (rr & 1)] = val[i];
+        for (int i = 0; i < PER; ++i) {
+            const int idx = threadIdx.x + i * kThreads;
+            if (TILE % kThreads == 0 || idx < TILE) {
+                const int rr = idx / N, t = idx % N;
+                bf[2 * (t * BP + (rr >> 1)) + (rr & 1)] = cur[i];
+            }
         }
-    }
-    __syncthreads();
-    fft_smem<N, -1, B, BP>(buf, tw);
-    // unpack the two real rows of each pair: X_a = (Z_k + conj Z_{N-k}) / 2,
-    // X_b = (Z_k - conj Z_{N-k}) / (2i)
-    for (int idx = threadIdx.x; idx < 2 * B * H; idx += kThreads) {
-        const int rr = idx / H, k = idx % H;
-        const long long grow = row0 + rr;
-        if (grow >= a.nrows) continue;
-        const int pair = rr >> 1;
-        const float2 zk = buf[k * BP + pair];
-        const float2 zn = buf[(k == 0 ? 0 : N - k) * BP + pair];
-        float2 x;
-        if ((rr & 1) == 0) x = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
-        else x = make_float2(0.5f * (zk.y + zn.y), 0.5f * (zn.x - zk.x));
-        a.dst[grow * NRP + k] = x;
+        __syncthreads();
+        fft_smem<N, -1, B, BP>(buf, tw);
+        // unpack the two real rows of each pair: X_a = (Z_k + conj Z_{N-k}) / 2,
+        // X_b = (Z_k - conj Z_{N-k}) / (2i)
+        const long long row0 = (long long)blk * (2 * B);
+        for (int idx = threadIdx.x; idx < 2 * B * H; idx += kThreads) {
+            const int rr = idx / H, k = idx % H;
+            const long long grow = row0 + rr;
+            if (grow >= a.nrows) continue;
+            const int pair = rr >> 1;
+            const float2 zk = buf[k * BP + pair];
+            const float2 zn = buf[(k == 0 ? 0 : N - k) * BP + pair];
+            float2 x;
+            if ((rr & 1) == 0) x = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
+            else x = make_float2(0.5f * (zk.y + zn.y), 0.5f * (zn.x - zk.x));
+            a.dst[grow * NRP + k] = x;
+        }
+#pragma unroll
+        for (int i = 0; i < PER; ++i) cur[i] = nxt[i];
+        blk = next;
     }
 }
 
@@ -196,26 +255,12 @@ __global__ void __launch_bounds__(col_threads_of(N)) k_cols(ColArgs a) {
     } else {
         // compact list of the ring slots that hold the slices of this step
         const bool dc_tile = (a.axis == 1) && !nyq && line == 0 && chunk == 0;
-        if (threadIdx.x == 0) {
-            int nv = 0;
-            double dc = 0.0;
-            for (int j = 0; j < a.A; ++j) {
-                const int n = a.step - j;
-                if (n < 0) break;
-                const int slot = n % a.n_ring;
-                if (a.slot_step[slot] != n) continue;
-                const long long tot = a.slot_total[slot];
-                if (tot == 0) continue;
-                const double lum = a.slot_S[slot] * (double)tot;
-                s_off[nv] = (long long)slot * a.slot_elems;
-                s_j[nv] = j;
-                s_D[nv] = (IN == COL_IN_MAC_BF16) ? (float)lum : 1.0f;
-                dc += a.g0[j] * lum;
-                ++nv;
-            }
-            s_nv = nv;
-            s_dc = dc;
-        }
+        int* s_slot = reinterpret_cast<int*>(s_D + kMaxShells);
+        if (threadIdx.x < 32)
+            mac_slot_list(a.A, a.step, a.n_ring, a.slot_step, a.slot_total, a.slot_S, a.g0,
+                          IN == COL_IN_MAC_BF16, s_slot, s_j, s_D, &s_nv, &s_dc);
+        __syncthreads();
+        for (int v = threadIdx.x; v < s_nv; v += NT) s_off[v] = (long long)s_slot[v] * a.slot_elems;
         for (int i = threadIdx.x; i < N; i += NT) tw[i] = a.tw[i];
         // wedge rows of Ghat for this thread's elements (x pass: t runs over p)
         const float* g[PER];
@@ -281,44 +326,293 @@ __global__ void __launch_bounds__(col_threads_of(N)) k_cols(ColArgs a) {
 }
 
 // ------------------------------------------------------------------------
+// Plain y / x pass, persistent: each CTA walks tiles blockIdx.x, +gridDim.x,
+// ... and issues the next tile's global loads (into registers) before it
+// transforms and stores the current one, so loads stay in flight while the
+// shared-memory FFT runs.
+template <int N> struct ColGeom {
+    static constexpr int CW = cw_of(N), NRP = nrp_of(N), M = N / 2, NCH = M / CW;
+    static constexpr long long PLANE = (long long)N * NRP;
+    long long base, ts, cs;
+    int line, chunk;
+    bool nyq;
+    __device__ __forceinline__ ColGeom(int tile, int axis) {
+        nyq = tile >= N * NCH;
+        if (!nyq) {
+            line = tile / NCH;
+            chunk = tile % NCH;
+            if (axis == 0) { base = line * PLANE + chunk * CW; ts = NRP; cs = 1; }
+            else { base = (long long)line * NRP + chunk * CW; ts = PLANE; cs = 1; }
+        } else {
+            line = (tile - N * NCH) * CW;
+            chunk = 0;
+            if (axis == 0) { base = line * PLANE + M; ts = NRP; cs = PLANE; }
+            else { base = (long long)line * NRP + M; ts = PLANE; cs = NRP; }
+        }
+    }
+    __device__ __forceinline__ long long at(int idx) const { return base + (long long)(idx / CW) * ts + (idx % CW) * cs; }
+};
+
+template <int N, int DIR, int OUT>
+__global__ void __launch_bounds__(col_threads_of(N)) k_cols_pp(ColArgs a, int ntiles) {
+    constexpr int NT = col_threads_of(N);
+    constexpr int CW = cw_of(N), BP = odd_pad(CW), M = N / 2;
+    constexpr int TILE = N * CW, PER = (TILE + NT - 1) / NT;
+    extern __shared__ float4 smem_raw[];
+    float2* tw = reinterpret_cast<float2*>(smem_raw);
+    float2* buf = tw + N;
+    for (int i = threadIdx.x; i < N; i += NT) tw[i] = a.tw[i];
+    int tile = blockIdx.x;
+    float2 cur[PER];
+    if (tile < ntiles) {
+        const ColGeom<N> g(tile + a.tile0, a.axis);
+#pragma unroll
+        for (int i = 0; i < PER; ++i)
+            if (TILE % NT == 0 || threadIdx.x + i * NT < TILE) cur[i] = a.src[g.at(threadIdx.x + i * NT)];
+    }
+    while (tile < ntiles) {
+        const ColGeom<N> g(tile + a.tile0, a.axis);
+        const int next = tile + gridDim.x;
+        float2 nxt[PER];
+        if (next < ntiles) {
+            const ColGeom<N> gn(next + a.tile0, a.axis);
+#pragma unroll
+            for (int i = 0; i < PER; ++i)
+                if (TILE % NT == 0 || threadIdx.x + i * NT < TILE) nxt[i] = a.src[gn.at(threadIdx.x + i * NT)];
+        }
+        __syncthreads(); // the previous tile's results have left shared memory
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int idx = threadIdx.x + i * NT;
+            if (TILE % NT == 0 || idx < TILE) buf[(idx / CW) * BP + (idx % CW)] = cur[i];
+        }
+        __syncthreads();
+        fft_smem<N, DIR, CW, BP, NT>(buf, tw);
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int idx = threadIdx.x + i * NT;
+            if (!(TILE % NT == 0 || idx < TILE)) continue;
+            const int t = idx / CW, col = idx % CW;
+            const float2 v = buf[t * BP + col];
+            if constexpr (OUT == COL_OUT_PLAIN) {
+                a.dst[g.at(idx)] = v;
+            } else if constexpr (OUT == COL_OUT_BF16) {
+                a.dst_bf16[g.at(idx)] = __floats2bfloat162_rn(v.x, v.y);
+            } else {
+                const int q = g.nyq ? g.line + col : g.line;
+                const int r = g.nyq ? M : g.chunk * CW + col;
+                if (t <= q && q <= r) a.wedge_out[wedge_index(t, q, r) * a.wedge_A + a.wedge_j] = v.x;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < PER; ++i) cur[i] = nxt[i];
+        tile = next;
+    }
+}
+
+// ------------------------------------------------------------------------
+// z rows, complex -> real, persistent with the next block's loads in flight.
 template <int N>
-__global__ void __launch_bounds__(kThreads) k_rows_c2r(RowC2RArgs a) {
+__global__ void __launch_bounds__(kThreads) k_rows_c2r(RowC2RArgs a, int nblocks) {
     constexpr int B = row_pairs_of(N), BP = odd_pad(B), NRP = nrp_of(N), H = N / 2 + 1;
     constexpr int TILE = B * H, PER = (TILE + kThreads - 1) / kThreads;
     extern __shared__ float4 smem_raw[];
     float2* tw = reinterpret_cast<float2*>(smem_raw);
     float2* buf = tw + N;
-    const long long row0 = (long long)blockIdx.x * (2 * B);
-    float2 xa[PER], xb[PER];
+    auto fetch = [&](int blk, float2* xa, float2* xb) {
+        const long long row0 = (long long)blk * (2 * B);
 #pragma unroll
-    for (int i = 0; i < PER; ++i) {
-        const int idx = threadIdx.x + i * kThreads;
-        const int pair = idx / H, k = idx % H;
-        const long long ra = row0 + 2 * pair, rb = ra + 1;
-        const bool ok = TILE % kThreads == 0 || idx < TILE;
-        xa[i] = (ok && ra < a.nrows) ? a.src[ra * NRP + k] : make_float2(0.f, 0.f);
-        xb[i] = (ok && rb < a.nrows) ? a.src[rb * NRP + k] : make_float2(0.f, 0.f);
-    }
+        for (int i = 0; i < PER; ++i) {
+            const int idx = threadIdx.x + i * kThreads;
+            const int pair = idx / H, k = idx % H;
+            const long long ra = row0 + 2 * pair, rb = ra + 1;
+            const bool ok = TILE % kThreads == 0 || idx < TILE;
+            xa[i] = (ok && ra < a.nrows) ? a.src[ra * NRP + k] : make_float2(0.f, 0.f);
+            xb[i] = (ok && rb < a.nrows) ? a.src[rb * NRP + k] : make_float2(0.f, 0.f);
+        }
+    };
     for (int i = threadIdx.x; i < N; i += kThreads) tw[i] = a.tw[i];
-    // Z_k = X_a(k) + i X_b(k), with the Hermitian extension X(N-k) = conj X(k)
+    float2 ca[PER], cb[PER], na[PER], nb[PER];
+    int blk = blockIdx.x;
+    if (blk < nblocks) fetch(blk, ca, cb);
+    while (blk < nblocks) {
+        const int next = blk + gridDim.x;
+        if (next < nblocks) fetch(next, na, nb);
+        __syncthreads();
+        // Z_k = X_a(k) + i X_b(k), with the Hermitian extension X(N-k) = conj X(k)
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int idx = threadIdx.x + i * kThreads;
+            if (!(TILE % kThreads == 0 || idx < TILE)) continue;
+            const int pair = idx / H, k = idx % H;
+            float2 A = ca[i], Bv = cb[i];
+            if (k == 0 || k == N / 2) { A.y = 0.f; Bv.y = 0.f; }
+            buf[k * BP + pair] = make_float2(A.x - Bv.y, A.y + Bv.x);
+            if (k > 0 && k < N / 2) buf[(N - k) * BP + pair] = make_float2(A.x + Bv.y, Bv.x - A.y);
+        }
+        __syncthreads();
+        fft_smem<N, 1, B, BP>(buf, tw);
+        const long long row0 = (long long)blk * (2 * B);
+        for (int idx = threadIdx.x; idx < 2 * B * N; idx += kThreads) {
+            const int rr = idx / N, t = idx % N;
+            const long long grow = row0 + rr;
+            if (grow >= a.nrows) continue;
+            const float2 v = buf[t * BP + (rr >> 1)];
+            a.out[grow * N + t] = ((rr & 1) ? v.y : v.x) * a.scale;
+        }
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            ca[i] = na[i];
+            cb[i] = nb[i];
+        }
+        blk = next;
+    }
+}
+
+// ------------------------------------------------------------------------
+// Plane kernels (grids whose half plane fits in shared memory, N <= 192):
+// one CTA per x-plane does the z and y axes of the forward (or inverse)
+// transform in shared memory, replacing two full passes through memory.
+// Layout: plane[y * H + k], H = N/2 + 1 (odd, so both axes are bank-conflict
+// free); the z transform runs on row pairs in the same buffer as [t * H + pair].
+__host__ __device__ constexpr int plane_threads_of(int n) { return n == 128 ? 1024 : (n >= 64 ? 512 : 256); }
+template <int N> __host__ __device__ constexpr size_t plane_smem_bytes() {
+    return sizeof(float2) * (N + (size_t)N * (N / 2 + 1));
+}
+template <int N> __host__ __device__ constexpr bool plane_ok() { return N <= 192 && plane_smem_bytes<N>() <= 227 * 1024; }
+
+template <int N, int IN>
+__global__ void __launch_bounds__(plane_threads_of(N)) k_plane_r2c(RowR2CArgs a) {
+    constexpr int NT = plane_threads_of(N), H = N / 2 + 1, NRP = nrp_of(N), P = N / 2;
+    constexpr int TILE = N * N, PER = (TILE + NT - 1) / NT;
+    constexpr int UN = P * H, UPER = (UN + NT - 1) / NT;
+    extern __shared__ float4 smem_raw[];
+    float2* tw = reinterpret_cast<float2*>(smem_raw);
+    float2* pl = tw + N;
+    const int x = blockIdx.x;
+    float scale = 1.0f;
+    double gsc = 1.0;
+    if constexpr (IN == ROW_IN_I64) {
+        const double S = a.slot_S[a.slot];
+        const long long tot = a.slot_total[a.slot];
+        scale = a.bf16 ? (tot > 0 ? (float)(1.0 / (double)tot) : 0.0f) : (float)S;
+    }
+    if constexpr (IN == ROW_IN_WEDGE) gsc = *a.gscale;
+    float val[PER];
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
-        const int idx = threadIdx.x + i * kThreads;
-        if (!(TILE % kThreads == 0 || idx < TILE)) continue;
-        const int pair = idx / H, k = idx % H;
-        float2 A = xa[i], Bv = xb[i];
-        if (k == 0 || k == N / 2) { A.y = 0.f; Bv.y = 0.f; }
-        buf[k * BP + pair] = make_float2(A.x - Bv.y, A.y + Bv.x);
-        if (k > 0 && k < N / 2) buf[(N - k) * BP + pair] = make_float2(A.x + Bv.y, Bv.x - A.y);
+        const int idx = threadIdx.x + i * NT;
+        val[i] = 0.0f;
+        if (TILE % NT == 0 || idx < TILE) {
+            const int y = idx / N, t = idx % N;
+            const long long g = ((long long)x * N + y) * N + t;
+            if constexpr (IN == ROW_IN_I64) val[i] = __ll2float_rn(a.grid[g]) * scale;
+            else if constexpr (IN == ROW_IN_F32) val[i] = a.fin[g];
+            else {
+                const int fx = x <= N - x ? x : N - x, fy = y <= N - y ? y : N - y, fz = t <= N - t ? t : N - t;
+                const int mx = fx > fy ? (fx > fz ? fx : fz) : (fy > fz ? fy : fz);
+                val[i] = mx <= a.near_r ? 0.0f : (float)(a.gw[wedge_of(x, y, t, N)] * gsc);
+            }
+        }
+    }
+    for (int i = threadIdx.x; i < N; i += NT) tw[i] = a.tw[i];
+    float* pf = reinterpret_cast<float*>(pl);
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int idx = threadIdx.x + i * NT;
+        if (TILE % NT == 0 || idx < TILE) {
+            const int y = idx / N, t = idx % N;
+            pf[2 * (t * H + (y >> 1)) + (y & 1)] = val[i]; // row pair y/2, real / imaginary part
+        }
     }
     __syncthreads();
-    fft_smem<N, 1, B, BP>(buf, tw);
-    for (int idx = threadIdx.x; idx < 2 * B * N; idx += kThreads) {
-        const int rr = idx / N, t = idx % N;
-        const long long grow = row0 + rr;
-        if (grow >= a.nrows) continue;
-        const float2 v = buf[t * BP + (rr >> 1)];
-        a.out[grow * N + t] = ((rr & 1) ? v.y : v.x) * a.scale;
+    fft_smem<N, -1, P, H, NT>(pl, tw); // z: N/2 complex row pairs
+    // unpack pairs into the half plane [y][k]
+    float2 xa[UPER], xb[UPER];
+#pragma unroll
+    for (int i = 0; i < UPER; ++i) {
+        const int idx = threadIdx.x + i * NT;
+        if (UN % NT == 0 || idx < UN) {
+            const int pair = idx / H, k = idx % H;
+            const float2 zk = pl[k * H + pair];
+            const float2 zn = pl[(k == 0 ? 0 : N - k) * H + pair];
+            xa[i] = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
+            xb[i] = make_float2(0.5f * (zk.y + zn.y), 0.5f * (zn.x - zk.x));
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < UPER; ++i) {
+        const int idx = threadIdx.x + i * NT;
+        if (UN % NT == 0 || idx < UN) {
+            const int pair = idx / H, k = idx % H;
+            pl[(2 * pair) * H + k] = xa[i];
+            pl[(2 * pair + 1) * H + k] = xb[i];
+        }
+    }
+    __syncthreads();
+    fft_smem<N, -1, H, H, NT>(pl, tw); // y: the H columns of the half plane
+    for (int idx = threadIdx.x; idx < N * H; idx += NT) {
+        const int y = idx / H, k = idx % H;
+        a.dst[((long long)x * N + y) * NRP + k] = pl[y * H + k];
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(plane_threads_of(N)) k_plane_c2r(RowC2RArgs a) {
+    constexpr int NT = plane_threads_of(N), H = N / 2 + 1, NRP = nrp_of(N), P = N / 2;
+    constexpr int LD = N * H, LPER = (LD + NT - 1) / NT;
+    constexpr int UN = P * H, UPER = (UN + NT - 1) / NT;
+    extern __shared__ float4 smem_raw[];
+    float2* tw = reinterpret_cast<float2*>(smem_raw);
+    float2* pl = tw + N;
+    const int x = blockIdx.x;
+    float2 v[LPER];
+#pragma unroll
+    for (int i = 0; i < LPER; ++i) {
+        const int idx = threadIdx.x + i * NT;
+        if (LD % NT == 0 || idx < LD) {
+            const int y = idx / H, k = idx % H;
+            v[i] = a.src[((long long)x * N + y) * NRP + k];
+        }
+    }
+    for (int i = threadIdx.x; i < N; i += NT) tw[i] = a.tw[i];
+#pragma unroll
+    for (int i = 0; i < LPER; ++i) {
+        const int idx = threadIdx.x + i * NT;
+        if (LD % NT == 0 || idx < LD) pl[idx] = v[i]; // [y][k]
+    }
+    __syncthreads();
+    fft_smem<N, 1, H, H, NT>(pl, tw); // y inverse
+    // pack rows (2 pair, 2 pair + 1) into Z_k = X_a(k) + i X_b(k), Hermitian-extended in k
+    float2 z0[UPER], z1[UPER];
+#pragma unroll
+    for (int i = 0; i < UPER; ++i) {
+        const int idx = threadIdx.x + i * NT;
+        if (UN % NT == 0 || idx < UN) {
+            const int pair = idx / H, k = idx % H;
+            float2 A = pl[(2 * pair) * H + k], B = pl[(2 * pair + 1) * H + k];
+            if (k == 0 || k == N / 2) { A.y = 0.f; B.y = 0.f; }
+            z0[i] = make_float2(A.x - B.y, A.y + B.x);
+            z1[i] = make_float2(A.x + B.y, B.x - A.y);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < UPER; ++i) {
+        const int idx = threadIdx.x + i * NT;
+        if (UN % NT == 0 || idx < UN) {
+            const int pair = idx / H, k = idx % H;
+            pl[k * H + pair] = z0[i];
+            if (k > 0 && k < N / 2) pl[(N - k) * H + pair] = z1[i];
+        }
+    }
+    __syncthreads();
+    fft_smem<N, 1, P, H, NT>(pl, tw); // z inverse on row pairs
+    for (int idx = threadIdx.x; idx < N * N; idx += NT) {
+        const int y = idx / N, t = idx % N;
+        const float2 w = pl[t * H + (y >> 1)];
+        a.out[((long long)x * N + y) * N + t] = ((y & 1) ? w.y : w.x) * a.scale;
     }
 }
 
@@ -331,6 +625,9 @@ struct FftOps {
     void (*rows_r2c)(const RowR2CArgs&, cudaStream_t);
     void (*cols)(const ColArgs&, cudaStream_t);
     void (*rows_c2r)(const RowC2RArgs&, cudaStream_t);
+    // z + y in one kernel per x-plane (null where the half plane does not fit)
+    void (*plane_r2c)(const RowR2CArgs&, cudaStream_t);
+    void (*plane_c2r)(const RowC2RArgs&, cudaStream_t);
     // fused TMA shell MAC over the full tiles (null where not built), FP32 / BF16 ring
     void (*mac_f32)(const void* tensor_map, const MacArgs&, cudaStream_t);
     void (*mac_bf16)(const void* tensor_map, const MacArgs&, cudaStream_t);
@@ -340,6 +637,19 @@ struct FftOps {
 template <int N> struct Launch {
     static constexpr int CW = cw_of(N), NCH = (N / 2) / CW;
     static int col_tiles() { return N * NCH + N / CW; }
+    // CTAs of a persistent pass: 4 per SM (the SM count is read once per process)
+    static int pp_ctas() {
+        static int sms = 0;
+        if (!sms) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+                cudaGetLastError();
+                sms = 148;
+            }
+        }
+        return 4 * sms;
+    }
     static long long row_blocks() { return ((long long)N * N + 2 * row_pairs_of(N) - 1) / (2 * row_pairs_of(N)); }
 
     static cudaError_t init() {
@@ -351,35 +661,59 @@ template <int N> struct Launch {
         LC_ATTR((k_rows_r2c<N, ROW_IN_F32>), rs);
         LC_ATTR((k_rows_r2c<N, ROW_IN_WEDGE>), rs);
         LC_ATTR((k_rows_c2r<N>), rs);
-        LC_ATTR((k_cols<N, -1, COL_IN_PLAIN, COL_OUT_PLAIN>), cs);
-        LC_ATTR((k_cols<N, -1, COL_IN_PLAIN, COL_OUT_BF16>), cs);
-        LC_ATTR((k_cols<N, -1, COL_IN_PLAIN, COL_OUT_WEDGE>), cs);
-        LC_ATTR((k_cols<N, 1, COL_IN_PLAIN, COL_OUT_PLAIN>), cs);
+        LC_ATTR((k_cols_pp<N, -1, COL_OUT_PLAIN>), cs);
+        LC_ATTR((k_cols_pp<N, -1, COL_OUT_BF16>), cs);
+        LC_ATTR((k_cols_pp<N, -1, COL_OUT_WEDGE>), cs);
+        LC_ATTR((k_cols_pp<N, 1, COL_OUT_PLAIN>), cs);
         LC_ATTR((k_cols<N, 1, COL_IN_MAC_F32, COL_OUT_PLAIN>), cs);
         LC_ATTR((k_cols<N, 1, COL_IN_MAC_BF16, COL_OUT_PLAIN>), cs);
+        if constexpr (plane_ok<N>()) {
+            const int ps = (int)plane_smem_bytes<N>();
+            LC_ATTR((k_plane_r2c<N, ROW_IN_I64>), ps);
+            LC_ATTR((k_plane_r2c<N, ROW_IN_F32>), ps);
+            LC_ATTR((k_plane_r2c<N, ROW_IN_WEDGE>), ps);
+            LC_ATTR((k_plane_c2r<N>), ps);
+        }
 #undef LC_ATTR
         return e;
     }
+    static void plane_r2c(const RowR2CArgs& a, cudaStream_t st) {
+        if constexpr (plane_ok<N>()) {
+            const size_t sm = plane_smem_bytes<N>();
+            constexpr int NT = plane_threads_of(N);
+            if (a.in_mode == ROW_IN_I64) k_plane_r2c<N, ROW_IN_I64><<<N, NT, sm, st>>>(a);
+            else if (a.in_mode == ROW_IN_F32) k_plane_r2c<N, ROW_IN_F32><<<N, NT, sm, st>>>(a);
+            else k_plane_r2c<N, ROW_IN_WEDGE><<<N, NT, sm, st>>>(a);
+        }
+    }
+    static void plane_c2r(const RowC2RArgs& a, cudaStream_t st) {
+        if constexpr (plane_ok<N>()) k_plane_c2r<N><<<N, plane_threads_of(N), plane_smem_bytes<N>(), st>>>(a);
+    }
     static void rows_r2c(const RowR2CArgs& a, cudaStream_t st) {
-        const dim3 g((unsigned)row_blocks());
+        const int nb = (int)row_blocks();
+        const dim3 g((unsigned)(nb < pp_ctas() ? nb : pp_ctas()));
         const size_t sm = rows_smem_bytes<N>();
-        if (a.in_mode == ROW_IN_I64) k_rows_r2c<N, ROW_IN_I64><<<g, kThreads, sm, st>>>(a);
-        else if (a.in_mode == ROW_IN_F32) k_rows_r2c<N, ROW_IN_F32><<<g, kThreads, sm, st>>>(a);
-        else k_rows_r2c<N, ROW_IN_WEDGE><<<g, kThreads, sm, st>>>(a);
+        if (a.in_mode == ROW_IN_I64) k_rows_r2c<N, ROW_IN_I64><<<g, kThreads, sm, st>>>(a, nb);
+        else if (a.in_mode == ROW_IN_F32) k_rows_r2c<N, ROW_IN_F32><<<g, kThreads, sm, st>>>(a, nb);
+        else k_rows_r2c<N, ROW_IN_WEDGE><<<g, kThreads, sm, st>>>(a, nb);
     }
     static void rows_c2r(const RowC2RArgs& a, cudaStream_t st) {
-        k_rows_c2r<N><<<(unsigned)row_blocks(), kThreads, rows_smem_bytes<N>(), st>>>(a);
+        const int nb = (int)row_blocks();
+        k_rows_c2r<N><<<(unsigned)(nb < pp_ctas() ? nb : pp_ctas()), kThreads, rows_smem_bytes<N>(), st>>>(a, nb);
     }
     static void cols(const ColArgs& a, cudaStream_t st) {
         const dim3 g((unsigned)(col_tiles() - a.tile0));
         const size_t sm = cols_smem_bytes<N>();
         constexpr int kThreads = col_threads_of(N);
+        const int ntiles = col_tiles() - a.tile0;
+        // persistent plain passes: a few CTAs per SM, each walking tiles
+        const dim3 gp((unsigned)(ntiles < pp_ctas() ? ntiles : pp_ctas()));
         if (a.dir < 0) {
-            if (a.out_mode == COL_OUT_PLAIN) k_cols<N, -1, COL_IN_PLAIN, COL_OUT_PLAIN><<<g, kThreads, sm, st>>>(a);
-            else if (a.out_mode == COL_OUT_BF16) k_cols<N, -1, COL_IN_PLAIN, COL_OUT_BF16><<<g, kThreads, sm, st>>>(a);
-            else k_cols<N, -1, COL_IN_PLAIN, COL_OUT_WEDGE><<<g, kThreads, sm, st>>>(a);
+            if (a.out_mode == COL_OUT_PLAIN) k_cols_pp<N, -1, COL_OUT_PLAIN><<<gp, kThreads, sm, st>>>(a, ntiles);
+            else if (a.out_mode == COL_OUT_BF16) k_cols_pp<N, -1, COL_OUT_BF16><<<gp, kThreads, sm, st>>>(a, ntiles);
+            else k_cols_pp<N, -1, COL_OUT_WEDGE><<<gp, kThreads, sm, st>>>(a, ntiles);
         } else {
-            if (a.in_mode == COL_IN_PLAIN) k_cols<N, 1, COL_IN_PLAIN, COL_OUT_PLAIN><<<g, kThreads, sm, st>>>(a);
+            if (a.in_mode == COL_IN_PLAIN) k_cols_pp<N, 1, COL_OUT_PLAIN><<<gp, kThreads, sm, st>>>(a, ntiles);
             else if (a.in_mode == COL_IN_MAC_F32) k_cols<N, 1, COL_IN_MAC_F32, COL_OUT_PLAIN><<<g, kThreads, sm, st>>>(a);
             else k_cols<N, 1, COL_IN_MAC_BF16, COL_OUT_PLAIN><<<g, kThreads, sm, st>>>(a);
         }

@@ -41,25 +41,32 @@ constexpr int kGRow = kGBlock + 1; // padded smem row (bank-conflict free)
 
 template <int N, bool BF16> struct MacCfg {
     static constexpr int CW = cw_of(N), NRP = nrp_of(N), M = N / 2, NCH = M / CW, BP = odd_pad(CW);
-    // pipeline depth: 4 stages where the shared memory allows, else 2
-    static constexpr int STAGES = (BF16 || N <= 128) ? 4 : 2;
-    static constexpr int NT = col_threads_of(N);
+    static constexpr int NT = col_threads_of(N), NWARPS = NT / 32;
     static constexpr int TILE = N * CW, PER = (TILE + NT - 1) / NT;
     static constexpr int EB = BF16 ? 4 : 8;                  // bytes per ring element
     static constexpr int STAGE_BYTES = TILE * EB;
     static constexpr int BOXES = N > 256 ? 2 : 1;           // TMA boxes per stage (p extent <= 256)
     static constexpr int GROWS = (M + 1) * CW;              // distinct Ghat rows of a tile
+    static constexpr int GLOADS = (2 * GROWS + NT - 1) / NT; // float4 Ghat loads per thread per block
+    static constexpr size_t G_BYTES = ((size_t)GROWS * kGRow * 4 + 127) / 128 * 128;
+    static constexpr size_t FIXED = G_BYTES + (size_t)N * 8 + (size_t)kMaxShells * 12 + 2 * 8 * 8 + 256;
+    static constexpr size_t BUDGET = 227 * 1024;
+    // as many stages (<= 8) as the shared memory holds; the x-transform
+    // buffer reuses the stage area once the MAC loop is done
+    static constexpr int FIT = BUDGET > FIXED ? (int)((BUDGET - FIXED) / STAGE_BYTES) : 0;
+    static constexpr int STAGES = FIT > 8 ? 8 : FIT;
+    static constexpr size_t STAGE_AREA = (size_t)STAGES * STAGE_BYTES > (size_t)N * BP * 8
+                                             ? (size_t)STAGES * STAGE_BYTES : (size_t)N * BP * 8;
     // shared memory layout (bytes)
     static constexpr size_t OFF_STAGE = 0;                                     // 128-B aligned
-    static constexpr size_t OFF_G = OFF_STAGE + (size_t)STAGES * STAGE_BYTES;
-    static constexpr size_t OFF_BUF = (OFF_G + (size_t)GROWS * kGRow * 4 + 15) / 16 * 16;
-    static constexpr size_t OFF_TW = OFF_BUF + (size_t)N * BP * 8;
+    static constexpr size_t OFF_G = (OFF_STAGE + STAGE_AREA + 127) / 128 * 128;
+    static constexpr size_t OFF_TW = OFF_G + G_BYTES;
     static constexpr size_t OFF_LIST = OFF_TW + (size_t)N * 8;
     static constexpr size_t OFF_BAR = (OFF_LIST + (size_t)kMaxShells * 12 + 15) / 16 * 16;
-    static constexpr size_t SMEM = OFF_BAR + STAGES * 8 + 128; // + alignment slack
+    static constexpr size_t SMEM = OFF_BAR + 2 * 8 * 8 + 128; // full + empty barriers, alignment slack
     // the fused TMA MAC serves grids whose tiles are 16 columns wide and whose
-    // p extent fits one or two TMA boxes within the shared-memory budget
-    static constexpr bool OK = N >= 32 && N <= 256 && SMEM <= 227 * 1024;
+    // p extent fits one or two TMA boxes, with at least 2 pipeline stages
+    static constexpr bool OK = N >= 32 && N <= 256 && STAGES >= 2 && SMEM <= BUDGET;
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -67,6 +74,9 @@ __device__ __forceinline__ unsigned smem_u32(const void* p) {
 }
 __device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 __device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
@@ -102,45 +112,35 @@ __device__ __forceinline__ void tma_load_4d(unsigned dst, const CUtensorMap* map
 template <int N, bool BF16>
 __global__ void __launch_bounds__(MacCfg<N, BF16>::NT) k_mac_tma(const __grid_constant__ CUtensorMap ring, MacArgs a) {
     using C = MacCfg<N, BF16>;
-    constexpr int NT = C::NT, CW = C::CW, PER = C::PER, TILE = C::TILE, M = C::M, BP = C::BP;
+    constexpr int NT = C::NT, CW = C::CW, PER = C::PER, TILE = C::TILE, BP = C::BP, S = C::STAGES;
     extern __shared__ unsigned char smem_raw2[];
     unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw2) + 127) & ~uintptr_t(127));
     unsigned char* stage = sm + C::OFF_STAGE;
+    float2* buf = reinterpret_cast<float2*>(sm + C::OFF_STAGE); // after the MAC loop only
     float* gblk = reinterpret_cast<float*>(sm + C::OFF_G);
-    float2* buf = reinterpret_cast<float2*>(sm + C::OFF_BUF);
     float2* tw = reinterpret_cast<float2*>(sm + C::OFF_TW);
     int* s_slot = reinterpret_cast<int*>(sm + C::OFF_LIST);
     int* s_j = s_slot + kMaxShells;
     float* s_D = reinterpret_cast<float*>(s_j + kMaxShells);
-    unsigned long long* bars = reinterpret_cast<unsigned long long*>(sm + C::OFF_BAR);
+    unsigned long long* full = reinterpret_cast<unsigned long long*>(sm + C::OFF_BAR);
+    unsigned long long* empty = full + 8;
     __shared__ int s_nv, s_fail;
     __shared__ double s_dc;
 
     const int tile = blockIdx.x; // full tiles only
     const int line = tile / C::NCH, chunk = tile % C::NCH;
     const bool dc_tile = line == 0 && chunk == 0;
+    const int lane = threadIdx.x & 31;
 
+    if (threadIdx.x < 32)
+        mac_slot_list(a.A, a.step, a.n_ring, a.slot_step, a.slot_total, a.slot_S, a.g0, a.bf16 != 0, s_slot, s_j, s_D,
+                      &s_nv, &s_dc);
     if (threadIdx.x == 0) {
-        int nv = 0;
-        double dc = 0.0;
-        for (int j = 0; j < a.A; ++j) {
-            const int n = a.step - j;
-            if (n < 0) break;
-            const int slot = n % a.n_ring;
-            if (a.slot_step[slot] != n) continue;
-            const long long tot = a.slot_total[slot];
-            if (tot == 0) continue;
-            const double lum = a.slot_S[slot] * (double)tot;
-            s_slot[nv] = slot;
-            s_j[nv] = j;
-            s_D[nv] = a.bf16 ? (float)lum : 1.0f;
-            dc += a.g0[j] * lum;
-            ++nv;
-        }
-        s_nv = nv;
-        s_dc = dc;
         s_fail = 0;
-        for (int s = 0; s < C::STAGES; ++s) mbar_init(smem_u32(&bars[s]), 1);
+        for (int s = 0; s < S; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), C::NWARPS);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     for (int i = threadIdx.x; i < N; i += NT) tw[i] = a.tw[i];
@@ -149,8 +149,8 @@ __global__ void __launch_bounds__(MacCfg<N, BF16>::NT) k_mac_tma(const __grid_co
     // ring coordinates: {r (elements), q, p, slot}; FP32 complex = 2 floats
     const int c0 = chunk * CW * (BF16 ? 1 : 2);
     auto issue = [&](int v) {
-        const int st = v % C::STAGES;
-        const unsigned bar = smem_u32(&bars[st]);
+        const int st = v % S;
+        const unsigned bar = smem_u32(&full[st]);
         mbar_expect_tx(bar, C::STAGE_BYTES);
 #pragma unroll
         for (int b = 0; b < C::BOXES; ++b)
@@ -158,7 +158,37 @@ __global__ void __launch_bounds__(MacCfg<N, BF16>::NT) k_mac_tma(const __grid_co
                         c0, line, b * (N / C::BOXES), s_slot[v], bar);
     };
     if (threadIdx.x == 0)
-        for (int v = 0; v < nv && v < C::STAGES; ++v) issue(v);
+        for (int v = 0; v < nv && v < S; ++v) issue(v);
+
+    // Ghat rows of the tile: row = p' * CW + col, wedge w(p', q, r)
+    long long gbase[C::GLOADS];
+#pragma unroll
+    for (int k = 0; k < C::GLOADS; ++k) {
+        const int rr = threadIdx.x + k * NT;
+        const int row = rr >> 1, half = rr & 1;
+        gbase[k] = rr < 2 * C::GROWS
+                       ? wedge_of(row / CW, line, chunk * CW + row % CW, N) * a.gstride + half * 4
+                       : -1;
+    }
+    float4 gpre[C::GLOADS];
+    auto gfetch = [&](int blk) {
+#pragma unroll
+        for (int k = 0; k < C::GLOADS; ++k)
+            if (gbase[k] >= 0) gpre[k] = __ldg(reinterpret_cast<const float4*>(a.ghat + gbase[k] + blk * kGBlock));
+    };
+    auto gstore = [&]() {
+#pragma unroll
+        for (int k = 0; k < C::GLOADS; ++k) {
+            const int rr = threadIdx.x + k * NT;
+            if (gbase[k] >= 0) {
+                float* d = gblk + (rr >> 1) * kGRow + (rr & 1) * 4;
+                d[0] = gpre[k].x;
+                d[1] = gpre[k].y;
+                d[2] = gpre[k].z;
+                d[3] = gpre[k].w;
+            }
+        }
+    };
 
     // this thread's elements: tile index idx -> (t = p, col)
     int grow[PER];
@@ -173,30 +203,29 @@ __global__ void __launch_bounds__(MacCfg<N, BF16>::NT) k_mac_tma(const __grid_co
 #pragma unroll
     for (int i = 0; i < PER; ++i) acc[i] = make_float2(0.f, 0.f);
 
-    int cur_blk = -1;
+    int cur_blk = -1, pre_blk = -1;
+    if (nv > 0) {
+        pre_blk = s_j[0] / kGBlock;
+        gfetch(pre_blk);
+    }
     bool ok = true;
     for (int v = 0; v < nv; ++v) {
         const int j = s_j[v];
         const int blk = j / kGBlock;
         if (blk != cur_blk) {
-            // stage Ghat rows w(p', q, r) for slices [8 blk, 8 blk + 8)
+            // switch the staged Ghat block (slices [8 blk, 8 blk + 8)); the next
+            // block's rows are fetched into registers while this one is used
             __syncthreads();
-            for (int rr = threadIdx.x; rr < C::GROWS * 2; rr += NT) {
-                const int row = rr >> 1, half = rr & 1;
-                const int pf = row / CW, col = row % CW;
-                const float4 g4 = __ldg(reinterpret_cast<const float4*>(
-                    a.ghat + wedge_of(pf, line, chunk * CW + col, N) * a.gstride + blk * kGBlock + half * 4));
-                float* d = gblk + row * kGRow + half * 4;
-                d[0] = g4.x;
-                d[1] = g4.y;
-                d[2] = g4.z;
-                d[3] = g4.w;
-            }
+            if (pre_blk != blk) gfetch(blk);
+            gstore();
             __syncthreads();
             cur_blk = blk;
+            pre_blk = blk + 1;
+            if ((blk + 1) * kGBlock < a.A) gfetch(blk + 1);
         }
-        const int st = v % C::STAGES;
-        ok = mbar_wait_bounded(smem_u32(&bars[st]), (unsigned)((v / C::STAGES) & 1)) && ok;
+        const int st = v % S;
+        const unsigned par = (unsigned)((v / S) & 1);
+        ok = mbar_wait_bounded(smem_u32(&full[st]), par) && ok;
         const int jj = j - blk * kGBlock;
         const float D = s_D[v];
 #pragma unroll
@@ -216,17 +245,22 @@ __global__ void __launch_bounds__(MacCfg<N, BF16>::NT) k_mac_tma(const __grid_co
                 acc[i].y = fmaf(g, f.y, acc[i].y);
             }
         }
-        __syncthreads(); // stage st consumed by every thread
-        if (threadIdx.x == 0 && v + C::STAGES < nv) issue(v + C::STAGES);
+        // release the stage: one arrival per warp; the producer refills it
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&empty[st]));
+        if (threadIdx.x == 0 && v + S < nv) {
+            ok = mbar_wait_bounded(smem_u32(&empty[st]), par) && ok;
+            issue(v + S);
+        }
     }
     if (!ok) {
         atomicOr(&s_fail, 1);
         // give copies still in flight a second bounded wait before the CTA
         // (and its shared memory) goes away
-        for (int v = nv - C::STAGES > 0 ? nv - C::STAGES : 0; v < nv; ++v)
-            mbar_wait_bounded(smem_u32(&bars[v % C::STAGES]), (unsigned)((v / C::STAGES) & 1));
+        for (int v = nv - S > 0 ? nv - S : 0; v < nv; ++v)
+            mbar_wait_bounded(smem_u32(&full[v % S]), (unsigned)((v / S) & 1));
     }
-    __syncthreads();
+    __syncthreads(); // every stage consumed: the stage area becomes the x-transform buffer
     if (s_fail && threadIdx.x == 0) atomicOr(a.err, 4);
     if (dc_tile && threadIdx.x == 0) acc[0] = make_float2((float)s_dc, 0.0f);
 #pragma unroll

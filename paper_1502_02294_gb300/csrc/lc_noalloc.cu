@@ -86,7 +86,6 @@ extern "C" lc_status lc_fft_r2c_static(int n, const float* in, float* out_comple
     ra.fin = in;
     ra.dst = work;
     ra.tw = tw;
-    ops->rows_r2c(ra, st);
     ColArgs c{};
     c.axis = 0;
     c.dir = -1;
@@ -95,7 +94,12 @@ extern "C" lc_status lc_fft_r2c_static(int n, const float* in, float* out_comple
     c.src = work;
     c.dst = work;
     c.tw = tw;
-    ops->cols(c, st);
+    if (ops->plane_r2c) {
+        ops->plane_r2c(ra, st);
+    } else {
+        ops->rows_r2c(ra, st);
+        ops->cols(c, st);
+    }
     c.axis = 1;
     ops->cols(c, st);
     const int h = n / 2 + 1;
