@@ -42,6 +42,8 @@ WORKLOADS = {
     "c1": "32^3 grid, 100 Mpc box, 8 equal-time steps z=20->15 (<=2 shells), 200 uniform sources, FP32",
     "c3": ("256^3 grid, 200 Mpc box, 128 equal-conformal-time shells spanning the LW horizon at z=15, "
            "1e5 clustered sources, BF16 history with per-slot FP32 scale"),
+    "c3s": ("256^3 grid, 200 Mpc box, 32 equal-conformal-time shells, 40 steps, 1e5 clustered sources, "
+            "BF16 history (profiling size of the c3 path)"),
 }
 
 

@@ -22,6 +22,7 @@ catalogues stand in for it.  Their structure follows the workload list:
 * ``c3``  256^3 grid, 200 Mpc box, 128 equal-conformal-time shells spanning
   the Lyman-Werner horizon at z_obs = 15, 160 steps, 1e5 clustered sources
   (1000 centres), history stored in BF16.
+* ``c3s`` the same 256^3 BF16 path with 32 shells and 40 steps (a profiling size).
 * ``c4``  16 uneven instances (grids 64..256, 32..128 shells, 1e3..1e5
   sources, 0.78 Mpc cells).
 * ``c5``  8 served simulations at 128^3..512^3.
@@ -154,6 +155,13 @@ def config(name: str) -> Workload:
         cat = make_catalogue(SEED_BASE + 2, 100_000, 200.0, 160, clustered=True,
                              n_centres=1000, sigma=2.0)
         return Workload("c3", 256, 200.0, 0.31, 0.68, st, 4, HISTORY_BF16, cat)
+    if name == "c3s":
+        # the 256^3 BF16 path at a profiling size: 32 equal-conformal-time
+        # shells (ring ~1.1 GB), 40 steps, 1e5 clustered sources
+        st = StepSpec(STEPS_EQUAL_TAU, 40, z_end=15.0, n_shell=32)
+        cat = make_catalogue(SEED_BASE + 77, 100_000, 200.0, 40, clustered=True,
+                             n_centres=1000, sigma=2.0)
+        return Workload("c3s", 256, 200.0, 0.31, 0.68, st, 4, HISTORY_BF16, cat)
     raise KeyError(name)
 
 
