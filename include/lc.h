@@ -185,6 +185,20 @@ lc_status lc_graph_create(lc_plan* plan, int step, int64_t n_src, const double* 
 lc_status lc_graph_launch(lc_step_graph* graph);
 lc_status lc_graph_destroy(lc_step_graph* graph);
 
+/* Many uneven instances (plans of different N, shell counts and source
+ * counts), one observing step each, captured as ONE CUDA graph: every
+ * instance's push + field is a parallel branch, so the instances overlap on
+ * the device and the whole batch is one launch.  Arguments are arrays of n
+ * (a plan at most once); pointers are device pointers, read/written at every
+ * replay.  Launch on `cuda_stream` (NULL: the default stream); each plan's
+ * steps must increase across launches as for lc_push_sources. */
+typedef struct lc_batch_graph lc_batch_graph;
+lc_status lc_batch_graph_create(lc_plan* const* plans, int n, const int* steps, const int64_t* n_src,
+                                const double* const* pos, const double* const* lum, float* const* outs,
+                                lc_batch_graph** graph);
+lc_status lc_batch_graph_launch(lc_batch_graph* graph, void* cuda_stream);
+lc_status lc_batch_graph_destroy(lc_batch_graph* graph);
+
 /* --- tracing ------------------------------------------------------------------ */
 
 /* Phases of one step, each timed with a pair of CUDA events on the plan's

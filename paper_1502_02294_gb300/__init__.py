@@ -81,6 +81,10 @@ SIGNATURES = [
     ("lc_graph_create", _I, [_P, _I, _I64, _VP, _VP, _VP, ctypes.POINTER(_P)]),
     ("lc_graph_launch", _I, [_P]),
     ("lc_graph_destroy", _I, [_P]),
+    ("lc_batch_graph_create", _I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_I), ctypes.POINTER(_I64),
+                                   ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_P)]),
+    ("lc_batch_graph_launch", _I, [_P, _VP]),
+    ("lc_batch_graph_destroy", _I, [_P]),
     ("lc_plan_set_timing", _I, [_P, _I]),
     ("lc_plan_timing", _I, [_P, _DP, ctypes.POINTER(_I64), _I]),
     ("lc_kernel_launches", ctypes.c_uint64, []),
@@ -317,6 +321,40 @@ class StepGraph:
             pass
 
 
+class BatchGraph:
+    """One step of several (uneven) plans captured as one CUDA graph whose
+    branches run concurrently; `sources[i]` = (pos, lum) device tensors,
+    `outs[i]` a device float32 tensor of plans[i].n ** 3."""
+
+    def __init__(self, plans, steps, sources, outs):
+        n = len(plans)
+        self.plans = list(plans)
+        self._keep = (list(sources), list(outs))
+        hp = (ctypes.c_void_p * n)(*[p._h for p in plans])
+        st = (ctypes.c_int * n)(*[int(s) for s in steps])
+        ns = (ctypes.c_int64 * n)(*[int(src[1].shape[0]) for src in sources])
+        pp = (ctypes.c_void_p * n)(*[src[0].data_ptr() if src[1].shape[0] else None for src in sources])
+        lp = (ctypes.c_void_p * n)(*[src[1].data_ptr() if src[1].shape[0] else None for src in sources])
+        op = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+        h = ctypes.c_void_p()
+        _check(_lib().lc_batch_graph_create(hp, n, st, ns, pp, lp, op, ctypes.byref(h)), "lc_batch_graph_create")
+        self._g = h
+
+    def launch(self, stream=None):
+        _check(_lib().lc_batch_graph_launch(self._g, _stream_ptr(stream)), "lc_batch_graph_launch")
+
+    def close(self):
+        if getattr(self, "_g", None):
+            _lib().lc_batch_graph_destroy(self._g)
+        self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def batch_step(plans, steps, sources, outs):
     """Push (if sources[i] is not None) and evaluate several plans at once."""
     n = len(plans)
@@ -398,6 +436,6 @@ def fft_c2r(X, scale: Optional[float] = None, stream=None):
     return out
 
 
-__all__ = ["Plan", "batch_step", "deposit_grid", "fft_r2c", "fft_c2r", "build", "estimate_bytes", "LCError",
+__all__ = ["Plan", "StepGraph", "BatchGraph", "batch_step", "deposit_grid", "fft_r2c", "fft_c2r", "build", "estimate_bytes", "LCError",
            "SIGNATURES", "LIB_PATH", "SUPPORTED_N", "STEPS_EXPLICIT", "STEPS_EQUAL_TIME", "STEPS_EQUAL_TAU",
            "HISTORY_FP32", "HISTORY_BF16"]

@@ -178,6 +178,14 @@ struct lc_plan {
     std::vector<lc_step_graph*> graphs;
 };
 
+struct lc_batch_graph {
+    std::vector<lc_plan*> plans;
+    std::vector<int> steps;
+    std::vector<long long> n_src;
+    cudaGraphExec_t exec = nullptr;
+    long long kernels = 0;
+};
+
 struct lc_step_graph {
     lc_plan* p = nullptr;
     int step = 0;
@@ -956,17 +964,18 @@ lc_status lc_plan_green_wedge(lc_plan* p, int step, int lookback, float* out, do
 }
 
 // ------------------------------------------------------------ step graphs
-lc_status lc_graph_create(lc_plan* p, int step, int64_t n_src, const double* pos, const double* lum, float* out,
-                          lc_step_graph** out_graph) {
-    if (!p || !out_graph || !out) return LC_ERR_INVALID_ARG;
-    *out_graph = nullptr;
+// Checks and preparation shared by the graph captures: device pointers
+// only, the step's table built and every buffer the step needs allocated
+// (nothing may be allocated or synchronised during a capture).
+static lc_status prepare_capture(lc_plan* p, int step, int64_t n_src, const double* pos, const double* lum,
+                                 float* out) {
+    if (!p || !out) return LC_ERR_INVALID_ARG;
     if (p->failed) return LC_ERR_CUDA;
     if (step < 0 || step >= p->n_steps || n_src < 0) return LC_ERR_INVALID_ARG;
     if (!is_device_ptr(out) || (n_src > 0 && (!pos || !lum || !is_device_ptr(pos) || !is_device_ptr(lum))))
         return LC_ERR_INVALID_ARG; // a graph holds device pointers only
     lc_status r = build_table(p, step);
     if (r != LC_OK) return r;
-    // make every buffer the step needs exist before capture
     if (p->near_on && n_src > p->near_cap) {
         cudaFree(p->d_src_cell);
         cudaFree(p->d_src_q);
@@ -978,6 +987,15 @@ lc_status lc_graph_create(lc_plan* p, int step, int64_t n_src, const double* pos
             return LC_ERR_OOM;
         p->near_cap = cap;
     }
+    return LC_OK;
+}
+
+lc_status lc_graph_create(lc_plan* p, int step, int64_t n_src, const double* pos, const double* lum, float* out,
+                          lc_step_graph** out_graph) {
+    if (!out_graph) return LC_ERR_INVALID_ARG;
+    *out_graph = nullptr;
+    lc_status r = prepare_capture(p, step, n_src, pos, lum, out);
+    if (r != LC_OK) return r;
     lc_step_graph* g = new (std::nothrow) lc_step_graph();
     if (!g) return LC_ERR_OOM;
     g->p = p;
@@ -1065,6 +1083,110 @@ lc_status lc_graph_destroy(lc_step_graph* g) {
             p->graphs.erase(p->graphs.begin() + i);
             break;
         }
+    delete g;
+    return LC_OK;
+}
+
+// ------------------------------------------------------------ batched instances
+lc_status lc_batch_graph_create(lc_plan* const* plans, int n, const int* steps, const int64_t* n_src,
+                                const double* const* pos, const double* const* lum, float* const* outs,
+                                lc_batch_graph** out_graph) {
+    if (!plans || n < 1 || !steps || !n_src || !outs || !out_graph) return LC_ERR_INVALID_ARG;
+    *out_graph = nullptr;
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < i; ++k)
+            if (plans[i] == plans[k]) return LC_ERR_INVALID_ARG; // one step per plan per batch
+    for (int i = 0; i < n; ++i) {
+        lc_status r = prepare_capture(plans[i], steps[i], n_src[i], pos ? pos[i] : nullptr, lum ? lum[i] : nullptr,
+                                      outs[i]);
+        if (r != LC_OK) return r;
+    }
+    lc_batch_graph* g = new (std::nothrow) lc_batch_graph();
+    if (!g) return LC_ERR_OOM;
+    g->plans.assign(plans, plans + n);
+    g->steps.assign(steps, steps + n);
+    g->n_src.assign(n_src, n_src + n);
+    // origin stream s0 forks one branch per instance (its own stream) and joins them
+    cudaStream_t s0 = nullptr;
+    std::vector<cudaStream_t> br(n, nullptr);
+    std::vector<cudaEvent_t> done(n, nullptr);
+    cudaEvent_t fork = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s0, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&br[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming);
+    }
+    cudaGraph_t graph = nullptr;
+    lc_status rs = LC_OK;
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaEventRecord(fork, s0);
+        for (int i = 0; i < n && rs == LC_OK; ++i) {
+            lc_plan* p = plans[i];
+            cudaStreamWaitEvent(br[i], fork, 0);
+            const cudaStream_t user_stream = p->stream;
+            const int saved_last = p->last_pushed;
+            const long long saved_near = p->near_n;
+            const bool saved_timing = p->timing;
+            for (int k = 0; k < LC_N_PHASES; ++k) p->cap_kernels[k] = 0;
+            p->stream = br[i];
+            p->capturing = true;
+            p->timing = false;
+            p->last_pushed = steps[i] - 1;
+            rs = lc_push_sources(p, steps[i], n_src[i], pos ? pos[i] : nullptr, lum ? lum[i] : nullptr);
+            if (rs == LC_OK) rs = lc_retarded_field(p, steps[i], outs[i]);
+            for (int k = 0; k < LC_N_PHASES; ++k) g->kernels += p->cap_kernels[k];
+            p->capturing = false;
+            p->timing = saved_timing;
+            p->stream = user_stream;
+            p->last_pushed = saved_last;
+            p->near_n = saved_near;
+            cudaEventRecord(done[i], br[i]);
+            cudaStreamWaitEvent(s0, done[i], 0);
+        }
+        cudaError_t e2 = cudaStreamEndCapture(s0, &graph);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess && rs == LC_OK) e = cudaGraphInstantiate(&g->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    for (int i = 0; i < n; ++i) {
+        if (br[i]) cudaStreamDestroy(br[i]);
+        if (done[i]) cudaEventDestroy(done[i]);
+    }
+    if (fork) cudaEventDestroy(fork);
+    if (s0) cudaStreamDestroy(s0);
+    if (rs != LC_OK || e != cudaSuccess) {
+        delete g;
+        cudaGetLastError();
+        return rs != LC_OK ? rs : LC_ERR_CUDA;
+    }
+    *out_graph = g;
+    return LC_OK;
+}
+
+lc_status lc_batch_graph_launch(lc_batch_graph* g, void* stream) {
+    if (!g || !g->exec) return LC_ERR_INVALID_ARG;
+    for (size_t i = 0; i < g->plans.size(); ++i) {
+        if (g->plans[i]->failed) return LC_ERR_CUDA;
+        if (g->steps[i] <= g->plans[i]->last_pushed) return LC_ERR_STEP_ORDER;
+    }
+    cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        for (auto* p : g->plans) p->failed = true;
+        return LC_ERR_CUDA;
+    }
+    for (size_t i = 0; i < g->plans.size(); ++i) {
+        g->plans[i]->last_pushed = g->steps[i];
+        g->plans[i]->near_n = g->plans[i]->near_on ? g->n_src[i] : 0;
+    }
+    count_launch((unsigned long long)g->kernels);
+    return LC_OK;
+}
+
+lc_status lc_batch_graph_destroy(lc_batch_graph* g) {
+    if (!g) return LC_ERR_INVALID_ARG;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
     delete g;
     return LC_OK;
 }
