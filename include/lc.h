@@ -118,6 +118,15 @@ lc_status lc_push_sources(lc_plan* plan, int step, int64_t n_src, const double* 
  * `out` it only enqueues work on the plan's stream. */
 lc_status lc_retarded_field(lc_plan* plan, int step, float* out);
 
+/* The same field computed "instantaneously" (action at a distance, Eq. 18 of
+ * Section 3): every shell's Green's function is applied to the sources of
+ * step `step` itself, i.e. the source distribution frozen at the observing
+ * redshift, with all other factors (dilution, (1+z)^3/(1+z_s), f_mod, the
+ * light-travel radius of each shell) kept.  The fractional difference
+ * (J_instant - J) / J is the paper's f_diff.  Same arguments and rules as
+ * lc_retarded_field. */
+lc_status lc_instant_field(lc_plan* plan, int step, float* out);
+
 /* Forget the history (ring) so that steps can start again at 0; the Green's
  * function tables are kept. */
 lc_status lc_plan_reset(lc_plan* plan);

@@ -252,6 +252,15 @@ def field_for(prob: Problem, cat, s: int, cells: Optional[np.ndarray] = None) ->
     return prob.field(s, source_grids(prob, cat, s), cells)
 
 
+def instant_field_for(prob: Problem, cat, s: int, cells: Optional[np.ndarray] = None) -> np.ndarray:
+    """Eq. 18: the same shells and kernel, every shell applied to the sources
+    of the observing step s (source term frozen at the observing redshift)."""
+    A = prob.active_shells(s)
+    pos, lum = cat.active(s)
+    g = deposit_ngp(prob.n, prob.box, pos, lum) if lum.shape[0] else None
+    return prob.field(s, [g] * A, cells)
+
+
 def dft3(x: np.ndarray, sign: int = -1) -> np.ndarray:
     n = x.shape[0]
     re = np.ascontiguousarray(x.real, dtype=np.float64).ravel()

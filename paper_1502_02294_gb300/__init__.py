@@ -65,6 +65,7 @@ SIGNATURES = [
     ("lc_plan_prepare", _I, [_P, _I, _I]),
     ("lc_push_sources", _I, [_P, _I, _I64, _VP, _VP]),
     ("lc_retarded_field", _I, [_P, _I, _VP]),
+    ("lc_instant_field", _I, [_P, _I, _VP]),
     ("lc_plan_reset", _I, [_P]),
     ("lc_plan_check", _I, [_P]),
     ("lc_plan_set_stream", _I, [_P, _VP]),
@@ -241,6 +242,16 @@ class Plan:
             assert out.dtype.itemsize == 4 and out.is_contiguous() and out.numel() == self.n ** 3
             ptr = out.data_ptr()
         _check(_lib().lc_retarded_field(self._h, int(step), ptr), "lc_retarded_field")
+        return out
+
+    def instant_field(self, step: int, out=None):
+        """Action-at-a-distance field of Eq. 18: every shell sees the sources
+        of `step` itself (the last pushed step)."""
+        if out is None:
+            torch = _torch()
+            out = torch.empty((self.n,) * 3, dtype=torch.float32, device="cuda")
+        ptr = out.ctypes.data if isinstance(out, np.ndarray) else out.data_ptr()
+        _check(_lib().lc_instant_field(self._h, int(step), ptr), "lc_instant_field")
         return out
 
     def reset(self):

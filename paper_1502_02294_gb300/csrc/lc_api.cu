@@ -17,9 +17,6 @@
 #include <new>
 #include <vector>
 
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
 #include "lc_internal.h"
 #include "lc_mac.cuh"
 
@@ -71,22 +68,6 @@ static bool is_device_ptr(const void* p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link)
-static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-    static std::once_flag once;
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    std::call_once(once, [] {
-        void* f = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
-        else
-            cudaGetLastError();
-    });
-    return fn;
-}
-
 static std::vector<float2> twiddles(int n) {
     std::vector<float2> t(n);
     for (int m = 0; m < n; ++m) {
@@ -134,9 +115,7 @@ struct lc_plan {
     long long src_cap = 0;
     float* d_out_stage = nullptr;
     // Green's function tables, one per observing step (built lazily)
-    // the ring as a 4-D tensor [slot][p][q][r] for the TMA shell MAC
-    alignas(64) CUtensorMap ring_map;
-    bool has_map = false;
+    long long ring_slot = 0; // complex elements per tile-major ring slot: N^2 (N/2 + 1)
     struct Table {
         int gstride = 0;        // row stride of ghat: A rounded up to 8
         float* ghat = nullptr;  // [W][gstride]; shell 0 without its near cube when near_on
@@ -491,10 +470,10 @@ lc_status lc_plan_estimate(int n, const lc_steps* steps, const lc_cosmology* cos
         StepGeom g = step_geometry(c, z, s, 1.0, 2, false);
         ring = g.A > ring ? g.A : ring;
     }
-    const long long nrp = nrp_of(n), spec = (long long)n * n * nrp;
+    const long long nrp = nrp_of(n), spec = (long long)n * n * nrp, slot = (long long)n * n * (n / 2 + 1);
     const long long hb = steps->history == LC_HISTORY_BF16 ? 4 : 8;
     const long long W = (long long)(n / 2 + 1) * (n / 2 + 2) * (n / 2 + 3) / 6;
-    if (base_bytes) *base_bytes = (size_t)(8LL * n * n * n + 8 * spec + hb * spec * ring + 4LL * n * n * n);
+    if (base_bytes) *base_bytes = (size_t)(8LL * n * n * n + 8 * spec + hb * slot * ring + 4LL * n * n * n);
     if (table_bytes_per_step) *table_bytes_per_step = (size_t)(4 * W * ring + 8 * ring);
     return LC_OK;
 }
@@ -528,6 +507,7 @@ lc_status lc_plan_create(int n, double box_mpc, const lc_cosmology* cosmo, const
     p->NRP = nrp_of(n);
     p->spec_elems = (long long)n * n * p->NRP;
     p->W = (long long)(n / 2 + 1) * (n / 2 + 2) * (n / 2 + 3) / 6;
+    p->ring_slot = (long long)n * n * (n / 2 + 1);
     if (step_edges(p->cosmo, *steps, p->z)) {
         delete p;
         return LC_ERR_INVALID_ARG;
@@ -556,7 +536,7 @@ lc_status lc_plan_create(int n, double box_mpc, const lc_cosmology* cosmo, const
     const size_t N3 = (size_t)n * n * n;
     const size_t hb = p->history == LC_HISTORY_BF16 ? 4 : 8;
     bool ok = dalloc(p, &p->d_grid, N3) == cudaSuccess && dalloc(p, &p->d_work, (size_t)p->spec_elems) == cudaSuccess &&
-              dalloc(p, (char**)&p->d_ring, hb * (size_t)p->spec_elems * p->n_ring) == cudaSuccess &&
+              dalloc(p, (char**)&p->d_ring, hb * (size_t)p->ring_slot * p->n_ring) == cudaSuccess &&
               dalloc(p, &p->d_slot_step, p->n_ring) == cudaSuccess && dalloc(p, &p->d_slot_S, p->n_ring) == cudaSuccess &&
               dalloc(p, &p->d_slot_total, p->n_ring) == cudaSuccess && dalloc(p, &p->d_tw, n) == cudaSuccess &&
               dalloc(p, &p->d_err, 1) == cudaSuccess && dalloc(p, &p->d_maxbits, 1) == cudaSuccess;
@@ -564,20 +544,6 @@ lc_status lc_plan_create(int n, double box_mpc, const lc_cosmology* cosmo, const
         free_all(p);
         delete p;
         return LC_ERR_OOM;
-    }
-    // ring tensor map for the TMA shell MAC: dims {r (4-B elements), q, p, slot}
-    if ((p->history == LC_HISTORY_BF16 ? ops->mac_bf16 : ops->mac_f32) && tensor_map_encoder()) {
-        const bool bf = p->history == LC_HISTORY_BF16;
-        const cuuint64_t inner = (cuuint64_t)(bf ? p->NRP : 2 * p->NRP);
-        cuuint64_t dims[4] = {inner, (cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)p->n_ring};
-        cuuint64_t strides[3] = {inner * 4, inner * 4 * n, inner * 4 * n * n};
-        cuuint32_t box[4] = {(cuuint32_t)(bf ? cw_of(n) : 2 * cw_of(n)), 1, (cuuint32_t)(n > 256 ? n / 2 : n), 1};
-        cuuint32_t es[4] = {1, 1, 1, 1};
-        CUresult r = tensor_map_encoder()(&p->ring_map, bf ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-                                          4, p->d_ring, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        p->has_map = r == CUDA_SUCCESS;
     }
     p->near_on = p->history == LC_HISTORY_FP32;
     if (p->near_on && dalloc(p, &p->d_near, N3) != cudaSuccess) {
@@ -697,10 +663,13 @@ lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos
     c.axis = 1;
     if (p->history == LC_HISTORY_BF16) {
         c.out_mode = COL_OUT_BF16;
-        c.dst_bf16 = reinterpret_cast<__nv_bfloat162*>(p->d_ring) + (size_t)slot * p->spec_elems;
+        c.dst_bf16 = reinterpret_cast<__nv_bfloat162*>(p->d_ring);
     } else {
-        c.dst = reinterpret_cast<float2*>(p->d_ring) + (size_t)slot * p->spec_elems;
+        c.out_mode = COL_OUT_RING_F32;
+        c.dst = reinterpret_cast<float2*>(p->d_ring);
     }
+    c.n_ring = p->n_ring;
+    c.wslot = slot;
     {
         Phase ph(p, LC_PHASE_FWD_X_RING, 1);
         p->ops->cols(c, st);
@@ -711,7 +680,13 @@ lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos
     return LC_OK;
 }
 
-lc_status lc_retarded_field(lc_plan* p, int step, float* out) {
+static lc_status field_impl(lc_plan* p, int step, float* out, int instant);
+
+lc_status lc_retarded_field(lc_plan* p, int step, float* out) { return field_impl(p, step, out, 0); }
+
+lc_status lc_instant_field(lc_plan* p, int step, float* out) { return field_impl(p, step, out, 1); }
+
+static lc_status field_impl(lc_plan* p, int step, float* out, int instant) {
     if (!p || !out) return LC_ERR_INVALID_ARG;
     if (p->failed) return LC_ERR_CUDA;
     if (step < 0 || step >= p->n_steps) return LC_ERR_INVALID_ARG;
@@ -738,7 +713,7 @@ lc_status lc_retarded_field(lc_plan* p, int step, float* out) {
         c.out_mode = COL_OUT_PLAIN;
         c.dst = p->d_work;
         c.ring = p->d_ring;
-        c.slot_elems = p->spec_elems;
+        c.slot_elems = p->ring_slot;
         c.n_ring = p->n_ring;
         c.step = step;
         c.A = T.A;
@@ -748,17 +723,18 @@ lc_status lc_retarded_field(lc_plan* p, int step, float* out) {
         c.ghat = T.ghat;
         c.g0 = T.g0;
         c.gstride = T.gstride;
+        c.instant = instant;
         c.tw = p->d_tw;
         const bool bf = p->history == LC_HISTORY_BF16;
         auto mac_fn = bf ? p->ops->mac_bf16 : p->ops->mac_f32;
         // the TMA pipeline pays off once there are enough slices to stream;
         // for a handful the register-gather pass is faster
-        if (mac_fn && p->has_map && T.A >= kMacTmaMinShells) {
-            // full tiles: TMA-pipelined MAC; the Nyquist column tiles: generic pass
+        if (mac_fn && T.A >= kMacTmaMinShells) {
+            // full tiles: bulk-copy pipelined MAC; the Nyquist column tiles: generic pass
             Phase ph(p, LC_PHASE_MAC_X, 2);
-            MacArgs ma{step, T.A, T.gstride, p->n_ring, p->d_slot_step, p->d_slot_S, p->d_slot_total,
-                       T.ghat, T.g0, p->d_work, p->d_tw, p->d_err, bf ? 1 : 0};
-            mac_fn(&p->ring_map, ma, st);
+            MacArgs ma{p->d_ring, p->ring_slot, step, T.A, T.gstride, p->n_ring, p->d_slot_step, p->d_slot_S,
+                       p->d_slot_total, T.ghat, T.g0, p->d_work, p->d_tw, p->d_err, bf ? 1 : 0, instant};
+            mac_fn(ma, st);
             c.tile0 = p->ops->full_tiles;
             p->ops->cols(c, st);
             c.tile0 = 0;

@@ -17,12 +17,8 @@ cudaError_t init_all() {
     if (e == cudaSuccess) e = MacLaunch<LC_N, true>::init();
     return e;
 }
-void mac_f32(const void* map, const MacArgs& a, cudaStream_t st) {
-    MacLaunch<LC_N, false>::run(static_cast<const CUtensorMap*>(map), a, st);
-}
-void mac_bf16(const void* map, const MacArgs& a, cudaStream_t st) {
-    MacLaunch<LC_N, true>::run(static_cast<const CUtensorMap*>(map), a, st);
-}
+void mac_f32(const MacArgs& a, cudaStream_t st) { MacLaunch<LC_N, false>::run(a, st); }
+void mac_bf16(const MacArgs& a, cudaStream_t st) { MacLaunch<LC_N, true>::run(a, st); }
 } // namespace
 extern const FftOps LC_CAT(fft_ops_, LC_N);
 const FftOps LC_CAT(fft_ops_, LC_N) = {LC_N,

@@ -21,7 +21,10 @@ namespace lc {
 
 enum { ROW_IN_I64 = 0, ROW_IN_F32 = 1, ROW_IN_WEDGE = 2 };
 enum { COL_IN_PLAIN = 0, COL_IN_MAC_F32 = 1, COL_IN_MAC_BF16 = 2 };
-enum { COL_OUT_PLAIN = 0, COL_OUT_BF16 = 1, COL_OUT_WEDGE = 2 };
+// COL_OUT_BF16 / COL_OUT_RING_F32 write one slot of the history ring, whose
+// layout is [tile][slot][N x CW elements]: the history of an x-pass tile over
+// all slots is one contiguous run, read as a stream by the shell MAC
+enum { COL_OUT_PLAIN = 0, COL_OUT_BF16 = 1, COL_OUT_WEDGE = 2, COL_OUT_RING_F32 = 3 };
 
 struct RowR2CArgs {
     int in_mode;
@@ -45,16 +48,18 @@ struct ColArgs {
     const float2* src;
     float2* dst;
     __nv_bfloat162* dst_bf16;
-    // shell MAC (inverse x-pass)
+    // shell MAC (inverse x-pass); the ring is [tile][slot][tile elements]
     const void* ring;
-    long long slot_elems;     // complex elements per ring slot
+    long long slot_elems;     // complex elements per ring slot (N^2 (N/2 + 1))
     int n_ring, step, A;
+    int wslot;                // ring write: the slot being written
     const int* slot_step;
     const double* slot_S;
     const long long* slot_total;
     const float* ghat;        // [wedge][A] real Ghat of this step
     const double* g0;         // [A] FP64 Ghat_j(0)
     int gstride;              // row stride of the Ghat table (A rounded up to 8)
+    int instant;              // 1: every shell uses the observing step's slice (Eq. 18)
     int tile0;                // first tile of this launch (tiles before it are skipped)
     // wedge extract (forward x-pass of a Green's function)
     float* wedge_out;
@@ -76,16 +81,18 @@ constexpr int kMaxShells = 1024;
 // increasing lookback j: slot, j, scale D (the slot's luminosity total for
 // BF16 history, 1 for FP32) and the FP64 k = 0 sum  sum_j Ghat_j(0) S_j q_j.
 // Run by one whole warp: 32 slices per round trip to memory.
+// instant != 0: every shell reads the slice of the observing step itself
+// (the source frozen at the observing redshift, Eq. 18).
 __device__ __forceinline__ void mac_slot_list(int A, int step, int n_ring, const int* slot_step,
                                               const long long* slot_total, const double* slot_S, const double* g0,
                                               bool bf16, int* out_slot, int* out_j, float* out_D, int* nv_out,
-                                              double* dc_out) {
+                                              double* dc_out, int instant = 0) {
     const int lane = threadIdx.x & 31;
     int nv = 0;
     double dc = 0.0;
     for (int j0 = 0; j0 < A; j0 += 32) {
         const int j = j0 + lane;
-        const int n = step - j;
+        const int n = instant ? step : step - j;
         bool valid = false;
         int slot = 0;
         double lum = 0.0;
@@ -258,9 +265,9 @@ __global__ void __launch_bounds__(col_threads_of(N)) k_cols(ColArgs a) {
         int* s_slot = reinterpret_cast<int*>(s_D + kMaxShells);
         if (threadIdx.x < 32)
             mac_slot_list(a.A, a.step, a.n_ring, a.slot_step, a.slot_total, a.slot_S, a.g0,
-                          IN == COL_IN_MAC_BF16, s_slot, s_j, s_D, &s_nv, &s_dc);
+                          IN == COL_IN_MAC_BF16, s_slot, s_j, s_D, &s_nv, &s_dc, a.instant);
         __syncthreads();
-        for (int v = threadIdx.x; v < s_nv; v += NT) s_off[v] = (long long)s_slot[v] * a.slot_elems;
+        for (int v = threadIdx.x; v < s_nv; v += NT) s_off[v] = (long long)s_slot[v] * TILE;
         for (int i = threadIdx.x; i < N; i += NT) tw[i] = a.tw[i];
         // wedge rows of Ghat for this thread's elements (x pass: t runs over p)
         const float* g[PER];
@@ -275,6 +282,7 @@ __global__ void __launch_bounds__(col_threads_of(N)) k_cols(ColArgs a) {
         }
         __syncthreads();
         const int nv = s_nv;
+        const long long tbase = (long long)tile * a.n_ring * TILE;
         // shells outer, the tile's elements inner: PER independent ring loads
         // (and Ghat loads) in flight per thread per shell
         for (int v = 0; v < nv; ++v) {
@@ -286,8 +294,9 @@ __global__ void __launch_bounds__(col_threads_of(N)) k_cols(ColArgs a) {
 #pragma unroll
             for (int i = 0; i < PER; ++i) {
                 if (TILE % NT == 0 || threadIdx.x + i * NT < TILE) {
-                    if constexpr (IN == COL_IN_MAC_F32) f[i] = reinterpret_cast<const float2*>(a.ring)[off + addr[i]];
-                    else f[i] = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(a.ring)[off + addr[i]]);
+                    const long long ri = off + tbase + threadIdx.x + i * NT; // tile-major ring slot
+                    if constexpr (IN == COL_IN_MAC_F32) f[i] = reinterpret_cast<const float2*>(a.ring)[ri];
+                    else f[i] = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(a.ring)[ri]);
                     gv[i] = __ldg(g[i] + jv);
                 }
             }
@@ -397,7 +406,10 @@ __global__ void __launch_bounds__(col_threads_of(N)) k_cols_pp(ColArgs a, int nt
             if constexpr (OUT == COL_OUT_PLAIN) {
                 a.dst[g.at(idx)] = v;
             } else if constexpr (OUT == COL_OUT_BF16) {
-                a.dst_bf16[g.at(idx)] = __floats2bfloat162_rn(v.x, v.y);
+                a.dst_bf16[((long long)(tile + a.tile0) * a.n_ring + a.wslot) * TILE + idx] =
+                    __floats2bfloat162_rn(v.x, v.y);
+            } else if constexpr (OUT == COL_OUT_RING_F32) {
+                a.dst[((long long)(tile + a.tile0) * a.n_ring + a.wslot) * TILE + idx] = v;
             } else {
                 const int q = g.nyq ? g.line + col : g.line;
                 const int r = g.nyq ? M : g.chunk * CW + col;
@@ -629,8 +641,8 @@ struct FftOps {
     void (*plane_r2c)(const RowR2CArgs&, cudaStream_t);
     void (*plane_c2r)(const RowC2RArgs&, cudaStream_t);
     // fused TMA shell MAC over the full tiles (null where not built), FP32 / BF16 ring
-    void (*mac_f32)(const void* tensor_map, const MacArgs&, cudaStream_t);
-    void (*mac_bf16)(const void* tensor_map, const MacArgs&, cudaStream_t);
+    void (*mac_f32)(const MacArgs&, cudaStream_t);
+    void (*mac_bf16)(const MacArgs&, cudaStream_t);
     int full_tiles; // tiles of the full 16-column chunks (the Nyquist tiles follow)
 };
 
@@ -664,6 +676,7 @@ template <int N> struct Launch {
         LC_ATTR((k_cols_pp<N, -1, COL_OUT_PLAIN>), cs);
         LC_ATTR((k_cols_pp<N, -1, COL_OUT_BF16>), cs);
         LC_ATTR((k_cols_pp<N, -1, COL_OUT_WEDGE>), cs);
+        LC_ATTR((k_cols_pp<N, -1, COL_OUT_RING_F32>), cs);
         LC_ATTR((k_cols_pp<N, 1, COL_OUT_PLAIN>), cs);
         LC_ATTR((k_cols<N, 1, COL_IN_MAC_F32, COL_OUT_PLAIN>), cs);
         LC_ATTR((k_cols<N, 1, COL_IN_MAC_BF16, COL_OUT_PLAIN>), cs);
@@ -711,6 +724,7 @@ template <int N> struct Launch {
         if (a.dir < 0) {
             if (a.out_mode == COL_OUT_PLAIN) k_cols_pp<N, -1, COL_OUT_PLAIN><<<gp, kThreads, sm, st>>>(a, ntiles);
             else if (a.out_mode == COL_OUT_BF16) k_cols_pp<N, -1, COL_OUT_BF16><<<gp, kThreads, sm, st>>>(a, ntiles);
+            else if (a.out_mode == COL_OUT_RING_F32) k_cols_pp<N, -1, COL_OUT_RING_F32><<<gp, kThreads, sm, st>>>(a, ntiles);
             else k_cols_pp<N, -1, COL_OUT_WEDGE><<<gp, kThreads, sm, st>>>(a, ntiles);
         } else {
             if (a.in_mode == COL_IN_PLAIN) k_cols_pp<N, 1, COL_OUT_PLAIN><<<gp, kThreads, sm, st>>>(a, ntiles);

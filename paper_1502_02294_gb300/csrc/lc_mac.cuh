@@ -5,10 +5,12 @@
 //   Jhat(p, q, r) = sum_j  Ghat_j(w(p, q, r)) * D_j * fhat_{s-j}(p, q, r)
 //
 // One CTA owns the tile (all p, line q, columns r in [c*CW, c*CW + CW)).
-//  * ring tiles: one TMA box per active slice (cp.async.bulk.tensor.4d over
-//    the ring viewed as [slot][p][q][r]), an S-stage mbarrier pipeline issued
-//    by thread 0; every wait is bounded and reports a timeout in the plan's
-//    error word instead of spinning;
+//  * ring tiles: the ring is [tile][slot][elements], so the tile's history
+//    over all slots is one contiguous run; a slice's tile is one block of it,
+//    brought in by one bulk asynchronous copy (cp.async.bulk, completion on
+//    an mbarrier) per slice in an S-stage pipeline issued by thread 0; every
+//    wait is bounded and reports a timeout in the plan's error word instead
+//    of spinning;
 //  * Ghat: the table is [wedge][A_pad] (slices of a wedge point contiguous);
 //    the tile needs the rows w(p', q, r) for p' = min(p, N - p), so blocks of
 //    8 slices are staged through shared memory, one 32-byte sector per
@@ -17,13 +19,13 @@
 //    transform and out to the work spectrum.
 // The k = 0 mode is replaced by its FP64 value.
 #pragma once
-#include <cuda.h>
-
 #include "lc_kernels.cuh"
 
 namespace lc {
 
 struct MacArgs {
+    const void* ring;      // [tile][slot][tile elements]
+    long long slot_elems;  // complex elements per slot
     int step, A, gstride, n_ring;
     const int* slot_step;
     const double* slot_S;
@@ -34,6 +36,7 @@ struct MacArgs {
     const float2* tw;
     int* err;          // bit 4: a pipeline wait gave up
     int bf16;
+    int instant;       // 1: every shell uses the observing step's slice (Eq. 18)
 };
 
 constexpr int kGBlock = 8;     // slices per staged Ghat block
@@ -45,7 +48,6 @@ template <int N, bool BF16> struct MacCfg {
     static constexpr int TILE = N * CW, PER = (TILE + NT - 1) / NT;
     static constexpr int EB = BF16 ? 4 : 8;                  // bytes per ring element
     static constexpr int STAGE_BYTES = TILE * EB;
-    static constexpr int BOXES = N > 256 ? 2 : 1;           // TMA boxes per stage (p extent <= 256)
     static constexpr int GROWS = (M + 1) * CW;              // distinct Ghat rows of a tile
     static constexpr int GLOADS = (2 * GROWS + NT - 1) / NT; // float4 Ghat loads per thread per block
     static constexpr size_t G_BYTES = ((size_t)GROWS * kGRow * 4 + 127) / 128 * 128;
@@ -64,8 +66,8 @@ template <int N, bool BF16> struct MacCfg {
     static constexpr size_t OFF_LIST = OFF_TW + (size_t)N * 8;
     static constexpr size_t OFF_BAR = (OFF_LIST + (size_t)kMaxShells * 12 + 15) / 16 * 16;
     static constexpr size_t SMEM = OFF_BAR + 2 * 8 * 8 + 128; // full + empty barriers, alignment slack
-    // the fused TMA MAC serves grids whose tiles are 16 columns wide and whose
-    // p extent fits one or two TMA boxes, with at least 2 pipeline stages
+    // the fused bulk-copy MAC serves grids whose tiles are 16 columns wide,
+    // with at least 2 pipeline stages in shared memory
     static constexpr bool OK = N >= 32 && N <= 256 && STAGES >= 2 && SMEM <= BUDGET;
 };
 
@@ -100,17 +102,16 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity)
     }
     return false;
 }
-__device__ __forceinline__ void tma_load_4d(unsigned dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
-                                            unsigned bar) {
+// one contiguous global -> shared copy, completion counted on an mbarrier
+__device__ __forceinline__ void bulk_load(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
     asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
-        "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(src)), "r"(bytes), "r"(bar)
         : "memory");
 }
 
 template <int N, bool BF16>
-__global__ void __launch_bounds__(MacCfg<N, BF16>::NT) k_mac_tma(const __grid_constant__ CUtensorMap ring, MacArgs a) {
+__global__ void __launch_bounds__(MacCfg<N, BF16>::NT) k_mac_tma(MacArgs a) {
     using C = MacCfg<N, BF16>;
     constexpr int NT = C::NT, CW = C::CW, PER = C::PER, TILE = C::TILE, BP = C::BP, S = C::STAGES;
     extern __shared__ unsigned char smem_raw2[];
@@ -134,7 +135,7 @@ __global__ void __launch_bounds__(MacCfg<N, BF16>::NT) k_mac_tma(const __grid_co
 
     if (threadIdx.x < 32)
         mac_slot_list(a.A, a.step, a.n_ring, a.slot_step, a.slot_total, a.slot_S, a.g0, a.bf16 != 0, s_slot, s_j, s_D,
-                      &s_nv, &s_dc);
+                      &s_nv, &s_dc, a.instant);
     if (threadIdx.x == 0) {
         s_fail = 0;
         for (int s = 0; s < S; ++s) {
@@ -146,16 +147,15 @@ __global__ void __launch_bounds__(MacCfg<N, BF16>::NT) k_mac_tma(const __grid_co
     for (int i = threadIdx.x; i < N; i += NT) tw[i] = a.tw[i];
     __syncthreads();
     const int nv = s_nv;
-    // ring coordinates: {r (elements), q, p, slot}; FP32 complex = 2 floats
-    const int c0 = chunk * CW * (BF16 ? 1 : 2);
+    // this tile's run of n_ring blocks
+    const unsigned char* ring_tile =
+        static_cast<const unsigned char*>(a.ring) + (size_t)tile * a.n_ring * C::STAGE_BYTES;
     auto issue = [&](int v) {
         const int st = v % S;
         const unsigned bar = smem_u32(&full[st]);
         mbar_expect_tx(bar, C::STAGE_BYTES);
-#pragma unroll
-        for (int b = 0; b < C::BOXES; ++b)
-            tma_load_4d(smem_u32(stage + (size_t)st * C::STAGE_BYTES + (size_t)b * (C::STAGE_BYTES / C::BOXES)), &ring,
-                        c0, line, b * (N / C::BOXES), s_slot[v], bar);
+        bulk_load(smem_u32(stage + (size_t)st * C::STAGE_BYTES), ring_tile + (size_t)s_slot[v] * C::STAGE_BYTES,
+                  C::STAGE_BYTES, bar);
     };
     if (threadIdx.x == 0)
         for (int v = 0; v < nv && v < S; ++v) issue(v);
@@ -288,8 +288,8 @@ template <int N, bool BF16> struct MacLaunch {
         if constexpr (!C::OK) return cudaSuccess;
         else return cudaFuncSetAttribute(k_mac_tma<N, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     }
-    static void run(const CUtensorMap* map, const MacArgs& a, cudaStream_t st) {
-        if constexpr (C::OK) k_mac_tma<N, BF16><<<N * C::NCH, C::NT, C::SMEM, st>>>(*map, a);
+    static void run(const MacArgs& a, cudaStream_t st) {
+        if constexpr (C::OK) k_mac_tma<N, BF16><<<N * C::NCH, C::NT, C::SMEM, st>>>(a);
     }
 };
 

@@ -294,3 +294,30 @@ def test_field_c3_bf16_full_size_sampled_cells():
         rel, mx, raw = errors(out[s].reshape(-1)[cells], ref)
         assert rel <= BF16_L2, (s, rel, raw)
     plan.close()
+
+
+def test_instant_field_eq18_against_oracle():
+    # Eq. 18: sources frozen at the observing redshift, all other factors kept
+    for hist, tol in ((synth.HISTORY_FP32, FP32_L2), (synth.HISTORY_BF16, BF16_L2)):
+        w = synth.config("c1")
+        w.history = hist
+        P = oracle.Problem.from_workload(w)
+        plan = lc.Plan.from_workload(w)
+        for s in range(8):
+            pos, lum = w.cat.active(s)
+            plan.push(s, torch.from_numpy(pos).cuda(), torch.from_numpy(lum).cuda())
+            if s in (4, 7):
+                Ji = plan.instant_field(s).cpu().numpy()
+                J = plan.field(s).cpu().numpy()
+                ref_i = oracle.instant_field_for(P, w.cat, s)
+                rel, mx, raw = errors(Ji, ref_i)
+                assert rel <= tol, (hist, s, rel)
+                if hist == synth.HISTORY_FP32:
+                    assert mx <= FP32_MAX, (s, mx, raw)
+                # the light-cone field differs from the instantaneous one
+                ref = oracle.field_for(P, w.cat, s)
+                fdiff = (ref_i - ref) / ref
+                gdiff = (Ji.astype(np.float64) - J) / J
+                assert np.abs(fdiff).max() > 1e-3
+                assert np.abs(gdiff - fdiff).max() < 50 * tol
+        plan.close()

@@ -228,3 +228,20 @@ def test_direct_convolution_equals_convolution_theorem(oracle_lib):
     # and the Green's function transforms are real (G even)
     for j in range(A):
         assert np.abs(np.fft.fftn(P.rgf_full(s, j)).imag).max() < 1e-12 * np.abs(P.rgf_full(s, j)).sum()
+
+
+def test_instant_field_equals_retarded_for_steady_sources(oracle_lib):
+    # Eq. 18 freezes the sources at the observing redshift; if the sources never
+    # change, the instantaneous and the light-cone fields coincide, and a source
+    # that switched on at the observing step is seen too early by Eq. 18.
+    w = synth.small(n=12, box=50.0, n_src=30, n_steps=5, life=(5, 5))
+    w.cat.birth[:] = 0
+    P = oracle_lib.Problem.from_workload(w)
+    s = 4
+    J = oracle_lib.field_for(P, w.cat, s)
+    Ji = oracle_lib.instant_field_for(P, w.cat, s)
+    assert np.allclose(Ji, J, rtol=1e-13)
+    w.cat.birth[:] = s  # all switched on at the observing step
+    Ji2 = oracle_lib.instant_field_for(P, w.cat, s)
+    J2 = oracle_lib.field_for(P, w.cat, s)
+    assert (Ji2 >= J2 - 1e-12 * np.abs(J2).max()).all() and Ji2.sum() > J2.sum()
