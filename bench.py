@@ -442,6 +442,9 @@ def main():
     plan.set_timing(True)
     graphs_timed = {s: plan.graph(s, *src_dev[s], out) for s in range(t0, T)}
     plan.set_timing(False)
+    # which shell-MAC kernel the autotuner picked for each active-slice count
+    tag = f"/N{w.n}/{'bf16' if w.history else 'fp32'}/"
+    mac_choice = {k.rsplit("/", 1)[1]: v for k, v in lc.autotune_report().items() if tag in k}
 
     def run_pass(gs, evs=None):
         refill()
@@ -568,11 +571,14 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32" if w.history else "f32", "data": "synthetic",
             "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "grid": w.n,
                        "box_mpc": w.box, "steps_in_run": T, "timed_window": [t0, T], "ring_slots": plan.n_ring,
-                       "history": "bf16" if w.history else "fp32", "l2": f"flushed between timed steps "
+                       "history": "bf16" if w.history else "fp32",
+                       "mac_kernel": {v: sum(1 for x in mac_choice.values() if x == v) for v in ("gather", "bulk")},
+                       "l2": f"flushed between timed steps "
                        f"({args.flush_mb} MB write outside the events)", "inputs": "device-resident"},
             "cell_shell_mac_per_s": world * mac_cells / t_max,
             "latency_ms": {"p50": float(np.percentile(per_step_ms, 50)), "p99": float(np.percentile(per_step_ms, 99))},
-            "roofline": {"bound": "hbm", "kernel": "k_cols<N,+1,MAC> (shell MAC + inverse x pass)",
+            "roofline": {"bound": "hbm", "kernel": "shell-MAC phase: k_cols<N,+1,MAC> (gather) or k_mac_tma + "
+                         "Nyquist k_cols (bulk), fused with the inverse x pass",
                          "achieved": mac_gbs, "peak": hbm_peak, "unit": "GB/s",
                          "frac": (mac_gbs / hbm_peak) if mac_gbs else None,
                          "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",

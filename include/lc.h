@@ -179,6 +179,30 @@ lc_status lc_plan_green_wedge(lc_plan* plan, int step, int lookback, float* out,
 lc_status lc_batch_step(lc_plan* const* plans, int n, const int* steps, const int64_t* n_src,
                         const double* const* pos, const double* const* lum, float* const* outs);
 
+/* --- checkpoint / resume ---------------------------------------------------------- */
+
+/* The state a plan carries from step to step is the history of past source
+ * spectra that the retarded sum of Eq. 11 reads (one slice per active shell),
+ * with each slice's fixed-point unit and exact total, the last pushed step,
+ * and the innermost slice's source cells (near field, FP32 history).  The
+ * Green's function tables are not part of it: they are a deterministic
+ * function of the plan's parameters and are rebuilt on demand.
+ *
+ * lc_plan_checkpoint_bytes: size of that state in bytes (a 256-byte header,
+ * the per-slot arrays, the near-field list, then the ring).
+ * lc_plan_save: writes it to buf (host or device memory, `size` >= that many
+ * bytes); returns after the copy has completed.  The header records N, the
+ * step count, ring depth, history precision and a 64-bit hash of every
+ * parameter that defines the method (box, cosmology, step edges, subsamples,
+ * normalisation, output unit).
+ * lc_plan_load: restores a checkpoint into a plan created with the same
+ * parameters (LC_ERR_INVALID_ARG if the header, hash or size does not match,
+ * leaving the plan unchanged); the next push must be for a later step than
+ * the saved one.  Both synchronise the plan's stream. */
+size_t lc_plan_checkpoint_bytes(const lc_plan* plan);
+lc_status lc_plan_save(lc_plan* plan, void* buf, size_t size);
+lc_status lc_plan_load(lc_plan* plan, const void* buf, size_t size);
+
 /* --- CUDA graphs of whole steps ------------------------------------------------ */
 
 /* One observing step captured as a CUDA graph: lc_push_sources(step, ...) then
@@ -231,6 +255,18 @@ lc_status lc_plan_timing(lc_plan* plan, double* ms, int64_t* launches, int reset
 /* Number of kernels this library has launched in this process (all plans and
  * stand-alone calls). */
 uint64_t lc_kernel_launches(void);
+
+/* --- autotuning ---------------------------------------------------------------- */
+
+/* The shell multiply-accumulate runs in one of two kernels (a register-gather
+ * pass, or a bulk-copy pipelined kernel for many slices); each plan times
+ * both on its own buffers when it first builds a table for a new (device, N,
+ * history, active slices) combination and keeps the faster.  Choices are
+ * shared by all plans of the process and persisted to the file named by the
+ * environment variable LC_AUTOTUNE_CACHE if set; LC_MAC_VARIANT=gather|bulk
+ * forces one kernel.  This writes the current choices ("key variant" lines)
+ * into buf (size bytes, NUL-terminated) and returns the full length. */
+int lc_autotune_report(char* buf, int size);
 
 /* --- the hot-path kernels as stand-alone calls (tests, users) --------------- */
 

@@ -29,6 +29,18 @@ SUPPORTED_N = (8, 16, 32, 64, 96, 128, 192, 256, 384, 512)
 PHASES = ("deposit", "r2c_z", "fwd_y", "fwd_x_ring", "mac_x", "inv_y", "c2r_z", "near")
 
 
+def autotune_report() -> dict:
+    """The autotuner's current kernel choices: {key: variant}."""
+    n = _lib().lc_autotune_report(None, 0)
+    buf = ctypes.create_string_buffer(n + 1)
+    _lib().lc_autotune_report(buf, n + 1)
+    out = {}
+    for line in buf.value.decode().splitlines():
+        k, v = line.split()
+        out[k] = v
+    return out
+
+
 def kernel_launches() -> int:
     """Kernels liblc has launched in this process."""
     return int(_lib().lc_kernel_launches())
@@ -93,6 +105,10 @@ SIGNATURES = [
     ("lc_fft_r2c", _I, [_I, _VP, _VP, _VP]),
     ("lc_fft_c2r", _I, [_I, _VP, _VP, ctypes.c_float, _VP]),
     ("lc_fft_r2c_static", _I, [_I, _VP, _VP, _VP]),
+    ("lc_autotune_report", _I, [ctypes.c_char_p, _I]),
+    ("lc_plan_checkpoint_bytes", ctypes.c_size_t, [_P]),
+    ("lc_plan_save", _I, [_P, _VP, ctypes.c_size_t]),
+    ("lc_plan_load", _I, [_P, _VP, ctypes.c_size_t]),
 ]
 
 _L = None
@@ -293,6 +309,26 @@ class Plan:
         _check(_lib().lc_plan_timing(self._h, ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                      cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), int(reset)), "lc_plan_timing")
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(PHASES)}
+
+    def checkpoint_bytes(self) -> int:
+        return int(_lib().lc_plan_checkpoint_bytes(self._h))
+
+    def save(self, buf=None):
+        """Write the plan's history state into `buf` (numpy uint8 array or torch
+        uint8 tensor, host or device); a new numpy array if buf is None."""
+        n = self.checkpoint_bytes()
+        if buf is None:
+            buf = np.empty(n, dtype=np.uint8)
+        ptr = buf.ctypes.data if isinstance(buf, np.ndarray) else buf.data_ptr()
+        size = buf.nbytes if isinstance(buf, np.ndarray) else buf.numel() * buf.element_size()
+        _check(_lib().lc_plan_save(self._h, ptr, size), "lc_plan_save")
+        return buf
+
+    def load(self, buf):
+        """Restore a state written by save() of a plan with the same parameters."""
+        ptr = buf.ctypes.data if isinstance(buf, np.ndarray) else buf.data_ptr()
+        size = buf.nbytes if isinstance(buf, np.ndarray) else buf.numel() * buf.element_size()
+        _check(_lib().lc_plan_load(self._h, ptr, size), "lc_plan_load")
 
     def green_wedge(self, step: int, lookback: int):
         out = np.zeros(self.wedge_size, dtype=np.float32)

@@ -13,7 +13,9 @@
 #include <string.h>
 
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <string>
 #include <new>
 #include <vector>
 
@@ -84,8 +86,45 @@ static inline void count_launch(unsigned long long k = 1) { g_launches.fetch_add
 
 using namespace lc;
 
-// fewest active slices for which the TMA shell MAC is used
-static const int kMacTmaMinShells = 12;
+// ---------------------------------------------------------------- autotuner
+// The shell MAC has two variants: a register-gather pass (MAC_GATHER) and a
+// bulk-copy pipelined kernel (MAC_BULK) for the full tiles.  Which one is
+// faster depends on the grid, the history precision and the number of
+// active slices; the plan times both on its own buffers the first time it
+// meets a (device, N, history, slices) combination and keeps the faster.
+// Choices are kept per process and, when LC_AUTOTUNE_CACHE names a file,
+// loaded from and appended to that file.  LC_MAC_VARIANT=gather|bulk
+// forces one variant (tests).
+enum { MAC_GATHER = 0, MAC_BULK = 1 };
+namespace {
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;
+bool g_tune_loaded = false;
+
+void tune_load() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char* path = getenv("LC_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE* f = fopen(path, "r");
+    if (!f) return;
+    char key[256];
+    int v;
+    double a, b;
+    while (fscanf(f, "%255s %d %lf %lf", key, &v, &a, &b) == 4) g_tune[key] = v;
+    fclose(f);
+}
+
+void tune_store(const std::string& key, int v, double ms_gather, double ms_bulk) {
+    g_tune[key] = v;
+    const char* path = getenv("LC_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s %d %.6f %.6f\n", key.c_str(), v, ms_gather, ms_bulk);
+    fclose(f);
+}
+} // namespace
 
 struct lc_plan {
     int N = 0;
@@ -121,6 +160,7 @@ struct lc_plan {
         float* ghat = nullptr;  // [W][gstride]; shell 0 without its near cube when near_on
         double* g0 = nullptr;   // [A] FP64 Ghat_j(0) of what the FFT path carries
         double* gnear = nullptr; // near cube of shell 0 on the wedge prefix (near_on)
+        int mac_variant = 0;    // MAC_GATHER or MAC_BULK, chosen by the autotuner
         int A = -1;             // -1: not built
     };
     std::vector<Table> tables;
@@ -132,6 +172,10 @@ struct lc_plan {
     long long* d_bnd = nullptr;
     double* d_I = nullptr;
     double* d_scale = nullptr;
+    // autotuner scratch: slot tables marking every slice valid
+    int* d_tune_step = nullptr;
+    double* d_tune_S = nullptr;
+    long long* d_tune_total = nullptr;
     // near field of the innermost shell, added exactly (FP32 history)
     bool near_on = false;
     double* d_near = nullptr;     // N^3 FP64 accumulator, kept all-zero between steps
@@ -277,6 +321,9 @@ void free_all(lc_plan* p) {
     cudaFree(p->d_I);
     cudaFree(p->d_scale);
     cudaFree(p->d_near);
+    cudaFree(p->d_tune_step);
+    cudaFree(p->d_tune_S);
+    cudaFree(p->d_tune_total);
     cudaFree(p->d_src_cell);
     cudaFree(p->d_src_q);
     for (auto& t : p->tables) {
@@ -304,6 +351,108 @@ bool valid_steps(const lc_steps* st) {
 
 bool valid_cosmo(const lc_cosmology* c) {
     return c && c->omega_m > 0.0 && c->omega_m <= 1.0 && c->h > 0.0 && isfinite(c->h);
+}
+
+// The shell-MAC phase of one field evaluation (inverse x pass with the
+// products summed over slices) in the given variant.
+void launch_mac(lc_plan* p, const lc_plan::Table& T, int step, int instant, int variant, const int* slot_step,
+                const double* slot_S, const long long* slot_total, cudaStream_t st) {
+    const bool bf = p->history == LC_HISTORY_BF16;
+    ColArgs c{};
+    c.axis = 1;
+    c.dir = 1;
+    c.in_mode = bf ? COL_IN_MAC_BF16 : COL_IN_MAC_F32;
+    c.out_mode = COL_OUT_PLAIN;
+    c.dst = p->d_work;
+    c.ring = p->d_ring;
+    c.slot_elems = p->ring_slot;
+    c.n_ring = p->n_ring;
+    c.step = step;
+    c.A = T.A;
+    c.slot_step = slot_step;
+    c.slot_S = slot_S;
+    c.slot_total = slot_total;
+    c.ghat = T.ghat;
+    c.g0 = T.g0;
+    c.gstride = T.gstride;
+    c.instant = instant;
+    c.tw = p->d_tw;
+    auto mac_fn = bf ? p->ops->mac_bf16 : p->ops->mac_f32;
+    if (variant == MAC_BULK && mac_fn) {
+        // full tiles: bulk-copy pipelined MAC; the Nyquist column tiles: generic pass
+        MacArgs ma{p->d_ring, p->ring_slot, step, T.A, T.gstride, p->n_ring, slot_step, slot_S,
+                   slot_total, T.ghat, T.g0, p->d_work, p->d_tw, p->d_err, bf ? 1 : 0, instant};
+        mac_fn(ma, st);
+        c.tile0 = p->ops->full_tiles;
+    }
+    p->ops->cols(c, st);
+}
+
+int mac_kernels(const lc_plan* p, int variant) {
+    const bool bf = p->history == LC_HISTORY_BF16;
+    return (variant == MAC_BULK && (bf ? p->ops->mac_bf16 : p->ops->mac_f32)) ? 2 : 1;
+}
+
+// Pick the MAC variant for a table (plan time: may synchronise).
+int choose_mac_variant(lc_plan* p, const lc_plan::Table& T, int s) {
+    const bool bf = p->history == LC_HISTORY_BF16;
+    if (!(bf ? p->ops->mac_bf16 : p->ops->mac_f32)) return MAC_GATHER;
+    if (const char* f = getenv("LC_MAC_VARIANT")) {
+        if (!strcmp(f, "gather")) return MAC_GATHER;
+        if (!strcmp(f, "bulk")) return MAC_BULK;
+    }
+    int dev = 0, major = 0, minor = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    char kb[128];
+    snprintf(kb, sizeof kb, "mac/sm%d%d/N%d/%s/A%d", major, minor, p->N, bf ? "bf16" : "fp32", T.A);
+    const std::string key(kb);
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        tune_load();
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) return it->second;
+    }
+    // time both variants with every slice marked valid (the ring's contents
+    // do not matter for timing; the output goes to the work buffer)
+    if (!p->d_tune_step) {
+        if (dalloc(p, &p->d_tune_step, p->n_ring) != cudaSuccess || dalloc(p, &p->d_tune_S, p->n_ring) != cudaSuccess ||
+            dalloc(p, &p->d_tune_total, p->n_ring) != cudaSuccess)
+            return MAC_GATHER;
+    }
+    std::vector<int> hs(p->n_ring, -1);
+    std::vector<double> hS(p->n_ring, 1.0);
+    std::vector<long long> ht(p->n_ring, 1);
+    for (int j = 0; j < T.A && s - j >= 0; ++j) hs[(s - j) % p->n_ring] = s - j;
+    cudaStream_t st = p->stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double ms[2] = {0, 0};
+    if (cudaMemcpy(p->d_tune_step, hs.data(), sizeof(int) * p->n_ring, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->d_tune_S, hS.data(), sizeof(double) * p->n_ring, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->d_tune_total, ht.data(), sizeof(long long) * p->n_ring, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        return MAC_GATHER;
+    }
+    for (int v = 0; v < 2; ++v) {
+        launch_mac(p, T, s, 0, v, p->d_tune_step, p->d_tune_S, p->d_tune_total, st); // warm-up
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3; ++r) launch_mac(p, T, s, 0, v, p->d_tune_step, p->d_tune_S, p->d_tune_total, st);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        ms[v] = t / 3.0;
+    }
+    count_launch(4ULL * (mac_kernels(p, 0) + mac_kernels(p, 1)));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (cudaGetLastError() != cudaSuccess) return MAC_GATHER;
+    const int best = ms[1] < ms[0] ? MAC_BULK : MAC_GATHER;
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    tune_store(key, best, ms[0], ms[1]);
+    return best;
 }
 
 // Build the Ghat table of observing step s (steps 2-3 of Section 2.2).
@@ -411,6 +560,7 @@ lc_status build_table(lc_plan* p, int s) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(st); // host table gt must outlive the copy
     if (e != cudaSuccess) return cuda_fail(p, e);
     T.A = A;
+    T.mac_variant = choose_mac_variant(p, T, s);
     return LC_OK;
 }
 
@@ -706,42 +856,15 @@ static lc_status field_impl(lc_plan* p, int step, float* out, int instant) {
     if (T.A == 0) {
         e = cudaMemsetAsync(dout, 0, sizeof(float) * N3, st);
     } else {
+        {
+            Phase ph(p, LC_PHASE_MAC_X, mac_kernels(p, T.mac_variant));
+            launch_mac(p, T, step, instant, T.mac_variant, p->d_slot_step, p->d_slot_S, p->d_slot_total, st);
+        }
         ColArgs c{};
-        c.axis = 1;
         c.dir = 1;
-        c.in_mode = p->history == LC_HISTORY_BF16 ? COL_IN_MAC_BF16 : COL_IN_MAC_F32;
         c.out_mode = COL_OUT_PLAIN;
         c.dst = p->d_work;
-        c.ring = p->d_ring;
-        c.slot_elems = p->ring_slot;
-        c.n_ring = p->n_ring;
-        c.step = step;
-        c.A = T.A;
-        c.slot_step = p->d_slot_step;
-        c.slot_S = p->d_slot_S;
-        c.slot_total = p->d_slot_total;
-        c.ghat = T.ghat;
-        c.g0 = T.g0;
-        c.gstride = T.gstride;
-        c.instant = instant;
         c.tw = p->d_tw;
-        const bool bf = p->history == LC_HISTORY_BF16;
-        auto mac_fn = bf ? p->ops->mac_bf16 : p->ops->mac_f32;
-        // the TMA pipeline pays off once there are enough slices to stream;
-        // for a handful the register-gather pass is faster
-        if (mac_fn && T.A >= kMacTmaMinShells) {
-            // full tiles: bulk-copy pipelined MAC; the Nyquist column tiles: generic pass
-            Phase ph(p, LC_PHASE_MAC_X, 2);
-            MacArgs ma{p->d_ring, p->ring_slot, step, T.A, T.gstride, p->n_ring, p->d_slot_step, p->d_slot_S,
-                       p->d_slot_total, T.ghat, T.g0, p->d_work, p->d_tw, p->d_err, bf ? 1 : 0, instant};
-            mac_fn(ma, st);
-            c.tile0 = p->ops->full_tiles;
-            p->ops->cols(c, st);
-            c.tile0 = 0;
-        } else {
-            Phase ph(p, LC_PHASE_MAC_X, 1);
-            p->ops->cols(c, st);
-        }
         c.axis = 0;
         c.in_mode = COL_IN_PLAIN;
         c.src = p->d_work;
@@ -787,6 +910,147 @@ lc_status lc_plan_reset(lc_plan* p) {
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_slot_total, 0, sizeof(long long) * p->n_ring, p->stream);
     if (e != cudaSuccess) return cuda_fail(p, e);
     p->last_pushed = -1;
+    return LC_OK;
+}
+
+// ---------------------------------------------------------------- checkpoint
+namespace {
+constexpr unsigned long long kCkptMagic = 0x31304b43505443ULL; // "CTPCK01"
+struct CkptHeader {
+    unsigned long long magic;
+    int version, N, n_steps, n_ring, history, last_pushed;
+    long long near_n;
+    unsigned long long params_hash;
+    long long ring_bytes;
+    unsigned char pad[256 - 8 - 6 * 4 - 8 - 8 - 8];
+};
+static_assert(sizeof(CkptHeader) == 256, "checkpoint header is 256 bytes");
+
+// FNV-1a over the bytes of every method parameter
+unsigned long long params_hash(const lc_plan* p) {
+    unsigned long long h = 1469598103934665603ULL;
+    auto mix = [&h](const void* d, size_t n) {
+        const unsigned char* b = static_cast<const unsigned char*>(d);
+        for (size_t i = 0; i < n; ++i) {
+            h ^= b[i];
+            h *= 1099511628211ULL;
+        }
+    };
+    mix(&p->N, sizeof p->N);
+    mix(&p->L, sizeof p->L);
+    mix(&p->cosmo, sizeof p->cosmo);
+    mix(&p->n_steps, sizeof p->n_steps);
+    mix(&p->S, sizeof p->S);
+    mix(&p->history, sizeof p->history);
+    mix(&p->normalise, sizeof p->normalise);
+    mix(&p->U, sizeof p->U);
+    mix(p->z.data(), sizeof(double) * p->z.size());
+    return h;
+}
+
+size_t ring_bytes_of(const lc_plan* p) {
+    return (size_t)p->n_ring * p->ring_slot * (p->history == LC_HISTORY_BF16 ? 4 : 8);
+}
+
+size_t meta_bytes_of(const lc_plan* p, long long near_n) {
+    return (size_t)p->n_ring * (sizeof(int) + sizeof(double) + sizeof(long long)) +
+           (size_t)near_n * 2 * sizeof(long long);
+}
+
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+} // namespace
+
+size_t lc_plan_checkpoint_bytes(const lc_plan* p) {
+    if (!p) return 0;
+    return sizeof(CkptHeader) + align256(meta_bytes_of(p, p->near_n)) + ring_bytes_of(p);
+}
+
+lc_status lc_plan_save(lc_plan* p, void* buf, size_t size) {
+    if (!p || !buf) return LC_ERR_INVALID_ARG;
+    if (p->failed) return LC_ERR_CUDA;
+    if (size < lc_plan_checkpoint_bytes(p)) return LC_ERR_INVALID_ARG;
+    CkptHeader h{};
+    h.magic = kCkptMagic;
+    h.version = 1;
+    h.N = p->N;
+    h.n_steps = p->n_steps;
+    h.n_ring = p->n_ring;
+    h.history = p->history;
+    h.last_pushed = p->last_pushed;
+    h.near_n = p->near_n;
+    h.params_hash = params_hash(p);
+    h.ring_bytes = (long long)ring_bytes_of(p);
+    unsigned char* b = static_cast<unsigned char*>(buf);
+    cudaStream_t st = p->stream;
+    const size_t nr = (size_t)p->n_ring;
+    size_t off = sizeof h;
+    cudaError_t e = cudaMemcpyAsync(b, &h, sizeof h, cudaMemcpyDefault, st);
+    auto put = [&](const void* src, size_t n) {
+        if (e == cudaSuccess && n) e = cudaMemcpyAsync(b + off, src, n, cudaMemcpyDefault, st);
+        off += n;
+    };
+    put(p->d_slot_step, nr * sizeof(int));
+    put(p->d_slot_S, nr * sizeof(double));
+    put(p->d_slot_total, nr * sizeof(long long));
+    put(p->d_src_cell, (size_t)p->near_n * sizeof(long long));
+    put(p->d_src_q, (size_t)p->near_n * sizeof(long long));
+    off = sizeof h + align256(meta_bytes_of(p, p->near_n));
+    put(p->d_ring, ring_bytes_of(p));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st); // the header copy reads a stack object
+    if (e != cudaSuccess) return cuda_fail(p, e);
+    return LC_OK;
+}
+
+lc_status lc_plan_load(lc_plan* p, const void* buf, size_t size) {
+    if (!p || !buf) return LC_ERR_INVALID_ARG;
+    if (p->failed) return LC_ERR_CUDA;
+    if (size < sizeof(CkptHeader)) return LC_ERR_INVALID_ARG;
+    CkptHeader h{};
+    cudaStream_t st = p->stream;
+    cudaError_t e = cudaMemcpyAsync(&h, buf, sizeof h, cudaMemcpyDefault, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(p, e);
+    if (h.magic != kCkptMagic || h.version != 1 || h.N != p->N || h.n_steps != p->n_steps ||
+        h.n_ring != p->n_ring || h.history != p->history || h.params_hash != params_hash(p) ||
+        h.ring_bytes != (long long)ring_bytes_of(p) || h.last_pushed < -1 || h.last_pushed >= p->n_steps ||
+        h.near_n < 0 || (!p->near_on && h.near_n != 0))
+        return LC_ERR_INVALID_ARG;
+    if (size < sizeof h + align256(meta_bytes_of(p, h.near_n)) + ring_bytes_of(p)) return LC_ERR_INVALID_ARG;
+    if (p->near_on && h.near_n > p->near_cap) {
+        long long cap = 1024;
+        while (cap < h.near_n) cap *= 2;
+        long long *cell = nullptr, *q = nullptr;
+        if (dalloc(p, &cell, (size_t)cap) != cudaSuccess) return LC_ERR_OOM;
+        if (dalloc(p, &q, (size_t)cap) != cudaSuccess) {
+            cudaFree(cell);
+            p->bytes -= sizeof(long long) * cap;
+            return LC_ERR_OOM;
+        }
+        cudaFree(p->d_src_cell);
+        cudaFree(p->d_src_q);
+        p->bytes -= sizeof(long long) * 2 * p->near_cap;
+        p->d_src_cell = cell;
+        p->d_src_q = q;
+        p->near_cap = cap;
+    }
+    const unsigned char* b = static_cast<const unsigned char*>(buf);
+    const size_t nr = (size_t)p->n_ring;
+    size_t off = sizeof h;
+    auto get = [&](void* dst, size_t n) {
+        if (e == cudaSuccess && n) e = cudaMemcpyAsync(dst, b + off, n, cudaMemcpyDefault, st);
+        off += n;
+    };
+    get(p->d_slot_step, nr * sizeof(int));
+    get(p->d_slot_S, nr * sizeof(double));
+    get(p->d_slot_total, nr * sizeof(long long));
+    get(p->d_src_cell, (size_t)h.near_n * sizeof(long long));
+    get(p->d_src_q, (size_t)h.near_n * sizeof(long long));
+    off = sizeof h + align256(meta_bytes_of(p, h.near_n));
+    get(p->d_ring, ring_bytes_of(p));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(p, e);
+    p->last_pushed = h.last_pushed;
+    p->near_n = h.near_n;
     return LC_OK;
 }
 
@@ -878,6 +1142,19 @@ lc_status lc_plan_info(const lc_plan* p, lc_plan_info_t* info) {
     info->box_mpc = p->L;
     info->z_edges = p->z.data();
     return LC_OK;
+}
+
+int lc_autotune_report(char* buf, int size) {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    tune_load();
+    std::string out;
+    for (auto& kv : g_tune) out += kv.first + " " + (kv.second == MAC_BULK ? "bulk" : "gather") + "\n";
+    if (buf && size > 0) {
+        const int n = (int)out.size() < size - 1 ? (int)out.size() : size - 1;
+        memcpy(buf, out.data(), n);
+        buf[n] = 0;
+    }
+    return (int)out.size();
 }
 
 lc_status lc_plan_green_wedge(lc_plan* p, int step, int lookback, float* out, double* ghat0) {

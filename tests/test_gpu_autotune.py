@@ -1,0 +1,90 @@
+"""The shell-MAC autotuner: both kernels agree with the FP64 oracle at every
+slice count, and the tuner's choices are reported and persisted."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1502_02294_gb300 as lc
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP32_L2, FP32_MAX, BF16_L2 = 1e-5, 1e-4, 5e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    lc.build()
+    oracle.build()
+
+
+def _fields(w, steps, check):
+    plan = lc.Plan.from_workload(w)
+    out = {}
+    for s in steps:
+        pos, lum = w.cat.active(s)
+        plan.push(s, torch.from_numpy(pos).cuda(), torch.from_numpy(lum).cuda())
+        if s in check:
+            out[s] = plan.field(s).cpu().numpy()
+    plan.close()
+    return out
+
+
+def _errors(J, ref):
+    J = np.asarray(J, dtype=np.float64)
+    a = np.abs(ref)
+    ulp = np.exp2(np.floor(np.log2(np.maximum(a, np.finfo(np.float32).tiny))) - 23)
+    rel = np.linalg.norm(J - ref) / np.linalg.norm(ref)
+    mx = np.maximum(np.abs(J - ref) - 2.0 * ulp, 0.0).max() / a.mean()
+    return rel, mx
+
+
+@pytest.mark.parametrize("history", [synth.HISTORY_FP32, synth.HISTORY_BF16])
+@pytest.mark.parametrize("variant", ["gather", "bulk"])
+def test_forced_variant_matches_oracle_every_slice_count(monkeypatch, variant, history):
+    # c1 (32^3, 8 steps): slice counts 1..8 cover a partial Ghat block and
+    # fewer slices than pipeline stages
+    monkeypatch.setenv("LC_MAC_VARIANT", variant)
+    w = synth.config("c1")
+    w.history = history
+    P = oracle.Problem.from_workload(w)
+    out = _fields(w, range(8), set(range(8)))
+    for s, J in out.items():
+        ref = oracle.field_for(P, w.cat, s)
+        rel, mx = _errors(J, ref)
+        if history == synth.HISTORY_FP32:
+            assert rel <= FP32_L2 and mx <= FP32_MAX, (variant, s, rel, mx)
+        else:
+            assert rel <= BF16_L2, (variant, s, rel)
+
+
+def test_forced_variants_agree_many_slices(monkeypatch):
+    # 64^3 with 20 steps: up to 20 slices, more than two Ghat blocks
+    w = synth.small(n=64, box=90.0, n_steps=20, n_src=300, subsamples=2, clustered=True, seed=4242)
+    P = oracle.Problem.from_workload(w)
+    res = {}
+    for v in ("gather", "bulk"):
+        monkeypatch.setenv("LC_MAC_VARIANT", v)
+        res[v] = _fields(w, range(20), {12, 19})
+    for s in (12, 19):
+        ref = oracle.field_for(P, w.cat, s)
+        for v in ("gather", "bulk"):
+            rel, mx = _errors(res[v][s], ref)
+            assert rel <= FP32_L2 and mx <= FP32_MAX, (v, s, rel, mx)
+
+
+def test_choices_reported_and_persisted(monkeypatch, tmp_path):
+    cache = tmp_path / "tune.txt"
+    monkeypatch.delenv("LC_MAC_VARIANT", raising=False)
+    monkeypatch.setenv("LC_AUTOTUNE_CACHE", str(cache))
+    # 96^3 with a BF16 history: keys no other test tunes, so they are new here
+    w = synth.small(n=96, box=120.0, n_steps=4, n_src=60, seed=515, history=synth.HISTORY_BF16)
+    _fields(w, range(4), {3})
+    rep = lc.autotune_report()
+    mine = {k: v for k, v in rep.items() if "/N96/bf16/" in k}
+    assert mine and set(mine.values()) <= {"gather", "bulk"}
+    lines = cache.read_text().split()
+    assert any("/N96/bf16/" in t for t in lines)
