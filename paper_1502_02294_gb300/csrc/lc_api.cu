@@ -87,15 +87,17 @@ static inline void count_launch(unsigned long long k = 1) { g_launches.fetch_add
 using namespace lc;
 
 // ---------------------------------------------------------------- autotuner
-// The shell MAC has two variants: a register-gather pass (MAC_GATHER) and a
-// bulk-copy pipelined kernel (MAC_BULK) for the full tiles.  Which one is
-// faster depends on the grid, the history precision and the number of
-// active slices; the plan times both on its own buffers the first time it
-// meets a (device, N, history, slices) combination and keeps the faster.
-// Choices are kept per process and, when LC_AUTOTUNE_CACHE names a file,
-// loaded from and appended to that file.  LC_MAC_VARIANT=gather|bulk
-// forces one variant (tests).
-enum { MAC_GATHER = 0, MAC_BULK = 1 };
+// The shell MAC has three variants: a register-gather pass (MAC_GATHER), a
+// bulk-copy pipelined kernel for the full tiles (MAC_BULK) and its
+// warp-specialised form (MAC_WS).  Which one is fastest depends on the
+// grid, the history precision and the number of active slices; the plan
+// times each on its own buffers the first time it meets a (device, N,
+// history, slices) combination and keeps the fastest.  Choices are kept per
+// process and, when LC_AUTOTUNE_CACHE names a file, loaded from and
+// appended to that file.  LC_MAC_VARIANT=gather|bulk|ws forces one variant
+// where it is built (tests).
+enum { MAC_GATHER = 0, MAC_BULK = 1, MAC_WS = 2, MAC_NVAR = 3 };
+const char* const kMacNames[MAC_NVAR] = {"gather", "bulk", "ws"};
 namespace {
 std::mutex g_tune_mu;
 std::map<std::string, int> g_tune;
@@ -108,20 +110,23 @@ void tune_load() {
     if (!path) return;
     FILE* f = fopen(path, "r");
     if (!f) return;
-    char key[256];
+    // one choice per line: key, variant, then the measured times (ignored)
+    char line[512], key[256];
     int v;
-    double a, b;
-    while (fscanf(f, "%255s %d %lf %lf", key, &v, &a, &b) == 4) g_tune[key] = v;
+    while (fgets(line, sizeof line, f))
+        if (sscanf(line, "%255s %d", key, &v) == 2 && v >= 0 && v < MAC_NVAR) g_tune[key] = v;
     fclose(f);
 }
 
-void tune_store(const std::string& key, int v, double ms_gather, double ms_bulk) {
+void tune_store(const std::string& key, int v, const double* ms) {
     g_tune[key] = v;
     const char* path = getenv("LC_AUTOTUNE_CACHE");
     if (!path) return;
     FILE* f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s %d %.6f %.6f\n", key.c_str(), v, ms_gather, ms_bulk);
+    fprintf(f, "%s %d", key.c_str(), v);
+    for (int i = 0; i < MAC_NVAR; ++i) fprintf(f, " %.6f", ms[i]);
+    fprintf(f, "\n");
     fclose(f);
 }
 } // namespace
@@ -160,7 +165,7 @@ struct lc_plan {
         float* ghat = nullptr;  // [W][gstride]; shell 0 without its near cube when near_on
         double* g0 = nullptr;   // [A] FP64 Ghat_j(0) of what the FFT path carries
         double* gnear = nullptr; // near cube of shell 0 on the wedge prefix (near_on)
-        int mac_variant = 0;    // MAC_GATHER or MAC_BULK, chosen by the autotuner
+        int mac_variant = 0;    // MAC_GATHER, MAC_BULK or MAC_WS, chosen by the autotuner
         int A = -1;             // -1: not built
     };
     std::vector<Table> tables;
@@ -377,8 +382,9 @@ void launch_mac(lc_plan* p, const lc_plan::Table& T, int step, int instant, int 
     c.gstride = T.gstride;
     c.instant = instant;
     c.tw = p->d_tw;
-    auto mac_fn = bf ? p->ops->mac_bf16 : p->ops->mac_f32;
-    if (variant == MAC_BULK && mac_fn) {
+    auto mac_fn = variant == MAC_WS ? (bf ? p->ops->mac_ws_bf16 : p->ops->mac_ws_f32)
+                                    : (bf ? p->ops->mac_bf16 : p->ops->mac_f32);
+    if (variant != MAC_GATHER && mac_fn) {
         // full tiles: bulk-copy pipelined MAC; the Nyquist column tiles: generic pass
         MacArgs ma{p->d_ring, p->ring_slot, step, T.A, T.gstride, p->n_ring, slot_step, slot_S,
                    slot_total, T.ghat, T.g0, p->d_work, p->d_tw, p->d_err, bf ? 1 : 0, instant};
@@ -388,34 +394,40 @@ void launch_mac(lc_plan* p, const lc_plan::Table& T, int step, int instant, int 
     p->ops->cols(c, st);
 }
 
-int mac_kernels(const lc_plan* p, int variant) {
+bool mac_built(const lc_plan* p, int variant) {
     const bool bf = p->history == LC_HISTORY_BF16;
-    return (variant == MAC_BULK && (bf ? p->ops->mac_bf16 : p->ops->mac_f32)) ? 2 : 1;
+    if (variant == MAC_BULK) return (bf ? p->ops->mac_bf16 : p->ops->mac_f32) != nullptr;
+    if (variant == MAC_WS) return (bf ? p->ops->mac_ws_bf16 : p->ops->mac_ws_f32) != nullptr;
+    return true;
 }
+
+int mac_kernels(const lc_plan* p, int variant) { return variant != MAC_GATHER && mac_built(p, variant) ? 2 : 1; }
 
 // Pick the MAC variant for a table (plan time: may synchronise).
 int choose_mac_variant(lc_plan* p, const lc_plan::Table& T, int s) {
     const bool bf = p->history == LC_HISTORY_BF16;
-    if (!(bf ? p->ops->mac_bf16 : p->ops->mac_f32)) return MAC_GATHER;
     if (const char* f = getenv("LC_MAC_VARIANT")) {
-        if (!strcmp(f, "gather")) return MAC_GATHER;
-        if (!strcmp(f, "bulk")) return MAC_BULK;
+        for (int v = 0; v < MAC_NVAR; ++v)
+            if (!strcmp(f, kMacNames[v])) return mac_built(p, v) ? v : MAC_GATHER;
     }
+    int nbuilt = 0;
+    for (int v = 1; v < MAC_NVAR; ++v) nbuilt += mac_built(p, v);
+    if (!nbuilt) return MAC_GATHER;
     int dev = 0, major = 0, minor = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
     cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
     char kb[128];
-    snprintf(kb, sizeof kb, "mac/sm%d%d/N%d/%s/A%d", major, minor, p->N, bf ? "bf16" : "fp32", T.A);
+    snprintf(kb, sizeof kb, "mac%d/sm%d%d/N%d/%s/A%d", MAC_NVAR, major, minor, p->N, bf ? "bf16" : "fp32", T.A);
     const std::string key(kb);
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
         tune_load();
         auto it = g_tune.find(key);
-        if (it != g_tune.end()) return it->second;
+        if (it != g_tune.end() && mac_built(p, it->second)) return it->second;
     }
-    // time both variants with every slice marked valid (the ring's contents
-    // do not matter for timing; the output goes to the work buffer)
+    // time every built variant with every slice marked valid (the ring's
+    // contents do not matter for timing; the output goes to the work buffer)
     if (!p->d_tune_step) {
         if (dalloc(p, &p->d_tune_step, p->n_ring) != cudaSuccess || dalloc(p, &p->d_tune_S, p->n_ring) != cudaSuccess ||
             dalloc(p, &p->d_tune_total, p->n_ring) != cudaSuccess)
@@ -427,7 +439,8 @@ int choose_mac_variant(lc_plan* p, const lc_plan::Table& T, int s) {
     for (int j = 0; j < T.A && s - j >= 0; ++j) hs[(s - j) % p->n_ring] = s - j;
     cudaStream_t st = p->stream;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    double ms[2] = {0, 0};
+    double ms[MAC_NVAR];
+    for (int v = 0; v < MAC_NVAR; ++v) ms[v] = -1.0;
     if (cudaMemcpy(p->d_tune_step, hs.data(), sizeof(int) * p->n_ring, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(p->d_tune_S, hS.data(), sizeof(double) * p->n_ring, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(p->d_tune_total, ht.data(), sizeof(long long) * p->n_ring, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -435,7 +448,9 @@ int choose_mac_variant(lc_plan* p, const lc_plan::Table& T, int s) {
         cudaGetLastError();
         return MAC_GATHER;
     }
-    for (int v = 0; v < 2; ++v) {
+    int best = MAC_GATHER;
+    for (int v = 0; v < MAC_NVAR; ++v) {
+        if (!mac_built(p, v)) continue;
         launch_mac(p, T, s, 0, v, p->d_tune_step, p->d_tune_S, p->d_tune_total, st); // warm-up
         cudaEventRecord(e0, st);
         for (int r = 0; r < 3; ++r) launch_mac(p, T, s, 0, v, p->d_tune_step, p->d_tune_S, p->d_tune_total, st);
@@ -444,14 +459,14 @@ int choose_mac_variant(lc_plan* p, const lc_plan::Table& T, int s) {
         float t = 0.f;
         cudaEventElapsedTime(&t, e0, e1);
         ms[v] = t / 3.0;
+        count_launch(4ULL * mac_kernels(p, v));
+        if (ms[v] < ms[best]) best = v;
     }
-    count_launch(4ULL * (mac_kernels(p, 0) + mac_kernels(p, 1)));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (cudaGetLastError() != cudaSuccess) return MAC_GATHER;
-    const int best = ms[1] < ms[0] ? MAC_BULK : MAC_GATHER;
     std::lock_guard<std::mutex> g(g_tune_mu);
-    tune_store(key, best, ms[0], ms[1]);
+    tune_store(key, best, ms);
     return best;
 }
 
@@ -1148,7 +1163,7 @@ int lc_autotune_report(char* buf, int size) {
     std::lock_guard<std::mutex> g(g_tune_mu);
     tune_load();
     std::string out;
-    for (auto& kv : g_tune) out += kv.first + " " + (kv.second == MAC_BULK ? "bulk" : "gather") + "\n";
+    for (auto& kv : g_tune) out += kv.first + " " + kMacNames[kv.second] + "\n";
     if (buf && size > 0) {
         const int n = (int)out.size() < size - 1 ? (int)out.size() : size - 1;
         memcpy(buf, out.data(), n);

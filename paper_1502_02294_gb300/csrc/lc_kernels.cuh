@@ -643,6 +643,9 @@ struct FftOps {
     // fused TMA shell MAC over the full tiles (null where not built), FP32 / BF16 ring
     void (*mac_f32)(const MacArgs&, cudaStream_t);
     void (*mac_bf16)(const MacArgs&, cudaStream_t);
+    // warp-specialised variant of the same MAC (null where not built)
+    void (*mac_ws_f32)(const MacArgs&, cudaStream_t);
+    void (*mac_ws_bf16)(const MacArgs&, cudaStream_t);
     int full_tiles; // tiles of the full 16-column chunks (the Nyquist tiles follow)
 };
 

@@ -282,6 +282,292 @@ __global__ void __launch_bounds__(MacCfg<N, BF16>::NT) k_mac_tma(MacArgs a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Warp-specialised variant of the same MAC (k_mac_ws).  The CTA has NC
+// consumer threads and one producer warp:
+//  * the producer streams the tile's slices through an S-stage ring of
+//    shared-memory buffers (one cp.async.bulk per slice, lane 0) and the
+//    tile's Ghat rows in blocks of 4 slices (one 16-byte cp.async per row,
+//    all lanes, completion counted on an mbarrier), double buffered;
+//  * a consumer thread owns UPT units; a unit is a row pair {p, N - p}
+//    (or {0, N/2}) times 4 consecutive columns, so the 8 elements of a unit
+//    share the Ghat values of wedge rows (min(p, N - p), q, r..r+3) and the
+//    ring data is read with 128-bit shared loads;
+//  * consumers only wait for data and release buffers; the producer alone
+//    waits for free buffers.  Every wait is bounded.
+// Arithmetic per element and slice is k_mac_tma's (g = Ghat * D, then two
+// fused multiply-adds) in the same slice order, so both give identical sums.
+constexpr int kWsGB = 4; // slices per Ghat block (16 bytes of a wedge row)
+
+template <int N, bool BF16> struct MacWsCfg {
+    static constexpr int CW = cw_of(N), NRP = nrp_of(N), M = N / 2, NCH = M / CW, BP = odd_pad(CW);
+    static constexpr int TILE = N * CW;
+    static constexpr int EB = BF16 ? 4 : 8;
+    static constexpr int STAGE_BYTES = TILE * EB;
+    static constexpr int CG = CW / 4;                 // 4-column groups
+    static constexpr int UNITS = M * CG;              // (row pair, column group)
+    static constexpr int UPT = 2;                     // units per consumer thread
+    static constexpr int NC = UNITS / UPT;            // consumer threads
+    static constexpr int NCW = NC / 32;               // consumer warps
+    static constexpr int NT = NC + 32;                // + the producer warp
+    static constexpr int GROWS = (M + 1) * CW;        // distinct Ghat rows of a tile
+    static constexpr int GPLANE = (M + 1) * CG;       // Ghat rows per column residue (col mod 4)
+    static constexpr int GBLK_BYTES = GROWS * 16;     // one Ghat block: 4 floats per row
+    static constexpr int MAXBLK = kMaxShells / kWsGB;
+    static constexpr size_t FIXED = 2 * (size_t)GBLK_BYTES + (size_t)GROWS * 4 + (size_t)N * 8 +
+                                    (size_t)kMaxShells * 12 + (size_t)MAXBLK * 12 + 64 + 256;
+    static constexpr size_t BUDGET = 227 * 1024;
+    static constexpr int FIT = BUDGET > FIXED ? (int)((BUDGET - FIXED) / STAGE_BYTES) : 0;
+    static constexpr int STAGES = FIT > 8 ? 8 : FIT;
+    static constexpr size_t STAGE_AREA = (size_t)STAGES * STAGE_BYTES > (size_t)N * BP * 8
+                                             ? (size_t)STAGES * STAGE_BYTES : (size_t)N * BP * 8;
+    static constexpr size_t OFF_STAGE = 0;
+    static constexpr size_t OFF_G = (OFF_STAGE + STAGE_AREA + 127) / 128 * 128;
+    static constexpr size_t OFF_WROW = OFF_G + 2 * (size_t)GBLK_BYTES;
+    static constexpr size_t OFF_TW = (OFF_WROW + (size_t)GROWS * 4 + 15) / 16 * 16;
+    static constexpr size_t OFF_LIST = OFF_TW + (size_t)N * 8;
+    static constexpr size_t OFF_BLK = OFF_LIST + (size_t)kMaxShells * 12;
+    static constexpr size_t OFF_BAR = (OFF_BLK + (size_t)MAXBLK * 12 + 15) / 16 * 16;
+    static constexpr int NBAR = 2 * 8 + 4; // full[8], empty[8], gfull[2], gempty[2]
+    static constexpr size_t SMEM = OFF_BAR + NBAR * 8 + 128;
+    static constexpr bool OK = N >= 32 && N <= 256 && CW == 16 && STAGES >= 2 && NC % 32 == 0 &&
+                               UNITS % UPT == 0 && SMEM <= BUDGET;
+};
+
+__device__ __forceinline__ void cp_async16(unsigned dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(reinterpret_cast<unsigned long long>(src))
+                 : "memory");
+}
+// arrive on the mbarrier once every cp.async issued so far by this thread has landed
+__device__ __forceinline__ void cp_async_mbar_arrive(unsigned bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+// complex from a BF16 pair (low half: real part)
+__device__ __forceinline__ float2 bf2_to_f2(unsigned w) {
+    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
+
+template <int N, bool BF16>
+__global__ void __launch_bounds__(MacWsCfg<N, BF16>::NT) k_mac_ws(MacArgs a) {
+    using C = MacWsCfg<N, BF16>;
+    constexpr int NT = C::NT, NC = C::NC, CW = C::CW, TILE = C::TILE, BP = C::BP, S = C::STAGES, M = C::M;
+    constexpr int UPT = C::UPT, CG = C::CG, GROWS = C::GROWS, GPLANE = C::GPLANE;
+    extern __shared__ unsigned char smem_raw3[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw3) + 127) & ~uintptr_t(127));
+    unsigned char* stage = sm + C::OFF_STAGE;
+    float2* buf = reinterpret_cast<float2*>(sm + C::OFF_STAGE); // after the MAC loop only
+    unsigned char* gsm = sm + C::OFF_G;
+    int* s_wrow = reinterpret_cast<int*>(sm + C::OFF_WROW);
+    float2* tw = reinterpret_cast<float2*>(sm + C::OFF_TW);
+    int* s_slot = reinterpret_cast<int*>(sm + C::OFF_LIST);
+    int* s_j = s_slot + kMaxShells;
+    float* s_D = reinterpret_cast<float*>(s_j + kMaxShells);
+    int* s_blk = reinterpret_cast<int*>(sm + C::OFF_BLK); // Ghat block of each block in use
+    int* s_bmask = s_blk + C::MAXBLK;                     // its valid slices (bit jj)
+    int* s_bv0 = s_bmask + C::MAXBLK;                     // index of its first valid slice
+    unsigned long long* full = reinterpret_cast<unsigned long long*>(sm + C::OFF_BAR);
+    unsigned long long* empty = full + 8;
+    unsigned long long* gfull = full + 16;
+    unsigned long long* gempty = full + 18;
+    __shared__ int s_nv, s_nb, s_fail;
+    __shared__ double s_dc;
+
+    const int tile = blockIdx.x; // full tiles only
+    const int line = tile / C::NCH, chunk = tile % C::NCH;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x < 32)
+        mac_slot_list(a.A, a.step, a.n_ring, a.slot_step, a.slot_total, a.slot_S, a.g0, a.bf16 != 0, s_slot, s_j, s_D,
+                      &s_nv, &s_dc, a.instant);
+    if (threadIdx.x == 32) {
+        s_fail = 0;
+        for (int i = 0; i < S; ++i) {
+            mbar_init(smem_u32(&full[i]), 1);
+            mbar_init(smem_u32(&empty[i]), C::NCW);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(smem_u32(&gfull[i]), 32);
+            mbar_init(smem_u32(&gempty[i]), C::NCW);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int i = threadIdx.x; i < N; i += NT) tw[i] = a.tw[i];
+    // wedge rows of the tile, row = p' * CW + col
+    for (int r = threadIdx.x; r < GROWS; r += NT) s_wrow[r] = (int)wedge_of(r / CW, line, chunk * CW + r % CW, N);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // the Ghat blocks in slice order, with their valid slices
+        int nb = 0;
+        for (int v = 0; v < s_nv; ++v) {
+            const int b = s_j[v] / kWsGB;
+            if (nb == 0 || s_blk[nb - 1] != b) {
+                s_blk[nb] = b;
+                s_bmask[nb] = 0;
+                s_bv0[nb] = v;
+                ++nb;
+            }
+            s_bmask[nb - 1] |= 1 << (s_j[v] - b * kWsGB);
+        }
+        s_nb = nb;
+    }
+    __syncthreads();
+    const int nv = s_nv, nb = s_nb;
+    bool ok = true;
+    // consumer state: unit u = threadIdx.x + k * NC is row pair pu = u / CG, columns 4 cg .. 4 cg + 3
+    float2 accA[UPT][4], accB[UPT][4];
+#pragma unroll
+    for (int k = 0; k < UPT; ++k)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) accA[k][c] = accB[k][c] = make_float2(0.f, 0.f);
+
+    if (warp == C::NCW) {
+        // ------------------------------------------------------------ producer
+        const unsigned char* ring_tile =
+            static_cast<const unsigned char*>(a.ring) + (size_t)tile * a.n_ring * C::STAGE_BYTES;
+        for (int gi = 0; gi < nb; ++gi) {
+            const int gb = gi & 1;
+            if (gi >= 2) ok = mbar_wait_bounded(smem_u32(&gempty[gb]), (unsigned)(((gi >> 1) - 1) & 1)) && ok;
+            // Ghat rows of block s_blk[gi]: row (p', col) goes to slot (col % 4) * GPLANE + p' * CG + col / 4
+            const float* gsrc = a.ghat + (size_t)s_blk[gi] * kWsGB;
+            const unsigned gdst = smem_u32(gsm + (size_t)gb * C::GBLK_BYTES);
+            for (int r = lane; r < GROWS; r += 32) {
+                const int pp = r / CW, col = r % CW;
+                cp_async16(gdst + ((col & 3) * GPLANE + pp * CG + (col >> 2)) * 16,
+                           gsrc + (size_t)s_wrow[r] * a.gstride);
+            }
+            cp_async_mbar_arrive(smem_u32(&gfull[gb]));
+            if (lane == 0) {
+                const int vend = gi + 1 < nb ? s_bv0[gi + 1] : nv;
+                for (int v = s_bv0[gi]; v < vend; ++v) {
+                    const int st = v % S;
+                    if (v >= S) ok = mbar_wait_bounded(smem_u32(&empty[st]), (unsigned)(((v / S) - 1) & 1)) && ok;
+                    const unsigned bar = smem_u32(&full[st]);
+                    mbar_expect_tx(bar, C::STAGE_BYTES);
+                    bulk_load(smem_u32(stage + (size_t)st * C::STAGE_BYTES),
+                              ring_tile + (size_t)s_slot[v] * C::STAGE_BYTES, C::STAGE_BYTES, bar);
+                }
+            }
+            __syncwarp();
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    } else {
+        // ------------------------------------------------------------ consumers
+        int offA[UPT], offB[UPT], goffA[UPT], goffB[UPT];
+#pragma unroll
+        for (int k = 0; k < UPT; ++k) {
+            const int u = threadIdx.x + k * NC;
+            const int pu = u / CG, cg = u % CG;
+            offA[k] = (pu * CW + cg * 4) * C::EB;                    // byte offset in a stage
+            offB[k] = ((pu == 0 ? M : N - pu) * CW + cg * 4) * C::EB;
+            goffA[k] = (pu * CG + cg) * 16;                          // Ghat slot of column residue 0
+            goffB[k] = ((pu == 0 ? M : pu) * CG + cg) * 16;
+        }
+        for (int gi = 0; gi < nb; ++gi) {
+            const int gb = gi & 1;
+            ok = mbar_wait_bounded(smem_u32(&gfull[gb]), (unsigned)((gi >> 1) & 1)) && ok;
+            const unsigned char* gblk = gsm + (size_t)gb * C::GBLK_BYTES;
+            float4 gA[UPT][4], gB[UPT][4];
+#pragma unroll
+            for (int k = 0; k < UPT; ++k)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    gA[k][c] = *reinterpret_cast<const float4*>(gblk + c * GPLANE * 16 + goffA[k]);
+                    gB[k][c] = *reinterpret_cast<const float4*>(gblk + c * GPLANE * 16 + goffB[k]);
+                }
+            const int mask = s_bmask[gi];
+            int v = s_bv0[gi];
+#pragma unroll
+            for (int jj = 0; jj < kWsGB; ++jj) {
+                if (!(mask & (1 << jj))) continue;
+                const int st = v % S;
+                ok = mbar_wait_bounded(smem_u32(&full[st]), (unsigned)((v / S) & 1)) && ok;
+                const float D = s_D[v];
+                const unsigned char* sb = stage + (size_t)st * C::STAGE_BYTES;
+#pragma unroll
+                for (int k = 0; k < UPT; ++k) {
+                    float2 fA[4], fB[4];
+                    if constexpr (BF16) {
+                        const uint4 wa = *reinterpret_cast<const uint4*>(sb + offA[k]);
+                        const uint4 wb = *reinterpret_cast<const uint4*>(sb + offB[k]);
+                        fA[0] = bf2_to_f2(wa.x); fA[1] = bf2_to_f2(wa.y);
+                        fA[2] = bf2_to_f2(wa.z); fA[3] = bf2_to_f2(wa.w);
+                        fB[0] = bf2_to_f2(wb.x); fB[1] = bf2_to_f2(wb.y);
+                        fB[2] = bf2_to_f2(wb.z); fB[3] = bf2_to_f2(wb.w);
+                    } else {
+                        const float4 a0 = *reinterpret_cast<const float4*>(sb + offA[k]);
+                        const float4 a1 = *reinterpret_cast<const float4*>(sb + offA[k] + 16);
+                        const float4 b0 = *reinterpret_cast<const float4*>(sb + offB[k]);
+                        const float4 b1 = *reinterpret_cast<const float4*>(sb + offB[k] + 16);
+                        fA[0] = make_float2(a0.x, a0.y); fA[1] = make_float2(a0.z, a0.w);
+                        fA[2] = make_float2(a1.x, a1.y); fA[3] = make_float2(a1.z, a1.w);
+                        fB[0] = make_float2(b0.x, b0.y); fB[1] = make_float2(b0.z, b0.w);
+                        fB[2] = make_float2(b1.x, b1.y); fB[3] = make_float2(b1.z, b1.w);
+                    }
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const float ga = jj == 0 ? gA[k][c].x : jj == 1 ? gA[k][c].y : jj == 2 ? gA[k][c].z : gA[k][c].w;
+                        const float gb2 = jj == 0 ? gB[k][c].x : jj == 1 ? gB[k][c].y : jj == 2 ? gB[k][c].z : gB[k][c].w;
+                        const float g1 = ga * D, g2 = gb2 * D;
+                        accA[k][c].x = fmaf(g1, fA[c].x, accA[k][c].x);
+                        accA[k][c].y = fmaf(g1, fA[c].y, accA[k][c].y);
+                        accB[k][c].x = fmaf(g2, fB[c].x, accB[k][c].x);
+                        accB[k][c].y = fmaf(g2, fB[c].y, accB[k][c].y);
+                    }
+                }
+                // release the stage: one arrival per warp
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&empty[st]));
+                ++v;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&gempty[gb]));
+        }
+        if (!ok) {
+            atomicOr(&s_fail, 1);
+            // give copies still in flight a second bounded wait before the
+            // stage area is reused
+            for (int v = nv - S > 0 ? nv - S : 0; v < nv; ++v)
+                mbar_wait_bounded(smem_u32(&full[v % S]), (unsigned)((v / S) & 1));
+        }
+    }
+    if (!ok) atomicOr(&s_fail, 1);
+    __syncthreads(); // every stage consumed: the stage area becomes the x-transform buffer
+    if (s_fail && threadIdx.x == 0) atomicOr(a.err, 4);
+    if (warp < C::NCW) {
+        if (line == 0 && chunk == 0 && threadIdx.x == 0) accA[0][0] = make_float2((float)s_dc, 0.0f);
+#pragma unroll
+        for (int k = 0; k < UPT; ++k) {
+            const int u = threadIdx.x + k * NC;
+            const int pu = u / CG, cg = u % CG;
+            const int tA = pu, tB = pu == 0 ? M : N - pu;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                buf[tA * BP + cg * 4 + c] = accA[k][c];
+                buf[tB * BP + cg * 4 + c] = accB[k][c];
+            }
+        }
+    }
+    __syncthreads();
+    fft_smem<N, 1, CW, BP, NT>(buf, tw);
+    constexpr long long PLANE = (long long)N * C::NRP;
+    const long long base = (long long)line * C::NRP + chunk * CW;
+    for (int idx = threadIdx.x; idx < TILE; idx += NT) {
+        const int t = idx / CW, col = idx % CW;
+        a.dst[base + t * PLANE + col] = buf[t * BP + col];
+    }
+}
+
+template <int N, bool BF16> struct MacWsLaunch {
+    using C = MacWsCfg<N, BF16>;
+    static cudaError_t init() {
+        if constexpr (!C::OK) return cudaSuccess;
+        else return cudaFuncSetAttribute(k_mac_ws<N, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    }
+    static void run(const MacArgs& a, cudaStream_t st) {
+        if constexpr (C::OK) k_mac_ws<N, BF16><<<N * C::NCH, C::NT, C::SMEM, st>>>(a);
+    }
+};
+
 template <int N, bool BF16> struct MacLaunch {
     using C = MacCfg<N, BF16>;
     static cudaError_t init() {
