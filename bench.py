@@ -586,7 +586,7 @@ def main():
             "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "grid": w.n,
                        "box_mpc": w.box, "steps_in_run": T, "timed_window": [t0, T], "ring_slots": plan.n_ring,
                        "history": "bf16" if w.history else "fp32",
-                       "mac_kernel": {v: sum(1 for x in mac_choice.values() if x == v) for v in ("gather", "bulk", "ws")},
+                       "mac_kernel": {v: sum(1 for x in mac_choice.values() if x == v) for v in ("gather", "bulk", "ws", "ws2")},
                        "l2": f"flushed between timed steps "
                        f"({args.flush_mb} MB write outside the events)", "inputs": "device-resident"},
             "cell_shell_mac_per_s": world * mac_cells / t_max,

@@ -87,17 +87,18 @@ static inline void count_launch(unsigned long long k = 1) { g_launches.fetch_add
 using namespace lc;
 
 // ---------------------------------------------------------------- autotuner
-// The shell MAC has three variants: a register-gather pass (MAC_GATHER), a
-// bulk-copy pipelined kernel for the full tiles (MAC_BULK) and its
-// warp-specialised form (MAC_WS).  Which one is fastest depends on the
-// grid, the history precision and the number of active slices; the plan
-// times each on its own buffers the first time it meets a (device, N,
-// history, slices) combination and keeps the fastest.  Choices are kept per
-// process and, when LC_AUTOTUNE_CACHE names a file, loaded from and
-// appended to that file.  LC_MAC_VARIANT=gather|bulk|ws forces one variant
-// where it is built (tests).
-enum { MAC_GATHER = 0, MAC_BULK = 1, MAC_WS = 2, MAC_NVAR = 3 };
-const char* const kMacNames[MAC_NVAR] = {"gather", "bulk", "ws"};
+// The shell MAC has four variants: a register-gather pass (MAC_GATHER), a
+// bulk-copy pipelined kernel for the full tiles (MAC_BULK), and its
+// warp-specialised form over every tile, one tile per CTA (MAC_WS) or the
+// tiles of lines q and N - q together (MAC_WS2).  Which one is fastest
+// depends on the grid, the history precision and the number of active
+// slices; the plan times each on its own buffers the first time it meets a
+// (device, N, history, slices) combination and keeps the fastest.  Choices
+// are kept per process and, when LC_AUTOTUNE_CACHE names a file, loaded
+// from and appended to that file.  LC_MAC_VARIANT=gather|bulk|ws|ws2 forces
+// one variant where it is built (tests).
+enum { MAC_GATHER = 0, MAC_BULK = 1, MAC_WS = 2, MAC_WS2 = 3, MAC_NVAR = 4 };
+const char* const kMacNames[MAC_NVAR] = {"gather", "bulk", "ws", "ws2"};
 namespace {
 std::mutex g_tune_mu;
 std::map<std::string, int> g_tune;
@@ -165,7 +166,7 @@ struct lc_plan {
         float* ghat = nullptr;  // [W][gstride]; shell 0 without its near cube when near_on
         double* g0 = nullptr;   // [A] FP64 Ghat_j(0) of what the FFT path carries
         double* gnear = nullptr; // near cube of shell 0 on the wedge prefix (near_on)
-        int mac_variant = 0;    // MAC_GATHER, MAC_BULK or MAC_WS, chosen by the autotuner
+        int mac_variant = 0;    // MAC_GATHER, MAC_BULK, MAC_WS or MAC_WS2, chosen by the autotuner
         int A = -1;             // -1: not built
     };
     std::vector<Table> tables;
@@ -382,13 +383,16 @@ void launch_mac(lc_plan* p, const lc_plan::Table& T, int step, int instant, int 
     c.gstride = T.gstride;
     c.instant = instant;
     c.tw = p->d_tw;
-    auto mac_fn = variant == MAC_WS ? (bf ? p->ops->mac_ws_bf16 : p->ops->mac_ws_f32)
-                                    : (bf ? p->ops->mac_bf16 : p->ops->mac_f32);
+    auto mac_fn = variant == MAC_WS    ? (bf ? p->ops->mac_ws_bf16 : p->ops->mac_ws_f32)
+                  : variant == MAC_WS2 ? (bf ? p->ops->mac_ws2_bf16 : p->ops->mac_ws2_f32)
+                                       : (bf ? p->ops->mac_bf16 : p->ops->mac_f32);
     if (variant != MAC_GATHER && mac_fn) {
-        // full tiles: bulk-copy pipelined MAC; the Nyquist column tiles: generic pass
+        // MAC_BULK: full tiles in the bulk-copy kernel, the Nyquist tiles in
+        // the generic pass; MAC_WS, MAC_WS2: every tile in one kernel
         MacArgs ma{p->d_ring, p->ring_slot, step, T.A, T.gstride, p->n_ring, slot_step, slot_S,
                    slot_total, T.ghat, T.g0, p->d_work, p->d_tw, p->d_err, bf ? 1 : 0, instant};
         mac_fn(ma, st);
+        if (variant == MAC_WS || variant == MAC_WS2) return;
         c.tile0 = p->ops->full_tiles;
     }
     p->ops->cols(c, st);
@@ -398,10 +402,11 @@ bool mac_built(const lc_plan* p, int variant) {
     const bool bf = p->history == LC_HISTORY_BF16;
     if (variant == MAC_BULK) return (bf ? p->ops->mac_bf16 : p->ops->mac_f32) != nullptr;
     if (variant == MAC_WS) return (bf ? p->ops->mac_ws_bf16 : p->ops->mac_ws_f32) != nullptr;
+    if (variant == MAC_WS2) return (bf ? p->ops->mac_ws2_bf16 : p->ops->mac_ws2_f32) != nullptr;
     return true;
 }
 
-int mac_kernels(const lc_plan* p, int variant) { return variant != MAC_GATHER && mac_built(p, variant) ? 2 : 1; }
+int mac_kernels(const lc_plan* p, int variant) { return variant == MAC_BULK && mac_built(p, variant) ? 2 : 1; }
 
 // Pick the MAC variant for a table (plan time: may synchronise).
 int choose_mac_variant(lc_plan* p, const lc_plan::Table& T, int s) {

@@ -643,9 +643,12 @@ struct FftOps {
     // fused TMA shell MAC over the full tiles (null where not built), FP32 / BF16 ring
     void (*mac_f32)(const MacArgs&, cudaStream_t);
     void (*mac_bf16)(const MacArgs&, cudaStream_t);
-    // warp-specialised variant of the same MAC (null where not built)
+    // warp-specialised MAC over every tile, Nyquist ones included (null where
+    // not built): one tile per CTA, or the tiles of lines q and N - q together
     void (*mac_ws_f32)(const MacArgs&, cudaStream_t);
     void (*mac_ws_bf16)(const MacArgs&, cudaStream_t);
+    void (*mac_ws2_f32)(const MacArgs&, cudaStream_t);
+    void (*mac_ws2_bf16)(const MacArgs&, cudaStream_t);
     int full_tiles; // tiles of the full 16-column chunks (the Nyquist tiles follow)
 };
 

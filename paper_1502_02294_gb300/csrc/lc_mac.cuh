@@ -283,30 +283,39 @@ __global__ void __launch_bounds__(MacCfg<N, BF16>::NT) k_mac_tma(MacArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Warp-specialised variant of the same MAC (k_mac_ws).  The CTA has NC
-// consumer threads and one producer warp:
-//  * the producer streams the tile's slices through an S-stage ring of
-//    shared-memory buffers (one cp.async.bulk per slice, lane 0) and the
-//    tile's Ghat rows in blocks of 4 slices (one 16-byte cp.async per row,
-//    all lanes, completion counted on an mbarrier), double buffered;
+// Warp-specialised form of the same MAC (k_mac_ws).  The CTA has NC consumer
+// threads and one producer warp:
+//  * the producer streams the slices of the CTA's tiles through an S-stage
+//    ring of shared-memory buffers (cp.async.bulk, lane 0) and the Ghat
+//    rows those tiles share in blocks of 4 slices (one 16-byte cp.async per
+//    row, all lanes, completion counted on an mbarrier), double buffered;
 //  * a consumer thread owns UPT units; a unit is a row pair {p, N - p}
-//    (or {0, N/2}) times 4 consecutive columns, so the 8 elements of a unit
-//    share the Ghat values of wedge rows (min(p, N - p), q, r..r+3) and the
-//    ring data is read with 128-bit shared loads;
+//    (or {0, N/2}) times 4 consecutive columns, whose elements share the
+//    Ghat values of wedge rows (min(p, N - p), q, r..r+3); the ring data is
+//    read with 128-bit shared loads;
 //  * consumers only wait for data and release buffers; the producer alone
 //    waits for free buffers.  Every wait is bounded.
-// Arithmetic per element and slice is k_mac_tma's (g = Ghat * D, then two
-// fused multiply-adds) in the same slice order, so both give identical sums.
+// PAIR = true: a CTA takes the tiles of lines q and N - q (same chunk),
+// whose Ghat rows are the same, so each gathered row serves both and the
+// gather traffic per ring byte halves; lines 0 and N/2 and the Nyquist tiles
+// (CW lines q of the column r = N/2) go one per CTA.  PAIR = false: one tile
+// per CTA.  Either way the launch covers every tile of the half spectrum.
+// Arithmetic per element and slice is that of k_mac_tma and of the gather
+// pass (g = Ghat * D, then two fused multiply-adds) in the same slice order,
+// so all of them give identical sums.
 constexpr int kWsGB = 4; // slices per Ghat block (16 bytes of a wedge row)
 
-template <int N, bool BF16> struct MacWsCfg {
+template <int N, bool BF16, bool PAIR> struct MacWsCfg {
     static constexpr int CW = cw_of(N), NRP = nrp_of(N), M = N / 2, NCH = M / CW, BP = odd_pad(CW);
+    static constexpr int P = PAIR ? 2 : 1;            // tiles per CTA
+    static constexpr int BPP = odd_pad(P * CW);       // x-transform buffer row (both tiles side by side)
     static constexpr int TILE = N * CW;
     static constexpr int EB = BF16 ? 4 : 8;
-    static constexpr int STAGE_BYTES = TILE * EB;
+    static constexpr int TILE_BYTES = TILE * EB;      // one slice of one tile
+    static constexpr int STAGE_BYTES = P * TILE_BYTES;
     static constexpr int CG = CW / 4;                 // 4-column groups
     static constexpr int UNITS = M * CG;              // (row pair, column group)
-    static constexpr int UPT = 2;                     // units per consumer thread
+    static constexpr int UPT = PAIR && BF16 ? 1 : 2;  // units per consumer thread
     static constexpr int NC = UNITS / UPT;            // consumer threads
     static constexpr int NCW = NC / 32;               // consumer warps
     static constexpr int NT = NC + 32;                // + the producer warp
@@ -314,13 +323,14 @@ template <int N, bool BF16> struct MacWsCfg {
     static constexpr int GPLANE = (M + 1) * CG;       // Ghat rows per column residue (col mod 4)
     static constexpr int GBLK_BYTES = GROWS * 16;     // one Ghat block: 4 floats per row
     static constexpr int MAXBLK = kMaxShells / kWsGB;
+    static constexpr int GRID = PAIR ? (M + 1) * NCH + N / CW : N * NCH + N / CW;
     static constexpr size_t FIXED = 2 * (size_t)GBLK_BYTES + (size_t)GROWS * 4 + (size_t)N * 8 +
                                     (size_t)kMaxShells * 12 + (size_t)MAXBLK * 12 + 64 + 256;
     static constexpr size_t BUDGET = 227 * 1024;
     static constexpr int FIT = BUDGET > FIXED ? (int)((BUDGET - FIXED) / STAGE_BYTES) : 0;
     static constexpr int STAGES = FIT > 8 ? 8 : FIT;
-    static constexpr size_t STAGE_AREA = (size_t)STAGES * STAGE_BYTES > (size_t)N * BP * 8
-                                             ? (size_t)STAGES * STAGE_BYTES : (size_t)N * BP * 8;
+    static constexpr size_t STAGE_AREA = (size_t)STAGES * STAGE_BYTES > (size_t)N * BPP * 8
+                                             ? (size_t)STAGES * STAGE_BYTES : (size_t)N * BPP * 8;
     static constexpr size_t OFF_STAGE = 0;
     static constexpr size_t OFF_G = (OFF_STAGE + STAGE_AREA + 127) / 128 * 128;
     static constexpr size_t OFF_WROW = OFF_G + 2 * (size_t)GBLK_BYTES;
@@ -330,7 +340,9 @@ template <int N, bool BF16> struct MacWsCfg {
     static constexpr size_t OFF_BAR = (OFF_BLK + (size_t)MAXBLK * 12 + 15) / 16 * 16;
     static constexpr int NBAR = 2 * 8 + 4; // full[8], empty[8], gfull[2], gempty[2]
     static constexpr size_t SMEM = OFF_BAR + NBAR * 8 + 128;
-    static constexpr bool OK = N >= 32 && N <= 256 && CW == 16 && STAGES >= 2 && NC % 32 == 0 &&
+    // built where the tiles are 16 columns wide and the ring holds at least
+    // 2 stages (3 when a stage carries two tiles)
+    static constexpr bool OK = N >= 32 && N <= 256 && CW == 16 && STAGES >= (PAIR ? 3 : 2) && NC % 32 == 0 &&
                                UNITS % UPT == 0 && SMEM <= BUDGET;
 };
 
@@ -347,11 +359,11 @@ __device__ __forceinline__ float2 bf2_to_f2(unsigned w) {
     return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
 }
 
-template <int N, bool BF16>
-__global__ void __launch_bounds__(MacWsCfg<N, BF16>::NT) k_mac_ws(MacArgs a) {
-    using C = MacWsCfg<N, BF16>;
-    constexpr int NT = C::NT, NC = C::NC, CW = C::CW, TILE = C::TILE, BP = C::BP, S = C::STAGES, M = C::M;
-    constexpr int UPT = C::UPT, CG = C::CG, GROWS = C::GROWS, GPLANE = C::GPLANE;
+template <int N, bool BF16, bool PAIR>
+__global__ void __launch_bounds__(MacWsCfg<N, BF16, PAIR>::NT, 1) k_mac_ws(MacArgs a) {
+    using C = MacWsCfg<N, BF16, PAIR>;
+    constexpr int NT = C::NT, NC = C::NC, CW = C::CW, TILE = C::TILE, BPP = C::BPP, S = C::STAGES, M = C::M;
+    constexpr int UPT = C::UPT, CG = C::CG, GROWS = C::GROWS, GPLANE = C::GPLANE, P = C::P, NCH = C::NCH;
     extern __shared__ unsigned char smem_raw3[];
     unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw3) + 127) & ~uintptr_t(127));
     unsigned char* stage = sm + C::OFF_STAGE;
@@ -372,8 +384,39 @@ __global__ void __launch_bounds__(MacWsCfg<N, BF16>::NT) k_mac_ws(MacArgs a) {
     __shared__ int s_nv, s_nb, s_fail;
     __shared__ double s_dc;
 
-    const int tile = blockIdx.x; // full tiles only
-    const int line = tile / C::NCH, chunk = tile % C::NCH;
+    // the CTA's tiles.  A full tile is (line q, columns [chunk CW, chunk CW + CW)),
+    // a Nyquist tile (lines [line, line + CW), column N/2); element (t, col) of
+    // tile h goes to dst[base[h] + t * N * NRP + col * cs]
+    int tile[2], line, chunk = 0;
+    bool nyq = false, two = false;
+    long long base[2], cs = 1;
+    {
+        const int b = blockIdx.x;
+        if (PAIR && b < (M - 1) * NCH) {
+            line = 1 + b / NCH;
+            chunk = b % NCH;
+            two = true;
+        } else if (PAIR && b < (M + 1) * NCH) {
+            const int k = b - (M - 1) * NCH;
+            line = k < NCH ? 0 : M;
+            chunk = k % NCH;
+        } else {
+            const int t0 = PAIR ? b - (M + 1) * NCH + N * NCH : b;
+            nyq = t0 >= N * NCH;
+            line = nyq ? (t0 - N * NCH) * CW : t0 / NCH;
+            chunk = nyq ? 0 : t0 % NCH;
+        }
+        if (nyq) {
+            tile[0] = N * NCH + line / CW;
+            base[0] = (long long)line * C::NRP + M;
+            cs = C::NRP;
+        } else {
+            tile[0] = line * NCH + chunk;
+            base[0] = (long long)line * C::NRP + chunk * CW;
+        }
+        tile[1] = two ? (N - line) * NCH + chunk : tile[0];
+        base[1] = two ? (long long)(N - line) * C::NRP + chunk * CW : base[0];
+    }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x < 32)
@@ -392,8 +435,11 @@ __global__ void __launch_bounds__(MacWsCfg<N, BF16>::NT) k_mac_ws(MacArgs a) {
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     for (int i = threadIdx.x; i < N; i += NT) tw[i] = a.tw[i];
-    // wedge rows of the tile, row = p' * CW + col
-    for (int r = threadIdx.x; r < GROWS; r += NT) s_wrow[r] = (int)wedge_of(r / CW, line, chunk * CW + r % CW, N);
+    // wedge rows of the tile(s), row = p' * CW + col (lines q and N - q share them)
+    for (int r = threadIdx.x; r < GROWS; r += NT) {
+        const int col = r % CW;
+        s_wrow[r] = nyq ? (int)wedge_of(r / CW, line + col, M, N) : (int)wedge_of(r / CW, line, chunk * CW + col, N);
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         // the Ghat blocks in slice order, with their valid slices
@@ -413,17 +459,20 @@ __global__ void __launch_bounds__(MacWsCfg<N, BF16>::NT) k_mac_ws(MacArgs a) {
     __syncthreads();
     const int nv = s_nv, nb = s_nb;
     bool ok = true;
-    // consumer state: unit u = threadIdx.x + k * NC is row pair pu = u / CG, columns 4 cg .. 4 cg + 3
-    float2 accA[UPT][4], accB[UPT][4];
+    // consumer state: unit u = threadIdx.x + k * NC is row pair pu = u / CG,
+    // columns 4 cg .. 4 cg + 3, in each of the CTA's tiles h
+    float2 accA[P][UPT][4], accB[P][UPT][4];
 #pragma unroll
-    for (int k = 0; k < UPT; ++k)
+    for (int h = 0; h < P; ++h)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) accA[k][c] = accB[k][c] = make_float2(0.f, 0.f);
+        for (int k = 0; k < UPT; ++k)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) accA[h][k][c] = accB[h][k][c] = make_float2(0.f, 0.f);
 
     if (warp == C::NCW) {
         // ------------------------------------------------------------ producer
-        const unsigned char* ring_tile =
-            static_cast<const unsigned char*>(a.ring) + (size_t)tile * a.n_ring * C::STAGE_BYTES;
+        const unsigned char* ring0 = static_cast<const unsigned char*>(a.ring) + (size_t)tile[0] * a.n_ring * C::TILE_BYTES;
+        const unsigned char* ring1 = static_cast<const unsigned char*>(a.ring) + (size_t)tile[1] * a.n_ring * C::TILE_BYTES;
         for (int gi = 0; gi < nb; ++gi) {
             const int gb = gi & 1;
             if (gi >= 2) ok = mbar_wait_bounded(smem_u32(&gempty[gb]), (unsigned)(((gi >> 1) - 1) & 1)) && ok;
@@ -442,9 +491,12 @@ __global__ void __launch_bounds__(MacWsCfg<N, BF16>::NT) k_mac_ws(MacArgs a) {
                     const int st = v % S;
                     if (v >= S) ok = mbar_wait_bounded(smem_u32(&empty[st]), (unsigned)(((v / S) - 1) & 1)) && ok;
                     const unsigned bar = smem_u32(&full[st]);
-                    mbar_expect_tx(bar, C::STAGE_BYTES);
-                    bulk_load(smem_u32(stage + (size_t)st * C::STAGE_BYTES),
-                              ring_tile + (size_t)s_slot[v] * C::STAGE_BYTES, C::STAGE_BYTES, bar);
+                    unsigned char* dst0 = stage + (size_t)st * C::STAGE_BYTES;
+                    mbar_expect_tx(bar, two ? 2 * C::TILE_BYTES : C::TILE_BYTES);
+                    bulk_load(smem_u32(dst0), ring0 + (size_t)s_slot[v] * C::TILE_BYTES, C::TILE_BYTES, bar);
+                    if (two)
+                        bulk_load(smem_u32(dst0 + C::TILE_BYTES), ring1 + (size_t)s_slot[v] * C::TILE_BYTES,
+                                  C::TILE_BYTES, bar);
                 }
             }
             __syncwarp();
@@ -457,7 +509,7 @@ __global__ void __launch_bounds__(MacWsCfg<N, BF16>::NT) k_mac_ws(MacArgs a) {
         for (int k = 0; k < UPT; ++k) {
             const int u = threadIdx.x + k * NC;
             const int pu = u / CG, cg = u % CG;
-            offA[k] = (pu * CW + cg * 4) * C::EB;                    // byte offset in a stage
+            offA[k] = (pu * CW + cg * 4) * C::EB;                    // byte offset in a tile's slice
             offB[k] = ((pu == 0 ? M : N - pu) * CW + cg * 4) * C::EB;
             goffA[k] = (pu * CG + cg) * 16;                          // Ghat slot of column residue 0
             goffB[k] = ((pu == 0 ? M : pu) * CG + cg) * 16;
@@ -482,36 +534,40 @@ __global__ void __launch_bounds__(MacWsCfg<N, BF16>::NT) k_mac_ws(MacArgs a) {
                 const int st = v % S;
                 ok = mbar_wait_bounded(smem_u32(&full[st]), (unsigned)((v / S) & 1)) && ok;
                 const float D = s_D[v];
-                const unsigned char* sb = stage + (size_t)st * C::STAGE_BYTES;
 #pragma unroll
-                for (int k = 0; k < UPT; ++k) {
-                    float2 fA[4], fB[4];
-                    if constexpr (BF16) {
-                        const uint4 wa = *reinterpret_cast<const uint4*>(sb + offA[k]);
-                        const uint4 wb = *reinterpret_cast<const uint4*>(sb + offB[k]);
-                        fA[0] = bf2_to_f2(wa.x); fA[1] = bf2_to_f2(wa.y);
-                        fA[2] = bf2_to_f2(wa.z); fA[3] = bf2_to_f2(wa.w);
-                        fB[0] = bf2_to_f2(wb.x); fB[1] = bf2_to_f2(wb.y);
-                        fB[2] = bf2_to_f2(wb.z); fB[3] = bf2_to_f2(wb.w);
-                    } else {
-                        const float4 a0 = *reinterpret_cast<const float4*>(sb + offA[k]);
-                        const float4 a1 = *reinterpret_cast<const float4*>(sb + offA[k] + 16);
-                        const float4 b0 = *reinterpret_cast<const float4*>(sb + offB[k]);
-                        const float4 b1 = *reinterpret_cast<const float4*>(sb + offB[k] + 16);
-                        fA[0] = make_float2(a0.x, a0.y); fA[1] = make_float2(a0.z, a0.w);
-                        fA[2] = make_float2(a1.x, a1.y); fA[3] = make_float2(a1.z, a1.w);
-                        fB[0] = make_float2(b0.x, b0.y); fB[1] = make_float2(b0.z, b0.w);
-                        fB[2] = make_float2(b1.x, b1.y); fB[3] = make_float2(b1.z, b1.w);
-                    }
+                for (int h = 0; h < P; ++h) {
+                    if (h == 1 && !two) continue;
+                    const unsigned char* sb = stage + (size_t)st * C::STAGE_BYTES + h * C::TILE_BYTES;
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const float ga = jj == 0 ? gA[k][c].x : jj == 1 ? gA[k][c].y : jj == 2 ? gA[k][c].z : gA[k][c].w;
-                        const float gb2 = jj == 0 ? gB[k][c].x : jj == 1 ? gB[k][c].y : jj == 2 ? gB[k][c].z : gB[k][c].w;
-                        const float g1 = ga * D, g2 = gb2 * D;
-                        accA[k][c].x = fmaf(g1, fA[c].x, accA[k][c].x);
-                        accA[k][c].y = fmaf(g1, fA[c].y, accA[k][c].y);
-                        accB[k][c].x = fmaf(g2, fB[c].x, accB[k][c].x);
-                        accB[k][c].y = fmaf(g2, fB[c].y, accB[k][c].y);
+                    for (int k = 0; k < UPT; ++k) {
+                        float2 fA[4], fB[4];
+                        if constexpr (BF16) {
+                            const uint4 wa = *reinterpret_cast<const uint4*>(sb + offA[k]);
+                            const uint4 wb = *reinterpret_cast<const uint4*>(sb + offB[k]);
+                            fA[0] = bf2_to_f2(wa.x); fA[1] = bf2_to_f2(wa.y);
+                            fA[2] = bf2_to_f2(wa.z); fA[3] = bf2_to_f2(wa.w);
+                            fB[0] = bf2_to_f2(wb.x); fB[1] = bf2_to_f2(wb.y);
+                            fB[2] = bf2_to_f2(wb.z); fB[3] = bf2_to_f2(wb.w);
+                        } else {
+                            const float4 a0 = *reinterpret_cast<const float4*>(sb + offA[k]);
+                            const float4 a1 = *reinterpret_cast<const float4*>(sb + offA[k] + 16);
+                            const float4 b0 = *reinterpret_cast<const float4*>(sb + offB[k]);
+                            const float4 b1 = *reinterpret_cast<const float4*>(sb + offB[k] + 16);
+                            fA[0] = make_float2(a0.x, a0.y); fA[1] = make_float2(a0.z, a0.w);
+                            fA[2] = make_float2(a1.x, a1.y); fA[3] = make_float2(a1.z, a1.w);
+                            fB[0] = make_float2(b0.x, b0.y); fB[1] = make_float2(b0.z, b0.w);
+                            fB[2] = make_float2(b1.x, b1.y); fB[3] = make_float2(b1.z, b1.w);
+                        }
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const float ga = jj == 0 ? gA[k][c].x : jj == 1 ? gA[k][c].y : jj == 2 ? gA[k][c].z : gA[k][c].w;
+                            const float gbv = jj == 0 ? gB[k][c].x : jj == 1 ? gB[k][c].y : jj == 2 ? gB[k][c].z : gB[k][c].w;
+                            const float g1 = ga * D, g2 = gbv * D;
+                            accA[h][k][c].x = fmaf(g1, fA[c].x, accA[h][k][c].x);
+                            accA[h][k][c].y = fmaf(g1, fA[c].y, accA[h][k][c].y);
+                            accB[h][k][c].x = fmaf(g2, fB[c].x, accB[h][k][c].x);
+                            accB[h][k][c].y = fmaf(g2, fB[c].y, accB[h][k][c].y);
+                        }
                     }
                 }
                 // release the stage: one arrival per warp
@@ -534,37 +590,41 @@ __global__ void __launch_bounds__(MacWsCfg<N, BF16>::NT) k_mac_ws(MacArgs a) {
     __syncthreads(); // every stage consumed: the stage area becomes the x-transform buffer
     if (s_fail && threadIdx.x == 0) atomicOr(a.err, 4);
     if (warp < C::NCW) {
-        if (line == 0 && chunk == 0 && threadIdx.x == 0) accA[0][0] = make_float2((float)s_dc, 0.0f);
+        if (!nyq && line == 0 && chunk == 0 && threadIdx.x == 0) accA[0][0][0] = make_float2((float)s_dc, 0.0f);
 #pragma unroll
-        for (int k = 0; k < UPT; ++k) {
-            const int u = threadIdx.x + k * NC;
-            const int pu = u / CG, cg = u % CG;
-            const int tA = pu, tB = pu == 0 ? M : N - pu;
+        for (int h = 0; h < P; ++h)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                buf[tA * BP + cg * 4 + c] = accA[k][c];
-                buf[tB * BP + cg * 4 + c] = accB[k][c];
+            for (int k = 0; k < UPT; ++k) {
+                const int u = threadIdx.x + k * NC;
+                const int pu = u / CG, cg = u % CG;
+                const int tA = pu, tB = pu == 0 ? M : N - pu;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    buf[tA * BPP + h * CW + cg * 4 + c] = accA[h][k][c];
+                    buf[tB * BPP + h * CW + cg * 4 + c] = accB[h][k][c];
+                }
             }
-        }
     }
     __syncthreads();
-    fft_smem<N, 1, CW, BP, NT>(buf, tw);
+    fft_smem<N, 1, P * CW, BPP, NT>(buf, tw);
     constexpr long long PLANE = (long long)N * C::NRP;
-    const long long base = (long long)line * C::NRP + chunk * CW;
-    for (int idx = threadIdx.x; idx < TILE; idx += NT) {
-        const int t = idx / CW, col = idx % CW;
-        a.dst[base + t * PLANE + col] = buf[t * BP + col];
+    for (int idx = threadIdx.x; idx < P * TILE; idx += NT) {
+        const int h = idx / TILE, e = idx % TILE;
+        if (h == 1 && !two) break;
+        const int t = e / CW, col = e % CW;
+        a.dst[base[h] + t * PLANE + col * cs] = buf[t * BPP + h * CW + col];
     }
 }
 
-template <int N, bool BF16> struct MacWsLaunch {
-    using C = MacWsCfg<N, BF16>;
+template <int N, bool BF16, bool PAIR> struct MacWsLaunch {
+    using C = MacWsCfg<N, BF16, PAIR>;
     static cudaError_t init() {
         if constexpr (!C::OK) return cudaSuccess;
-        else return cudaFuncSetAttribute(k_mac_ws<N, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        else return cudaFuncSetAttribute(k_mac_ws<N, BF16, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     }
+    // every tile of the half spectrum: full ones (paired or single), then the Nyquist ones
     static void run(const MacArgs& a, cudaStream_t st) {
-        if constexpr (C::OK) k_mac_ws<N, BF16><<<N * C::NCH, C::NT, C::SMEM, st>>>(a);
+        if constexpr (C::OK) k_mac_ws<N, BF16, PAIR><<<C::GRID, C::NT, C::SMEM, st>>>(a);
     }
 };
 

@@ -43,7 +43,7 @@ def _errors(J, ref):
 
 
 @pytest.mark.parametrize("history", [synth.HISTORY_FP32, synth.HISTORY_BF16])
-@pytest.mark.parametrize("variant", ["gather", "bulk", "ws"])
+@pytest.mark.parametrize("variant", ["gather", "bulk", "ws", "ws2"])
 def test_forced_variant_matches_oracle_every_slice_count(monkeypatch, variant, history):
     # c1 (32^3, 8 steps): slice counts 1..8 cover a partial Ghat block and
     # fewer slices than pipeline stages
@@ -66,14 +66,15 @@ def test_forced_variants_agree_many_slices(monkeypatch):
     w = synth.small(n=64, box=90.0, n_steps=20, n_src=300, subsamples=2, clustered=True, seed=4242)
     P = oracle.Problem.from_workload(w)
     res = {}
-    for v in ("gather", "bulk", "ws"):
+    for v in ("gather", "bulk", "ws", "ws2"):
         monkeypatch.setenv("LC_MAC_VARIANT", v)
         res[v] = _fields(w, range(20), {12, 19})
     for s in (12, 19):
-        # the two bulk-copy kernels do the same arithmetic in the same order
-        assert np.array_equal(res["bulk"][s], res["ws"][s]), s
+        # every MAC kernel does the same arithmetic in the same order
+        for v in ("bulk", "ws", "ws2"):
+            assert np.array_equal(res["gather"][s], res[v][s]), (v, s)
         ref = oracle.field_for(P, w.cat, s)
-        for v in ("gather", "bulk", "ws"):
+        for v in ("gather", "bulk", "ws", "ws2"):
             rel, mx = _errors(res[v][s], ref)
             assert rel <= FP32_L2 and mx <= FP32_MAX, (v, s, rel, mx)
 
@@ -87,6 +88,6 @@ def test_choices_reported_and_persisted(monkeypatch, tmp_path):
     _fields(w, range(4), {3})
     rep = lc.autotune_report()
     mine = {k: v for k, v in rep.items() if "/N96/bf16/" in k}
-    assert mine and set(mine.values()) <= {"gather", "bulk", "ws"}
+    assert mine and set(mine.values()) <= {"gather", "bulk", "ws", "ws2"}
     lines = cache.read_text().split()
     assert any("/N96/bf16/" in t for t in lines)
