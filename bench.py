@@ -46,8 +46,9 @@ WORKLOADS = {
             "BF16 history (profiling size of the c3 path)"),
     "c4": ("16 uneven instances (grids 64..256 cycled, 32..128 shells, 1e3..1e5 clustered sources, 0.78 Mpc "
            "cells), FP32, all instances' step in one CUDA graph replay (parallel branches)"),
-    "c5": ("serving: 8 simulations 128^3-256^3, 48..128 shells, BF16 history, 16 requests each, continuous "
-           "batching with per-simulation streams, HBM-budget admission; saturation + Poisson passes"),
+    "c5": ("serving: 8 simulations N = 128, 192, 256, 256, 384, 384, 512, 512 with 128, 112, 96, 128, 96, 64, "
+           "96, 96 shells, BF16 history, 1e4-1e5 clustered sources, 16 requests each, continuous batching under an "
+           "HBM budget; beside it the plain FP32 one-instance path on the same requests"),
 }
 
 
@@ -234,6 +235,7 @@ def run_batched(args, ClockSampler=ClockSampler):
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     mac_gbs = mac_bytes / (mac_ms / 1e3) / 1e9 if mac_ms > 0 else None
+    traffic, traffic_src = mac_traffic(args.workload)
     # e2e: host buffers through the plain batched call
     host_in = [[(np.ascontiguousarray(w.cat.active(s)[0]), np.ascontiguousarray(w.cat.active(s)[1]))
                 for s in range(w.steps.n_steps)] for w in ws]
@@ -284,7 +286,11 @@ def run_batched(args, ClockSampler=ClockSampler):
 
 
 def run_serving(args, ClockSampler=ClockSampler):
-    """Continuous batching of field requests from 8 simulations."""
+    """Continuous batching of field requests from the 8 served simulations
+    (128^3..512^3, BF16 history), beside the plain FP32 one-instance path on
+    the same requests."""
+    import dataclasses
+
     import torch
 
     import paper_1502_02294_gb300 as lc
@@ -293,24 +299,21 @@ def run_serving(args, ClockSampler=ClockSampler):
 
     lc.build()
     torch.cuda.set_device(0)
-    grids = [128, 128, 192, 192, 256, 256, 128, 192]
-    shells = [64, 96, 64, 96, 64, 96, 128, 48]
+    ws = synth.served_simulations()
     per_sim = 16
-    ws = []
-    for i, (n, sh) in enumerate(zip(grids, shells)):
-        box = 0.78125 * n
-        st = synth.StepSpec(synth.STEPS_EQUAL_TAU, sh + per_sim, z_end=15.0, n_shell=sh)
-        cat = synth.make_catalogue(synth.SEED_BASE + 4000 + i, 20000, box, sh + per_sim, clustered=True,
-                                   n_centres=200, sigma=2.0)
-        ws.append(synth.Workload(f"s{i}", n, box, 0.31, 0.68, st, 4, synth.HISTORY_BF16, cat))
+    grids = [w.n for w in ws]
+    shells = [w.steps.n_shell for w in ws]
+
+    def fill(p, w):
+        for s in range(w.steps.n_shell):
+            p.push(s, *w.cat.active(s))
 
     def one_pass(rate):
         srv = Server(hbm_budget_bytes=int(0.6 * torch.cuda.get_device_properties(0).total_memory))
         reqs = []
         for w in ws:
             sh = w.steps.n_shell
-            srv.add_simulation(w.name, w, sh, sh + per_sim - 1,
-                               fill=lambda p, w=w: [p.push(s, *w.cat.active(s)) for s in range(w.steps.n_shell)])
+            srv.add_simulation(w.name, w, sh, sh + per_sim - 1, fill=lambda p, w=w: fill(p, w))
             for s in range(sh, sh + per_sim):
                 reqs.append(Request(w.name, s, *w.cat.active(s)))
         torch.cuda.synchronize()
@@ -331,12 +334,39 @@ def run_serving(args, ClockSampler=ClockSampler):
                     arr[i] = tt
         return srv.run_stream(reqs, arr, limit_s=300.0)
 
-    one_pass(None)  # warm-up: compiles nothing, but touches every code path
+    def plain_fp32():
+        """The same requests, one simulation at a time in FP32 history: eager
+        push + field per request on the default stream, no graph, no overlap;
+        tables and history filled before the clock starts."""
+        total, n = 0.0, 0
+        for w in ws:
+            wf = dataclasses.replace(w, history=synth.HISTORY_FP32)
+            sh = w.steps.n_shell
+            plan = lc.Plan.from_workload(wf)
+            plan.prepare(sh, sh + per_sim)
+            fill(plan, wf)
+            reqs = [wf.cat.active(s) for s in range(sh, sh + per_sim)]
+            out = torch.empty((w.n,) * 3, dtype=torch.float32, device="cuda")
+            torch.cuda.synchronize()
+            tic = time.perf_counter()
+            for k, (pos, lum) in enumerate(reqs):
+                plan.push(sh + k, torch.from_numpy(pos).to("cuda"), torch.from_numpy(lum).to("cuda"))
+                plan.field(sh + k, out)
+            torch.cuda.synchronize()
+            total += time.perf_counter() - tic
+            n += len(reqs)
+            plan.close()
+            del out
+            torch.cuda.empty_cache()
+        return n / total, total
+
+    one_pass(None)  # warm-up: touches every code path and tunes the kernels
     sampler = ClockSampler(0)
     sampler.start()
     sat = one_pass(None)
     clocks = sampler.stop()
     pois = one_pass(0.8 * sat["fields_per_s"])
+    plain_rate, plain_s = plain_fp32()
     line = {
         "metric": METRIC, "value": sat["fields_per_s"], "unit": UNIT, "n_gpus": 1, "steps": sat["requests"],
         "warmup": len(ws) * per_sim, "ms_per_step": 1e3 / sat["fields_per_s"], "higher_is_better": True,
@@ -346,6 +376,10 @@ def run_serving(args, ClockSampler=ClockSampler):
         "latency_ms": {"saturation_p50": sat["p50_ms"], "saturation_p99": sat["p99_ms"],
                        "poisson_p50": pois["p50_ms"], "poisson_p99": pois["p99_ms"]},
         "poisson_fields_per_s": pois["fields_per_s"],
+        "plain_fp32_one_instance": {"fields_per_s": plain_rate, "seconds": plain_s,
+                                    "served_over_plain": sat["fields_per_s"] / plain_rate,
+                                    "path": "FP32 history, one plan at a time, eager push + field per request, "
+                                            "no graph, no overlap (tables and history prepared untimed)"},
         "clocks": clocks,
         "e2e": {"value": sat["fields_per_s"], "unit": UNIT,
                 "h2d_bytes_per_step": int(np.mean([w.cat.active(w.steps.n_shell)[1].nbytes * 4 for w in ws])),
@@ -355,6 +389,36 @@ def run_serving(args, ClockSampler=ClockSampler):
     }
     print(json.dumps(line))
     return 0
+
+
+# DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum) of the
+# shell-MAC phase per step, from the captures summarised in profiles/, valid
+# only for the kernel sources they were taken with (hash below); c3 is the
+# c3s capture (32 slices) with its reads scaled to 128 slices.
+MAC_SOURCES = ("lc_mac.cuh", "lc_kernels.cuh", "lc_fft.cuh")
+MAC_TRAFFIC = {
+    "c2": {"sources": "326f27066b6e7021", "bytes": 38.466e6,
+           "from": "profiles/c2_dram_traffic.md (64-step window, all MAC-phase launches)"},
+    "c3": {"sources": "326f27066b6e7021", "bytes": 4 * 1.187670e9 + 72.543e6,
+           "from": "profiles/k_mac_ws_256_bf16_pair.md (c3s, reads x 128/32)"},
+}
+
+
+def mac_sources_hash():
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in MAC_SOURCES:
+        with open(os.path.join(ROOT, "paper_1502_02294_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def mac_traffic(workload):
+    t = MAC_TRAFFIC.get(workload)
+    if t is None or t["sources"] != mac_sources_hash():
+        return None, None
+    return t["bytes"], t["from"]
 
 
 DEFAULT_STEPS = {"c1": 2048, "c2": 2048, "c3": 64, "c3s": 32, "c4": 32, "c5": 32}
@@ -458,7 +522,7 @@ def main():
     tag = f"/N{w.n}/{'bf16' if w.history else 'fp32'}/"
     mac_choice = {k.rsplit("/", 1)[1]: v for k, v in lc.autotune_report().items() if tag in k}
 
-    def run_pass(gs, evs=None):
+    def run_pass(gs, evs=None, nvtx=False):
         refill()
         steps_done = []
         for i in range(args.steps):
@@ -468,7 +532,11 @@ def main():
             flush.zero_()  # L2 flush between timed steps, outside the events
             if evs:
                 evs[i][0].record(stream)
+            if nvtx:
+                torch.cuda.nvtx.range_push("step")  # lets a profiler select the timed replays
             gs[s].launch()
+            if nvtx:
+                torch.cuda.nvtx.range_pop()
             if evs:
                 evs[i][1].record(stream)
             steps_done.append(s)
@@ -488,10 +556,8 @@ def main():
     torch.cuda.synchronize()
     launches0 = lc.kernel_launches()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    torch.cuda.nvtx.range_push("timed")  # lets a profiler select the timed launches
-    done_steps = run_pass(graphs, evs)
+    done_steps = run_pass(graphs, evs, nvtx=True)
     torch.cuda.synchronize()
-    torch.cuda.nvtx.range_pop()
     launches = lc.kernel_launches() - launches0
     if world > 1:
         torch.distributed.barrier()
@@ -529,6 +595,7 @@ def main():
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     mac_gbs = mac_bytes / (mac_ms / 1e3) / 1e9 if mac_ms > 0 else None
+    traffic, traffic_src = mac_traffic(args.workload)
     phase_share = {k: round(v[0] / max(1e-12, sum(x[0] for x in phases.values())), 4) for k, v in phases.items()}
 
     # end to end through the public API: pinned host inputs, host output
@@ -586,7 +653,7 @@ def main():
             "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "grid": w.n,
                        "box_mpc": w.box, "steps_in_run": T, "timed_window": [t0, T], "ring_slots": plan.n_ring,
                        "history": "bf16" if w.history else "fp32",
-                       "mac_kernel": {v: sum(1 for x in mac_choice.values() if x == v) for v in ("gather", "bulk", "ws", "ws2")},
+                       "mac_kernel": dict(sorted(mac_choice.items(), key=lambda kv: int(kv[0][1:]))),
                        "l2": f"flushed between timed steps "
                        f"({args.flush_mb} MB write outside the events)", "inputs": "device-resident"},
             "cell_shell_mac_per_s": world * mac_cells / t_max,
@@ -595,7 +662,8 @@ def main():
                          "Nyquist k_cols (bulk), fused with the inverse x pass",
                          "achieved": mac_gbs, "peak": hbm_peak, "unit": "GB/s",
                          "frac": (mac_gbs / hbm_peak) if mac_gbs else None,
-                         "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+                         "traffic": traffic, "traffic_source": traffic_src,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
                          "bytes_per_launch": mac_bytes / max(1, len(mac_steps)),
                          "ms_per_launch": mac_ms / max(1, len(mac_steps))},
             "phase_ms_per_step": {k: v[0] / max(1, len(mac_steps)) for k, v in phases.items()},

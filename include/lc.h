@@ -268,6 +268,17 @@ uint64_t lc_kernel_launches(void);
  * into buf (size bytes, NUL-terminated) and returns the full length. */
 int lc_autotune_report(char* buf, int size);
 
+/* --- light-cone vs instantaneous field ------------------------------------------ */
+
+/* The fractional difference f_diff = (J_instant - J) / J that Section 3 uses
+ * (after Eq. 18) to measure the light-cone effect, per cell, from a field of
+ * lc_retarded_field and one of lc_instant_field for the same step.  All
+ * three arrays hold n floats in device memory (LC_ERR_INVALID_ARG
+ * otherwise); the difference and quotient are taken in FP64 and rounded
+ * once.  Cells where both fields are 0 get 0; where only J is 0, IEEE
+ * +-infinity.  Asynchronous on `stream`. */
+lc_status lc_fdiff_map(int64_t n, const float* j_retarded, const float* j_instant, float* out, void* stream);
+
 /* --- the hot-path kernels as stand-alone calls (tests, users) --------------- */
 
 /* Nearest-grid-point fixed-point deposit: scale S = 2^(E-62) with

@@ -106,6 +106,7 @@ SIGNATURES = [
     ("lc_fft_c2r", _I, [_I, _VP, _VP, ctypes.c_float, _VP]),
     ("lc_fft_r2c_static", _I, [_I, _VP, _VP, _VP]),
     ("lc_autotune_report", _I, [ctypes.c_char_p, _I]),
+    ("lc_fdiff_map", _I, [_I64, _VP, _VP, _VP, _VP]),
     ("lc_plan_checkpoint_bytes", ctypes.c_size_t, [_P]),
     ("lc_plan_save", _I, [_P, _VP, ctypes.c_size_t]),
     ("lc_plan_load", _I, [_P, _VP, ctypes.c_size_t]),
@@ -434,6 +435,18 @@ def estimate_bytes(n, steps, omega_m, h, history=HISTORY_FP32) -> Tuple[int, int
     _check(_lib().lc_plan_estimate(int(n), ctypes.byref(st), ctypes.byref(c), ctypes.byref(b), ctypes.byref(t)),
            "lc_plan_estimate")
     return int(b.value), int(t.value)
+
+
+def fdiff_map(j_retarded, j_instant, out=None, stream=None):
+    """f_diff = (J_instant - J) / J per cell (torch CUDA float32 tensors)."""
+    torch = _torch()
+    assert j_retarded.dtype == torch.float32 and j_instant.dtype == torch.float32
+    assert j_retarded.is_contiguous() and j_instant.is_contiguous() and j_retarded.numel() == j_instant.numel()
+    if out is None:
+        out = torch.empty_like(j_retarded)
+    _check(_lib().lc_fdiff_map(j_retarded.numel(), j_retarded.data_ptr(), j_instant.data_ptr(), out.data_ptr(),
+                               _stream_ptr(stream)), "lc_fdiff_map")
+    return out
 
 
 def deposit_grid(n: int, box: float, pos, lum, out=None, stream=None):

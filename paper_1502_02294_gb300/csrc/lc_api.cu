@@ -12,6 +12,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <map>
 #include <mutex>
@@ -443,13 +444,17 @@ int choose_mac_variant(lc_plan* p, const lc_plan::Table& T, int s) {
     std::vector<long long> ht(p->n_ring, 1);
     for (int j = 0; j < T.A && s - j >= 0; ++j) hs[(s - j) % p->n_ring] = s - j;
     cudaStream_t st = p->stream;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    constexpr int kReps = 5; // timed launches per variant, each between its own events
+    cudaEvent_t ev[kReps + 1] = {};
     double ms[MAC_NVAR];
     for (int v = 0; v < MAC_NVAR; ++v) ms[v] = -1.0;
-    if (cudaMemcpy(p->d_tune_step, hs.data(), sizeof(int) * p->n_ring, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(p->d_tune_S, hS.data(), sizeof(double) * p->n_ring, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(p->d_tune_total, ht.data(), sizeof(long long) * p->n_ring, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    bool ok = cudaMemcpy(p->d_tune_step, hs.data(), sizeof(int) * p->n_ring, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(p->d_tune_S, hS.data(), sizeof(double) * p->n_ring, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(p->d_tune_total, ht.data(), sizeof(long long) * p->n_ring, cudaMemcpyHostToDevice) == cudaSuccess;
+    for (int r = 0; ok && r <= kReps; ++r) ok = cudaEventCreate(&ev[r]) == cudaSuccess;
+    if (!ok) {
+        for (auto e : ev)
+            if (e) cudaEventDestroy(e);
         cudaGetLastError();
         return MAC_GATHER;
     }
@@ -457,18 +462,23 @@ int choose_mac_variant(lc_plan* p, const lc_plan::Table& T, int s) {
     for (int v = 0; v < MAC_NVAR; ++v) {
         if (!mac_built(p, v)) continue;
         launch_mac(p, T, s, 0, v, p->d_tune_step, p->d_tune_S, p->d_tune_total, st); // warm-up
-        cudaEventRecord(e0, st);
-        for (int r = 0; r < 3; ++r) launch_mac(p, T, s, 0, v, p->d_tune_step, p->d_tune_S, p->d_tune_total, st);
-        cudaEventRecord(e1, st);
-        cudaEventSynchronize(e1);
-        float t = 0.f;
-        cudaEventElapsedTime(&t, e0, e1);
-        ms[v] = t / 3.0;
-        count_launch(4ULL * mac_kernels(p, v));
-        if (ms[v] < ms[best]) best = v;
+        cudaEventRecord(ev[0], st);
+        for (int r = 0; r < kReps; ++r) {
+            launch_mac(p, T, s, 0, v, p->d_tune_step, p->d_tune_S, p->d_tune_total, st);
+            cudaEventRecord(ev[r + 1], st);
+        }
+        cudaEventSynchronize(ev[kReps]);
+        float t[kReps];
+        for (int r = 0; r < kReps; ++r) {
+            t[r] = 0.f;
+            cudaEventElapsedTime(&t[r], ev[r], ev[r + 1]);
+        }
+        std::sort(t, t + kReps);
+        ms[v] = t[kReps / 2]; // median launch
+        count_launch((unsigned long long)(kReps + 1) * mac_kernels(p, v));
+        if (ms[v] < ms[best] || ms[best] < 0) best = v;
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    for (auto e : ev) cudaEventDestroy(e);
     if (cudaGetLastError() != cudaSuccess) return MAC_GATHER;
     std::lock_guard<std::mutex> g(g_tune_mu);
     tune_store(key, best, ms);
@@ -1465,6 +1475,16 @@ lc_status lc_batch_graph_destroy(lc_batch_graph* g) {
 }
 
 // ------------------------------------------------------------ stand-alone kernels
+lc_status lc_fdiff_map(int64_t n, const float* j_retarded, const float* j_instant, float* out, void* stream) {
+    if (n < 0 || (n > 0 && (!j_retarded || !j_instant || !out))) return LC_ERR_INVALID_ARG;
+    if (n > 0 && (!is_device_ptr(j_retarded) || !is_device_ptr(j_instant) || !is_device_ptr(out)))
+        return LC_ERR_INVALID_ARG;
+    launch_fdiff(n, j_retarded, j_instant, out, (cudaStream_t)stream);
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) count_launch(n > 0 ? 1 : 0);
+    return e == cudaSuccess ? LC_OK : LC_ERR_CUDA;
+}
+
 lc_status lc_deposit_grid(int n, double box, int64_t n_src, const double* pos, const double* lum, int64_t* grid,
                           double* scale, int64_t* total, void* stream) {
     if (n < 1 || n > 4096 || !(box > 0.0) || n_src < 0 || !grid || (n_src > 0 && (!pos || !lum)))

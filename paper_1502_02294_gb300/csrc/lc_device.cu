@@ -290,6 +290,22 @@ void launch_deposit(const double* pos, const double* lum, long long n, int N, do
     k_deposit<<<(unsigned)blocks, 256, 0, st>>>(pos, lum, n, N, l, maxbits, grid, m, cell_out, q_out);
 }
 
+// f_diff = (J_instant - J) / J, the difference taken and divided in FP64 and
+// rounded once; 0 where both fields are 0 (IEEE +-inf where only J is 0)
+__global__ void __launch_bounds__(256) k_fdiff(long long n, const float* __restrict__ j,
+                                               const float* __restrict__ ji, float* __restrict__ out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double a = j[i], b = ji[i];
+        out[i] = (a == 0.0 && b == 0.0) ? 0.0f : (float)((b - a) / a);
+    }
+}
+
+void launch_fdiff(long long n, const float* j, const float* j_inst, float* out, cudaStream_t st) {
+    if (n <= 0) return;
+    const long long blocks = (n + 255) / 256;
+    k_fdiff<<<(unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, st>>>(n, j, j_inst, out);
+}
+
 void launch_rgf_accum(const RgfAccumArgs& a, cudaStream_t st) {
     if (a.W <= 0) return;
     k_rgf_accum<<<(unsigned)((a.W + 127) / 128), 128, 0, st>>>(a);

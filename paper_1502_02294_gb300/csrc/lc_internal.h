@@ -77,6 +77,8 @@ struct RgfAccumArgs {
     double rh;
 };
 void launch_rgf_accum(const RgfAccumArgs& a, cudaStream_t st);
+// f_diff = (J_instant - J) / J per cell (Section 3 after Eq. 18)
+void launch_fdiff(long long n, const float* j, const float* j_inst, float* out, cudaStream_t st);
 // per shell: full-grid sum with multiplicities -> scale (normalisation) and Ghat(0)
 void launch_rgf_norm(int N, long long W, int A, const double* gw, const double* I, double l3, int normalise,
                      double* scale, double* g0, cudaStream_t st);
