@@ -404,6 +404,19 @@ MAC_TRAFFIC = {
 }
 
 
+def max_over_ranks(x, device):
+    """The largest of every rank's x (the job's time is its slowest rank's);
+    x itself when no process group is running."""
+    import torch
+    import torch.distributed as dist
+
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def mac_sources_hash():
     import hashlib
 
@@ -571,11 +584,7 @@ def main():
         g.close()
     per_step_ms = np.array([a.elapsed_time(b) for a, b in evs])
     t_total = float(per_step_ms.sum()) / 1e3
-    t_max = t_total
-    if world > 1:
-        tt = torch.tensor([t_total], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = max_over_ranks(t_total, dev)
     value = world * args.steps / t_max
     mac_cells = sum(nk * work[s][0] for s in done_steps)
 
@@ -627,10 +636,7 @@ def main():
         e2e_t += time.perf_counter() - tic
         h2d += pinned[s][0].numel() * 8 + pinned[s][1].numel() * 8
         e_cursor = t0 + (s + 1 - t0) % (T - t0)
-    if world > 1:
-        tt = torch.tensor([e2e_t], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_t = float(tt.item())
+    e2e_t = max_over_ranks(e2e_t, dev)
     e2e = {"value": world * args.steps / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(h2d // args.steps),
            "d2h_bytes_per_step": int(w.n ** 3 * 4)}
 

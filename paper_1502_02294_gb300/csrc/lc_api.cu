@@ -87,6 +87,14 @@ static inline void count_launch(unsigned long long k = 1) { g_launches.fetch_add
 
 using namespace lc;
 
+bool lc::pdl_enabled() {
+    static const bool on = [] {
+        const char* f = getenv("LC_PDL");
+        return !(f && f[0] == '0');
+    }();
+    return on;
+}
+
 // ---------------------------------------------------------------- autotuner
 // The shell MAC has four variants: a register-gather pass (MAC_GATHER), a
 // bulk-copy pipelined kernel for the full tiles (MAC_BULK), and its
@@ -732,7 +740,8 @@ lc_status lc_plan_create(int n, double box_mpc, const lc_cosmology* cosmo, const
         return LC_ERR_OOM;
     }
     std::vector<float2> tw = twiddles(n);
-    e = cudaMemcpyAsync(p->d_tw, tw.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, p->stream);
+    e = cudaMemsetAsync(p->d_grid, 0, sizeof(long long) * N3, p->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_tw, tw.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, p->stream);
     if (e == cudaSuccess && p->near_on) e = cudaMemsetAsync(p->d_near, 0, sizeof(double) * N3, p->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_slot_step, 0xff, sizeof(int) * p->n_ring, p->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_slot_total, 0, sizeof(long long) * p->n_ring, p->stream);
@@ -801,9 +810,9 @@ lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos
     SlotMeta m{slot, step, p->d_slot_step, p->d_slot_S, p->d_slot_total};
     const long long N = p->N;
     {
+        // the grid is all zero here: zeroed at creation, and the forward z
+        // pass sets every cell back to 0 as it reads it
         Phase ph(p, LC_PHASE_DEPOSIT, n_src > 0 ? 2 : 1);
-        e = cudaMemsetAsync(p->d_grid, 0, sizeof(long long) * N * N * N, st);
-        if (e != cudaSuccess) return cuda_fail(p, e);
         launch_src_prep(dpos, dlum, n_src, p->d_maxbits, p->d_err, m, st);
         if (n_src > 0)
             launch_deposit(dpos, dlum, n_src, p->N, p->l, p->d_maxbits, p->d_grid, m, st,

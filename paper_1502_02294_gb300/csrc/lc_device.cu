@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "lc_fft.cuh"
 #include "lc_internal.h"
 
 namespace lc {
@@ -27,6 +28,7 @@ __device__ __forceinline__ bool finite_d(double x) { return isfinite(x); }
 __global__ void __launch_bounds__(kPrepThreads)
     k_src_prep(const double* __restrict__ pos, const double* __restrict__ lum, long long n,
                unsigned long long* maxbits, int* err, SlotMeta m) {
+    pdl_enter();
     __shared__ unsigned long long s_max[kPrepThreads / 32];
     __shared__ int s_bad;
     if (threadIdx.x == 0) s_bad = 0;
@@ -69,6 +71,7 @@ __global__ void __launch_bounds__(256)
     k_deposit(const double* __restrict__ pos, const double* __restrict__ lum, long long n, int N, double l,
               const unsigned long long* __restrict__ maxbits, long long* __restrict__ grid, SlotMeta m,
               long long* __restrict__ cell_out, long long* __restrict__ q_out) {
+    pdl_enter();
     __shared__ long long s_sum[8];
     const double lmax = __longlong_as_double((long long)*maxbits);
     double S = 1.0;
@@ -232,6 +235,7 @@ __global__ void __launch_bounds__(256) k_near_scatter(const long long* __restric
                                                       long long n, int N, const double* __restrict__ gnear,
                                                       const double* __restrict__ slot_S, int slot, double U,
                                                       double* __restrict__ acc) {
+    pdl_enter();
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n * kNearCube) return;
     const long long s = idx / kNearCube;
@@ -245,6 +249,7 @@ __global__ void __launch_bounds__(256) k_near_scatter(const long long* __restric
 
 __global__ void __launch_bounds__(256) k_near_fold(const long long* __restrict__ cell, const long long* __restrict__ q,
                                                    long long n, int N, double* __restrict__ acc, float* __restrict__ out) {
+    pdl_enter();
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n * kNearCube) return;
     const long long s = idx / kNearCube;
@@ -268,26 +273,26 @@ void launch_near_scatter(const long long* cell, const long long* q, long long n,
                          const double* slot_S, int slot, double U, double* acc, cudaStream_t st) {
     const long long total = n * kNearCube;
     if (total <= 0) return;
-    k_near_scatter<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(cell, q, n, N, gnear, slot_S, slot, U, acc);
+    launch_k(k_near_scatter, (unsigned)((total + 255) / 256), 256, 0, st, cell, q, n, N, gnear, slot_S, slot, U, acc);
 }
 
 void launch_near_fold(const long long* cell, const long long* q, long long n, int N, double* acc, float* out,
                       cudaStream_t st) {
     const long long total = n * kNearCube;
     if (total <= 0) return;
-    k_near_fold<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(cell, q, n, N, acc, out);
+    launch_k(k_near_fold, (unsigned)((total + 255) / 256), 256, 0, st, cell, q, n, N, acc, out);
 }
 
 void launch_src_prep(const double* pos, const double* lum, long long n, unsigned long long* maxbits, int* err,
                      SlotMeta m, cudaStream_t st) {
-    k_src_prep<<<1, kPrepThreads, 0, st>>>(pos, lum, n, maxbits, err, m);
+    launch_k(k_src_prep, 1, kPrepThreads, 0, st, pos, lum, n, maxbits, err, m);
 }
 
 void launch_deposit(const double* pos, const double* lum, long long n, int N, double l,
                     const unsigned long long* maxbits, long long* grid, SlotMeta m, cudaStream_t st,
                     long long* cell_out, long long* q_out) {
     const long long blocks = n > 0 ? (n + 255) / 256 : 1;
-    k_deposit<<<(unsigned)blocks, 256, 0, st>>>(pos, lum, n, N, l, maxbits, grid, m, cell_out, q_out);
+    launch_k(k_deposit, (unsigned)blocks, 256, 0, st, pos, lum, n, N, l, maxbits, grid, m, cell_out, q_out);
 }
 
 // f_diff = (J_instant - J) / J, the difference taken and divided in FP64 and

@@ -17,9 +17,40 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <utility>
+
 namespace lc {
 
 constexpr int kThreads = 256;
+
+// Programmatic dependent launch.  Every kernel of the per-step chain starts
+// with pdl_enter(): it lets its successor launch once all of its own CTAs
+// are running, and it touches no memory before its predecessor has
+// completed and flushed.  Both instructions are no-ops for a kernel launched
+// without the programmatic-serialization attribute.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// Launch with programmatic stream serialization (plain launches when the
+// environment sets LC_PDL=0).
+bool pdl_enabled();
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                            Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 __host__ __device__ constexpr int nrp_of(int n) { return ((n / 2 + 1) + 7) / 8 * 8; }
 __host__ __device__ constexpr int cw_of(int n) { return n / 2 < 16 ? n / 2 : 16; }

@@ -112,6 +112,7 @@ __device__ __forceinline__ void bulk_load(unsigned dst, const void* src, unsigne
 
 template <int N, bool BF16>
 __global__ void __launch_bounds__(MacCfg<N, BF16>::NT) k_mac_tma(MacArgs a) {
+    pdl_enter();
     using C = MacCfg<N, BF16>;
     constexpr int NT = C::NT, CW = C::CW, PER = C::PER, TILE = C::TILE, BP = C::BP, S = C::STAGES;
     extern __shared__ unsigned char smem_raw2[];
@@ -361,6 +362,7 @@ __device__ __forceinline__ float2 bf2_to_f2(unsigned w) {
 
 template <int N, bool BF16, bool PAIR>
 __global__ void __launch_bounds__(MacWsCfg<N, BF16, PAIR>::NT, 1) k_mac_ws(MacArgs a) {
+    pdl_enter();
     using C = MacWsCfg<N, BF16, PAIR>;
     constexpr int NT = C::NT, NC = C::NC, CW = C::CW, TILE = C::TILE, BPP = C::BPP, S = C::STAGES, M = C::M;
     constexpr int UPT = C::UPT, CG = C::CG, GROWS = C::GROWS, GPLANE = C::GPLANE, P = C::P, NCH = C::NCH;
@@ -624,7 +626,7 @@ template <int N, bool BF16, bool PAIR> struct MacWsLaunch {
     }
     // every tile of the half spectrum: full ones (paired or single), then the Nyquist ones
     static void run(const MacArgs& a, cudaStream_t st) {
-        if constexpr (C::OK) k_mac_ws<N, BF16, PAIR><<<C::GRID, C::NT, C::SMEM, st>>>(a);
+        if constexpr (C::OK) launch_k(k_mac_ws<N, BF16, PAIR>, C::GRID, C::NT, C::SMEM, st, a);
     }
 };
 
@@ -635,7 +637,7 @@ template <int N, bool BF16> struct MacLaunch {
         else return cudaFuncSetAttribute(k_mac_tma<N, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     }
     static void run(const MacArgs& a, cudaStream_t st) {
-        if constexpr (C::OK) k_mac_tma<N, BF16><<<N * C::NCH, C::NT, C::SMEM, st>>>(a);
+        if constexpr (C::OK) launch_k(k_mac_tma<N, BF16>, N * C::NCH, C::NT, C::SMEM, st, a);
     }
 };
 
