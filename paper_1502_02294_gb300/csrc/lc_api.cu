@@ -87,6 +87,8 @@ static inline void count_launch(unsigned long long k = 1) { g_launches.fetch_add
 
 using namespace lc;
 
+thread_local bool lc::t_pdl_chain = false;
+
 bool lc::pdl_enabled() {
     static const bool on = [] {
         const char* f = getenv("LC_PDL");
@@ -769,6 +771,7 @@ lc_status lc_plan_prepare(lc_plan* p, int b, int e) {
 
 lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos, const double* lum) {
     if (!p) return LC_ERR_INVALID_ARG;
+    PdlChain chain(false); // the first kernel follows copies or other work: plain launch
     if (p->failed) return LC_ERR_CUDA;
     if (step < 0 || step >= p->n_steps || n_src < 0) return LC_ERR_INVALID_ARG;
     if (n_src > 0 && (!pos || !lum)) return LC_ERR_INVALID_ARG;
@@ -814,6 +817,8 @@ lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos
         // pass sets every cell back to 0 as it reads it
         Phase ph(p, LC_PHASE_DEPOSIT, n_src > 0 ? 2 : 1);
         launch_src_prep(dpos, dlum, n_src, p->d_maxbits, p->d_err, m, st);
+        // the rest of the push is a chain of this library's kernels
+        t_pdl_chain = !p->timing;
         if (n_src > 0)
             launch_deposit(dpos, dlum, n_src, p->N, p->l, p->d_maxbits, p->d_grid, m, st,
                            p->near_on ? p->d_src_cell : nullptr, p->near_on ? p->d_src_q : nullptr);
@@ -877,6 +882,7 @@ lc_status lc_instant_field(lc_plan* p, int step, float* out) { return field_impl
 
 static lc_status field_impl(lc_plan* p, int step, float* out, int instant) {
     if (!p || !out) return LC_ERR_INVALID_ARG;
+    PdlChain chain(false); // the first kernel follows whatever the stream holds: plain launch
     if (p->failed) return LC_ERR_CUDA;
     if (step < 0 || step >= p->n_steps) return LC_ERR_INVALID_ARG;
     if (step != p->last_pushed) return LC_ERR_STEP_ORDER;
@@ -899,6 +905,7 @@ static lc_status field_impl(lc_plan* p, int step, float* out, int instant) {
             Phase ph(p, LC_PHASE_MAC_X, mac_kernels(p, T.mac_variant));
             launch_mac(p, T, step, instant, T.mac_variant, p->d_slot_step, p->d_slot_S, p->d_slot_total, st);
         }
+        t_pdl_chain = !p->timing; // the inverse passes and the near field follow the MAC
         ColArgs c{};
         c.dir = 1;
         c.out_mode = COL_OUT_PLAIN;

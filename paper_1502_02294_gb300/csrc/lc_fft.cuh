@@ -33,9 +33,19 @@ __device__ __forceinline__ void pdl_enter() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
-// Launch with programmatic stream serialization (plain launches when the
-// environment sets LC_PDL=0).
+// Launch with programmatic stream serialization only inside a chain of
+// this library's kernels: a launch whose stream predecessor may be a copy,
+// a memset or another library's work must be plain, because
+// griddepcontrol.wait orders a kernel after the grids it depends on, not
+// after copies.  The caller marks a chain with PdlChain; LC_PDL=0 in the
+// environment turns programmatic launches off altogether.
 bool pdl_enabled();
+extern thread_local bool t_pdl_chain;
+struct PdlChain {
+    bool old;
+    explicit PdlChain(bool on) : old(t_pdl_chain) { t_pdl_chain = on; }
+    ~PdlChain() { t_pdl_chain = old; }
+};
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                             Args&&... args) {
@@ -48,12 +58,15 @@ inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, siz
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    cfg.numAttrs = t_pdl_chain && pdl_enabled() ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 __host__ __device__ constexpr int nrp_of(int n) { return ((n / 2 + 1) + 7) / 8 * 8; }
-__host__ __device__ constexpr int cw_of(int n) { return n / 2 < 16 ? n / 2 : 16; }
+// columns per x-pass tile: 16, or 8 from N = 384 up, so that a tile
+// (N x CW elements) stays within 4096 elements and the shell MAC's pipeline
+// fits in shared memory at every grid size
+__host__ __device__ constexpr int cw_of(int n) { return n >= 384 ? 8 : (n / 2 < 16 ? n / 2 : 16); }
 // pairs of real rows per CTA in the z (row) passes
 __host__ __device__ constexpr int row_pairs_of(int n) {
     return n <= 8 ? 32 : n <= 16 ? 32 : n <= 32 ? 32 : n <= 64 ? 32 : n <= 128 ? 16 : n <= 256 ? 8 : 4;

@@ -341,10 +341,11 @@ template <int N, bool BF16, bool PAIR> struct MacWsCfg {
     static constexpr size_t OFF_BAR = (OFF_BLK + (size_t)MAXBLK * 12 + 15) / 16 * 16;
     static constexpr int NBAR = 2 * 8 + 4; // full[8], empty[8], gfull[2], gempty[2]
     static constexpr size_t SMEM = OFF_BAR + NBAR * 8 + 128;
-    // built where the tiles are 16 columns wide and the ring holds at least
-    // 2 stages (3 when a stage carries two tiles)
-    static constexpr bool OK = N >= 32 && N <= 256 && CW == 16 && STAGES >= (PAIR ? 3 : 2) && NC % 32 == 0 &&
-                               UNITS % UPT == 0 && SMEM <= BUDGET;
+    // built where a tile has 4096 elements at most (16 columns up to N = 256,
+    // 8 above) and the ring holds at least 2 stages (3 when a stage carries
+    // two tiles)
+    static constexpr bool OK = N >= 32 && N <= 512 && CW % 4 == 0 && TILE <= 4096 &&
+                               STAGES >= (PAIR ? 3 : 2) && NC % 32 == 0 && UNITS % UPT == 0 && SMEM <= BUDGET;
 };
 
 __device__ __forceinline__ void cp_async16(unsigned dst, const void* src) {

@@ -91,3 +91,38 @@ def test_choices_reported_and_persisted(monkeypatch, tmp_path):
     assert mine and set(mine.values()) <= {"gather", "bulk", "ws", "ws2"}
     lines = cache.read_text().split()
     assert any("/N96/bf16/" in t for t in lines)
+
+
+@pytest.mark.parametrize("history", [synth.HISTORY_FP32, synth.HISTORY_BF16])
+def test_large_grid_8_column_tiles_against_oracle(monkeypatch, history):
+    # 384^3 (8-column x-pass tiles): every MAC kernel built at this size gives
+    # the same field, which matches the oracle on sampled cells
+    w = synth.small(n=384, box=300.0, n_steps=8, n_src=60, subsamples=2, clustered=True, seed=384,
+                    z_start=16.0, z_end=15.0, history=history)
+    res = {}
+    for v in ("gather", "ws", "ws2"):
+        monkeypatch.setenv("LC_MAC_VARIANT", v)
+        res[v] = _fields(w, range(8), {7})[7]
+    for v in ("ws", "ws2"):
+        assert np.array_equal(res["gather"], res[v]), v
+    P = oracle.Problem.from_workload(w)
+    assert P.active_shells(7) >= 4
+    pos, lum = w.cat.active(7)
+    dense = np.floor(pos[np.argmax(lum)] / (w.box / w.n) + 0.5).astype(int) % w.n
+    cells = synth.sample_cells(4242, w.n, 2000, dense_line_through=dense)
+    ref = oracle.field_for(P, w.cat, 7, cells=cells)
+    got = res["gather"].reshape(-1)[cells].astype(np.float64)
+    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert rel <= (FP32_L2 if history == synth.HISTORY_FP32 else BF16_L2), rel
+
+
+def test_512_bf16_mac_kernels_agree(monkeypatch):
+    # 512^3 BF16: the paired warp-specialised kernel equals the gather pass bit for bit
+    w = synth.small(n=512, box=400.0, n_steps=8, n_src=40, subsamples=2, clustered=True, seed=512,
+                    z_start=16.0, z_end=15.0, history=synth.HISTORY_BF16)
+    res = {}
+    for v in ("gather", "ws2"):
+        monkeypatch.setenv("LC_MAC_VARIANT", v)
+        res[v] = _fields(w, range(8), {7})[7]
+    assert np.array_equal(res["gather"], res["ws2"])
+    assert np.isfinite(res["ws2"]).all() and res["ws2"].max() > 0

@@ -111,7 +111,7 @@ def test_fft_against_brute_force_dft_8():
     assert np.abs(back - x).max() <= 1e-5 * np.abs(x).max()
 
 
-@pytest.mark.parametrize("n", [16, 32, 64, 96, 128, 192, 256])
+@pytest.mark.parametrize("n", [16, 32, 64, 96, 128, 192, 256, 384, 512])
 def test_fft_sizes_parseval_and_roundtrip(n):
     rng = np.random.default_rng(n)
     x = rng.standard_normal((n, n, n)).astype(np.float32)
