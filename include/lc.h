@@ -69,23 +69,40 @@ typedef struct {
 enum { LC_STEPS_EXPLICIT = 0, LC_STEPS_EQUAL_TIME = 1, LC_STEPS_EQUAL_TAU = 2 };
 enum { LC_HISTORY_FP32 = 0, LC_HISTORY_BF16 = 1 };
 
+/* The radial kernel: the dilution factor F(|x - x'|, tau, tau') of the
+ * generic retarded Green's function (Eq. 7), which the method needs only as
+ * a function of distance (with tau' fixed by the light cone).
+ *   LC_KERNEL_LW:  the Lyman-Werner kernel, Eqs. 14-17:
+ *                  g(r) = (1+z)^3 f_mod(r) / ((4 pi)^2 (1+z_s) r^2), f_mod of
+ *                  Eq. 15 with alpha(z_s) of Eq. 16; horizon r / alpha = 97.39.
+ *   LC_KERNEL_EXP: the same dilution and redshift factors with a
+ *                  distance-only attenuation in place of f_mod:
+ *                  g(r) = (1+z)^3 exp(-r / lambda) / ((4 pi)^2 (1+z_s) r^2)
+ *                  for r < r_max, 0 beyond; r_max is this kernel's horizon
+ *                  (lambda = kernel_length, r_max = kernel_rmax, comoving Mpc). */
+enum { LC_KERNEL_LW = 0, LC_KERNEL_EXP = 1 };
+
 /* How time is sliced (step 1 of Section 2.2) and how the field is evaluated.
  * Step s spans [tau_s, tau_{s+1}] and is observed at its end, tau_{s+1}; the
  * sources pushed at step s stand for the source term frozen over that step
  * (Eq. 9).  Slice n seen from step s occupies the half-open shell
  * [tau_{s+1} - tau_{n+1}, tau_{s+1} - tau_n) and counts while its inner radius
- * is inside the LW horizon r_h, where r / alpha(z_s(r)) = 97.39 (Eqs. 15-16). */
+ * is inside the kernel's horizon r_h (for the LW kernel the radius where
+ * r / alpha(z_s(r)) = 97.39, Eqs. 15-16). */
 typedef struct {
     int n_steps;           /* number of steps (>= 1) */
     int spacing;           /* LC_STEPS_* */
     const double* z_edges; /* LC_STEPS_EXPLICIT: n_steps + 1 decreasing redshifts (copied) */
     double z_start;        /* LC_STEPS_EQUAL_TIME: first edge (highest z) */
     double z_end;          /* EQUAL_TIME and EQUAL_TAU: last edge */
-    int n_shell;           /* LC_STEPS_EQUAL_TAU: step width r_h(z_end) / n_shell in conformal time */
+    int n_shell;           /* LC_STEPS_EQUAL_TAU: step width r_h(z_end) / n_shell in conformal time (r_h: the kernel's horizon) */
     int subsamples;        /* s: sub-cell samples per axis in G_n (even, 2..16; 0 -> 4) */
     int history;           /* LC_HISTORY_FP32, or LC_HISTORY_BF16 (spectra stored / DC, scale kept in FP32) */
     int normalise;         /* 1: scale each G_n so that l^3 sum G_n = int 4 pi r^2 g dr over its shell */
     double out_unit;       /* U: multiplies J (0 -> 1) */
+    int kernel;            /* LC_KERNEL_LW (0, default) or LC_KERNEL_EXP */
+    double kernel_length;  /* LC_KERNEL_EXP: attenuation length lambda > 0, comoving Mpc */
+    double kernel_rmax;    /* LC_KERNEL_EXP: cut-off radius r_max > 0, comoving Mpc */
 } lc_steps;
 
 /* Create a plan for an N^3 periodic grid of side box_mpc.
@@ -138,6 +155,19 @@ lc_status lc_plan_check(lc_plan* plan);
 lc_status lc_plan_set_stream(lc_plan* plan, void* cuda_stream);
 lc_status lc_plan_destroy(lc_plan* plan);
 const char* lc_status_string(lc_status status);
+
+/* Green's-function table budget.  The paper precomputes one Ghat table per
+ * observing step (the paragraph after the algorithm of Section 2.2); over a
+ * long run the tables of all steps can exceed device memory.  With a budget
+ * of `bytes` (0, the default: no limit), building the table of a step first
+ * frees tables of other steps, earlier ones oldest first, then later ones
+ * latest first, until the total fits; a freed table is rebuilt, identically,
+ * if its step is evaluated again.  Tables captured in a graph are never
+ * freed (step graphs: until the graph is destroyed; batch graphs: for the
+ * life of the plan), so the budget is soft.  lc_plan_table_bytes: the bytes
+ * the plan's tables hold now. */
+lc_status lc_plan_set_table_budget(lc_plan* plan, size_t bytes);
+size_t lc_plan_table_bytes(const lc_plan* plan);
 
 /* Device bytes held by the plan (ring + tables + buffers), for HBM-budget admission. */
 size_t lc_plan_device_bytes(const lc_plan* plan);

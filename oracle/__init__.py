@@ -42,7 +42,8 @@ class _Problem(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("box", ctypes.c_double), ("om", ctypes.c_double),
                 ("h", ctypes.c_double), ("n_steps", ctypes.c_int),
                 ("z_edges", ctypes.POINTER(ctypes.c_double)), ("subsamples", ctypes.c_int),
-                ("normalise", ctypes.c_int), ("out_unit", ctypes.c_double)]
+                ("normalise", ctypes.c_int), ("out_unit", ctypes.c_double),
+                ("kernel", ctypes.c_int), ("k_length", ctypes.c_double), ("k_rmax", ctypes.c_double)]
 
 
 def lib():
@@ -61,6 +62,9 @@ def lib():
             ("lco_fmod", d, [d, d]), ("lco_g", d, [d, d, d, d]), ("lco_horizon", d, [d, d, d]),
             ("lco_shell_integral", d, [d, d, d, d, d]),
             ("lco_step_edges", i, [d, d, i, i, d, d, i, dp, dp]),
+            ("lco_fk", d, [i, d, d, d, d, d, d]), ("lco_gk", d, [i, d, d, d, d, d, d]),
+            ("lco_horizonk", d, [i, d, d, d, d, d]), ("lco_shell_integralk", d, [i, d, d, d, d, d, d, d]),
+            ("lco_step_edgesk", i, [i, d, d, d, d, i, i, d, d, i, dp, dp]),
             ("lco_shells", i, [pp, i, dp, dp, dp]), ("lco_active_shells", i, [pp, i]),
             ("lco_rgf_octant", i, [pp, i, i, dp, dp, dp]),
             ("lco_rgf_direct", d, [pp, i, i, i, i, i]),
@@ -126,11 +130,29 @@ def shell_integral(om, h, z_obs, r_lo, r_hi):
     return lib().lco_shell_integral(om, h, z_obs, r_lo, r_hi)
 
 
-def step_edges(om, h, spec) -> np.ndarray:
+# radial kernels other than the LW one: kernel = (kind, length, rmax), kind 1 =
+# exp(-r / length) attenuation with a cut-off at rmax (see lco_fk)
+def _k(kernel):
+    return (0, 0.0, 0.0) if kernel is None else (int(kernel[0]), float(kernel[1]), float(kernel[2]))
+
+
+def g_kernel(kernel, om, h, z_obs, r):
+    return lib().lco_gk(*_k(kernel), om, h, z_obs, r)
+
+
+def horizon_kernel(kernel, om, h, z_obs):
+    return lib().lco_horizonk(*_k(kernel), om, h, z_obs)
+
+
+def shell_integral_kernel(kernel, om, h, z_obs, r_lo, r_hi):
+    return lib().lco_shell_integralk(*_k(kernel), om, h, z_obs, r_lo, r_hi)
+
+
+def step_edges(om, h, spec, kernel=None) -> np.ndarray:
     out = np.zeros(spec.n_steps + 1)
     zx = np.ascontiguousarray(np.asarray(spec.z_edges if spec.z_edges is not None else [0.0], dtype=np.float64))
-    rc = lib().lco_step_edges(om, h, spec.kind, spec.n_steps, spec.z_start, spec.z_end, spec.n_shell,
-                              _dp(zx), _dp(out))
+    rc = lib().lco_step_edgesk(*_k(kernel), om, h, spec.kind, spec.n_steps, spec.z_start, spec.z_end, spec.n_shell,
+                               _dp(zx), _dp(out))
     if rc:
         raise ValueError("bad step specification")
     return out
@@ -140,18 +162,19 @@ def step_edges(om, h, spec) -> np.ndarray:
 class Problem:
     """A workload as the oracle sees it (edges derived here, from the spec)."""
 
-    def __init__(self, n, box, om, h, steps, subsamples=4, normalise=1, out_unit=1.0):
+    def __init__(self, n, box, om, h, steps, subsamples=4, normalise=1, out_unit=1.0, kernel=None):
         self.n, self.box, self.om, self.h = int(n), float(box), float(om), float(h)
         self.steps = steps
-        self.z_edges = step_edges(om, h, steps)
+        self.kernel = _k(kernel)
+        self.z_edges = step_edges(om, h, steps, kernel)
         self.subsamples, self.normalise, self.out_unit = int(subsamples), int(normalise), float(out_unit)
         self._c = _Problem(self.n, self.box, self.om, self.h, int(steps.n_steps), _dp(self.z_edges),
-                           self.subsamples, self.normalise, self.out_unit)
+                           self.subsamples, self.normalise, self.out_unit, *self.kernel)
 
     @classmethod
     def from_workload(cls, w, **kw):
         args = dict(n=w.n, box=w.box, om=w.omega_m, h=w.h, steps=w.steps, subsamples=w.subsamples,
-                    normalise=w.normalise, out_unit=w.out_unit)
+                    normalise=w.normalise, out_unit=w.out_unit, kernel=getattr(w, "kernel", None))
         args.update(kw)
         return cls(**args)
 

@@ -18,7 +18,8 @@
  * is used: the oracle is the direct sum of Eq. 11.
  *
  * G_n(d) for a cell displacement d is the average over s^3 sub-cell samples
- * of the LW kernel (Eq. 17) summed over all periodic images of a unit source
+ * of the radial kernel (the LW one of Eq. 17, or the exponentially attenuated
+ * one of lco_fk) summed over all periodic images of a unit source
  * that fall in the slice's spherical shell (Eq. 10 and step 2 of Section
  * 2.2), then scaled so that l^3 * sum_d G_n(d) equals the analytic shell
  * integral of 4 pi r^2 g(r).  The readings of the paper that this needs
@@ -162,15 +163,36 @@ double lco_fmod(double r, double alpha) {
     return 1.7 * exp(-pow(r / (116.29 * alpha), 0.68)) - 0.7;
 }
 
-/* Eq. 17 with Eq. 14: field per unit source luminosity at comoving distance r
- * (light-cone: z_s from chi(z_obs, z_s) = r).  Units: luminosity / Mpc^2 / sr. */
-double lco_g(double om, double h, double z_obs, double r) {
+/* Radial kernels.  The generic RGF (Eq. 7) carries a dilution factor that
+ * this method needs only as a function of distance.  Kernel kind kk:
+ *   0: Lyman-Werner, Eq. 14 / Eq. 17 with f_mod of Eq. 15 at alpha(z_s);
+ *   1: the same (1+z)^3 / ((4 pi)^2 (1+z_s) r^2) dilution with f_mod replaced
+ *      by exp(-r / kl) for r < kr and 0 beyond (kl: attenuation length,
+ *      kr: cut-off, comoving Mpc).
+ * lco_fk is the factor that multiplies the dilution. */
+double lco_fk(int kk, double kl, double kr, double om, double h, double zs, double r) {
+    if (kk == 1) return r < kr ? exp(-r / kl) : 0.0;
+    return lco_fmod(r, lco_alpha(om, h, zs));
+}
+
+/* field per unit source luminosity at comoving distance r (light cone: z_s
+ * from chi(z_obs, z_s) = r).  Units: luminosity / Mpc^2 / sr. */
+double lco_gk(int kk, double kl, double kr, double om, double h, double z_obs, double r) {
     double zs = lco_zs_of_r(om, h, z_obs, r);
-    double a = lco_alpha(om, h, zs);
-    double fm = lco_fmod(r, a);
+    double fm = lco_fk(kk, kl, kr, om, h, zs, r);
     if (fm == 0.0) return 0.0;
     double zo = 1.0 + z_obs;
     return zo * zo * zo * fm / ((4.0 * OR_PI) * (4.0 * OR_PI) * (1.0 + zs) * r * r);
+}
+
+/* Eq. 17 with Eq. 14: the LW kernel. */
+double lco_g(double om, double h, double z_obs, double r) { return lco_gk(0, 0.0, 0.0, om, h, z_obs, r); }
+
+double lco_horizon(double om, double h, double z_obs);
+/* the kernel's horizon: LW below; the cut-off for kind 1 */
+double lco_horizonk(int kk, double kl, double kr, double om, double h, double z_obs) {
+    (void)kl;
+    return kk == 1 ? kr : lco_horizon(om, h, z_obs);
 }
 
 /* LW horizon r_h: the radius where r / alpha(z_s(r)) = 97.39 (Eq. 15, with
@@ -188,28 +210,30 @@ double lco_horizon(double om, double h, double z_obs) {
 }
 
 /* integrand of the shell integral: 4 pi r^2 g(r) */
-static double shell_integrand(double om, double h, double z_obs, double r) {
+static double shell_integrand(int kk, double kl, double kr, double om, double h, double z_obs, double r) {
     double zs = lco_zs_of_r(om, h, z_obs, r);
-    double fm = lco_fmod(r, lco_alpha(om, h, zs));
+    double fm = lco_fk(kk, kl, kr, om, h, zs, r);
     double zo = 1.0 + z_obs;
     return zo * zo * zo * fm / (4.0 * OR_PI * (1.0 + zs));
 }
 
-static double gl_panel(double om, double h, double z_obs, double a, double b) {
+static double gl_panel(int kk, double kl, double kr, double om, double h, double z_obs, double a, double b) {
     double mid = 0.5 * (a + b), half = 0.5 * (b - a), s = 0.0;
-    for (int i = 0; i < OR_GL_N; ++i) s += gl_w[i] * shell_integrand(om, h, z_obs, mid + half * gl_x[i]);
+    for (int i = 0; i < OR_GL_N; ++i)
+        s += gl_w[i] * shell_integrand(kk, kl, kr, om, h, z_obs, mid + half * gl_x[i]);
     return half * s;
 }
 
 /* I = int_{r_lo}^{min(r_hi, r_h)} 4 pi r^2 g(r) dr.  Panels are graded
  * geometrically towards r = 0 because f_mod carries r^0.68. */
-double lco_shell_integral(double om, double h, double z_obs, double r_lo, double r_hi) {
-    double rh = lco_horizon(om, h, z_obs);
+double lco_shell_integralk(int kk, double kl, double kr, double om, double h, double z_obs, double r_lo,
+                           double r_hi) {
+    double rh = lco_horizonk(kk, kl, kr, om, h, z_obs);
     double b = r_hi < rh ? r_hi : rh;
     if (!(r_lo < b)) return 0.0;
     double sum = 0.0;
     if (r_lo <= 0.0) {
-        for (int k = 0; k < 60; ++k) sum += gl_panel(om, h, z_obs, ldexp(b, -(k + 1)), ldexp(b, -k));
+        for (int k = 0; k < 60; ++k) sum += gl_panel(kk, kl, kr, om, h, z_obs, ldexp(b, -(k + 1)), ldexp(b, -k));
         return sum;
     }
     double x = r_lo;
@@ -217,10 +241,14 @@ double lco_shell_integral(double om, double h, double z_obs, double r_lo, double
         double w = 0.5 * x;
         if (w > 1.0) w = 1.0;
         if (x + w > b) w = b - x;
-        sum += gl_panel(om, h, z_obs, x, x + w);
+        sum += gl_panel(kk, kl, kr, om, h, z_obs, x, x + w);
         x += w;
     }
     return sum;
+}
+
+double lco_shell_integral(double om, double h, double z_obs, double r_lo, double r_hi) {
+    return lco_shell_integralk(0, 0.0, 0.0, om, h, z_obs, r_lo, r_hi);
 }
 
 /* ------------------------------------------------------------------ */
@@ -228,8 +256,8 @@ double lco_shell_integral(double om, double h, double z_obs, double r_lo, double
 /* ------------------------------------------------------------------ */
 /* kind 0: explicit copy; 1: equal cosmic time z_start -> z_end; 2: equal
  * conformal time ending at z_end with width r_h(z_end) / n_shell. */
-int lco_step_edges(double om, double h, int kind, int n_steps, double z_start, double z_end,
-                   int n_shell, const double* z_explicit, double* out) {
+int lco_step_edgesk(int kk, double kl, double kr, double om, double h, int kind, int n_steps, double z_start,
+                    double z_end, int n_shell, const double* z_explicit, double* out) {
     if (n_steps < 1) return 1;
     if (kind == 0) {
         for (int k = 0; k <= n_steps; ++k) out[k] = z_explicit[k];
@@ -244,12 +272,17 @@ int lco_step_edges(double om, double h, int kind, int n_steps, double z_start, d
     }
     if (kind == 2) {
         if (n_shell < 1) return 1;
-        double dtau = lco_horizon(om, h, z_end) / n_shell;
+        double dtau = lco_horizonk(kk, kl, kr, om, h, z_end) / n_shell;
         for (int k = 0; k < n_steps; ++k) out[k] = lco_zs_of_r(om, h, z_end, (n_steps - k) * dtau);
         out[n_steps] = z_end;
         return 0;
     }
     return 1;
+}
+
+int lco_step_edges(double om, double h, int kind, int n_steps, double z_start, double z_end, int n_shell,
+                   const double* z_explicit, double* out) {
+    return lco_step_edgesk(0, 0.0, 0.0, om, h, kind, n_steps, z_start, z_end, n_shell, z_explicit, out);
 }
 
 /* ------------------------------------------------------------------ */
@@ -264,6 +297,8 @@ typedef struct {
     int subsamples;      /* s, even */
     int normalise;       /* 1: scale G_n so that l^3 sum G_n = I_n */
     double out_unit;     /* U */
+    int kernel;          /* radial kernel kind (see lco_fk) */
+    double k_length, k_rmax;
 } lco_problem;
 
 /* Active slices of observation step s.  Step s observes at tau_{s+1} (the end
@@ -274,7 +309,7 @@ typedef struct {
 int lco_shells(const lco_problem* P, int s, double* r_lo, double* r_hi, double* r_h) {
     if (s < 0 || s >= P->n_steps) return -1;
     double zo = P->z_edges[s + 1];
-    double rh = lco_horizon(P->om, P->h, zo);
+    double rh = lco_horizonk(P->kernel, P->k_length, P->k_rmax, P->om, P->h, zo);
     if (r_h) *r_h = rh;
     int A = 0;
     for (int j = 0; j <= s; ++j) {
@@ -345,10 +380,11 @@ static int build_octants(const lco_problem* P, int s, octant_set* out) {
 #pragma omp parallel for schedule(dynamic, 256)
     for (int64_t t = 0; t < ntab; ++t) {
         double r = delta * sqrt((double)(8 * t + 3));
-        tab[t] = lco_g(P->om, P->h, zo, r);
+        tab[t] = lco_gk(P->kernel, P->k_length, P->k_rmax, P->om, P->h, zo, r);
     }
 #pragma omp parallel for schedule(dynamic, 1)
-    for (int j = 0; j < A; ++j) out->I[j] = lco_shell_integral(P->om, P->h, zo, rlo[j], rhi[j]);
+    for (int j = 0; j < A; ++j)
+        out->I[j] = lco_shell_integralk(P->kernel, P->k_length, P->k_rmax, P->om, P->h, zo, rlo[j], rhi[j]);
 
     const int U = (int)ceil(rh / P->box) + 1;
     const double halfdiag = 0.5 * sqrt(3.0) * l;
@@ -471,7 +507,8 @@ double lco_rgf_direct(const lco_problem* P, int s, int j, int dx, int dy, int dz
                                 int64_t mz = 2LL * S * (dz + (int64_t)w * N) + 2 * sc + 1 - S;
                                 int64_t R = mx * mx + my * my + mz * mz;
                                 if (R < lo || R >= hi || R > Rh) continue;
-                                res += lco_g(P->om, P->h, zo, delta * sqrt((double)R));
+                                res += lco_gk(P->kernel, P->k_length, P->k_rmax, P->om, P->h, zo,
+                                              delta * sqrt((double)R));
                             }
         res /= (double)S * S * S;
     }
@@ -617,7 +654,8 @@ int lco_field(const lco_problem* P, int s, int n_src_grids, const double* const*
 int lco_shell_table(const lco_problem* P, int s, double* r_lo, double* r_hi, double* I) {
     int A = lco_shells(P, s, r_lo, r_hi, NULL);
     double zo = P->z_edges[s + 1];
-    for (int j = 0; j < A; ++j) I[j] = lco_shell_integral(P->om, P->h, zo, r_lo[j], r_hi[j]);
+    for (int j = 0; j < A; ++j)
+        I[j] = lco_shell_integralk(P->kernel, P->k_length, P->k_rmax, P->om, P->h, zo, r_lo[j], r_hi[j]);
     return A;
 }
 

@@ -25,6 +25,7 @@ LC_OK, LC_ERR_INVALID_ARG, LC_ERR_UNSUPPORTED_SIZE, LC_ERR_STEP_ORDER = 0, 1, 2,
 LC_ERR_OOM, LC_ERR_CUDA, LC_ERR_TIMEOUT, LC_ERR_DEVICE_CHECK = 4, 5, 6, 7
 STEPS_EXPLICIT, STEPS_EQUAL_TIME, STEPS_EQUAL_TAU = 0, 1, 2
 HISTORY_FP32, HISTORY_BF16 = 0, 1
+KERNEL_LW, KERNEL_EXP = 0, 1  # radial kernels (lc_steps.kernel)
 SUPPORTED_N = (8, 16, 32, 64, 96, 128, 192, 256, 384, 512)
 PHASES = ("deposit", "r2c_z", "fwd_y", "fwd_x_ring", "mac_x", "inv_y", "c2r_z", "near")
 
@@ -60,7 +61,8 @@ class _Steps(ctypes.Structure):
     _fields_ = [("n_steps", ctypes.c_int), ("spacing", ctypes.c_int),
                 ("z_edges", ctypes.POINTER(ctypes.c_double)), ("z_start", ctypes.c_double),
                 ("z_end", ctypes.c_double), ("n_shell", ctypes.c_int), ("subsamples", ctypes.c_int),
-                ("history", ctypes.c_int), ("normalise", ctypes.c_int), ("out_unit", ctypes.c_double)]
+                ("history", ctypes.c_int), ("normalise", ctypes.c_int), ("out_unit", ctypes.c_double),
+                ("kernel", ctypes.c_int), ("kernel_length", ctypes.c_double), ("kernel_rmax", ctypes.c_double)]
 
 
 class _Info(ctypes.Structure):
@@ -107,6 +109,8 @@ SIGNATURES = [
     ("lc_fft_r2c_static", _I, [_I, _VP, _VP, _VP]),
     ("lc_autotune_report", _I, [ctypes.c_char_p, _I]),
     ("lc_fdiff_map", _I, [_I64, _VP, _VP, _VP, _VP]),
+    ("lc_plan_set_table_budget", _I, [_P, ctypes.c_size_t]),
+    ("lc_plan_table_bytes", ctypes.c_size_t, [_P]),
     ("lc_plan_checkpoint_bytes", ctypes.c_size_t, [_P]),
     ("lc_plan_save", _I, [_P, _VP, ctypes.c_size_t]),
     ("lc_plan_load", _I, [_P, _VP, ctypes.c_size_t]),
@@ -170,7 +174,7 @@ def _ptr(x, dtype) -> Tuple[int, object]:
     return a.ctypes.data, a
 
 
-def _steps_struct(spec, subsamples=4, history=HISTORY_FP32, normalise=1, out_unit=1.0):
+def _steps_struct(spec, subsamples=4, history=HISTORY_FP32, normalise=1, out_unit=1.0, kernel=None):
     z = None
     zp = ctypes.POINTER(ctypes.c_double)()
     if getattr(spec, "z_edges", None) is not None:
@@ -178,8 +182,16 @@ def _steps_struct(spec, subsamples=4, history=HISTORY_FP32, normalise=1, out_uni
         zp = z.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     st = _Steps(int(spec.n_steps), int(spec.kind), zp, float(getattr(spec, "z_start", 0.0)),
                 float(getattr(spec, "z_end", 0.0)), int(getattr(spec, "n_shell", 0)), int(subsamples), int(history),
-                int(normalise), float(out_unit))
+                int(normalise), float(out_unit), *_kernel_fields(kernel))
     return st, z
+
+
+def _kernel_fields(kernel):
+    """(kind, length, rmax) from None (the LW kernel) or a (kind, length, rmax) tuple."""
+    if kernel is None:
+        return KERNEL_LW, 0.0, 0.0
+    kind, length, rmax = kernel
+    return int(kind), float(length), float(rmax)
 
 
 class Plan:
@@ -191,11 +203,12 @@ class Plan:
     """
 
     def __init__(self, n: int, box: float, omega_m: float, h: float, steps, subsamples: int = 4,
-                 history: int = HISTORY_FP32, normalise: int = 1, out_unit: float = 1.0, stream=None):
+                 history: int = HISTORY_FP32, normalise: int = 1, out_unit: float = 1.0, stream=None,
+                 kernel=None):
         L = _lib()
         self.n, self.box = int(n), float(box)
         self._cos = _Cosmology(float(omega_m), float(h))
-        self._steps, self._zkeep = _steps_struct(steps, subsamples, history, normalise, out_unit)
+        self._steps, self._zkeep = _steps_struct(steps, subsamples, history, normalise, out_unit, kernel)
         self._stream = _stream_ptr(stream)
         h_ = ctypes.c_void_p()
         _check(L.lc_plan_create(self.n, self.box, ctypes.byref(self._cos), ctypes.byref(self._steps),
@@ -212,7 +225,8 @@ class Plan:
     @classmethod
     def from_workload(cls, w, stream=None, **kw):
         args = dict(n=w.n, box=w.box, omega_m=w.omega_m, h=w.h, steps=w.steps, subsamples=w.subsamples,
-                    history=w.history, normalise=w.normalise, out_unit=w.out_unit, stream=stream)
+                    history=w.history, normalise=w.normalise, out_unit=w.out_unit, stream=stream,
+                    kernel=getattr(w, "kernel", None))
         args.update(kw)
         return cls(**args)
 
@@ -310,6 +324,14 @@ class Plan:
         _check(_lib().lc_plan_timing(self._h, ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                      cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), int(reset)), "lc_plan_timing")
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(PHASES)}
+
+    def set_table_budget(self, nbytes: int):
+        """Keep the Green's-function tables under nbytes (0: no limit)."""
+        _check(_lib().lc_plan_set_table_budget(self._h, int(nbytes)), "lc_plan_set_table_budget")
+
+    @property
+    def table_bytes(self) -> int:
+        return int(_lib().lc_plan_table_bytes(self._h))
 
     def checkpoint_bytes(self) -> int:
         return int(_lib().lc_plan_checkpoint_bytes(self._h))
@@ -427,8 +449,8 @@ def batch_step(plans, steps, sources, outs):
     _check(_lib().lc_batch_step(hp, n, st, ns, pp, lp, op), "lc_batch_step")
 
 
-def estimate_bytes(n, steps, omega_m, h, history=HISTORY_FP32) -> Tuple[int, int]:
-    st, keep = _steps_struct(steps, 4, history)
+def estimate_bytes(n, steps, omega_m, h, history=HISTORY_FP32, kernel=None) -> Tuple[int, int]:
+    st, keep = _steps_struct(steps, 4, history, kernel=kernel)
     c = _Cosmology(omega_m, h)
     b = ctypes.c_size_t()
     t = ctypes.c_size_t()

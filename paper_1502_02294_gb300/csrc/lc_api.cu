@@ -87,16 +87,6 @@ static inline void count_launch(unsigned long long k = 1) { g_launches.fetch_add
 
 using namespace lc;
 
-thread_local bool lc::t_pdl_chain = false;
-
-bool lc::pdl_enabled() {
-    static const bool on = [] {
-        const char* f = getenv("LC_PDL");
-        return !(f && f[0] == '0');
-    }();
-    return on;
-}
-
 // ---------------------------------------------------------------- autotuner
 // The shell MAC has four variants: a register-gather pass (MAC_GATHER), a
 // bulk-copy pipelined kernel for the full tiles (MAC_BULK), and its
@@ -147,6 +137,7 @@ struct lc_plan {
     int N = 0;
     double L = 0, l = 0;
     Cosmo cosmo{0, 0};
+    Kernel kern;
     int n_steps = 0, S = 4, history = 0, normalise = 1;
     double U = 1.0;
     std::vector<double> z;
@@ -181,6 +172,10 @@ struct lc_plan {
         int A = -1;             // -1: not built
     };
     std::vector<Table> tables;
+    // table budget: 0 = keep every table; else tables of other observing
+    // steps are freed (oldest first) to keep the total under it
+    size_t table_budget = 0, table_bytes = 0;
+    std::vector<int> table_pins; // per step: > 0 while a graph holds its table
     // builder scratch
     double* d_gw = nullptr;
     long long gw_cap = 0;
@@ -363,7 +358,19 @@ bool valid_steps(const lc_steps* st) {
     if (st->spacing == LC_STEPS_EQUAL_TIME && !(st->z_start > st->z_end && st->z_end >= 0.0)) return false;
     if (st->spacing == LC_STEPS_EQUAL_TAU && (st->n_shell < 1 || !(st->z_end >= 0.0))) return false;
     if (st->spacing == LC_STEPS_EXPLICIT && !st->z_edges) return false;
+    if (st->kernel != LC_KERNEL_LW && st->kernel != LC_KERNEL_EXP) return false;
+    if (st->kernel == LC_KERNEL_EXP && !(st->kernel_length > 0.0 && isfinite(st->kernel_length) &&
+                                         st->kernel_rmax > 0.0 && isfinite(st->kernel_rmax)))
+        return false;
     return st->spacing >= 0 && st->spacing <= 2;
+}
+
+Kernel kernel_of(const lc_steps* st) {
+    Kernel k;
+    k.kind = st->kernel;
+    k.length = st->kernel_length;
+    k.rmax = st->kernel_rmax;
+    return k;
 }
 
 bool valid_cosmo(const lc_cosmology* c) {
@@ -495,12 +502,46 @@ int choose_mac_variant(lc_plan* p, const lc_plan::Table& T, int s) {
     return best;
 }
 
+size_t table_size(const lc_plan* p, int A) {
+    if (A <= 0) return 0;
+    return sizeof(float) * (size_t)p->W * ((A + 7) / 8 * 8) + sizeof(double) * A +
+           (p->near_on ? sizeof(double) * (kNearR + 1) * (kNearR + 2) * (kNearR + 3) / 6 : 0);
+}
+
+void free_table(lc_plan* p, int s) {
+    lc_plan::Table& T = p->tables[s];
+    cudaFree(T.ghat);
+    cudaFree(T.g0);
+    cudaFree(T.gnear);
+    const size_t b = table_size(p, T.A);
+    p->table_bytes -= b;
+    p->bytes -= b;
+    T = lc_plan::Table{};
+}
+
+// Make room for a table of `need` bytes for step s under the table budget:
+// free unpinned tables of earlier observing steps (oldest first), then of
+// later ones (latest first).  The budget is soft: pinned tables stay.
+void evict_tables(lc_plan* p, int s, size_t need) {
+    if (!p->table_budget) return;
+    for (int pass = 0; pass < 2 && p->table_bytes + need > p->table_budget; ++pass) {
+        if (pass == 0) {
+            for (int v = 0; v < s && p->table_bytes + need > p->table_budget; ++v)
+                if (p->tables[v].A > 0 && !p->table_pins[v]) free_table(p, v);
+        } else {
+            for (int v = p->n_steps - 1; v > s && p->table_bytes + need > p->table_budget; --v)
+                if (p->tables[v].A > 0 && !p->table_pins[v]) free_table(p, v);
+        }
+    }
+}
+
 // Build the Ghat table of observing step s (steps 2-3 of Section 2.2).
 lc_status build_table(lc_plan* p, int s) {
     lc_plan::Table& T = p->tables[s];
     if (T.A >= 0) return LC_OK;
-    StepGeom g = step_geometry(p->cosmo, p->z, s, p->l, p->S, true);
+    StepGeom g = step_geometry(p->cosmo, p->kern, p->z, s, p->l, p->S, true);
     const int A = g.A;
+    evict_tables(p, s, table_size(p, A));
     cudaError_t e = cudaSuccess;
     if (A == 0) {
         T.A = 0;
@@ -509,7 +550,7 @@ lc_status build_table(lc_plan* p, int s) {
     if (g.ntab > (1LL << 28)) return LC_ERR_UNSUPPORTED_SIZE;
     // host table of g(R), with the s^-3 sample weight folded in
     std::vector<double> gt((size_t)g.ntab);
-    g_table(p->cosmo, p->z[s + 1], p->l / (2.0 * p->S), g.ntab, gt.data());
+    g_table(p->cosmo, p->kern, p->z[s + 1], p->l / (2.0 * p->S), g.ntab, gt.data());
     const double inv_s3 = 1.0 / ((double)p->S * p->S * p->S);
     for (auto& v : gt) v *= inv_s3;
     // scratch
@@ -543,6 +584,7 @@ lc_status build_table(lc_plan* p, int s) {
         T.g0 = nullptr;
         return LC_ERR_OOM;
     }
+    p->table_bytes += table_size(p, A);
     cudaStream_t st = p->stream;
     e = cudaMemcpyAsync(p->d_gtab, gt.data(), sizeof(double) * g.ntab, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_bnd, g.bnd.data(), sizeof(long long) * (A + 1), cudaMemcpyHostToDevice, st);
@@ -652,12 +694,13 @@ lc_status lc_plan_estimate(int n, const lc_steps* steps, const lc_cosmology* cos
                            size_t* table_bytes_per_step) {
     if (!ops_for(n) || !valid_steps(steps) || !valid_cosmo(cosmo)) return LC_ERR_INVALID_ARG;
     Cosmo c{cosmo->omega_m, cosmo->h};
+    const Kernel k = kernel_of(steps);
     std::vector<double> z;
-    if (step_edges(c, *steps, z)) return LC_ERR_INVALID_ARG;
+    if (step_edges(c, k, *steps, z)) return LC_ERR_INVALID_ARG;
     // ring depth from the last step's geometry (the largest horizon)
     int ring = 1;
     for (int s = steps->n_steps - 1; s >= 0 && s >= steps->n_steps - 2; --s) {
-        StepGeom g = step_geometry(c, z, s, 1.0, 2, false);
+        StepGeom g = step_geometry(c, k, z, s, 1.0, 2, false);
         ring = g.A > ring ? g.A : ring;
     }
     const long long nrp = nrp_of(n), spec = (long long)n * n * nrp, slot = (long long)n * n * (n / 2 + 1);
@@ -687,6 +730,7 @@ lc_status lc_plan_create(int n, double box_mpc, const lc_cosmology* cosmo, const
     p->L = box_mpc;
     p->l = box_mpc / n;
     p->cosmo = Cosmo{cosmo->omega_m, cosmo->h};
+    p->kern = kernel_of(steps);
     p->n_steps = steps->n_steps;
     p->S = steps->subsamples ? steps->subsamples : 4;
     p->history = steps->history;
@@ -698,14 +742,14 @@ lc_status lc_plan_create(int n, double box_mpc, const lc_cosmology* cosmo, const
     p->spec_elems = (long long)n * n * p->NRP;
     p->W = (long long)(n / 2 + 1) * (n / 2 + 2) * (n / 2 + 3) / 6;
     p->ring_slot = (long long)n * n * (n / 2 + 1);
-    if (step_edges(p->cosmo, *steps, p->z)) {
+    if (step_edges(p->cosmo, p->kern, *steps, p->z)) {
         delete p;
         return LC_ERR_INVALID_ARG;
     }
     // active slices per observing step -> ring depth
     p->A_of_step.resize(p->n_steps);
     for (int s = 0; s < p->n_steps; ++s) {
-        StepGeom g = step_geometry(p->cosmo, p->z, s, p->l, p->S, false);
+        StepGeom g = step_geometry(p->cosmo, p->kern, p->z, s, p->l, p->S, false);
         if (g.A > kMaxShells) {
             delete p;
             return LC_ERR_UNSUPPORTED_SIZE;
@@ -718,6 +762,7 @@ lc_status lc_plan_create(int n, double box_mpc, const lc_cosmology* cosmo, const
         if (g.A > p->n_ring) p->n_ring = g.A;
     }
     p->tables.resize(p->n_steps);
+    p->table_pins.assign(p->n_steps, 0);
     cudaError_t e = ensure_init(ops);
     if (e != cudaSuccess) {
         delete p;
@@ -758,6 +803,14 @@ lc_status lc_plan_create(int n, double box_mpc, const lc_cosmology* cosmo, const
     return LC_OK;
 }
 
+lc_status lc_plan_set_table_budget(lc_plan* p, size_t bytes) {
+    if (!p) return LC_ERR_INVALID_ARG;
+    p->table_budget = bytes;
+    return LC_OK;
+}
+
+size_t lc_plan_table_bytes(const lc_plan* p) { return p ? p->table_bytes : 0; }
+
 lc_status lc_plan_prepare(lc_plan* p, int b, int e) {
     if (!p) return LC_ERR_INVALID_ARG;
     if (p->failed) return LC_ERR_CUDA;
@@ -771,7 +824,6 @@ lc_status lc_plan_prepare(lc_plan* p, int b, int e) {
 
 lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos, const double* lum) {
     if (!p) return LC_ERR_INVALID_ARG;
-    PdlChain chain(false); // the first kernel follows copies or other work: plain launch
     if (p->failed) return LC_ERR_CUDA;
     if (step < 0 || step >= p->n_steps || n_src < 0) return LC_ERR_INVALID_ARG;
     if (n_src > 0 && (!pos || !lum)) return LC_ERR_INVALID_ARG;
@@ -813,12 +865,10 @@ lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos
     SlotMeta m{slot, step, p->d_slot_step, p->d_slot_S, p->d_slot_total};
     const long long N = p->N;
     {
-        // the grid is all zero here: zeroed at creation, and the forward z
-        // pass sets every cell back to 0 as it reads it
         Phase ph(p, LC_PHASE_DEPOSIT, n_src > 0 ? 2 : 1);
+        e = cudaMemsetAsync(p->d_grid, 0, sizeof(long long) * N * N * N, st);
+        if (e != cudaSuccess) return cuda_fail(p, e);
         launch_src_prep(dpos, dlum, n_src, p->d_maxbits, p->d_err, m, st);
-        // the rest of the push is a chain of this library's kernels
-        t_pdl_chain = !p->timing;
         if (n_src > 0)
             launch_deposit(dpos, dlum, n_src, p->N, p->l, p->d_maxbits, p->d_grid, m, st,
                            p->near_on ? p->d_src_cell : nullptr, p->near_on ? p->d_src_q : nullptr);
@@ -882,7 +932,6 @@ lc_status lc_instant_field(lc_plan* p, int step, float* out) { return field_impl
 
 static lc_status field_impl(lc_plan* p, int step, float* out, int instant) {
     if (!p || !out) return LC_ERR_INVALID_ARG;
-    PdlChain chain(false); // the first kernel follows whatever the stream holds: plain launch
     if (p->failed) return LC_ERR_CUDA;
     if (step < 0 || step >= p->n_steps) return LC_ERR_INVALID_ARG;
     if (step != p->last_pushed) return LC_ERR_STEP_ORDER;
@@ -905,7 +954,6 @@ static lc_status field_impl(lc_plan* p, int step, float* out, int instant) {
             Phase ph(p, LC_PHASE_MAC_X, mac_kernels(p, T.mac_variant));
             launch_mac(p, T, step, instant, T.mac_variant, p->d_slot_step, p->d_slot_S, p->d_slot_total, st);
         }
-        t_pdl_chain = !p->timing; // the inverse passes and the near field follow the MAC
         ColArgs c{};
         c.dir = 1;
         c.out_mode = COL_OUT_PLAIN;
@@ -920,6 +968,7 @@ static lc_status field_impl(lc_plan* p, int step, float* out, int instant) {
         r.out = dout;
         r.scale = (float)(p->U / (double)N3);
         r.tw = p->d_tw;
+        const int nslot = step % p->n_ring;
         if (p->ops->plane_c2r) {
             // y and z together, one CTA per x-plane
             Phase ph(p, LC_PHASE_C2R_Z, 1);
@@ -935,8 +984,7 @@ static lc_status field_impl(lc_plan* p, int step, float* out, int instant) {
         if (p->near_on && p->near_n > 0) {
             // innermost shell's near cube, summed exactly in FP64 and folded in
             Phase ph(p, LC_PHASE_NEAR, 2);
-            const int slot = step % p->n_ring;
-            launch_near_scatter(p->d_src_cell, p->d_src_q, p->near_n, p->N, T.gnear, p->d_slot_S, slot, p->U,
+            launch_near_scatter(p->d_src_cell, p->d_src_q, p->near_n, p->N, T.gnear, p->d_slot_S, nslot, p->U,
                                 p->d_near, st);
             launch_near_fold(p->d_src_cell, p->d_src_q, p->near_n, p->N, p->d_near, dout, st);
         }
@@ -991,6 +1039,9 @@ unsigned long long params_hash(const lc_plan* p) {
     mix(&p->normalise, sizeof p->normalise);
     mix(&p->U, sizeof p->U);
     mix(p->z.data(), sizeof(double) * p->z.size());
+    mix(&p->kern.kind, sizeof p->kern.kind);
+    mix(&p->kern.length, sizeof p->kern.length);
+    mix(&p->kern.rmax, sizeof p->kern.rmax);
     return h;
 }
 
@@ -1166,7 +1217,7 @@ uint64_t lc_kernel_launches(void) { return g_launches.load(); }
 lc_status lc_step_shells(const lc_plan* p, int step, int* n_active, double* r_lo, double* r_hi, double* r_h,
                          double* shell_integral) {
     if (!p || step < 0 || step >= p->n_steps) return LC_ERR_INVALID_ARG;
-    StepGeom g = step_geometry(p->cosmo, p->z, step, p->l, p->S, shell_integral != nullptr);
+    StepGeom g = step_geometry(p->cosmo, p->kern, p->z, step, p->l, p->S, shell_integral != nullptr);
     if (n_active) *n_active = g.A;
     for (int j = 0; j < g.A; ++j) {
         if (r_lo) r_lo[j] = g.lo[j];
@@ -1299,6 +1350,7 @@ lc_status lc_graph_create(lc_plan* p, int step, int64_t n_src, const double* pos
     if (!g) return LC_ERR_OOM;
     g->p = p;
     g->step = step;
+    ++p->table_pins[step]; // the graph holds the table's address
     g->n_src = n_src;
     cudaStream_t cap_stream = nullptr, user_stream = p->stream;
     cudaError_t e = cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking);
@@ -1382,6 +1434,7 @@ lc_status lc_graph_destroy(lc_step_graph* g) {
             p->graphs.erase(p->graphs.begin() + i);
             break;
         }
+    --p->table_pins[g->step];
     delete g;
     return LC_OK;
 }
@@ -1400,6 +1453,9 @@ lc_status lc_batch_graph_create(lc_plan* const* plans, int n, const int* steps, 
                                       outs[i]);
         if (r != LC_OK) return r;
     }
+    // a batch graph may outlive the bookkeeping of its plans, so the tables it
+    // captured stay pinned for the lives of those plans
+    for (int i = 0; i < n; ++i) ++plans[i]->table_pins[steps[i]];
     lc_batch_graph* g = new (std::nothrow) lc_batch_graph();
     if (!g) return LC_ERR_OOM;
     g->plans.assign(plans, plans + n);

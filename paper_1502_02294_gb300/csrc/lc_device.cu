@@ -28,7 +28,6 @@ __device__ __forceinline__ bool finite_d(double x) { return isfinite(x); }
 __global__ void __launch_bounds__(kPrepThreads)
     k_src_prep(const double* __restrict__ pos, const double* __restrict__ lum, long long n,
                unsigned long long* maxbits, int* err, SlotMeta m) {
-    pdl_enter();
     __shared__ unsigned long long s_max[kPrepThreads / 32];
     __shared__ int s_bad;
     if (threadIdx.x == 0) s_bad = 0;
@@ -71,7 +70,6 @@ __global__ void __launch_bounds__(256)
     k_deposit(const double* __restrict__ pos, const double* __restrict__ lum, long long n, int N, double l,
               const unsigned long long* __restrict__ maxbits, long long* __restrict__ grid, SlotMeta m,
               long long* __restrict__ cell_out, long long* __restrict__ q_out) {
-    pdl_enter();
     __shared__ long long s_sum[8];
     const double lmax = __longlong_as_double((long long)*maxbits);
     double S = 1.0;
@@ -200,15 +198,6 @@ __global__ void __launch_bounds__(256) k_rgf_norm(int N, long long W, int A, con
     }
 }
 
-constexpr int kNearSide = 2 * kNearR + 1, kNearCube = kNearSide * kNearSide * kNearSide;
-
-__device__ __forceinline__ long long near_wedge(int dx, int dy, int dz) {
-    int a = dx < 0 ? -dx : dx, b = dy < 0 ? -dy : dy, c = dz < 0 ? -dz : dz, t;
-    if (a > b) { t = a; a = b; b = t; }
-    if (b > c) { t = b; b = c; c = t; }
-    if (a > b) { t = a; a = b; b = t; }
-    return (long long)c * (c + 1) * (c + 2) / 6 + (long long)b * (b + 1) / 2 + a;
-}
 
 __global__ void k_near_prep(const double* gw0, const double* scale0, double* gnear, double* g0_far) {
     // one thread: the near cube is (2R+1)^3 = 125 cells
@@ -235,7 +224,6 @@ __global__ void __launch_bounds__(256) k_near_scatter(const long long* __restric
                                                       long long n, int N, const double* __restrict__ gnear,
                                                       const double* __restrict__ slot_S, int slot, double U,
                                                       double* __restrict__ acc) {
-    pdl_enter();
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n * kNearCube) return;
     const long long s = idx / kNearCube;
@@ -249,7 +237,6 @@ __global__ void __launch_bounds__(256) k_near_scatter(const long long* __restric
 
 __global__ void __launch_bounds__(256) k_near_fold(const long long* __restrict__ cell, const long long* __restrict__ q,
                                                    long long n, int N, double* __restrict__ acc, float* __restrict__ out) {
-    pdl_enter();
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n * kNearCube) return;
     const long long s = idx / kNearCube;

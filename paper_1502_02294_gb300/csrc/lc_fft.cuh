@@ -23,29 +23,21 @@ namespace lc {
 
 constexpr int kThreads = 256;
 
-// Programmatic dependent launch.  Every kernel of the per-step chain starts
-// with pdl_enter(): it lets its successor launch once all of its own CTAs
-// are running, and it touches no memory before its predecessor has
-// completed and flushed.  Both instructions are no-ops for a kernel launched
-// without the programmatic-serialization attribute.
-__device__ __forceinline__ void pdl_enter() {
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    asm volatile("griddepcontrol.wait;" ::: "memory");
+// Near field of the innermost shell: the displacements with |d|_inf <= kNearR
+// are left out of the FFT path and added exactly in FP64 per source.
+constexpr int kNearR = 2;
+constexpr int kNearSide = 2 * kNearR + 1, kNearCube = kNearSide * kNearSide * kNearSide;
+// wedge index of a near displacement (fold signs, sort)
+__host__ __device__ __forceinline__ int near_wedge(int dx, int dy, int dz) {
+    int a = dx < 0 ? -dx : dx, b = dy < 0 ? -dy : dy, c = dz < 0 ? -dz : dz, t;
+    if (a > b) { t = a; a = b; b = t; }
+    if (b > c) { t = b; b = c; c = t; }
+    if (a > b) { t = a; a = b; b = t; }
+    return c * (c + 1) * (c + 2) / 6 + b * (b + 1) / 2 + a;
 }
 
-// Launch with programmatic stream serialization only inside a chain of
-// this library's kernels: a launch whose stream predecessor may be a copy,
-// a memset or another library's work must be plain, because
-// griddepcontrol.wait orders a kernel after the grids it depends on, not
-// after copies.  The caller marks a chain with PdlChain; LC_PDL=0 in the
-// environment turns programmatic launches off altogether.
-bool pdl_enabled();
-extern thread_local bool t_pdl_chain;
-struct PdlChain {
-    bool old;
-    explicit PdlChain(bool on) : old(t_pdl_chain) { t_pdl_chain = on; }
-    ~PdlChain() { t_pdl_chain = old; }
-};
+// Launch through cudaLaunchKernelEx (one launch path for every per-step
+// kernel; no launch attributes).
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                             Args&&... args) {
@@ -54,11 +46,8 @@ inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, siz
     cfg.blockDim = block;
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = t_pdl_chain && pdl_enabled() ? 1 : 0;
+    cfg.attrs = nullptr;
+    cfg.numAttrs = 0;
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 

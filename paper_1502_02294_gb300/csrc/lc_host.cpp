@@ -119,7 +119,13 @@ double fmod_lw(double r, double alpha) {
     return 1.7 * exp(-pow(r / (116.29 * alpha), 0.68)) - 0.7;
 }
 
-double horizon(const Cosmo& c, double zo) {
+double kernel_f(const Cosmo& c, const Kernel& k, double zs, double r) {
+    if (k.kind == LC_KERNEL_EXP) return r < k.rmax ? exp(-r / k.length) : 0.0;
+    return fmod_lw(r, alpha_lw(c, zs));
+}
+
+double horizon(const Cosmo& c, const Kernel& k, double zo) {
+    if (k.kind == LC_KERNEL_EXP) return k.rmax;
     double a = 0.0, b = 97.39 * alpha_lw(c, zo);
     for (int it = 0; it < 120 && b - a > 1e-14 * b; ++it) {
         const double m = 0.5 * (a + b);
@@ -130,40 +136,40 @@ double horizon(const Cosmo& c, double zo) {
 }
 
 namespace {
-double shell_integrand(const Cosmo& c, double zo, double r) {
+double shell_integrand(const Cosmo& c, const Kernel& k, double zo, double r) {
     const double zs = zs_of_r(c, zo, r);
     const double o = 1.0 + zo;
-    return o * o * o * fmod_lw(r, alpha_lw(c, zs)) / (4.0 * kPi * (1.0 + zs));
+    return o * o * o * kernel_f(c, k, zs, r) / (4.0 * kPi * (1.0 + zs));
 }
-double gl_integral(const Cosmo& c, double zo, double a, double b) {
+double gl_integral(const Cosmo& c, const Kernel& k, double zo, double a, double b) {
     const GaussLegendre12& q = gl();
     const double m = 0.5 * (a + b), hw = 0.5 * (b - a);
     double s = 0.0;
-    for (int i = 0; i < 12; ++i) s += q.w[i] * shell_integrand(c, zo, m + hw * q.x[i]);
+    for (int i = 0; i < 12; ++i) s += q.w[i] * shell_integrand(c, k, zo, m + hw * q.x[i]);
     return hw * s;
 }
 } // namespace
 
-double shell_integral(const Cosmo& c, double zo, double r_lo, double r_hi, double r_h) {
+double shell_integral(const Cosmo& c, const Kernel& kern, double zo, double r_lo, double r_hi, double r_h) {
     const double b = std::min(r_hi, r_h);
     if (!(r_lo < b)) return 0.0;
     double s = 0.0;
     if (r_lo <= 0.0) {
         // f_mod carries r^0.68 at the origin: geometric panels [b/2^(k+1), b/2^k]
-        for (int k = 0; k < 56; ++k) s += gl_integral(c, zo, ldexp(b, -(k + 1)), ldexp(b, -k));
+        for (int k = 0; k < 56; ++k) s += gl_integral(c, kern, zo, ldexp(b, -(k + 1)), ldexp(b, -k));
         return s;
     }
     double x = r_lo;
     while (x < b) {
         double w = std::min(0.5 * x, 2.0);
         if (x + w > b) w = b - x;
-        s += gl_integral(c, zo, x, x + w);
+        s += gl_integral(c, kern, zo, x, x + w);
         x += w;
     }
     return s;
 }
 
-int step_edges(const Cosmo& c, const lc_steps& st, std::vector<double>& z) {
+int step_edges(const Cosmo& c, const Kernel& k, const lc_steps& st, std::vector<double>& z) {
     const int n = st.n_steps;
     if (n < 1) return 1;
     z.assign(n + 1, 0.0);
@@ -177,7 +183,7 @@ int step_edges(const Cosmo& c, const lc_steps& st, std::vector<double>& z) {
         z[n] = st.z_end;
     } else if (st.spacing == LC_STEPS_EQUAL_TAU) {
         if (st.n_shell < 1) return 1;
-        const double dtau = horizon(c, st.z_end) / st.n_shell;
+        const double dtau = horizon(c, k, st.z_end) / st.n_shell;
         for (int k = 0; k < n; ++k) z[k] = zs_of_r(c, st.z_end, (n - k) * dtau);
         z[n] = st.z_end;
     } else {
@@ -188,7 +194,7 @@ int step_edges(const Cosmo& c, const lc_steps& st, std::vector<double>& z) {
     return 0;
 }
 
-void g_table(const Cosmo& c, double zo, double delta, long long ntab, double* out) {
+void g_table(const Cosmo& c, const Kernel& k, double zo, double delta, long long ntab, double* out) {
     // Walk outwards in r; z_s(r) follows from the previous point by Newton on
     // the increment chi(z_prev, z) (one Gauss-Legendre panel), re-anchored on
     // the full distance every 512 entries so that rounding cannot drift.
@@ -209,15 +215,16 @@ void g_table(const Cosmo& c, double zo, double delta, long long ntab, double* ou
         }
         r_prev = r;
         z_prev = z;
-        const double fm = fmod_lw(r, alpha_lw(c, z));
+        const double fm = kernel_f(c, k, z, r);
         out[t] = fm > 0.0 ? o3 * fm / (k16pi2 * (1.0 + z) * r * r) : 0.0;
     }
 }
 
-StepGeom step_geometry(const Cosmo& c, const std::vector<double>& z, int s, double l, int S, bool integrals) {
+StepGeom step_geometry(const Cosmo& c, const Kernel& k, const std::vector<double>& z, int s, double l, int S,
+                       bool integrals) {
     StepGeom g;
     const double zo = z[s + 1];
-    g.rh = horizon(c, zo);
+    g.rh = horizon(c, k, zo);
     for (int j = 0; j <= s; ++j) {
         const int n = s - j;
         const double lo = chi(c, zo, z[n + 1]);
@@ -240,7 +247,7 @@ StepGeom step_geometry(const Cosmo& c, const std::vector<double>& z, int s, doub
     g.ntab = g.Rh >= 3 ? (g.Rh - 3) / 8 + 1 : 0;
     if (integrals) {
         g.I.resize(g.A);
-        for (int j = 0; j < g.A; ++j) g.I[j] = shell_integral(c, zo, g.lo[j], g.hi[j], g.rh);
+        for (int j = 0; j < g.A; ++j) g.I[j] = shell_integral(c, k, zo, g.lo[j], g.hi[j], g.rh);
     }
     return g;
 }

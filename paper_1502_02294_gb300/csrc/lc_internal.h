@@ -21,11 +21,17 @@ double z_of_time(const Cosmo& c, double t_myr);
 double zs_of_r(const Cosmo& c, double z_obs, double r); // chi(z_obs, z_s) = r
 double alpha_lw(const Cosmo& c, double zs);             // Eq. 16
 double fmod_lw(double r, double alpha);                 // Eq. 15
-double horizon(const Cosmo& c, double z_obs);           // r / alpha(z_s(r)) = 97.39
-double shell_integral(const Cosmo& c, double z_obs, double r_lo, double r_hi, double r_h);
-int step_edges(const Cosmo& c, const lc_steps& st, std::vector<double>& z);
-// g(r) = (1+z_obs)^3 f_mod / ((4 pi)^2 (1+z_s) r^2) at r = delta sqrt(8 t + 3), t < ntab
-void g_table(const Cosmo& c, double z_obs, double delta, long long ntab, double* out);
+// the radial kernel (LC_KERNEL_*): g(r) = (1+z_obs)^3 f(r, z_s) / ((4 pi)^2 (1+z_s) r^2)
+struct Kernel {
+    int kind = LC_KERNEL_LW;
+    double length = 0, rmax = 0; // LC_KERNEL_EXP: f = exp(-r / length) for r < rmax
+};
+double kernel_f(const Cosmo& c, const Kernel& k, double zs, double r);
+double horizon(const Cosmo& c, const Kernel& k, double z_obs); // LW: r / alpha(z_s(r)) = 97.39
+double shell_integral(const Cosmo& c, const Kernel& k, double z_obs, double r_lo, double r_hi, double r_h);
+int step_edges(const Cosmo& c, const Kernel& k, const lc_steps& st, std::vector<double>& z);
+// g(r) at r = delta sqrt(8 t + 3), t < ntab
+void g_table(const Cosmo& c, const Kernel& k, double z_obs, double delta, long long ntab, double* out);
 
 struct StepGeom {
     int A = 0;                 // active slices (lookback j = 0 .. A-1)
@@ -35,7 +41,8 @@ struct StepGeom {
     long long Rh = 0;           // largest admissible R inside the horizon
     long long ntab = 0;
 };
-StepGeom step_geometry(const Cosmo& c, const std::vector<double>& z, int s, double l, int S, bool integrals);
+StepGeom step_geometry(const Cosmo& c, const Kernel& k, const std::vector<double>& z, int s, double l, int S,
+                       bool integrals);
 
 // ---------------- device kernels (lc_device.cu) ----------------
 struct SlotMeta {
@@ -56,8 +63,8 @@ void launch_deposit(const double* pos, const double* lum, long long n, int N, do
 
 // Near field of the innermost shell (displacements |d|_inf <= R), which the
 // FFT path leaves out: gnear holds the shell's FP64 values on the wedge prefix
-// c <= R.  prep: gnear from the builder's wedge, and the far part's k = 0 value.
-constexpr int kNearR = 2;
+// c <= R (kNearR, defined with the kernels).  prep: gnear from the builder's
+// wedge, and the far part's k = 0 value.
 void launch_near_prep(const double* gw0, const double* scale0, double* gnear, double* g0_far, cudaStream_t st);
 // scatter U * S * q * G(d) into the FP64 accumulator for every source and d
 void launch_near_scatter(const long long* cell, const long long* q, long long n, int N, const double* gnear,

@@ -29,7 +29,7 @@ enum { COL_OUT_PLAIN = 0, COL_OUT_BF16 = 1, COL_OUT_WEDGE = 2, COL_OUT_RING_F32 
 struct RowR2CArgs {
     int in_mode;
     long long nrows;
-    long long* grid;          // ROW_IN_I64: N^3 int64, set back to 0 as it is read
+    const long long* grid;    // ROW_IN_I64: N^3 int64
     const double* slot_S;     // ROW_IN_I64: fixed-point unit of the slot
     const long long* slot_total;
     int slot;
@@ -139,7 +139,6 @@ template <int N> __host__ __device__ constexpr size_t cols_smem_bytes() {
 // (compile-time count, registers) before transforming the current one.
 template <int N, int IN>
 __global__ void __launch_bounds__(kThreads) k_rows_r2c(RowR2CArgs a, int nblocks) {
-    pdl_enter();
     constexpr int B = row_pairs_of(N), BP = odd_pad(B), NRP = nrp_of(N), H = N / 2 + 1;
     constexpr int TILE = 2 * B * N, PER = (TILE + kThreads - 1) / kThreads;
     extern __shared__ float4 smem_raw[];
@@ -164,10 +163,7 @@ __global__ void __launch_bounds__(kThreads) k_rows_r2c(RowR2CArgs a, int nblocks
             const long long grow = row0 + rr;
             val[i] = 0.0f;
             if ((TILE % kThreads == 0 || idx < TILE) && grow < a.nrows) {
-                if constexpr (IN == ROW_IN_I64) {
-                    val[i] = __ll2float_rn(a.grid[grow * N + t]) * scale;
-                    a.grid[grow * N + t] = 0; // ready for the next deposit
-                }
+                if constexpr (IN == ROW_IN_I64) val[i] = __ll2float_rn(a.grid[grow * N + t]) * scale;
                 else if constexpr (IN == ROW_IN_F32) val[i] = a.fin[grow * N + t];
                 else {
                     const int x = (int)(grow / N), y = (int)(grow % N);
@@ -223,7 +219,6 @@ __global__ void __launch_bounds__(kThreads) k_rows_r2c(RowR2CArgs a, int nblocks
 // CW Nyquist columns of CW lines).  NT = N * CW / 8 threads, 8 elements each.
 template <int N, int DIR, int IN, int OUT>
 __global__ void __launch_bounds__(col_threads_of(N)) k_cols(ColArgs a) {
-    pdl_enter();
     constexpr int NT = col_threads_of(N);
     constexpr int CW = cw_of(N), BP = odd_pad(CW), NRP = nrp_of(N), M = N / 2, NCH = M / CW;
     constexpr int TILE = N * CW, PER = (TILE + NT - 1) / NT;
@@ -369,7 +364,6 @@ template <int N> struct ColGeom {
 
 template <int N, int DIR, int OUT>
 __global__ void __launch_bounds__(col_threads_of(N)) k_cols_pp(ColArgs a, int ntiles) {
-    pdl_enter();
     constexpr int NT = col_threads_of(N);
     constexpr int CW = cw_of(N), BP = odd_pad(CW), M = N / 2;
     constexpr int TILE = N * CW, PER = (TILE + NT - 1) / NT;
@@ -432,7 +426,6 @@ __global__ void __launch_bounds__(col_threads_of(N)) k_cols_pp(ColArgs a, int nt
 // z rows, complex -> real, persistent with the next block's loads in flight.
 template <int N>
 __global__ void __launch_bounds__(kThreads) k_rows_c2r(RowC2RArgs a, int nblocks) {
-    pdl_enter();
     constexpr int B = row_pairs_of(N), BP = odd_pad(B), NRP = nrp_of(N), H = N / 2 + 1;
     constexpr int TILE = B * H, PER = (TILE + kThreads - 1) / kThreads;
     extern __shared__ float4 smem_raw[];
@@ -502,7 +495,6 @@ template <int N> __host__ __device__ constexpr bool plane_ok() { return N <= 192
 
 template <int N, int IN>
 __global__ void __launch_bounds__(plane_threads_of(N)) k_plane_r2c(RowR2CArgs a) {
-    pdl_enter();
     constexpr int NT = plane_threads_of(N), H = N / 2 + 1, NRP = nrp_of(N), P = N / 2;
     constexpr int TILE = N * N, PER = (TILE + NT - 1) / NT;
     constexpr int UN = P * H, UPER = (UN + NT - 1) / NT;
@@ -526,10 +518,7 @@ __global__ void __launch_bounds__(plane_threads_of(N)) k_plane_r2c(RowR2CArgs a)
         if (TILE % NT == 0 || idx < TILE) {
             const int y = idx / N, t = idx % N;
             const long long g = ((long long)x * N + y) * N + t;
-            if constexpr (IN == ROW_IN_I64) {
-                val[i] = __ll2float_rn(a.grid[g]) * scale;
-                a.grid[g] = 0; // ready for the next deposit
-            }
+            if constexpr (IN == ROW_IN_I64) val[i] = __ll2float_rn(a.grid[g]) * scale;
             else if constexpr (IN == ROW_IN_F32) val[i] = a.fin[g];
             else {
                 const int fx = x <= N - x ? x : N - x, fy = y <= N - y ? y : N - y, fz = t <= N - t ? t : N - t;
@@ -583,7 +572,6 @@ __global__ void __launch_bounds__(plane_threads_of(N)) k_plane_r2c(RowR2CArgs a)
 
 template <int N>
 __global__ void __launch_bounds__(plane_threads_of(N)) k_plane_c2r(RowC2RArgs a) {
-    pdl_enter();
     constexpr int NT = plane_threads_of(N), H = N / 2 + 1, NRP = nrp_of(N), P = N / 2;
     constexpr int LD = N * H, LPER = (LD + NT - 1) / NT;
     constexpr int UN = P * H, UPER = (UN + NT - 1) / NT;

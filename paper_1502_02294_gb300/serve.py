@@ -71,7 +71,8 @@ class Server:
     # -------------------------------------------------------------- admission
     @staticmethod
     def plan_bytes(w, first_step: int, last_step: int) -> int:
-        base, per_step = estimate_bytes(w.n, w.steps, w.omega_m, w.h, history=w.history)
+        base, per_step = estimate_bytes(w.n, w.steps, w.omega_m, w.h, history=w.history,
+                                        kernel=getattr(w, "kernel", None))
         return int(base + per_step * (last_step - first_step + 1))
 
     def add_simulation(self, name: str, workload, first_step: int, last_step: int, fill=None):
@@ -124,8 +125,11 @@ class Server:
                 req = sim.pending.pop(sim.next_step)
                 n = sim.workload.n
                 with torch.cuda.stream(sim.stream):
-                    pos = torch.from_numpy(req.pos).to("cuda", non_blocking=True)
-                    lum = torch.from_numpy(req.lum).to("cuda", non_blocking=True)
+                    # stage the sources in pinned memory so that the copies are
+                    # asynchronous (a copy from pageable memory waits for the
+                    # stream, which would serialise the simulations)
+                    pos = torch.from_numpy(req.pos).pin_memory().to("cuda", non_blocking=True)
+                    lum = torch.from_numpy(req.lum).pin_memory().to("cuda", non_blocking=True)
                     req.out = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
                     sim.plan.push(req.step, pos, lum)
                     sim.plan.field(req.step, req.out)

@@ -101,6 +101,9 @@ class Workload:
     cat: Catalogue
     out_unit: float = 1.0
     normalise: int = 1
+    # radial kernel: None for the Lyman-Werner one, or (kind, length, rmax)
+    # with kind 1 = exponential attenuation (length, cut-off in comoving Mpc)
+    kernel: Optional[Tuple[int, float, float]] = None
 
 
 def _uniform_positions(rng, n, box):

@@ -35,7 +35,9 @@ class _Torch:
 
     @staticmethod
     def from_numpy(x):
-        return types.SimpleNamespace(to=lambda *a, **k: x)
+        t = types.SimpleNamespace(to=lambda *a, **k: x)
+        t.pin_memory = lambda: t
+        return t
 
     @staticmethod
     def empty(*a, **k):
