@@ -393,13 +393,13 @@ def run_serving(args, ClockSampler=ClockSampler):
 
 # DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum) of the
 # shell-MAC phase per step, from the captures summarised in profiles/, valid
-# only for the kernel sources they were taken with (hash below); c3 is the
-# c3s capture (32 slices) with its reads scaled to 128 slices.
-MAC_SOURCES = ("lc_mac.cuh", "lc_kernels.cuh", "lc_fft.cuh")
+# only for the MAC kernel sources they were taken with (hash below: the
+# warp-specialised and bulk kernels, the gather pass and its slot list); c3 is
+# the c3s capture (32 slices) with its reads scaled to 128 slices.
 MAC_TRAFFIC = {
-    "c2": {"sources": "326f27066b6e7021", "bytes": 38.466e6,
+    "c2": {"sources": "f0507b60d3cab092", "bytes": 38.480e6,
            "from": "profiles/c2_dram_traffic.md (64-step window, all MAC-phase launches)"},
-    "c3": {"sources": "326f27066b6e7021", "bytes": 4 * 1.187670e9 + 72.543e6,
+    "c3": {"sources": "f0507b60d3cab092", "bytes": 4 * 1.187908e9 + 72.553e6,
            "from": "profiles/k_mac_ws_256_bf16_pair.md (c3s, reads x 128/32)"},
 }
 
@@ -417,13 +417,23 @@ def max_over_ranks(x, device):
     return float(t.item())
 
 
+def _function_text(src, head):
+    """The text of the function whose definition starts with `head`."""
+    i = src.index(head)
+    return src[i:src.index("\n}\n", i) + 3]
+
+
 def mac_sources_hash():
     import hashlib
 
+    d = os.path.join(ROOT, "paper_1502_02294_gb300", "csrc")
     h = hashlib.sha256()
-    for f in MAC_SOURCES:
-        with open(os.path.join(ROOT, "paper_1502_02294_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    with open(os.path.join(d, "lc_mac.cuh"), "rb") as fh:
+        h.update(fh.read())
+    with open(os.path.join(d, "lc_kernels.cuh")) as fh:
+        k = fh.read()
+    h.update(_function_text(k, "__device__ __forceinline__ void mac_slot_list(").encode())
+    h.update(_function_text(k, "__global__ void __launch_bounds__(col_threads_of(N)) k_cols(ColArgs a)").encode())
     return h.hexdigest()[:16]
 
 
