@@ -82,6 +82,19 @@ enum { LC_HISTORY_FP32 = 0, LC_HISTORY_BF16 = 1 };
  *                  (lambda = kernel_length, r_max = kernel_rmax, comoving Mpc). */
 enum { LC_KERNEL_LW = 0, LC_KERNEL_EXP = 1 };
 
+/* The near field of the innermost slice (FP32 history).  The 5^3 cells around
+ * each source's NGP cell are taken out of the FFT path of the innermost shell
+ * and added per source in FP64:
+ *   LC_NEAR_NGP:     with the source at its cell centre (the grid Green's
+ *                    function itself, so the field is exactly Eq. 11);
+ *   LC_NEAR_SUBCELL: from the source's own position, the particle-mesh hybrid
+ *                    that the Discussion suggests for sources resolved below
+ *                    the mesh: each target cell gets the s^3 sub-sample average
+ *                    of g around the source (over the periodic images, inside
+ *                    the innermost shell and the horizon) times the shell's
+ *                    normalisation factor.  Needs the FP32 history. */
+enum { LC_NEAR_NGP = 0, LC_NEAR_SUBCELL = 1 };
+
 /* How time is sliced (step 1 of Section 2.2) and how the field is evaluated.
  * Step s spans [tau_s, tau_{s+1}] and is observed at its end, tau_{s+1}; the
  * sources pushed at step s stand for the source term frozen over that step
@@ -103,6 +116,7 @@ typedef struct {
     int kernel;            /* LC_KERNEL_LW (0, default) or LC_KERNEL_EXP */
     double kernel_length;  /* LC_KERNEL_EXP: attenuation length lambda > 0, comoving Mpc */
     double kernel_rmax;    /* LC_KERNEL_EXP: cut-off radius r_max > 0, comoving Mpc */
+    int near_mode;         /* LC_NEAR_NGP (0, default) or LC_NEAR_SUBCELL */
 } lc_steps;
 
 /* Create a plan for an N^3 periodic grid of side box_mpc.

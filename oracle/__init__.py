@@ -72,6 +72,7 @@ def lib():
             ("lco_deposit_fixed", i, [i, d, i64, dp, dp, i64p, dp, i64p]),
             ("lco_field", i, [pp, i, i, ctypes.POINTER(dp), i64, i64p, dp]),
             ("lco_shell_table", i, [pp, i, dp, dp, dp]),
+            ("lco_near_cube", i, [pp, i, i64, dp, dp, i, d, i, dp]),
             ("lco_dft3", i, [i, dp, dp, i, dp, dp]), ("lco_threads", i, []),
         ]:
             f = getattr(L, name)
@@ -273,6 +274,35 @@ def source_grids(prob: Problem, cat, s: int) -> List[Optional[np.ndarray]]:
 
 def field_for(prob: Problem, cat, s: int, cells: Optional[np.ndarray] = None) -> np.ndarray:
     return prob.field(s, source_grids(prob, cat, s), cells)
+
+
+NEAR_R = 2  # near cube of the innermost slice: |d| <= NEAR_R cells per axis
+
+
+def near_cube(prob: Problem, s: int, pos, lum, centred: bool, R: int = NEAR_R) -> np.ndarray:
+    """The innermost slice's near cube around each source (see lco_near_cube):
+    from the sources' own positions, or (centred) from their NGP cells."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    lum = np.ascontiguousarray(lum, dtype=np.float64)
+    out = np.zeros(prob.n ** 3)
+    if prob.active_shells(s) == 0 or lum.shape[0] == 0:
+        return out.reshape((prob.n,) * 3)
+    _, I0, sm0 = prob.rgf_octant(s, 0)
+    l = prob.box / prob.n
+    f0 = I0 / (l ** 3 * sm0) if (prob.normalise and sm0 > 0) else 1.0
+    rc = lib().lco_near_cube(prob.ref, s, lum.shape[0], _dp(pos), _dp(lum), int(R), float(f0), int(centred), _dp(out))
+    if rc:
+        raise ValueError("bad step")
+    return out.reshape((prob.n,) * 3)
+
+
+def hybrid_field_for(prob: Problem, cat, s: int) -> np.ndarray:
+    """The field with the particle-mesh hybrid near the sources (Discussion):
+    the innermost slice's near cube of every source taken from its position
+    instead of its NGP cell; everything else as field_for."""
+    J = field_for(prob, cat, s)
+    pos, lum = cat.active(s)
+    return J - near_cube(prob, s, pos, lum, centred=True) + near_cube(prob, s, pos, lum, centred=False)
 
 
 def instant_field_for(prob: Problem, cat, s: int, cells: Optional[np.ndarray] = None) -> np.ndarray:

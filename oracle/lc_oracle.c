@@ -651,6 +651,84 @@ int lco_field(const lco_problem* P, int s, int n_src_grids, const double* const*
 }
 
 /* Shell integrals I_j (Green's-function k = 0 values times l^3) of step s. */
+/* Near field of the innermost slice from the sources' own positions (the
+ * particle-mesh hybrid the Discussion suggests for sources resolved below the
+ * mesh).  For every source of the observing step's own slice (j = 0) and
+ * every target cell within R cells (per axis) of the source's NGP cell, add
+ *   U * lum * f0 / s^3 * sum_{s^3 sub-samples y of the target cell}
+ *        sum_{periodic images u} [r < r_hi(0), r <= r_h] g(r),   r = |y - x_src + u L|,
+ * to out (N^3, C order, accumulated): the same sub-sampled shell average as
+ * G_0 (Eq. 10), with f0 its normalisation factor, but centred on the source
+ * position instead of its cell.  centred != 0 puts every source at its cell
+ * centre, which gives back U * lum * G_0(target - cell) exactly: the near
+ * cube of the NGP field. */
+int lco_near_cube(const lco_problem* P, int s, int64_t n_src, const double* pos, const double* lum, int R,
+                  double f0, int centred, double* out) {
+    const int N = P->n, S = P->subsamples;
+    const double l = P->box / N, L = P->box;
+    const double zo = P->z_edges[s + 1];
+    double rlo[1], rhi[1], rh;
+    if (s < 0 || s >= P->n_steps) return 1;
+    double* lo_all = (double*)malloc(sizeof(double) * (s + 1));
+    double* hi_all = (double*)malloc(sizeof(double) * (s + 1));
+    int A = lco_shells(P, s, lo_all, hi_all, &rh);
+    if (A <= 0) {
+        free(lo_all);
+        free(hi_all);
+        return 0;
+    }
+    rlo[0] = lo_all[0];
+    rhi[0] = hi_all[0];
+    free(lo_all);
+    free(hi_all);
+    const double top = rhi[0];
+    const int U = (int)ceil((top + 2.0 * (R + 1) * l) / L) + 1;
+    const double wgt = P->out_unit * f0 / ((double)S * S * S);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t q = 0; q < n_src; ++q) {
+        const double x[3] = {pos[3 * q], pos[3 * q + 1], pos[3 * q + 2]};
+        int64_t c[3];
+        double off[3];
+        for (int d = 0; d < 3; ++d) {
+            c[d] = ngp_index(x[d], l, N);
+            /* the source relative to its cell centre, in [-l/2, l/2) */
+            double t = x[d] / l + 0.5;
+            off[d] = centred ? 0.0 : (t - floor(t) - 0.5) * l;
+        }
+        const double halfdiag = 0.5 * sqrt(3.0) * l;
+        for (int dx = -R; dx <= R; ++dx)
+            for (int dy = -R; dy <= R; ++dy)
+                for (int dz = -R; dz <= R; ++dz) {
+                    double acc = 0.0;
+                    for (int u = -U; u <= U; ++u)
+                        for (int v = -U; v <= U; ++v)
+                            for (int w = -U; w <= U; ++w) {
+                                /* target cell centre minus source, this image */
+                                double cx = l * dx - off[0] + u * L, cy = l * dy - off[1] + v * L,
+                                       cz = l * dz - off[2] + w * L;
+                                /* every sample is within halfdiag of the centre */
+                                if (sqrt(cx * cx + cy * cy + cz * cz) - halfdiag >= top) continue;
+                                for (int a = 0; a < S; ++a)
+                                    for (int b = 0; b < S; ++b)
+                                        for (int e = 0; e < S; ++e) {
+                                            double px = cx + l * ((a + 0.5) / S - 0.5);
+                                            double py = cy + l * ((b + 0.5) / S - 0.5);
+                                            double pz = cz + l * ((e + 0.5) / S - 0.5);
+                                            double r = sqrt(px * px + py * py + pz * pz);
+                                            if (!(r >= rlo[0] && r < top && r <= rh)) continue;
+                                            acc += lco_gk(P->kernel, P->k_length, P->k_rmax, P->om, P->h, zo, r);
+                                        }
+                            }
+                    int64_t tx = ((c[0] + dx) % N + N) % N, ty = ((c[1] + dy) % N + N) % N,
+                            tz = ((c[2] + dz) % N + N) % N;
+                    double val = wgt * lum[q] * acc;
+#pragma omp atomic
+                    out[(tx * N + ty) * N + tz] += val;
+                }
+    }
+    return 0;
+}
+
 int lco_shell_table(const lco_problem* P, int s, double* r_lo, double* r_hi, double* I) {
     int A = lco_shells(P, s, r_lo, r_hi, NULL);
     double zo = P->z_edges[s + 1];

@@ -26,6 +26,7 @@ LC_ERR_OOM, LC_ERR_CUDA, LC_ERR_TIMEOUT, LC_ERR_DEVICE_CHECK = 4, 5, 6, 7
 STEPS_EXPLICIT, STEPS_EQUAL_TIME, STEPS_EQUAL_TAU = 0, 1, 2
 HISTORY_FP32, HISTORY_BF16 = 0, 1
 KERNEL_LW, KERNEL_EXP = 0, 1  # radial kernels (lc_steps.kernel)
+NEAR_NGP, NEAR_SUBCELL = 0, 1  # near field of the innermost slice (lc_steps.near_mode)
 SUPPORTED_N = (8, 16, 32, 64, 96, 128, 192, 256, 384, 512)
 PHASES = ("deposit", "r2c_z", "fwd_y", "fwd_x_ring", "mac_x", "inv_y", "c2r_z", "near")
 
@@ -62,7 +63,8 @@ class _Steps(ctypes.Structure):
                 ("z_edges", ctypes.POINTER(ctypes.c_double)), ("z_start", ctypes.c_double),
                 ("z_end", ctypes.c_double), ("n_shell", ctypes.c_int), ("subsamples", ctypes.c_int),
                 ("history", ctypes.c_int), ("normalise", ctypes.c_int), ("out_unit", ctypes.c_double),
-                ("kernel", ctypes.c_int), ("kernel_length", ctypes.c_double), ("kernel_rmax", ctypes.c_double)]
+                ("kernel", ctypes.c_int), ("kernel_length", ctypes.c_double), ("kernel_rmax", ctypes.c_double),
+                ("near_mode", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -174,7 +176,7 @@ def _ptr(x, dtype) -> Tuple[int, object]:
     return a.ctypes.data, a
 
 
-def _steps_struct(spec, subsamples=4, history=HISTORY_FP32, normalise=1, out_unit=1.0, kernel=None):
+def _steps_struct(spec, subsamples=4, history=HISTORY_FP32, normalise=1, out_unit=1.0, kernel=None, near_mode=0):
     z = None
     zp = ctypes.POINTER(ctypes.c_double)()
     if getattr(spec, "z_edges", None) is not None:
@@ -182,7 +184,7 @@ def _steps_struct(spec, subsamples=4, history=HISTORY_FP32, normalise=1, out_uni
         zp = z.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     st = _Steps(int(spec.n_steps), int(spec.kind), zp, float(getattr(spec, "z_start", 0.0)),
                 float(getattr(spec, "z_end", 0.0)), int(getattr(spec, "n_shell", 0)), int(subsamples), int(history),
-                int(normalise), float(out_unit), *_kernel_fields(kernel))
+                int(normalise), float(out_unit), *_kernel_fields(kernel), int(near_mode))
     return st, z
 
 
@@ -204,11 +206,11 @@ class Plan:
 
     def __init__(self, n: int, box: float, omega_m: float, h: float, steps, subsamples: int = 4,
                  history: int = HISTORY_FP32, normalise: int = 1, out_unit: float = 1.0, stream=None,
-                 kernel=None):
+                 kernel=None, near_mode: int = NEAR_NGP):
         L = _lib()
         self.n, self.box = int(n), float(box)
         self._cos = _Cosmology(float(omega_m), float(h))
-        self._steps, self._zkeep = _steps_struct(steps, subsamples, history, normalise, out_unit, kernel)
+        self._steps, self._zkeep = _steps_struct(steps, subsamples, history, normalise, out_unit, kernel, near_mode)
         self._stream = _stream_ptr(stream)
         h_ = ctypes.c_void_p()
         _check(L.lc_plan_create(self.n, self.box, ctypes.byref(self._cos), ctypes.byref(self._steps),
@@ -226,7 +228,7 @@ class Plan:
     def from_workload(cls, w, stream=None, **kw):
         args = dict(n=w.n, box=w.box, omega_m=w.omega_m, h=w.h, steps=w.steps, subsamples=w.subsamples,
                     history=w.history, normalise=w.normalise, out_unit=w.out_unit, stream=stream,
-                    kernel=getattr(w, "kernel", None))
+                    kernel=getattr(w, "kernel", None), near_mode=getattr(w, "near_mode", 0))
         args.update(kw)
         return cls(**args)
 

@@ -168,6 +168,8 @@ struct lc_plan {
         float* ghat = nullptr;  // [W][gstride]; shell 0 without its near cube when near_on
         double* g0 = nullptr;   // [A] FP64 Ghat_j(0) of what the FFT path carries
         double* gnear = nullptr; // near cube of shell 0 on the wedge prefix (near_on)
+        float* zs1 = nullptr;   // near_pm: 1 + z_s(r) on [0, rtop] (kZsTab points)
+        double rtop = 0, rhi0 = 0, rh = 0;
         int mac_variant = 0;    // MAC_GATHER, MAC_BULK, MAC_WS or MAC_WS2, chosen by the autotuner
         int A = -1;             // -1: not built
     };
@@ -193,6 +195,8 @@ struct lc_plan {
     double* d_near = nullptr;     // N^3 FP64 accumulator, kept all-zero between steps
     long long* d_src_cell = nullptr;
     long long* d_src_q = nullptr;
+    bool near_pm = false;           // near cube from the sources' own positions
+    double* d_src_off = nullptr;    // near_pm: positions relative to the cell centres (3 per source)
     long long near_cap = 0, near_n = 0;
     size_t bytes = 0;
     int last_pushed = -1;
@@ -338,10 +342,12 @@ void free_all(lc_plan* p) {
     cudaFree(p->d_tune_total);
     cudaFree(p->d_src_cell);
     cudaFree(p->d_src_q);
+    cudaFree(p->d_src_off);
     for (auto& t : p->tables) {
         cudaFree(t.ghat);
         cudaFree(t.g0);
         cudaFree(t.gnear);
+        cudaFree(t.zs1);
     }
     for (auto& m : p->marks) {
         cudaEventDestroy(m.a);
@@ -359,6 +365,8 @@ bool valid_steps(const lc_steps* st) {
     if (st->spacing == LC_STEPS_EQUAL_TAU && (st->n_shell < 1 || !(st->z_end >= 0.0))) return false;
     if (st->spacing == LC_STEPS_EXPLICIT && !st->z_edges) return false;
     if (st->kernel != LC_KERNEL_LW && st->kernel != LC_KERNEL_EXP) return false;
+    if (st->near_mode != LC_NEAR_NGP && st->near_mode != LC_NEAR_SUBCELL) return false;
+    if (st->near_mode == LC_NEAR_SUBCELL && st->history != LC_HISTORY_FP32) return false;
     if (st->kernel == LC_KERNEL_EXP && !(st->kernel_length > 0.0 && isfinite(st->kernel_length) &&
                                          st->kernel_rmax > 0.0 && isfinite(st->kernel_rmax)))
         return false;
@@ -502,10 +510,43 @@ int choose_mac_variant(lc_plan* p, const lc_plan::Table& T, int s) {
     return best;
 }
 
+constexpr int kZsTab = 4096; // points of the 1 + z_s(r) table of the sub-cell near field
+
+// room for the near-field source lists of n sources (cells, charges, and the
+// sub-cell offsets with near_pm); the old lists are kept on failure
+lc_status ensure_near(lc_plan* p, long long n) {
+    if (!p->near_on || n <= p->near_cap) return LC_OK;
+    long long cap = 1024;
+    while (cap < n) cap *= 2;
+    long long *cell = nullptr, *q = nullptr;
+    double* off = nullptr;
+    if (dalloc(p, &cell, (size_t)cap) != cudaSuccess || dalloc(p, &q, (size_t)cap) != cudaSuccess ||
+        (p->near_pm && dalloc(p, &off, (size_t)cap * 3) != cudaSuccess)) {
+        if (cell) p->bytes -= sizeof(long long) * cap;
+        if (q) p->bytes -= sizeof(long long) * cap;
+        if (off) p->bytes -= sizeof(double) * 3 * cap;
+        cudaFree(cell);
+        cudaFree(q);
+        cudaFree(off);
+        cudaGetLastError();
+        return LC_ERR_OOM;
+    }
+    cudaFree(p->d_src_cell);
+    cudaFree(p->d_src_q);
+    cudaFree(p->d_src_off);
+    p->bytes -= sizeof(long long) * 2 * p->near_cap + (p->near_pm ? sizeof(double) * 3 * p->near_cap : 0);
+    p->d_src_cell = cell;
+    p->d_src_q = q;
+    p->d_src_off = off;
+    p->near_cap = cap;
+    return LC_OK;
+}
+
 size_t table_size(const lc_plan* p, int A) {
     if (A <= 0) return 0;
     return sizeof(float) * (size_t)p->W * ((A + 7) / 8 * 8) + sizeof(double) * A +
-           (p->near_on ? sizeof(double) * (kNearR + 1) * (kNearR + 2) * (kNearR + 3) / 6 : 0);
+           (p->near_on ? sizeof(double) * ((kNearR + 1) * (kNearR + 2) * (kNearR + 3) / 6 + 1) : 0) +
+           (p->near_pm ? sizeof(float) * kZsTab : 0);
 }
 
 void free_table(lc_plan* p, int s) {
@@ -513,6 +554,7 @@ void free_table(lc_plan* p, int s) {
     cudaFree(T.ghat);
     cudaFree(T.g0);
     cudaFree(T.gnear);
+    cudaFree(T.zs1);
     const size_t b = table_size(p, T.A);
     p->table_bytes -= b;
     p->bytes -= b;
@@ -577,7 +619,10 @@ lc_status build_table(lc_plan* p, int s) {
     T.gstride = (A + 7) / 8 * 8;
     if (dalloc(p, &T.ghat, (size_t)p->W * T.gstride) != cudaSuccess) return LC_ERR_OOM;
     if (dalloc(p, &T.g0, (size_t)A) != cudaSuccess ||
-        (p->near_on && dalloc(p, &T.gnear, (size_t)(kNearR + 1) * (kNearR + 2) * (kNearR + 3) / 6) != cudaSuccess)) {
+        (p->near_on && dalloc(p, &T.gnear, (size_t)(kNearR + 1) * (kNearR + 2) * (kNearR + 3) / 6 + 1) != cudaSuccess) ||
+        (p->near_pm && dalloc(p, &T.zs1, (size_t)kZsTab) != cudaSuccess)) {
+        cudaFree(T.gnear);
+        T.gnear = nullptr;
         cudaFree(T.ghat);
         cudaFree(T.g0);
         T.ghat = nullptr;
@@ -585,6 +630,16 @@ lc_status build_table(lc_plan* p, int s) {
         return LC_ERR_OOM;
     }
     p->table_bytes += table_size(p, A);
+    if (p->near_pm) {
+        // the light-cone redshift over the innermost shell, for the sub-cell near field
+        T.rhi0 = g.hi[0];
+        T.rh = g.rh;
+        T.rtop = std::min(g.hi[0], g.rh);
+        std::vector<float> zt(kZsTab);
+        for (int k = 0; k < kZsTab; ++k) zt[k] = (float)(1.0 + zs_of_r(p->cosmo, p->z[s + 1], T.rtop * k / (kZsTab - 1)));
+        e = cudaMemcpy(T.zs1, zt.data(), sizeof(float) * kZsTab, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(p, e);
+    }
     cudaStream_t st = p->stream;
     e = cudaMemcpyAsync(p->d_gtab, gt.data(), sizeof(double) * g.ntab, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_bnd, g.bnd.data(), sizeof(long long) * (A + 1), cudaMemcpyHostToDevice, st);
@@ -781,6 +836,7 @@ lc_status lc_plan_create(int n, double box_mpc, const lc_cosmology* cosmo, const
         return LC_ERR_OOM;
     }
     p->near_on = p->history == LC_HISTORY_FP32;
+    p->near_pm = p->near_on && steps->near_mode == LC_NEAR_SUBCELL;
     if (p->near_on && dalloc(p, &p->d_near, N3) != cudaSuccess) {
         free_all(p);
         delete p;
@@ -846,21 +902,7 @@ lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos
             dlum = p->d_lum;
         }
     }
-    if (p->near_on && n_src > p->near_cap) {
-        cudaFree(p->d_src_cell);
-        cudaFree(p->d_src_q);
-        p->bytes -= sizeof(long long) * 2 * p->near_cap;
-        p->near_cap = 0;
-        long long cap = 1024;
-        while (cap < n_src) cap *= 2;
-        if (dalloc(p, &p->d_src_cell, (size_t)cap) != cudaSuccess || dalloc(p, &p->d_src_q, (size_t)cap) != cudaSuccess) {
-            cudaFree(p->d_src_cell);
-            cudaFree(p->d_src_q);
-            p->d_src_cell = p->d_src_q = nullptr;
-            return LC_ERR_OOM;
-        }
-        p->near_cap = cap;
-    }
+    if (lc_status r = ensure_near(p, n_src); r != LC_OK) return r;
     const int slot = step % p->n_ring;
     SlotMeta m{slot, step, p->d_slot_step, p->d_slot_S, p->d_slot_total};
     const long long N = p->N;
@@ -871,7 +913,8 @@ lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos
         launch_src_prep(dpos, dlum, n_src, p->d_maxbits, p->d_err, m, st);
         if (n_src > 0)
             launch_deposit(dpos, dlum, n_src, p->N, p->l, p->d_maxbits, p->d_grid, m, st,
-                           p->near_on ? p->d_src_cell : nullptr, p->near_on ? p->d_src_q : nullptr);
+                           p->near_on ? p->d_src_cell : nullptr, p->near_on ? p->d_src_q : nullptr,
+                           p->near_pm ? p->d_src_off : nullptr);
     }
     p->near_n = p->near_on ? n_src : 0;
     RowR2CArgs r{};
@@ -984,8 +1027,37 @@ static lc_status field_impl(lc_plan* p, int step, float* out, int instant) {
         if (p->near_on && p->near_n > 0) {
             // innermost shell's near cube, summed exactly in FP64 and folded in
             Phase ph(p, LC_PHASE_NEAR, 2);
-            launch_near_scatter(p->d_src_cell, p->d_src_q, p->near_n, p->N, T.gnear, p->d_slot_S, nslot, p->U,
-                                p->d_near, st);
+            if (p->near_pm) {
+                NearPmArgs na{};
+                na.cell = p->d_src_cell;
+                na.q = p->d_src_q;
+                na.off = p->d_src_off;
+                na.n = p->near_n;
+                na.N = p->N;
+                na.S = p->S;
+                na.l = p->l;
+                na.L = p->L;
+                na.rtop = T.rtop;
+                na.rhi = T.rhi0;
+                na.rh = T.rh;
+                na.rtop2f = (float)(T.rtop * T.rtop);
+                na.U = (int)ceil((T.rtop + 2.0 * (kNearR + 1) * p->l) / p->L) + 1;
+                na.zs1 = T.zs1;
+                na.K = kZsTab;
+                na.zo = p->z[step + 1];
+                na.kind = p->kern.kind;
+                na.klen = (float)p->kern.length;
+                na.kmax = (float)p->kern.rmax;
+                na.alpha0 = (float)alpha_lw(p->cosmo, 20.0);
+                na.f0 = T.gnear + (kNearR + 1) * (kNearR + 2) * (kNearR + 3) / 6;
+                na.slot_S = p->d_slot_S;
+                na.slot = nslot;
+                na.U_out = p->U;
+                launch_near_pm(na, p->d_near, st);
+            } else {
+                launch_near_scatter(p->d_src_cell, p->d_src_q, p->near_n, p->N, T.gnear, p->d_slot_S, nslot, p->U,
+                                    p->d_near, st);
+            }
             launch_near_fold(p->d_src_cell, p->d_src_q, p->near_n, p->N, p->d_near, dout, st);
         }
         e = cudaGetLastError();
@@ -1042,6 +1114,7 @@ unsigned long long params_hash(const lc_plan* p) {
     mix(&p->kern.kind, sizeof p->kern.kind);
     mix(&p->kern.length, sizeof p->kern.length);
     mix(&p->kern.rmax, sizeof p->kern.rmax);
+    mix(&p->near_pm, sizeof p->near_pm);
     return h;
 }
 
@@ -1051,7 +1124,7 @@ size_t ring_bytes_of(const lc_plan* p) {
 
 size_t meta_bytes_of(const lc_plan* p, long long near_n) {
     return (size_t)p->n_ring * (sizeof(int) + sizeof(double) + sizeof(long long)) +
-           (size_t)near_n * 2 * sizeof(long long);
+           (size_t)near_n * 2 * sizeof(long long) + (p->near_pm ? (size_t)near_n * 3 * sizeof(double) : 0);
 }
 
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
@@ -1091,6 +1164,7 @@ lc_status lc_plan_save(lc_plan* p, void* buf, size_t size) {
     put(p->d_slot_total, nr * sizeof(long long));
     put(p->d_src_cell, (size_t)p->near_n * sizeof(long long));
     put(p->d_src_q, (size_t)p->near_n * sizeof(long long));
+    if (p->near_pm) put(p->d_src_off, (size_t)p->near_n * 3 * sizeof(double));
     off = sizeof h + align256(meta_bytes_of(p, p->near_n));
     put(p->d_ring, ring_bytes_of(p));
     if (e == cudaSuccess) e = cudaStreamSynchronize(st); // the header copy reads a stack object
@@ -1113,23 +1187,7 @@ lc_status lc_plan_load(lc_plan* p, const void* buf, size_t size) {
         h.near_n < 0 || (!p->near_on && h.near_n != 0))
         return LC_ERR_INVALID_ARG;
     if (size < sizeof h + align256(meta_bytes_of(p, h.near_n)) + ring_bytes_of(p)) return LC_ERR_INVALID_ARG;
-    if (p->near_on && h.near_n > p->near_cap) {
-        long long cap = 1024;
-        while (cap < h.near_n) cap *= 2;
-        long long *cell = nullptr, *q = nullptr;
-        if (dalloc(p, &cell, (size_t)cap) != cudaSuccess) return LC_ERR_OOM;
-        if (dalloc(p, &q, (size_t)cap) != cudaSuccess) {
-            cudaFree(cell);
-            p->bytes -= sizeof(long long) * cap;
-            return LC_ERR_OOM;
-        }
-        cudaFree(p->d_src_cell);
-        cudaFree(p->d_src_q);
-        p->bytes -= sizeof(long long) * 2 * p->near_cap;
-        p->d_src_cell = cell;
-        p->d_src_q = q;
-        p->near_cap = cap;
-    }
+    if (lc_status r = ensure_near(p, h.near_n); r != LC_OK) return r;
     const unsigned char* b = static_cast<const unsigned char*>(buf);
     const size_t nr = (size_t)p->n_ring;
     size_t off = sizeof h;
@@ -1142,6 +1200,7 @@ lc_status lc_plan_load(lc_plan* p, const void* buf, size_t size) {
     get(p->d_slot_total, nr * sizeof(long long));
     get(p->d_src_cell, (size_t)h.near_n * sizeof(long long));
     get(p->d_src_q, (size_t)h.near_n * sizeof(long long));
+    if (p->near_pm) get(p->d_src_off, (size_t)h.near_n * 3 * sizeof(double));
     off = sizeof h + align256(meta_bytes_of(p, h.near_n));
     get(p->d_ring, ring_bytes_of(p));
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -1326,17 +1385,7 @@ static lc_status prepare_capture(lc_plan* p, int step, int64_t n_src, const doub
         return LC_ERR_INVALID_ARG; // a graph holds device pointers only
     lc_status r = build_table(p, step);
     if (r != LC_OK) return r;
-    if (p->near_on && n_src > p->near_cap) {
-        cudaFree(p->d_src_cell);
-        cudaFree(p->d_src_q);
-        p->bytes -= sizeof(long long) * 2 * p->near_cap;
-        p->near_cap = 0;
-        long long cap = 1024;
-        while (cap < n_src) cap *= 2;
-        if (dalloc(p, &p->d_src_cell, (size_t)cap) != cudaSuccess || dalloc(p, &p->d_src_q, (size_t)cap) != cudaSuccess)
-            return LC_ERR_OOM;
-        p->near_cap = cap;
-    }
+    if (lc_status r2 = ensure_near(p, n_src); r2 != LC_OK) return r2;
     return LC_OK;
 }
 

@@ -69,7 +69,7 @@ __device__ __forceinline__ long long ngp_cell(double x, double l, int N) {
 __global__ void __launch_bounds__(256)
     k_deposit(const double* __restrict__ pos, const double* __restrict__ lum, long long n, int N, double l,
               const unsigned long long* __restrict__ maxbits, long long* __restrict__ grid, SlotMeta m,
-              long long* __restrict__ cell_out, long long* __restrict__ q_out) {
+              long long* __restrict__ cell_out, long long* __restrict__ q_out, double* __restrict__ off_out) {
     __shared__ long long s_sum[8];
     const double lmax = __longlong_as_double((long long)*maxbits);
     double S = 1.0;
@@ -93,6 +93,14 @@ __global__ void __launch_bounds__(256)
         if (cell_out) {
             cell_out[i] = c;
             q_out[i] = q;
+        }
+        if (off_out) {
+            // the source relative to its cell centre, in [-l/2, l/2) per axis
+            const double p3[3] = {x, y, z};
+            for (int d = 0; d < 3; ++d) {
+                const double t = p3[d] / l + 0.5;
+                off_out[3 * i + d] = finite_d(t) ? (t - floor(t) - 0.5) * l : 0.0;
+            }
         }
     }
     for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
@@ -203,6 +211,7 @@ __global__ void k_near_prep(const double* gw0, const double* scale0, double* gne
     // one thread: the near cube is (2R+1)^3 = 125 cells
     const int Wn = (kNearR + 1) * (kNearR + 2) * (kNearR + 3) / 6;
     for (int w = 0; w < Wn; ++w) gnear[w] = gw0[w] * (*scale0);
+    gnear[Wn] = *scale0; // the shell's normalisation factor, for the sub-cell near field
     double sum = 0.0;
     for (int dx = -kNearR; dx <= kNearR; ++dx)
         for (int dy = -kNearR; dy <= kNearR; ++dy)
@@ -250,7 +259,79 @@ __global__ void __launch_bounds__(256) k_near_fold(const long long* __restrict__
     if (v != 0.0) out[t] = (float)((double)out[t] + v);
 }
 
+// Sub-cell near field (particle-mesh hybrid of the Discussion): one thread
+// per (source, target cell of its near cube).  The target's value is the s^3
+// sub-sample average of g around the source's own position, over the periodic
+// images, inside the innermost shell [0, r_hi) and the horizon, times the
+// shell's normalisation factor f0 and U S q.  Per sample in FP32: the
+// light-cone redshift 1 + z_s(r) from a table (linear in r), then the kernel
+// formula; shell and horizon tests in FP64 where FP32 is too close to call.
+__global__ void __launch_bounds__(256) k_near_pm(NearPmArgs a, double* __restrict__ acc) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= a.n * kNearCube) return;
+    const long long s = idx / kNearCube;
+    const int m = (int)(idx % kNearCube);
+    const long long qs = a.q[s];
+    if (qs == 0) return;
+    int dx, dy, dz;
+    const long long t = near_target(a.cell[s], m, a.N, dx, dy, dz);
+    const double l = a.l;
+    // sample minus source, relative to the source's cell centre (central image)
+    const double bx = l * dx - a.off[3 * s], by = l * dy - a.off[3 * s + 1], bz = l * dz - a.off[3 * s + 2];
+    const int S = a.S;
+    const double hd = 0.5 * 1.7320508075688772 * l; // half-diagonal of a cell
+    const float inv_h = (float)((a.K - 1) / a.rtop);
+    const float o3 = (float)((1.0 + a.zo) * (1.0 + a.zo) * (1.0 + a.zo));
+    const float k16pi2 = 157.91367041742973f; // (4 pi)^2
+    double sum = 0.0;
+    for (int u = -a.U; u <= a.U; ++u)
+        for (int v = -a.U; v <= a.U; ++v)
+            for (int w = -a.U; w <= a.U; ++w) {
+                const double cx = bx + u * a.L, cy = by + v * a.L, cz = bz + w * a.L;
+                // no sample of this image's target cell can reach the shell
+                if (sqrt(cx * cx + cy * cy + cz * cz) - hd >= a.rtop) continue;
+                for (int ia = 0; ia < S; ++ia)
+                    for (int ib = 0; ib < S; ++ib)
+                        for (int ic = 0; ic < S; ++ic) {
+                            const float px = (float)(cx + l * ((ia + 0.5) / S - 0.5));
+                            const float py = (float)(cy + l * ((ib + 0.5) / S - 0.5));
+                            const float pz = (float)(cz + l * ((ic + 0.5) / S - 0.5));
+                            const float r2 = px * px + py * py + pz * pz;
+                            bool in = r2 < a.rtop2f;
+                            if (fabsf(r2 - a.rtop2f) <= 1e-5f * a.rtop2f) {
+                                // too close to call in FP32: decide in FP64
+                                const double qx = cx + l * ((ia + 0.5) / S - 0.5), qy = cy + l * ((ib + 0.5) / S - 0.5),
+                                             qz = cz + l * ((ic + 0.5) / S - 0.5);
+                                const double r = sqrt(qx * qx + qy * qy + qz * qz);
+                                in = r < a.rhi && r <= a.rh;
+                            }
+                            if (!in) continue;
+                            const float r = sqrtf(r2);
+                            float xt = r * inv_h;
+                            int k0 = (int)xt;
+                            if (k0 > a.K - 2) k0 = a.K - 2;
+                            const float fr = xt - (float)k0;
+                            const float zs1 = a.zs1[k0] + fr * (a.zs1[k0 + 1] - a.zs1[k0]); // 1 + z_s(r)
+                            float f;
+                            if (a.kind == 1) {
+                                f = r < a.kmax ? expf(-r / a.klen) : 0.0f;
+                            } else {
+                                const float al = a.alpha0 * rsqrtf(zs1 / 21.0f);
+                                f = r > 97.39f * al ? 0.0f : 1.7f * expf(-powf(r / (116.29f * al), 0.68f)) - 0.7f;
+                            }
+                            if (f != 0.0f) sum += (double)(o3 * f / (k16pi2 * zs1 * r2));
+                        }
+            }
+    if (sum != 0.0) atomicAdd(acc + t, a.U_out * a.slot_S[a.slot] * (double)qs * a.f0[0] * sum / ((double)S * S * S));
+}
+
 } // namespace
+
+void launch_near_pm(const NearPmArgs& a, double* acc, cudaStream_t st) {
+    const long long total = a.n * kNearCube;
+    if (total <= 0) return;
+    launch_k(k_near_pm, (unsigned)((total + 255) / 256), 256, 0, st, a, acc);
+}
 
 void launch_near_prep(const double* gw0, const double* scale0, double* gnear, double* g0_far, cudaStream_t st) {
     k_near_prep<<<1, 1, 0, st>>>(gw0, scale0, gnear, g0_far);
@@ -277,9 +358,9 @@ void launch_src_prep(const double* pos, const double* lum, long long n, unsigned
 
 void launch_deposit(const double* pos, const double* lum, long long n, int N, double l,
                     const unsigned long long* maxbits, long long* grid, SlotMeta m, cudaStream_t st,
-                    long long* cell_out, long long* q_out) {
+                    long long* cell_out, long long* q_out, double* off_out) {
     const long long blocks = n > 0 ? (n + 255) / 256 : 1;
-    launch_k(k_deposit, (unsigned)blocks, 256, 0, st, pos, lum, n, N, l, maxbits, grid, m, cell_out, q_out);
+    launch_k(k_deposit, (unsigned)blocks, 256, 0, st, pos, lum, n, N, l, maxbits, grid, m, cell_out, q_out, off_out);
 }
 
 // f_diff = (J_instant - J) / J, the difference taken and divided in FP64 and

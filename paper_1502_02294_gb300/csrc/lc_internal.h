@@ -59,13 +59,36 @@ void launch_src_prep(const double* pos, const double* lum, long long n, unsigned
 // luminosity, kept for the near-field correction of the innermost shell.
 void launch_deposit(const double* pos, const double* lum, long long n, int N, double l,
                     const unsigned long long* maxbits, long long* grid, SlotMeta m, cudaStream_t st,
-                    long long* cell_out = nullptr, long long* q_out = nullptr);
+                    long long* cell_out = nullptr, long long* q_out = nullptr, double* off_out = nullptr);
 
 // Near field of the innermost shell (displacements |d|_inf <= R), which the
 // FFT path leaves out: gnear holds the shell's FP64 values on the wedge prefix
 // c <= R (kNearR, defined with the kernels).  prep: gnear from the builder's
 // wedge, and the far part's k = 0 value.
 void launch_near_prep(const double* gw0, const double* scale0, double* gnear, double* g0_far, cudaStream_t st);
+// sub-cell near field of the innermost shell from the sources' own positions
+struct NearPmArgs {
+    const long long* cell;  // NGP cells of the sources
+    const long long* q;     // fixed-point charges
+    const double* off;      // positions relative to the cell centres (3 per source)
+    long long n;
+    int N, S, U;            // grid, sub-samples per axis, periodic images per axis (-U..U)
+    double l, L;            // cell and box side
+    double rtop;            // min(shell outer radius, horizon): the z_s table's range
+    double rhi, rh;         // shell outer radius, horizon (FP64 decisions)
+    float rtop2f;           // rtop^2 in FP32
+    const float* zs1;       // 1 + z_s(r) at r = k rtop / (K - 1)
+    int K;
+    double zo;              // observing redshift
+    int kind;               // radial kernel (LC_KERNEL_*)
+    float klen, kmax;       // LC_KERNEL_EXP parameters
+    float alpha0;           // LW: alpha at 1 + z_s = 21 (Eq. 16)
+    const double* f0;       // the shell's normalisation factor (device)
+    const double* slot_S;
+    int slot;
+    double U_out;
+};
+void launch_near_pm(const NearPmArgs& a, double* acc, cudaStream_t st);
 // scatter U * S * q * G(d) into the FP64 accumulator for every source and d
 void launch_near_scatter(const long long* cell, const long long* q, long long n, int N, const double* gnear,
                          const double* slot_S, int slot, double U, double* acc, cudaStream_t st);

@@ -104,6 +104,9 @@ class Workload:
     # radial kernel: None for the Lyman-Werner one, or (kind, length, rmax)
     # with kind 1 = exponential attenuation (length, cut-off in comoving Mpc)
     kernel: Optional[Tuple[int, float, float]] = None
+    # near field of the innermost slice: 0 from NGP cells, 1 from the sources'
+    # own positions (sub-cell)
+    near_mode: int = 0
 
 
 def _uniform_positions(rng, n, box):
