@@ -22,6 +22,7 @@ ranks.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import subprocess
@@ -62,7 +63,16 @@ def parse():
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--flush-mb", type=int, default=512)
+    ap.add_argument("--kernel", default="lw", choices=["lw", "exp"],
+                    help="radial kernel: Lyman-Werner (Eqs. 14-17) or exp(-r/30 Mpc) cut off at 80 Mpc")
+    ap.add_argument("--near", default="ngp", choices=["ngp", "subcell"],
+                    help="innermost slice's near field: cell-centred (NGP) or from the sources' own positions")
+    ap.add_argument("--fdiff", action="store_true",
+                    help="each step also builds the instantaneous field (Eq. 18) and the f_diff map")
     return ap.parse_args()
+
+
+EXP_KERNEL = (1, 30.0, 80.0)  # exp(-r / 30 Mpc), cut off at r_max = 80 Mpc
 
 
 # ---------------------------------------------------------------- clocks
@@ -461,6 +471,15 @@ def main():
     import synth
 
     w = synth.config(args.workload)
+    variant = {}
+    if args.kernel == "exp":
+        w = dataclasses.replace(w, kernel=EXP_KERNEL)
+        variant["radial_kernel"] = "exp(-r/30 Mpc), cut off at 80 Mpc"
+    if args.near == "subcell":
+        w = dataclasses.replace(w, near_mode=1)
+        variant["near_field"] = "sub-cell (s^3 sub-samples around each source's own position)"
+    if args.fdiff:
+        variant["step_adds"] = "instantaneous field (Eq. 18) + f_diff map, inside the timed step"
 
     if args.impl == "reference":
         if rank != 0:
@@ -486,11 +505,12 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "grid": w.n,
-                           "steps_in_run": w.steps.n_steps},
+                           "steps_in_run": w.steps.n_steps, **variant},
                 "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                                  "sample": f"each step: one observing step's Green's functions + {cells} sampled "
                                            "cells (1024 on the first), full-field time extrapolated from the per-cell "
-                                           "rate"},
+                                           "rate" + ("; the retarded field alone (cell-centred near field, no "
+                                                     "f_diff map)" if args.near != "ngp" or args.fdiff else "")},
                 "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
                 "cpu_seconds": spent}
         print(json.dumps(line))
@@ -520,7 +540,14 @@ def main():
         pos, lum = w.cat.active(s)
         src_dev.append((torch.from_numpy(pos).to(dev), torch.from_numpy(lum).to(dev)))
     out = torch.empty((w.n,) * 3, dtype=torch.float32, device=dev)
+    out_inst = torch.empty_like(out) if args.fdiff else None
+    out_fdiff = torch.empty_like(out) if args.fdiff else None
     flush = torch.empty(args.flush_mb << 20, dtype=torch.uint8, device=dev)
+
+    def fdiff_after(s):
+        # the instantaneous field of step s and f_diff = (J_inst - J) / J per cell
+        plan.instant_field(s, out_inst)
+        lc.fdiff_map(out, out_inst, out_fdiff, stream=stream)
     # timed window: every step for the equal-time runs; for the equal-conformal-time
     # run the last n_shell/4 steps, after n_shell untimed fill steps (history only)
     t0 = 0 if w.steps.kind != synth.STEPS_EQUAL_TAU else w.steps.n_shell
@@ -558,6 +585,8 @@ def main():
             if nvtx:
                 torch.cuda.nvtx.range_push("step")  # lets a profiler select the timed replays
             gs[s].launch()
+            if args.fdiff:
+                fdiff_after(s)
             if nvtx:
                 torch.cuda.nvtx.range_pop()
             if evs:
@@ -571,6 +600,8 @@ def main():
         if i and s == t0:
             refill()
         graphs[s].launch()
+        if args.fdiff:
+            fdiff_after(s)
     torch.cuda.synchronize()
     sampler = ClockSampler(dev.index)
     sampler.start()
@@ -592,6 +623,17 @@ def main():
     phases = plan.timing(reset=True)
     for g in list(graphs.values()) + list(graphs_timed.values()):
         g.close()
+    fdiff_stats = None
+    if args.fdiff:
+        # the profiling pass ended on the same step as the timed one: its maps are in place
+        f = out_fdiff.double()
+        lit = out > 0
+        fa = f[lit].abs()
+        fdiff_stats = {"step": done_steps[-1], "cells_with_flux": int(lit.sum()),
+                       "mean_abs": float(fa.mean()) if fa.numel() else None,
+                       "p50_abs": float(fa.kthvalue(max(1, fa.numel() // 2))[0]) if fa.numel() else None,
+                       "p99_abs": float(fa.kthvalue(max(1, int(0.99 * fa.numel())))[0]) if fa.numel() else None,
+                       "frac_over_10pct": float((fa > 0.1).double().mean()) if fa.numel() else None}
     per_step_ms = np.array([a.elapsed_time(b) for a, b in evs])
     t_total = float(per_step_ms.sum()) / 1e3
     t_max = max_over_ranks(t_total, dev)
@@ -614,7 +656,8 @@ def main():
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     mac_gbs = mac_bytes / (mac_ms / 1e3) / 1e9 if mac_ms > 0 else None
-    traffic, traffic_src = mac_traffic(args.workload)
+    # the captured DRAM traffic is for the Lyman-Werner kernel's shell count
+    traffic, traffic_src = mac_traffic(args.workload) if args.kernel == "lw" else (None, None)
     phase_share = {k: round(v[0] / max(1e-12, sum(x[0] for x in phases.values())), 4) for k, v in phases.items()}
 
     # end to end through the public API: pinned host inputs, host output
@@ -623,11 +666,23 @@ def main():
         pos, lum = w.cat.active(s)
         pinned.append((torch.from_numpy(pos).pin_memory(), torch.from_numpy(lum).pin_memory()))
     host_out = torch.empty((w.n,) * 3, dtype=torch.float32).pin_memory()
+    host_fdiff = torch.empty((w.n,) * 3, dtype=torch.float32).pin_memory() if args.fdiff else None
+
+    def e2e_field(s):
+        if not args.fdiff:
+            plan.field(s, host_out)  # synchronises and copies to the host
+            return
+        plan.field(s, out)
+        fdiff_after(s)
+        host_out.copy_(out, non_blocking=True)
+        host_fdiff.copy_(out_fdiff, non_blocking=True)
+        stream.synchronize()
+
     refill()
     e_cursor = t0
     for _ in range(max(3, args.warmup)):
         plan.push(e_cursor, *pinned[e_cursor])
-        plan.field(e_cursor, host_out)
+        e2e_field(e_cursor)
         e_cursor += 1
         if e_cursor == T:
             refill()
@@ -642,13 +697,13 @@ def main():
         torch.cuda.synchronize()
         tic = time.perf_counter()
         plan.push(s, *pinned[s])
-        plan.field(s, host_out)  # synchronises and copies to the host
+        e2e_field(s)
         e2e_t += time.perf_counter() - tic
         h2d += pinned[s][0].numel() * 8 + pinned[s][1].numel() * 8
         e_cursor = t0 + (s + 1 - t0) % (T - t0)
     e2e_t = max_over_ranks(e2e_t, dev)
     e2e = {"value": world * args.steps / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(h2d // args.steps),
-           "d2h_bytes_per_step": int(w.n ** 3 * 4)}
+           "d2h_bytes_per_step": int(w.n ** 3 * 4 * (2 if args.fdiff else 1))}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -658,6 +713,8 @@ def main():
             rate, spent, desc = oracle_field_rate(w, [10, 20, 30, 41, 50, 63], cells_per_step=131072)
         else:
             rate, spent, desc = oracle_field_rate(w, [w.steps.n_steps - 1], cells_per_step=2048)
+        if args.near != "ngp" or args.fdiff:
+            desc += "; the sample times the retarded field alone (cell-centred near field, no f_diff map)"
         cpu = {"value": rate, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle", "sample": desc,
                "seconds": round(spent, 2)}
 
@@ -671,7 +728,7 @@ def main():
                        "history": "bf16" if w.history else "fp32",
                        "mac_kernel": dict(sorted(mac_choice.items(), key=lambda kv: int(kv[0][1:]))),
                        "l2": f"flushed between timed steps "
-                       f"({args.flush_mb} MB write outside the events)", "inputs": "device-resident"},
+                       f"({args.flush_mb} MB write outside the events)", "inputs": "device-resident", **variant},
             "cell_shell_mac_per_s": world * mac_cells / t_max,
             "latency_ms": {"p50": float(np.percentile(per_step_ms, 50)), "p99": float(np.percentile(per_step_ms, 99))},
             "roofline": {"bound": "hbm", "kernel": "shell-MAC phase: k_cols<N,+1,MAC> (gather) or k_mac_tma + "
@@ -691,6 +748,8 @@ def main():
             "gpu_launches": int(launches),
             "cpu_baseline": cpu,
         }
+        if fdiff_stats is not None:
+            line["fdiff"] = fdiff_stats
         print(json.dumps(line))
     plan.close()
     if world > 1:

@@ -1041,6 +1041,11 @@ static lc_status field_impl(lc_plan* p, int step, float* out, int instant) {
                 na.rhi = T.rhi0;
                 na.rh = T.rh;
                 na.rtop2f = (float)(T.rtop * T.rtop);
+                na.win2f = (float)(1e-5 * (T.rtop * T.rtop + T.rtop * p->l));
+                {
+                    const double reach = T.rtop + 0.5 * 1.7320508075688772 * p->l;
+                    na.prune2f = (float)(reach * reach * (1.0 + 1e-5));
+                }
                 na.U = (int)ceil((T.rtop + 2.0 * (kNearR + 1) * p->l) / p->L) + 1;
                 na.zs1 = T.zs1;
                 na.K = kZsTab;

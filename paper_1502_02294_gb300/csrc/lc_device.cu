@@ -263,9 +263,26 @@ __global__ void __launch_bounds__(256) k_near_fold(const long long* __restrict__
 // per (source, target cell of its near cube).  The target's value is the s^3
 // sub-sample average of g around the source's own position, over the periodic
 // images, inside the innermost shell [0, r_hi) and the horizon, times the
-// shell's normalisation factor f0 and U S q.  Per sample in FP32: the
-// light-cone redshift 1 + z_s(r) from a table (linear in r), then the kernel
-// formula; shell and horizon tests in FP64 where FP32 is too close to call.
+// shell's normalisation factor f0 and U S q.
+//
+// Everything per sample is FP32: the sample's offset from the source, r^2,
+// the light-cone redshift 1 + z_s(r) from a table (linear in r), the kernel
+// formula, and a compensated (Kahan) sum.  Only the shell and horizon test of
+// a sample whose FP32 r^2 lies within `win2f` of rtop^2 is redone in FP64 from
+// the FP64 sample position.  The FP32 sample coordinate is off by at most
+// u (2 rtop + 5 l) per axis (u = 2^-24: the roundings of the image offset,
+// of the sub-sample offset and of their sum, for an image with |c| < rtop +
+// l/2 on every axis), so near the shell edge r^2 is off by at most
+// u (10 rtop^2 + 18 rtop l); win2f = 1e-5 (rtop^2 + rtop l) is nine times
+// that or more.
+__device__ __forceinline__ void image_range(double b, double L, double invL, double reach, int U, int& lo, int& hi) {
+    // images u with |b + u L| < reach (reach carries a relative margin)
+    lo = (int)ceil((-reach - b) * invL);
+    hi = (int)floor((reach - b) * invL);
+    lo = lo < -U ? -U : lo;
+    hi = hi > U ? U : hi;
+}
+
 __global__ void __launch_bounds__(256) k_near_pm(NearPmArgs a, double* __restrict__ acc) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= a.n * kNearCube) return;
@@ -276,29 +293,42 @@ __global__ void __launch_bounds__(256) k_near_pm(NearPmArgs a, double* __restric
     int dx, dy, dz;
     const long long t = near_target(a.cell[s], m, a.N, dx, dy, dz);
     const double l = a.l;
-    // sample minus source, relative to the source's cell centre (central image)
+    // target cell centre minus source (central image)
     const double bx = l * dx - a.off[3 * s], by = l * dy - a.off[3 * s + 1], bz = l * dz - a.off[3 * s + 2];
     const int S = a.S;
-    const double hd = 0.5 * 1.7320508075688772 * l; // half-diagonal of a cell
+    // an image contributes only if on every axis its cell centre lies within
+    // rtop + l/2 of the source (every sample is within l/2 of the centre)
+    const double reach = (a.rtop + 0.5 * l) * (1.0 + 1e-6) + 1e-6 * l;
+    const double invL = 1.0 / a.L;
+    int ulo, uhi, vlo, vhi, wlo, whi;
+    image_range(bx, a.L, invL, reach, a.U, ulo, uhi);
+    image_range(by, a.L, invL, reach, a.U, vlo, vhi);
+    image_range(bz, a.L, invL, reach, a.U, wlo, whi);
     const float inv_h = (float)((a.K - 1) / a.rtop);
-    const float o3 = (float)((1.0 + a.zo) * (1.0 + a.zo) * (1.0 + a.zo));
-    const float k16pi2 = 157.91367041742973f; // (4 pi)^2
-    double sum = 0.0;
-    for (int u = -a.U; u <= a.U; ++u)
-        for (int v = -a.U; v <= a.U; ++v)
-            for (int w = -a.U; w <= a.U; ++w) {
+    const float o3 = (float)((1.0 + a.zo) * (1.0 + a.zo) * (1.0 + a.zo) / 157.91367041742973); // (1+z)^3/(4 pi)^2
+    const float lf = (float)l;
+    const float invS = 1.0f / (float)S;
+    const float rtop2f = a.rtop2f, win2f = a.win2f;
+    float sum = 0.0f, comp = 0.0f; // Kahan
+    for (int u = ulo; u <= uhi; ++u)
+        for (int v = vlo; v <= vhi; ++v)
+            for (int w = wlo; w <= whi; ++w) {
                 const double cx = bx + u * a.L, cy = by + v * a.L, cz = bz + w * a.L;
-                // no sample of this image's target cell can reach the shell
-                if (sqrt(cx * cx + cy * cy + cz * cz) - hd >= a.rtop) continue;
-                for (int ia = 0; ia < S; ++ia)
-                    for (int ib = 0; ib < S; ++ib)
+                const float cxf = (float)cx, cyf = (float)cy, czf = (float)cz;
+                // no sample of this image's target cell can reach the shell:
+                // |c| >= rtop + half-diagonal, with a relative margin
+                if (cxf * cxf + cyf * cyf + czf * czf > a.prune2f) continue;
+                for (int ia = 0; ia < S; ++ia) {
+                    const float px = cxf + lf * (((float)ia + 0.5f) * invS - 0.5f);
+                    for (int ib = 0; ib < S; ++ib) {
+                        const float py = cyf + lf * (((float)ib + 0.5f) * invS - 0.5f);
+                        const float rxy2 = px * px + py * py;
+                        if (rxy2 > rtop2f + win2f) continue; // every sample of the row is outside
                         for (int ic = 0; ic < S; ++ic) {
-                            const float px = (float)(cx + l * ((ia + 0.5) / S - 0.5));
-                            const float py = (float)(cy + l * ((ib + 0.5) / S - 0.5));
-                            const float pz = (float)(cz + l * ((ic + 0.5) / S - 0.5));
-                            const float r2 = px * px + py * py + pz * pz;
-                            bool in = r2 < a.rtop2f;
-                            if (fabsf(r2 - a.rtop2f) <= 1e-5f * a.rtop2f) {
+                            const float pz = czf + lf * (((float)ic + 0.5f) * invS - 0.5f);
+                            const float r2 = rxy2 + pz * pz;
+                            bool in = r2 < rtop2f;
+                            if (fabsf(r2 - rtop2f) <= win2f) {
                                 // too close to call in FP32: decide in FP64
                                 const double qx = cx + l * ((ia + 0.5) / S - 0.5), qy = cy + l * ((ib + 0.5) / S - 0.5),
                                              qz = cz + l * ((ic + 0.5) / S - 0.5);
@@ -307,22 +337,32 @@ __global__ void __launch_bounds__(256) k_near_pm(NearPmArgs a, double* __restric
                             }
                             if (!in) continue;
                             const float r = sqrtf(r2);
-                            float xt = r * inv_h;
+                            const float xt = r * inv_h;
                             int k0 = (int)xt;
                             if (k0 > a.K - 2) k0 = a.K - 2;
                             const float fr = xt - (float)k0;
-                            const float zs1 = a.zs1[k0] + fr * (a.zs1[k0 + 1] - a.zs1[k0]); // 1 + z_s(r)
+                            const float z0 = __ldg(a.zs1 + k0);
+                            const float zs1 = z0 + fr * (__ldg(a.zs1 + k0 + 1) - z0); // 1 + z_s(r)
                             float f;
                             if (a.kind == 1) {
                                 f = r < a.kmax ? expf(-r / a.klen) : 0.0f;
                             } else {
-                                const float al = a.alpha0 * rsqrtf(zs1 / 21.0f);
-                                f = r > 97.39f * al ? 0.0f : 1.7f * expf(-powf(r / (116.29f * al), 0.68f)) - 0.7f;
+                                const float al = a.alpha0 * rsqrtf(zs1 * (1.0f / 21.0f));
+                                // (r / 116.29 alpha)^0.68 as 2^(0.68 log2(.)), the argument > 0
+                                f = r > 97.39f * al ? 0.0f
+                                                    : 1.7f * expf(-exp2f(0.68f * log2f(r / (116.29f * al)))) - 0.7f;
                             }
-                            if (f != 0.0f) sum += (double)(o3 * f / (k16pi2 * zs1 * r2));
+                            if (f == 0.0f) continue;
+                            const float y = o3 * f / (zs1 * r2) - comp;
+                            const float tt = sum + y;
+                            comp = (tt - sum) - y;
+                            sum = tt;
                         }
+                    }
+                }
             }
-    if (sum != 0.0) atomicAdd(acc + t, a.U_out * a.slot_S[a.slot] * (double)qs * a.f0[0] * sum / ((double)S * S * S));
+    const double tot = (double)sum - (double)comp;
+    if (tot != 0.0) atomicAdd(acc + t, a.U_out * a.slot_S[a.slot] * (double)qs * a.f0[0] * tot / ((double)S * S * S));
 }
 
 } // namespace

@@ -77,6 +77,8 @@ struct NearPmArgs {
     double rtop;            // min(shell outer radius, horizon): the z_s table's range
     double rhi, rh;         // shell outer radius, horizon (FP64 decisions)
     float rtop2f;           // rtop^2 in FP32
+    float win2f;            // |r^2 - rtop^2| <= win2f: decide the sample in FP64
+    float prune2f;          // |c|^2 above this: no sample of the image reaches rtop
     const float* zs1;       // 1 + z_s(r) at r = k rtop / (K - 1)
     int K;
     double zo;              // observing redshift

@@ -1,0 +1,30 @@
+"""bench.py's command line on CPU: the reference arm (the oracle) runs the
+workload variants and names them in its config, and keeps the JSON line's
+contract keys."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _run(*extra):
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "c1",
+                        "--steps", "1", "--warmup", "0", *extra], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def test_reference_arm_default_and_variants():
+    base = _run()
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in base
+    assert base["impl"] == "reference" and base["value"] > 0
+    assert "radial_kernel" not in base["config"] and "near_field" not in base["config"]
+    v = _run("--kernel", "exp", "--near", "subcell", "--fdiff")
+    assert v["config"]["radial_kernel"].startswith("exp(")
+    assert "sub-cell" in v["config"]["near_field"]
+    assert "f_diff" in v["config"]["step_adds"]
+    assert v["value"] > 0
