@@ -168,7 +168,7 @@ struct lc_plan {
         float* ghat = nullptr;  // [W][gstride]; shell 0 without its near cube when near_on
         double* g0 = nullptr;   // [A] FP64 Ghat_j(0) of what the FFT path carries
         double* gnear = nullptr; // near cube of shell 0 on the wedge prefix (near_on)
-        float* zs1 = nullptr;   // near_pm: 1 + z_s(r) on [0, rtop] (kZsTab points)
+        float2* pmtab = nullptr; // near_pm: the redshift factors of g on [0, rtop] (kZsTab points)
         double rtop = 0, rhi0 = 0, rh = 0;
         int mac_variant = 0;    // MAC_GATHER, MAC_BULK, MAC_WS or MAC_WS2, chosen by the autotuner
         int A = -1;             // -1: not built
@@ -347,7 +347,7 @@ void free_all(lc_plan* p) {
         cudaFree(t.ghat);
         cudaFree(t.g0);
         cudaFree(t.gnear);
-        cudaFree(t.zs1);
+        cudaFree(t.pmtab);
     }
     for (auto& m : p->marks) {
         cudaEventDestroy(m.a);
@@ -546,7 +546,7 @@ size_t table_size(const lc_plan* p, int A) {
     if (A <= 0) return 0;
     return sizeof(float) * (size_t)p->W * ((A + 7) / 8 * 8) + sizeof(double) * A +
            (p->near_on ? sizeof(double) * ((kNearR + 1) * (kNearR + 2) * (kNearR + 3) / 6 + 1) : 0) +
-           (p->near_pm ? sizeof(float) * kZsTab : 0);
+           (p->near_pm ? sizeof(float2) * kZsTab : 0);
 }
 
 void free_table(lc_plan* p, int s) {
@@ -554,7 +554,7 @@ void free_table(lc_plan* p, int s) {
     cudaFree(T.ghat);
     cudaFree(T.g0);
     cudaFree(T.gnear);
-    cudaFree(T.zs1);
+    cudaFree(T.pmtab);
     const size_t b = table_size(p, T.A);
     p->table_bytes -= b;
     p->bytes -= b;
@@ -620,7 +620,7 @@ lc_status build_table(lc_plan* p, int s) {
     if (dalloc(p, &T.ghat, (size_t)p->W * T.gstride) != cudaSuccess) return LC_ERR_OOM;
     if (dalloc(p, &T.g0, (size_t)A) != cudaSuccess ||
         (p->near_on && dalloc(p, &T.gnear, (size_t)(kNearR + 1) * (kNearR + 2) * (kNearR + 3) / 6 + 1) != cudaSuccess) ||
-        (p->near_pm && dalloc(p, &T.zs1, (size_t)kZsTab) != cudaSuccess)) {
+        (p->near_pm && dalloc(p, &T.pmtab, (size_t)kZsTab) != cudaSuccess)) {
         cudaFree(T.gnear);
         T.gnear = nullptr;
         cudaFree(T.ghat);
@@ -631,13 +631,22 @@ lc_status build_table(lc_plan* p, int s) {
     }
     p->table_bytes += table_size(p, A);
     if (p->near_pm) {
-        // the light-cone redshift over the innermost shell, for the sub-cell near field
+        // the factors of g (Eq. 17) that depend on r only through the
+        // light-cone redshift z_s(r), over the innermost shell, for the
+        // sub-cell near field: both are smooth in r, so linear interpolation
+        // on kZsTab points is far below FP32 rounding
         T.rhi0 = g.hi[0];
         T.rh = g.rh;
         T.rtop = std::min(g.hi[0], g.rh);
-        std::vector<float> zt(kZsTab);
-        for (int k = 0; k < kZsTab; ++k) zt[k] = (float)(1.0 + zs_of_r(p->cosmo, p->z[s + 1], T.rtop * k / (kZsTab - 1)));
-        e = cudaMemcpy(T.zs1, zt.data(), sizeof(float) * kZsTab, cudaMemcpyHostToDevice);
+        const double zo = p->z[s + 1];
+        const double o3 = (1.0 + zo) * (1.0 + zo) * (1.0 + zo) / (16.0 * M_PI * M_PI);
+        std::vector<float2> zt(kZsTab);
+        for (int k = 0; k < kZsTab; ++k) {
+            const double zs = zs_of_r(p->cosmo, zo, T.rtop * k / (kZsTab - 1));
+            zt[k].x = (float)(o3 / (1.0 + zs));
+            zt[k].y = p->kern.kind == LC_KERNEL_EXP ? 0.0f : (float)(1.0 / (116.29 * alpha_lw(p->cosmo, zs)));
+        }
+        e = cudaMemcpy(T.pmtab, zt.data(), sizeof(float2) * kZsTab, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return cuda_fail(p, e);
     }
     cudaStream_t st = p->stream;
@@ -1047,13 +1056,11 @@ static lc_status field_impl(lc_plan* p, int step, float* out, int instant) {
                     na.prune2f = (float)(reach * reach * (1.0 + 1e-5));
                 }
                 na.U = (int)ceil((T.rtop + 2.0 * (kNearR + 1) * p->l) / p->L) + 1;
-                na.zs1 = T.zs1;
+                na.tab = T.pmtab;
                 na.K = kZsTab;
-                na.zo = p->z[step + 1];
                 na.kind = p->kern.kind;
-                na.klen = (float)p->kern.length;
+                na.inv_klen = (float)(1.0 / p->kern.length);
                 na.kmax = (float)p->kern.rmax;
-                na.alpha0 = (float)alpha_lw(p->cosmo, 20.0);
                 na.f0 = T.gnear + (kNearR + 1) * (kNearR + 2) * (kNearR + 3) / 6;
                 na.slot_S = p->d_slot_S;
                 na.slot = nslot;

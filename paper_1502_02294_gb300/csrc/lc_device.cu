@@ -266,8 +266,9 @@ __global__ void __launch_bounds__(256) k_near_fold(const long long* __restrict__
 // shell's normalisation factor f0 and U S q.
 //
 // Everything per sample is FP32: the sample's offset from the source, r^2,
-// the light-cone redshift 1 + z_s(r) from a table (linear in r), the kernel
-// formula, and a compensated (Kahan) sum.  Only the shell and horizon test of
+// the two factors of g that depend on r through the light-cone redshift
+// z_s(r) from a table (linear in r), the kernel formula, and a compensated
+// (Kahan) sum.  Only the shell and horizon test of
 // a sample whose FP32 r^2 lies within `win2f` of rtop^2 is redone in FP64 from
 // the FP64 sample position.  The FP32 sample coordinate is off by at most
 // u (2 rtop + 5 l) per axis (u = 2^-24: the roundings of the image offset,
@@ -283,7 +284,7 @@ __device__ __forceinline__ void image_range(double b, double L, double invL, dou
     hi = hi > U ? U : hi;
 }
 
-__global__ void __launch_bounds__(256) k_near_pm(NearPmArgs a, double* __restrict__ acc) {
+__global__ void __launch_bounds__(256, 2) k_near_pm(NearPmArgs a, double* __restrict__ acc) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= a.n * kNearCube) return;
     const long long s = idx / kNearCube;
@@ -305,7 +306,7 @@ __global__ void __launch_bounds__(256) k_near_pm(NearPmArgs a, double* __restric
     image_range(by, a.L, invL, reach, a.U, vlo, vhi);
     image_range(bz, a.L, invL, reach, a.U, wlo, whi);
     const float inv_h = (float)((a.K - 1) / a.rtop);
-    const float o3 = (float)((1.0 + a.zo) * (1.0 + a.zo) * (1.0 + a.zo) / 157.91367041742973); // (1+z)^3/(4 pi)^2
+    const float xcut = (float)(97.39 / 116.29); // the LW horizon r = 97.39 alpha (Eq. 16) as r / (116.29 alpha)
     const float lf = (float)l;
     const float invS = 1.0f / (float)S;
     const float rtop2f = a.rtop2f, win2f = a.win2f;
@@ -341,19 +342,18 @@ __global__ void __launch_bounds__(256) k_near_pm(NearPmArgs a, double* __restric
                             int k0 = (int)xt;
                             if (k0 > a.K - 2) k0 = a.K - 2;
                             const float fr = xt - (float)k0;
-                            const float z0 = __ldg(a.zs1 + k0);
-                            const float zs1 = z0 + fr * (__ldg(a.zs1 + k0 + 1) - z0); // 1 + z_s(r)
+                            const float2 t0 = __ldg(a.tab + k0), t1 = __ldg(a.tab + k0 + 1);
+                            const float hz = t0.x + fr * (t1.x - t0.x); // (1+z_obs)^3 / ((4 pi)^2 (1+z_s))
                             float f;
                             if (a.kind == 1) {
-                                f = r < a.kmax ? expf(-r / a.klen) : 0.0f;
+                                f = r < a.kmax ? expf(-r * a.inv_klen) : 0.0f;
                             } else {
-                                const float al = a.alpha0 * rsqrtf(zs1 * (1.0f / 21.0f));
-                                // (r / 116.29 alpha)^0.68 as 2^(0.68 log2(.)), the argument > 0
-                                f = r > 97.39f * al ? 0.0f
-                                                    : 1.7f * expf(-exp2f(0.68f * log2f(r / (116.29f * al)))) - 0.7f;
+                                const float x = r * (t0.y + fr * (t1.y - t0.y)); // r / (116.29 alpha(z_s))
+                                // f_mod of Eq. 15 with x^0.68 = 2^(0.68 log2 x)
+                                f = x > xcut ? 0.0f : 1.7f * expf(-exp2f(0.68f * log2f(x))) - 0.7f;
                             }
                             if (f == 0.0f) continue;
-                            const float y = o3 * f / (zs1 * r2) - comp;
+                            const float y = __fdividef(hz * f, r2) - comp;
                             const float tt = sum + y;
                             comp = (tt - sum) - y;
                             sum = tt;

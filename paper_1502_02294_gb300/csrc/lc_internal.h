@@ -79,12 +79,12 @@ struct NearPmArgs {
     float rtop2f;           // rtop^2 in FP32
     float win2f;            // |r^2 - rtop^2| <= win2f: decide the sample in FP64
     float prune2f;          // |c|^2 above this: no sample of the image reaches rtop
-    const float* zs1;       // 1 + z_s(r) at r = k rtop / (K - 1)
+    // at r = k rtop / (K - 1): x = (1 + z_obs)^3 / ((4 pi)^2 (1 + z_s(r))),
+    // y = 1 / (116.29 alpha(z_s(r))) for the LW kernel (Eq. 16), else 0
+    const float2* tab;
     int K;
-    double zo;              // observing redshift
     int kind;               // radial kernel (LC_KERNEL_*)
-    float klen, kmax;       // LC_KERNEL_EXP parameters
-    float alpha0;           // LW: alpha at 1 + z_s = 21 (Eq. 16)
+    float inv_klen, kmax;   // LC_KERNEL_EXP parameters: 1 / length, cut-off
     const double* f0;       // the shell's normalisation factor (device)
     const double* slot_S;
     int slot;
