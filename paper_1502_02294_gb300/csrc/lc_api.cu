@@ -198,6 +198,9 @@ struct lc_plan {
     bool near_pm = false;           // near cube from the sources' own positions
     double* d_src_off = nullptr;    // near_pm: positions relative to the cell centres (3 per source)
     long long near_cap = 0, near_n = 0;
+    // near-field lists replaced by larger ones: a captured step graph may still
+    // write and read them, so they stay allocated until the plan is destroyed
+    std::vector<void*> retired;
     size_t bytes = 0;
     int last_pushed = -1;
     bool failed = false;
@@ -343,6 +346,7 @@ void free_all(lc_plan* p) {
     cudaFree(p->d_src_cell);
     cudaFree(p->d_src_q);
     cudaFree(p->d_src_off);
+    for (void* r : p->retired) cudaFree(r);
     for (auto& t : p->tables) {
         cudaFree(t.ghat);
         cudaFree(t.g0);
@@ -531,10 +535,9 @@ lc_status ensure_near(lc_plan* p, long long n) {
         cudaGetLastError();
         return LC_ERR_OOM;
     }
-    cudaFree(p->d_src_cell);
-    cudaFree(p->d_src_q);
-    cudaFree(p->d_src_off);
-    p->bytes -= sizeof(long long) * 2 * p->near_cap + (p->near_pm ? sizeof(double) * 3 * p->near_cap : 0);
+    // graphs captured earlier hold the old lists' addresses: retire, do not free
+    for (void* r : {(void*)p->d_src_cell, (void*)p->d_src_q, (void*)p->d_src_off})
+        if (r) p->retired.push_back(r);
     p->d_src_cell = cell;
     p->d_src_q = q;
     p->d_src_off = off;

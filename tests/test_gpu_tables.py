@@ -74,3 +74,35 @@ def test_graph_pins_its_table():
     p.prepare(0, 8)
     assert p.table_bytes == sum(sizes)
     p.close()
+
+
+def test_graph_keeps_its_near_lists_when_they_grow():
+    # the second graph's step has more sources than the near-field lists the
+    # first graph was captured with: the lists grow, and the first graph must
+    # still replay on the lists it holds
+    w = _w()
+    rng = np.random.default_rng(5)
+    src = []
+    for n in (40, 3000):
+        src.append((rng.uniform(0.0, w.box, (n, 3)), rng.uniform(0.5, 2.0, n)))
+    ref = lc.Plan.from_workload(w)
+    want = []
+    for s, (pos, lum) in enumerate(src):
+        ref.push(s, torch.from_numpy(pos).cuda(), torch.from_numpy(lum).cuda())
+        want.append(ref.field(s).cpu().numpy())
+    ref.close()
+    p = lc.Plan.from_workload(w)
+    dev = [(torch.from_numpy(pos).cuda(), torch.from_numpy(lum).cuda()) for pos, lum in src]
+    outs = [torch.empty((w.n,) * 3, dtype=torch.float32, device="cuda") for _ in src]
+    graphs = [p.graph(s, *dev[s], outs[s]) for s in range(2)]
+    for _ in range(2):
+        p.reset()
+        for g in graphs:
+            g.launch()
+        torch.cuda.synchronize()
+        for s in range(2):
+            got = outs[s].cpu().numpy()
+            assert np.allclose(got, want[s], rtol=1e-6, atol=1e-6 * np.abs(want[s]).max()), s
+    for g in graphs:
+        g.close()
+    p.close()
