@@ -172,6 +172,12 @@ struct lc_plan {
         double rtop = 0, rhi0 = 0, rh = 0;
         int mac_variant = 0;    // MAC_GATHER, MAC_BULK, MAC_WS or MAC_WS2, chosen by the autotuner
         int A = -1;             // -1: not built
+        // the instantaneous field (Eq. 18) sees one slice through every shell:
+        // sum_j Ghat_j as a one-shell table [W][8] and sum_j Ghat_j(0) in FP64,
+        // built on the first lc_instant_field of the step
+        float* gsum = nullptr;
+        double* g0sum = nullptr;
+        int inst_variant = 0;
     };
     std::vector<Table> tables;
     // table budget: 0 = keep every table; else tables of other observing
@@ -352,6 +358,8 @@ void free_all(lc_plan* p) {
         cudaFree(t.g0);
         cudaFree(t.gnear);
         cudaFree(t.pmtab);
+        cudaFree(t.gsum);
+        cudaFree(t.g0sum);
     }
     for (auto& m : p->marks) {
         cudaEventDestroy(m.a);
@@ -552,12 +560,20 @@ size_t table_size(const lc_plan* p, int A) {
            (p->near_pm ? sizeof(float2) * kZsTab : 0);
 }
 
+size_t gsum_size(const lc_plan* p) { return sizeof(float) * 8 * (size_t)p->W + sizeof(double); }
+
 void free_table(lc_plan* p, int s) {
     lc_plan::Table& T = p->tables[s];
     cudaFree(T.ghat);
     cudaFree(T.g0);
     cudaFree(T.gnear);
     cudaFree(T.pmtab);
+    if (T.gsum) {
+        p->table_bytes -= gsum_size(p);
+        p->bytes -= gsum_size(p);
+    }
+    cudaFree(T.gsum);
+    cudaFree(T.g0sum);
     const size_t b = table_size(p, T.A);
     p->table_bytes -= b;
     p->bytes -= b;
@@ -1001,13 +1017,43 @@ static lc_status field_impl(lc_plan* p, int step, float* out, int instant) {
         if (!p->d_out_stage && dalloc(p, &p->d_out_stage, (size_t)N3) != cudaSuccess) return LC_ERR_OOM;
         dout = p->d_out_stage;
     }
-    const lc_plan::Table& T = p->tables[step];
+    lc_plan::Table& T = p->tables[step];
+    lc_plan::Table Ti; // the one-shell view of the instantaneous field
+    if (instant && T.A > 0) {
+        if (!T.gsum) {
+            if (p->capturing) return LC_ERR_INVALID_ARG; // built outside a capture only
+            if (dalloc(p, &T.gsum, (size_t)8 * p->W) != cudaSuccess) return LC_ERR_OOM;
+            if (dalloc(p, &T.g0sum, 1) != cudaSuccess) {
+                cudaFree(T.gsum);
+                p->bytes -= sizeof(float) * 8 * (size_t)p->W;
+                T.gsum = nullptr;
+                return LC_ERR_OOM;
+            }
+            p->table_bytes += gsum_size(p);
+            launch_gsum(p->W, T.A, T.gstride, T.ghat, T.g0, T.gsum, T.g0sum, st);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_fail(p, e);
+            Ti = T;
+            Ti.ghat = T.gsum;
+            Ti.g0 = T.g0sum;
+            Ti.gstride = 8;
+            Ti.A = 1;
+            T.inst_variant = choose_mac_variant(p, Ti, step);
+        }
+        Ti = T;
+        Ti.ghat = T.gsum;
+        Ti.g0 = T.g0sum;
+        Ti.gstride = 8;
+        Ti.A = 1;
+        Ti.mac_variant = T.inst_variant;
+    }
+    const lc_plan::Table& M = (instant && T.A > 0) ? Ti : T;
     if (T.A == 0) {
         e = cudaMemsetAsync(dout, 0, sizeof(float) * N3, st);
     } else {
         {
-            Phase ph(p, LC_PHASE_MAC_X, mac_kernels(p, T.mac_variant));
-            launch_mac(p, T, step, instant, T.mac_variant, p->d_slot_step, p->d_slot_S, p->d_slot_total, st);
+            Phase ph(p, LC_PHASE_MAC_X, mac_kernels(p, M.mac_variant));
+            launch_mac(p, M, step, instant, M.mac_variant, p->d_slot_step, p->d_slot_S, p->d_slot_total, st);
         }
         ColArgs c{};
         c.dir = 1;

@@ -207,6 +207,24 @@ __global__ void __launch_bounds__(256) k_rgf_norm(int N, long long W, int A, con
 }
 
 
+// One-shell table of the instantaneous field: sum_j Ghat_j per wedge row.
+__global__ void __launch_bounds__(256) k_gsum(long long W, int A, int gstride, const float* __restrict__ ghat,
+                                              const double* __restrict__ g0, float* __restrict__ gsum,
+                                              double* __restrict__ g0sum) {
+    const long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w < W) {
+        double s = 0.0;
+        for (int j = 0; j < A; ++j) s += (double)ghat[w * gstride + j];
+        gsum[8 * w] = (float)s;
+        for (int c = 1; c < 8; ++c) gsum[8 * w + c] = 0.0f;
+    }
+    if (w == 0) {
+        double d = 0.0;
+        for (int j = 0; j < A; ++j) d += g0[j];
+        *g0sum = d;
+    }
+}
+
 __global__ void k_near_prep(const double* gw0, const double* scale0, double* gnear, double* g0_far) {
     // one thread: the near cube is (2R+1)^3 = 125 cells
     const int Wn = (kNearR + 1) * (kNearR + 2) * (kNearR + 3) / 6;
@@ -371,6 +389,13 @@ void launch_near_pm(const NearPmArgs& a, double* acc, cudaStream_t st) {
     const long long total = a.n * kNearCube;
     if (total <= 0) return;
     launch_k(k_near_pm, (unsigned)((total + 255) / 256), 256, 0, st, a, acc);
+}
+
+void launch_gsum(long long W, int A, int gstride, const float* ghat, const double* g0, float* gsum, double* g0sum,
+                 cudaStream_t st) {
+    if (W <= 0) return;
+    const long long blocks = (W + 255) / 256;
+    k_gsum<<<(unsigned)blocks, 256, 0, st>>>(W, A, gstride, ghat, g0, gsum, g0sum);
 }
 
 void launch_near_prep(const double* gw0, const double* scale0, double* gnear, double* g0_far, cudaStream_t st) {

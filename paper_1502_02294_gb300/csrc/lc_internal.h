@@ -91,6 +91,11 @@ struct NearPmArgs {
     double U_out;
 };
 void launch_near_pm(const NearPmArgs& a, double* acc, cudaStream_t st);
+// sum over the A shells of a step's Ghat table ([W][gstride] FP32, summed in
+// FP64 and rounded once) into column 0 of gsum [W][8] (other columns 0), and
+// of the FP64 k = 0 values g0[A] into *g0sum
+void launch_gsum(long long W, int A, int gstride, const float* ghat, const double* g0, float* gsum, double* g0sum,
+                 cudaStream_t st);
 // scatter U * S * q * G(d) into the FP64 accumulator for every source and d
 void launch_near_scatter(const long long* cell, const long long* q, long long n, int N, const double* gnear,
                          const double* slot_S, int slot, double U, double* acc, cudaStream_t st);

@@ -62,3 +62,30 @@ def test_fdiff_zero_cells_and_argument_errors():
     host = np.zeros(4, dtype=np.float32)
     with pytest.raises(lc.LCError):
         lc._check(lc._lib().lc_fdiff_map(4, host.ctypes.data, host.ctypes.data, host.ctypes.data, None), "lc_fdiff_map")
+
+
+@pytest.mark.parametrize("hist,tol", [(synth.HISTORY_FP32, 1e-5), (synth.HISTORY_BF16, 5e-3)])
+def test_instant_field_many_shells(hist, tol):
+    # Eq. 18 through ten shells: every shell sees the observing step's sources
+    st = synth.StepSpec(synth.STEPS_EQUAL_TAU, 14, z_end=15.0, n_shell=10)
+    cat = synth.make_catalogue(4242, 150, 60.0, 14, clustered=True, n_centres=5, sigma=3.0, lum_kind="lognormal",
+                               life=(1, 3))
+    w = synth.Workload("ten-shells", 32, 60.0, 0.31, 0.68, st, 4, hist, cat)
+    P = oracle.Problem.from_workload(w)
+    plan = lc.Plan.from_workload(w)
+    for s in range(14):
+        pos, lum = w.cat.active(s)
+        plan.push(s, torch.from_numpy(pos).cuda(), torch.from_numpy(lum).cuda())
+        if s in (9, 13):
+            assert len(plan.shells(s)[0]) == 10
+            Ji = plan.instant_field(s).cpu().numpy()
+            ref_i = oracle.instant_field_for(P, w.cat, s)
+            rel = np.linalg.norm(Ji - ref_i) / np.linalg.norm(ref_i)
+            assert rel <= tol, (s, rel)
+            # a second call reuses the step's summed table: the same field
+            assert np.array_equal(plan.instant_field(s).cpu().numpy(), Ji)
+            # and the retarded field of the step is unchanged by it
+            J = plan.field(s).cpu().numpy()
+            ref = oracle.field_for(P, w.cat, s)
+            assert np.linalg.norm(J - ref) / np.linalg.norm(ref) <= tol
+    plan.close()
