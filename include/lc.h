@@ -149,6 +149,25 @@ lc_status lc_push_sources(lc_plan* plan, int step, int64_t n_src, const double* 
  * `out` it only enqueues work on the plan's stream. */
 lc_status lc_retarded_field(lc_plan* plan, int step, float* out);
 
+/* lc_retarded_field without the wait: the same field of the same step (same
+ * rules), but with a host `out` the call returns once the work and the
+ * device-to-host copy are enqueued, and *ticket (> 0) names that copy.  The
+ * copy runs on a copy stream of the plan, out of one of two device stages,
+ * so the next steps' pushes and fields compute while it drains; `out` holds
+ * the field once lc_plan_wait(plan, *ticket) returns, and must stay valid
+ * until then (page-locked host memory makes the copy asynchronous; with
+ * pageable memory the call itself waits for the copy).  With a device `out`
+ * this is lc_retarded_field and *ticket = 0.
+ * Errors: LC_ERR_INVALID_ARG for ticket == NULL or a host `out` inside a
+ * graph capture, otherwise those of lc_retarded_field. */
+lc_status lc_retarded_field_async(lc_plan* plan, int step, float* out, uint64_t* ticket);
+
+/* Block the calling thread until the output named by `ticket` is in host
+ * memory (ticket 0: until the plan's stream is idle).  Waiting on an older
+ * ticket than the last is allowed; a ticket never issued is
+ * LC_ERR_INVALID_ARG. */
+lc_status lc_plan_wait(lc_plan* plan, uint64_t ticket);
+
 /* The same field computed "instantaneously" (action at a distance, Eq. 18 of
  * Section 3): every shell's Green's function is applied to the sources of
  * step `step` itself, i.e. the source distribution frozen at the observing

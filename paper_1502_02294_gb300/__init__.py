@@ -82,6 +82,8 @@ SIGNATURES = [
     ("lc_push_sources", _I, [_P, _I, _I64, _VP, _VP]),
     ("lc_retarded_field", _I, [_P, _I, _VP]),
     ("lc_instant_field", _I, [_P, _I, _VP]),
+    ("lc_retarded_field_async", _I, [_P, _I, _VP, ctypes.POINTER(ctypes.c_uint64)]),
+    ("lc_plan_wait", _I, [_P, ctypes.c_uint64]),
     ("lc_plan_reset", _I, [_P]),
     ("lc_plan_check", _I, [_P]),
     ("lc_plan_set_stream", _I, [_P, _VP]),
@@ -276,6 +278,25 @@ class Plan:
             ptr = out.data_ptr()
         _check(_lib().lc_retarded_field(self._h, int(step), ptr), "lc_retarded_field")
         return out
+
+    def field_async(self, step: int, out) -> int:
+        """Enqueue the retarded field of `step` into `out` and return a ticket.
+        A host `out` (numpy, or a pinned torch CPU tensor) is filled by a copy
+        that overlaps the next steps' work: read it only after wait(ticket).
+        A CUDA `out` is stream-ordered (ticket 0)."""
+        if isinstance(out, np.ndarray):
+            assert out.dtype == np.float32 and out.flags.c_contiguous and out.size == self.n ** 3
+            ptr = out.ctypes.data
+        else:
+            assert out.dtype.itemsize == 4 and out.is_contiguous() and out.numel() == self.n ** 3
+            ptr = out.data_ptr()
+        t = ctypes.c_uint64()
+        _check(_lib().lc_retarded_field_async(self._h, int(step), ptr, ctypes.byref(t)), "lc_retarded_field_async")
+        return int(t.value)
+
+    def wait(self, ticket: int):
+        """Block until the output of `ticket` (from field_async) is in place."""
+        _check(_lib().lc_plan_wait(self._h, int(ticket)), "lc_plan_wait")
 
     def instant_field(self, step: int, out=None):
         """Action-at-a-distance field of Eq. 18: every shell sees the sources

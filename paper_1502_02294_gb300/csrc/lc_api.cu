@@ -161,6 +161,13 @@ struct lc_plan {
     double* d_lum = nullptr;
     long long src_cap = 0;
     float* d_out_stage = nullptr;
+    // asynchronous host output (lc_retarded_field_async): two device stages,
+    // each copied out on a copy stream while the next step computes
+    cudaStream_t copy_stream = nullptr;
+    float* d_out_async[2] = {nullptr, nullptr};
+    cudaEvent_t ev_computed[2] = {nullptr, nullptr}, ev_copied[2] = {nullptr, nullptr};
+    uint64_t tickets = 0;              // tickets issued; ticket t used stage (t - 1) % 2
+    uint64_t stage_ticket[2] = {0, 0}; // the last ticket of each stage
     // Green's function tables, one per observing step (built lazily)
     long long ring_slot = 0; // complex elements per tile-major ring slot: N^2 (N/2 + 1)
     struct Table {
@@ -340,6 +347,13 @@ void free_all(lc_plan* p) {
     cudaFree(p->d_pos);
     cudaFree(p->d_lum);
     cudaFree(p->d_out_stage);
+    if (p->copy_stream) cudaStreamSynchronize(p->copy_stream);
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(p->d_out_async[k]);
+        if (p->ev_computed[k]) cudaEventDestroy(p->ev_computed[k]);
+        if (p->ev_copied[k]) cudaEventDestroy(p->ev_copied[k]);
+    }
+    if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
     cudaFree(p->d_gw);
     cudaFree(p->d_gtab);
     cudaFree(p->d_bnd);
@@ -995,13 +1009,50 @@ lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos
     return LC_OK;
 }
 
-static lc_status field_impl(lc_plan* p, int step, float* out, int instant);
+static lc_status field_impl(lc_plan* p, int step, float* out, int instant, uint64_t* ticket = nullptr);
 
 lc_status lc_retarded_field(lc_plan* p, int step, float* out) { return field_impl(p, step, out, 0); }
 
 lc_status lc_instant_field(lc_plan* p, int step, float* out) { return field_impl(p, step, out, 1); }
 
-static lc_status field_impl(lc_plan* p, int step, float* out, int instant) {
+lc_status lc_retarded_field_async(lc_plan* p, int step, float* out, uint64_t* ticket) {
+    if (!ticket) return LC_ERR_INVALID_ARG;
+    *ticket = 0;
+    return field_impl(p, step, out, 0, ticket);
+}
+
+lc_status lc_plan_wait(lc_plan* p, uint64_t ticket) {
+    if (!p) return LC_ERR_INVALID_ARG;
+    if (ticket > p->tickets) return LC_ERR_INVALID_ARG;
+    cudaError_t e;
+    if (ticket == 0) {
+        e = cudaStreamSynchronize(p->stream);
+    } else {
+        // a stage re-used by a later ticket has an event that completes later
+        // still: waiting on it is correct, only later than needed
+        const int k = (int)((ticket - 1) % 2);
+        e = cudaEventSynchronize(p->ev_copied[k]);
+    }
+    return e == cudaSuccess ? LC_OK : cuda_fail(p, e);
+}
+
+// the stage an asynchronous host output computes into: waits (on the plan's
+// stream) for the copy that last read it
+static cudaError_t async_stage(lc_plan* p, int& k) {
+    const long long N3 = p->N * p->N * p->N;
+    k = (int)(p->tickets % 2);
+    cudaError_t e = cudaSuccess;
+    if (!p->copy_stream) e = cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        if (!p->ev_computed[i]) e = cudaEventCreateWithFlags(&p->ev_computed[i], cudaEventDisableTiming);
+        if (e == cudaSuccess && !p->ev_copied[i]) e = cudaEventCreateWithFlags(&p->ev_copied[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess && !p->d_out_async[k]) e = dalloc(p, &p->d_out_async[k], (size_t)N3);
+    if (e == cudaSuccess && p->stage_ticket[k]) e = cudaStreamWaitEvent(p->stream, p->ev_copied[k], 0);
+    return e;
+}
+
+static lc_status field_impl(lc_plan* p, int step, float* out, int instant, uint64_t* ticket) {
     if (!p || !out) return LC_ERR_INVALID_ARG;
     if (p->failed) return LC_ERR_CUDA;
     if (step < 0 || step >= p->n_steps) return LC_ERR_INVALID_ARG;
@@ -1011,9 +1062,17 @@ static lc_status field_impl(lc_plan* p, int step, float* out, int instant) {
     cudaStream_t st = p->stream;
     const long long N = p->N, N3 = N * N * N;
     const bool dev_out = is_device_ptr(out);
+    const bool async_out = ticket && !dev_out;
+    if (async_out && p->capturing) return LC_ERR_INVALID_ARG; // a graph holds device pointers only
     float* dout = out;
     cudaError_t e = cudaSuccess;
-    if (!dev_out) {
+    int stage = 0;
+    if (async_out) {
+        e = async_stage(p, stage);
+        if (e == cudaErrorMemoryAllocation) return LC_ERR_OOM;
+        if (e != cudaSuccess) return cuda_fail(p, e);
+        dout = p->d_out_async[stage];
+    } else if (!dev_out) {
         if (!p->d_out_stage && dalloc(p, &p->d_out_stage, (size_t)N3) != cudaSuccess) return LC_ERR_OOM;
         dout = p->d_out_stage;
     }
@@ -1123,7 +1182,19 @@ static lc_status field_impl(lc_plan* p, int step, float* out, int instant) {
         }
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess && !dev_out) {
+    if (e == cudaSuccess && async_out) {
+        // copy out on the copy stream once computed; the next step's kernels
+        // run meanwhile on the plan's stream
+        e = cudaEventRecord(p->ev_computed[stage], st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(p->copy_stream, p->ev_computed[stage], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(out, dout, sizeof(float) * N3, cudaMemcpyDeviceToHost, p->copy_stream);
+        if (e == cudaSuccess) e = cudaEventRecord(p->ev_copied[stage], p->copy_stream);
+        if (e == cudaSuccess) {
+            *ticket = ++p->tickets;
+            p->stage_ticket[stage] = *ticket;
+        }
+    } else if (e == cudaSuccess && !dev_out) {
         e = cudaMemcpyAsync(out, dout, sizeof(float) * N3, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }

@@ -1,0 +1,67 @@
+"""Asynchronous host output: lc_retarded_field_async returns once the field
+and its device-to-host copy are enqueued, the copy overlapping the next
+steps; lc_plan_wait makes the output readable.  Fields equal the waiting
+call's, with pinned and pageable host buffers, across stage reuse."""
+import numpy as np
+import pytest
+
+import paper_1502_02294_gb300 as lc
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    lc.build()
+
+
+def test_async_outputs_equal_waiting_outputs():
+    w = synth.small(n=32, box=60.0, n_steps=8, n_src=150, seed=2718, clustered=True)
+    a = lc.Plan.from_workload(w)
+    b = lc.Plan.from_workload(w)
+    want = []
+    pinned = [torch.empty((w.n,) * 3, dtype=torch.float32).pin_memory() for _ in range(3)]
+    tickets = []
+    for s in range(8):
+        pos, lum = w.cat.active(s)
+        a.push(s, pos, lum)
+        want.append(a.field(s, np.empty((w.n,) * 3, dtype=np.float32)))
+        b.push(s, pos, lum)
+        tickets.append(b.field_async(s, pinned[s % 3]))
+        assert tickets[-1] == s + 1
+        if s >= 1:  # the previous step's copy, while this one computes
+            b.wait(tickets[s - 1])
+            got = pinned[(s - 1) % 3].numpy()
+            assert np.allclose(got, want[s - 1], rtol=1e-6, atol=1e-6 * np.abs(want[s - 1]).max()), s - 1
+    b.wait(tickets[-1])
+    assert np.allclose(pinned[7 % 3].numpy(), want[7], rtol=1e-6, atol=1e-6 * np.abs(want[7]).max())
+    b.wait(tickets[0])  # an old ticket returns at once
+    with pytest.raises(lc.LCError):
+        b.wait(tickets[-1] + 5)  # never issued
+    a.close()
+    b.close()
+
+
+def test_async_pageable_and_device_outputs():
+    w = synth.small(n=16, box=40.0, n_steps=4, n_src=60, seed=2719)
+    p = lc.Plan.from_workload(w)
+    ref = lc.Plan.from_workload(w)
+    for s in range(4):
+        pos, lum = w.cat.active(s)
+        p.push(s, pos, lum)
+        ref.push(s, pos, lum)
+        want = ref.field(s).cpu().numpy()
+        host = np.empty((w.n,) * 3, dtype=np.float32)  # pageable
+        t = p.field_async(s, host)
+        p.wait(t)
+        assert np.allclose(host, want, rtol=1e-6, atol=1e-6 * np.abs(want).max())
+    dev = torch.empty((w.n,) * 3, dtype=torch.float32, device="cuda")
+    assert p.field_async(3, dev) == 0  # a device output is stream-ordered
+    p.wait(0)
+    assert np.allclose(dev.cpu().numpy(), want, rtol=1e-6, atol=1e-6 * np.abs(want).max())
+    p.close()
+    ref.close()
