@@ -422,6 +422,93 @@ __global__ void __launch_bounds__(col_threads_of(N)) k_cols_pp(ColArgs a, int nt
     }
 }
 
+// Asynchronous global -> shared copies (LDGSTS) for the pipelined passes.
+__device__ __forceinline__ void ldgsts16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(reinterpret_cast<unsigned long long>(src))
+                 : "memory");
+}
+__device__ __forceinline__ void ldgsts8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(reinterpret_cast<unsigned long long>(src))
+                 : "memory");
+}
+__device__ __forceinline__ void ldgsts_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int PENDING> __device__ __forceinline__ void ldgsts_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory");
+}
+
+// The pipelined plain pass (N >= 256): threads (8 elements each) and stages
+// of tiles per CTA, one CTA per SM (measured at 256^3 against 6 stages, and
+// against 3 stages with two CTAs of 256 threads per SM: both slower)
+__host__ __device__ constexpr int cols_pl_threads(int n) { return col_threads_of(n); }
+__host__ __device__ constexpr int cols_pl_stages(int n) { return 4; }
+template <int N> __host__ __device__ constexpr size_t cols_pl_smem_bytes() {
+    return sizeof(float2) * ((size_t)N + (size_t)cols_pl_stages(N) * N * cw_of(N));
+}
+
+// The pipelined persistent plain pass: tiles blockIdx.x, +gridDim.x, ... each copied
+// straight into one of S shared-memory stages (16-byte asynchronous copies,
+// 8-byte ones for the strided Nyquist tiles), S - 1 tiles in flight while
+// one is transformed in place ([N][CW] rows: a half-warp reads one row of
+// 16 complex or two of 8, so the dense layout is free of bank conflicts).
+template <int N, int DIR, int OUT>
+__global__ void __launch_bounds__(cols_pl_threads(N)) k_cols_pl(ColArgs a, int ntiles) {
+    constexpr int NT = cols_pl_threads(N);
+    constexpr int CW = cw_of(N), M = N / 2, S = cols_pl_stages(N);
+    constexpr int TILE = N * CW;
+    static_assert(CW % 2 == 0, "16-byte copies take two columns");
+    extern __shared__ float4 smem_raw[];
+    float2* tw = reinterpret_cast<float2*>(smem_raw);
+    float2* stages = tw + N; // 16-byte aligned: N is even
+    for (int i = threadIdx.x; i < N; i += NT) tw[i] = a.tw[i];
+    auto load = [&](int tile, float2* dst) {
+        const ColGeom<N> g(tile + a.tile0, a.axis);
+        if (!g.nyq) {
+            for (int c = threadIdx.x; c < TILE / 2; c += NT) ldgsts16(dst + 2 * c, a.src + g.at(2 * c));
+        } else {
+            for (int i = threadIdx.x; i < TILE; i += NT) ldgsts8(dst + i, a.src + g.at(i));
+        }
+    };
+#pragma unroll
+    for (int k = 0; k < S - 1; ++k) {
+        const int t = blockIdx.x + k * gridDim.x;
+        if (t < ntiles) load(t, stages + k * TILE);
+        ldgsts_commit();
+    }
+    for (int k = 0;; ++k) {
+        const int tile = blockIdx.x + k * gridDim.x;
+        if (tile >= ntiles) break;
+        // refill the stage that tile k - 1 used (its outputs are written)
+        const int nt = blockIdx.x + (k + S - 1) * gridDim.x;
+        if (nt < ntiles) load(nt, stages + ((k + S - 1) % S) * TILE);
+        ldgsts_commit();
+        ldgsts_wait<S - 1>(); // this thread's copies of tile k have landed
+        __syncthreads();      // and everyone else's
+        float2* buf = stages + (k % S) * TILE;
+        fft_smem<N, DIR, CW, CW, NT>(buf, tw);
+        const ColGeom<N> g(tile + a.tile0, a.axis);
+        for (int idx = threadIdx.x; idx < TILE; idx += NT) {
+            const int t = idx / CW, col = idx % CW;
+            const float2 v = buf[idx];
+            if constexpr (OUT == COL_OUT_PLAIN) {
+                a.dst[g.at(idx)] = v;
+            } else if constexpr (OUT == COL_OUT_BF16) {
+                a.dst_bf16[((long long)(tile + a.tile0) * a.n_ring + a.wslot) * TILE + idx] =
+                    __floats2bfloat162_rn(v.x, v.y);
+            } else if constexpr (OUT == COL_OUT_RING_F32) {
+                a.dst[((long long)(tile + a.tile0) * a.n_ring + a.wslot) * TILE + idx] = v;
+            } else {
+                const int q = g.nyq ? g.line + col : g.line;
+                const int r = g.nyq ? M : g.chunk * CW + col;
+                if (t <= q && q <= r) a.wedge_out[wedge_index(t, q, r) * a.wedge_A + a.wedge_j] = v.x;
+            }
+        }
+        __syncthreads(); // the stage is read out before it is refilled
+    }
+    ldgsts_wait<0>(); // no copy outlives the CTA
+}
+
 // ------------------------------------------------------------------------
 // z rows, complex -> real, persistent with the next block's loads in flight.
 template <int N>
@@ -655,18 +742,47 @@ struct FftOps {
 template <int N> struct Launch {
     static constexpr int CW = cw_of(N), NCH = (N / 2) / CW;
     static int col_tiles() { return N * NCH + N / CW; }
-    // CTAs of a persistent pass: 4 per SM (the SM count is read once per process)
-    static int pp_ctas() {
-        static int sms = 0;
-        if (!sms) {
+    // the SM count, read once per process
+    static int sms() {
+        static int n = 0;
+        if (!n) {
             int dev = 0;
             cudaGetDevice(&dev);
-            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+            if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
                 cudaGetLastError();
-                sms = 148;
+                n = 148;
             }
         }
-        return 4 * sms;
+        return n;
+    }
+    // CTAs of a persistent row pass: 4 per SM
+    static int pp_ctas() { return 4 * sms(); }
+    // the pipelined column pass (N >= 256) or the register-prefetch one
+    static constexpr bool kColsPl = N >= 256;
+    // CTAs of the pipelined column pass: as many as fit on the device at once
+    template <int DIR, int OUT> static int cols_pl_ctas() {
+        static int ctas = 0;
+        if (!ctas) {
+            int occ = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cols_pl<N, DIR, OUT>, cols_pl_threads(N),
+                                                              cols_pl_smem_bytes<N>()) != cudaSuccess || occ <= 0) {
+                cudaGetLastError();
+                occ = 1;
+            }
+            ctas = occ * sms();
+        }
+        return ctas;
+    }
+    template <int DIR, int OUT> static void cols_plain(const ColArgs& a, int ntiles, cudaStream_t st) {
+        if constexpr (kColsPl) {
+            const int c = cols_pl_ctas<DIR, OUT>();
+            launch_k(k_cols_pl<N, DIR, OUT>, dim3((unsigned)(ntiles < c ? ntiles : c)), cols_pl_threads(N),
+                     cols_pl_smem_bytes<N>(), st, a, ntiles);
+        } else {
+            // persistent: a few CTAs per SM, each walking tiles
+            launch_k(k_cols_pp<N, DIR, OUT>, dim3((unsigned)(ntiles < pp_ctas() ? ntiles : pp_ctas())),
+                     col_threads_of(N), cols_smem_bytes<N>(), st, a, ntiles);
+        }
     }
     static long long row_blocks() { return ((long long)N * N + 2 * row_pairs_of(N) - 1) / (2 * row_pairs_of(N)); }
 
@@ -679,11 +795,20 @@ template <int N> struct Launch {
         LC_ATTR((k_rows_r2c<N, ROW_IN_F32>), rs);
         LC_ATTR((k_rows_r2c<N, ROW_IN_WEDGE>), rs);
         LC_ATTR((k_rows_c2r<N>), rs);
-        LC_ATTR((k_cols_pp<N, -1, COL_OUT_PLAIN>), cs);
-        LC_ATTR((k_cols_pp<N, -1, COL_OUT_BF16>), cs);
-        LC_ATTR((k_cols_pp<N, -1, COL_OUT_WEDGE>), cs);
-        LC_ATTR((k_cols_pp<N, -1, COL_OUT_RING_F32>), cs);
-        LC_ATTR((k_cols_pp<N, 1, COL_OUT_PLAIN>), cs);
+        if constexpr (kColsPl) {
+            const int ps2 = (int)cols_pl_smem_bytes<N>();
+            LC_ATTR((k_cols_pl<N, -1, COL_OUT_PLAIN>), ps2);
+            LC_ATTR((k_cols_pl<N, -1, COL_OUT_BF16>), ps2);
+            LC_ATTR((k_cols_pl<N, -1, COL_OUT_WEDGE>), ps2);
+            LC_ATTR((k_cols_pl<N, -1, COL_OUT_RING_F32>), ps2);
+            LC_ATTR((k_cols_pl<N, 1, COL_OUT_PLAIN>), ps2);
+        } else {
+            LC_ATTR((k_cols_pp<N, -1, COL_OUT_PLAIN>), cs);
+            LC_ATTR((k_cols_pp<N, -1, COL_OUT_BF16>), cs);
+            LC_ATTR((k_cols_pp<N, -1, COL_OUT_WEDGE>), cs);
+            LC_ATTR((k_cols_pp<N, -1, COL_OUT_RING_F32>), cs);
+            LC_ATTR((k_cols_pp<N, 1, COL_OUT_PLAIN>), cs);
+        }
         LC_ATTR((k_cols<N, 1, COL_IN_MAC_F32, COL_OUT_PLAIN>), cs);
         LC_ATTR((k_cols<N, 1, COL_IN_MAC_BF16, COL_OUT_PLAIN>), cs);
         if constexpr (plane_ok<N>()) {
@@ -725,15 +850,13 @@ template <int N> struct Launch {
         const size_t sm = cols_smem_bytes<N>();
         constexpr int kThreads = col_threads_of(N);
         const int ntiles = col_tiles() - a.tile0;
-        // persistent plain passes: a few CTAs per SM, each walking tiles
-        const dim3 gp((unsigned)(ntiles < pp_ctas() ? ntiles : pp_ctas()));
         if (a.dir < 0) {
-            if (a.out_mode == COL_OUT_PLAIN) launch_k(k_cols_pp<N, -1, COL_OUT_PLAIN>, gp, kThreads, sm, st, a, ntiles);
-            else if (a.out_mode == COL_OUT_BF16) launch_k(k_cols_pp<N, -1, COL_OUT_BF16>, gp, kThreads, sm, st, a, ntiles);
-            else if (a.out_mode == COL_OUT_RING_F32) launch_k(k_cols_pp<N, -1, COL_OUT_RING_F32>, gp, kThreads, sm, st, a, ntiles);
-            else launch_k(k_cols_pp<N, -1, COL_OUT_WEDGE>, gp, kThreads, sm, st, a, ntiles);
+            if (a.out_mode == COL_OUT_PLAIN) cols_plain<-1, COL_OUT_PLAIN>(a, ntiles, st);
+            else if (a.out_mode == COL_OUT_BF16) cols_plain<-1, COL_OUT_BF16>(a, ntiles, st);
+            else if (a.out_mode == COL_OUT_RING_F32) cols_plain<-1, COL_OUT_RING_F32>(a, ntiles, st);
+            else cols_plain<-1, COL_OUT_WEDGE>(a, ntiles, st);
         } else {
-            if (a.in_mode == COL_IN_PLAIN) launch_k(k_cols_pp<N, 1, COL_OUT_PLAIN>, gp, kThreads, sm, st, a, ntiles);
+            if (a.in_mode == COL_IN_PLAIN) cols_plain<1, COL_OUT_PLAIN>(a, ntiles, st);
             else if (a.in_mode == COL_IN_MAC_F32) launch_k(k_cols<N, 1, COL_IN_MAC_F32, COL_OUT_PLAIN>, g, kThreads, sm, st, a);
             else launch_k(k_cols<N, 1, COL_IN_MAC_BF16, COL_OUT_PLAIN>, g, kThreads, sm, st, a);
         }
