@@ -569,6 +569,141 @@ __global__ void __launch_bounds__(kThreads) k_rows_c2r(RowC2RArgs a, int nblocks
 }
 
 // ------------------------------------------------------------------------
+// Pipelined z passes (N >= 256, where N^2 rows split into whole blocks of B
+// row pairs): the rows of a block are one contiguous run in memory, copied by
+// 16-byte asynchronous copies into one of S shared-memory stages, S - 1 blocks
+// in flight while one is packed into the transform buffer and transformed.
+// Forward: int64 deposit grid or float input (the Green's-function wedge
+// gather stays with k_rows_r2c); inverse: half-spectrum rows of NRP.
+__host__ __device__ constexpr int rows_pl_stages(int n) { return 4; }
+template <int N, int E> __host__ __device__ constexpr size_t rows_pl_stage_bytes() {
+    return (size_t)2 * row_pairs_of(N) * N * E;
+}
+template <int N, int IN> __host__ __device__ constexpr size_t rows_r2c_pl_smem_bytes() {
+    return sizeof(float2) * ((size_t)N + (size_t)N * odd_pad(row_pairs_of(N))) +
+           (size_t)rows_pl_stages(N) * rows_pl_stage_bytes<N, IN == ROW_IN_I64 ? 8 : 4>();
+}
+template <int N> __host__ __device__ constexpr size_t rows_c2r_pl_smem_bytes() {
+    return sizeof(float2) * ((size_t)N + (size_t)N * odd_pad(row_pairs_of(N))) +
+           (size_t)rows_pl_stages(N) * 2 * row_pairs_of(N) * nrp_of(N) * sizeof(float2);
+}
+
+template <int N, int IN>
+__global__ void __launch_bounds__(kThreads) k_rows_r2c_pl(RowR2CArgs a, int nblocks) {
+    constexpr int B = row_pairs_of(N), BP = odd_pad(B), NRP = nrp_of(N), H = N / 2 + 1, S = rows_pl_stages(N);
+    constexpr int E = IN == ROW_IN_I64 ? 8 : 4, R2 = 2 * B;
+    constexpr int SB = (int)rows_pl_stage_bytes<N, E>(), CH = SB / 16;
+    static_assert(IN != ROW_IN_WEDGE && (N * N) % R2 == 0 && SB % 16 == 0, "whole contiguous blocks");
+    extern __shared__ float4 smem_raw[];
+    float2* tw = reinterpret_cast<float2*>(smem_raw);
+    float2* buf = tw + N;
+    unsigned char* stages = reinterpret_cast<unsigned char*>(buf + N * BP); // 16-byte aligned
+    float scale = 1.0f;
+    if constexpr (IN == ROW_IN_I64) {
+        // as k_rows_r2c: S per unit (FP32 history), 1 / total (BF16 history)
+        const double Su = a.slot_S[a.slot];
+        const long long tot = a.slot_total[a.slot];
+        scale = a.bf16 ? (tot > 0 ? (float)(1.0 / (double)tot) : 0.0f) : (float)Su;
+    }
+    const unsigned char* src = IN == ROW_IN_I64 ? reinterpret_cast<const unsigned char*>(a.grid)
+                                                : reinterpret_cast<const unsigned char*>(a.fin);
+    auto load = [&](int blk, unsigned char* dst) {
+        const unsigned char* s = src + (size_t)blk * SB;
+        for (int c = threadIdx.x; c < CH; c += kThreads) ldgsts16(dst + 16 * c, s + 16 * c);
+    };
+    for (int i = threadIdx.x; i < N; i += kThreads) tw[i] = a.tw[i];
+#pragma unroll
+    for (int k = 0; k < S - 1; ++k) {
+        const int b = blockIdx.x + k * gridDim.x;
+        if (b < nblocks) load(b, stages + k * SB);
+        ldgsts_commit();
+    }
+    float* bf = reinterpret_cast<float*>(buf);
+    for (int k = 0;; ++k) {
+        const int blk = blockIdx.x + k * gridDim.x;
+        if (blk >= nblocks) break;
+        const int nb = blockIdx.x + (k + S - 1) * gridDim.x;
+        if (nb < nblocks) load(nb, stages + ((k + S - 1) % S) * SB);
+        ldgsts_commit();
+        ldgsts_wait<S - 1>();
+        __syncthreads(); // block k has landed; the previous block has left buf
+        const unsigned char* st = stages + (k % S) * SB;
+        for (int idx = threadIdx.x; idx < R2 * N; idx += kThreads) {
+            const int rr = idx / N, t = idx % N;
+            float v;
+            if constexpr (IN == ROW_IN_I64) v = __ll2float_rn(reinterpret_cast<const long long*>(st)[idx]) * scale;
+            else v = reinterpret_cast<const float*>(st)[idx];
+            bf[2 * (t * BP + (rr >> 1)) + (rr & 1)] = v; // row pair rr/2, real / imaginary part
+        }
+        __syncthreads();
+        fft_smem<N, -1, B, BP>(buf, tw);
+        const long long row0 = (long long)blk * R2;
+        for (int idx = threadIdx.x; idx < R2 * H; idx += kThreads) {
+            const int rr = idx / H, kk = idx % H;
+            const int pair = rr >> 1;
+            const float2 zk = buf[kk * BP + pair];
+            const float2 zn = buf[(kk == 0 ? 0 : N - kk) * BP + pair];
+            float2 x;
+            if ((rr & 1) == 0) x = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
+            else x = make_float2(0.5f * (zk.y + zn.y), 0.5f * (zn.x - zk.x));
+            a.dst[(row0 + rr) * NRP + kk] = x;
+        }
+        __syncthreads(); // buf and the stage are free again
+    }
+    ldgsts_wait<0>();
+}
+
+template <int N>
+__global__ void __launch_bounds__(kThreads) k_rows_c2r_pl(RowC2RArgs a, int nblocks) {
+    constexpr int B = row_pairs_of(N), BP = odd_pad(B), NRP = nrp_of(N), H = N / 2 + 1, S = rows_pl_stages(N);
+    constexpr int R2 = 2 * B, SE = R2 * NRP, CH = SE / 2; // stage elements, 16-byte chunks
+    static_assert((N * N) % R2 == 0 && NRP % 2 == 0, "whole contiguous blocks");
+    extern __shared__ float4 smem_raw[];
+    float2* tw = reinterpret_cast<float2*>(smem_raw);
+    float2* buf = tw + N;
+    float2* stages = buf + N * BP;
+    auto load = [&](int blk, float2* dst) {
+        const float2* s = a.src + (size_t)blk * SE;
+        for (int c = threadIdx.x; c < CH; c += kThreads) ldgsts16(dst + 2 * c, s + 2 * c);
+    };
+    for (int i = threadIdx.x; i < N; i += kThreads) tw[i] = a.tw[i];
+#pragma unroll
+    for (int k = 0; k < S - 1; ++k) {
+        const int b = blockIdx.x + k * gridDim.x;
+        if (b < nblocks) load(b, stages + k * SE);
+        ldgsts_commit();
+    }
+    for (int k = 0;; ++k) {
+        const int blk = blockIdx.x + k * gridDim.x;
+        if (blk >= nblocks) break;
+        const int nb = blockIdx.x + (k + S - 1) * gridDim.x;
+        if (nb < nblocks) load(nb, stages + ((k + S - 1) % S) * SE);
+        ldgsts_commit();
+        ldgsts_wait<S - 1>();
+        __syncthreads();
+        const float2* st = stages + (k % S) * SE;
+        // Z_k = X_a(k) + i X_b(k), with the Hermitian extension X(N-k) = conj X(k)
+        for (int idx = threadIdx.x; idx < B * H; idx += kThreads) {
+            const int pair = idx / H, kk = idx % H;
+            float2 A = st[(2 * pair) * NRP + kk], Bv = st[(2 * pair + 1) * NRP + kk];
+            if (kk == 0 || kk == N / 2) { A.y = 0.f; Bv.y = 0.f; }
+            buf[kk * BP + pair] = make_float2(A.x - Bv.y, A.y + Bv.x);
+            if (kk > 0 && kk < N / 2) buf[(N - kk) * BP + pair] = make_float2(A.x + Bv.y, Bv.x - A.y);
+        }
+        __syncthreads();
+        fft_smem<N, 1, B, BP>(buf, tw);
+        const long long row0 = (long long)blk * R2;
+        for (int idx = threadIdx.x; idx < R2 * N; idx += kThreads) {
+            const int rr = idx / N, t = idx % N;
+            const float2 v = buf[t * BP + (rr >> 1)];
+            a.out[(row0 + rr) * N + t] = ((rr & 1) ? v.y : v.x) * a.scale;
+        }
+        __syncthreads();
+    }
+    ldgsts_wait<0>();
+}
+
+// ------------------------------------------------------------------------
 // Plane kernels (grids whose half plane fits in shared memory, N <= 192):
 // one CTA per x-plane does the z and y axes of the forward (or inverse)
 // transform in shared memory, replacing two full passes through memory.
@@ -773,16 +908,19 @@ template <int N> struct Launch {
         }
         return ctas;
     }
+    static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
     template <int DIR, int OUT> static void cols_plain(const ColArgs& a, int ntiles, cudaStream_t st) {
         if constexpr (kColsPl) {
-            const int c = cols_pl_ctas<DIR, OUT>();
-            launch_k(k_cols_pl<N, DIR, OUT>, dim3((unsigned)(ntiles < c ? ntiles : c)), cols_pl_threads(N),
-                     cols_pl_smem_bytes<N>(), st, a, ntiles);
-        } else {
-            // persistent: a few CTAs per SM, each walking tiles
-            launch_k(k_cols_pp<N, DIR, OUT>, dim3((unsigned)(ntiles < pp_ctas() ? ntiles : pp_ctas())),
-                     col_threads_of(N), cols_smem_bytes<N>(), st, a, ntiles);
+            if (aligned16(a.src)) { // 16-byte copies need a 16-byte aligned source
+                const int c = cols_pl_ctas<DIR, OUT>();
+                launch_k(k_cols_pl<N, DIR, OUT>, dim3((unsigned)(ntiles < c ? ntiles : c)), cols_pl_threads(N),
+                         cols_pl_smem_bytes<N>(), st, a, ntiles);
+                return;
+            }
         }
+        // persistent: a few CTAs per SM, each walking tiles
+        launch_k(k_cols_pp<N, DIR, OUT>, dim3((unsigned)(ntiles < pp_ctas() ? ntiles : pp_ctas())), col_threads_of(N),
+                 cols_smem_bytes<N>(), st, a, ntiles);
     }
     static long long row_blocks() { return ((long long)N * N + 2 * row_pairs_of(N) - 1) / (2 * row_pairs_of(N)); }
 
@@ -795,6 +933,12 @@ template <int N> struct Launch {
         LC_ATTR((k_rows_r2c<N, ROW_IN_F32>), rs);
         LC_ATTR((k_rows_r2c<N, ROW_IN_WEDGE>), rs);
         LC_ATTR((k_rows_c2r<N>), rs);
+        if constexpr (kRowsPl) {
+            const int r64 = (int)rows_r2c_pl_smem_bytes<N, ROW_IN_I64>(), r32 = (int)rows_r2c_pl_smem_bytes<N, ROW_IN_F32>();
+            LC_ATTR((k_rows_r2c_pl<N, ROW_IN_I64>), r64);
+            LC_ATTR((k_rows_r2c_pl<N, ROW_IN_F32>), r32);
+            LC_ATTR((k_rows_c2r_pl<N>), (int)rows_c2r_pl_smem_bytes<N>());
+        }
         if constexpr (kColsPl) {
             const int ps2 = (int)cols_pl_smem_bytes<N>();
             LC_ATTR((k_cols_pl<N, -1, COL_OUT_PLAIN>), ps2);
@@ -833,8 +977,31 @@ template <int N> struct Launch {
     static void plane_c2r(const RowC2RArgs& a, cudaStream_t st) {
         if constexpr (plane_ok<N>()) launch_k(k_plane_c2r<N>, N, plane_threads_of(N), plane_smem_bytes<N>(), st, a);
     }
+    static constexpr bool kRowsPl = N >= 256;
+    template <class Kern> static int occ_ctas(Kern k, size_t smem) {
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kThreads, smem) != cudaSuccess || occ <= 0) {
+            cudaGetLastError();
+            occ = 1;
+        }
+        return occ * sms();
+    }
     static void rows_r2c(const RowR2CArgs& a, cudaStream_t st) {
         const int nb = (int)row_blocks();
+        if constexpr (kRowsPl) {
+            if (a.in_mode == ROW_IN_I64 && aligned16(a.grid)) {
+                static const int c = occ_ctas(k_rows_r2c_pl<N, ROW_IN_I64>, rows_r2c_pl_smem_bytes<N, ROW_IN_I64>());
+                launch_k(k_rows_r2c_pl<N, ROW_IN_I64>, dim3((unsigned)(nb < c ? nb : c)), kThreads,
+                         rows_r2c_pl_smem_bytes<N, ROW_IN_I64>(), st, a, nb);
+                return;
+            }
+            if (a.in_mode == ROW_IN_F32 && aligned16(a.fin)) {
+                static const int c = occ_ctas(k_rows_r2c_pl<N, ROW_IN_F32>, rows_r2c_pl_smem_bytes<N, ROW_IN_F32>());
+                launch_k(k_rows_r2c_pl<N, ROW_IN_F32>, dim3((unsigned)(nb < c ? nb : c)), kThreads,
+                         rows_r2c_pl_smem_bytes<N, ROW_IN_F32>(), st, a, nb);
+                return;
+            }
+        }
         const dim3 g((unsigned)(nb < pp_ctas() ? nb : pp_ctas()));
         const size_t sm = rows_smem_bytes<N>();
         if (a.in_mode == ROW_IN_I64) launch_k(k_rows_r2c<N, ROW_IN_I64>, g, kThreads, sm, st, a, nb);
@@ -843,6 +1010,14 @@ template <int N> struct Launch {
     }
     static void rows_c2r(const RowC2RArgs& a, cudaStream_t st) {
         const int nb = (int)row_blocks();
+        if constexpr (kRowsPl) {
+            if (aligned16(a.src)) {
+                static const int c = occ_ctas(k_rows_c2r_pl<N>, rows_c2r_pl_smem_bytes<N>());
+                launch_k(k_rows_c2r_pl<N>, dim3((unsigned)(nb < c ? nb : c)), kThreads, rows_c2r_pl_smem_bytes<N>(), st,
+                         a, nb);
+                return;
+            }
+        }
         launch_k(k_rows_c2r<N>, (unsigned)(nb < pp_ctas() ? nb : pp_ctas()), kThreads, rows_smem_bytes<N>(), st, a, nb);
     }
     static void cols(const ColArgs& a, cudaStream_t st) {
