@@ -954,7 +954,7 @@ lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos
         if (e != cudaSuccess) return cuda_fail(p, e);
         launch_src_prep(dpos, dlum, n_src, p->d_maxbits, p->d_err, m, st);
         if (n_src > 0)
-            launch_deposit(dpos, dlum, n_src, p->N, p->l, p->d_maxbits, p->d_grid, m, st,
+            launch_deposit(dpos, dlum, n_src, p->N, p->l, p->d_maxbits, p->d_grid, m, p->d_err, st,
                            p->near_on ? p->d_src_cell : nullptr, p->near_on ? p->d_src_q : nullptr,
                            p->near_pm ? p->d_src_off : nullptr);
     }
@@ -1785,7 +1785,7 @@ lc_status lc_deposit_grid(int n, double box, int64_t n_src, const double* pos, c
     SlotMeta m{0, 0, dstep, dS, dtot};
     if (e == cudaSuccess) {
         launch_src_prep(dpos, dlum, n_src, dmax, derr, m, st);
-        if (n_src > 0) launch_deposit(dpos, dlum, n_src, n, box / n, dmax, dgrid, m, st);
+        if (n_src > 0) launch_deposit(dpos, dlum, n_src, n, box / n, dmax, dgrid, m, derr, st);
         count_launch(n_src > 0 ? 2 : 1);
         e = cudaGetLastError();
     }

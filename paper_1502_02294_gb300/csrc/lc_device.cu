@@ -32,15 +32,23 @@ __global__ void __launch_bounds__(kPrepThreads)
     __shared__ int s_bad;
     if (threadIdx.x == 0) s_bad = 0;
     __syncthreads();
+    // the luminosities only (positions are checked where they are used, in
+    // k_deposit), four loads in flight per thread
     unsigned long long mx = 0;
     int bad = 0;
-    for (long long i = threadIdx.x; i < n; i += kPrepThreads) {
-        const double L = lum[i];
-        const bool ok = finite_d(L) && L >= 0.0 && finite_d(pos[3 * i]) && finite_d(pos[3 * i + 1]) &&
-                        finite_d(pos[3 * i + 2]);
-        if (!ok) bad = 1;
-        // non-negative doubles order like their bit patterns
-        else mx = max(mx, (unsigned long long)__double_as_longlong(L));
+    for (long long i0 = threadIdx.x; i0 < n; i0 += 4 * kPrepThreads) {
+        double L[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const long long i = i0 + (long long)u * kPrepThreads;
+            L[u] = i < n ? lum[i] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (!(finite_d(L[u]) && L[u] >= 0.0)) bad = 1;
+            // non-negative doubles order like their bit patterns
+            else mx = max(mx, (unsigned long long)__double_as_longlong(L[u]));
+        }
     }
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = mx;
@@ -68,7 +76,7 @@ __device__ __forceinline__ long long ngp_cell(double x, double l, int N) {
 
 __global__ void __launch_bounds__(256)
     k_deposit(const double* __restrict__ pos, const double* __restrict__ lum, long long n, int N, double l,
-              const unsigned long long* __restrict__ maxbits, long long* __restrict__ grid, SlotMeta m,
+              const unsigned long long* __restrict__ maxbits, long long* __restrict__ grid, SlotMeta m, int* err,
               long long* __restrict__ cell_out, long long* __restrict__ q_out, double* __restrict__ off_out) {
     __shared__ long long s_sum[8];
     const double lmax = __longlong_as_double((long long)*maxbits);
@@ -89,6 +97,8 @@ __global__ void __launch_bounds__(256)
             q = llrint(__ddiv_rn(L, S));
             c = (ngp_cell(x, l, N) * N + ngp_cell(y, l, N)) * N + ngp_cell(z, l, N);
             if (q) atomicAdd(reinterpret_cast<unsigned long long*>(grid + c), (unsigned long long)q);
+        } else {
+            atomicOr(err, 1); // an invalid source is left out and reported
         }
         if (cell_out) {
             cell_out[i] = c;
@@ -422,10 +432,11 @@ void launch_src_prep(const double* pos, const double* lum, long long n, unsigned
 }
 
 void launch_deposit(const double* pos, const double* lum, long long n, int N, double l,
-                    const unsigned long long* maxbits, long long* grid, SlotMeta m, cudaStream_t st,
+                    const unsigned long long* maxbits, long long* grid, SlotMeta m, int* err, cudaStream_t st,
                     long long* cell_out, long long* q_out, double* off_out) {
     const long long blocks = n > 0 ? (n + 255) / 256 : 1;
-    launch_k(k_deposit, (unsigned)blocks, 256, 0, st, pos, lum, n, N, l, maxbits, grid, m, cell_out, q_out, off_out);
+    launch_k(k_deposit, (unsigned)blocks, 256, 0, st, pos, lum, n, N, l, maxbits, grid, m, err, cell_out, q_out,
+             off_out);
 }
 
 // f_diff = (J_instant - J) / J, the difference taken and divided in FP64 and

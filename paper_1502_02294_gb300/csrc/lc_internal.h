@@ -51,14 +51,17 @@ struct SlotMeta {
     double* slot_S;
     long long* slot_total;
 };
-// Validates sources and records max(lum) bits; marks the slot (step, total = 0).
+// Checks the luminosities (finite, >= 0; a bad one sets *err) and records the
+// bits of their maximum; marks the slot (step, total = 0).
 void launch_src_prep(const double* pos, const double* lum, long long n, unsigned long long* maxbits, int* err,
                      SlotMeta m, cudaStream_t st);
-// Fixed-point NGP deposit into grid (int64, pre-zeroed), total into slot_total.
-// cell_out / q_out (may be null): each source's flat cell index and integer
-// luminosity, kept for the near-field correction of the innermost shell.
+// Fixed-point NGP deposit into grid (int64, pre-zeroed), total into slot_total;
+// a source with a non-finite position or luminosity, or a negative one, is
+// left out and sets *err.  cell_out / q_out (may be null): each source's flat
+// cell index and integer luminosity, kept for the near-field correction of
+// the innermost shell.
 void launch_deposit(const double* pos, const double* lum, long long n, int N, double l,
-                    const unsigned long long* maxbits, long long* grid, SlotMeta m, cudaStream_t st,
+                    const unsigned long long* maxbits, long long* grid, SlotMeta m, int* err, cudaStream_t st,
                     long long* cell_out = nullptr, long long* q_out = nullptr, double* off_out = nullptr);
 
 // Near field of the innermost shell (displacements |d|_inf <= R), which the

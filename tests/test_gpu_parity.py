@@ -339,3 +339,24 @@ def test_fft_sources_not_16_byte_aligned():
     assert spec.data_ptr() % 16 == 8
     back = lc.fft_c2r(spec)
     assert torch.equal(back, lc.fft_c2r(X.clone()))
+
+
+def test_device_source_with_bad_position_is_reported_and_left_out():
+    w = synth.config("c1")
+    pos, lum = w.cat.active(0)
+    bad = pos.copy()
+    bad[0, 1] = np.inf
+    a = lc.Plan.from_workload(w)
+    a.push(0, torch.from_numpy(bad).cuda(), torch.from_numpy(lum).cuda())
+    with pytest.raises(lc.LCError) as e:
+        a.check()
+    assert e.value.status == lc.LC_ERR_DEVICE_CHECK
+    # the other sources are deposited as if the bad one were absent (its
+    # luminosity still counts towards the fixed-point unit, so compare in
+    # relative terms)
+    b = lc.Plan.from_workload(w)
+    b.push(0, pos[1:], lum[1:])
+    ja, jb = a.field(0).cpu().numpy(), b.field(0).cpu().numpy()
+    assert np.linalg.norm(ja - jb) <= 1e-5 * np.linalg.norm(jb)
+    a.close()
+    b.close()
