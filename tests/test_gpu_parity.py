@@ -326,7 +326,7 @@ def test_instant_field_eq18_against_oracle():
 def test_fft_sources_not_16_byte_aligned():
     # the pipelined passes copy 16 bytes at a time; a source that is only
     # 8-byte aligned goes through the register passes, with the same result
-    n = 256
+    n = 384
     rng = np.random.default_rng(77)
     flat = torch.from_numpy(rng.standard_normal(n ** 3 + 2).astype(np.float32)).cuda()
     x = flat[2:].view(n, n, n)
