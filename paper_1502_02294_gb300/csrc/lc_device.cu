@@ -449,6 +449,19 @@ __global__ void __launch_bounds__(256) k_fdiff(long long n, const float* __restr
     }
 }
 
+// Device -> page-locked host copy by the SMs (16-byte stores through the
+// host mapping of the buffer), for the waiting host output path.
+__global__ void __launch_bounds__(256) k_copy_out(long long n4, const float4* __restrict__ src, float4* dst) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+void launch_copy_out(long long n4, const float4* src, float4* dst, int ctas, cudaStream_t st) {
+    if (n4 <= 0) return;
+    const long long need = (n4 + 255) / 256;
+    k_copy_out<<<(unsigned)(need < ctas ? need : ctas), 256, 0, st>>>(n4, src, dst);
+}
+
 void launch_fdiff(long long n, const float* j, const float* j_inst, float* out, cudaStream_t st) {
     if (n <= 0) return;
     const long long blocks = (n + 255) / 256;

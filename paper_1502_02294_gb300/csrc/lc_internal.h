@@ -94,6 +94,8 @@ struct NearPmArgs {
     double U_out;
 };
 void launch_near_pm(const NearPmArgs& a, double* acc, cudaStream_t st);
+// copy n4 float4 from device memory to the device view of page-locked host memory
+void launch_copy_out(long long n4, const float4* src, float4* dst, int ctas, cudaStream_t st);
 // sum over the A shells of a step's Ghat table ([W][gstride] FP32, summed in
 // FP64 and rounded once) into column 0 of gsum [W][8] (other columns 0), and
 // of the FP64 k = 0 values g0[A] into *g0sum

@@ -65,3 +65,20 @@ def test_async_pageable_and_device_outputs():
     assert np.allclose(dev.cpu().numpy(), want, rtol=1e-6, atol=1e-6 * np.abs(want).max())
     p.close()
     ref.close()
+
+
+def test_waiting_field_into_page_locked_host_memory():
+    # a page-locked output is written by the SMs through its device view
+    w = synth.small(n=32, box=60.0, n_steps=4, n_src=100, seed=2720)
+    a = lc.Plan.from_workload(w)
+    b = lc.Plan.from_workload(w)
+    pinned = torch.empty((w.n,) * 3, dtype=torch.float32).pin_memory()
+    for s in range(4):
+        pos, lum = w.cat.active(s)
+        a.push(s, pos, lum)
+        b.push(s, pos, lum)
+        want = a.field(s).cpu().numpy()
+        b.field(s, pinned)
+        assert np.array_equal(pinned.numpy(), want), s
+    a.close()
+    b.close()
