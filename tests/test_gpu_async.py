@@ -82,3 +82,26 @@ def test_waiting_field_into_page_locked_host_memory():
         assert np.array_equal(pinned.numpy(), want), s
     a.close()
     b.close()
+
+
+def test_page_locked_host_inputs():
+    # page-locked sources give the fields of device inputs, and bad values
+    # still fail on the host
+    w = synth.small(n=32, box=60.0, n_steps=4, n_src=120, seed=2721, clustered=True)
+    a = lc.Plan.from_workload(w)
+    b = lc.Plan.from_workload(w)
+    for s in range(4):
+        pos, lum = w.cat.active(s)
+        a.push(s, torch.from_numpy(pos).cuda(), torch.from_numpy(lum).cuda())
+        pp, lp = torch.from_numpy(pos).pin_memory(), torch.from_numpy(lum).pin_memory()
+        b.push(s, pp, lp)
+        assert np.array_equal(b.field(s).cpu().numpy(), a.field(s).cpu().numpy()), s
+    bad = torch.from_numpy(w.cat.active(3)[1].copy()).pin_memory()
+    if bad.numel():
+        bad[0] = -1.0
+        b.reset()
+        with pytest.raises(lc.LCError) as e:
+            b.push(0, torch.from_numpy(w.cat.active(3)[0]).pin_memory(), bad)
+        assert e.value.status == lc.LC_ERR_INVALID_ARG
+    a.close()
+    b.close()
