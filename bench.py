@@ -431,8 +431,9 @@ def max_over_ranks(x, device):
 
 
 def _function_text(src, head):
-    """The text of the function whose definition starts with `head`."""
-    i = src.index(head)
+    """The text of the function whose definition line contains `head`, from
+    the start of that line to the closing brace at the start of a line."""
+    i = src.rfind("\n", 0, src.index(head)) + 1
     return src[i:src.index("\n}\n", i) + 3]
 
 
@@ -446,7 +447,7 @@ def mac_sources_hash():
     with open(os.path.join(d, "lc_kernels.cuh")) as fh:
         k = fh.read()
     h.update(_function_text(k, "__device__ __forceinline__ void mac_slot_list(").encode())
-    h.update(_function_text(k, "__global__ void __launch_bounds__(col_threads_of(N)) k_cols(ColArgs a)").encode())
+    h.update(_function_text(k, " k_cols(ColArgs a) {").encode())
     return h.hexdigest()[:16]
 
 
