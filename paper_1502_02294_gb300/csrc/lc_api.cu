@@ -943,6 +943,10 @@ lc_status lc_plan_prepare(lc_plan* p, int b, int e) {
     return LC_OK;
 }
 
+// Whether the forward z pass clears the deposit grid as it reads it (the
+// staged pass of N >= 256, which the plane kernels of smaller N are not).
+static bool zeroed_by_r2c(const lc_plan* p) { return p->N >= 256 && !p->ops->plane_r2c; }
+
 lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos, const double* lum) {
     if (!p) return LC_ERR_INVALID_ARG;
     if (p->failed) return LC_ERR_CUDA;
@@ -973,7 +977,9 @@ lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos
     const long long N = p->N;
     {
         Phase ph(p, LC_PHASE_DEPOSIT, n_src > 0 ? 2 : 1);
-        e = cudaMemsetAsync(p->d_grid, 0, sizeof(long long) * N * N * N, st);
+        // the staged z pass (N >= 256) leaves the grid zero after reading it;
+        // smaller grids are cleared here
+        if (!zeroed_by_r2c(p)) e = cudaMemsetAsync(p->d_grid, 0, sizeof(long long) * N * N * N, st);
         if (e != cudaSuccess) return cuda_fail(p, e);
         launch_src_prep(dpos, dlum, n_src, p->d_maxbits, p->d_err, m, st);
         if (n_src > 0)
@@ -990,6 +996,7 @@ lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos
     r.slot_total = p->d_slot_total;
     r.slot = slot;
     r.bf16 = p->history == LC_HISTORY_BF16;
+    r.zero_in = zeroed_by_r2c(p) ? 1 : 0;
     r.dst = p->d_work;
     r.tw = p->d_tw;
     ColArgs c{};

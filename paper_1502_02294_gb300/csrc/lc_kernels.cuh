@@ -34,6 +34,7 @@ struct RowR2CArgs {
     const long long* slot_total;
     int slot;
     int bf16;                 // ROW_IN_I64: 1 -> values / (S * total), else * S
+    int zero_in;              // ROW_IN_I64: leave the grid all zero for the next deposit
     const float* fin;         // ROW_IN_F32
     const double* gw;         // ROW_IN_WEDGE: wedge values of one shell (FP64)
     const double* gscale;     // ROW_IN_WEDGE: that shell's normalisation factor
@@ -628,6 +629,13 @@ __global__ void __launch_bounds__(kThreads) k_rows_r2c_pl(RowR2CArgs a, int nblo
         ldgsts_wait<S - 1>();
         __syncthreads(); // block k has landed; the previous block has left buf
         const unsigned char* st = stages + (k % S) * SB;
+        if constexpr (IN == ROW_IN_I64) {
+            // the block's grid cells are read: zero them for the next deposit
+            if (a.zero_in) {
+                int4* g = reinterpret_cast<int4*>(const_cast<long long*>(a.grid)) + (size_t)blk * CH;
+                for (int c = threadIdx.x; c < CH; c += kThreads) g[c] = make_int4(0, 0, 0, 0);
+            }
+        }
         for (int idx = threadIdx.x; idx < R2 * N; idx += kThreads) {
             const int rr = idx / N, t = idx % N;
             float v;
@@ -989,6 +997,13 @@ template <int N> struct Launch {
     static void rows_r2c(const RowR2CArgs& a, cudaStream_t st) {
         const int nb = (int)row_blocks();
         if constexpr (kRowsPl) {
+            if (a.in_mode == ROW_IN_I64 && !aligned16(a.grid) && a.zero_in) {
+                // the register pass does not zero the grid: clear it after
+                launch_k(k_rows_r2c<N, ROW_IN_I64>, dim3((unsigned)(nb < pp_ctas() ? nb : pp_ctas())), kThreads,
+                         rows_smem_bytes<N>(), st, a, nb);
+                cudaMemsetAsync(const_cast<long long*>(a.grid), 0, sizeof(long long) * N * N * N, st);
+                return;
+            }
             if (a.in_mode == ROW_IN_I64 && aligned16(a.grid)) {
                 static const int c = occ_ctas(k_rows_r2c_pl<N, ROW_IN_I64>, rows_r2c_pl_smem_bytes<N, ROW_IN_I64>());
                 launch_k(k_rows_r2c_pl<N, ROW_IN_I64>, dim3((unsigned)(nb < c ? nb : c)), kThreads,
