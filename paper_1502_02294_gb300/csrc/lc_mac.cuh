@@ -284,17 +284,18 @@ __global__ void __launch_bounds__(MacCfg<N, BF16>::NT) k_mac_tma(MacArgs a) {
 
 // ---------------------------------------------------------------------------
 // Warp-specialised form of the same MAC (k_mac_ws).  The CTA has NC consumer
-// threads and one producer warp:
-//  * the producer streams the slices of the CTA's tiles through an S-stage
-//    ring of shared-memory buffers (cp.async.bulk, lane 0) and the Ghat
-//    rows those tiles share in blocks of 4 slices (one 16-byte cp.async per
-//    row, all lanes, completion counted on an mbarrier), double buffered;
+// threads and two producer warps:
+//  * the ring producer streams the slices of the CTA's tiles through an
+//    S-stage ring of shared-memory buffers (cp.async.bulk, lane 0);
+//  * the Ghat producer gathers the Ghat rows those tiles share, in blocks of
+//    4 slices (one 16-byte cp.async per row, all lanes, completion counted on
+//    an mbarrier), double buffered, independently of the ring's progress;
 //  * a consumer thread owns UPT units; a unit is a row pair {p, N - p}
 //    (or {0, N/2}) times 4 consecutive columns, whose elements share the
 //    Ghat values of wedge rows (min(p, N - p), q, r..r+3); the ring data is
 //    read with 128-bit shared loads;
-//  * consumers only wait for data and release buffers; the producer alone
-//    waits for free buffers.  Every wait is bounded.
+//  * consumers only wait for data and release buffers; the producers alone
+//    wait for free buffers.  Every wait is bounded.
 // PAIR = true: a CTA takes the tiles of lines q and N - q (same chunk),
 // whose Ghat rows are the same, so each gathered row serves both and the
 // gather traffic per ring byte halves; lines 0 and N/2 and the Nyquist tiles
@@ -318,7 +319,7 @@ template <int N, bool BF16, bool PAIR> struct MacWsCfg {
     static constexpr int UPT = PAIR && BF16 ? 1 : 2;  // units per consumer thread
     static constexpr int NC = UNITS / UPT;            // consumer threads
     static constexpr int NCW = NC / 32;               // consumer warps
-    static constexpr int NT = NC + 32;                // + the producer warp
+    static constexpr int NT = NC + 64;                // + the ring and the Ghat producer warps
     static constexpr int GROWS = (M + 1) * CW;        // distinct Ghat rows of a tile
     static constexpr int GPLANE = (M + 1) * CG;       // Ghat rows per column residue (col mod 4)
     static constexpr int GBLK_BYTES = GROWS * 16;     // one Ghat block: 4 floats per row
@@ -471,9 +472,26 @@ __global__ void __launch_bounds__(MacWsCfg<N, BF16, PAIR>::NT, 1) k_mac_ws(MacAr
             for (int c = 0; c < 4; ++c) accA[h][k][c] = accB[h][k][c] = make_float2(0.f, 0.f);
 
     if (warp == C::NCW) {
-        // ------------------------------------------------------------ producer
+        // ------------------------------------------------------- ring producer
         const unsigned char* ring0 = static_cast<const unsigned char*>(a.ring) + (size_t)tile[0] * a.n_ring * C::TILE_BYTES;
         const unsigned char* ring1 = static_cast<const unsigned char*>(a.ring) + (size_t)tile[1] * a.n_ring * C::TILE_BYTES;
+        if (lane == 0) {
+            for (int v = 0; v < nv; ++v) {
+                const int st = v % S;
+                if (v >= S) ok = mbar_wait_bounded(smem_u32(&empty[st]), (unsigned)(((v / S) - 1) & 1)) && ok;
+                const unsigned bar = smem_u32(&full[st]);
+                unsigned char* dst0 = stage + (size_t)st * C::STAGE_BYTES;
+                mbar_expect_tx(bar, two ? 2 * C::TILE_BYTES : C::TILE_BYTES);
+                bulk_load(smem_u32(dst0), ring0 + (size_t)s_slot[v] * C::TILE_BYTES, C::TILE_BYTES, bar);
+                if (two)
+                    bulk_load(smem_u32(dst0 + C::TILE_BYTES), ring1 + (size_t)s_slot[v] * C::TILE_BYTES, C::TILE_BYTES,
+                              bar);
+            }
+        }
+        __syncwarp();
+    } else if (warp == C::NCW + 1) {
+        // ------------------------------------------------------- Ghat producer
+        // (runs up to two blocks ahead of the consumers, whatever the ring does)
         for (int gi = 0; gi < nb; ++gi) {
             const int gb = gi & 1;
             if (gi >= 2) ok = mbar_wait_bounded(smem_u32(&gempty[gb]), (unsigned)(((gi >> 1) - 1) & 1)) && ok;
@@ -486,21 +504,6 @@ __global__ void __launch_bounds__(MacWsCfg<N, BF16, PAIR>::NT, 1) k_mac_ws(MacAr
                            gsrc + (size_t)s_wrow[r] * a.gstride);
             }
             cp_async_mbar_arrive(smem_u32(&gfull[gb]));
-            if (lane == 0) {
-                const int vend = gi + 1 < nb ? s_bv0[gi + 1] : nv;
-                for (int v = s_bv0[gi]; v < vend; ++v) {
-                    const int st = v % S;
-                    if (v >= S) ok = mbar_wait_bounded(smem_u32(&empty[st]), (unsigned)(((v / S) - 1) & 1)) && ok;
-                    const unsigned bar = smem_u32(&full[st]);
-                    unsigned char* dst0 = stage + (size_t)st * C::STAGE_BYTES;
-                    mbar_expect_tx(bar, two ? 2 * C::TILE_BYTES : C::TILE_BYTES);
-                    bulk_load(smem_u32(dst0), ring0 + (size_t)s_slot[v] * C::TILE_BYTES, C::TILE_BYTES, bar);
-                    if (two)
-                        bulk_load(smem_u32(dst0 + C::TILE_BYTES), ring1 + (size_t)s_slot[v] * C::TILE_BYTES,
-                                  C::TILE_BYTES, bar);
-                }
-            }
-            __syncwarp();
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
     } else {
