@@ -319,7 +319,8 @@ template <int N, bool BF16, bool PAIR> struct MacWsCfg {
     static constexpr int UPT = PAIR && BF16 ? 1 : 2;  // units per consumer thread
     static constexpr int NC = UNITS / UPT;            // consumer threads
     static constexpr int NCW = NC / 32;               // consumer warps
-    static constexpr int NT = NC + 64;                // + the ring and the Ghat producer warps
+    static constexpr int GW = 2;                      // Ghat producer warps
+    static constexpr int NT = NC + 32 + 32 * GW;      // + the ring and the Ghat producer warps
     static constexpr int GROWS = (M + 1) * CW;        // distinct Ghat rows of a tile
     static constexpr int GPLANE = (M + 1) * CG;       // Ghat rows per column residue (col mod 4)
     static constexpr int GBLK_BYTES = GROWS * 16;     // one Ghat block: 4 floats per row
@@ -431,7 +432,7 @@ __global__ void __launch_bounds__(MacWsCfg<N, BF16, PAIR>::NT, 1) k_mac_ws(MacAr
             mbar_init(smem_u32(&empty[i]), C::NCW);
         }
         for (int i = 0; i < 2; ++i) {
-            mbar_init(smem_u32(&gfull[i]), 32);
+            mbar_init(smem_u32(&gfull[i]), 32 * C::GW);
             mbar_init(smem_u32(&gempty[i]), C::NCW);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -489,16 +490,18 @@ __global__ void __launch_bounds__(MacWsCfg<N, BF16, PAIR>::NT, 1) k_mac_ws(MacAr
             }
         }
         __syncwarp();
-    } else if (warp == C::NCW + 1) {
-        // ------------------------------------------------------- Ghat producer
-        // (runs up to two blocks ahead of the consumers, whatever the ring does)
+    } else if (warp > C::NCW) {
+        // ------------------------------------------------------ Ghat producers
+        // (run up to two blocks ahead of the consumers, whatever the ring does;
+        // GW warps share the rows of a block)
+        const int gl = lane + 32 * (warp - C::NCW - 1);
         for (int gi = 0; gi < nb; ++gi) {
             const int gb = gi & 1;
             if (gi >= 2) ok = mbar_wait_bounded(smem_u32(&gempty[gb]), (unsigned)(((gi >> 1) - 1) & 1)) && ok;
             // Ghat rows of block s_blk[gi]: row (p', col) goes to slot (col % 4) * GPLANE + p' * CG + col / 4
             const float* gsrc = a.ghat + (size_t)s_blk[gi] * kWsGB;
             const unsigned gdst = smem_u32(gsm + (size_t)gb * C::GBLK_BYTES);
-            for (int r = lane; r < GROWS; r += 32) {
+            for (int r = gl; r < GROWS; r += 32 * C::GW) {
                 const int pp = r / CW, col = r % CW;
                 cp_async16(gdst + ((col & 3) * GPLANE + pp * CG + (col >> 2)) * 16,
                            gsrc + (size_t)s_wrow[r] * a.gstride);
