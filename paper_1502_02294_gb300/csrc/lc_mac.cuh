@@ -319,7 +319,7 @@ template <int N, bool BF16, bool PAIR> struct MacWsCfg {
     static constexpr int UPT = PAIR && BF16 ? 1 : 2;  // units per consumer thread
     static constexpr int NC = UNITS / UPT;            // consumer threads
     static constexpr int NCW = NC / 32;               // consumer warps
-    static constexpr int GW = 2;                      // Ghat producer warps
+    static constexpr int GW = BF16 && PAIR ? 3 : 2;   // Ghat producer warps
     static constexpr int NT = NC + 32 + 32 * GW;      // + the ring and the Ghat producer warps
     static constexpr int GROWS = (M + 1) * CW;        // distinct Ghat rows of a tile
     static constexpr int GPLANE = (M + 1) * CG;       // Ghat rows per column residue (col mod 4)
