@@ -362,6 +362,68 @@ __device__ __forceinline__ float2 bf2_to_f2(unsigned w) {
     return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
 }
 
+// mac_slot_list over the whole CTA: warp w takes rounds of 32 slices w,
+// w + NW, ..., all of whose metadata loads are issued at once, instead of
+// one warp walking the rounds.  The compaction keeps increasing lookback j,
+// and the FP64 k = 0 sum adds the same per-round partials (lane 0 of each
+// round's shuffle tree) in the same round order, so the list and the sum are
+// identical to mac_slot_list's.  Every thread of the CTA calls it.
+template <int NW>
+__device__ __forceinline__ void ws_slot_list(const MacArgs& a, int* out_slot, int* out_j, float* out_D, int* nv_out,
+                                             double* dc_out, int* s_wcnt, double* s_wdc) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int nv = 0;      // thread 0's running count and sum
+    double dc = 0.0;
+    for (int r0 = 0; r0 * 32 < a.A; r0 += NW) {
+        const int round = r0 + warp;
+        const int j = round * 32 + lane;
+        const int n = a.instant ? a.step : a.step - j;
+        bool valid = false;
+        int slot = 0;
+        double lum = 0.0, part = 0.0;
+        if (j < a.A && n >= 0) {
+            slot = n % a.n_ring;
+            const int ss = a.slot_step[slot];
+            const long long tot = a.slot_total[slot];
+            const double S = a.slot_S[slot];
+            const double g = a.g0[j];
+            if (ss == n && tot != 0) {
+                valid = true;
+                lum = S * (double)tot;
+                part = g * lum;
+            }
+        }
+        const unsigned ball = __ballot_sync(0xffffffffu, valid);
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (lane == 0) {
+            s_wcnt[warp] = round * 32 < a.A ? __popc(ball) : 0;
+            s_wdc[warp] = part;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            // rounds in order: exclusive prefix of the counts, and the k = 0 sum
+            for (int w = 0; w < NW && (r0 + w) * 32 < a.A; ++w) {
+                const int c = s_wcnt[w];
+                s_wcnt[w] = nv;
+                nv += c;
+                dc += s_wdc[w];
+            }
+        }
+        __syncthreads();
+        if (valid) {
+            const int pos = s_wcnt[warp] + __popc(ball & ((1u << lane) - 1u));
+            out_slot[pos] = slot;
+            out_j[pos] = j;
+            out_D[pos] = a.bf16 ? (float)lum : 1.0f;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *nv_out = nv;
+        *dc_out = dc;
+    }
+}
+
 template <int N, bool BF16, bool PAIR>
 __global__ void __launch_bounds__(MacWsCfg<N, BF16, PAIR>::NT, 1) k_mac_ws(MacArgs a) {
     using C = MacWsCfg<N, BF16, PAIR>;
@@ -386,6 +448,8 @@ __global__ void __launch_bounds__(MacWsCfg<N, BF16, PAIR>::NT, 1) k_mac_ws(MacAr
     unsigned long long* gempty = full + 18;
     __shared__ int s_nv, s_nb, s_fail;
     __shared__ double s_dc;
+    __shared__ int s_wcnt[NT / 32];
+    __shared__ double s_wdc[NT / 32];
 
     // the CTA's tiles.  A full tile is (line q, columns [chunk CW, chunk CW + CW)),
     // a Nyquist tile (lines [line, line + CW), column N/2); element (t, col) of
@@ -422,9 +486,7 @@ __global__ void __launch_bounds__(MacWsCfg<N, BF16, PAIR>::NT, 1) k_mac_ws(MacAr
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    if (threadIdx.x < 32)
-        mac_slot_list(a.A, a.step, a.n_ring, a.slot_step, a.slot_total, a.slot_S, a.g0, a.bf16 != 0, s_slot, s_j, s_D,
-                      &s_nv, &s_dc, a.instant);
+    ws_slot_list<NT / 32>(a, s_slot, s_j, s_D, &s_nv, &s_dc, s_wcnt, s_wdc);
     if (threadIdx.x == 32) {
         s_fail = 0;
         for (int i = 0; i < S; ++i) {
@@ -444,20 +506,32 @@ __global__ void __launch_bounds__(MacWsCfg<N, BF16, PAIR>::NT, 1) k_mac_ws(MacAr
         s_wrow[r] = nyq ? (int)wedge_of(r / CW, line + col, M, N) : (int)wedge_of(r / CW, line, chunk * CW + col, N);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        // the Ghat blocks in slice order, with their valid slices
+    if (threadIdx.x < 32) {
+        // the Ghat blocks in slice order, with their valid slices: a block
+        // starts at every v whose block differs from v - 1's, and its lane
+        // collects the (at most kWsGB) slices that follow in it
+        const int lane = threadIdx.x;
         int nb = 0;
-        for (int v = 0; v < s_nv; ++v) {
-            const int b = s_j[v] / kWsGB;
-            if (nb == 0 || s_blk[nb - 1] != b) {
-                s_blk[nb] = b;
-                s_bmask[nb] = 0;
-                s_bv0[nb] = v;
-                ++nb;
+        for (int v0 = 0; v0 < s_nv; v0 += 32) {
+            const int v = v0 + lane;
+            int b = 0;
+            bool start = false;
+            if (v < s_nv) {
+                b = s_j[v] / kWsGB;
+                start = v == 0 || s_j[v - 1] / kWsGB != b;
             }
-            s_bmask[nb - 1] |= 1 << (s_j[v] - b * kWsGB);
+            const unsigned ball = __ballot_sync(0xffffffffu, start);
+            if (start) {
+                const int pos = nb + __popc(ball & ((1u << lane) - 1u));
+                int mask = 0;
+                for (int k = v; k < s_nv && s_j[k] / kWsGB == b; ++k) mask |= 1 << (s_j[k] - b * kWsGB);
+                s_blk[pos] = b;
+                s_bmask[pos] = mask;
+                s_bv0[pos] = v;
+            }
+            nb += __popc(ball);
         }
-        s_nb = nb;
+        if (lane == 0) s_nb = nb;
     }
     __syncthreads();
     const int nv = s_nv, nb = s_nb;
