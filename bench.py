@@ -410,9 +410,9 @@ def run_serving(args, ClockSampler=ClockSampler):
 # warp-specialised and bulk kernels, the gather pass and its slot list); c3 is
 # the c3s capture (32 slices) with its reads scaled to 128 slices.
 MAC_TRAFFIC = {
-    "c2": {"sources": "058468ab19648ad6", "bytes": 38.467e6,
+    "c2": {"sources": "575a4b4d64a0d777", "bytes": 38.472e6,
            "from": "profiles/c2_dram_traffic.md (64-step window, all MAC-phase launches)"},
-    "c3": {"sources": "058468ab19648ad6", "bytes": 4 * 1.192421e9 + 73.883e6,
+    "c3": {"sources": "575a4b4d64a0d777", "bytes": 4 * 1.192879e9 + 73.619e6,
            "from": "profiles/k_mac_ws_256_bf16_pair.md (c3s, reads x 128/32)"},
 }
 
