@@ -28,3 +28,18 @@ def test_reference_arm_default_and_variants():
     assert "sub-cell" in v["config"]["near_field"]
     assert "f_diff" in v["config"]["step_adds"]
     assert v["value"] > 0
+
+
+def test_mac_source_hash_finds_the_kernel_texts():
+    # the roofline's captured DRAM traffic is tied to a hash over the MAC
+    # kernels' sources; the helper must find every function it hashes
+    import sys
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    h = bench.mac_sources_hash()
+    assert len(h) == 16 and int(h, 16) >= 0
+    for name, t in bench.MAC_TRAFFIC.items():
+        assert t["bytes"] > 0 and t["from"].startswith("profiles/")
+        assert os.path.exists(os.path.join(ROOT, t["from"].split(" ")[0]))
