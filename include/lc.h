@@ -321,14 +321,17 @@ uint64_t lc_kernel_launches(void);
 
 /* --- autotuning ---------------------------------------------------------------- */
 
-/* The shell multiply-accumulate runs in one of two kernels (a register-gather
- * pass, or a bulk-copy pipelined kernel for many slices); each plan times
- * both on its own buffers when it first builds a table for a new (device, N,
- * history, active slices) combination and keeps the faster.  Choices are
- * shared by all plans of the process and persisted to the file named by the
- * environment variable LC_AUTOTUNE_CACHE if set; LC_MAC_VARIANT=gather|bulk
- * forces one kernel.  This writes the current choices ("key variant" lines)
- * into buf (size bytes, NUL-terminated) and returns the full length. */
+/* The shell multiply-accumulate runs in one of four kernels: a register-gather
+ * pass (gather), a bulk-copy pipelined kernel over the full tiles plus the
+ * gather pass for the Nyquist tiles (bulk), and a warp-specialised kernel
+ * over every tile, one tile per CTA (ws) or the tiles of lines q and N - q
+ * together (ws2).  Each plan times every kernel built for its grid on its own
+ * buffers when it first builds a table for a new (device, N, history, active
+ * slices) combination and keeps the fastest.  Choices are shared by all plans
+ * of the process and persisted to the file named by the environment variable
+ * LC_AUTOTUNE_CACHE if set; LC_MAC_VARIANT=gather|bulk|ws|ws2 forces one
+ * kernel where it is built.  This writes the current choices ("key variant"
+ * lines) into buf (size bytes, NUL-terminated) and returns the full length. */
 int lc_autotune_report(char* buf, int size);
 
 /* --- light-cone vs instantaneous field ------------------------------------------ */
@@ -368,10 +371,12 @@ lc_status lc_fft_c2r(int n, const float* in_complex, float* out, float scale, vo
  *   n: 8, 16, 32, 64 or 96 (larger grids do not fit: LC_ERR_UNSUPPORTED_SIZE).
  *   in, out_complex: device pointers as for lc_fft_r2c.
  * The work is only enqueued on cuda_stream (no synchronisation).  The first
- * call on a device looks up the array's device address (cudaGetSymbolAddress);
- * make that first call before capturing a stream.  All calls share the one
- * array: calls whose work may overlap on the GPU (different streams without
- * ordering) race and must not be issued. */
+ * call on a device looks up the array's device address (cudaGetSymbolAddress),
+ * and so does the first call in each new context of the device (after
+ * cudaDeviceReset); make that first call before capturing a stream.  All calls
+ * share the one array: calls queued one after another on one stream are
+ * ordered and safe, but calls whose work may overlap on the GPU (different
+ * streams without ordering) race and must not be issued. */
 lc_status lc_fft_r2c_static(int n, const float* in, float* out_complex, void* cuda_stream);
 
 #ifdef __cplusplus

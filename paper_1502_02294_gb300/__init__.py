@@ -521,11 +521,25 @@ def fft_r2c(x, stream=None):
 
 def fft_r2c_static(x, out=None, stream=None):
     """fft_r2c without device allocation inside the library (N <= 96); the
-    result is enqueued on the stream, not waited for."""
+    result is enqueued on the stream, not waited for.
+
+    `x` must be a cubic CUDA tensor; it is made a contiguous float32 tensor
+    first (which may copy it, on the caller's side).  `out`, if given, must be
+    a contiguous complex64 CUDA tensor of shape (N, N, N/2 + 1) on x's device;
+    anything else raises ValueError before the library is called."""
     torch = _torch()
-    n = x.shape[0]
+    if not getattr(x, "is_cuda", False):
+        raise ValueError("fft_r2c_static: x must be a CUDA tensor")
+    if x.dim() != 3 or not (x.shape[0] == x.shape[1] == x.shape[2]):
+        raise ValueError(f"fft_r2c_static: x must be cubic (N, N, N), got {tuple(x.shape)}")
+    n = int(x.shape[0])
+    x = x.contiguous().to(torch.float32)
     if out is None:
         out = torch.empty((n, n, n // 2 + 1), dtype=torch.complex64, device=x.device)
+    elif (not getattr(out, "is_cuda", False) or out.device != x.device or out.dtype != torch.complex64
+          or not out.is_contiguous() or tuple(out.shape) != (n, n, n // 2 + 1)):
+        raise ValueError("fft_r2c_static: out must be a contiguous complex64 CUDA tensor of shape "
+                         f"({n}, {n}, {n // 2 + 1}) on {x.device}")
     _check(_lib().lc_fft_r2c_static(n, x.data_ptr(), out.data_ptr(), _stream_ptr(stream)), "lc_fft_r2c_static")
     return out
 
@@ -541,6 +555,7 @@ def fft_c2r(X, scale: Optional[float] = None, stream=None):
     return out
 
 
-__all__ = ["Plan", "StepGraph", "BatchGraph", "batch_step", "deposit_grid", "fft_r2c", "fft_c2r", "build", "estimate_bytes", "LCError",
+__all__ = ["Plan", "StepGraph", "BatchGraph", "batch_step", "deposit_grid", "fft_r2c", "fft_r2c_static", "fft_c2r",
+           "build", "estimate_bytes", "LCError",
            "SIGNATURES", "LIB_PATH", "SUPPORTED_N", "STEPS_EXPLICIT", "STEPS_EQUAL_TIME", "STEPS_EQUAL_TAU",
            "HISTORY_FP32", "HISTORY_BF16"]

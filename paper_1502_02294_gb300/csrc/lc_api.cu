@@ -104,7 +104,7 @@ static std::vector<float2> twiddles(int n) {
 }
 
 static std::atomic<unsigned long long> g_launches{0};
-static inline void count_launch(unsigned long long k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+void count_launch(unsigned long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 } // namespace lc
 

@@ -10,6 +10,10 @@
 
 namespace lc {
 
+// Kernels launched by the library in this process (lc_kernel_launches);
+// every launch site adds its count here.
+void count_launch(unsigned long long k = 1);
+
 // ---------------- host FP64 planner (lc_host.cpp) ----------------
 struct Cosmo {
     double om, h;

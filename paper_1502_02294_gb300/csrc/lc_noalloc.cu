@@ -10,9 +10,13 @@
 //
 // The array below is part of the library image: every GPU on which the
 // library is used keeps kStaticScratchBytes of device memory reserved for it
-// until the process exits.  Its device address is obtained once per device
-// with cudaGetSymbolAddress (the host-side name is only a stand-in and must
-// never be passed to a kernel).
+// until the process exits.  Its device address is obtained with
+// cudaGetSymbolAddress once per device and CUDA context (the host-side name is
+// only a stand-in and must never be passed to a kernel).  The cache is keyed
+// on the context's unique ID as well as the device, so a context rebuilt by
+// cudaDeviceReset (which reloads the module and may move the array) gets its
+// own lookup instead of a stale address.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -32,6 +36,34 @@ static __device__ __align__(256) unsigned char g_scratch[kStaticScratchBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_addr[kMaxDevices] = {nullptr};
+unsigned long long g_scratch_ctx[kMaxDevices] = {0}; // context ID the address belongs to
+
+// The unique ID of the calling thread's current context (0 if none or if the
+// driver does not offer it), through the driver entry points the runtime
+// hands out, so the library needs no link against the driver library.
+unsigned long long current_context_id() {
+    using GetCurrent = CUresult (*)(CUcontext*);
+    using GetId = CUresult (*)(CUcontext, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        looked_up = true;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", (void**)&get_current, 12000, cudaEnableDefault, &q1) !=
+                cudaSuccess || q1 != cudaDriverEntryPointSuccess)
+            get_current = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", (void**)&get_id, 12000, cudaEnableDefault, &q2) !=
+                cudaSuccess || q2 != cudaDriverEntryPointSuccess)
+            get_id = nullptr;
+        cudaGetLastError();
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
 
 __global__ void k_twiddles(float2* tw, int n) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -62,14 +94,19 @@ extern "C" lc_status lc_fft_r2c_static(int n, const float* in, float* out_comple
     }
     void* base = nullptr;
     {
-        // first call on this device: resolve the array's device address
+        // first call on this device (or in a new context of it): resolve the
+        // array's device address in the current context
         std::lock_guard<std::mutex> g(g_mu);
-        if (!g_scratch_addr[dev]) {
-            if (cudaGetSymbolAddress(&g_scratch_addr[dev], g_scratch) != cudaSuccess) {
+        const unsigned long long ctx = current_context_id();
+        if (!g_scratch_addr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
+            void* addr = nullptr;
+            if (cudaGetSymbolAddress(&addr, g_scratch) != cudaSuccess || !addr) {
                 g_scratch_addr[dev] = nullptr;
                 cudaGetLastError();
                 return LC_ERR_CUDA;
             }
+            g_scratch_addr[dev] = addr;
+            g_scratch_ctx[dev] = current_context_id(); // the lookup made the primary context current if none was
         }
         base = g_scratch_addr[dev];
     }
@@ -104,6 +141,7 @@ extern "C" lc_status lc_fft_r2c_static(int n, const float* in, float* out_comple
     ops->cols(c, st);
     const int h = n / 2 + 1;
     cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) count_launch(ops->plane_r2c ? 3 : 4); // twiddles + the transform's passes
     if (e == cudaSuccess)
         e = cudaMemcpy2DAsync(out_complex, sizeof(float2) * h, work, sizeof(float2) * nrp_of(n), sizeof(float2) * h,
                               (size_t)n * n, cudaMemcpyDeviceToDevice, st);

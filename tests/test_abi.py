@@ -71,3 +71,19 @@ def test_no_cpu_fallback_without_device(lib):
     assert lib.lc_plan_create(32, 100.0, ctypes.byref(c), ctypes.byref(st), None, ctypes.byref(out)) == lc.LC_ERR_CUDA
     with pytest.raises(lc.LCError):
         lc.Plan.from_workload(synth.config("c1"))
+
+
+def test_static_fft_wrapper_rejects_bad_arguments_before_the_library():
+    import torch
+
+    with pytest.raises(ValueError):
+        lc.fft_r2c_static(torch.zeros((8, 8, 8)))  # not a CUDA tensor
+    if torch.cuda.is_available():
+        with pytest.raises(ValueError):
+            lc.fft_r2c_static(torch.zeros((8, 8, 4), device="cuda"))  # not cubic
+        with pytest.raises(ValueError):
+            lc.fft_r2c_static(torch.zeros((8, 8, 8), device="cuda"),
+                              out=torch.zeros((8, 8, 4), dtype=torch.complex64, device="cuda"))
+        with pytest.raises(ValueError):
+            lc.fft_r2c_static(torch.zeros((8, 8, 8), device="cuda"),
+                              out=torch.zeros((8, 8, 5), dtype=torch.complex128, device="cuda"))
