@@ -11,7 +11,10 @@ and time), the paper's printed numbers (f_mod(0) = 1, the horizon constants,
 alpha = 1 at the fiducial cosmology, r_LW inside 10 Myr of lookback at
 z = 27.90), brute-force symmetry checks, the uniform-source closed form,
 linearity, translation and rotation covariance, causality, and a brute-force
-DFT checked against numpy on 8^3 grids (see tests/test_oracle_*.py).
+DFT checked against numpy on 8^3 grids; the cloud-in-cell deposit by charge
+conservation, its first moment, midpoint halves, equality with the nearest
+grid point at cell centres and translation covariance; the rough horizon by
+its matter-only closed form (see tests/test_oracle_*.py).
 """
 from __future__ import annotations
 
@@ -43,7 +46,8 @@ class _Problem(ctypes.Structure):
                 ("h", ctypes.c_double), ("n_steps", ctypes.c_int),
                 ("z_edges", ctypes.POINTER(ctypes.c_double)), ("subsamples", ctypes.c_int),
                 ("normalise", ctypes.c_int), ("out_unit", ctypes.c_double),
-                ("kernel", ctypes.c_int), ("k_length", ctypes.c_double), ("k_rmax", ctypes.c_double)]
+                ("kernel", ctypes.c_int), ("k_length", ctypes.c_double), ("k_rmax", ctypes.c_double),
+                ("n_shell_max", ctypes.c_int)]
 
 
 def lib():
@@ -70,6 +74,9 @@ def lib():
             ("lco_rgf_direct", d, [pp, i, i, i, i, i]),
             ("lco_deposit_ngp", i, [i, d, i64, dp, dp, dp]),
             ("lco_deposit_fixed", i, [i, d, i64, dp, dp, i64p, dp, i64p]),
+            ("lco_deposit_cic", i, [i, d, i64, dp, dp, dp]),
+            ("lco_deposit_cic_fixed", i, [i, d, i64, dp, dp, i64p, dp, i64p]),
+            ("lco_rough_horizon", d, [d]), ("lco_rough_horizon_r", d, [d, d, d]), ("lco_fzero_r", d, [d, d, d]),
             ("lco_field", i, [pp, i, i, ctypes.POINTER(dp), i64, i64p, dp]),
             ("lco_shell_table", i, [pp, i, dp, dp, dp]),
             ("lco_near_cube", i, [pp, i, i64, dp, dp, i, d, i, dp]),
@@ -132,9 +139,32 @@ def shell_integral(om, h, z_obs, r_lo, r_hi):
 
 
 # radial kernels other than the LW one: kernel = (kind, length, rmax), kind 1 =
-# exp(-r / length) attenuation with a cut-off at rmax (see lco_fk)
-def _k(kernel):
-    return (0, 0.0, 0.0) if kernel is None else (int(kernel[0]), float(kernel[1]), float(kernel[2]))
+# exp(-r / length) attenuation with a cut-off at rmax, kind 2 = the LW kernel
+# with the rough horizon of Section 1 (see lco_fk)
+KERNEL_LW, KERNEL_EXP, KERNEL_LW_ROUGH = 0, 1, 2
+DEPOSIT_NGP, DEPOSIT_CIC = 0, 1
+
+
+def _k(kernel, horizon_mode=0):
+    k = (0, 0.0, 0.0) if kernel is None else (int(kernel[0]), float(kernel[1]), float(kernel[2]))
+    if horizon_mode and k[0] == KERNEL_LW:
+        k = (KERNEL_LW_ROUGH, 0.0, 0.0)
+    return k
+
+
+def rough_horizon(zs):
+    """100 [21 / (1 + z_s)]^0.5 comoving Mpc (Section 1)."""
+    return lib().lco_rough_horizon(zs)
+
+
+def rough_horizon_radius(om, h, z_obs):
+    """The radius r with r = 100 [21 / (1 + z_s(r))]^0.5 seen from z_obs."""
+    return lib().lco_rough_horizon_r(om, h, z_obs)
+
+
+def fmod_zero_radius(om, h, z_obs):
+    """The radius where the unclamped f_mod of Eq. 15 reaches 0, seen from z_obs."""
+    return lib().lco_fzero_r(om, h, z_obs)
 
 
 def g_kernel(kernel, om, h, z_obs, r):
@@ -163,19 +193,24 @@ def step_edges(om, h, spec, kernel=None) -> np.ndarray:
 class Problem:
     """A workload as the oracle sees it (edges derived here, from the spec)."""
 
-    def __init__(self, n, box, om, h, steps, subsamples=4, normalise=1, out_unit=1.0, kernel=None):
+    def __init__(self, n, box, om, h, steps, subsamples=4, normalise=1, out_unit=1.0, kernel=None,
+                 horizon_mode=0, n_shell_max=0, deposit=DEPOSIT_NGP):
         self.n, self.box, self.om, self.h = int(n), float(box), float(om), float(h)
         self.steps = steps
-        self.kernel = _k(kernel)
-        self.z_edges = step_edges(om, h, steps, kernel)
+        self.kernel = _k(kernel, horizon_mode)
+        self.z_edges = step_edges(om, h, steps, self.kernel)
         self.subsamples, self.normalise, self.out_unit = int(subsamples), int(normalise), float(out_unit)
+        self.n_shell_max = int(n_shell_max)
+        self.deposit = int(deposit)
         self._c = _Problem(self.n, self.box, self.om, self.h, int(steps.n_steps), _dp(self.z_edges),
-                           self.subsamples, self.normalise, self.out_unit, *self.kernel)
+                           self.subsamples, self.normalise, self.out_unit, *self.kernel, self.n_shell_max)
 
     @classmethod
     def from_workload(cls, w, **kw):
         args = dict(n=w.n, box=w.box, om=w.omega_m, h=w.h, steps=w.steps, subsamples=w.subsamples,
-                    normalise=w.normalise, out_unit=w.out_unit, kernel=getattr(w, "kernel", None))
+                    normalise=w.normalise, out_unit=w.out_unit, kernel=getattr(w, "kernel", None),
+                    horizon_mode=getattr(w, "horizon_mode", 0), n_shell_max=getattr(w, "n_shell_max", 0),
+                    deposit=getattr(w, "deposit", DEPOSIT_NGP))
         args.update(kw)
         return cls(**args)
 
@@ -262,13 +297,44 @@ def deposit_fixed(n, box, pos, lum):
     return out.reshape(n, n, n), S.value, tot.value
 
 
+def deposit_cic(n, box, pos, lum) -> np.ndarray:
+    """FP64 cloud-in-cell luminosity per cell (see lco_deposit_cic)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    lum = np.ascontiguousarray(lum, dtype=np.float64)
+    out = np.zeros(n ** 3)
+    rc = lib().lco_deposit_cic(n, box, lum.shape[0], _dp(pos), _dp(lum), _dp(out))
+    if rc:
+        raise ValueError("invalid sources")
+    return out.reshape(n, n, n)
+
+
+def deposit_cic_fixed(n, box, pos, lum):
+    """Integer fixed-point cloud-in-cell grid, unit and total (see lco_deposit_cic_fixed)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    lum = np.ascontiguousarray(lum, dtype=np.float64)
+    out = np.zeros(n ** 3, dtype=np.int64)
+    S = ctypes.c_double()
+    tot = ctypes.c_int64()
+    rc = lib().lco_deposit_cic_fixed(n, box, lum.shape[0], _dp(pos), _dp(lum), _i64p(out), ctypes.byref(S),
+                                     ctypes.byref(tot))
+    if rc:
+        raise ValueError("invalid sources")
+    return out.reshape(n, n, n), S.value, tot.value
+
+
+def deposit(prob: "Problem", pos, lum) -> np.ndarray:
+    """The FP64 source grid of one slice with the problem's assignment (NGP or CIC)."""
+    f = deposit_cic if prob.deposit == DEPOSIT_CIC else deposit_ngp
+    return f(prob.n, prob.box, pos, lum)
+
+
 def source_grids(prob: Problem, cat, s: int) -> List[Optional[np.ndarray]]:
     """FP64 source grids of the active slices of step s (index j = lookback)."""
     A = prob.active_shells(s)
     out = []
     for j in range(A):
         pos, lum = cat.active(s - j)
-        out.append(deposit_ngp(prob.n, prob.box, pos, lum) if lum.shape[0] else None)
+        out.append(deposit(prob, pos, lum) if lum.shape[0] else None)
     return out
 
 
@@ -310,7 +376,7 @@ def instant_field_for(prob: Problem, cat, s: int, cells: Optional[np.ndarray] = 
     of the observing step s (source term frozen at the observing redshift)."""
     A = prob.active_shells(s)
     pos, lum = cat.active(s)
-    g = deposit_ngp(prob.n, prob.box, pos, lum) if lum.shape[0] else None
+    g = deposit(prob, pos, lum) if lum.shape[0] else None
     return prob.field(s, [g] * A, cells)
 
 

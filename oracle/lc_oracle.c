@@ -163,15 +163,28 @@ double lco_fmod(double r, double alpha) {
     return 1.7 * exp(-pow(r / (116.29 * alpha), 0.68)) - 0.7;
 }
 
+/* The rough LW horizon of Section 1, 100 [21 / (1 + z)]^0.5 comoving Mpc,
+ * read with z the emission redshift z_s (as Eq. 16 reads alpha). */
+double lco_rough_horizon(double zs) { return 100.0 * sqrt(21.0 / (1.0 + zs)); }
+
 /* Radial kernels.  The generic RGF (Eq. 7) carries a dilution factor that
  * this method needs only as a function of distance.  Kernel kind kk:
  *   0: Lyman-Werner, Eq. 14 / Eq. 17 with f_mod of Eq. 15 at alpha(z_s);
  *   1: the same (1+z)^3 / ((4 pi)^2 (1+z_s) r^2) dilution with f_mod replaced
  *      by exp(-r / kl) for r < kr and 0 beyond (kl: attenuation length,
- *      kr: cut-off, comoving Mpc).
+ *      kr: cut-off, comoving Mpc);
+ *   2: Lyman-Werner with the rough horizon of Section 1 in place of Eq. 15's
+ *      97.39 alpha: the modulation of Eq. 15 without its cut, clamped at 0
+ *      (it turns negative at r / alpha = 116.29 ln(1.7/0.7)^(1/0.68)), for
+ *      r <= 100 [21 / (1 + z_s)]^0.5, and 0 beyond.
  * lco_fk is the factor that multiplies the dilution. */
 double lco_fk(int kk, double kl, double kr, double om, double h, double zs, double r) {
     if (kk == 1) return r < kr ? exp(-r / kl) : 0.0;
+    if (kk == 2) {
+        if (r > lco_rough_horizon(zs)) return 0.0;
+        double f = 1.7 * exp(-pow(r / (116.29 * lco_alpha(om, h, zs)), 0.68)) - 0.7;
+        return f > 0.0 ? f : 0.0;
+    }
     return lco_fmod(r, lco_alpha(om, h, zs));
 }
 
@@ -189,10 +202,27 @@ double lco_gk(int kk, double kl, double kr, double om, double h, double z_obs, d
 double lco_g(double om, double h, double z_obs, double r) { return lco_gk(0, 0.0, 0.0, om, h, z_obs, r); }
 
 double lco_horizon(double om, double h, double z_obs);
-/* the kernel's horizon: LW below; the cut-off for kind 1 */
+double lco_rough_horizon_r(double om, double h, double z_obs);
+/* the kernel's horizon: LW below; the cut-off for kind 1; the rough one for kind 2 */
 double lco_horizonk(int kk, double kl, double kr, double om, double h, double z_obs) {
     (void)kl;
-    return kk == 1 ? kr : lco_horizon(om, h, z_obs);
+    if (kk == 1) return kr;
+    if (kk == 2) return lco_rough_horizon_r(om, h, z_obs);
+    return lco_horizon(om, h, z_obs);
+}
+
+/* The radius where r = 100 [21 / (1 + z_s(r))]^0.5 (kernel kind 2).  The
+ * right-hand side falls as r grows, so the root is unique.  Bisection. */
+double lco_rough_horizon_r(double om, double h, double z_obs) {
+    double lo = 0.0, hi = lco_rough_horizon(z_obs);
+    for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi);
+        double phi = mid - lco_rough_horizon(lco_zs_of_r(om, h, z_obs, mid));
+        if (phi > 0.0) hi = mid;
+        else lo = mid;
+        if (hi - lo <= 1e-14 * hi) break;
+    }
+    return 0.5 * (lo + hi);
 }
 
 /* LW horizon r_h: the radius where r / alpha(z_s(r)) = 97.39 (Eq. 15, with
@@ -224,12 +254,34 @@ static double gl_panel(int kk, double kl, double kr, double om, double h, double
     return half * s;
 }
 
+/* Kernel kind 2: the radius where the unclamped modulation of Eq. 15 reaches
+ * 0, r = 116.29 ln(1.7 / 0.7)^(1 / 0.68) alpha(z_s(r)); the clamped kernel is
+ * 0 beyond it.  Bisection (alpha falls with r, so the root is unique). */
+double lco_fzero_r(double om, double h, double z_obs) {
+    const double x0 = 116.29 * pow(log(1.7 / 0.7), 1.0 / 0.68);
+    double lo = 0.0, hi = x0 * lco_alpha(om, h, z_obs);
+    for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi);
+        double phi = mid - x0 * lco_alpha(om, h, lco_zs_of_r(om, h, z_obs, mid));
+        if (phi > 0.0) hi = mid;
+        else lo = mid;
+        if (hi - lo <= 1e-14 * hi) break;
+    }
+    return 0.5 * (lo + hi);
+}
+
 /* I = int_{r_lo}^{min(r_hi, r_h)} 4 pi r^2 g(r) dr.  Panels are graded
- * geometrically towards r = 0 because f_mod carries r^0.68. */
+ * geometrically towards r = 0 because f_mod carries r^0.68.  For kernel kind
+ * 2 the upper limit also stops where the clamped modulation reaches 0, so
+ * that no panel straddles the kink of the clamp. */
 double lco_shell_integralk(int kk, double kl, double kr, double om, double h, double z_obs, double r_lo,
                            double r_hi) {
     double rh = lco_horizonk(kk, kl, kr, om, h, z_obs);
     double b = r_hi < rh ? r_hi : rh;
+    if (kk == 2) {
+        double rz = lco_fzero_r(om, h, z_obs);
+        if (rz < b) b = rz;
+    }
     if (!(r_lo < b)) return 0.0;
     double sum = 0.0;
     if (r_lo <= 0.0) {
@@ -299,13 +351,16 @@ typedef struct {
     double out_unit;     /* U */
     int kernel;          /* radial kernel kind (see lco_fk) */
     double k_length, k_rmax;
+    int n_shell_max;     /* > 0: at most this many slices per step (the newest ones) */
 } lco_problem;
 
 /* Active slices of observation step s.  Step s observes at tau_{s+1} (the end
  * of the step, so sources pushed at step s are included).  Slice n = s - j
  * covers the shell [chi(z_{s+1}, z_{n+1}), chi(z_{s+1}, z_n)) (Eq. 9 with a
  * half-open window); it is active while its inner radius is below
- * r_h (1 - 1e-9). */
+ * r_h (1 - 1e-9), and, when n_shell_max > 0, while j < n_shell_max (the
+ * number of lookback slices kept per observing time, which the paragraph
+ * after the algorithm of Section 2.2 lets vary; here a user's cap). */
 int lco_shells(const lco_problem* P, int s, double* r_lo, double* r_hi, double* r_h) {
     if (s < 0 || s >= P->n_steps) return -1;
     double zo = P->z_edges[s + 1];
@@ -313,6 +368,7 @@ int lco_shells(const lco_problem* P, int s, double* r_lo, double* r_hi, double* 
     if (r_h) *r_h = rh;
     int A = 0;
     for (int j = 0; j <= s; ++j) {
+        if (P->n_shell_max > 0 && j >= P->n_shell_max) break;
         int n = s - j;
         double lo = lco_chi(P->om, P->h, zo, P->z_edges[n + 1]);
         double hi = lco_chi(P->om, P->h, zo, P->z_edges[n]);
@@ -577,6 +633,100 @@ int lco_deposit_fixed(int N, double box, int64_t n_src, const double* pos, const
         int64_t i = ngp_index(pos[3 * s + 0], l, N), j = ngp_index(pos[3 * s + 1], l, N),
                 k = ngp_index(pos[3 * s + 2], l, N);
         grid[(i * N + j) * N + k] += q;
+        tot += q;
+    }
+    *scale = S;
+    *total = tot;
+    return 0;
+}
+
+/* Cloud-in-cell assignment (an alternative to the nearest grid point for the
+ * source term of Eq. 11 and Eq. 17): a source at coordinate x shares its
+ * luminosity between the two cell centres around it along each axis, cells
+ * i0 = floor(x / l) and i0 + 1 (mod N), with weights 1 - f and f,
+ * f = x / l - floor(x / l); the 8 cells of a source get the products of the
+ * per-axis weights (trilinear).  A source exactly at a cell centre (f = 0 on
+ * every axis) puts everything in that cell, as the nearest grid point does. */
+static void cic_axis(double x, double l, int N, int64_t* i0, int64_t* i1, double* f) {
+    double t = x / l;
+    double fl = floor(t);
+    *f = t - fl;
+    double m = fmod(fl, (double)N); /* exact */
+    if (m < 0.0) m += (double)N;
+    int64_t i = (int64_t)m;
+    if (i < 0 || i >= N) i = 0;
+    *i0 = i;
+    *i1 = (i + 1) % N;
+}
+
+/* FP64 luminosity per cell, CIC weights. */
+int lco_deposit_cic(int N, double box, int64_t n_src, const double* pos, const double* lum, double* grid) {
+    int e = check_sources(n_src, pos, lum);
+    if (e) return e;
+    const double l = box / N;
+    memset(grid, 0, sizeof(double) * (size_t)N * N * N);
+    for (int64_t s = 0; s < n_src; ++s) {
+        int64_t c[3][2];
+        double w[3][2];
+        for (int d = 0; d < 3; ++d) {
+            double f;
+            cic_axis(pos[3 * s + d], l, N, &c[d][0], &c[d][1], &f);
+            w[d][0] = 1.0 - f;
+            w[d][1] = f;
+        }
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b)
+                for (int k = 0; k < 2; ++k)
+                    grid[(c[0][a] * N + c[1][b]) * N + c[2][k]] += lum[s] * w[0][a] * w[1][b] * w[2][k];
+    }
+    return 0;
+}
+
+/* Split an integer charge q >= 0 by weight f in [0, 1]: the part for the
+ * upper cell, rint(q f) (at most q), and the rest for the lower one; the two
+ * parts always sum to q. */
+static void split_charge(int64_t q, double f, int64_t* lo, int64_t* hi) {
+    int64_t h = (int64_t)rint((double)q * f);
+    if (h > q) h = q;
+    if (h < 0) h = 0;
+    *hi = h;
+    *lo = q - h;
+}
+
+/* Integer fixed-point CIC: the unit S and q_s = rint(L_s / S) as
+ * lco_deposit_fixed; each q_s is split along x, then each part along y, then
+ * each of those along z (split_charge), so the 8 integer charges of a source
+ * sum to q_s exactly and the grid total equals the sum of all q_s. */
+int lco_deposit_cic_fixed(int N, double box, int64_t n_src, const double* pos, const double* lum, int64_t* grid,
+                          double* scale, int64_t* total) {
+    int e = check_sources(n_src, pos, lum);
+    if (e) return e;
+    const double l = box / N;
+    memset(grid, 0, sizeof(int64_t) * (size_t)N * N * N);
+    double lmax = 0.0;
+    for (int64_t s = 0; s < n_src; ++s)
+        if (lum[s] > lmax) lmax = lum[s];
+    double S = 1.0;
+    if (lmax > 0.0) {
+        int E;
+        frexp((double)n_src * lmax, &E);
+        S = ldexp(1.0, E - 62);
+    }
+    int64_t tot = 0;
+    for (int64_t s = 0; s < n_src; ++s) {
+        int64_t q = (int64_t)rint(lum[s] / S);
+        int64_t c[3][2];
+        double f[3];
+        for (int d = 0; d < 3; ++d) cic_axis(pos[3 * s + d], l, N, &c[d][0], &c[d][1], &f[d]);
+        int64_t qx[2], qxy[2][2], qxyz[2][2][2];
+        split_charge(q, f[0], &qx[0], &qx[1]);
+        for (int a = 0; a < 2; ++a) {
+            split_charge(qx[a], f[1], &qxy[a][0], &qxy[a][1]);
+            for (int b = 0; b < 2; ++b) split_charge(qxy[a][b], f[2], &qxyz[a][b][0], &qxyz[a][b][1]);
+        }
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b)
+                for (int k = 0; k < 2; ++k) grid[(c[0][a] * N + c[1][b]) * N + c[2][k]] += qxyz[a][b][k];
         tot += q;
     }
     *scale = S;

@@ -107,6 +107,12 @@ class Workload:
     # near field of the innermost slice: 0 from NGP cells, 1 from the sources'
     # own positions (sub-cell)
     near_mode: int = 0
+    # source assignment: 0 nearest grid point, 1 cloud in cell
+    deposit: int = 0
+    # Lyman-Werner horizon: 0 the cut of Eq. 15, 1 the rough horizon of Section 1
+    horizon_mode: int = 0
+    # > 0: at most this many lookback slices per observing step
+    n_shell_max: int = 0
 
 
 def _uniform_positions(rng, n, box):
