@@ -78,6 +78,7 @@ def lib():
             ("lco_deposit_cic_fixed", i, [i, d, i64, dp, dp, i64p, dp, i64p]),
             ("lco_rough_horizon", d, [d]), ("lco_rough_horizon_r", d, [d, d, d]), ("lco_fzero_r", d, [d, d, d]),
             ("lco_field", i, [pp, i, i, ctypes.POINTER(dp), i64, i64p, dp]),
+            ("lco_field_sparse", i, [pp, i, i, i64p, i64p, dp, i64, i64p, dp]),
             ("lco_shell_table", i, [pp, i, dp, dp, dp]),
             ("lco_near_cube", i, [pp, i, i64, dp, dp, i, d, i, dp]),
             ("lco_dft3", i, [i, dp, dp, i, dp, dp]), ("lco_threads", i, []),
@@ -272,6 +273,29 @@ class Problem:
             raise RuntimeError("oracle field failed")
         return out
 
+    def field_sparse(self, s, slices, cells: Optional[np.ndarray] = None) -> np.ndarray:
+        """As field(), from each slice's occupied cells: slices[j] = (flat
+        C-order indices, FP64 values) of lookback j, or None for no sources."""
+        counts = np.array([0 if sl is None else len(sl[0]) for sl in slices] or [0], dtype=np.int64)
+        flat = np.ascontiguousarray(np.concatenate([sl[0] for sl in slices if sl is not None] or [np.zeros(0)]),
+                                    dtype=np.int64)
+        val = np.ascontiguousarray(np.concatenate([sl[1] for sl in slices if sl is not None] or [np.zeros(0)]),
+                                   dtype=np.float64)
+        n_slices = len(slices)
+        if cells is None:
+            out = np.zeros(self.n ** 3)
+            rc = lib().lco_field_sparse(self.ref, s, n_slices, _i64p(counts), _i64p(flat), _dp(val), 0,
+                                        ctypes.POINTER(ctypes.c_int64)(), _dp(out))
+            out = out.reshape(self.n, self.n, self.n)
+        else:
+            cells = np.ascontiguousarray(cells, dtype=np.int64)
+            out = np.zeros(cells.shape[0])
+            rc = lib().lco_field_sparse(self.ref, s, n_slices, _i64p(counts), _i64p(flat), _dp(val), cells.shape[0],
+                                        _i64p(cells), _dp(out))
+        if rc:
+            raise RuntimeError("oracle field failed")
+        return out
+
 
 # ---------------------------------------------------------------- deposit
 def deposit_ngp(n, box, pos, lum) -> np.ndarray:
@@ -338,8 +362,24 @@ def source_grids(prob: Problem, cat, s: int) -> List[Optional[np.ndarray]]:
     return out
 
 
+def source_lists(prob: Problem, cat, s: int):
+    """The occupied cells (flat index, FP64 value) of each active slice of
+    step s, one dense grid alive at a time."""
+    out = []
+    for j in range(prob.active_shells(s)):
+        pos, lum = cat.active(s - j)
+        if not lum.shape[0]:
+            out.append(None)
+            continue
+        g = deposit(prob, pos, lum).reshape(-1)
+        flat = np.flatnonzero(g)
+        out.append((flat.astype(np.int64), g[flat].copy()))
+        del g
+    return out
+
+
 def field_for(prob: Problem, cat, s: int, cells: Optional[np.ndarray] = None) -> np.ndarray:
-    return prob.field(s, source_grids(prob, cat, s), cells)
+    return prob.field_sparse(s, source_lists(prob, cat, s), cells)
 
 
 NEAR_R = 2  # near cube of the innermost slice: |d| <= NEAR_R cells per axis

@@ -738,40 +738,31 @@ int lco_deposit_cic_fixed(int N, double box, int64_t n_src, const double* pos, c
 /* Retarded field by direct periodic convolution (Eq. 11), summed over  */
 /* slices (Eq. 9, step 6 of Section 2.2).                              */
 /* ------------------------------------------------------------------ */
-/* src[j] is the FP64 source grid of slice s - j (NULL: no sources), for
- * j < n_src_grids.  cells: flat C-order indices, or NULL for all N^3. */
-int lco_field(const lco_problem* P, int s, int n_src_grids, const double* const* src, int64_t n_cells,
-              const int64_t* cells, double* out) {
+/* The sum of Eq. 11 over slices at the requested cells, from the occupied
+ * cells of each slice: slice j (lookback j, j < n_slices) has counts[j]
+ * entries, flat C-order cell indices flat[] and FP64 values val[], the slices'
+ * entries concatenated in order of j.  cells: flat indices to evaluate, or
+ * NULL for all N^3.  Slices at or beyond the step's active count add
+ * nothing. */
+static int field_sum(const lco_problem* P, int s, int n_slices, const int64_t* counts, const int64_t* flat,
+                     const double* val, int64_t n_cells, const int64_t* cells, double* out) {
     const int N = P->n, M = N / 2;
     const size_t NN = (size_t)N * N * N;
     octant_set o;
     if (build_octants(P, s, &o)) return 1;
     const size_t oct = (size_t)(M + 1) * (M + 1) * (M + 1);
-    /* occupied cells of every active slice */
-    int64_t total_occ = 0;
-    int64_t* occ_start = (int64_t*)calloc(o.A + 1, sizeof(int64_t));
-    for (int j = 0; j < o.A; ++j) {
-        occ_start[j] = total_occ;
-        if (j < n_src_grids && src[j])
-            for (size_t t = 0; t < NN; ++t)
-                if (src[j][t] != 0.0) ++total_occ;
-    }
-    occ_start[o.A] = total_occ;
+    const int A = o.A < n_slices ? o.A : n_slices;
+    int64_t* occ_start = (int64_t*)calloc(A + 1, sizeof(int64_t));
+    for (int j = 0; j < A; ++j) occ_start[j + 1] = occ_start[j] + counts[j];
+    const int64_t total_occ = occ_start[A];
     int* oi = (int*)malloc(sizeof(int) * (total_occ + 1));
     int* oj = (int*)malloc(sizeof(int) * (total_occ + 1));
     int* ok = (int*)malloc(sizeof(int) * (total_occ + 1));
-    double* ov = (double*)malloc(sizeof(double) * (total_occ + 1));
-    for (int j = 0; j < o.A; ++j) {
-        int64_t p = occ_start[j];
-        if (j < n_src_grids && src[j])
-            for (size_t t = 0; t < NN; ++t)
-                if (src[j][t] != 0.0) {
-                    oi[p] = (int)(t / ((size_t)N * N));
-                    oj[p] = (int)((t / N) % N);
-                    ok[p] = (int)(t % N);
-                    ov[p] = src[j][t];
-                    ++p;
-                }
+    for (int64_t p = 0; p < total_occ; ++p) {
+        const int64_t t = flat[p];
+        oi[p] = (int)(t / ((int64_t)N * N));
+        oj[p] = (int)((t / N) % N);
+        ok[p] = (int)(t % N);
     }
     const int64_t nc = cells ? n_cells : (int64_t)NN;
 #pragma omp parallel for schedule(dynamic, 64)
@@ -779,14 +770,14 @@ int lco_field(const lco_problem* P, int s, int n_src_grids, const double* const*
         int64_t t = cells ? cells[c] : c;
         int x = (int)(t / ((int64_t)N * N)), y = (int)((t / N) % N), z = (int)(t % N);
         double acc = 0.0;
-        for (int j = 0; j < o.A; ++j) {
+        for (int j = 0; j < A; ++j) {
             const double* G = o.G + (size_t)j * oct;
             for (int64_t p = occ_start[j]; p < occ_start[j + 1]; ++p) {
                 int dx = ((x - oi[p]) % N + N) % N, dy = ((y - oj[p]) % N + N) % N, dz = ((z - ok[p]) % N + N) % N;
                 if (dx > M) dx = N - dx;
                 if (dy > M) dy = N - dy;
                 if (dz > M) dz = N - dz;
-                acc += G[((size_t)dx * (M + 1) + dy) * (M + 1) + dz] * ov[p];
+                acc += G[((size_t)dx * (M + 1) + dy) * (M + 1) + dz] * val[p];
             }
         }
         out[c] = P->out_unit * acc;
@@ -794,10 +785,50 @@ int lco_field(const lco_problem* P, int s, int n_src_grids, const double* const*
     free(oi);
     free(oj);
     free(ok);
-    free(ov);
     free(occ_start);
     octant_free(&o);
     return 0;
+}
+
+/* src[j] is the FP64 source grid of slice s - j (NULL: no sources), for
+ * j < n_src_grids.  cells: flat C-order indices, or NULL for all N^3.  The
+ * occupied cells of each grid, in increasing flat index, go to field_sum. */
+int lco_field(const lco_problem* P, int s, int n_src_grids, const double* const* src, int64_t n_cells,
+              const int64_t* cells, double* out) {
+    const int N = P->n;
+    const size_t NN = (size_t)N * N * N;
+    const int ns = n_src_grids > 0 ? n_src_grids : 0;
+    int64_t* counts = (int64_t*)calloc(ns + 1, sizeof(int64_t));
+    int64_t total = 0;
+    for (int j = 0; j < ns; ++j) {
+        if (src[j])
+            for (size_t t = 0; t < NN; ++t)
+                if (src[j][t] != 0.0) ++counts[j];
+        total += counts[j];
+    }
+    int64_t* flat = (int64_t*)malloc(sizeof(int64_t) * (total + 1));
+    double* val = (double*)malloc(sizeof(double) * (total + 1));
+    int64_t p = 0;
+    for (int j = 0; j < ns; ++j)
+        if (src[j])
+            for (size_t t = 0; t < NN; ++t)
+                if (src[j][t] != 0.0) {
+                    flat[p] = (int64_t)t;
+                    val[p] = src[j][t];
+                    ++p;
+                }
+    int rc = field_sum(P, s, ns, counts, flat, val, n_cells, cells, out);
+    free(counts);
+    free(flat);
+    free(val);
+    return rc;
+}
+
+/* The same field from the slices' occupied-cell lists (see field_sum), for
+ * grids too large to hold every slice's dense grid at once. */
+int lco_field_sparse(const lco_problem* P, int s, int n_slices, const int64_t* counts, const int64_t* flat,
+                     const double* val, int64_t n_cells, const int64_t* cells, double* out) {
+    return field_sum(P, s, n_slices, counts, flat, val, n_cells, cells, out);
 }
 
 /* Shell integrals I_j (Green's-function k = 0 values times l^3) of step s. */

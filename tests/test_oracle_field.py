@@ -245,3 +245,15 @@ def test_instant_field_equals_retarded_for_steady_sources(oracle_lib):
     Ji2 = oracle_lib.instant_field_for(P, w.cat, s)
     J2 = oracle_lib.field_for(P, w.cat, s)
     assert (Ji2 >= J2 - 1e-12 * np.abs(J2).max()).all() and Ji2.sum() > J2.sum()
+
+
+def test_field_from_occupied_cells_equals_dense_grids(oracle_lib):
+    # field_for hands the oracle each slice's occupied cells instead of dense
+    # grids; the sum is the same, in the same order, so the bits agree
+    w = synth.small(n=16, box=40.0, n_steps=6, n_src=60, seed=1234, clustered=True)
+    P = oracle_lib.Problem.from_workload(w)
+    for s in (3, 5):
+        dense = P.field(s, oracle_lib.source_grids(P, w.cat, s))
+        assert np.array_equal(oracle_lib.field_for(P, w.cat, s), dense)
+        cells = synth.sample_cells(s, w.n, 50)
+        assert np.array_equal(oracle_lib.field_for(P, w.cat, s, cells=cells), dense.reshape(-1)[cells])
