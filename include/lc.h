@@ -95,6 +95,29 @@ enum { LC_KERNEL_LW = 0, LC_KERNEL_EXP = 1 };
  *                    normalisation factor.  Needs the FP32 history. */
 enum { LC_NEAR_NGP = 0, LC_NEAR_SUBCELL = 1 };
 
+/* How a source's luminosity is assigned to the grid (the source term f_n of
+ * Eq. 11 and Eq. 17, l^3 absorbed), in integer fixed point either way: a unit
+ * S = 2^(E-62) with n_src * max(lum) < 2^E, q = rint(lum / S) per source, and
+ * int64 sums per cell, so the grid is bit-exact and independent of source
+ * order.
+ *   LC_DEPOSIT_NGP: all of q to the nearest cell centre,
+ *                   i = floor(x / l + 1/2) mod N per axis;
+ *   LC_DEPOSIT_CIC: cloud in cell: along each axis the two cell centres
+ *                   around the source, i0 = floor(x / l) and i0 + 1 (mod N),
+ *                   with weights 1 - f and f, f = x / l - i0; q is split along
+ *                   x, each part along y, each of those along z, the upper
+ *                   part of a split being min(q', rint(q' f)) and the lower
+ *                   the rest, so the 8 integer shares sum to q exactly. */
+enum { LC_DEPOSIT_NGP = 0, LC_DEPOSIT_CIC = 1 };
+
+/* Which horizon the Lyman-Werner kernel is cut at (LC_KERNEL_LW only).
+ *   LC_HORIZON_EQ15:  f_mod of Eq. 15, zero where r / alpha(z_s) > 97.39;
+ *   LC_HORIZON_ROUGH: the rough horizon of Section 1, r <= 100 [21 / (1 + z_s)]^0.5
+ *                     Mpc, with z the emission redshift z_s; inside it f_mod of
+ *                     Eq. 15 without its cut, clamped at 0 (it turns negative at
+ *                     r / alpha = 116.29 ln(1.7 / 0.7)^(1 / 0.68), about 97.54). */
+enum { LC_HORIZON_EQ15 = 0, LC_HORIZON_ROUGH = 1 };
+
 /* How time is sliced (step 1 of Section 2.2) and how the field is evaluated.
  * Step s spans [tau_s, tau_{s+1}] and is observed at its end, tau_{s+1}; the
  * sources pushed at step s stand for the source term frozen over that step
@@ -116,7 +139,12 @@ typedef struct {
     int kernel;            /* LC_KERNEL_LW (0, default) or LC_KERNEL_EXP */
     double kernel_length;  /* LC_KERNEL_EXP: attenuation length lambda > 0, comoving Mpc */
     double kernel_rmax;    /* LC_KERNEL_EXP: cut-off radius r_max > 0, comoving Mpc */
-    int near_mode;         /* LC_NEAR_NGP (0, default) or LC_NEAR_SUBCELL */
+    int near_mode;         /* LC_NEAR_NGP (0, default) or LC_NEAR_SUBCELL (NGP deposit only) */
+    int deposit;           /* LC_DEPOSIT_NGP (0, default) or LC_DEPOSIT_CIC */
+    int horizon_mode;      /* LC_HORIZON_EQ15 (0, default) or LC_HORIZON_ROUGH (LW kernel only) */
+    int n_shell_max;       /* > 0: at most this many lookback slices per observing step (the newest
+                              ones; the number of stored Green's functions per observing time, which the
+                              paragraph after the algorithm of Section 2.2 lets vary); 0: no cap */
 } lc_steps;
 
 /* Create a plan for an N^3 periodic grid of side box_mpc.
@@ -132,9 +160,10 @@ lc_status lc_plan_create(int n, double box_mpc, const lc_cosmology* cosmo, const
  * "data files" of the paragraph after it.  Idempotent. */
 lc_status lc_plan_prepare(lc_plan* plan, int step_begin, int step_end);
 
-/* Deposit the sources active during step `step` (nearest grid point, integer
- * fixed point: bit-exact and independent of source order) and transform them
- * into the history ring (step 4 of Section 2.2).
+/* Deposit the sources active during step `step` (nearest grid point or cloud
+ * in cell, lc_steps.deposit; integer fixed point: bit-exact and independent of
+ * source order) and transform them into the history ring (step 4 of
+ * Section 2.2).
  *   pos: n_src * 3 doubles (x, y, z in comoving Mpc, any real value; wrapped
  *        periodically), host or device.
  *   lum: n_src doubles, finite and >= 0, host or device.
@@ -347,10 +376,13 @@ lc_status lc_fdiff_map(int64_t n, const float* j_retarded, const float* j_instan
 
 /* --- the hot-path kernels as stand-alone calls (tests, users) --------------- */
 
-/* Nearest-grid-point fixed-point deposit: scale S = 2^(E-62) with
- * n_src * max(lum) < 2^E, q = rint(lum / S), grid[cell] = sum q (int64, N^3,
- * device or host), *total = sum q.  Cell = floor(x / l + 1/2) mod N per axis. */
-lc_status lc_deposit_grid(int n, double box_mpc, int64_t n_src, const double* pos, const double* lum,
+/* The fixed-point deposit of lc_push_sources on its own: scale S = 2^(E-62)
+ * with n_src * max(lum) < 2^E, q = rint(lum / S), grid[cell] = sum of the
+ * shares (int64, N^3, device or host), *total = sum q.  deposit:
+ * LC_DEPOSIT_NGP (cell = floor(x / l + 1/2) mod N per axis) or LC_DEPOSIT_CIC
+ * (the 8 shares of each q described with LC_DEPOSIT_CIC).  Synchronises the
+ * stream; LC_ERR_DEVICE_CHECK if a source was invalid (it is left out). */
+lc_status lc_deposit_grid(int n, double box_mpc, int deposit, int64_t n_src, const double* pos, const double* lum,
                           int64_t* grid, double* scale, int64_t* total, void* cuda_stream);
 
 /* 3D real-to-complex DFT with the forward sign of Eq. 12 (e^{-2 pi i k.x / N},

@@ -27,6 +27,8 @@ STEPS_EXPLICIT, STEPS_EQUAL_TIME, STEPS_EQUAL_TAU = 0, 1, 2
 HISTORY_FP32, HISTORY_BF16 = 0, 1
 KERNEL_LW, KERNEL_EXP = 0, 1  # radial kernels (lc_steps.kernel)
 NEAR_NGP, NEAR_SUBCELL = 0, 1  # near field of the innermost slice (lc_steps.near_mode)
+DEPOSIT_NGP, DEPOSIT_CIC = 0, 1  # source assignment (lc_steps.deposit)
+HORIZON_EQ15, HORIZON_ROUGH = 0, 1  # Lyman-Werner horizon (lc_steps.horizon_mode)
 SUPPORTED_N = (8, 16, 32, 64, 96, 128, 192, 256, 384, 512)
 PHASES = ("deposit", "r2c_z", "fwd_y", "fwd_x_ring", "mac_x", "inv_y", "c2r_z", "near")
 
@@ -64,7 +66,8 @@ class _Steps(ctypes.Structure):
                 ("z_end", ctypes.c_double), ("n_shell", ctypes.c_int), ("subsamples", ctypes.c_int),
                 ("history", ctypes.c_int), ("normalise", ctypes.c_int), ("out_unit", ctypes.c_double),
                 ("kernel", ctypes.c_int), ("kernel_length", ctypes.c_double), ("kernel_rmax", ctypes.c_double),
-                ("near_mode", ctypes.c_int)]
+                ("near_mode", ctypes.c_int), ("deposit", ctypes.c_int), ("horizon_mode", ctypes.c_int),
+                ("n_shell_max", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -107,7 +110,7 @@ SIGNATURES = [
     ("lc_plan_set_timing", _I, [_P, _I]),
     ("lc_plan_timing", _I, [_P, _DP, ctypes.POINTER(_I64), _I]),
     ("lc_kernel_launches", ctypes.c_uint64, []),
-    ("lc_deposit_grid", _I, [_I, _D, _I64, _VP, _VP, _VP, _DP, ctypes.POINTER(_I64), _VP]),
+    ("lc_deposit_grid", _I, [_I, _D, _I, _I64, _VP, _VP, _VP, _DP, ctypes.POINTER(_I64), _VP]),
     ("lc_fft_r2c", _I, [_I, _VP, _VP, _VP]),
     ("lc_fft_c2r", _I, [_I, _VP, _VP, ctypes.c_float, _VP]),
     ("lc_fft_r2c_static", _I, [_I, _VP, _VP, _VP]),
@@ -178,7 +181,8 @@ def _ptr(x, dtype) -> Tuple[int, object]:
     return a.ctypes.data, a
 
 
-def _steps_struct(spec, subsamples=4, history=HISTORY_FP32, normalise=1, out_unit=1.0, kernel=None, near_mode=0):
+def _steps_struct(spec, subsamples=4, history=HISTORY_FP32, normalise=1, out_unit=1.0, kernel=None, near_mode=0,
+                  deposit=DEPOSIT_NGP, horizon_mode=HORIZON_EQ15, n_shell_max=0):
     z = None
     zp = ctypes.POINTER(ctypes.c_double)()
     if getattr(spec, "z_edges", None) is not None:
@@ -186,7 +190,8 @@ def _steps_struct(spec, subsamples=4, history=HISTORY_FP32, normalise=1, out_uni
         zp = z.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     st = _Steps(int(spec.n_steps), int(spec.kind), zp, float(getattr(spec, "z_start", 0.0)),
                 float(getattr(spec, "z_end", 0.0)), int(getattr(spec, "n_shell", 0)), int(subsamples), int(history),
-                int(normalise), float(out_unit), *_kernel_fields(kernel), int(near_mode))
+                int(normalise), float(out_unit), *_kernel_fields(kernel), int(near_mode), int(deposit),
+                int(horizon_mode), int(n_shell_max))
     return st, z
 
 
@@ -208,11 +213,13 @@ class Plan:
 
     def __init__(self, n: int, box: float, omega_m: float, h: float, steps, subsamples: int = 4,
                  history: int = HISTORY_FP32, normalise: int = 1, out_unit: float = 1.0, stream=None,
-                 kernel=None, near_mode: int = NEAR_NGP):
+                 kernel=None, near_mode: int = NEAR_NGP, deposit: int = DEPOSIT_NGP,
+                 horizon_mode: int = HORIZON_EQ15, n_shell_max: int = 0):
         L = _lib()
         self.n, self.box = int(n), float(box)
         self._cos = _Cosmology(float(omega_m), float(h))
-        self._steps, self._zkeep = _steps_struct(steps, subsamples, history, normalise, out_unit, kernel, near_mode)
+        self._steps, self._zkeep = _steps_struct(steps, subsamples, history, normalise, out_unit, kernel, near_mode,
+                                                 deposit, horizon_mode, n_shell_max)
         self._stream = _stream_ptr(stream)
         h_ = ctypes.c_void_p()
         _check(L.lc_plan_create(self.n, self.box, ctypes.byref(self._cos), ctypes.byref(self._steps),
@@ -230,7 +237,9 @@ class Plan:
     def from_workload(cls, w, stream=None, **kw):
         args = dict(n=w.n, box=w.box, omega_m=w.omega_m, h=w.h, steps=w.steps, subsamples=w.subsamples,
                     history=w.history, normalise=w.normalise, out_unit=w.out_unit, stream=stream,
-                    kernel=getattr(w, "kernel", None), near_mode=getattr(w, "near_mode", 0))
+                    kernel=getattr(w, "kernel", None), near_mode=getattr(w, "near_mode", 0),
+                    deposit=getattr(w, "deposit", DEPOSIT_NGP), horizon_mode=getattr(w, "horizon_mode", HORIZON_EQ15),
+                    n_shell_max=getattr(w, "n_shell_max", 0))
         args.update(kw)
         return cls(**args)
 
@@ -472,8 +481,9 @@ def batch_step(plans, steps, sources, outs):
     _check(_lib().lc_batch_step(hp, n, st, ns, pp, lp, op), "lc_batch_step")
 
 
-def estimate_bytes(n, steps, omega_m, h, history=HISTORY_FP32, kernel=None) -> Tuple[int, int]:
-    st, keep = _steps_struct(steps, 4, history, kernel=kernel)
+def estimate_bytes(n, steps, omega_m, h, history=HISTORY_FP32, kernel=None, horizon_mode=HORIZON_EQ15,
+                   n_shell_max=0) -> Tuple[int, int]:
+    st, keep = _steps_struct(steps, 4, history, kernel=kernel, horizon_mode=horizon_mode, n_shell_max=n_shell_max)
     c = _Cosmology(omega_m, h)
     b = ctypes.c_size_t()
     t = ctypes.c_size_t()
@@ -494,8 +504,9 @@ def fdiff_map(j_retarded, j_instant, out=None, stream=None):
     return out
 
 
-def deposit_grid(n: int, box: float, pos, lum, out=None, stream=None):
-    """Fixed-point NGP deposit on the device: returns (int64 grid, scale, total)."""
+def deposit_grid(n: int, box: float, pos, lum, out=None, stream=None, deposit: int = DEPOSIT_NGP):
+    """Fixed-point deposit (nearest grid point or cloud in cell) on the device:
+    returns (int64 grid, scale, total)."""
     nsrc = int(lum.shape[0])
     if out is None:
         out = np.zeros((n, n, n), dtype=np.int64)
@@ -504,7 +515,7 @@ def deposit_grid(n: int, box: float, pos, lum, out=None, stream=None):
     optr = out.ctypes.data if isinstance(out, np.ndarray) else out.data_ptr()
     S = ctypes.c_double()
     tot = ctypes.c_int64()
-    _check(_lib().lc_deposit_grid(int(n), float(box), nsrc, pp if nsrc else None, lp if nsrc else None, optr,
+    _check(_lib().lc_deposit_grid(int(n), float(box), int(deposit), nsrc, pp if nsrc else None, lp if nsrc else None, optr,
                                   ctypes.byref(S), ctypes.byref(tot), _stream_ptr(stream)), "lc_deposit_grid")
     return out, S.value, tot.value
 
@@ -558,4 +569,4 @@ def fft_c2r(X, scale: Optional[float] = None, stream=None):
 __all__ = ["Plan", "StepGraph", "BatchGraph", "batch_step", "deposit_grid", "fft_r2c", "fft_r2c_static", "fft_c2r",
            "build", "estimate_bytes", "LCError",
            "SIGNATURES", "LIB_PATH", "SUPPORTED_N", "STEPS_EXPLICIT", "STEPS_EQUAL_TIME", "STEPS_EQUAL_TAU",
-           "HISTORY_FP32", "HISTORY_BF16"]
+           "HISTORY_FP32", "HISTORY_BF16", "DEPOSIT_NGP", "DEPOSIT_CIC", "HORIZON_EQ15", "HORIZON_ROUGH"]

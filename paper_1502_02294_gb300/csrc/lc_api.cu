@@ -162,6 +162,8 @@ struct lc_plan {
     Cosmo cosmo{0, 0};
     Kernel kern;
     int n_steps = 0, S = 4, history = 0, normalise = 1;
+    int deposit = LC_DEPOSIT_NGP; // source assignment (LC_DEPOSIT_*)
+    int n_shell_max = 0;          // > 0: at most this many lookback slices per step
     double U = 1.0;
     std::vector<double> z;
     cudaStream_t stream = nullptr;
@@ -419,15 +421,26 @@ bool valid_steps(const lc_steps* st) {
     if (st->kernel == LC_KERNEL_EXP && !(st->kernel_length > 0.0 && isfinite(st->kernel_length) &&
                                          st->kernel_rmax > 0.0 && isfinite(st->kernel_rmax)))
         return false;
+    if (st->deposit != LC_DEPOSIT_NGP && st->deposit != LC_DEPOSIT_CIC) return false;
+    // the sub-cell near field replaces the near cube of a source's NGP cell
+    if (st->deposit == LC_DEPOSIT_CIC && st->near_mode == LC_NEAR_SUBCELL) return false;
+    if (st->horizon_mode != LC_HORIZON_EQ15 && st->horizon_mode != LC_HORIZON_ROUGH) return false;
+    if (st->horizon_mode == LC_HORIZON_ROUGH && st->kernel != LC_KERNEL_LW) return false;
+    if (st->n_shell_max < 0) return false;
     return st->spacing >= 0 && st->spacing <= 2;
 }
 
 Kernel kernel_of(const lc_steps* st) {
     Kernel k;
-    k.kind = st->kernel;
+    k.kind = st->kernel == LC_KERNEL_LW && st->horizon_mode == LC_HORIZON_ROUGH ? kKernelLwRough : st->kernel;
     k.length = st->kernel_length;
     k.rmax = st->kernel_rmax;
     return k;
+}
+
+// entries of the near-field list per source: its one NGP cell, or its 8 CIC cells
+long long near_entries(const lc_plan* p, long long n_src) {
+    return p->near_on ? n_src * (p->deposit == LC_DEPOSIT_CIC ? 8 : 1) : 0;
 }
 
 bool valid_cosmo(const lc_cosmology* c) {
@@ -637,7 +650,7 @@ void evict_tables(lc_plan* p, int s, size_t need) {
 lc_status build_table(lc_plan* p, int s) {
     lc_plan::Table& T = p->tables[s];
     if (T.A >= 0) return LC_OK;
-    StepGeom g = step_geometry(p->cosmo, p->kern, p->z, s, p->l, p->S, true);
+    StepGeom g = step_geometry(p->cosmo, p->kern, p->z, s, p->l, p->S, true, p->n_shell_max);
     const int A = g.A;
     evict_tables(p, s, table_size(p, A));
     cudaError_t e = cudaSuccess;
@@ -820,7 +833,7 @@ lc_status lc_plan_estimate(int n, const lc_steps* steps, const lc_cosmology* cos
     // ring depth from the last step's geometry (the largest horizon)
     int ring = 1;
     for (int s = steps->n_steps - 1; s >= 0 && s >= steps->n_steps - 2; --s) {
-        StepGeom g = step_geometry(c, k, z, s, 1.0, 2, false);
+        StepGeom g = step_geometry(c, k, z, s, 1.0, 2, false, steps->n_shell_max);
         ring = g.A > ring ? g.A : ring;
     }
     const long long nrp = nrp_of(n), spec = (long long)n * n * nrp, slot = (long long)n * n * (n / 2 + 1);
@@ -855,6 +868,8 @@ lc_status lc_plan_create(int n, double box_mpc, const lc_cosmology* cosmo, const
     p->S = steps->subsamples ? steps->subsamples : 4;
     p->history = steps->history;
     p->normalise = steps->normalise ? 1 : 0;
+    p->deposit = steps->deposit;
+    p->n_shell_max = steps->n_shell_max;
     p->U = steps->out_unit > 0.0 ? steps->out_unit : 1.0;
     p->stream = (cudaStream_t)cuda_stream;
     p->ops = ops;
@@ -869,7 +884,7 @@ lc_status lc_plan_create(int n, double box_mpc, const lc_cosmology* cosmo, const
     // active slices per observing step -> ring depth
     p->A_of_step.resize(p->n_steps);
     for (int s = 0; s < p->n_steps; ++s) {
-        StepGeom g = step_geometry(p->cosmo, p->kern, p->z, s, p->l, p->S, false);
+        StepGeom g = step_geometry(p->cosmo, p->kern, p->z, s, p->l, p->S, false, p->n_shell_max);
         if (g.A > kMaxShells) {
             delete p;
             return LC_ERR_UNSUPPORTED_SIZE;
@@ -971,7 +986,7 @@ lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos
             dlum = p->d_lum;
         }
     }
-    if (lc_status r = ensure_near(p, n_src); r != LC_OK) return r;
+    if (lc_status r = ensure_near(p, near_entries(p, n_src)); r != LC_OK) return r;
     const int slot = step % p->n_ring;
     SlotMeta m{slot, step, p->d_slot_step, p->d_slot_S, p->d_slot_total};
     const long long N = p->N;
@@ -983,11 +998,11 @@ lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos
         if (e != cudaSuccess) return cuda_fail(p, e);
         launch_src_prep(dpos, dlum, n_src, p->d_maxbits, p->d_err, m, st);
         if (n_src > 0)
-            launch_deposit(dpos, dlum, n_src, p->N, p->l, p->d_maxbits, p->d_grid, m, p->d_err, st,
+            launch_deposit(dpos, dlum, n_src, p->N, p->l, p->deposit, p->d_maxbits, p->d_grid, m, p->d_err, st,
                            p->near_on ? p->d_src_cell : nullptr, p->near_on ? p->d_src_q : nullptr,
                            p->near_pm ? p->d_src_off : nullptr);
     }
-    p->near_n = p->near_on ? n_src : 0;
+    p->near_n = near_entries(p, n_src);
     RowR2CArgs r{};
     r.in_mode = ROW_IN_I64;
     r.nrows = N * N;
@@ -1197,6 +1212,9 @@ static lc_status field_impl(lc_plan* p, int step, float* out, int instant, uint6
                 na.tab = T.pmtab;
                 na.K = kZsTab;
                 na.kind = p->kern.kind;
+                // Eq. 15's cut as r / (116.29 alpha); none with the rough horizon
+                // (the rough horizon is rtop's bound, f_mod clamped at 0)
+                na.xcut = p->kern.kind == kKernelLwRough ? 3.0e38f : (float)(97.39 / 116.29);
                 na.inv_klen = (float)(1.0 / p->kern.length);
                 na.kmax = (float)p->kern.rmax;
                 na.f0 = T.gnear + (kNearR + 1) * (kNearR + 2) * (kNearR + 3) / 6;
@@ -1287,6 +1305,8 @@ unsigned long long params_hash(const lc_plan* p) {
     mix(&p->kern.length, sizeof p->kern.length);
     mix(&p->kern.rmax, sizeof p->kern.rmax);
     mix(&p->near_pm, sizeof p->near_pm);
+    mix(&p->deposit, sizeof p->deposit);
+    mix(&p->n_shell_max, sizeof p->n_shell_max);
     return h;
 }
 
@@ -1448,7 +1468,7 @@ uint64_t lc_kernel_launches(void) { return g_launches.load(); }
 lc_status lc_step_shells(const lc_plan* p, int step, int* n_active, double* r_lo, double* r_hi, double* r_h,
                          double* shell_integral) {
     if (!p || step < 0 || step >= p->n_steps) return LC_ERR_INVALID_ARG;
-    StepGeom g = step_geometry(p->cosmo, p->kern, p->z, step, p->l, p->S, shell_integral != nullptr);
+    StepGeom g = step_geometry(p->cosmo, p->kern, p->z, step, p->l, p->S, shell_integral != nullptr, p->n_shell_max);
     if (n_active) *n_active = g.A;
     for (int j = 0; j < g.A; ++j) {
         if (r_lo) r_lo[j] = g.lo[j];
@@ -1557,7 +1577,7 @@ static lc_status prepare_capture(lc_plan* p, int step, int64_t n_src, const doub
         return LC_ERR_INVALID_ARG; // a graph holds device pointers only
     lc_status r = build_table(p, step);
     if (r != LC_OK) return r;
-    if (lc_status r2 = ensure_near(p, n_src); r2 != LC_OK) return r2;
+    if (lc_status r2 = ensure_near(p, near_entries(p, n_src)); r2 != LC_OK) return r2;
     return LC_OK;
 }
 
@@ -1629,7 +1649,7 @@ lc_status lc_graph_launch(lc_step_graph* g) {
     cudaError_t e = cudaGraphLaunch(g->exec, p->stream);
     if (e != cudaSuccess) return cuda_fail(p, e);
     p->last_pushed = g->step;
-    p->near_n = p->near_on ? g->n_src : 0;
+    p->near_n = near_entries(p, g->n_src);
     long long tot = 0;
     for (int i = 0; i < LC_N_PHASES; ++i) {
         p->launches[i] += g->kernels[i];
@@ -1754,7 +1774,7 @@ lc_status lc_batch_graph_launch(lc_batch_graph* g, void* stream) {
     }
     for (size_t i = 0; i < g->plans.size(); ++i) {
         g->plans[i]->last_pushed = g->steps[i];
-        g->plans[i]->near_n = g->plans[i]->near_on ? g->n_src[i] : 0;
+        g->plans[i]->near_n = near_entries(g->plans[i], g->n_src[i]);
     }
     count_launch((unsigned long long)g->kernels);
     return LC_OK;
@@ -1778,10 +1798,11 @@ lc_status lc_fdiff_map(int64_t n, const float* j_retarded, const float* j_instan
     return e == cudaSuccess ? LC_OK : LC_ERR_CUDA;
 }
 
-lc_status lc_deposit_grid(int n, double box, int64_t n_src, const double* pos, const double* lum, int64_t* grid,
-                          double* scale, int64_t* total, void* stream) {
+lc_status lc_deposit_grid(int n, double box, int deposit, int64_t n_src, const double* pos, const double* lum,
+                          int64_t* grid, double* scale, int64_t* total, void* stream) {
     if (n < 1 || n > 4096 || !(box > 0.0) || n_src < 0 || !grid || (n_src > 0 && (!pos || !lum)))
         return LC_ERR_INVALID_ARG;
+    if (deposit != LC_DEPOSIT_NGP && deposit != LC_DEPOSIT_CIC) return LC_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     lc_plan tmp; // only for the allocation helper
     const size_t N3 = (size_t)n * n * n;
@@ -1825,7 +1846,7 @@ lc_status lc_deposit_grid(int n, double box, int64_t n_src, const double* pos, c
     SlotMeta m{0, 0, dstep, dS, dtot};
     if (e == cudaSuccess) {
         launch_src_prep(dpos, dlum, n_src, dmax, derr, m, st);
-        if (n_src > 0) launch_deposit(dpos, dlum, n_src, n, box / n, dmax, dgrid, m, derr, st);
+        if (n_src > 0) launch_deposit(dpos, dlum, n_src, n, box / n, deposit, dmax, dgrid, m, derr, st);
         count_launch(n_src > 0 ? 2 : 1);
         e = cudaGetLastError();
     }

@@ -1,10 +1,11 @@
 // lc_device.cu -- source deposit and Green's function builder kernels.
 //
 // Deposit (Eq. 11 with l^3 absorbed into f_n; Eq. 17 source term): nearest
-// grid point, integer fixed point.  The unit S = 2^(E - 62) with
-// n_src * max(L) < 2^E bounds every cell and the total below 2^62 + n_src/2;
-// q_s = rint(L_s / S) is added with 64-bit integer atomics, so the grid and
-// the total are bit-exact and independent of source order.
+// grid point or cloud in cell, integer fixed point.  The unit S = 2^(E - 62)
+// with n_src * max(L) < 2^E bounds every cell and the total below
+// 2^62 + n_src/2; q_s = rint(L_s / S) (or, for cloud in cell, its 8 integer
+// shares, which sum to q_s exactly) is added with 64-bit integer atomics, so
+// the grid and the total are bit-exact and independent of source order.
 //
 // Green's function builder (Eq. 10, step 2 of Section 2.2): for every cell
 // displacement on the symmetric wedge 0 <= a <= b <= c <= N/2, sum the LW
@@ -74,6 +75,31 @@ __device__ __forceinline__ long long ngp_cell(double x, double l, int N) {
     return (i >= 0 && i < N) ? i : 0;
 }
 
+// Cloud in cell along one axis: the cells i0 = floor(x / l) mod N and
+// i0 + 1 (mod N) around x, and the weight f = x / l - floor(x / l) of the
+// upper one, in IEEE double (fmod exact, no contraction).
+__device__ __forceinline__ void cic_axis(double x, double l, int N, long long& i0, long long& i1, double& f) {
+    const double t = __ddiv_rn(x, l);
+    const double fl = floor(t);
+    f = __dsub_rn(t, fl);
+    double m = fmod(fl, (double)N);
+    if (m < 0.0) m += (double)N;
+    long long i = (long long)m;
+    if (i < 0 || i >= N) i = 0;
+    i0 = i;
+    i1 = i + 1 == N ? 0 : i + 1;
+}
+
+// Split an integer share q >= 0 by weight f: the upper cell's part
+// min(q, rint(q f)), the lower cell's the rest (the two always sum to q).
+__device__ __forceinline__ void split_share(long long q, double f, long long& lo, long long& hi) {
+    long long h = __double2ll_rn(__dmul_rn(__ll2double_rn(q), f));
+    h = h > q ? q : (h < 0 ? 0 : h);
+    hi = h;
+    lo = q - h;
+}
+
+template <int CIC>
 __global__ void __launch_bounds__(256)
     k_deposit(const double* __restrict__ pos, const double* __restrict__ lum, long long n, int N, double l,
               const unsigned long long* __restrict__ maxbits, long long* __restrict__ grid, SlotMeta m, int* err,
@@ -92,17 +118,43 @@ __global__ void __launch_bounds__(256)
     if (i < n) {
         const double L = lum[i];
         const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
-        long long c = 0;
-        if (finite_d(L) && L >= 0.0 && finite_d(x) && finite_d(y) && finite_d(z)) {
-            q = llrint(__ddiv_rn(L, S));
-            c = (ngp_cell(x, l, N) * N + ngp_cell(y, l, N)) * N + ngp_cell(z, l, N);
-            if (q) atomicAdd(reinterpret_cast<unsigned long long*>(grid + c), (unsigned long long)q);
+        const bool ok = finite_d(L) && L >= 0.0 && finite_d(x) && finite_d(y) && finite_d(z);
+        if (!ok) atomicOr(err, 1); // an invalid source is left out and reported
+        if constexpr (CIC) {
+            long long cx[2] = {0, 0}, cy[2] = {0, 0}, cz[2] = {0, 0};
+            long long sh[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            if (ok) {
+                q = llrint(__ddiv_rn(L, S));
+                double fx, fy, fz;
+                cic_axis(x, l, N, cx[0], cx[1], fx);
+                cic_axis(y, l, N, cy[0], cy[1], fy);
+                cic_axis(z, l, N, cz[0], cz[1], fz);
+                // split along x, then each part along y, then each of those along z
+                long long qx[2], qxy[4];
+                split_share(q, fx, qx[0], qx[1]);
+                for (int a = 0; a < 2; ++a) split_share(qx[a], fy, qxy[2 * a], qxy[2 * a + 1]);
+                for (int ab = 0; ab < 4; ++ab) split_share(qxy[ab], fz, sh[2 * ab], sh[2 * ab + 1]);
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const long long c = (cx[k >> 2] * N + cy[(k >> 1) & 1]) * N + cz[k & 1];
+                if (sh[k]) atomicAdd(reinterpret_cast<unsigned long long*>(grid + c), (unsigned long long)sh[k]);
+                if (cell_out) {
+                    cell_out[8 * i + k] = c;
+                    q_out[8 * i + k] = sh[k];
+                }
+            }
         } else {
-            atomicOr(err, 1); // an invalid source is left out and reported
-        }
-        if (cell_out) {
-            cell_out[i] = c;
-            q_out[i] = q;
+            long long c = 0;
+            if (ok) {
+                q = llrint(__ddiv_rn(L, S));
+                c = (ngp_cell(x, l, N) * N + ngp_cell(y, l, N)) * N + ngp_cell(z, l, N);
+                if (q) atomicAdd(reinterpret_cast<unsigned long long*>(grid + c), (unsigned long long)q);
+            }
+            if (cell_out) {
+                cell_out[i] = c;
+                q_out[i] = q;
+            }
         }
         if (off_out) {
             // the source relative to its cell centre, in [-l/2, l/2) per axis
@@ -334,7 +386,7 @@ __global__ void __launch_bounds__(256, 2) k_near_pm(NearPmArgs a, double* __rest
     image_range(by, a.L, invL, reach, a.U, vlo, vhi);
     image_range(bz, a.L, invL, reach, a.U, wlo, whi);
     const float inv_h = (float)((a.K - 1) / a.rtop);
-    const float xcut = (float)(97.39 / 116.29); // the LW horizon r = 97.39 alpha (Eq. 16) as r / (116.29 alpha)
+    const float xcut = a.xcut; // Eq. 15's cut r = 97.39 alpha as r / (116.29 alpha); none for the rough horizon
     const float lf = (float)l;
     const float invS = 1.0f / (float)S;
     const float rtop2f = a.rtop2f, win2f = a.win2f;
@@ -377,8 +429,9 @@ __global__ void __launch_bounds__(256, 2) k_near_pm(NearPmArgs a, double* __rest
                                 f = r < a.kmax ? expf(-r * a.inv_klen) : 0.0f;
                             } else {
                                 const float x = r * (t0.y + fr * (t1.y - t0.y)); // r / (116.29 alpha(z_s))
-                                // f_mod of Eq. 15 with x^0.68 = 2^(0.68 log2 x)
-                                f = x > xcut ? 0.0f : 1.7f * expf(-exp2f(0.68f * log2f(x))) - 0.7f;
+                                // f_mod of Eq. 15 with x^0.68 = 2^(0.68 log2 x), clamped at 0
+                                // (only the rough horizon reaches where it turns negative)
+                                f = x > xcut ? 0.0f : fmaxf(1.7f * expf(-exp2f(0.68f * log2f(x))) - 0.7f, 0.0f);
                             }
                             if (f == 0.0f) continue;
                             const float y = __fdividef(hz * f, r2) - comp;
@@ -431,12 +484,16 @@ void launch_src_prep(const double* pos, const double* lum, long long n, unsigned
     launch_k(k_src_prep, 1, kPrepThreads, 0, st, pos, lum, n, maxbits, err, m);
 }
 
-void launch_deposit(const double* pos, const double* lum, long long n, int N, double l,
+void launch_deposit(const double* pos, const double* lum, long long n, int N, double l, int deposit,
                     const unsigned long long* maxbits, long long* grid, SlotMeta m, int* err, cudaStream_t st,
                     long long* cell_out, long long* q_out, double* off_out) {
     const long long blocks = n > 0 ? (n + 255) / 256 : 1;
-    launch_k(k_deposit, (unsigned)blocks, 256, 0, st, pos, lum, n, N, l, maxbits, grid, m, err, cell_out, q_out,
-             off_out);
+    if (deposit == LC_DEPOSIT_CIC)
+        launch_k(k_deposit<1>, (unsigned)blocks, 256, 0, st, pos, lum, n, N, l, maxbits, grid, m, err, cell_out, q_out,
+                 (double*)nullptr);
+    else
+        launch_k(k_deposit<0>, (unsigned)blocks, 256, 0, st, pos, lum, n, N, l, maxbits, grid, m, err, cell_out, q_out,
+                 off_out);
 }
 
 // f_diff = (J_instant - J) / J, the difference taken and divided in FP64 and

@@ -119,20 +119,43 @@ double fmod_lw(double r, double alpha) {
     return 1.7 * exp(-pow(r / (116.29 * alpha), 0.68)) - 0.7;
 }
 
+double rough_horizon(double zs) { return 100.0 * sqrt(21.0 / (1.0 + zs)); }
+
 double kernel_f(const Cosmo& c, const Kernel& k, double zs, double r) {
     if (k.kind == LC_KERNEL_EXP) return r < k.rmax ? exp(-r / k.length) : 0.0;
+    if (k.kind == kKernelLwRough) {
+        // Eq. 15's modulation without its cut, clamped at 0, inside the rough horizon
+        if (r > rough_horizon(zs)) return 0.0;
+        const double f = 1.7 * exp(-pow(r / (116.29 * alpha_lw(c, zs)), 0.68)) - 0.7;
+        return f > 0.0 ? f : 0.0;
+    }
     return fmod_lw(r, alpha_lw(c, zs));
 }
 
-double horizon(const Cosmo& c, const Kernel& k, double zo) {
-    if (k.kind == LC_KERNEL_EXP) return k.rmax;
-    double a = 0.0, b = 97.39 * alpha_lw(c, zo);
+namespace {
+// the radius r (seen from z_obs) where r = h(z_s(r)) for a function h that
+// falls as z_s grows: bisection from [0, h(z_obs)]
+template <class H> double light_cone_root(const Cosmo& c, double zo, H h) {
+    double a = 0.0, b = h(zo);
     for (int it = 0; it < 120 && b - a > 1e-14 * b; ++it) {
         const double m = 0.5 * (a + b);
-        if (m - 97.39 * alpha_lw(c, zs_of_r(c, zo, m)) > 0.0) b = m;
+        if (m - h(zs_of_r(c, zo, m)) > 0.0) b = m;
         else a = m;
     }
     return 0.5 * (a + b);
+}
+// kKernelLwRough: where the unclamped modulation of Eq. 15 reaches 0,
+// r = 116.29 ln(1.7 / 0.7)^(1 / 0.68) alpha(z_s(r))
+double fmod_zero_radius(const Cosmo& c, double zo) {
+    const double x0 = 116.29 * pow(log(1.7 / 0.7), 1.0 / 0.68);
+    return light_cone_root(c, zo, [&](double zs) { return x0 * alpha_lw(c, zs); });
+}
+} // namespace
+
+double horizon(const Cosmo& c, const Kernel& k, double zo) {
+    if (k.kind == LC_KERNEL_EXP) return k.rmax;
+    if (k.kind == kKernelLwRough) return light_cone_root(c, zo, [](double zs) { return rough_horizon(zs); });
+    return light_cone_root(c, zo, [&](double zs) { return 97.39 * alpha_lw(c, zs); });
 }
 
 namespace {
@@ -151,7 +174,10 @@ double gl_integral(const Cosmo& c, const Kernel& k, double zo, double a, double 
 } // namespace
 
 double shell_integral(const Cosmo& c, const Kernel& kern, double zo, double r_lo, double r_hi, double r_h) {
-    const double b = std::min(r_hi, r_h);
+    double b = std::min(r_hi, r_h);
+    // the clamped kernel is 0 beyond its zero: stop there, so that no
+    // quadrature panel straddles the kink
+    if (kern.kind == kKernelLwRough) b = std::min(b, fmod_zero_radius(c, zo));
     if (!(r_lo < b)) return 0.0;
     double s = 0.0;
     if (r_lo <= 0.0) {
@@ -221,11 +247,12 @@ void g_table(const Cosmo& c, const Kernel& k, double zo, double delta, long long
 }
 
 StepGeom step_geometry(const Cosmo& c, const Kernel& k, const std::vector<double>& z, int s, double l, int S,
-                       bool integrals) {
+                       bool integrals, int cap) {
     StepGeom g;
     const double zo = z[s + 1];
     g.rh = horizon(c, k, zo);
     for (int j = 0; j <= s; ++j) {
+        if (cap > 0 && j >= cap) break; // the newest `cap` slices only
         const int n = s - j;
         const double lo = chi(c, zo, z[n + 1]);
         const double hi = chi(c, zo, z[n]);

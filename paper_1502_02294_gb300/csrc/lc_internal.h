@@ -26,10 +26,14 @@ double zs_of_r(const Cosmo& c, double z_obs, double r); // chi(z_obs, z_s) = r
 double alpha_lw(const Cosmo& c, double zs);             // Eq. 16
 double fmod_lw(double r, double alpha);                 // Eq. 15
 // the radial kernel (LC_KERNEL_*): g(r) = (1+z_obs)^3 f(r, z_s) / ((4 pi)^2 (1+z_s) r^2)
+// kKernelLwRough: the LW kernel with the rough horizon of Section 1
+// (LC_KERNEL_LW with LC_HORIZON_ROUGH)
+constexpr int kKernelLwRough = 2;
 struct Kernel {
     int kind = LC_KERNEL_LW;
     double length = 0, rmax = 0; // LC_KERNEL_EXP: f = exp(-r / length) for r < rmax
 };
+double rough_horizon(double zs); // 100 [21 / (1 + z_s)]^0.5 Mpc (Section 1)
 double kernel_f(const Cosmo& c, const Kernel& k, double zs, double r);
 double horizon(const Cosmo& c, const Kernel& k, double z_obs); // LW: r / alpha(z_s(r)) = 97.39
 double shell_integral(const Cosmo& c, const Kernel& k, double z_obs, double r_lo, double r_hi, double r_h);
@@ -45,8 +49,9 @@ struct StepGeom {
     long long Rh = 0;           // largest admissible R inside the horizon
     long long ntab = 0;
 };
+// cap > 0: at most cap lookback slices (the newest)
 StepGeom step_geometry(const Cosmo& c, const Kernel& k, const std::vector<double>& z, int s, double l, int S,
-                       bool integrals);
+                       bool integrals, int cap = 0);
 
 // ---------------- device kernels (lc_device.cu) ----------------
 struct SlotMeta {
@@ -59,12 +64,14 @@ struct SlotMeta {
 // bits of their maximum; marks the slot (step, total = 0).
 void launch_src_prep(const double* pos, const double* lum, long long n, unsigned long long* maxbits, int* err,
                      SlotMeta m, cudaStream_t st);
-// Fixed-point NGP deposit into grid (int64, pre-zeroed), total into slot_total;
-// a source with a non-finite position or luminosity, or a negative one, is
-// left out and sets *err.  cell_out / q_out (may be null): each source's flat
-// cell index and integer luminosity, kept for the near-field correction of
-// the innermost shell.
-void launch_deposit(const double* pos, const double* lum, long long n, int N, double l,
+// Fixed-point deposit (LC_DEPOSIT_NGP or LC_DEPOSIT_CIC) into grid (int64,
+// pre-zeroed), total into slot_total; a source with a non-finite position or
+// luminosity, or a negative one, is left out and sets *err.  cell_out / q_out
+// (may be null): the flat cell index and integer share of each of a source's
+// cells (1 for NGP, 8 for CIC, at [k * n_src ... ] no: at [cells * i + k]),
+// kept for the near-field correction of the innermost shell; off_out (NGP
+// only): each source's position relative to its cell centre.
+void launch_deposit(const double* pos, const double* lum, long long n, int N, double l, int deposit,
                     const unsigned long long* maxbits, long long* grid, SlotMeta m, int* err, cudaStream_t st,
                     long long* cell_out = nullptr, long long* q_out = nullptr, double* off_out = nullptr);
 
@@ -90,7 +97,8 @@ struct NearPmArgs {
     // y = 1 / (116.29 alpha(z_s(r))) for the LW kernel (Eq. 16), else 0
     const float2* tab;
     int K;
-    int kind;               // radial kernel (LC_KERNEL_*)
+    int kind;               // radial kernel (LC_KERNEL_*, or kKernelLwRough)
+    float xcut;             // LW kernels: f = 0 where r / (116.29 alpha) > xcut (Eq. 15's cut; none for the rough horizon)
     float inv_klen, kmax;   // LC_KERNEL_EXP parameters: 1 / length, cut-off
     const double* f0;       // the shell's normalisation factor (device)
     const double* slot_S;

@@ -87,3 +87,25 @@ def test_static_fft_wrapper_rejects_bad_arguments_before_the_library():
         with pytest.raises(ValueError):
             lc.fft_r2c_static(torch.zeros((8, 8, 8), device="cuda"),
                               out=torch.zeros((8, 8, 5), dtype=torch.complex128, device="cuda"))
+
+
+def test_step_options_are_checked_on_the_host(lib):
+    c = lc._Cosmology(0.31, 0.68)
+    out = ctypes.c_void_p()
+    spec = synth.config("c1").steps
+
+    def create(**kw):
+        st, keep = lc._steps_struct(spec, **kw)
+        return lib.lc_plan_create(32, 100.0, ctypes.byref(c), ctypes.byref(st), None, ctypes.byref(out))
+
+    # the sub-cell near field is built on NGP cells; the rough horizon belongs to the LW kernel
+    assert create(deposit=lc.DEPOSIT_CIC, near_mode=lc.NEAR_SUBCELL) == lc.LC_ERR_INVALID_ARG
+    assert create(horizon_mode=lc.HORIZON_ROUGH, kernel=(lc.KERNEL_EXP, 30.0, 80.0)) == lc.LC_ERR_INVALID_ARG
+    assert create(deposit=2) == lc.LC_ERR_INVALID_ARG
+    assert create(horizon_mode=2) == lc.LC_ERR_INVALID_ARG
+    assert create(n_shell_max=-1) == lc.LC_ERR_INVALID_ARG
+    # the cap bounds the ring depth in the host-only estimate
+    w = synth.config("c3")
+    b_full, t_full = lc.estimate_bytes(w.n, w.steps, w.omega_m, w.h, history=lc.HISTORY_BF16)
+    b_cap, t_cap = lc.estimate_bytes(w.n, w.steps, w.omega_m, w.h, history=lc.HISTORY_BF16, n_shell_max=16)
+    assert b_cap < b_full / 4 and t_cap < t_full / 6

@@ -1,10 +1,13 @@
 """Batched uneven instances (one CUDA graph) and the continuous-batching
-server: every result equals the same instance computed alone."""
+server: every result equals the same instance computed alone, and every
+served field matches the FP64 oracle."""
 import numpy as np
 import pytest
 
+import oracle
 import paper_1502_02294_gb300 as lc
 import synth
+from test_gpu_parity import BF16_L2, FP32_L2, FP32_MAX, errors
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -15,6 +18,7 @@ def built():
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA device")
     lc.build()
+    oracle.build()
 
 
 def ulp32(x):
@@ -102,6 +106,15 @@ def test_server_results_alone_equal_mixed():
 
     mixed, st = serve({"s0", "s1", "s2"}, 0.01)
     assert st["requests"] == 12 and st["p99_ms"] >= st["p50_ms"] > 0
+    # every served field against the FP64 oracle (Eq. 11), full grid
+    for k, w in enumerate(ws):
+        P = oracle.Problem.from_workload(w)
+        for s in range(2, 6):
+            rel, mx, raw = errors(mixed[(f"s{k}", s)], oracle.field_for(P, w.cat, s))
+            if w.history == synth.HISTORY_BF16:
+                assert rel <= BF16_L2, (k, s, rel)
+            else:
+                assert rel <= FP32_L2 and mx <= FP32_MAX, (k, s, rel, mx, raw)
     for k, w in enumerate(ws):
         alone, _ = serve({f"s{k}"}, 0.0)
         for key, a in alone.items():

@@ -1,0 +1,85 @@
+"""Parity with the FP64 oracle at the grid sizes the workloads run: the
+512^3 BF16 simulation of the serving set (96 shells) and the 256^3 path with
+FP32 history (128 shells), on sampled cells the oracle evaluates one by one
+(uniform draws plus the x-line through the brightest source).  Definition
+matched: Eq. 11 with the shell Green's functions of Eq. 10 (Section 2.2).
+
+Tolerances: BF16 history relative L2 <= 5e-3; FP32 history relative L2 <=
+1e-5 and the max criterion beyond two FP32 ulps <= 1e-4 of the mean field.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1502_02294_gb300 as lc
+import synth
+from test_gpu_parity import BF16_L2, FP32_L2, FP32_MAX, errors
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    lc.build()
+    oracle.build()
+
+
+def _fields_at(w, check):
+    """Push every step up to max(check) through the plan (device inputs) and
+    return the fields of the steps in `check` (host numpy)."""
+    plan = lc.Plan.from_workload(w)
+    out = {}
+    for s in range(max(check) + 1):
+        pos, lum = w.cat.active(s)
+        plan.push(s, torch.from_numpy(pos).cuda(), torch.from_numpy(lum).cuda())
+        if s in check:
+            out[s] = plan.field(s).cpu().numpy()
+    shells = {s: len(plan.shells(s)[0]) for s in check}
+    plan.close()
+    torch.cuda.empty_cache()
+    return out, shells
+
+
+def _sample(w, s, count, seed):
+    pos, lum = w.cat.active(s)
+    dense = np.floor(pos[np.argmax(lum)] / (w.box / w.n) + 0.5).astype(int) % w.n
+    return synth.sample_cells(seed, w.n, count, dense_line_through=dense)
+
+
+def test_field_512_bf16_served_simulation_sampled_cells():
+    # the 512^3, 96-shell BF16 simulation of the serving workload: a step with
+    # a full ring (96 active shells) and an early one (12 active shells)
+    w = synth.served_simulations()[7]
+    assert w.n == 512 and w.history == synth.HISTORY_BF16
+    P = oracle.Problem.from_workload(w)
+    full = w.steps.n_shell + 3
+    check = {11, full}
+    out, shells = _fields_at(w, check)
+    for s in sorted(check):
+        assert shells[s] == P.active_shells(s) >= 4
+        cells = _sample(w, s, 1200, 9000 + s)
+        ref = oracle.field_for(P, w.cat, s, cells=cells)
+        rel, mx, raw = errors(out[s].reshape(-1)[cells], ref)
+        print(f"512^3 BF16 step {s} ({shells[s]} shells): rel-L2 {rel:.2e} raw max/mean {raw:.2e}")
+        assert rel <= BF16_L2, (s, rel, raw)
+
+
+def test_field_256_fp32_history_sampled_cells():
+    # the 256^3, 200 Mpc, 128-shell path with the spectrum history in FP32
+    w = dataclasses.replace(synth.config("c3"), history=synth.HISTORY_FP32)
+    P = oracle.Problem.from_workload(w)
+    T = w.steps.n_steps
+    check = {T - 1}
+    out, shells = _fields_at(w, check)
+    for s in sorted(check):
+        assert shells[s] == P.active_shells(s) == 128
+        cells = _sample(w, s, 1200, 8000 + s)
+        ref = oracle.field_for(P, w.cat, s, cells=cells)
+        rel, mx, raw = errors(out[s].reshape(-1)[cells], ref)
+        print(f"256^3 FP32 step {s}: rel-L2 {rel:.2e} max beyond 2 ulp / mean {mx:.2e} raw {raw:.2e}")
+        assert rel <= FP32_L2 and mx <= FP32_MAX, (s, rel, mx, raw)
