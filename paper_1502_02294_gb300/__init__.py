@@ -87,6 +87,7 @@ SIGNATURES = [
     ("lc_instant_field", _I, [_P, _I, _VP]),
     ("lc_retarded_field_async", _I, [_P, _I, _VP, ctypes.POINTER(ctypes.c_uint64)]),
     ("lc_plan_wait", _I, [_P, ctypes.c_uint64]),
+    ("lc_plan_poll", _I, [_P, ctypes.c_uint64, ctypes.POINTER(_I)]),
     ("lc_plan_reset", _I, [_P]),
     ("lc_plan_check", _I, [_P]),
     ("lc_plan_set_stream", _I, [_P, _VP]),
@@ -306,6 +307,12 @@ class Plan:
     def wait(self, ticket: int):
         """Block until the output of `ticket` (from field_async) is in place."""
         _check(_lib().lc_plan_wait(self._h, int(ticket)), "lc_plan_wait")
+
+    def poll(self, ticket: int) -> bool:
+        """True once the output of `ticket` (from field_async) is in place; never blocks."""
+        d = ctypes.c_int()
+        _check(_lib().lc_plan_poll(self._h, int(ticket), ctypes.byref(d)), "lc_plan_poll")
+        return bool(d.value)
 
     def instant_field(self, step: int, out=None):
         """Action-at-a-distance field of Eq. 18: every shell sees the sources

@@ -1081,6 +1081,24 @@ lc_status lc_plan_wait(lc_plan* p, uint64_t ticket) {
     return e == cudaSuccess ? LC_OK : cuda_fail(p, e);
 }
 
+lc_status lc_plan_poll(lc_plan* p, uint64_t ticket, int* done) {
+    if (!p || !done) return LC_ERR_INVALID_ARG;
+    if (ticket > p->tickets) return LC_ERR_INVALID_ARG;
+    *done = 0;
+    cudaError_t e;
+    if (ticket == 0) e = cudaStreamQuery(p->stream);
+    else e = cudaEventQuery(p->ev_copied[(ticket - 1) % 2]);
+    if (e == cudaSuccess) {
+        *done = 1;
+        return LC_OK;
+    }
+    if (e == cudaErrorNotReady) {
+        cudaGetLastError();
+        return LC_OK;
+    }
+    return cuda_fail(p, e);
+}
+
 // the stage an asynchronous host output computes into: waits (on the plan's
 // stream) for the copy that last read it
 static cudaError_t async_stage(lc_plan* p, int& k) {

@@ -209,9 +209,11 @@ def batched_instances() -> List[Workload]:
     return out
 
 
-def served_simulations() -> List[Workload]:
+def served_simulations(served_steps: int = 32) -> List[Workload]:
     """8 simulations for the serving loop: N in {128,192,256,256,384,384,512,512},
-    64..128 shells (96 at 512^3), BF16 history, 0.78 Mpc cells."""
+    64..128 shells (96 at 512^3), BF16 history, 0.78 Mpc cells; each runs
+    its shell count of history-filling steps and then `served_steps` steps
+    that requests ask for."""
     grids = [128, 192, 256, 256, 384, 384, 512, 512]
     shells = [128, 112, 96, 128, 96, 64, 96, 96]
     rng = np.random.Generator(np.random.PCG64(SEED_BASE + 4))
@@ -219,7 +221,7 @@ def served_simulations() -> List[Workload]:
     out = []
     for i, (n, sh) in enumerate(zip(grids, shells)):
         box = 0.78125 * n
-        steps = sh + 32
+        steps = sh + served_steps
         st = StepSpec(STEPS_EQUAL_TAU, steps, z_end=15.0, n_shell=sh)
         cat = make_catalogue(SEED_BASE + 2000 + i, int(n_srcs[i]), box, steps,
                              clustered=True, n_centres=max(10, int(n_srcs[i]) // 100),
