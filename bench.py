@@ -244,6 +244,14 @@ def max_over_ranks(x, device):
     return float(t.item())
 
 
+def fft_choices():
+    """The FFT pass form in use per grid size (autotuned): {N: name}."""
+    import paper_1502_02294_gb300 as lc
+
+    names = {lc.FFT_STAGES: "stages", lc.FFT_LANES: "lanes"}
+    return {n: names.get(lc.fft_variant(n), "-") for n in lc.SUPPORTED_N if n >= 256}
+
+
 def config_of(workload, w=None, extra=None):
     """The `config` object, the same for both arms of one workload."""
     c = {"workload": f"{workload}: {WORKLOADS[workload]}"}
@@ -573,6 +581,8 @@ def run_serving(args):
         "vs_baseline": None, "dtype": "bf16+f32", "data": "synthetic",
         "config": config_of("c5", extra={"grids": grids, "shells": shells, "requests_per_sim": K}),
         "details": {"hbm_budget_bytes": budget, "admitted_at_once": len(admitted), "slots_per_sim": 4,
+                    "fft_passes": fft_choices(),
+                    "mac_kernel": {k: v for k, v in lc.autotune_report().items() if k.startswith("mac")},
                     "l2": "no flush: every request streams its simulation's history ring (0.55-26 GB, far above "
                           "the 129 MB L2) from HBM",
                     "inputs": "host sources staged through page-locked slots, fields on the device",
@@ -923,6 +933,7 @@ def run_single(args, w, variant, quick=False):
             "config": config_of(args.workload, w, variant),
             "details": {"timed_window": [t0, T], "ring_slots": plan.n_ring,
                         "mac_kernel": dict(sorted(mac_choice.items(), key=lambda kv: int(kv[0][1:]))),
+                        "fft_passes": fft_choices(),
                         "l2": f"flushed between timed steps ({args.flush_mb} MB write outside the events)",
                         "inputs": "device-resident"},
             "cell_shell_mac_per_s": world * mac_cells / t_max,

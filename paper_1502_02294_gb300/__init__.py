@@ -45,6 +45,19 @@ def autotune_report() -> dict:
     return out
 
 
+FFT_STAGES, FFT_LANES = 0, 1  # FFT pass forms (lc_fft_set_variant)
+
+
+def fft_set_variant(n: int, variant: int):
+    """Force the FFT pass form for grid size n (FFT_STAGES or FFT_LANES)."""
+    _check(_lib().lc_fft_set_variant(int(n), int(variant)), "lc_fft_set_variant")
+
+
+def fft_variant(n: int) -> int:
+    """The FFT pass form in use for grid size n (-1: n not supported)."""
+    return int(_lib().lc_fft_variant(int(n)))
+
+
 def kernel_launches() -> int:
     """Kernels liblc has launched in this process."""
     return int(_lib().lc_kernel_launches())
@@ -116,6 +129,8 @@ SIGNATURES = [
     ("lc_fft_c2r", _I, [_I, _VP, _VP, ctypes.c_float, _VP]),
     ("lc_fft_r2c_static", _I, [_I, _VP, _VP, _VP]),
     ("lc_autotune_report", _I, [ctypes.c_char_p, _I]),
+    ("lc_fft_set_variant", _I, [_I, _I]),
+    ("lc_fft_variant", _I, [_I]),
     ("lc_fdiff_map", _I, [_I64, _VP, _VP, _VP, _VP]),
     ("lc_plan_set_table_budget", _I, [_P, ctypes.c_size_t]),
     ("lc_plan_table_bytes", ctypes.c_size_t, [_P]),

@@ -127,6 +127,7 @@ namespace {
 std::mutex g_tune_mu;
 std::map<std::string, int> g_tune;
 bool g_tune_loaded = false;
+std::map<int, int> g_fft_forced; // grid size -> FFT variant forced by lc_fft_set_variant
 
 void tune_load() {
     if (g_tune_loaded) return;
@@ -572,6 +573,142 @@ int choose_mac_variant(lc_plan* p, const lc_plan::Table& T, int s) {
     return best;
 }
 
+const char* const kFftNames[FFT_NVAR] = {"stages", "lanes"};
+
+// One step's FFT passes on the plan's own buffers (forward from the int64
+// grid into ring slot 0, inverse from the work spectrum into the grid's
+// memory viewed as N^3 floats); the grid is all zero, and the caller clears
+// it again afterwards.
+void fft_step_passes(lc_plan* p, cudaStream_t st) {
+    const long long N = p->N;
+    RowR2CArgs r{};
+    r.in_mode = ROW_IN_I64;
+    r.nrows = N * N;
+    r.grid = p->d_grid;
+    r.slot_S = p->d_slot_S;
+    r.slot_total = p->d_slot_total;
+    r.slot = 0;
+    r.bf16 = p->history == LC_HISTORY_BF16;
+    r.zero_in = 1;
+    r.dst = p->d_work;
+    r.tw = p->d_tw;
+    p->ops->rows_r2c(r, st);
+    ColArgs c{};
+    c.axis = 0;
+    c.dir = -1;
+    c.in_mode = COL_IN_PLAIN;
+    c.out_mode = COL_OUT_PLAIN;
+    c.src = p->d_work;
+    c.dst = p->d_work;
+    c.tw = p->d_tw;
+    p->ops->cols(c, st);
+    c.axis = 1;
+    if (p->history == LC_HISTORY_BF16) {
+        c.out_mode = COL_OUT_BF16;
+        c.dst_bf16 = reinterpret_cast<__nv_bfloat162*>(p->d_ring);
+    } else {
+        c.out_mode = COL_OUT_RING_F32;
+        c.dst = reinterpret_cast<float2*>(p->d_ring);
+    }
+    c.n_ring = p->n_ring;
+    c.wslot = 0;
+    p->ops->cols(c, st);
+    ColArgs ci{};
+    ci.axis = 0;
+    ci.dir = 1;
+    ci.in_mode = COL_IN_PLAIN;
+    ci.out_mode = COL_OUT_PLAIN;
+    ci.src = p->d_work;
+    ci.dst = p->d_work;
+    ci.tw = p->d_tw;
+    p->ops->cols(ci, st);
+    RowC2RArgs rc{};
+    rc.nrows = N * N;
+    rc.src = p->d_work;
+    rc.out = reinterpret_cast<float*>(p->d_grid);
+    rc.scale = 1.0f;
+    rc.tw = p->d_tw;
+    p->ops->rows_c2r(rc, st);
+    count_launch(5);
+}
+
+// Pick the FFT pass form for the plan's grid size (plan creation: may
+// synchronise).  Forced by lc_fft_set_variant or LC_FFT_VARIANT, else the
+// process's earlier choice (or the cache file's), else timed: each form runs
+// one step's passes once to warm up, then five times between events; the
+// median decides.  The choice holds for every later plan of this size, so
+// tables built later all use the same passes.
+void choose_fft_variant(lc_plan* p) {
+    const FftOps* ops = p->ops;
+    const int built = ops->cols_variants();
+    if ((built & (built - 1)) == 0) return; // a single form
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto f = g_fft_forced.find(p->N);
+        if (f != g_fft_forced.end()) {
+            ops->set_cols_variant(f->second);
+            return;
+        }
+    }
+    if (const char* f = getenv("LC_FFT_VARIANT")) {
+        for (int v = 0; v < FFT_NVAR; ++v)
+            if (!strcmp(f, kFftNames[v]) && (built >> v & 1)) {
+                ops->set_cols_variant(v);
+                return;
+            }
+    }
+    int dev = 0, major = 0, minor = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    char kb[96];
+    snprintf(kb, sizeof kb, "fft%d/sm%d%d/N%d", FFT_NVAR, major, minor, p->N);
+    const std::string key(kb);
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        tune_load();
+        auto it = g_tune.find(key);
+        if (it != g_tune.end() && it->second < FFT_NVAR && (built >> it->second & 1)) {
+            ops->set_cols_variant(it->second);
+            return;
+        }
+    }
+    cudaStream_t st = p->stream;
+    constexpr int kReps = 5;
+    cudaEvent_t ev[kReps + 1] = {};
+    bool ok = true;
+    for (int r = 0; ok && r <= kReps; ++r) ok = cudaEventCreate(&ev[r]) == cudaSuccess;
+    double ms[MAC_NVAR] = {-1.0, -1.0, -1.0, -1.0};
+    int best = ops->cols_variant();
+    for (int v = 0; ok && v < FFT_NVAR; ++v) {
+        if (!(built >> v & 1)) continue;
+        ops->set_cols_variant(v);
+        fft_step_passes(p, st); // warm-up
+        cudaEventRecord(ev[0], st);
+        for (int r = 0; r < kReps; ++r) {
+            fft_step_passes(p, st);
+            cudaEventRecord(ev[r + 1], st);
+        }
+        cudaEventSynchronize(ev[kReps]);
+        float t[kReps];
+        for (int r = 0; r < kReps; ++r) {
+            t[r] = 0.f;
+            cudaEventElapsedTime(&t[r], ev[r], ev[r + 1]);
+        }
+        std::sort(t, t + kReps);
+        ms[v] = t[kReps / 2];
+        if (ms[best] < 0 || ms[v] < ms[best]) best = v;
+    }
+    for (auto e : ev)
+        if (e) cudaEventDestroy(e);
+    ops->set_cols_variant(best);
+    // the grid's memory held float outputs: clear it for the first deposit
+    cudaMemsetAsync(p->d_grid, 0, sizeof(long long) * (size_t)p->N * p->N * p->N, st);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) return;
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    tune_store(key, best, ms);
+}
+
 constexpr int kZsTab = 4096; // points of the 1 + z_s(r) table of the sub-cell near field
 
 // room for the near-field source lists of n sources (cells, charges, and the
@@ -809,6 +946,21 @@ bool host_sources_ok(long long n, const double* pos, const double* lum) {
 
 extern "C" {
 
+lc_status lc_fft_set_variant(int n, int v) {
+    const FftOps* ops = ops_for(n);
+    if (!ops) return LC_ERR_UNSUPPORTED_SIZE;
+    if (v < 0 || v >= FFT_NVAR || !(ops->cols_variants() >> v & 1)) return LC_ERR_UNSUPPORTED_SIZE;
+    ops->set_cols_variant(v);
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_fft_forced[n] = v;
+    return LC_OK;
+}
+
+int lc_fft_variant(int n) {
+    const FftOps* ops = ops_for(n);
+    return ops ? ops->cols_variant() : -1;
+}
+
 const char* lc_status_string(lc_status s) {
     switch (s) {
     case LC_OK: return "ok";
@@ -928,9 +1080,16 @@ lc_status lc_plan_create(int n, double box_mpc, const lc_cosmology* cosmo, const
     if (e == cudaSuccess && p->near_on) e = cudaMemsetAsync(p->d_near, 0, sizeof(double) * N3, p->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_slot_step, 0xff, sizeof(int) * p->n_ring, p->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_slot_total, 0, sizeof(long long) * p->n_ring, p->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_slot_S, 0, sizeof(double) * p->n_ring, p->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_err, 0, sizeof(int), p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) {
+        free_all(p);
+        delete p;
+        return LC_ERR_CUDA;
+    }
+    choose_fft_variant(p);
+    if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaStreamSynchronize(p->stream)) != cudaSuccess) {
         free_all(p);
         delete p;
         return LC_ERR_CUDA;
@@ -1514,7 +1673,8 @@ int lc_autotune_report(char* buf, int size) {
     std::lock_guard<std::mutex> g(g_tune_mu);
     tune_load();
     std::string out;
-    for (auto& kv : g_tune) out += kv.first + " " + kMacNames[kv.second] + "\n";
+    for (auto& kv : g_tune)
+        out += kv.first + " " + (kv.first.compare(0, 3, "fft") == 0 ? kFftNames[kv.second] : kMacNames[kv.second]) + "\n";
     if (buf && size > 0) {
         const int n = (int)out.size() < size - 1 ? (int)out.size() : size - 1;
         memcpy(buf, out.data(), n);

@@ -42,5 +42,8 @@ const FftOps LC_CAT(fft_ops_, LC_N) = {LC_N,
                                       MacWsCfg<LC_N, true, false>::OK ? &mac_ws_bf16 : nullptr,
                                       MacWsCfg<LC_N, false, true>::OK ? &mac_ws2_f32 : nullptr,
                                       MacWsCfg<LC_N, true, true>::OK ? &mac_ws2_bf16 : nullptr,
-                                      LC_N * Launch<LC_N>::NCH};
+                                      LC_N * Launch<LC_N>::NCH,
+                                      &Launch<LC_N>::variants_built,
+                                      &Launch<LC_N>::set_variant,
+                                      &Launch<LC_N>::get_variant};
 } // namespace lc

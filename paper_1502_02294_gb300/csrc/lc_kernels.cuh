@@ -511,6 +511,324 @@ __global__ void __launch_bounds__(cols_pl_threads(N)) k_cols_pl(ColArgs a, int n
 }
 
 // ------------------------------------------------------------------------
+// Column passes with one lane per tile column (N = 256 and 512).
+//
+// The tile (N rows x CW columns, dense [N][CW] in shared memory) is
+// transformed by 256 threads in two radix stages, N = 16 G:
+//   stage 1: thread (column c, residue q < G) holds x[q + G p], p < 16, in
+//            registers, applies a 16-point DFT and the twiddle W_N^(q k1),
+//            and writes Y[q][k1] back over the 16 elements it read (rows
+//            k1 G + q are exactly rows q + G p), so no barrier is needed
+//            before the write;
+//   stage 2 (after one barrier): thread (c, k1) takes Y[q][k1] over q and
+//            applies the G-point DFT: a 16-point DFT in registers (G = 16),
+//            or (G = 32) two 16-point DFTs over the even and odd q, held by
+//            the two lanes 8 apart, combined by one radix-2 step through a
+//            warp shuffle.
+// Lanes of a warp always touch whole 64- or 128-byte row segments of the
+// tile, so every shared-memory access is free of bank conflicts, and each
+// thread ends with 16 outputs of its column, at rows tb + 16 k (k < 16).
+template <int N> __host__ __device__ constexpr bool cols_lanes_ok() { return N == 256 || N == 512; }
+
+template <int N, int DIR>
+__device__ __forceinline__ void fft_cols_lanes(float2* __restrict__ buf, const float2* __restrict__ tw, float2 (&v)[16],
+                                               int& col, int& tb) {
+    constexpr int CW = cw_of(N), G = N / 16;
+    static_assert(CW * G == 256, "256 threads: one per (column, residue)");
+    const int tid = threadIdx.x;
+    {
+        const int c = tid % CW, q = tid / CW;
+#pragma unroll
+        for (int p = 0; p < 16; ++p) v[p] = buf[(q + G * p) * CW + c];
+        dft16<DIR>(v);
+#pragma unroll
+        for (int k1 = 1; k1 < 16; ++k1) {
+            float2 w = tw[q * k1]; // W_N^(q k1), q k1 < N
+            if (DIR > 0) w.y = -w.y;
+            v[k1] = cmul(v[k1], w);
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < 16; ++k1) buf[(k1 * G + q) * CW + c] = v[k1];
+    }
+    __syncthreads();
+    if constexpr (G == 16) {
+        const int c = tid % 16, k1 = tid / 16;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = buf[(k1 * 16 + q) * 16 + c];
+        dft16<DIR>(v); // v[k2] = X[k1 + 16 k2]
+        col = c;
+        tb = k1;
+    } else {
+        // q = 2 m + b: E_b = 16-point DFT over m; X[k1 + 16 (k2 + 16 c')] = E_0 + (-1)^c' W_32^k2 E_1
+        const int c = tid % 8, b = (tid >> 3) & 1, k1 = tid >> 4;
+#pragma unroll
+        for (int m = 0; m < 16; ++m) v[m] = buf[(k1 * 32 + 2 * m + b) * 8 + c];
+        dft16<DIR>(v);
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) {
+            const float2 f = make_float2(__shfl_xor_sync(0xffffffffu, v[k2].x, 8),
+                                         __shfl_xor_sync(0xffffffffu, v[k2].y, 8));
+            float2 w = tw[16 * k2]; // W_512^(16 k2) = W_32^k2
+            if (DIR > 0) w.y = -w.y;
+            v[k2] = b == 0 ? cadd(v[k2], cmul(w, f)) : csub(f, cmul(w, v[k2]));
+        }
+        col = c;
+        tb = k1 + 256 * b;
+    }
+}
+
+// The pipelined persistent column pass with fft_cols_lanes: as k_cols_pl
+// (tiles copied by 16-byte asynchronous copies into S shared-memory stages,
+// S - 1 in flight), with 256 threads and the outputs written straight from
+// registers (two or four whole row segments per warp store).
+__host__ __device__ constexpr int cols_lanes_threads() { return 256; }
+template <int N, int DIR, int OUT>
+__global__ void __launch_bounds__(cols_lanes_threads()) k_cols_lanes(ColArgs a, int ntiles) {
+    constexpr int NT = cols_lanes_threads();
+    constexpr int CW = cw_of(N), M = N / 2, S = cols_pl_stages(N);
+    constexpr int TILE = N * CW;
+    static_assert(cols_lanes_ok<N>(), "N = 256 or 512");
+    extern __shared__ float4 smem_raw[];
+    float2* tw = reinterpret_cast<float2*>(smem_raw);
+    float2* stages = tw + N;
+    for (int i = threadIdx.x; i < N; i += NT) tw[i] = a.tw[i];
+    auto load = [&](int tile, float2* dst) {
+        const ColGeom<N> g(tile + a.tile0, a.axis);
+        if (!g.nyq) {
+            for (int c = threadIdx.x; c < TILE / 2; c += NT) ldgsts16(dst + 2 * c, a.src + g.at(2 * c));
+        } else {
+            for (int i = threadIdx.x; i < TILE; i += NT) ldgsts8(dst + i, a.src + g.at(i));
+        }
+    };
+#pragma unroll
+    for (int k = 0; k < S - 1; ++k) {
+        const int t = blockIdx.x + k * gridDim.x;
+        if (t < ntiles) load(t, stages + k * TILE);
+        ldgsts_commit();
+    }
+    for (int k = 0;; ++k) {
+        const int tile = blockIdx.x + k * gridDim.x;
+        if (tile >= ntiles) break;
+        const int nt = blockIdx.x + (k + S - 1) * gridDim.x;
+        if (nt < ntiles) load(nt, stages + ((k + S - 1) % S) * TILE);
+        ldgsts_commit();
+        ldgsts_wait<S - 1>();
+        __syncthreads();
+        float2* buf = stages + (k % S) * TILE;
+        float2 v[16];
+        int col, tb;
+        fft_cols_lanes<N, DIR>(buf, tw, v, col, tb);
+        const ColGeom<N> g(tile + a.tile0, a.axis);
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            const int t = tb + 16 * kk;
+            const int idx = t * CW + col;
+            if constexpr (OUT == COL_OUT_PLAIN) {
+                a.dst[g.at(idx)] = v[kk];
+            } else if constexpr (OUT == COL_OUT_BF16) {
+                a.dst_bf16[((long long)(tile + a.tile0) * a.n_ring + a.wslot) * TILE + idx] =
+                    __floats2bfloat162_rn(v[kk].x, v[kk].y);
+            } else if constexpr (OUT == COL_OUT_RING_F32) {
+                a.dst[((long long)(tile + a.tile0) * a.n_ring + a.wslot) * TILE + idx] = v[kk];
+            } else {
+                const int q = g.nyq ? g.line + col : g.line;
+                const int r = g.nyq ? M : g.chunk * CW + col;
+                if (t <= q && q <= r) a.wedge_out[wedge_index(t, q, r) * a.wedge_A + a.wedge_j] = v[kk].x;
+            }
+        }
+        __syncthreads(); // the stage is read out before it is refilled
+    }
+    ldgsts_wait<0>();
+}
+
+// ------------------------------------------------------------------------
+// z passes with one row pair per group of G = N / 16 lanes (N = 256: a half
+// warp, N = 512: a warp).  The two real rows a, b of a pair are transformed
+// as one complex row z = a + i b (Eq. 12 along z), N = 16 G:
+//   stage 1: lane q holds z[q + G p], p < 16: 16-point DFT, twiddle
+//            W_N^(q k1), written to a warp-private exchange buffer at
+//            k1 (G + 1) + q (the skew keeps both directions free of bank
+//            conflicts);
+//   stage 2: G = 16: lane k1 reads Y[q][k1] over q, 16-point DFT:
+//            Z[k1 + 16 k2]; G = 32: lane (k1, b) reads the even (b = 0) or
+//            odd q, 16-point DFT, and one radix-2 step with lane ^ 1 through
+//            a shuffle: Z[k1 + 16 k2 + 256 b].
+// Only warp-level synchronisation is needed: a group never waits for the
+// rest of the block.  Row pairs are assigned per warp, so both half warps of
+// a warp run the same number of iterations.
+template <int N> __host__ __device__ constexpr bool rows_lanes_ok() { return N == 256 || N == 512; }
+constexpr int kRowsLanesThreads = 256;
+template <int N> __host__ __device__ constexpr int rows_lanes_ex() {
+    return 16 * (N / 16 + 1) > N + 2 ? 16 * (N / 16 + 1) : N + 2; // float2 per group's exchange buffer
+}
+template <int N> __host__ __device__ constexpr size_t rows_lanes_smem_bytes() {
+    return sizeof(float2) * ((size_t)N + (size_t)(kRowsLanesThreads / (N / 16)) * rows_lanes_ex<N>());
+}
+
+// In: v[p] = z[q + G p] of this lane (q = lane within its group).  Out: this
+// lane's 16 outputs Z[t0 + 16 k], k < 16, t0 returned.
+template <int N, int DIR>
+__device__ __forceinline__ int fft_row_lanes(float2 (&v)[16], float2* __restrict__ ex, const float2* __restrict__ tw,
+                                             int q) {
+    constexpr int G = N / 16, XS = G + 1;
+    dft16<DIR>(v);
+#pragma unroll
+    for (int k1 = 1; k1 < 16; ++k1) {
+        float2 w = tw[q * k1];
+        if (DIR > 0) w.y = -w.y;
+        v[k1] = cmul(v[k1], w);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) ex[k1 * XS + q] = v[k1];
+    __syncwarp();
+    if constexpr (G == 16) {
+#pragma unroll
+        for (int qq = 0; qq < 16; ++qq) v[qq] = ex[q * XS + qq];
+        dft16<DIR>(v);
+        __syncwarp();
+        return q;
+    } else {
+        const int k1 = q >> 1, b = q & 1;
+#pragma unroll
+        for (int m = 0; m < 16; ++m) v[m] = ex[k1 * XS + 2 * m + b];
+        dft16<DIR>(v);
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) {
+            const float2 f = make_float2(__shfl_xor_sync(0xffffffffu, v[k2].x, 1),
+                                         __shfl_xor_sync(0xffffffffu, v[k2].y, 1));
+            float2 w = tw[16 * k2]; // W_32^k2
+            if (DIR > 0) w.y = -w.y;
+            v[k2] = b == 0 ? cadd(v[k2], cmul(w, f)) : csub(f, cmul(w, v[k2]));
+        }
+        __syncwarp();
+        return k1 + 256 * b;
+    }
+}
+
+// z forward, real -> complex: int64 deposit grid (times the slot's scale,
+// cleared after reading when zero_in) or float input; output rows of NRP.
+template <int N, int IN>
+__global__ void __launch_bounds__(kRowsLanesThreads, 2) k_rows_r2c_lanes(RowR2CArgs a, long long npairs) {
+    constexpr int G = N / 16, PW = 32 / G, NRP = nrp_of(N), H = N / 2 + 1, EX = rows_lanes_ex<N>();
+    static_assert(IN == ROW_IN_I64 || IN == ROW_IN_F32, "grid or float input");
+    extern __shared__ float4 smem_raw[];
+    float2* tw = reinterpret_cast<float2*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane / G, q = lane % G;
+    float2* ex = tw + N + (warp * PW + grp) * EX;
+    for (int i = threadIdx.x; i < N; i += kRowsLanesThreads) tw[i] = a.tw[i];
+    float scale = 1.0f;
+    if constexpr (IN == ROW_IN_I64) {
+        const double Su = a.slot_S[a.slot];
+        const long long tot = a.slot_total[a.slot];
+        // as k_rows_r2c: S per unit (FP32 history), 1 / total (BF16 history)
+        scale = a.bf16 ? (tot > 0 ? (float)(1.0 / (double)tot) : 0.0f) : (float)Su;
+    }
+    __syncthreads();
+    const long long nwarps = (long long)gridDim.x * (kRowsLanesThreads / 32);
+    for (long long u = (long long)blockIdx.x * (kRowsLanesThreads / 32) + warp; u * PW < npairs; u += nwarps) {
+        const long long rp = u * PW + grp; // npairs is a multiple of PW: every group of the warp has a pair
+        const long long ra = 2 * rp * N, rb = ra + N;
+        float2 v[16];
+        if constexpr (IN == ROW_IN_I64) {
+            long long xa[16], xb[16];
+#pragma unroll
+            for (int p = 0; p < 16; ++p) {
+                xa[p] = a.grid[ra + q + G * p];
+                xb[p] = a.grid[rb + q + G * p];
+            }
+            if (a.zero_in) {
+                long long* g = const_cast<long long*>(a.grid);
+#pragma unroll
+                for (int p = 0; p < 16; ++p) {
+                    g[ra + q + G * p] = 0;
+                    g[rb + q + G * p] = 0;
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < 16; ++p) v[p] = make_float2(__ll2float_rn(xa[p]) * scale, __ll2float_rn(xb[p]) * scale);
+        } else {
+#pragma unroll
+            for (int p = 0; p < 16; ++p) v[p] = make_float2(a.fin[ra + q + G * p], a.fin[rb + q + G * p]);
+        }
+        const int t0 = fft_row_lanes<N, -1>(v, ex, tw, q);
+        // Z in natural order, then the two real rows' half spectra:
+        // X_a = (Z_k + conj Z_{N-k}) / 2, X_b = (Z_k - conj Z_{N-k}) / (2 i)
+#pragma unroll
+        for (int k = 0; k < 16; ++k) ex[t0 + 16 * k] = v[k];
+        __syncwarp();
+        float2* da = a.dst + (2 * rp) * NRP;
+        float2* db = da + NRP;
+#pragma unroll
+        for (int m = 0; m < (H + G - 1) / G; ++m) {
+            const int k = q + G * m;
+            if (k < H) {
+                const float2 zk = ex[k], zn = ex[k == 0 ? 0 : N - k];
+                da[k] = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
+                db[k] = make_float2(0.5f * (zk.y + zn.y), 0.5f * (zn.x - zk.x));
+            }
+        }
+        __syncwarp(); // the exchange buffer is free for the next pair
+    }
+}
+
+// z inverse, complex -> real, times `scale`: rows of NRP in, N floats out.
+template <int N>
+__global__ void __launch_bounds__(kRowsLanesThreads, 2) k_rows_c2r_lanes(RowC2RArgs a, long long npairs) {
+    constexpr int G = N / 16, PW = 32 / G, NRP = nrp_of(N), H = N / 2 + 1, EX = rows_lanes_ex<N>();
+    static_assert(2 * H <= EX, "both half spectra fit the exchange buffer");
+    extern __shared__ float4 smem_raw[];
+    float2* tw = reinterpret_cast<float2*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane / G, q = lane % G;
+    float2* ex = tw + N + (warp * PW + grp) * EX;
+    for (int i = threadIdx.x; i < N; i += kRowsLanesThreads) tw[i] = a.tw[i];
+    __syncthreads();
+    const long long nwarps = (long long)gridDim.x * (kRowsLanesThreads / 32);
+    for (long long u = (long long)blockIdx.x * (kRowsLanesThreads / 32) + warp; u * PW < npairs; u += nwarps) {
+        const long long rp = u * PW + grp;
+        const float2* sa = a.src + (2 * rp) * NRP;
+        const float2* sb = sa + NRP;
+        float2* xa = ex;
+        float2* xb = ex + H;
+#pragma unroll
+        for (int m = 0; m < (H + G - 1) / G; ++m) {
+            const int k = q + G * m;
+            if (k < H) {
+                float2 A = sa[k], B = sb[k];
+                if (k == 0 || k == N / 2) {
+                    A.y = 0.f;
+                    B.y = 0.f;
+                }
+                xa[k] = A;
+                xb[k] = B;
+            }
+        }
+        __syncwarp();
+        // Z_n = X_a(n) + i X_b(n), with the Hermitian extension X(N - k) = conj X(k)
+        float2 v[16];
+#pragma unroll
+        for (int p = 0; p < 16; ++p) {
+            const int n = q + G * p;
+            if (n < H) {
+                const float2 A = xa[n], B = xb[n];
+                v[p] = make_float2(A.x - B.y, A.y + B.x);
+            } else {
+                const float2 A = xa[N - n], B = xb[N - n];
+                v[p] = make_float2(A.x + B.y, B.x - A.y);
+            }
+        }
+        __syncwarp();
+        const int t0 = fft_row_lanes<N, 1>(v, ex, tw, q);
+        float* oa = a.out + (2 * rp) * N;
+        float* ob = oa + N;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            oa[t0 + 16 * k] = v[k].x * a.scale;
+            ob[t0 + 16 * k] = v[k].y * a.scale;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------
 // z rows, complex -> real, persistent with the next block's loads in flight.
 template <int N>
 __global__ void __launch_bounds__(kThreads) k_rows_c2r(RowC2RArgs a, int nblocks) {
@@ -880,7 +1198,14 @@ struct FftOps {
     void (*mac_ws2_f32)(const MacArgs&, cudaStream_t);
     void (*mac_ws2_bf16)(const MacArgs&, cudaStream_t);
     int full_tiles; // tiles of the full 16-column chunks (the Nyquist tiles follow)
+    // the y / x pass kernel of grids with more than one: FFT_COLS_STAGES
+    // (block-wide Stockham stages) or FFT_COLS_LANES (one lane per column);
+    // chosen by the autotuner or LC_FFT_VARIANT, shared by the process
+    int (*cols_variants)();          // bit mask of the variants built for this N
+    void (*set_cols_variant)(int);
+    int (*cols_variant)();
 };
+enum { FFT_COLS_STAGES = 0, FFT_COLS_LANES = 1, FFT_NVAR = 2 };
 
 template <int N> struct Launch {
     static constexpr int CW = cw_of(N), NCH = (N / 2) / CW;
@@ -917,7 +1242,40 @@ template <int N> struct Launch {
         return ctas;
     }
     static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+    // the column-pass variant in use (FFT_COLS_*)
+    static int& variant() {
+        static int v = cols_lanes_ok<N>() ? FFT_COLS_LANES : FFT_COLS_STAGES;
+        return v;
+    }
+    static int variants_built() { return (1 << FFT_COLS_STAGES) | (cols_lanes_ok<N>() ? 1 << FFT_COLS_LANES : 0); }
+    static void set_variant(int v) {
+        if (v >= 0 && v < FFT_NVAR && (variants_built() >> v & 1)) variant() = v;
+    }
+    static int get_variant() { return variant(); }
+    template <int DIR, int OUT> static int cols_lanes_ctas() {
+        static int ctas = 0;
+        if (!ctas) {
+            int occ = 0;
+            if constexpr (cols_lanes_ok<N>()) {
+                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cols_lanes<N, DIR, OUT>, cols_lanes_threads(),
+                                                                  cols_pl_smem_bytes<N>()) != cudaSuccess || occ <= 0) {
+                    cudaGetLastError();
+                    occ = 1;
+                }
+            }
+            ctas = (occ > 0 ? occ : 1) * sms();
+        }
+        return ctas;
+    }
     template <int DIR, int OUT> static void cols_plain(const ColArgs& a, int ntiles, cudaStream_t st) {
+        if constexpr (cols_lanes_ok<N>()) {
+            if (variant() == FFT_COLS_LANES && aligned16(a.src)) {
+                const int c = cols_lanes_ctas<DIR, OUT>();
+                launch_k(k_cols_lanes<N, DIR, OUT>, dim3((unsigned)(ntiles < c ? ntiles : c)), cols_lanes_threads(),
+                         cols_pl_smem_bytes<N>(), st, a, ntiles);
+                return;
+            }
+        }
         if constexpr (kColsPl) {
             if (aligned16(a.src)) { // 16-byte copies need a 16-byte aligned source
                 const int c = cols_pl_ctas<DIR, OUT>();
@@ -954,6 +1312,19 @@ template <int N> struct Launch {
             LC_ATTR((k_cols_pl<N, -1, COL_OUT_WEDGE>), ps2);
             LC_ATTR((k_cols_pl<N, -1, COL_OUT_RING_F32>), ps2);
             LC_ATTR((k_cols_pl<N, 1, COL_OUT_PLAIN>), ps2);
+            if constexpr (rows_lanes_ok<N>()) {
+                const int rl = (int)rows_lanes_smem_bytes<N>();
+                LC_ATTR((k_rows_r2c_lanes<N, ROW_IN_I64>), rl);
+                LC_ATTR((k_rows_r2c_lanes<N, ROW_IN_F32>), rl);
+                LC_ATTR((k_rows_c2r_lanes<N>), rl);
+            }
+            if constexpr (cols_lanes_ok<N>()) {
+                LC_ATTR((k_cols_lanes<N, -1, COL_OUT_PLAIN>), ps2);
+                LC_ATTR((k_cols_lanes<N, -1, COL_OUT_BF16>), ps2);
+                LC_ATTR((k_cols_lanes<N, -1, COL_OUT_WEDGE>), ps2);
+                LC_ATTR((k_cols_lanes<N, -1, COL_OUT_RING_F32>), ps2);
+                LC_ATTR((k_cols_lanes<N, 1, COL_OUT_PLAIN>), ps2);
+            }
         } else {
             LC_ATTR((k_cols_pp<N, -1, COL_OUT_PLAIN>), cs);
             LC_ATTR((k_cols_pp<N, -1, COL_OUT_BF16>), cs);
@@ -994,8 +1365,30 @@ template <int N> struct Launch {
         }
         return occ * sms();
     }
+    template <class Kern> static int occ_ctas_t(Kern k, int threads, size_t smem) {
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, threads, smem) != cudaSuccess || occ <= 0) {
+            cudaGetLastError();
+            occ = 1;
+        }
+        return occ * sms();
+    }
     static void rows_r2c(const RowR2CArgs& a, cudaStream_t st) {
         const int nb = (int)row_blocks();
+        if constexpr (rows_lanes_ok<N>()) {
+            if (variant() == FFT_COLS_LANES && (a.in_mode == ROW_IN_I64 || a.in_mode == ROW_IN_F32)) {
+                const long long npairs = a.nrows / 2;
+                const size_t sm = rows_lanes_smem_bytes<N>();
+                if (a.in_mode == ROW_IN_I64) {
+                    static const int c = occ_ctas_t(k_rows_r2c_lanes<N, ROW_IN_I64>, kRowsLanesThreads, sm);
+                    launch_k(k_rows_r2c_lanes<N, ROW_IN_I64>, dim3((unsigned)c), kRowsLanesThreads, sm, st, a, npairs);
+                } else {
+                    static const int c = occ_ctas_t(k_rows_r2c_lanes<N, ROW_IN_F32>, kRowsLanesThreads, sm);
+                    launch_k(k_rows_r2c_lanes<N, ROW_IN_F32>, dim3((unsigned)c), kRowsLanesThreads, sm, st, a, npairs);
+                }
+                return;
+            }
+        }
         if constexpr (kRowsPl) {
             if (a.in_mode == ROW_IN_I64 && !aligned16(a.grid) && a.zero_in) {
                 // the register pass does not zero the grid: clear it after
@@ -1025,6 +1418,14 @@ template <int N> struct Launch {
     }
     static void rows_c2r(const RowC2RArgs& a, cudaStream_t st) {
         const int nb = (int)row_blocks();
+        if constexpr (rows_lanes_ok<N>()) {
+            if (variant() == FFT_COLS_LANES) {
+                const size_t sm = rows_lanes_smem_bytes<N>();
+                static const int c = occ_ctas_t(k_rows_c2r_lanes<N>, kRowsLanesThreads, sm);
+                launch_k(k_rows_c2r_lanes<N>, dim3((unsigned)c), kRowsLanesThreads, sm, st, a, a.nrows / 2);
+                return;
+            }
+        }
         if constexpr (kRowsPl) {
             if (aligned16(a.src)) {
                 static const int c = occ_ctas(k_rows_c2r_pl<N>, rows_c2r_pl_smem_bytes<N>());

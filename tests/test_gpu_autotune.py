@@ -126,3 +126,50 @@ def test_512_bf16_mac_kernels_agree(monkeypatch):
         res[v] = _fields(w, range(8), {7})[7]
     assert np.array_equal(res["gather"], res["ws2"])
     assert np.isfinite(res["ws2"]).all() and res["ws2"].max() > 0
+
+
+@pytest.mark.parametrize("n", [256, 512])
+def test_fft_pass_forms_against_numpy_and_each_other(n):
+    # both forms of the FFT passes (block-wide stages, one lane per column)
+    # against numpy's FP64 transform, Parseval, and the round trip
+    before = lc.fft_variant(n)
+    rng = np.random.default_rng(n + 7)
+    x = rng.standard_normal((n, n, n)).astype(np.float32)
+    xt = torch.from_numpy(x).cuda()
+    ref = np.fft.rfftn(x.astype(np.float64))
+    res = {}
+    try:
+        for v in (lc.FFT_STAGES, lc.FFT_LANES):
+            lc.fft_set_variant(n, v)
+            assert lc.fft_variant(n) == v
+            X = lc.fft_r2c(xt)
+            Xn = X.cpu().numpy().astype(np.complex128)
+            err = np.linalg.norm(Xn - ref) / np.linalg.norm(ref)
+            assert err < 2e-6, (v, err)
+            back = lc.fft_c2r(X).cpu().numpy()
+            assert np.abs(back - x).max() < 1e-5 * np.abs(x).max(), v
+            res[v] = Xn
+    finally:
+        lc.fft_set_variant(n, before)
+    d = np.linalg.norm(res[0] - res[1]) / np.linalg.norm(ref)
+    assert d < 2e-6, d
+
+
+def test_fft_pass_forms_give_oracle_fields():
+    # a 256^3 field with each form of the passes against the FP64 oracle
+    w = synth.small(n=256, box=200.0, n_steps=8, n_src=300, subsamples=2, clustered=True, seed=2561,
+                    z_start=16.0, z_end=15.0, history=synth.HISTORY_FP32)
+    P = oracle.Problem.from_workload(w)
+    pos, lum = w.cat.active(7)
+    dense = np.floor(pos[np.argmax(lum)] / (w.box / w.n) + 0.5).astype(int) % w.n
+    cells = synth.sample_cells(2562, w.n, 1500, dense_line_through=dense)
+    ref = oracle.field_for(P, w.cat, 7, cells=cells)
+    before = lc.fft_variant(256)
+    try:
+        for v in (lc.FFT_STAGES, lc.FFT_LANES):
+            lc.fft_set_variant(256, v)
+            got = _fields(w, range(8), {7})[7].reshape(-1)[cells].astype(np.float64)
+            rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+            assert rel <= FP32_L2, (v, rel)
+    finally:
+        lc.fft_set_variant(256, before)
