@@ -82,9 +82,10 @@ enum { LC_HISTORY_FP32 = 0, LC_HISTORY_BF16 = 1 };
  *                  (lambda = kernel_length, r_max = kernel_rmax, comoving Mpc). */
 enum { LC_KERNEL_LW = 0, LC_KERNEL_EXP = 1 };
 
-/* The near field of the innermost slice (FP32 history).  The 5^3 cells around
- * each source's NGP cell are taken out of the FFT path of the innermost shell
- * and added per source in FP64:
+/* The near field of the innermost slice.  The 5^3 cells around each source's
+ * cell (each of its 8 cells with the cloud-in-cell deposit) are taken out of
+ * the FFT path of the innermost shell and added per source in FP64, so the
+ * largest Green's-function values never pass through FP32 (or BF16) spectra:
  *   LC_NEAR_NGP:     with the source at its cell centre (the grid Green's
  *                    function itself, so the field is exactly Eq. 11);
  *   LC_NEAR_SUBCELL: from the source's own position, the particle-mesh hybrid
@@ -92,8 +93,11 @@ enum { LC_KERNEL_LW = 0, LC_KERNEL_EXP = 1 };
  *                    the mesh: each target cell gets the s^3 sub-sample average
  *                    of g around the source (over the periodic images, inside
  *                    the innermost shell and the horizon) times the shell's
- *                    normalisation factor.  Needs the FP32 history. */
-enum { LC_NEAR_NGP = 0, LC_NEAR_SUBCELL = 1 };
+ *                    normalisation factor.  Needs the FP32 history and the NGP
+ *                    deposit;
+ *   LC_NEAR_NONE:    no split: the innermost shell goes through the FFT path
+ *                    whole (no per-source near-field work). */
+enum { LC_NEAR_NGP = 0, LC_NEAR_SUBCELL = 1, LC_NEAR_NONE = 2 };
 
 /* How a source's luminosity is assigned to the grid (the source term f_n of
  * Eq. 11 and Eq. 17, l^3 absorbed), in integer fixed point either way: a unit
@@ -139,7 +143,7 @@ typedef struct {
     int kernel;            /* LC_KERNEL_LW (0, default) or LC_KERNEL_EXP */
     double kernel_length;  /* LC_KERNEL_EXP: attenuation length lambda > 0, comoving Mpc */
     double kernel_rmax;    /* LC_KERNEL_EXP: cut-off radius r_max > 0, comoving Mpc */
-    int near_mode;         /* LC_NEAR_NGP (0, default) or LC_NEAR_SUBCELL (NGP deposit only) */
+    int near_mode;         /* LC_NEAR_NGP (0, default), LC_NEAR_SUBCELL (FP32 history, NGP deposit) or LC_NEAR_NONE */
     int deposit;           /* LC_DEPOSIT_NGP (0, default) or LC_DEPOSIT_CIC */
     int horizon_mode;      /* LC_HORIZON_EQ15 (0, default) or LC_HORIZON_ROUGH (LW kernel only) */
     int n_shell_max;       /* > 0: at most this many lookback slices per observing step (the newest

@@ -26,7 +26,7 @@ LC_ERR_OOM, LC_ERR_CUDA, LC_ERR_TIMEOUT, LC_ERR_DEVICE_CHECK = 4, 5, 6, 7
 STEPS_EXPLICIT, STEPS_EQUAL_TIME, STEPS_EQUAL_TAU = 0, 1, 2
 HISTORY_FP32, HISTORY_BF16 = 0, 1
 KERNEL_LW, KERNEL_EXP = 0, 1  # radial kernels (lc_steps.kernel)
-NEAR_NGP, NEAR_SUBCELL = 0, 1  # near field of the innermost slice (lc_steps.near_mode)
+NEAR_NGP, NEAR_SUBCELL, NEAR_NONE = 0, 1, 2  # near field of the innermost slice (lc_steps.near_mode)
 DEPOSIT_NGP, DEPOSIT_CIC = 0, 1  # source assignment (lc_steps.deposit)
 HORIZON_EQ15, HORIZON_ROUGH = 0, 1  # Lyman-Werner horizon (lc_steps.horizon_mode)
 SUPPORTED_N = (8, 16, 32, 64, 96, 128, 192, 256, 384, 512)

@@ -241,6 +241,11 @@ struct lc_plan {
     // write and read them, so they stay allocated until the plan is destroyed
     std::vector<void*> retired;
     size_t bytes = 0;
+    // the deposit grid holds the charges of the last push until its cells
+    // are cleared; with a near-field list (near_on) only those cells are
+    // zeroed (by the near fold of the step's field, or before the next
+    // deposit when no field ran), never the whole grid
+    bool grid_dirty = false;
     int last_pushed = -1;
     bool failed = false;
     // per-phase event timing
@@ -417,7 +422,8 @@ bool valid_steps(const lc_steps* st) {
     if (st->spacing == LC_STEPS_EQUAL_TAU && (st->n_shell < 1 || !(st->z_end >= 0.0))) return false;
     if (st->spacing == LC_STEPS_EXPLICIT && !st->z_edges) return false;
     if (st->kernel != LC_KERNEL_LW && st->kernel != LC_KERNEL_EXP) return false;
-    if (st->near_mode != LC_NEAR_NGP && st->near_mode != LC_NEAR_SUBCELL) return false;
+    if (st->near_mode != LC_NEAR_NGP && st->near_mode != LC_NEAR_SUBCELL && st->near_mode != LC_NEAR_NONE)
+        return false;
     if (st->near_mode == LC_NEAR_SUBCELL && st->history != LC_HISTORY_FP32) return false;
     if (st->kernel == LC_KERNEL_EXP && !(st->kernel_length > 0.0 && isfinite(st->kernel_length) &&
                                          st->kernel_rmax > 0.0 && isfinite(st->kernel_rmax)))
@@ -442,6 +448,17 @@ Kernel kernel_of(const lc_steps* st) {
 // entries of the near-field list per source: its one NGP cell, or its 8 CIC cells
 long long near_entries(const lc_plan* p, long long n_src) {
     return p->near_on ? n_src * (p->deposit == LC_DEPOSIT_CIC ? 8 : 1) : 0;
+}
+
+// Zero the cells the last push deposited into, if a field has not done so
+// yet (sparse clear: the plan keeps a near-field list); on stream st.
+void clear_grid_cells(lc_plan* p, cudaStream_t st) {
+    if (!p->grid_dirty) return;
+    if (p->near_on) {
+        launch_cells_clear(p->d_src_cell, p->d_src_q, p->near_n, p->d_grid, st);
+        count_launch(1);
+    }
+    p->grid_dirty = false;
 }
 
 bool valid_cosmo(const lc_cosmology* c) {
@@ -1067,7 +1084,7 @@ lc_status lc_plan_create(int n, double box_mpc, const lc_cosmology* cosmo, const
         delete p;
         return LC_ERR_OOM;
     }
-    p->near_on = p->history == LC_HISTORY_FP32;
+    p->near_on = steps->near_mode != LC_NEAR_NONE;
     p->near_pm = p->near_on && steps->near_mode == LC_NEAR_SUBCELL;
     if (p->near_on && dalloc(p, &p->d_near, N3) != cudaSuccess) {
         free_all(p);
@@ -1117,9 +1134,12 @@ lc_status lc_plan_prepare(lc_plan* p, int b, int e) {
     return LC_OK;
 }
 
-// Whether the forward z pass clears the deposit grid as it reads it (the
-// staged pass of N >= 256, which the plane kernels of smaller N are not).
-static bool zeroed_by_r2c(const lc_plan* p) { return p->N >= 256 && !p->ops->plane_r2c; }
+// How the deposit grid is cleared between pushes: with a near-field list,
+// only the cells the push deposited into (sparse clear); without one, the
+// staged z pass of N >= 256 zeroes every block it reads, and smaller grids
+// (plane kernels) are cleared by a memset before each deposit.
+static bool zeroed_by_r2c(const lc_plan* p) { return !p->near_on && p->N >= 256 && !p->ops->plane_r2c; }
+static bool memset_before_deposit(const lc_plan* p) { return !p->near_on && !zeroed_by_r2c(p); }
 
 lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos, const double* lum) {
     if (!p) return LC_ERR_INVALID_ARG;
@@ -1145,15 +1165,16 @@ lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos
             dlum = p->d_lum;
         }
     }
+    // the previous push's cells, if no field has cleared them (its list is
+    // overwritten by this deposit); inside a capture the graph's launch does it
+    if (!p->capturing) clear_grid_cells(p, st);
     if (lc_status r = ensure_near(p, near_entries(p, n_src)); r != LC_OK) return r;
     const int slot = step % p->n_ring;
     SlotMeta m{slot, step, p->d_slot_step, p->d_slot_S, p->d_slot_total};
     const long long N = p->N;
     {
         Phase ph(p, LC_PHASE_DEPOSIT, n_src > 0 ? 2 : 1);
-        // the staged z pass (N >= 256) leaves the grid zero after reading it;
-        // smaller grids are cleared here
-        if (!zeroed_by_r2c(p)) e = cudaMemsetAsync(p->d_grid, 0, sizeof(long long) * N * N * N, st);
+        if (memset_before_deposit(p)) e = cudaMemsetAsync(p->d_grid, 0, sizeof(long long) * N * N * N, st);
         if (e != cudaSuccess) return cuda_fail(p, e);
         launch_src_prep(dpos, dlum, n_src, p->d_maxbits, p->d_err, m, st);
         if (n_src > 0)
@@ -1162,6 +1183,7 @@ lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos
                            p->near_pm ? p->d_src_off : nullptr);
     }
     p->near_n = near_entries(p, n_src);
+    if (n_src > 0) p->grid_dirty = true;
     RowR2CArgs r{};
     r.in_mode = ROW_IN_I64;
     r.nrows = N * N;
@@ -1403,8 +1425,14 @@ static lc_status field_impl(lc_plan* p, int step, float* out, int instant, uint6
                 launch_near_scatter(p->d_src_cell, p->d_src_q, p->near_n, p->N, T.gnear, p->d_slot_S, nslot, p->U,
                                     p->d_near, st);
             }
-            launch_near_fold(p->d_src_cell, p->d_src_q, p->near_n, p->N, p->d_near, dout, st);
+            launch_near_fold(p->d_src_cell, p->d_src_q, p->near_n, p->N, p->d_near, dout, p->d_grid, st);
+            p->grid_dirty = false; // the fold cleared the deposit cells
         }
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && p->grid_dirty && p->near_on) {
+        // no fold ran (no active shell, or no sources): clear the cells here
+        clear_grid_cells(p, st);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && async_out) {
@@ -1556,6 +1584,7 @@ lc_status lc_plan_load(lc_plan* p, const void* buf, size_t size) {
         h.near_n < 0 || (!p->near_on && h.near_n != 0))
         return LC_ERR_INVALID_ARG;
     if (size < sizeof h + align256(meta_bytes_of(p, h.near_n)) + ring_bytes_of(p)) return LC_ERR_INVALID_ARG;
+    clear_grid_cells(p, st); // the current list's cells, before the list is replaced
     if (lc_status r = ensure_near(p, h.near_n); r != LC_OK) return r;
     const unsigned char* b = static_cast<const unsigned char*>(buf);
     const size_t nr = (size_t)p->n_ring;
@@ -1779,6 +1808,7 @@ lc_status lc_graph_create(lc_plan* p, int step, int64_t n_src, const double* pos
     }
     const int saved_last = p->last_pushed;
     const long long saved_near = p->near_n;
+    const bool saved_dirty = p->grid_dirty;
     const size_t marks0 = p->marks.size();
     for (int i = 0; i < LC_N_PHASES; ++i) p->cap_kernels[i] = 0;
     p->stream = cap_stream;
@@ -1797,6 +1827,7 @@ lc_status lc_graph_create(lc_plan* p, int step, int64_t n_src, const double* pos
     p->stream = user_stream;
     p->last_pushed = saved_last;
     p->near_n = saved_near;
+    p->grid_dirty = saved_dirty;
     g->marks.assign(p->marks.begin() + marks0, p->marks.end());
     p->marks.resize(marks0);
     for (int i = 0; i < LC_N_PHASES; ++i) g->kernels[i] = p->cap_kernels[i];
@@ -1824,8 +1855,10 @@ lc_status lc_graph_launch(lc_step_graph* g) {
     if (p->failed) return LC_ERR_CUDA;
     if (g->step <= p->last_pushed) return LC_ERR_STEP_ORDER;
     harvest_graph(p, g); // its previous replay, long finished in a step cycle
+    clear_grid_cells(p, p->stream); // a push outside the graph left its cells (the graph's field clears its own)
     cudaError_t e = cudaGraphLaunch(g->exec, p->stream);
     if (e != cudaSuccess) return cuda_fail(p, e);
+    p->grid_dirty = false;
     p->last_pushed = g->step;
     p->near_n = near_entries(p, g->n_src);
     long long tot = 0;
@@ -1902,6 +1935,7 @@ lc_status lc_batch_graph_create(lc_plan* const* plans, int n, const int* steps, 
             const cudaStream_t user_stream = p->stream;
             const int saved_last = p->last_pushed;
             const long long saved_near = p->near_n;
+            const bool saved_dirty = p->grid_dirty;
             const bool saved_timing = p->timing;
             for (int k = 0; k < LC_N_PHASES; ++k) p->cap_kernels[k] = 0;
             p->stream = br[i];
@@ -1916,6 +1950,7 @@ lc_status lc_batch_graph_create(lc_plan* const* plans, int n, const int* steps, 
             p->stream = user_stream;
             p->last_pushed = saved_last;
             p->near_n = saved_near;
+            p->grid_dirty = saved_dirty;
             cudaEventRecord(done[i], br[i]);
             cudaStreamWaitEvent(s0, done[i], 0);
         }
@@ -1945,12 +1980,14 @@ lc_status lc_batch_graph_launch(lc_batch_graph* g, void* stream) {
         if (g->plans[i]->failed) return LC_ERR_CUDA;
         if (g->steps[i] <= g->plans[i]->last_pushed) return LC_ERR_STEP_ORDER;
     }
+    for (auto* p : g->plans) clear_grid_cells(p, (cudaStream_t)stream);
     cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
     if (e != cudaSuccess) {
         for (auto* p : g->plans) p->failed = true;
         return LC_ERR_CUDA;
     }
     for (size_t i = 0; i < g->plans.size(); ++i) {
+        g->plans[i]->grid_dirty = false;
         g->plans[i]->last_pushed = g->steps[i];
         g->plans[i]->near_n = near_entries(g->plans[i], g->n_src[i]);
     }

@@ -325,12 +325,16 @@ __global__ void __launch_bounds__(256) k_near_scatter(const long long* __restric
 }
 
 __global__ void __launch_bounds__(256) k_near_fold(const long long* __restrict__ cell, const long long* __restrict__ q,
-                                                   long long n, int N, double* __restrict__ acc, float* __restrict__ out) {
+                                                   long long n, int N, double* __restrict__ acc, float* __restrict__ out,
+                                                   long long* __restrict__ grid) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n * kNearCube) return;
     const long long s = idx / kNearCube;
     const int m = (int)(idx % kNearCube);
     if (q[s] == 0) return;
+    // the entry's own deposit cell (the cube's centre): the transforms have
+    // read it, so it is cleared for the next deposit
+    if (grid && m == kNearCube / 2) grid[cell[s]] = 0;
     int dx, dy, dz;
     const long long t = near_target(cell[s], m, N, dx, dy, dz);
     // the first thread to reach a cell takes its whole sum and clears it
@@ -473,10 +477,23 @@ void launch_near_scatter(const long long* cell, const long long* q, long long n,
 }
 
 void launch_near_fold(const long long* cell, const long long* q, long long n, int N, double* acc, float* out,
-                      cudaStream_t st) {
+                      long long* grid, cudaStream_t st) {
     const long long total = n * kNearCube;
     if (total <= 0) return;
-    launch_k(k_near_fold, (unsigned)((total + 255) / 256), 256, 0, st, cell, q, n, N, acc, out);
+    launch_k(k_near_fold, (unsigned)((total + 255) / 256), 256, 0, st, cell, q, n, N, acc, out, grid);
+}
+
+// Zero the deposit cells of a near-field list (entries with a non-zero share).
+__global__ void __launch_bounds__(256) k_cells_clear(const long long* __restrict__ cell,
+                                                     const long long* __restrict__ q, long long n,
+                                                     long long* __restrict__ grid) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && q[i] != 0) grid[cell[i]] = 0;
+}
+
+void launch_cells_clear(const long long* cell, const long long* q, long long n, long long* grid, cudaStream_t st) {
+    if (n <= 0) return;
+    launch_k(k_cells_clear, (unsigned)((n + 255) / 256), 256, 0, st, cell, q, n, grid);
 }
 
 void launch_src_prep(const double* pos, const double* lum, long long n, unsigned long long* maxbits, int* err,

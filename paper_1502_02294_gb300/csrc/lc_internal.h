@@ -116,9 +116,13 @@ void launch_gsum(long long W, int A, int gstride, const float* ghat, const doubl
 // scatter U * S * q * G(d) into the FP64 accumulator for every source and d
 void launch_near_scatter(const long long* cell, const long long* q, long long n, int N, const double* gnear,
                          const double* slot_S, int slot, double U, double* acc, cudaStream_t st);
-// fold the accumulator into out (one rounding per cell) and clear it
+// fold the accumulator into out (one rounding per cell) and clear it; with a
+// grid, also zero each entry's own deposit cell there (the sparse clear of the
+// deposit grid, once the transforms have read it)
 void launch_near_fold(const long long* cell, const long long* q, long long n, int N, double* acc, float* out,
-                      cudaStream_t st);
+                      long long* grid, cudaStream_t st);
+// zero grid[cell[i]] for the n entries of a near-field list with q[i] != 0
+void launch_cells_clear(const long long* cell, const long long* q, long long n, long long* grid, cudaStream_t st);
 
 struct RgfAccumArgs {
     int N, S, A, U;

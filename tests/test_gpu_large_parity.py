@@ -83,3 +83,36 @@ def test_field_256_fp32_history_sampled_cells():
         rel, mx, raw = errors(out[s].reshape(-1)[cells], ref)
         print(f"256^3 FP32 step {s}: rel-L2 {rel:.2e} max beyond 2 ulp / mean {mx:.2e} raw {raw:.2e}")
         assert rel <= FP32_L2 and mx <= FP32_MAX, (s, rel, mx, raw)
+
+
+def test_bf16_near_split_against_oracle_near_bright_sources():
+    # the 256^3, 128-shell BF16 path with and without the near-field split of
+    # the innermost shell, on the cells around the brightest sources (where
+    # the largest Green's-function values act) and on uniform cells
+    w = synth.config("c3")
+    P = oracle.Problem.from_workload(w)
+    s = w.steps.n_steps - 1
+    pos, lum = w.cat.active(s)
+    l = w.box / w.n
+    bright = np.argsort(lum)[-20:]
+    near = []
+    for b in bright:
+        c = np.floor(pos[b] / l + 0.5).astype(int) % w.n
+        for dx in range(-2, 3):
+            for dy in range(-2, 3):
+                for dz in range(-2, 3):
+                    near.append((((c[0] + dx) % w.n) * w.n + (c[1] + dy) % w.n) * w.n + (c[2] + dz) % w.n)
+    cells_near = np.unique(np.array(near, dtype=np.int64))
+    cells_uni = synth.sample_cells(4321, w.n, 1000)
+    ref_near = oracle.field_for(P, w.cat, s, cells=cells_near)
+    ref_uni = oracle.field_for(P, w.cat, s, cells=cells_uni)
+    res = {}
+    for mode in (lc.NEAR_NONE, lc.NEAR_NGP):
+        out, _ = _fields_at(dataclasses.replace(w, near_mode=mode), {s})
+        J = out[s].reshape(-1)
+        res[mode] = (errors(J[cells_near], ref_near), errors(J[cells_uni], ref_uni))
+        print(f"BF16 near mode {mode}: near bright sources rel-L2 {res[mode][0][0]:.3e} raw max/mean "
+              f"{res[mode][0][2]:.3e}; uniform rel-L2 {res[mode][1][0]:.3e}")
+        assert res[mode][0][0] <= BF16_L2 and res[mode][1][0] <= BF16_L2
+    # the split takes the innermost shell's near cube out of the BF16 spectra
+    assert res[lc.NEAR_NGP][0][0] <= res[lc.NEAR_NONE][0][0]
