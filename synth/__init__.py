@@ -23,6 +23,7 @@ catalogues stand in for it.  Their structure follows the workload list:
   the Lyman-Werner horizon at z_obs = 15, 160 steps, 1e5 clustered sources
   (1000 centres), history stored in BF16.
 * ``c3s`` the same 256^3 BF16 path with 32 shells and 40 steps (a profiling size).
+* ``c5s`` the 512^3 BF16 path of the serving set with 16 shells and 24 steps (a profiling size).
 * ``c4``  16 uneven instances (grids 64..256, 32..128 shells, 1e3..1e5
   sources, 0.78 Mpc cells).
 * ``c5``  8 served simulations at 128^3..512^3.
@@ -174,6 +175,13 @@ def config(name: str) -> Workload:
         cat = make_catalogue(SEED_BASE + 77, 100_000, 200.0, 40, clustered=True,
                              n_centres=1000, sigma=2.0)
         return Workload("c3s", 256, 200.0, 0.31, 0.68, st, 4, HISTORY_BF16, cat)
+    if name == "c5s":
+        # the 512^3 BF16 path of the serving set at a profiling size: 16
+        # equal-conformal-time shells (ring ~4.3 GB), 24 steps, 4e4 clustered sources
+        st = StepSpec(STEPS_EQUAL_TAU, 24, z_end=15.0, n_shell=16)
+        cat = make_catalogue(SEED_BASE + 78, 40_000, 400.0, 24, clustered=True,
+                             n_centres=400, sigma=2.0)
+        return Workload("c5s", 512, 400.0, 0.31, 0.68, st, 4, HISTORY_BF16, cat)
     raise KeyError(name)
 
 
