@@ -265,7 +265,7 @@ def fft_choices():
     """The FFT pass form in use per grid size (autotuned): {N: name}."""
     import paper_1502_02294_gb300 as lc
 
-    names = {lc.FFT_STAGES: "stages", lc.FFT_LANES: "lanes"}
+    names = {lc.FFT_STAGES: "stages", lc.FFT_LANES: "lanes", lc.FFT_LANES3: "lanes3"}
     return {n: names.get(lc.fft_variant(n), "-") for n in lc.SUPPORTED_N if n >= 256}
 
 

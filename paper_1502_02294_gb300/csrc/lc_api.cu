@@ -590,7 +590,7 @@ int choose_mac_variant(lc_plan* p, const lc_plan::Table& T, int s) {
     return best;
 }
 
-const char* const kFftNames[FFT_NVAR] = {"stages", "lanes"};
+const char* const kFftNames[FFT_NVAR] = {"stages", "lanes", "lanes3"};
 
 // One step's FFT passes on the plan's own buffers (forward from the int64
 // grid into ring slot 0, inverse from the work spectrum into the grid's
@@ -695,6 +695,7 @@ void choose_fft_variant(lc_plan* p) {
     cudaEvent_t ev[kReps + 1] = {};
     bool ok = true;
     for (int r = 0; ok && r <= kReps; ++r) ok = cudaEventCreate(&ev[r]) == cudaSuccess;
+    static_assert(FFT_NVAR <= MAC_NVAR, "the cache line format holds MAC_NVAR times");
     double ms[MAC_NVAR] = {-1.0, -1.0, -1.0, -1.0};
     int best = ops->cols_variant();
     for (int v = 0; ok && v < FFT_NVAR; ++v) {

@@ -580,12 +580,17 @@ __device__ __forceinline__ void fft_cols_lanes(float2* __restrict__ buf, const f
 // The pipelined persistent column pass with fft_cols_lanes: as k_cols_pl
 // (tiles copied by 16-byte asynchronous copies into S shared-memory stages,
 // S - 1 in flight), with 256 threads and the outputs written straight from
-// registers (two or four whole row segments per warp store).
+// registers (two or four whole row segments per warp store).  Two tile
+// schedules: S = 4 stages, one CTA per SM (133 KB), or S = 3 stages, two CTAs
+// per SM (100 KB each), so one CTA's transforms overlap the other's waits.
 __host__ __device__ constexpr int cols_lanes_threads() { return 256; }
-template <int N, int DIR, int OUT>
+template <int N, int S> __host__ __device__ constexpr size_t cols_lanes_smem_bytes() {
+    return sizeof(float2) * ((size_t)N + (size_t)S * N * cw_of(N));
+}
+template <int N, int DIR, int OUT, int S>
 __global__ void __launch_bounds__(cols_lanes_threads()) k_cols_lanes(ColArgs a, int ntiles) {
     constexpr int NT = cols_lanes_threads();
-    constexpr int CW = cw_of(N), M = N / 2, S = cols_pl_stages(N);
+    constexpr int CW = cw_of(N), M = N / 2;
     constexpr int TILE = N * CW;
     static_assert(cols_lanes_ok<N>(), "N = 256 or 512");
     extern __shared__ float4 smem_raw[];
@@ -1199,13 +1204,14 @@ struct FftOps {
     void (*mac_ws2_bf16)(const MacArgs&, cudaStream_t);
     int full_tiles; // tiles of the full 16-column chunks (the Nyquist tiles follow)
     // the y / x pass kernel of grids with more than one: FFT_COLS_STAGES
-    // (block-wide Stockham stages) or FFT_COLS_LANES (one lane per column);
-    // chosen by the autotuner or LC_FFT_VARIANT, shared by the process
+    // (block-wide Stockham stages), FFT_COLS_LANES (one lane per column, four
+    // tile stages, one CTA per SM) or FFT_COLS_LANES3 (three stages, two CTAs
+    // per SM); chosen by the autotuner or LC_FFT_VARIANT, shared by the process
     int (*cols_variants)();          // bit mask of the variants built for this N
     void (*set_cols_variant)(int);
     int (*cols_variant)();
 };
-enum { FFT_COLS_STAGES = 0, FFT_COLS_LANES = 1, FFT_NVAR = 2 };
+enum { FFT_COLS_STAGES = 0, FFT_COLS_LANES = 1, FFT_COLS_LANES3 = 2, FFT_NVAR = 3 };
 
 template <int N> struct Launch {
     static constexpr int CW = cw_of(N), NCH = (N / 2) / CW;
@@ -1247,18 +1253,22 @@ template <int N> struct Launch {
         static int v = cols_lanes_ok<N>() ? FFT_COLS_LANES : FFT_COLS_STAGES;
         return v;
     }
-    static int variants_built() { return (1 << FFT_COLS_STAGES) | (cols_lanes_ok<N>() ? 1 << FFT_COLS_LANES : 0); }
+    static int variants_built() {
+        return (1 << FFT_COLS_STAGES) | (cols_lanes_ok<N>() ? (1 << FFT_COLS_LANES) | (1 << FFT_COLS_LANES3) : 0);
+    }
     static void set_variant(int v) {
         if (v >= 0 && v < FFT_NVAR && (variants_built() >> v & 1)) variant() = v;
     }
     static int get_variant() { return variant(); }
-    template <int DIR, int OUT> static int cols_lanes_ctas() {
+    template <int DIR, int OUT, int S> static int cols_lanes_ctas() {
         static int ctas = 0;
         if (!ctas) {
             int occ = 0;
             if constexpr (cols_lanes_ok<N>()) {
-                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cols_lanes<N, DIR, OUT>, cols_lanes_threads(),
-                                                                  cols_pl_smem_bytes<N>()) != cudaSuccess || occ <= 0) {
+                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cols_lanes<N, DIR, OUT, S>,
+                                                                  cols_lanes_threads(),
+                                                                  cols_lanes_smem_bytes<N, S>()) != cudaSuccess ||
+                    occ <= 0) {
                     cudaGetLastError();
                     occ = 1;
                 }
@@ -1267,12 +1277,19 @@ template <int N> struct Launch {
         }
         return ctas;
     }
+    template <int DIR, int OUT, int S> static void cols_lanes_launch(const ColArgs& a, int ntiles, cudaStream_t st) {
+        if constexpr (cols_lanes_ok<N>()) {
+            const int c = cols_lanes_ctas<DIR, OUT, S>();
+            launch_k(k_cols_lanes<N, DIR, OUT, S>, dim3((unsigned)(ntiles < c ? ntiles : c)), cols_lanes_threads(),
+                     cols_lanes_smem_bytes<N, S>(), st, a, ntiles);
+        }
+    }
+    static bool lanes_form() { return variant() == FFT_COLS_LANES || variant() == FFT_COLS_LANES3; }
     template <int DIR, int OUT> static void cols_plain(const ColArgs& a, int ntiles, cudaStream_t st) {
         if constexpr (cols_lanes_ok<N>()) {
-            if (variant() == FFT_COLS_LANES && aligned16(a.src)) {
-                const int c = cols_lanes_ctas<DIR, OUT>();
-                launch_k(k_cols_lanes<N, DIR, OUT>, dim3((unsigned)(ntiles < c ? ntiles : c)), cols_lanes_threads(),
-                         cols_pl_smem_bytes<N>(), st, a, ntiles);
+            if (lanes_form() && aligned16(a.src)) {
+                if (variant() == FFT_COLS_LANES3) cols_lanes_launch<DIR, OUT, 3>(a, ntiles, st);
+                else cols_lanes_launch<DIR, OUT, 4>(a, ntiles, st);
                 return;
             }
         }
@@ -1319,11 +1336,17 @@ template <int N> struct Launch {
                 LC_ATTR((k_rows_c2r_lanes<N>), rl);
             }
             if constexpr (cols_lanes_ok<N>()) {
-                LC_ATTR((k_cols_lanes<N, -1, COL_OUT_PLAIN>), ps2);
-                LC_ATTR((k_cols_lanes<N, -1, COL_OUT_BF16>), ps2);
-                LC_ATTR((k_cols_lanes<N, -1, COL_OUT_WEDGE>), ps2);
-                LC_ATTR((k_cols_lanes<N, -1, COL_OUT_RING_F32>), ps2);
-                LC_ATTR((k_cols_lanes<N, 1, COL_OUT_PLAIN>), ps2);
+                const int l4 = (int)cols_lanes_smem_bytes<N, 4>(), l3 = (int)cols_lanes_smem_bytes<N, 3>();
+                LC_ATTR((k_cols_lanes<N, -1, COL_OUT_PLAIN, 4>), l4);
+                LC_ATTR((k_cols_lanes<N, -1, COL_OUT_BF16, 4>), l4);
+                LC_ATTR((k_cols_lanes<N, -1, COL_OUT_WEDGE, 4>), l4);
+                LC_ATTR((k_cols_lanes<N, -1, COL_OUT_RING_F32, 4>), l4);
+                LC_ATTR((k_cols_lanes<N, 1, COL_OUT_PLAIN, 4>), l4);
+                LC_ATTR((k_cols_lanes<N, -1, COL_OUT_PLAIN, 3>), l3);
+                LC_ATTR((k_cols_lanes<N, -1, COL_OUT_BF16, 3>), l3);
+                LC_ATTR((k_cols_lanes<N, -1, COL_OUT_WEDGE, 3>), l3);
+                LC_ATTR((k_cols_lanes<N, -1, COL_OUT_RING_F32, 3>), l3);
+                LC_ATTR((k_cols_lanes<N, 1, COL_OUT_PLAIN, 3>), l3);
             }
         } else {
             LC_ATTR((k_cols_pp<N, -1, COL_OUT_PLAIN>), cs);
@@ -1376,7 +1399,7 @@ template <int N> struct Launch {
     static void rows_r2c(const RowR2CArgs& a, cudaStream_t st) {
         const int nb = (int)row_blocks();
         if constexpr (rows_lanes_ok<N>()) {
-            if (variant() == FFT_COLS_LANES && (a.in_mode == ROW_IN_I64 || a.in_mode == ROW_IN_F32)) {
+            if (lanes_form() && (a.in_mode == ROW_IN_I64 || a.in_mode == ROW_IN_F32)) {
                 const long long npairs = a.nrows / 2;
                 const size_t sm = rows_lanes_smem_bytes<N>();
                 if (a.in_mode == ROW_IN_I64) {
@@ -1419,7 +1442,7 @@ template <int N> struct Launch {
     static void rows_c2r(const RowC2RArgs& a, cudaStream_t st) {
         const int nb = (int)row_blocks();
         if constexpr (rows_lanes_ok<N>()) {
-            if (variant() == FFT_COLS_LANES) {
+            if (lanes_form()) {
                 const size_t sm = rows_lanes_smem_bytes<N>();
                 static const int c = occ_ctas_t(k_rows_c2r_lanes<N>, kRowsLanesThreads, sm);
                 launch_k(k_rows_c2r_lanes<N>, dim3((unsigned)c), kRowsLanesThreads, sm, st, a, a.nrows / 2);
