@@ -644,8 +644,12 @@ def run_serving(args):
         "roofline": {"bound": "hbm", "kernel": "shell-MAC phase of every served step (each simulation alone): "
                      "k_mac_ws paired (ws2) or the autotuned variant, fused with the inverse x pass",
                      "achieved": mac_gbs, "peak": peak, "unit": "GB/s",
-                     "frac": (mac_gbs / peak) if mac_gbs else None, "traffic": None,
-                     "traffic_note": "null: no ncu capture of this window's MAC launches yet",
+                     "frac": (mac_gbs / peak) if mac_gbs else None,
+                     "traffic": MAC512_TRAFFIC["bytes"] if MAC512_TRAFFIC["sources"] == mac_sources_hash() else None,
+                     "traffic_algorithmic": MAC512_TRAFFIC["algorithmic"],
+                     "traffic_note": "per launch of the dominant kernel, k_mac_ws<512, bf16, pair> at 96 slices: "
+                                     "DRAM bytes scaled from a 16-slice capture (" + MAC512_TRAFFIC["from"] + "), "
+                                     "reads x 96/16, writes as captured",
                      "peak_source": peak_src, "bytes": mac_bytes, "ms": mac_ms, "launches": mac_launches,
                      "bytes_per_unit": "N_k (4 A + 8) + 4 W A per field (N_k = N^2 (N/2+1) modes, A active "
                                        "slices with sources, W wedge rows)"},
@@ -682,6 +686,14 @@ MAC_TRAFFIC = {
     "c3": {"sources": "575a4b4d64a0d777", "bytes": 4 * 1.192879e9 + 73.619e6,
            "from": "profiles/k_mac_ws_256_bf16_pair.md (c3s, reads x 128/32)"},
 }
+
+
+# the served 512^3 MAC launch (96 slices, BF16, paired kernel): DRAM traffic
+# scaled from the c5s capture (16 slices: reads x 96/16, writes as captured)
+# and the launch's algorithmic bytes N_k (4 A + 8) + 4 W A
+MAC512_TRAFFIC = {"sources": "575a4b4d64a0d777", "bytes": 4.877360555e9 * 96 / 16 + 0.598957994e9,
+                  "algorithmic": 67371008 * (4 * 96 + 8) + 4 * 2862209 * 96,
+                  "from": "profiles/k_mac_ws_512_bf16_pair.md"}
 
 
 def _function_text(src, head):

@@ -43,3 +43,5 @@ def test_mac_source_hash_finds_the_kernel_texts():
     for name, t in bench.MAC_TRAFFIC.items():
         assert t["bytes"] > 0 and t["from"].startswith("profiles/")
         assert os.path.exists(os.path.join(ROOT, t["from"].split(" ")[0]))
+    t = bench.MAC512_TRAFFIC
+    assert t["bytes"] > t["algorithmic"] > 0 and os.path.exists(os.path.join(ROOT, t["from"]))
