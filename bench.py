@@ -265,7 +265,7 @@ def fft_choices():
     """The FFT pass form in use per grid size (autotuned): {N: name}."""
     import paper_1502_02294_gb300 as lc
 
-    names = {lc.FFT_STAGES: "stages", lc.FFT_LANES: "lanes", lc.FFT_LANES3: "lanes3"}
+    names = {lc.FFT_STAGES: "stages", lc.FFT_LANES: "lanes", lc.FFT_LANES3: "lanes3", lc.FFT_TMA: "tma"}
     return {n: names.get(lc.fft_variant(n), "-") for n in lc.SUPPORTED_N if n >= 256}
 
 
@@ -681,9 +681,9 @@ def run_serving(args):
 # warp-specialised and bulk kernels, the gather pass and its slot list); c3 is
 # the c3s capture (32 slices) with its reads scaled to 128 slices.
 MAC_TRAFFIC = {
-    "c2": {"sources": "575a4b4d64a0d777", "bytes": 38.472e6,
+    "c2": {"sources": "731331f0d508e08e", "bytes": 38.472e6,
            "from": "profiles/c2_dram_traffic.md (64-step window, all MAC-phase launches)"},
-    "c3": {"sources": "575a4b4d64a0d777", "bytes": 4 * 1.192879e9 + 73.619e6,
+    "c3": {"sources": "731331f0d508e08e", "bytes": 4 * 1.192879e9 + 73.619e6,
            "from": "profiles/k_mac_ws_256_bf16_pair.md (c3s, reads x 128/32)"},
 }
 
@@ -691,7 +691,7 @@ MAC_TRAFFIC = {
 # the served 512^3 MAC launch (96 slices, BF16, paired kernel): DRAM traffic
 # scaled from the c5s capture (16 slices: reads x 96/16, writes as captured)
 # and the launch's algorithmic bytes N_k (4 A + 8) + 4 W A
-MAC512_TRAFFIC = {"sources": "575a4b4d64a0d777", "bytes": 4.877360555e9 * 96 / 16 + 0.598957994e9,
+MAC512_TRAFFIC = {"sources": "731331f0d508e08e", "bytes": 4.877360555e9 * 96 / 16 + 0.598957994e9,
                   "algorithmic": 67371008 * (4 * 96 + 8) + 4 * 2862209 * 96,
                   "from": "profiles/k_mac_ws_512_bf16_pair.md"}
 

@@ -7,6 +7,7 @@
 //           -> y-pass -> x-pass with ring-slot epilogue         (step 4, Sec. 2.2)
 //   field : x-pass with shell-MAC prologue (+ FP64 k = 0) -> y-pass
 //           -> rows c2r with U / N^3 epilogue                   (steps 5-6)
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdlib.h>
@@ -93,6 +94,62 @@ static int sm_count() {
     }
     return n;
 }
+
+// ---- tensor maps of the TMA column passes ----
+// cuTensorMapEncodeTiled through the driver entry point the runtime hands out
+// (no link against the driver library)
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static bool looked_up = false;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> g(mu);
+    if (!looked_up) {
+        looked_up = true;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void**)&fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess || q != cudaDriverEntryPointSuccess)
+            fn = nullptr;
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+// The half spectrum at `work` ([p][q][NRP complex], C order) as a rank-3
+// tensor of floats (2 NRP, N, N), with the box of one column-pass tile: CW
+// columns by min(N, 256) lines q of one plane p (y pass, axis 0), or CW
+// columns by min(N, 256) planes p of one line q (x pass, axis 1).
+bool make_cols_map(CUtensorMap* m, const float2* work, int n, int axis) {
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn || (reinterpret_cast<uintptr_t>(work) & 15)) return false;
+    const cuuint64_t nrp = (cuuint64_t)nrp_of(n), N = (cuuint64_t)n;
+    const cuuint32_t cw = (cuuint32_t)cw_of(n), box_t = n > 256 ? 256u : (cuuint32_t)n;
+    const cuuint64_t dims[3] = {2 * nrp, N, N};
+    const cuuint64_t strides[2] = {nrp * sizeof(float2), N * nrp * sizeof(float2)};
+    const cuuint32_t box[3] = {2 * cw, axis == 0 ? box_t : 1u, axis == 0 ? 1u : box_t};
+    const cuuint32_t es[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float2*>(work), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The two maps of a work spectrum (y and x pass), made where a TMA form exists for n.
+struct ColsMaps {
+    CUtensorMap y, x;
+    bool ok = false;
+    void make(const float2* work, int n) {
+        const FftOps* ops = fft_ops_for(n);
+        ok = ops && (ops->cols_variants() >> FFT_COLS_TMA & 1) && make_cols_map(&y, work, n, 0) &&
+             make_cols_map(&x, work, n, 1);
+    }
+    // a plain column pass over the spectrum these maps describe: its map by axis
+    void set(ColArgs& c, int* err) const {
+        c.tmap = ok ? (c.axis == 0 ? &y : &x) : nullptr;
+        c.err = err;
+    }
+};
 
 static std::vector<float2> twiddles(int n) {
     std::vector<float2> t(n);
@@ -181,6 +238,7 @@ struct lc_plan {
     double* d_slot_S = nullptr;
     long long* d_slot_total = nullptr;
     float2* d_tw = nullptr;
+    ColsMaps maps; // tensor maps of d_work for the TMA column passes
     int* d_err = nullptr;
     unsigned long long* d_maxbits = nullptr;
     double* d_pos = nullptr;
@@ -590,7 +648,7 @@ int choose_mac_variant(lc_plan* p, const lc_plan::Table& T, int s) {
     return best;
 }
 
-const char* const kFftNames[FFT_NVAR] = {"stages", "lanes", "lanes3"};
+const char* const kFftNames[FFT_NVAR] = {"stages", "lanes", "lanes3", "tma"};
 
 // One step's FFT passes on the plan's own buffers (forward from the int64
 // grid into ring slot 0, inverse from the work spectrum into the grid's
@@ -618,6 +676,7 @@ void fft_step_passes(lc_plan* p, cudaStream_t st) {
     c.src = p->d_work;
     c.dst = p->d_work;
     c.tw = p->d_tw;
+    p->maps.set(c, p->d_err);
     p->ops->cols(c, st);
     c.axis = 1;
     if (p->history == LC_HISTORY_BF16) {
@@ -629,6 +688,7 @@ void fft_step_passes(lc_plan* p, cudaStream_t st) {
     }
     c.n_ring = p->n_ring;
     c.wslot = 0;
+    p->maps.set(c, p->d_err);
     p->ops->cols(c, st);
     ColArgs ci{};
     ci.axis = 0;
@@ -638,6 +698,7 @@ void fft_step_passes(lc_plan* p, cudaStream_t st) {
     ci.src = p->d_work;
     ci.dst = p->d_work;
     ci.tw = p->d_tw;
+    p->maps.set(ci, p->d_err);
     p->ops->cols(ci, st);
     RowC2RArgs rc{};
     rc.nrows = N * N;
@@ -917,6 +978,7 @@ lc_status build_table(lc_plan* p, int s) {
             p->ops->plane_r2c(r, st);
         } else {
             p->ops->rows_r2c(r, st);
+            p->maps.set(c, p->d_err);
             p->ops->cols(c, st);
         }
         c.axis = 1;
@@ -924,6 +986,7 @@ lc_status build_table(lc_plan* p, int s) {
         c.wedge_out = T.ghat;
         c.wedge_A = T.gstride;
         c.wedge_j = j;
+        p->maps.set(c, p->d_err);
         p->ops->cols(c, st);
     }
     e = cudaGetLastError();
@@ -1093,6 +1156,7 @@ lc_status lc_plan_create(int n, double box_mpc, const lc_cosmology* cosmo, const
         return LC_ERR_OOM;
     }
     std::vector<float2> tw = twiddles(n);
+    p->maps.make(p->d_work, n);
     e = cudaMemsetAsync(p->d_grid, 0, sizeof(long long) * N3, p->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_tw, tw.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, p->stream);
     if (e == cudaSuccess && p->near_on) e = cudaMemsetAsync(p->d_near, 0, sizeof(double) * N3, p->stream);
@@ -1214,6 +1278,7 @@ lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos
             p->ops->rows_r2c(r, st);
         }
         Phase ph(p, LC_PHASE_FWD_Y, 1);
+        p->maps.set(c, p->d_err);
         p->ops->cols(c, st);
     }
     c.axis = 1;
@@ -1228,6 +1293,7 @@ lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos
     c.wslot = slot;
     {
         Phase ph(p, LC_PHASE_FWD_X_RING, 1);
+        p->maps.set(c, p->d_err);
         p->ops->cols(c, st);
     }
     e = cudaGetLastError();
@@ -1381,6 +1447,7 @@ static lc_status field_impl(lc_plan* p, int step, float* out, int instant, uint6
         } else {
             {
                 Phase ph(p, LC_PHASE_INV_Y, 1);
+                p->maps.set(c, p->d_err);
                 p->ops->cols(c, st);
             }
             Phase ph(p, LC_PHASE_C2R_Z, 1);
@@ -2124,13 +2191,17 @@ lc_status lc_fft_r2c(int n, const float* in, float* out_complex, void* stream) {
     c.src = work;
     c.dst = work;
     c.tw = tw;
+    ColsMaps maps;
+    maps.make(work, n);
     if (ops->plane_r2c) {
         ops->plane_r2c(ra, st);
     } else {
         ops->rows_r2c(ra, st);
+        maps.set(c, nullptr);
         ops->cols(c, st);
     }
     c.axis = 1;
+    maps.set(c, nullptr);
     ops->cols(c, st);
     count_launch(ops->plane_r2c ? 2 : 3);
     const int h = n / 2 + 1;
@@ -2163,8 +2234,12 @@ lc_status lc_fft_c2r(int n, const float* in_complex, float* out, float scale, vo
         c.src = work;
         c.dst = work;
         c.tw = tw;
+        ColsMaps maps;
+        maps.make(work, n);
+        maps.set(c, nullptr);
         ops->cols(c, st);
         c.axis = 0;
+        maps.set(c, nullptr);
         RowC2RArgs ra{};
         ra.nrows = (long long)n * n;
         ra.src = work;

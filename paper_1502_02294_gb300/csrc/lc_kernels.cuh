@@ -66,6 +66,11 @@ struct ColArgs {
     float* wedge_out;
     int wedge_A, wedge_j;     // wedge_A: row stride of the table written
     const float2* tw;
+    // tensor map of `src` seen as [p][q][2 NRP floats] with the box of this
+    // pass's axis (TMA column passes; null: none made for this buffer), and
+    // the error word a timed-out copy wait reports to (may be null)
+    const CUtensorMap* tmap;
+    int* err;
 };
 
 struct RowC2RArgs {
@@ -647,6 +652,124 @@ __global__ void __launch_bounds__(cols_lanes_threads()) k_cols_lanes(ColArgs a, 
 }
 
 // ------------------------------------------------------------------------
+// Column passes with the tiles moved by tensor-map TMA (N = 256 and 512):
+// the transform is fft_cols_lanes; a full tile is one box (two at N = 512:
+// the box holds at most 256 rows) of the half spectrum seen as a 3D tensor
+// [p][q][2 NRP floats], copied by cp.async.bulk.tensor into one of S
+// shared-memory stages, completion counted on the stage's mbarrier, issued
+// by one thread S - 1 tiles ahead.  Nyquist tiles (CW single columns of CW
+// lines, not a box of contiguous columns) are loaded by the threads
+// themselves when their turn comes.  Every wait is bounded: a wait that
+// gives up sets bit 8 of the error word; the CTA then waits once more (also
+// bounded) for each copy it has in flight and returns.
+template <int N, int S> __host__ __device__ constexpr size_t cols_tma_smem_bytes() {
+    return (size_t)S * N * cw_of(N) * sizeof(float2) + (size_t)N * sizeof(float2) + (size_t)S * 8 + 128;
+}
+constexpr int kColsTmaStages = 3;
+
+template <int N, int DIR, int OUT, int S>
+__global__ void __launch_bounds__(cols_lanes_threads()) k_cols_tma(ColArgs a, int ntiles,
+                                                                    const __grid_constant__ CUtensorMap tmap) {
+    constexpr int NT = cols_lanes_threads();
+    constexpr int CW = cw_of(N), M = N / 2, TILE = N * CW, NCH = M / CW;
+    constexpr int BOX = N > 256 ? 256 : N, NBOX = N / BOX;
+    constexpr unsigned TILE_BYTES = TILE * sizeof(float2);
+    static_assert(cols_lanes_ok<N>(), "N = 256 or 512");
+    extern __shared__ unsigned char smem_tma[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_tma) + 127) & ~uintptr_t(127));
+    float2* stages = reinterpret_cast<float2*>(sm); // S tiles, each 128-byte aligned
+    float2* tw = stages + S * TILE;
+    unsigned long long* full = reinterpret_cast<unsigned long long*>(tw + N);
+    __shared__ int s_fail;
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        for (int k = 0; k < S; ++k) mbar_init(smem_u32(&full[k]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int i = threadIdx.x; i < N; i += NT) tw[i] = a.tw[i];
+    __syncthreads();
+    auto is_nyq = [&](int tile) { return tile + a.tile0 >= N * NCH; };
+    auto issue = [&](int tile, int st) { // thread 0; full tiles only
+        const int t = tile + a.tile0, line = t / NCH, chunk = t % NCH;
+        const unsigned bar = smem_u32(&full[st]);
+        mbar_expect_tx(bar, TILE_BYTES);
+#pragma unroll
+        for (int b = 0; b < NBOX; ++b) {
+            const unsigned dst = smem_u32(stages + st * TILE + b * BOX * CW);
+            // coordinates (float along r, q, p): y pass (axis 0) p = line, x pass q = line
+            if (a.axis == 0) tma_load_3d(dst, &tmap, 2 * chunk * CW, b * BOX, line, bar);
+            else tma_load_3d(dst, &tmap, 2 * chunk * CW, line, b * BOX, bar);
+        }
+    };
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < S - 1; ++k) {
+            const int t = blockIdx.x + k * gridDim.x;
+            if (t < ntiles && !is_nyq(t)) issue(t, k);
+        }
+    }
+    unsigned phase = 0; // bit st: parity of the next completion of stage st
+    for (int k = 0;; ++k) {
+        const int tile = blockIdx.x + k * gridDim.x;
+        if (tile >= ntiles) break;
+        const int st = k % S;
+        // refill the stage of tile k - 1 (every thread is done with it: the
+        // barrier that ended tile k - 1)
+        if (threadIdx.x == 0) {
+            const int nt = blockIdx.x + (k + S - 1) * gridDim.x;
+            if (nt < ntiles && !is_nyq(nt)) {
+                fence_proxy_async();
+                issue(nt, (k + S - 1) % S);
+            }
+        }
+        float2* buf = stages + st * TILE;
+        const ColGeom<N> g(tile + a.tile0, a.axis);
+        bool ok = true;
+        if (g.nyq) {
+            for (int i = threadIdx.x; i < TILE; i += NT) buf[i] = a.src[g.at(i)];
+            __syncthreads();
+        } else {
+            ok = mbar_wait_bounded(smem_u32(&full[st]), (phase >> st) & 1u);
+            phase ^= 1u << st;
+        }
+        if (__syncthreads_or(!ok)) {
+            // give every copy still in flight (this tile's, and those issued
+            // ahead) a second bounded wait before the shared memory goes away
+            if (threadIdx.x == 0) {
+                if (!g.nyq) mbar_wait_bounded(smem_u32(&full[st]), ((phase >> st) & 1u) ^ 1u);
+                for (int d = 1; d < S; ++d) {
+                    const int t2 = blockIdx.x + (k + d) * gridDim.x;
+                    const int s2 = (k + d) % S;
+                    if (t2 < ntiles && !is_nyq(t2)) mbar_wait_bounded(smem_u32(&full[s2]), (phase >> s2) & 1u);
+                }
+                if (a.err) atomicOr(a.err, 8);
+            }
+            return;
+        }
+        float2 v[16];
+        int col, tb;
+        fft_cols_lanes<N, DIR>(buf, tw, v, col, tb);
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            const int t = tb + 16 * kk;
+            const int idx = t * CW + col;
+            if constexpr (OUT == COL_OUT_PLAIN) {
+                a.dst[g.at(idx)] = v[kk];
+            } else if constexpr (OUT == COL_OUT_BF16) {
+                a.dst_bf16[((long long)(tile + a.tile0) * a.n_ring + a.wslot) * TILE + idx] =
+                    __floats2bfloat162_rn(v[kk].x, v[kk].y);
+            } else if constexpr (OUT == COL_OUT_RING_F32) {
+                a.dst[((long long)(tile + a.tile0) * a.n_ring + a.wslot) * TILE + idx] = v[kk];
+            } else {
+                const int q = g.nyq ? g.line + col : g.line;
+                const int r = g.nyq ? M : g.chunk * CW + col;
+                if (t <= q && q <= r) a.wedge_out[wedge_index(t, q, r) * a.wedge_A + a.wedge_j] = v[kk].x;
+            }
+        }
+        __syncthreads(); // the stage is read out before it is refilled
+    }
+}
+
+// ------------------------------------------------------------------------
 // z passes with one row pair per group of G = N / 16 lanes (N = 256: a half
 // warp, N = 512: a warp).  The two real rows a, b of a pair are transformed
 // as one complex row z = a + i b (Eq. 12 along z), N = 16 G:
@@ -1205,13 +1328,15 @@ struct FftOps {
     int full_tiles; // tiles of the full 16-column chunks (the Nyquist tiles follow)
     // the y / x pass kernel of grids with more than one: FFT_COLS_STAGES
     // (block-wide Stockham stages), FFT_COLS_LANES (one lane per column, four
-    // tile stages, one CTA per SM) or FFT_COLS_LANES3 (three stages, two CTAs
-    // per SM); chosen by the autotuner or LC_FFT_VARIANT, shared by the process
+    // tile stages, one CTA per SM), FFT_COLS_LANES3 (three stages, two CTAs
+    // per SM) or FFT_COLS_TMA (the tiles moved by tensor-map TMA, three stages,
+    // two CTAs per SM); chosen by the autotuner or LC_FFT_VARIANT, shared by
+    // the process
     int (*cols_variants)();          // bit mask of the variants built for this N
     void (*set_cols_variant)(int);
     int (*cols_variant)();
 };
-enum { FFT_COLS_STAGES = 0, FFT_COLS_LANES = 1, FFT_COLS_LANES3 = 2, FFT_NVAR = 3 };
+enum { FFT_COLS_STAGES = 0, FFT_COLS_LANES = 1, FFT_COLS_LANES3 = 2, FFT_COLS_TMA = 3, FFT_NVAR = 4 };
 
 template <int N> struct Launch {
     static constexpr int CW = cw_of(N), NCH = (N / 2) / CW;
@@ -1254,7 +1379,8 @@ template <int N> struct Launch {
         return v;
     }
     static int variants_built() {
-        return (1 << FFT_COLS_STAGES) | (cols_lanes_ok<N>() ? (1 << FFT_COLS_LANES) | (1 << FFT_COLS_LANES3) : 0);
+        return (1 << FFT_COLS_STAGES) |
+               (cols_lanes_ok<N>() ? (1 << FFT_COLS_LANES) | (1 << FFT_COLS_LANES3) | (1 << FFT_COLS_TMA) : 0);
     }
     static void set_variant(int v) {
         if (v >= 0 && v < FFT_NVAR && (variants_built() >> v & 1)) variant() = v;
@@ -1284,9 +1410,33 @@ template <int N> struct Launch {
                      cols_lanes_smem_bytes<N, S>(), st, a, ntiles);
         }
     }
-    static bool lanes_form() { return variant() == FFT_COLS_LANES || variant() == FFT_COLS_LANES3; }
+    static bool lanes_form() {
+        return variant() == FFT_COLS_LANES || variant() == FFT_COLS_LANES3 || variant() == FFT_COLS_TMA;
+    }
+    template <int DIR, int OUT> static void cols_tma_launch(const ColArgs& a, int ntiles, cudaStream_t st) {
+        if constexpr (cols_lanes_ok<N>()) {
+            constexpr int S = kColsTmaStages;
+            static int ctas = 0;
+            if (!ctas) {
+                int occ = 0;
+                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cols_tma<N, DIR, OUT, S>, cols_lanes_threads(),
+                                                                  cols_tma_smem_bytes<N, S>()) != cudaSuccess ||
+                    occ <= 0) {
+                    cudaGetLastError();
+                    occ = 1;
+                }
+                ctas = occ * sms();
+            }
+            launch_k(k_cols_tma<N, DIR, OUT, S>, dim3((unsigned)(ntiles < ctas ? ntiles : ctas)), cols_lanes_threads(),
+                     cols_tma_smem_bytes<N, S>(), st, a, ntiles, *a.tmap);
+        }
+    }
     template <int DIR, int OUT> static void cols_plain(const ColArgs& a, int ntiles, cudaStream_t st) {
         if constexpr (cols_lanes_ok<N>()) {
+            if (variant() == FFT_COLS_TMA && a.tmap) {
+                cols_tma_launch<DIR, OUT>(a, ntiles, st);
+                return;
+            }
             if (lanes_form() && aligned16(a.src)) {
                 if (variant() == FFT_COLS_LANES3) cols_lanes_launch<DIR, OUT, 3>(a, ntiles, st);
                 else cols_lanes_launch<DIR, OUT, 4>(a, ntiles, st);
@@ -1347,6 +1497,12 @@ template <int N> struct Launch {
                 LC_ATTR((k_cols_lanes<N, -1, COL_OUT_WEDGE, 3>), l3);
                 LC_ATTR((k_cols_lanes<N, -1, COL_OUT_RING_F32, 3>), l3);
                 LC_ATTR((k_cols_lanes<N, 1, COL_OUT_PLAIN, 3>), l3);
+                const int tm = (int)cols_tma_smem_bytes<N, kColsTmaStages>();
+                LC_ATTR((k_cols_tma<N, -1, COL_OUT_PLAIN, kColsTmaStages>), tm);
+                LC_ATTR((k_cols_tma<N, -1, COL_OUT_BF16, kColsTmaStages>), tm);
+                LC_ATTR((k_cols_tma<N, -1, COL_OUT_WEDGE, kColsTmaStages>), tm);
+                LC_ATTR((k_cols_tma<N, -1, COL_OUT_RING_F32, kColsTmaStages>), tm);
+                LC_ATTR((k_cols_tma<N, 1, COL_OUT_PLAIN, kColsTmaStages>), tm);
             }
         } else {
             LC_ATTR((k_cols_pp<N, -1, COL_OUT_PLAIN>), cs);
