@@ -88,6 +88,8 @@ def parse(argv=None):
     ap.add_argument("--fdiff", action="store_true",
                     help="each step also builds the instantaneous field (Eq. 18) and the f_diff map")
     ap.add_argument("--no-c3", action="store_true", help="c5: skip the 256^3 single-instance extra key")
+    ap.add_argument("--priorities", action="store_true",
+                    help="c5: run small grids' streams at higher CUDA stream priority")
     return ap.parse_args(argv)
 
 
@@ -265,7 +267,7 @@ def fft_choices():
     """The FFT pass form in use per grid size (autotuned): {N: name}."""
     import paper_1502_02294_gb300 as lc
 
-    names = {lc.FFT_STAGES: "stages", lc.FFT_LANES: "lanes", lc.FFT_LANES3: "lanes3", lc.FFT_TMA: "tma"}
+    names = {lc.FFT_STAGES: "stages", lc.FFT_LANES: "lanes", lc.FFT_LANES3: "lanes3", lc.FFT_TMA: "tma", lc.FFT_TMA4: "tma4"}
     return {n: names.get(lc.fft_variant(n), "-") for n in lc.SUPPORTED_N if n >= 256}
 
 
@@ -482,7 +484,7 @@ def run_serving(args):
         return arr
 
     budget = int(0.6 * torch.cuda.get_device_properties(dev).total_memory)
-    srv = Server(hbm_budget_bytes=budget, slots=4, retain=True)
+    srv = Server(hbm_budget_bytes=budget, slots=4, retain=True, priorities=args.priorities)
     for w in ws:
         srv.add_simulation(w.name, w, w.steps.n_shell, w.steps.n_shell + K - 1, fill=lambda p, w=w: fill(p, w))
     admitted = [n for n, s in srv.sims.items() if s.plan is not None]
@@ -621,6 +623,7 @@ def run_serving(args):
         "vs_baseline": None, "dtype": "bf16+f32", "data": "synthetic",
         "config": config_of("c5", extra={"grids": grids, "shells": shells, "requests_per_sim": K}),
         "details": {"hbm_budget_bytes": budget, "admitted_at_once": len(admitted), "slots_per_sim": 4,
+                    "stream_priorities": "by grid size (small first)" if args.priorities else "equal",
                     "fft_passes": fft_choices(),
                     "mac_kernel": {k: v for k, v in lc.autotune_report().items() if k.startswith("mac")},
                     "l2": "no flush: every request streams its simulation's history ring (0.55-26 GB, far above "

@@ -373,24 +373,25 @@ uint64_t lc_kernel_launches(void);
  * lines) into buf (size bytes, NUL-terminated) and returns the full length. */
 int lc_autotune_report(char* buf, int size);
 
-/* The FFT passes of Eq. 12 along y and x (and along z) come in four kernel
- * forms for N = 256 and 512: LC_FFT_STAGES, block-wide Stockham radix stages
+/* The FFT passes of Eq. 12 along y and x (and along z) come in five kernel
+ * forms for N = 256, 384 and 512: LC_FFT_STAGES, block-wide Stockham radix stages
  * in shared memory (every N), and three forms with one lane per tile column
  * (a lane group per row pair along z), the 16-point DFTs in registers and a
  * single shared-memory exchange between the two radix stages:
  * LC_FFT_LANES (tiles copied by 16-byte asynchronous copies into four
- * stages, one CTA per SM), LC_FFT_LANES3 (three stages, two CTAs per SM) and
- * LC_FFT_TMA (tiles moved by tensor-map TMA, three stages, two CTAs per SM).
+ * stages, one CTA per SM), LC_FFT_LANES3 (three stages, two CTAs per SM),
+ * LC_FFT_TMA (tiles moved by tensor-map TMA, three stages, two CTAs per SM)
+ * and LC_FFT_TMA4 (TMA, four stages, one CTA per SM).
  * The first plan created for a grid size times every form on its own
  * buffers (forward and inverse passes of one step) and keeps the fastest
  * for the rest of the process (the choice is listed by lc_autotune_report
  * and persisted with the shell-MAC choices);
- * LC_FFT_VARIANT=stages|lanes|lanes3|tma forces one.
+ * LC_FFT_VARIANT=stages|lanes|lanes3|tma|tma4 forces one.
  * lc_fft_set_variant(n, v) forces v for grid size n from now on (later plans
  * and stand-alone calls; a table already built keeps its values), and
  * lc_fft_variant(n) returns the form in use (-1: n not supported).
  * LC_ERR_UNSUPPORTED_SIZE if n has no such form. */
-enum { LC_FFT_STAGES = 0, LC_FFT_LANES = 1, LC_FFT_LANES3 = 2, LC_FFT_TMA = 3 };
+enum { LC_FFT_STAGES = 0, LC_FFT_LANES = 1, LC_FFT_LANES3 = 2, LC_FFT_TMA = 3, LC_FFT_TMA4 = 4 };
 lc_status lc_fft_set_variant(int n, int variant);
 int lc_fft_variant(int n);
 

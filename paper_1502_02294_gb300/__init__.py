@@ -45,7 +45,7 @@ def autotune_report() -> dict:
     return out
 
 
-FFT_STAGES, FFT_LANES, FFT_LANES3, FFT_TMA = 0, 1, 2, 3  # FFT pass forms (lc_fft_set_variant)
+FFT_STAGES, FFT_LANES, FFT_LANES3, FFT_TMA, FFT_TMA4 = 0, 1, 2, 3, 4  # FFT pass forms (lc_fft_set_variant)
 
 
 def fft_set_variant(n: int, variant: int):

@@ -119,13 +119,13 @@ static EncodeTiledFn encode_tiled() {
 
 // The half spectrum at `work` ([p][q][NRP complex], C order) as a rank-3
 // tensor of floats (2 NRP, N, N), with the box of one column-pass tile: CW
-// columns by min(N, 256) lines q of one plane p (y pass, axis 0), or CW
-// columns by min(N, 256) planes p of one line q (x pass, axis 1).
+// columns by N (from 384: N / 2) lines q of one plane p (y pass, axis 0), or
+// CW columns by as many planes p of one line q (x pass, axis 1).
 bool make_cols_map(CUtensorMap* m, const float2* work, int n, int axis) {
     EncodeTiledFn fn = encode_tiled();
     if (!fn || (reinterpret_cast<uintptr_t>(work) & 15)) return false;
     const cuuint64_t nrp = (cuuint64_t)nrp_of(n), N = (cuuint64_t)n;
-    const cuuint32_t cw = (cuuint32_t)cw_of(n), box_t = n > 256 ? 256u : (cuuint32_t)n;
+    const cuuint32_t cw = (cuuint32_t)cw_of(n), box_t = n > 256 ? (cuuint32_t)(n / 2) : (cuuint32_t)n;
     const cuuint64_t dims[3] = {2 * nrp, N, N};
     const cuuint64_t strides[2] = {nrp * sizeof(float2), N * nrp * sizeof(float2)};
     const cuuint32_t box[3] = {2 * cw, axis == 0 ? box_t : 1u, axis == 0 ? 1u : box_t};
@@ -197,18 +197,18 @@ void tune_load() {
     char line[512], key[256];
     int v;
     while (fgets(line, sizeof line, f))
-        if (sscanf(line, "%255s %d", key, &v) == 2 && v >= 0 && v < MAC_NVAR) g_tune[key] = v;
+        if (sscanf(line, "%255s %d", key, &v) == 2 && v >= 0 && v < 16) g_tune[key] = v; // range checked at use
     fclose(f);
 }
 
-void tune_store(const std::string& key, int v, const double* ms) {
+void tune_store(const std::string& key, int v, const double* ms, int nms) {
     g_tune[key] = v;
     const char* path = getenv("LC_AUTOTUNE_CACHE");
     if (!path) return;
     FILE* f = fopen(path, "a");
     if (!f) return;
     fprintf(f, "%s %d", key.c_str(), v);
-    for (int i = 0; i < MAC_NVAR; ++i) fprintf(f, " %.6f", ms[i]);
+    for (int i = 0; i < nms; ++i) fprintf(f, " %.6f", ms[i]);
     fprintf(f, "\n");
     fclose(f);
 }
@@ -593,7 +593,7 @@ int choose_mac_variant(lc_plan* p, const lc_plan::Table& T, int s) {
         std::lock_guard<std::mutex> g(g_tune_mu);
         tune_load();
         auto it = g_tune.find(key);
-        if (it != g_tune.end() && mac_built(p, it->second)) return it->second;
+        if (it != g_tune.end() && it->second < MAC_NVAR && mac_built(p, it->second)) return it->second;
     }
     // time every built variant with every slice marked valid (the ring's
     // contents do not matter for timing; the output goes to the work buffer)
@@ -644,11 +644,11 @@ int choose_mac_variant(lc_plan* p, const lc_plan::Table& T, int s) {
     for (auto e : ev) cudaEventDestroy(e);
     if (cudaGetLastError() != cudaSuccess) return MAC_GATHER;
     std::lock_guard<std::mutex> g(g_tune_mu);
-    tune_store(key, best, ms);
+    tune_store(key, best, ms, MAC_NVAR);
     return best;
 }
 
-const char* const kFftNames[FFT_NVAR] = {"stages", "lanes", "lanes3", "tma"};
+const char* const kFftNames[FFT_NVAR] = {"stages", "lanes", "lanes3", "tma", "tma4"};
 
 // One step's FFT passes on the plan's own buffers (forward from the int64
 // grid into ring slot 0, inverse from the work spectrum into the grid's
@@ -756,8 +756,8 @@ void choose_fft_variant(lc_plan* p) {
     cudaEvent_t ev[kReps + 1] = {};
     bool ok = true;
     for (int r = 0; ok && r <= kReps; ++r) ok = cudaEventCreate(&ev[r]) == cudaSuccess;
-    static_assert(FFT_NVAR <= MAC_NVAR, "the cache line format holds MAC_NVAR times");
-    double ms[MAC_NVAR] = {-1.0, -1.0, -1.0, -1.0};
+    double ms[FFT_NVAR > MAC_NVAR ? FFT_NVAR : MAC_NVAR];
+    for (auto& m : ms) m = -1.0;
     int best = ops->cols_variant();
     for (int v = 0; ok && v < FFT_NVAR; ++v) {
         if (!(built >> v & 1)) continue;
@@ -785,7 +785,7 @@ void choose_fft_variant(lc_plan* p) {
     cudaMemsetAsync(p->d_grid, 0, sizeof(long long) * (size_t)p->N * p->N * p->N, st);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) return;
     std::lock_guard<std::mutex> g(g_tune_mu);
-    tune_store(key, best, ms);
+    tune_store(key, best, ms, FFT_NVAR);
 }
 
 constexpr int kZsTab = 4096; // points of the 1 + z_s(r) table of the sub-cell near field
@@ -1771,7 +1771,10 @@ int lc_autotune_report(char* buf, int size) {
     tune_load();
     std::string out;
     for (auto& kv : g_tune)
-        out += kv.first + " " + (kv.first.compare(0, 3, "fft") == 0 ? kFftNames[kv.second] : kMacNames[kv.second]) + "\n";
+        out += kv.first + " " +
+               (kv.first.compare(0, 3, "fft") == 0 ? (kv.second < FFT_NVAR ? kFftNames[kv.second] : "?")
+                                                   : (kv.second < MAC_NVAR ? kMacNames[kv.second] : "?")) +
+               "\n";
     if (buf && size > 0) {
         const int n = (int)out.size() < size - 1 ? (int)out.size() : size - 1;
         memcpy(buf, out.data(), n);

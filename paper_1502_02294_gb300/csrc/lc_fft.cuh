@@ -220,11 +220,42 @@ template <int DIR> __device__ __forceinline__ void dft16(float2* v) {
         for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[4 * k1 + k2];
 }
 
+// 12-point DFT as 4 x 3: n = 3 a + b, k = k1 + 4 k2: a 4-point DFT over a for
+// each b, the twiddle W12^(b k1), a 3-point DFT over b for each k1
+template <int DIR> __device__ __forceinline__ void dft12(float2* v) {
+    const float h = 0.86602540378443864676f; // sqrt(3)/2
+    const float ds = (float)DIR;
+    float2 a[3][4];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) a[b][q] = v[3 * q + b];
+        dft4<DIR>(a[b]);
+    }
+    // W12^m = (cos(2 pi m / 12), DIR sin(2 pi m / 12)) for m = 1, 2, 3, 4, 6
+    const float2 w1 = make_float2(h, ds * 0.5f), w2 = make_float2(0.5f, ds * h);
+    const float2 w4 = make_float2(-0.5f, ds * h);
+    a[1][1] = cmul(a[1][1], w1);
+    a[1][2] = cmul(a[1][2], w2);
+    a[1][3] = mul_i<DIR>(a[1][3]); // W12^3 = DIR i
+    a[2][1] = cmul(a[2][1], w2);
+    a[2][2] = cmul(a[2][2], w4);
+    a[2][3] = make_float2(-a[2][3].x, -a[2][3].y); // W12^6 = -1
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        float2 t[3] = {a[0][k1], a[1][k1], a[2][k1]};
+        dft3<DIR>(t);
+#pragma unroll
+        for (int k2 = 0; k2 < 3; ++k2) v[k1 + 4 * k2] = t[k2];
+    }
+}
+
 template <int R, int DIR> __device__ __forceinline__ void dft(float2* v) {
     if constexpr (R == 2) dft2<DIR>(v[0], v[1]);
     else if constexpr (R == 3) dft3<DIR>(v);
     else if constexpr (R == 4) dft4<DIR>(v);
     else if constexpr (R == 8) dft8<DIR>(v);
+    else if constexpr (R == 12) dft12<DIR>(v);
     else if constexpr (R == 16) dft16<DIR>(v);
 }
 

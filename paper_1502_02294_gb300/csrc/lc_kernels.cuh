@@ -516,44 +516,48 @@ __global__ void __launch_bounds__(cols_pl_threads(N)) k_cols_pl(ColArgs a, int n
 }
 
 // ------------------------------------------------------------------------
-// Column passes with one lane per tile column (N = 256 and 512).
+// Column passes with one lane per tile column (N = 256, 384 and 512).
 //
 // The tile (N rows x CW columns, dense [N][CW] in shared memory) is
-// transformed by 256 threads in two radix stages, N = 16 G:
-//   stage 1: thread (column c, residue q < G) holds x[q + G p], p < 16, in
-//            registers, applies a 16-point DFT and the twiddle W_N^(q k1),
-//            and writes Y[q][k1] back over the 16 elements it read (rows
+// transformed by 256 threads in two radix stages, N = R1 G (R1 = 16, or 12
+// at N = 384; G = 16 at N = 256, else 32):
+//   stage 1: thread (column c, residue q < G) holds x[q + G p], p < R1, in
+//            registers, applies an R1-point DFT and the twiddle W_N^(q k1),
+//            and writes Y[q][k1] back over the R1 elements it read (rows
 //            k1 G + q are exactly rows q + G p), so no barrier is needed
 //            before the write;
 //   stage 2 (after one barrier): thread (c, k1) takes Y[q][k1] over q and
 //            applies the G-point DFT: a 16-point DFT in registers (G = 16),
 //            or (G = 32) two 16-point DFTs over the even and odd q, held by
 //            the two lanes 8 apart, combined by one radix-2 step through a
-//            warp shuffle.
+//            warp shuffle (at N = 384 the last two warps have no k1 < 12 and
+//            sit this stage out).
 // Lanes of a warp always touch whole 64- or 128-byte row segments of the
 // tile, so every shared-memory access is free of bank conflicts, and each
-// thread ends with 16 outputs of its column, at rows tb + 16 k (k < 16).
-template <int N> __host__ __device__ constexpr bool cols_lanes_ok() { return N == 256 || N == 512; }
+// active thread ends with 16 outputs of its column, at rows tb + ts k (k < 16).
+template <int N> __host__ __device__ constexpr bool cols_lanes_ok() { return N == 256 || N == 384 || N == 512; }
+// first-stage radix of the lanes passes: 16, or 12 at N = 384 (= 12 x 32)
+template <int N> __host__ __device__ constexpr int lanes_r1(int) { return N == 384 ? 12 : 16; }
 
 template <int N, int DIR>
-__device__ __forceinline__ void fft_cols_lanes(float2* __restrict__ buf, const float2* __restrict__ tw, float2 (&v)[16],
-                                               int& col, int& tb) {
-    constexpr int CW = cw_of(N), G = N / 16;
+__device__ __forceinline__ bool fft_cols_lanes(float2* __restrict__ buf, const float2* __restrict__ tw,
+                                               float2 (&v)[16], int& col, int& tb, int& ts) {
+    constexpr int CW = cw_of(N), R1 = lanes_r1<N>(0), G = N / R1;
     static_assert(CW * G == 256, "256 threads: one per (column, residue)");
     const int tid = threadIdx.x;
     {
         const int c = tid % CW, q = tid / CW;
 #pragma unroll
-        for (int p = 0; p < 16; ++p) v[p] = buf[(q + G * p) * CW + c];
-        dft16<DIR>(v);
+        for (int p = 0; p < R1; ++p) v[p] = buf[(q + G * p) * CW + c];
+        dft<R1, DIR>(v);
 #pragma unroll
-        for (int k1 = 1; k1 < 16; ++k1) {
+        for (int k1 = 1; k1 < R1; ++k1) {
             float2 w = tw[q * k1]; // W_N^(q k1), q k1 < N
             if (DIR > 0) w.y = -w.y;
             v[k1] = cmul(v[k1], w);
         }
 #pragma unroll
-        for (int k1 = 0; k1 < 16; ++k1) buf[(k1 * G + q) * CW + c] = v[k1];
+        for (int k1 = 0; k1 < R1; ++k1) buf[(k1 * G + q) * CW + c] = v[k1];
     }
     __syncthreads();
     if constexpr (G == 16) {
@@ -563,22 +567,29 @@ __device__ __forceinline__ void fft_cols_lanes(float2* __restrict__ buf, const f
         dft16<DIR>(v); // v[k2] = X[k1 + 16 k2]
         col = c;
         tb = k1;
+        ts = 16;
+        return true;
     } else {
-        // q = 2 m + b: E_b = 16-point DFT over m; X[k1 + 16 (k2 + 16 c')] = E_0 + (-1)^c' W_32^k2 E_1
+        // q = 2 m + b: E_b = 16-point DFT over m; X[k1 + R1 (k2 + 16 c')] = E_0 + (-1)^c' W_32^k2 E_1
         const int c = tid % 8, b = (tid >> 3) & 1, k1 = tid >> 4;
+        const bool active = k1 < R1; // whole warps: k1 = 2 w or 2 w + 1
+        if (active) {
 #pragma unroll
-        for (int m = 0; m < 16; ++m) v[m] = buf[(k1 * 32 + 2 * m + b) * 8 + c];
-        dft16<DIR>(v);
+            for (int m = 0; m < 16; ++m) v[m] = buf[(k1 * 32 + 2 * m + b) * 8 + c];
+            dft16<DIR>(v);
+        }
 #pragma unroll
         for (int k2 = 0; k2 < 16; ++k2) {
             const float2 f = make_float2(__shfl_xor_sync(0xffffffffu, v[k2].x, 8),
                                          __shfl_xor_sync(0xffffffffu, v[k2].y, 8));
-            float2 w = tw[16 * k2]; // W_512^(16 k2) = W_32^k2
+            float2 w = tw[R1 * k2]; // W_N^(R1 k2) = W_32^k2
             if (DIR > 0) w.y = -w.y;
             v[k2] = b == 0 ? cadd(v[k2], cmul(w, f)) : csub(f, cmul(w, v[k2]));
         }
         col = c;
-        tb = k1 + 256 * b;
+        tb = k1 + 16 * R1 * b;
+        ts = R1;
+        return active;
     }
 }
 
@@ -597,7 +608,7 @@ __global__ void __launch_bounds__(cols_lanes_threads()) k_cols_lanes(ColArgs a, 
     constexpr int NT = cols_lanes_threads();
     constexpr int CW = cw_of(N), M = N / 2;
     constexpr int TILE = N * CW;
-    static_assert(cols_lanes_ok<N>(), "N = 256 or 512");
+    static_assert(cols_lanes_ok<N>(), "N = 256, 384 or 512");
     extern __shared__ float4 smem_raw[];
     float2* tw = reinterpret_cast<float2*>(smem_raw);
     float2* stages = tw + N;
@@ -626,12 +637,13 @@ __global__ void __launch_bounds__(cols_lanes_threads()) k_cols_lanes(ColArgs a, 
         __syncthreads();
         float2* buf = stages + (k % S) * TILE;
         float2 v[16];
-        int col, tb;
-        fft_cols_lanes<N, DIR>(buf, tw, v, col, tb);
+        int col, tb, ts;
+        const bool active = fft_cols_lanes<N, DIR>(buf, tw, v, col, tb, ts);
         const ColGeom<N> g(tile + a.tile0, a.axis);
 #pragma unroll
         for (int kk = 0; kk < 16; ++kk) {
-            const int t = tb + 16 * kk;
+            if (!active) break;
+            const int t = tb + ts * kk;
             const int idx = t * CW + col;
             if constexpr (OUT == COL_OUT_PLAIN) {
                 a.dst[g.at(idx)] = v[kk];
@@ -653,8 +665,8 @@ __global__ void __launch_bounds__(cols_lanes_threads()) k_cols_lanes(ColArgs a, 
 
 // ------------------------------------------------------------------------
 // Column passes with the tiles moved by tensor-map TMA (N = 256 and 512):
-// the transform is fft_cols_lanes; a full tile is one box (two at N = 512:
-// the box holds at most 256 rows) of the half spectrum seen as a 3D tensor
+// the transform is fft_cols_lanes; a full tile is one box (two from N = 384:
+// a box holds at most 256 rows) of the half spectrum seen as a 3D tensor
 // [p][q][2 NRP floats], copied by cp.async.bulk.tensor into one of S
 // shared-memory stages, completion counted on the stage's mbarrier, issued
 // by one thread S - 1 tiles ahead.  Nyquist tiles (CW single columns of CW
@@ -665,16 +677,15 @@ __global__ void __launch_bounds__(cols_lanes_threads()) k_cols_lanes(ColArgs a, 
 template <int N, int S> __host__ __device__ constexpr size_t cols_tma_smem_bytes() {
     return (size_t)S * N * cw_of(N) * sizeof(float2) + (size_t)N * sizeof(float2) + (size_t)S * 8 + 128;
 }
-constexpr int kColsTmaStages = 3;
-
 template <int N, int DIR, int OUT, int S>
 __global__ void __launch_bounds__(cols_lanes_threads()) k_cols_tma(ColArgs a, int ntiles,
                                                                     const __grid_constant__ CUtensorMap tmap) {
     constexpr int NT = cols_lanes_threads();
     constexpr int CW = cw_of(N), M = N / 2, TILE = N * CW, NCH = M / CW;
-    constexpr int BOX = N > 256 ? 256 : N, NBOX = N / BOX;
+    constexpr int BOX = N > 256 ? N / 2 : N, NBOX = N / BOX; // a box holds at most 256 rows
+    static_assert(BOX <= 256 && N % BOX == 0, "whole boxes of at most 256 rows");
     constexpr unsigned TILE_BYTES = TILE * sizeof(float2);
-    static_assert(cols_lanes_ok<N>(), "N = 256 or 512");
+    static_assert(cols_lanes_ok<N>(), "N = 256, 384 or 512");
     extern __shared__ unsigned char smem_tma[];
     unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_tma) + 127) & ~uintptr_t(127));
     float2* stages = reinterpret_cast<float2*>(sm); // S tiles, each 128-byte aligned
@@ -746,11 +757,12 @@ __global__ void __launch_bounds__(cols_lanes_threads()) k_cols_tma(ColArgs a, in
             return;
         }
         float2 v[16];
-        int col, tb;
-        fft_cols_lanes<N, DIR>(buf, tw, v, col, tb);
+        int col, tb, ts;
+        const bool active = fft_cols_lanes<N, DIR>(buf, tw, v, col, tb, ts);
 #pragma unroll
         for (int kk = 0; kk < 16; ++kk) {
-            const int t = tb + 16 * kk;
+            if (!active) break;
+            const int t = tb + ts * kk;
             const int idx = t * CW + col;
             if constexpr (OUT == COL_OUT_PLAIN) {
                 a.dst[g.at(idx)] = v[kk];
@@ -770,66 +782,78 @@ __global__ void __launch_bounds__(cols_lanes_threads()) k_cols_tma(ColArgs a, in
 }
 
 // ------------------------------------------------------------------------
-// z passes with one row pair per group of G = N / 16 lanes (N = 256: a half
-// warp, N = 512: a warp).  The two real rows a, b of a pair are transformed
-// as one complex row z = a + i b (Eq. 12 along z), N = 16 G:
-//   stage 1: lane q holds z[q + G p], p < 16: 16-point DFT, twiddle
+// z passes with one row pair per group of G lanes (N = 256: a half warp,
+// N = 384 and 512: a warp).  The two real rows a, b of a pair are
+// transformed as one complex row z = a + i b (Eq. 12 along z), N = R1 G:
+//   stage 1: lane q holds z[q + G p], p < R1: R1-point DFT, twiddle
 //            W_N^(q k1), written to a warp-private exchange buffer at
 //            k1 (G + 1) + q (the skew keeps both directions free of bank
 //            conflicts);
 //   stage 2: G = 16: lane k1 reads Y[q][k1] over q, 16-point DFT:
 //            Z[k1 + 16 k2]; G = 32: lane (k1, b) reads the even (b = 0) or
 //            odd q, 16-point DFT, and one radix-2 step with lane ^ 1 through
-//            a shuffle: Z[k1 + 16 k2 + 256 b].
+//            a shuffle: Z[k1 + R1 k2 + 16 R1 b] (at N = 384 lanes 24..31
+//            have no k1 < 12 and sit this stage out).
 // Only warp-level synchronisation is needed: a group never waits for the
 // rest of the block.  Row pairs are assigned per warp, so both half warps of
 // a warp run the same number of iterations.
-template <int N> __host__ __device__ constexpr bool rows_lanes_ok() { return N == 256 || N == 512; }
+template <int N> __host__ __device__ constexpr bool rows_lanes_ok() { return N == 256 || N == 384 || N == 512; }
 constexpr int kRowsLanesThreads = 256;
+template <int N> __host__ __device__ constexpr int rows_lanes_g() { return N / lanes_r1<N>(0); }
 template <int N> __host__ __device__ constexpr int rows_lanes_ex() {
-    return 16 * (N / 16 + 1) > N + 2 ? 16 * (N / 16 + 1) : N + 2; // float2 per group's exchange buffer
+    // float2 per group's exchange buffer: the skewed R1 x G exchange, or Z
+    // in natural order plus two, or both half spectra
+    return lanes_r1<N>(0) * (rows_lanes_g<N>() + 1) > N + 2 ? lanes_r1<N>(0) * (rows_lanes_g<N>() + 1) : N + 2;
 }
 template <int N> __host__ __device__ constexpr size_t rows_lanes_smem_bytes() {
-    return sizeof(float2) * ((size_t)N + (size_t)(kRowsLanesThreads / (N / 16)) * rows_lanes_ex<N>());
+    return sizeof(float2) * ((size_t)N + (size_t)(kRowsLanesThreads / rows_lanes_g<N>()) * rows_lanes_ex<N>());
 }
 
 // In: v[p] = z[q + G p] of this lane (q = lane within its group).  Out: this
-// lane's 16 outputs Z[t0 + 16 k], k < 16, t0 returned.
+// lane's 16 outputs Z[t0 + ts k], k < 16 (t0, ts returned; active false:
+// the lane holds no outputs).
 template <int N, int DIR>
-__device__ __forceinline__ int fft_row_lanes(float2 (&v)[16], float2* __restrict__ ex, const float2* __restrict__ tw,
-                                             int q) {
-    constexpr int G = N / 16, XS = G + 1;
-    dft16<DIR>(v);
+__device__ __forceinline__ bool fft_row_lanes(float2 (&v)[16], float2* __restrict__ ex, const float2* __restrict__ tw,
+                                              int q, int& t0, int& ts) {
+    constexpr int R1 = lanes_r1<N>(0), G = N / R1, XS = G + 1;
+    dft<R1, DIR>(v);
 #pragma unroll
-    for (int k1 = 1; k1 < 16; ++k1) {
+    for (int k1 = 1; k1 < R1; ++k1) {
         float2 w = tw[q * k1];
         if (DIR > 0) w.y = -w.y;
         v[k1] = cmul(v[k1], w);
     }
 #pragma unroll
-    for (int k1 = 0; k1 < 16; ++k1) ex[k1 * XS + q] = v[k1];
+    for (int k1 = 0; k1 < R1; ++k1) ex[k1 * XS + q] = v[k1];
     __syncwarp();
     if constexpr (G == 16) {
 #pragma unroll
         for (int qq = 0; qq < 16; ++qq) v[qq] = ex[q * XS + qq];
         dft16<DIR>(v);
         __syncwarp();
-        return q;
+        t0 = q;
+        ts = 16;
+        return true;
     } else {
         const int k1 = q >> 1, b = q & 1;
+        const bool active = k1 < R1;
+        if (active) {
 #pragma unroll
-        for (int m = 0; m < 16; ++m) v[m] = ex[k1 * XS + 2 * m + b];
-        dft16<DIR>(v);
+            for (int m = 0; m < 16; ++m) v[m] = ex[k1 * XS + 2 * m + b];
+            dft16<DIR>(v);
+        }
 #pragma unroll
         for (int k2 = 0; k2 < 16; ++k2) {
             const float2 f = make_float2(__shfl_xor_sync(0xffffffffu, v[k2].x, 1),
                                          __shfl_xor_sync(0xffffffffu, v[k2].y, 1));
-            float2 w = tw[16 * k2]; // W_32^k2
+            float2 w = tw[R1 * k2]; // W_N^(R1 k2) = W_32^k2
             if (DIR > 0) w.y = -w.y;
             v[k2] = b == 0 ? cadd(v[k2], cmul(w, f)) : csub(f, cmul(w, v[k2]));
         }
         __syncwarp();
-        return k1 + 256 * b;
+        t0 = k1 + 16 * R1 * b;
+        ts = R1;
+        return active;
     }
 }
 
@@ -837,7 +861,7 @@ __device__ __forceinline__ int fft_row_lanes(float2 (&v)[16], float2* __restrict
 // cleared after reading when zero_in) or float input; output rows of NRP.
 template <int N, int IN>
 __global__ void __launch_bounds__(kRowsLanesThreads, 2) k_rows_r2c_lanes(RowR2CArgs a, long long npairs) {
-    constexpr int G = N / 16, PW = 32 / G, NRP = nrp_of(N), H = N / 2 + 1, EX = rows_lanes_ex<N>();
+    constexpr int R1 = lanes_r1<N>(0), G = N / R1, PW = 32 / G, NRP = nrp_of(N), H = N / 2 + 1, EX = rows_lanes_ex<N>();
     static_assert(IN == ROW_IN_I64 || IN == ROW_IN_F32, "grid or float input");
     extern __shared__ float4 smem_raw[];
     float2* tw = reinterpret_cast<float2*>(smem_raw);
@@ -858,31 +882,34 @@ __global__ void __launch_bounds__(kRowsLanesThreads, 2) k_rows_r2c_lanes(RowR2CA
         const long long ra = 2 * rp * N, rb = ra + N;
         float2 v[16];
         if constexpr (IN == ROW_IN_I64) {
-            long long xa[16], xb[16];
+            long long xa[R1], xb[R1];
 #pragma unroll
-            for (int p = 0; p < 16; ++p) {
+            for (int p = 0; p < R1; ++p) {
                 xa[p] = a.grid[ra + q + G * p];
                 xb[p] = a.grid[rb + q + G * p];
             }
             if (a.zero_in) {
                 long long* g = const_cast<long long*>(a.grid);
 #pragma unroll
-                for (int p = 0; p < 16; ++p) {
+                for (int p = 0; p < R1; ++p) {
                     g[ra + q + G * p] = 0;
                     g[rb + q + G * p] = 0;
                 }
             }
 #pragma unroll
-            for (int p = 0; p < 16; ++p) v[p] = make_float2(__ll2float_rn(xa[p]) * scale, __ll2float_rn(xb[p]) * scale);
+            for (int p = 0; p < R1; ++p) v[p] = make_float2(__ll2float_rn(xa[p]) * scale, __ll2float_rn(xb[p]) * scale);
         } else {
 #pragma unroll
-            for (int p = 0; p < 16; ++p) v[p] = make_float2(a.fin[ra + q + G * p], a.fin[rb + q + G * p]);
+            for (int p = 0; p < R1; ++p) v[p] = make_float2(a.fin[ra + q + G * p], a.fin[rb + q + G * p]);
         }
-        const int t0 = fft_row_lanes<N, -1>(v, ex, tw, q);
+        int t0, ts;
+        const bool active = fft_row_lanes<N, -1>(v, ex, tw, q, t0, ts);
         // Z in natural order, then the two real rows' half spectra:
         // X_a = (Z_k + conj Z_{N-k}) / 2, X_b = (Z_k - conj Z_{N-k}) / (2 i)
+        if (active) {
 #pragma unroll
-        for (int k = 0; k < 16; ++k) ex[t0 + 16 * k] = v[k];
+            for (int k = 0; k < 16; ++k) ex[t0 + ts * k] = v[k];
+        }
         __syncwarp();
         float2* da = a.dst + (2 * rp) * NRP;
         float2* db = da + NRP;
@@ -902,7 +929,7 @@ __global__ void __launch_bounds__(kRowsLanesThreads, 2) k_rows_r2c_lanes(RowR2CA
 // z inverse, complex -> real, times `scale`: rows of NRP in, N floats out.
 template <int N>
 __global__ void __launch_bounds__(kRowsLanesThreads, 2) k_rows_c2r_lanes(RowC2RArgs a, long long npairs) {
-    constexpr int G = N / 16, PW = 32 / G, NRP = nrp_of(N), H = N / 2 + 1, EX = rows_lanes_ex<N>();
+    constexpr int R1 = lanes_r1<N>(0), G = N / R1, PW = 32 / G, NRP = nrp_of(N), H = N / 2 + 1, EX = rows_lanes_ex<N>();
     static_assert(2 * H <= EX, "both half spectra fit the exchange buffer");
     extern __shared__ float4 smem_raw[];
     float2* tw = reinterpret_cast<float2*>(smem_raw);
@@ -934,7 +961,7 @@ __global__ void __launch_bounds__(kRowsLanesThreads, 2) k_rows_c2r_lanes(RowC2RA
         // Z_n = X_a(n) + i X_b(n), with the Hermitian extension X(N - k) = conj X(k)
         float2 v[16];
 #pragma unroll
-        for (int p = 0; p < 16; ++p) {
+        for (int p = 0; p < R1; ++p) {
             const int n = q + G * p;
             if (n < H) {
                 const float2 A = xa[n], B = xb[n];
@@ -945,13 +972,16 @@ __global__ void __launch_bounds__(kRowsLanesThreads, 2) k_rows_c2r_lanes(RowC2RA
             }
         }
         __syncwarp();
-        const int t0 = fft_row_lanes<N, 1>(v, ex, tw, q);
+        int t0, ts;
+        const bool active = fft_row_lanes<N, 1>(v, ex, tw, q, t0, ts);
         float* oa = a.out + (2 * rp) * N;
         float* ob = oa + N;
+        if (active) {
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            oa[t0 + 16 * k] = v[k].x * a.scale;
-            ob[t0 + 16 * k] = v[k].y * a.scale;
+            for (int k = 0; k < 16; ++k) {
+                oa[t0 + ts * k] = v[k].x * a.scale;
+                ob[t0 + ts * k] = v[k].y * a.scale;
+            }
         }
     }
 }
@@ -1329,14 +1359,14 @@ struct FftOps {
     // the y / x pass kernel of grids with more than one: FFT_COLS_STAGES
     // (block-wide Stockham stages), FFT_COLS_LANES (one lane per column, four
     // tile stages, one CTA per SM), FFT_COLS_LANES3 (three stages, two CTAs
-    // per SM) or FFT_COLS_TMA (the tiles moved by tensor-map TMA, three stages,
-    // two CTAs per SM); chosen by the autotuner or LC_FFT_VARIANT, shared by
-    // the process
+    // per SM), FFT_COLS_TMA (the tiles moved by tensor-map TMA, three stages,
+    // two CTAs per SM) or FFT_COLS_TMA4 (TMA, four stages, one CTA per SM);
+    // chosen by the autotuner or LC_FFT_VARIANT, shared by the process
     int (*cols_variants)();          // bit mask of the variants built for this N
     void (*set_cols_variant)(int);
     int (*cols_variant)();
 };
-enum { FFT_COLS_STAGES = 0, FFT_COLS_LANES = 1, FFT_COLS_LANES3 = 2, FFT_COLS_TMA = 3, FFT_NVAR = 4 };
+enum { FFT_COLS_STAGES = 0, FFT_COLS_LANES = 1, FFT_COLS_LANES3 = 2, FFT_COLS_TMA = 3, FFT_COLS_TMA4 = 4, FFT_NVAR = 5 };
 
 template <int N> struct Launch {
     static constexpr int CW = cw_of(N), NCH = (N / 2) / CW;
@@ -1380,7 +1410,9 @@ template <int N> struct Launch {
     }
     static int variants_built() {
         return (1 << FFT_COLS_STAGES) |
-               (cols_lanes_ok<N>() ? (1 << FFT_COLS_LANES) | (1 << FFT_COLS_LANES3) | (1 << FFT_COLS_TMA) : 0);
+               (cols_lanes_ok<N>()
+                    ? (1 << FFT_COLS_LANES) | (1 << FFT_COLS_LANES3) | (1 << FFT_COLS_TMA) | (1 << FFT_COLS_TMA4)
+                    : 0);
     }
     static void set_variant(int v) {
         if (v >= 0 && v < FFT_NVAR && (variants_built() >> v & 1)) variant() = v;
@@ -1410,12 +1442,9 @@ template <int N> struct Launch {
                      cols_lanes_smem_bytes<N, S>(), st, a, ntiles);
         }
     }
-    static bool lanes_form() {
-        return variant() == FFT_COLS_LANES || variant() == FFT_COLS_LANES3 || variant() == FFT_COLS_TMA;
-    }
-    template <int DIR, int OUT> static void cols_tma_launch(const ColArgs& a, int ntiles, cudaStream_t st) {
+    static bool lanes_form() { return variant() != FFT_COLS_STAGES; }
+    template <int DIR, int OUT, int S> static void cols_tma_launch(const ColArgs& a, int ntiles, cudaStream_t st) {
         if constexpr (cols_lanes_ok<N>()) {
-            constexpr int S = kColsTmaStages;
             static int ctas = 0;
             if (!ctas) {
                 int occ = 0;
@@ -1433,8 +1462,9 @@ template <int N> struct Launch {
     }
     template <int DIR, int OUT> static void cols_plain(const ColArgs& a, int ntiles, cudaStream_t st) {
         if constexpr (cols_lanes_ok<N>()) {
-            if (variant() == FFT_COLS_TMA && a.tmap) {
-                cols_tma_launch<DIR, OUT>(a, ntiles, st);
+            if ((variant() == FFT_COLS_TMA || variant() == FFT_COLS_TMA4) && a.tmap) {
+                if (variant() == FFT_COLS_TMA4) cols_tma_launch<DIR, OUT, 4>(a, ntiles, st);
+                else cols_tma_launch<DIR, OUT, 3>(a, ntiles, st);
                 return;
             }
             if (lanes_form() && aligned16(a.src)) {
@@ -1497,12 +1527,17 @@ template <int N> struct Launch {
                 LC_ATTR((k_cols_lanes<N, -1, COL_OUT_WEDGE, 3>), l3);
                 LC_ATTR((k_cols_lanes<N, -1, COL_OUT_RING_F32, 3>), l3);
                 LC_ATTR((k_cols_lanes<N, 1, COL_OUT_PLAIN, 3>), l3);
-                const int tm = (int)cols_tma_smem_bytes<N, kColsTmaStages>();
-                LC_ATTR((k_cols_tma<N, -1, COL_OUT_PLAIN, kColsTmaStages>), tm);
-                LC_ATTR((k_cols_tma<N, -1, COL_OUT_BF16, kColsTmaStages>), tm);
-                LC_ATTR((k_cols_tma<N, -1, COL_OUT_WEDGE, kColsTmaStages>), tm);
-                LC_ATTR((k_cols_tma<N, -1, COL_OUT_RING_F32, kColsTmaStages>), tm);
-                LC_ATTR((k_cols_tma<N, 1, COL_OUT_PLAIN, kColsTmaStages>), tm);
+                const int tm = (int)cols_tma_smem_bytes<N, 3>(), t4 = (int)cols_tma_smem_bytes<N, 4>();
+                LC_ATTR((k_cols_tma<N, -1, COL_OUT_PLAIN, 3>), tm);
+                LC_ATTR((k_cols_tma<N, -1, COL_OUT_BF16, 3>), tm);
+                LC_ATTR((k_cols_tma<N, -1, COL_OUT_WEDGE, 3>), tm);
+                LC_ATTR((k_cols_tma<N, -1, COL_OUT_RING_F32, 3>), tm);
+                LC_ATTR((k_cols_tma<N, 1, COL_OUT_PLAIN, 3>), tm);
+                LC_ATTR((k_cols_tma<N, -1, COL_OUT_PLAIN, 4>), t4);
+                LC_ATTR((k_cols_tma<N, -1, COL_OUT_BF16, 4>), t4);
+                LC_ATTR((k_cols_tma<N, -1, COL_OUT_WEDGE, 4>), t4);
+                LC_ATTR((k_cols_tma<N, -1, COL_OUT_RING_F32, 4>), t4);
+                LC_ATTR((k_cols_tma<N, 1, COL_OUT_PLAIN, 4>), t4);
             }
         } else {
             LC_ATTR((k_cols_pp<N, -1, COL_OUT_PLAIN>), cs);

@@ -128,7 +128,7 @@ def test_512_bf16_mac_kernels_agree(monkeypatch):
     assert np.isfinite(res["ws2"]).all() and res["ws2"].max() > 0
 
 
-@pytest.mark.parametrize("n", [256, 512])
+@pytest.mark.parametrize("n", [256, 384, 512])
 def test_fft_pass_forms_against_numpy_and_each_other(n):
     # both forms of the FFT passes (block-wide stages, one lane per column)
     # against numpy's FP64 transform, Parseval, and the round trip
@@ -139,7 +139,7 @@ def test_fft_pass_forms_against_numpy_and_each_other(n):
     ref = np.fft.rfftn(x.astype(np.float64))
     res = {}
     try:
-        for v in (lc.FFT_STAGES, lc.FFT_LANES, lc.FFT_LANES3, lc.FFT_TMA):
+        for v in (lc.FFT_STAGES, lc.FFT_LANES, lc.FFT_LANES3, lc.FFT_TMA, lc.FFT_TMA4):
             lc.fft_set_variant(n, v)
             assert lc.fft_variant(n) == v
             X = lc.fft_r2c(xt)
@@ -151,12 +151,13 @@ def test_fft_pass_forms_against_numpy_and_each_other(n):
             res[v] = Xn
     finally:
         lc.fft_set_variant(n, before)
-    for v in (lc.FFT_LANES, lc.FFT_LANES3, lc.FFT_TMA):
+    for v in (lc.FFT_LANES, lc.FFT_LANES3, lc.FFT_TMA, lc.FFT_TMA4):
         d = np.linalg.norm(res[lc.FFT_STAGES] - res[v]) / np.linalg.norm(ref)
         assert d < 2e-6, (v, d)
     # the same arithmetic under other tile schedules and copy engines
     assert np.array_equal(res[lc.FFT_LANES], res[lc.FFT_LANES3])
     assert np.array_equal(res[lc.FFT_LANES], res[lc.FFT_TMA])
+    assert np.array_equal(res[lc.FFT_LANES], res[lc.FFT_TMA4])
 
 
 def test_fft_pass_forms_give_oracle_fields():
@@ -170,7 +171,7 @@ def test_fft_pass_forms_give_oracle_fields():
     ref = oracle.field_for(P, w.cat, 7, cells=cells)
     before = lc.fft_variant(256)
     try:
-        for v in (lc.FFT_STAGES, lc.FFT_LANES, lc.FFT_LANES3, lc.FFT_TMA):
+        for v in (lc.FFT_STAGES, lc.FFT_LANES, lc.FFT_LANES3, lc.FFT_TMA, lc.FFT_TMA4):
             lc.fft_set_variant(256, v)
             got = _fields(w, range(8), {7})[7].reshape(-1)[cells].astype(np.float64)
             rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
