@@ -88,8 +88,9 @@ def parse(argv=None):
     ap.add_argument("--fdiff", action="store_true",
                     help="each step also builds the instantaneous field (Eq. 18) and the f_diff map")
     ap.add_argument("--no-c3", action="store_true", help="c5: skip the 256^3 single-instance extra key")
-    ap.add_argument("--priorities", action="store_true",
-                    help="c5: run small grids' streams at higher CUDA stream priority")
+    ap.add_argument("--equal-priorities", action="store_true",
+                    help="c5: every simulation's stream at the default CUDA stream priority (default: small grids "
+                         "higher, the Server's default)")
     return ap.parse_args(argv)
 
 
@@ -484,7 +485,7 @@ def run_serving(args):
         return arr
 
     budget = int(0.6 * torch.cuda.get_device_properties(dev).total_memory)
-    srv = Server(hbm_budget_bytes=budget, slots=4, retain=True, priorities=args.priorities)
+    srv = Server(hbm_budget_bytes=budget, slots=4, retain=True, priorities=not args.equal_priorities)
     for w in ws:
         srv.add_simulation(w.name, w, w.steps.n_shell, w.steps.n_shell + K - 1, fill=lambda p, w=w: fill(p, w))
     admitted = [n for n, s in srv.sims.items() if s.plan is not None]
@@ -623,8 +624,8 @@ def run_serving(args):
         "vs_baseline": None, "dtype": "bf16+f32", "data": "synthetic",
         "config": config_of("c5", extra={"grids": grids, "shells": shells, "requests_per_sim": K}),
         "details": {"hbm_budget_bytes": budget, "admitted_at_once": len(admitted), "slots_per_sim": 4,
-                    "stream_priorities": "by grid size (small first)" if args.priorities else "equal",
-                    "fft_passes": fft_choices(),
+                    "stream_priorities": "equal" if args.equal_priorities else "by grid size (small first)",
+                    "fft_passes": fft_choices(), "launch_overlap": bool(lc.launch_overlap(-1)),
                     "mac_kernel": {k: v for k, v in lc.autotune_report().items() if k.startswith("mac")},
                     "l2": "no flush: every request streams its simulation's history ring (0.55-26 GB, far above "
                           "the 129 MB L2) from HBM",
@@ -987,7 +988,7 @@ def run_single(args, w, variant, quick=False):
             "config": config_of(args.workload, w, variant),
             "details": {"timed_window": [t0, T], "ring_slots": plan.n_ring,
                         "mac_kernel": dict(sorted(mac_choice.items(), key=lambda kv: int(kv[0][1:]))),
-                        "fft_passes": fft_choices(),
+                        "fft_passes": fft_choices(), "launch_overlap": bool(lc.launch_overlap(-1)),
                         "l2": f"flushed between timed steps ({args.flush_mb} MB write outside the events)",
                         "inputs": "device-resident"},
             "cell_shell_mac_per_s": world * mac_cells / t_max,

@@ -286,7 +286,7 @@ lc_status lc_batch_step(lc_plan* const* plans, int n, const int* steps, const in
 /* The state a plan carries from step to step is the history of past source
  * spectra that the retarded sum of Eq. 11 reads (one slice per active shell),
  * with each slice's fixed-point unit and exact total, the last pushed step,
- * and the innermost slice's source cells (near field, FP32 history).  The
+ * and the innermost slice's source cells (near field).  The
  * Green's function tables are not part of it: they are a deterministic
  * function of the plan's parameters and are rebuilt on demand.
  *
@@ -346,7 +346,7 @@ enum {
     LC_PHASE_MAC_X = 4,      /* shell multiply-accumulate fused with the inverse x pass */
     LC_PHASE_INV_Y = 5,      /* y pass, inverse */
     LC_PHASE_C2R_Z = 6,      /* z rows, complex -> real, scaled output */
-    LC_PHASE_NEAR = 7,       /* innermost shell's near cube, exact FP64 scatter + fold (FP32 history) */
+    LC_PHASE_NEAR = 7,       /* innermost shell's near cube, exact FP64 scatter + fold */
     LC_N_PHASES = 8
 };
 /* Enable (1) or disable (0) per-phase event timing on this plan. */
@@ -394,6 +394,17 @@ int lc_autotune_report(char* buf, int size);
 enum { LC_FFT_STAGES = 0, LC_FFT_LANES = 1, LC_FFT_LANES3 = 2, LC_FFT_TMA = 3, LC_FFT_TMA4 = 4 };
 lc_status lc_fft_set_variant(int n, int variant);
 int lc_fft_variant(int n);
+
+/* Launch overlap (programmatic dependent launch).  While on (the default;
+ * LC_PDL=0 in the environment starts the process with it off), each per-step
+ * kernel of a plan is launched so that it may be scheduled onto SMs that the
+ * kernel before it in the stream has already released; it touches no memory
+ * until that kernel has completed, so results are identical either way.  It
+ * applies to eager launches and to graphs captured while it is on, and is
+ * left off while a plan's phase timing is on (phase events between kernels).
+ * lc_launch_overlap(on): on = 1 or 0 sets it for plans' later launches and
+ * captures, on < 0 only queries; returns the previous setting (1 or 0). */
+int lc_launch_overlap(int on);
 
 /* --- light-cone vs instantaneous field ------------------------------------------ */
 

@@ -49,13 +49,19 @@ FFT_STAGES, FFT_LANES, FFT_LANES3, FFT_TMA, FFT_TMA4 = 0, 1, 2, 3, 4  # FFT pass
 
 
 def fft_set_variant(n: int, variant: int):
-    """Force the FFT pass form for grid size n (FFT_STAGES or FFT_LANES)."""
+    """Force the FFT pass form for grid size n (one of FFT_STAGES ... FFT_TMA4)."""
     _check(_lib().lc_fft_set_variant(int(n), int(variant)), "lc_fft_set_variant")
 
 
 def fft_variant(n: int) -> int:
     """The FFT pass form in use for grid size n (-1: n not supported)."""
     return int(_lib().lc_fft_variant(int(n)))
+
+
+def launch_overlap(on: int = -1) -> bool:
+    """Programmatic dependent launch of the per-step kernels: set it (on = 1
+    or 0) or only query it (on < 0); returns the previous setting."""
+    return bool(_lib().lc_launch_overlap(int(on)))
 
 
 def kernel_launches() -> int:
@@ -131,6 +137,7 @@ SIGNATURES = [
     ("lc_autotune_report", _I, [ctypes.c_char_p, _I]),
     ("lc_fft_set_variant", _I, [_I, _I]),
     ("lc_fft_variant", _I, [_I]),
+    ("lc_launch_overlap", _I, [_I]),
     ("lc_fdiff_map", _I, [_I64, _VP, _VP, _VP, _VP]),
     ("lc_plan_set_table_budget", _I, [_P, ctypes.c_size_t]),
     ("lc_plan_table_bytes", ctypes.c_size_t, [_P]),

@@ -90,10 +90,14 @@ class Server:
     admission (the tables the paper precomputes); k to keep at most k steps'
     tables (lc_plan_set_table_budget), building later ones when their step
     is served.  retain: keep simulations admitted after their last request
-    (rewind() then serves the same steps again)."""
+    (rewind() then serves the same steps again).  priorities: each
+    simulation's stream gets a CUDA stream priority by grid size (the
+    highest up to 192^3, the middle one at 256^3, the lowest above), so short
+    requests of small grids are not queued behind the blocks of large ones;
+    False gives every stream the default priority."""
 
     def __init__(self, hbm_budget_bytes: int, keep_outputs: bool = False, host_outputs: bool = False,
-                 slots: int = 4, table_steps: Optional[int] = None, retain: bool = False, priorities: bool = False):
+                 slots: int = 4, table_steps: Optional[int] = None, retain: bool = False, priorities: bool = True):
         import torch
 
         self.torch = torch

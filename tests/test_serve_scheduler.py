@@ -212,3 +212,19 @@ def test_rewind_serves_the_same_steps_from_a_refilled_history():
         srv.rewind()
     assert log == [2, 3, "reset", "fill", 2, 3, "reset", "fill"]
     assert st["by_grid"][8]["requests"] == 2
+
+
+def test_stream_priority_by_grid_size():
+    srv = _server(1 << 40)
+    got = {}
+    for pr in (True, False):
+        srv.priorities = pr
+        for n in (128, 192, 256, 384, 512):
+            sim = sv.Simulation("s%d" % n, types.SimpleNamespace(n=n), 0, 0, fill=None, plan=None, stream=None,
+                                next_step=0, remaining=1)
+            got[pr, n] = srv._stream_for(sim).priority
+    # CUDA: a lower number is a higher priority; range (0, -5) in the stand-in
+    assert got[True, 128] == got[True, 192] == -5
+    assert got[True, 256] in (-2, -3)
+    assert got[True, 384] == got[True, 512] == 0
+    assert all(got[False, n] == 0 for n in (128, 192, 256, 384, 512))
