@@ -625,7 +625,7 @@ def run_serving(args):
         "config": config_of("c5", extra={"grids": grids, "shells": shells, "requests_per_sim": K}),
         "details": {"hbm_budget_bytes": budget, "admitted_at_once": len(admitted), "slots_per_sim": 4,
                     "stream_priorities": "equal" if args.equal_priorities else "by grid size (small first)",
-                    "fft_passes": fft_choices(), "launch_overlap": bool(lc.launch_overlap(-1)),
+                    "fft_passes": fft_choices(),
                     "mac_kernel": {k: v for k, v in lc.autotune_report().items() if k.startswith("mac")},
                     "l2": "no flush: every request streams its simulation's history ring (0.55-26 GB, far above "
                           "the 129 MB L2) from HBM",
@@ -988,7 +988,7 @@ def run_single(args, w, variant, quick=False):
             "config": config_of(args.workload, w, variant),
             "details": {"timed_window": [t0, T], "ring_slots": plan.n_ring,
                         "mac_kernel": dict(sorted(mac_choice.items(), key=lambda kv: int(kv[0][1:]))),
-                        "fft_passes": fft_choices(), "launch_overlap": bool(lc.launch_overlap(-1)),
+                        "fft_passes": fft_choices(),
                         "l2": f"flushed between timed steps ({args.flush_mb} MB write outside the events)",
                         "inputs": "device-resident"},
             "cell_shell_mac_per_s": world * mac_cells / t_max,

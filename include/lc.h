@@ -395,17 +395,6 @@ enum { LC_FFT_STAGES = 0, LC_FFT_LANES = 1, LC_FFT_LANES3 = 2, LC_FFT_TMA = 3, L
 lc_status lc_fft_set_variant(int n, int variant);
 int lc_fft_variant(int n);
 
-/* Launch overlap (programmatic dependent launch).  While on (the default;
- * LC_PDL=0 in the environment starts the process with it off), each per-step
- * kernel of a plan is launched so that it may be scheduled onto SMs that the
- * kernel before it in the stream has already released; it touches no memory
- * until that kernel has completed, so results are identical either way.  It
- * applies to eager launches and to graphs captured while it is on, and is
- * left off while a plan's phase timing is on (phase events between kernels).
- * lc_launch_overlap(on): on = 1 or 0 sets it for plans' later launches and
- * captures, on < 0 only queries; returns the previous setting (1 or 0). */
-int lc_launch_overlap(int on);
-
 /* --- light-cone vs instantaneous field ------------------------------------------ */
 
 /* The fractional difference f_diff = (J_instant - J) / J that Section 3 uses

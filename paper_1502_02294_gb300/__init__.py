@@ -58,12 +58,6 @@ def fft_variant(n: int) -> int:
     return int(_lib().lc_fft_variant(int(n)))
 
 
-def launch_overlap(on: int = -1) -> bool:
-    """Programmatic dependent launch of the per-step kernels: set it (on = 1
-    or 0) or only query it (on < 0); returns the previous setting."""
-    return bool(_lib().lc_launch_overlap(int(on)))
-
-
 def kernel_launches() -> int:
     """Kernels liblc has launched in this process."""
     return int(_lib().lc_kernel_launches())
@@ -137,7 +131,6 @@ SIGNATURES = [
     ("lc_autotune_report", _I, [ctypes.c_char_p, _I]),
     ("lc_fft_set_variant", _I, [_I, _I]),
     ("lc_fft_variant", _I, [_I]),
-    ("lc_launch_overlap", _I, [_I]),
     ("lc_fdiff_map", _I, [_I64, _VP, _VP, _VP, _VP]),
     ("lc_plan_set_table_budget", _I, [_P, ctypes.c_size_t]),
     ("lc_plan_table_bytes", ctypes.c_size_t, [_P]),

@@ -185,19 +185,6 @@ std::mutex g_tune_mu;
 std::map<std::string, int> g_tune;
 bool g_tune_loaded = false;
 std::map<int, int> g_fft_forced; // grid size -> FFT variant forced by lc_fft_set_variant
-// programmatic dependent launch of the per-step kernels (lc_launch_overlap)
-std::atomic<int> g_overlap{-1};
-bool overlap_on() {
-    int v = g_overlap.load(std::memory_order_relaxed);
-    if (v < 0) {
-        const char* e = getenv("LC_PDL");
-        v = (e && e[0] == '0') ? 0 : 1;
-        int expect = -1;
-        g_overlap.compare_exchange_strong(expect, v);
-        v = g_overlap.load(std::memory_order_relaxed);
-    }
-    return v != 0;
-}
 
 void tune_load() {
     if (g_tune_loaded) return;
@@ -379,17 +366,13 @@ struct Phase {
         if (p->capturing) cudaEventRecordWithFlags(e, p->stream, cudaEventRecordExternal);
         else cudaEventRecord(e, p->stream);
     }
-    bool pdl_prev;
-    Phase(lc_plan* p_, int ph_, int kernels) : p(p_), ph(ph_), k(kernels), pdl_prev(tl_pdl) {
-        // overlapped launches only when no phase events sit between kernels
-        tl_pdl = !p->timing && overlap_on();
+    Phase(lc_plan* p_, int ph_, int kernels) : p(p_), ph(ph_), k(kernels) {
         if (p->timing) {
             a = take_event(p);
             record(a);
         }
     }
     ~Phase() {
-        tl_pdl = pdl_prev;
         if (p->timing) {
             cudaEvent_t b = take_event(p);
             record(b);
@@ -1057,12 +1040,6 @@ lc_status lc_fft_set_variant(int n, int v) {
 int lc_fft_variant(int n) {
     const FftOps* ops = ops_for(n);
     return ops ? ops->cols_variant() : -1;
-}
-
-int lc_launch_overlap(int on) {
-    const int prev = overlap_on() ? 1 : 0;
-    if (on >= 0) g_overlap.store(on ? 1 : 0, std::memory_order_relaxed);
-    return prev;
 }
 
 const char* lc_status_string(lc_status s) {

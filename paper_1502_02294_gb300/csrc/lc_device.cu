@@ -29,7 +29,6 @@ __device__ __forceinline__ bool finite_d(double x) { return isfinite(x); }
 __global__ void __launch_bounds__(kPrepThreads)
     k_src_prep(const double* __restrict__ pos, const double* __restrict__ lum, long long n,
                unsigned long long* maxbits, int* err, SlotMeta m) {
-    pdl_begin();
     __shared__ unsigned long long s_max[kPrepThreads / 32];
     __shared__ int s_bad;
     if (threadIdx.x == 0) s_bad = 0;
@@ -105,7 +104,6 @@ __global__ void __launch_bounds__(256)
     k_deposit(const double* __restrict__ pos, const double* __restrict__ lum, long long n, int N, double l,
               const unsigned long long* __restrict__ maxbits, long long* __restrict__ grid, SlotMeta m, int* err,
               long long* __restrict__ cell_out, long long* __restrict__ q_out, double* __restrict__ off_out) {
-    pdl_begin();
     __shared__ long long s_sum[8];
     const double lmax = __longlong_as_double((long long)*maxbits);
     double S = 1.0;
@@ -315,7 +313,6 @@ __global__ void __launch_bounds__(256) k_near_scatter(const long long* __restric
                                                       long long n, int N, const double* __restrict__ gnear,
                                                       const double* __restrict__ slot_S, int slot, double U,
                                                       double* __restrict__ acc) {
-    pdl_begin();
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n * kNearCube) return;
     const long long s = idx / kNearCube;
@@ -330,7 +327,6 @@ __global__ void __launch_bounds__(256) k_near_scatter(const long long* __restric
 __global__ void __launch_bounds__(256) k_near_fold(const long long* __restrict__ cell, const long long* __restrict__ q,
                                                    long long n, int N, double* __restrict__ acc, float* __restrict__ out,
                                                    long long* __restrict__ grid) {
-    pdl_begin();
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n * kNearCube) return;
     const long long s = idx / kNearCube;
@@ -373,7 +369,6 @@ __device__ __forceinline__ void image_range(double b, double L, double invL, dou
 }
 
 __global__ void __launch_bounds__(256, 2) k_near_pm(NearPmArgs a, double* __restrict__ acc) {
-    pdl_begin();
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= a.n * kNearCube) return;
     const long long s = idx / kNearCube;
@@ -492,7 +487,6 @@ void launch_near_fold(const long long* cell, const long long* q, long long n, in
 __global__ void __launch_bounds__(256) k_cells_clear(const long long* __restrict__ cell,
                                                      const long long* __restrict__ q, long long n,
                                                      long long* __restrict__ grid) {
-    pdl_begin();
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n && q[i] != 0) grid[cell[i]] = 0;
 }

@@ -37,38 +37,18 @@ __host__ __device__ __forceinline__ int near_wedge(int dx, int dy, int dz) {
     return c * (c + 1) * (c + 2) / 6 + b * (b + 1) / 2 + a;
 }
 
-// Programmatic dependent launch.  While tl_pdl is set, launch_k gives a
-// launch the programmatic stream-serialisation attribute: the grid may be
-// scheduled onto SMs that the kernel before it in the stream has released,
-// before that kernel has finished.  Every kernel launched through launch_k
-// therefore begins with pdl_begin(): griddepcontrol.wait returns once the
-// preceding grid has completed and its writes are visible (at once when the
-// launch had no programmatic dependency), so no global memory is read or
-// written before it; griddepcontrol.launch_dependents then lets the next
-// grid be scheduled.  Because every CTA waits before it can finish, a grid
-// completes only after its predecessor has, so the ordering is transitive.
-inline thread_local bool tl_pdl = false;
-
-__device__ __forceinline__ void pdl_begin() {
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
 // Launch through cudaLaunchKernelEx (one launch path for every per-step
-// kernel; the only attribute is the programmatic serialisation above).
+// kernel; no launch attributes).
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                             Args&&... args) {
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    cfg.attrs = tl_pdl ? attr : nullptr;
-    cfg.numAttrs = tl_pdl ? 1 : 0;
+    cfg.attrs = nullptr;
+    cfg.numAttrs = 0;
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 

@@ -145,7 +145,6 @@ template <int N> __host__ __device__ constexpr size_t cols_smem_bytes() {
 // (compile-time count, registers) before transforming the current one.
 template <int N, int IN>
 __global__ void __launch_bounds__(kThreads) k_rows_r2c(RowR2CArgs a, int nblocks) {
-    pdl_begin();
     constexpr int B = row_pairs_of(N), BP = odd_pad(B), NRP = nrp_of(N), H = N / 2 + 1;
     constexpr int TILE = 2 * B * N, PER = (TILE + kThreads - 1) / kThreads;
     extern __shared__ float4 smem_raw[];
@@ -226,7 +225,6 @@ __global__ void __launch_bounds__(kThreads) k_rows_r2c(RowR2CArgs a, int nblocks
 // CW Nyquist columns of CW lines).  NT = N * CW / 8 threads, 8 elements each.
 template <int N, int DIR, int IN, int OUT>
 __global__ void __launch_bounds__(col_threads_of(N)) k_cols(ColArgs a) {
-    pdl_begin();
     constexpr int NT = col_threads_of(N);
     constexpr int CW = cw_of(N), BP = odd_pad(CW), NRP = nrp_of(N), M = N / 2, NCH = M / CW;
     constexpr int TILE = N * CW, PER = (TILE + NT - 1) / NT;
@@ -372,7 +370,6 @@ template <int N> struct ColGeom {
 
 template <int N, int DIR, int OUT>
 __global__ void __launch_bounds__(col_threads_of(N)) k_cols_pp(ColArgs a, int ntiles) {
-    pdl_begin();
     constexpr int NT = col_threads_of(N);
     constexpr int CW = cw_of(N), BP = odd_pad(CW), M = N / 2;
     constexpr int TILE = N * CW, PER = (TILE + NT - 1) / NT;
@@ -463,7 +460,6 @@ template <int N> __host__ __device__ constexpr size_t cols_pl_smem_bytes() {
 // 16 complex or two of 8, so the dense layout is free of bank conflicts).
 template <int N, int DIR, int OUT>
 __global__ void __launch_bounds__(cols_pl_threads(N)) k_cols_pl(ColArgs a, int ntiles) {
-    pdl_begin();
     constexpr int NT = cols_pl_threads(N);
     constexpr int CW = cw_of(N), M = N / 2, S = cols_pl_stages(N);
     constexpr int TILE = N * CW;
@@ -609,7 +605,6 @@ template <int N, int S> __host__ __device__ constexpr size_t cols_lanes_smem_byt
 }
 template <int N, int DIR, int OUT, int S>
 __global__ void __launch_bounds__(cols_lanes_threads()) k_cols_lanes(ColArgs a, int ntiles) {
-    pdl_begin();
     constexpr int NT = cols_lanes_threads();
     constexpr int CW = cw_of(N), M = N / 2;
     constexpr int TILE = N * CW;
@@ -685,7 +680,6 @@ template <int N, int S> __host__ __device__ constexpr size_t cols_tma_smem_bytes
 template <int N, int DIR, int OUT, int S>
 __global__ void __launch_bounds__(cols_lanes_threads()) k_cols_tma(ColArgs a, int ntiles,
                                                                     const __grid_constant__ CUtensorMap tmap) {
-    pdl_begin();
     constexpr int NT = cols_lanes_threads();
     constexpr int CW = cw_of(N), M = N / 2, TILE = N * CW, NCH = M / CW;
     constexpr int BOX = N > 256 ? N / 2 : N, NBOX = N / BOX; // a box holds at most 256 rows
@@ -867,7 +861,6 @@ __device__ __forceinline__ bool fft_row_lanes(float2 (&v)[16], float2* __restric
 // cleared after reading when zero_in) or float input; output rows of NRP.
 template <int N, int IN>
 __global__ void __launch_bounds__(kRowsLanesThreads, 2) k_rows_r2c_lanes(RowR2CArgs a, long long npairs) {
-    pdl_begin();
     constexpr int R1 = lanes_r1<N>(0), G = N / R1, PW = 32 / G, NRP = nrp_of(N), H = N / 2 + 1, EX = rows_lanes_ex<N>();
     static_assert(IN == ROW_IN_I64 || IN == ROW_IN_F32, "grid or float input");
     extern __shared__ float4 smem_raw[];
@@ -936,7 +929,6 @@ __global__ void __launch_bounds__(kRowsLanesThreads, 2) k_rows_r2c_lanes(RowR2CA
 // z inverse, complex -> real, times `scale`: rows of NRP in, N floats out.
 template <int N>
 __global__ void __launch_bounds__(kRowsLanesThreads, 2) k_rows_c2r_lanes(RowC2RArgs a, long long npairs) {
-    pdl_begin();
     constexpr int R1 = lanes_r1<N>(0), G = N / R1, PW = 32 / G, NRP = nrp_of(N), H = N / 2 + 1, EX = rows_lanes_ex<N>();
     static_assert(2 * H <= EX, "both half spectra fit the exchange buffer");
     extern __shared__ float4 smem_raw[];
@@ -998,7 +990,6 @@ __global__ void __launch_bounds__(kRowsLanesThreads, 2) k_rows_c2r_lanes(RowC2RA
 // z rows, complex -> real, persistent with the next block's loads in flight.
 template <int N>
 __global__ void __launch_bounds__(kThreads) k_rows_c2r(RowC2RArgs a, int nblocks) {
-    pdl_begin();
     constexpr int B = row_pairs_of(N), BP = odd_pad(B), NRP = nrp_of(N), H = N / 2 + 1;
     constexpr int TILE = B * H, PER = (TILE + kThreads - 1) / kThreads;
     extern __shared__ float4 smem_raw[];
@@ -1076,7 +1067,6 @@ template <int N> __host__ __device__ constexpr size_t rows_c2r_pl_smem_bytes() {
 
 template <int N, int IN>
 __global__ void __launch_bounds__(kThreads) k_rows_r2c_pl(RowR2CArgs a, int nblocks) {
-    pdl_begin();
     constexpr int B = row_pairs_of(N), BP = odd_pad(B), NRP = nrp_of(N), H = N / 2 + 1, S = rows_pl_stages(N);
     constexpr int E = IN == ROW_IN_I64 ? 8 : 4, R2 = 2 * B;
     constexpr int SB = (int)rows_pl_stage_bytes<N, E>(), CH = SB / 16;
@@ -1149,7 +1139,6 @@ __global__ void __launch_bounds__(kThreads) k_rows_r2c_pl(RowR2CArgs a, int nblo
 
 template <int N>
 __global__ void __launch_bounds__(kThreads) k_rows_c2r_pl(RowC2RArgs a, int nblocks) {
-    pdl_begin();
     constexpr int B = row_pairs_of(N), BP = odd_pad(B), NRP = nrp_of(N), H = N / 2 + 1, S = rows_pl_stages(N);
     constexpr int R2 = 2 * B, SE = R2 * NRP, CH = SE / 2; // stage elements, 16-byte chunks
     static_assert((N * N) % R2 == 0 && NRP % 2 == 0, "whole contiguous blocks");
@@ -1212,7 +1201,6 @@ template <int N> __host__ __device__ constexpr bool plane_ok() { return N <= 192
 
 template <int N, int IN>
 __global__ void __launch_bounds__(plane_threads_of(N)) k_plane_r2c(RowR2CArgs a) {
-    pdl_begin();
     constexpr int NT = plane_threads_of(N), H = N / 2 + 1, NRP = nrp_of(N), P = N / 2;
     constexpr int TILE = N * N, PER = (TILE + NT - 1) / NT;
     constexpr int UN = P * H, UPER = (UN + NT - 1) / NT;
@@ -1290,7 +1278,6 @@ __global__ void __launch_bounds__(plane_threads_of(N)) k_plane_r2c(RowR2CArgs a)
 
 template <int N>
 __global__ void __launch_bounds__(plane_threads_of(N)) k_plane_c2r(RowC2RArgs a) {
-    pdl_begin();
     constexpr int NT = plane_threads_of(N), H = N / 2 + 1, NRP = nrp_of(N), P = N / 2;
     constexpr int LD = N * H, LPER = (LD + NT - 1) / NT;
     constexpr int UN = P * H, UPER = (UN + NT - 1) / NT;

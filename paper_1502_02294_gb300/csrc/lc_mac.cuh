@@ -73,7 +73,6 @@ template <int N, bool BF16> struct MacCfg {
 
 template <int N, bool BF16>
 __global__ void __launch_bounds__(MacCfg<N, BF16>::NT) k_mac_tma(MacArgs a) {
-    pdl_begin();
     using C = MacCfg<N, BF16>;
     constexpr int NT = C::NT, CW = C::CW, PER = C::PER, TILE = C::TILE, BP = C::BP, S = C::STAGES;
     extern __shared__ unsigned char smem_raw2[];
@@ -388,7 +387,6 @@ __device__ __forceinline__ void ws_slot_list(const MacArgs& a, int* out_slot, in
 
 template <int N, bool BF16, bool PAIR>
 __global__ void __launch_bounds__(MacWsCfg<N, BF16, PAIR>::NT, 1) k_mac_ws(MacArgs a) {
-    pdl_begin();
     using C = MacWsCfg<N, BF16, PAIR>;
     constexpr int NT = C::NT, NC = C::NC, CW = C::CW, TILE = C::TILE, BPP = C::BPP, S = C::STAGES, M = C::M;
     constexpr int UPT = C::UPT, CG = C::CG, GROWS = C::GROWS, GPLANE = C::GPLANE, P = C::P, NCH = C::NCH;
