@@ -38,17 +38,19 @@ __global__ void __launch_bounds__(kPrepThreads)
     unsigned long long mx = 0;
     int bad = 0;
     for (long long i0 = threadIdx.x; i0 < n; i0 += 4 * kPrepThreads) {
-        double L[4];
+        unsigned long long B[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const long long i = i0 + (long long)u * kPrepThreads;
-            L[u] = i < n ? lum[i] : 0.0;
+            B[u] = i < n ? (unsigned long long)__double_as_longlong(lum[i]) : 0ULL;
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            if (!(finite_d(L[u]) && L[u] >= 0.0)) bad = 1;
+            // on the bit patterns (integer work; FP64 issue is narrow): finite
+            // and >= 0 is a clear sign bit below the infinity pattern, or -0;
             // non-negative doubles order like their bit patterns
-            else mx = max(mx, (unsigned long long)__double_as_longlong(L[u]));
+            if (B[u] < 0x7ff0000000000000ULL) mx = max(mx, B[u]);
+            else if (B[u] != 0x8000000000000000ULL) bad = 1;
         }
     }
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -66,13 +68,27 @@ __global__ void __launch_bounds__(kPrepThreads)
     }
 }
 
-__device__ __forceinline__ long long ngp_cell(double x, double l, int N) {
-    // floor(x / l + 1/2) mod N in IEEE double (fmod is exact), no contraction
-    const double t = floor(__dadd_rn(__ddiv_rn(x, l), 0.5));
-    double m = fmod(t, (double)N);
-    if (m < 0.0) m += (double)N;
-    long long i = (long long)m;
+// t mod N for an integer-valued double t, in [0, N).  Below 2^53 in
+// magnitude t converts to an integer exactly and the remainder is taken in
+// integers; beyond, by fmod (exact as well).  FP64 issues at a small fraction
+// of the FP32 rate on this GPU, and fmod is a loop of FP64 operations, so the
+// integer path matters for the deposit's throughput.
+__device__ __forceinline__ long long wrap_cell(double t, int N) {
+    long long i;
+    if (fabs(t) < 9007199254740992.0) {
+        i = (long long)t % N;
+        if (i < 0) i += N;
+    } else {
+        double m = fmod(t, (double)N);
+        if (m < 0.0) m += (double)N;
+        i = (long long)m;
+    }
     return (i >= 0 && i < N) ? i : 0;
+}
+
+__device__ __forceinline__ long long ngp_cell(double x, double l, int N) {
+    // floor(x / l + 1/2) mod N in IEEE double, no contraction
+    return wrap_cell(floor(__dadd_rn(__ddiv_rn(x, l), 0.5)), N);
 }
 
 // Cloud in cell along one axis: the cells i0 = floor(x / l) mod N and
@@ -82,10 +98,7 @@ __device__ __forceinline__ void cic_axis(double x, double l, int N, long long& i
     const double t = __ddiv_rn(x, l);
     const double fl = floor(t);
     f = __dsub_rn(t, fl);
-    double m = fmod(fl, (double)N);
-    if (m < 0.0) m += (double)N;
-    long long i = (long long)m;
-    if (i < 0 || i >= N) i = 0;
+    const long long i = wrap_cell(fl, N);
     i0 = i;
     i1 = i + 1 == N ? 0 : i + 1;
 }
@@ -106,11 +119,15 @@ __global__ void __launch_bounds__(256)
               long long* __restrict__ cell_out, long long* __restrict__ q_out, double* __restrict__ off_out) {
     __shared__ long long s_sum[8];
     const double lmax = __longlong_as_double((long long)*maxbits);
-    double S = 1.0;
+    double S = 1.0, invS = 1.0;
     if (lmax > 0.0) {
         int E;
         frexp(__dmul_rn((double)n, lmax), &E);
         S = ldexp(1.0, E - 62);
+        // L / S for a power of two S is the exact L 2^(62-E) rounded once, so
+        // the product with 1/S is the same double whenever 1/S is a normal
+        // number (E - 62 within the normal exponent range both ways)
+        invS = (E - 62 > -1022 && E - 62 < 1022) ? ldexp(1.0, 62 - E) : 0.0;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) m.slot_S[m.slot] = S;
     long long q = 0;
@@ -124,7 +141,7 @@ __global__ void __launch_bounds__(256)
             long long cx[2] = {0, 0}, cy[2] = {0, 0}, cz[2] = {0, 0};
             long long sh[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             if (ok) {
-                q = llrint(__ddiv_rn(L, S));
+                q = llrint(invS != 0.0 ? __dmul_rn(L, invS) : __ddiv_rn(L, S));
                 double fx, fy, fz;
                 cic_axis(x, l, N, cx[0], cx[1], fx);
                 cic_axis(y, l, N, cy[0], cy[1], fy);
@@ -147,7 +164,7 @@ __global__ void __launch_bounds__(256)
         } else {
             long long c = 0;
             if (ok) {
-                q = llrint(__ddiv_rn(L, S));
+                q = llrint(invS != 0.0 ? __dmul_rn(L, invS) : __ddiv_rn(L, S));
                 c = (ngp_cell(x, l, N) * N + ngp_cell(y, l, N)) * N + ngp_cell(z, l, N);
                 if (q) atomicAdd(reinterpret_cast<unsigned long long*>(grid + c), (unsigned long long)q);
             }
@@ -504,12 +521,17 @@ void launch_src_prep(const double* pos, const double* lum, long long n, unsigned
 void launch_deposit(const double* pos, const double* lum, long long n, int N, double l, int deposit,
                     const unsigned long long* maxbits, long long* grid, SlotMeta m, int* err, cudaStream_t st,
                     long long* cell_out, long long* q_out, double* off_out) {
-    const long long blocks = n > 0 ? (n + 255) / 256 : 1;
+    // one source per thread, in blocks of 32 to 256 threads chosen so that
+    // the sources spread over about two CTAs per SM: each costs a few FP64
+    // divisions, and FP64 issue per SM is narrow on this GPU
+    const long long per_cta = (n + 2 * 152 - 1) / (2 * 152);
+    const int tb = (int)(per_cta <= 32 ? 32 : per_cta >= 256 ? 256 : (per_cta + 31) / 32 * 32);
+    const long long blocks = n > 0 ? (n + tb - 1) / tb : 1;
     if (deposit == LC_DEPOSIT_CIC)
-        launch_k(k_deposit<1>, (unsigned)blocks, 256, 0, st, pos, lum, n, N, l, maxbits, grid, m, err, cell_out, q_out,
+        launch_k(k_deposit<1>, (unsigned)blocks, tb, 0, st, pos, lum, n, N, l, maxbits, grid, m, err, cell_out, q_out,
                  (double*)nullptr);
     else
-        launch_k(k_deposit<0>, (unsigned)blocks, 256, 0, st, pos, lum, n, N, l, maxbits, grid, m, err, cell_out, q_out,
+        launch_k(k_deposit<0>, (unsigned)blocks, tb, 0, st, pos, lum, n, N, l, maxbits, grid, m, err, cell_out, q_out,
                  off_out);
 }
 

@@ -175,3 +175,26 @@ def test_n_shell_max_against_oracle(cap, hist):
         else:
             assert rel <= BF16_L2, (cap, s, rel)
     plan.close()
+
+
+# ------------------------------------------------------------------ launch shapes and special values
+@pytest.mark.parametrize("n_src", [1, 31, 33, 300, 5000, 70000])
+@pytest.mark.parametrize("dep", [lc.DEPOSIT_NGP, CIC])
+def test_deposit_launch_shapes_and_special_values(n_src, dep):
+    """Sources spread over CTAs of 32 to 256 threads; a -0 luminosity (valid,
+    no effect on the fixed-point unit), coordinates far outside the box
+    (cell wrap beyond 2^53 cells), negative coordinates; bit-exact grid, unit
+    and total against the oracle."""
+    N, box = 32, 64.0
+    rng = np.random.default_rng(n_src + 7 * dep)
+    pos = rng.uniform(-2 * box, 3 * box, size=(n_src, 3))
+    lum = 10.0 ** rng.normal(0, 1.5, size=n_src)
+    lum[0] = -0.0
+    if n_src > 3:
+        pos[1] = [1e17 + 0.25, -3e18, 5.5]
+        pos[2] = [-1e-320, 2.0 * box, -0.5 * box / N]
+        lum[3] = 0.0
+    f = oracle.deposit_cic_fixed if dep == CIC else oracle.deposit_fixed
+    go, So, to = f(N, box, pos, lum)
+    g, S, t = lc.deposit_grid(N, box, pos, lum, deposit=dep)
+    assert S == So and t == to and np.array_equal(g, go)
