@@ -202,9 +202,11 @@ lc_status lc_retarded_field_async(lc_plan* plan, int step, float* out, uint64_t*
 lc_status lc_plan_wait(lc_plan* plan, uint64_t ticket);
 
 /* lc_plan_wait without blocking: *done = 1 if the output named by `ticket`
- * is in host memory (ticket 0: the plan's stream is idle), else 0.  A ticket
- * whose stage a later ticket has reused reports done once that later copy
- * has finished too (never early).  Same errors as lc_plan_wait. */
+ * is in host memory (ticket 0: the plan's stream is idle), else 0.  Each
+ * ticket has its own completion event for the next 16 tickets; a ticket
+ * older than that reports done once a later copy has finished (copies of a
+ * plan complete in ticket order; never early).  Same errors as
+ * lc_plan_wait. */
 lc_status lc_plan_poll(lc_plan* plan, uint64_t ticket, int* done);
 
 /* The same field computed "instantaneously" (action at a distance, Eq. 18 of

@@ -252,6 +252,12 @@ struct lc_plan {
     cudaEvent_t ev_computed[2] = {nullptr, nullptr}, ev_copied[2] = {nullptr, nullptr};
     uint64_t tickets = 0;              // tickets issued; ticket t used stage (t - 1) % 2
     uint64_t stage_ticket[2] = {0, 0}; // the last ticket of each stage
+    // completion of each ticket's copy: its own event (a ring of kTicketEvents,
+    // re-recorded only kTicketEvents tickets later), and the highest ticket
+    // known complete (copies complete in ticket order on the one copy stream)
+    static constexpr int kTicketEvents = 16;
+    cudaEvent_t ev_ticket[kTicketEvents] = {};
+    uint64_t done_upto = 0;
     // Green's function tables, one per observing step (built lazily)
     long long ring_slot = 0; // complex elements per tile-major ring slot: N^2 (N/2 + 1)
     struct Table {
@@ -442,6 +448,8 @@ void free_all(lc_plan* p) {
         if (p->ev_computed[k]) cudaEventDestroy(p->ev_computed[k]);
         if (p->ev_copied[k]) cudaEventDestroy(p->ev_copied[k]);
     }
+    for (auto& ev : p->ev_ticket)
+        if (ev) cudaEventDestroy(ev);
     if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
     cudaFree(p->d_gw);
     cudaFree(p->d_gtab);
@@ -667,6 +675,20 @@ void fft_step_passes(lc_plan* p, cudaStream_t st) {
     r.zero_in = 1;
     r.dst = p->d_work;
     r.tw = p->d_tw;
+    if (p->ops->plane_r2c) {
+        // grids with plane kernels: only the z + y passes depend on the form
+        r.zero_in = 0;
+        p->ops->plane_r2c(r, st);
+        RowC2RArgs rc{};
+        rc.nrows = N * N;
+        rc.src = p->d_work;
+        rc.out = reinterpret_cast<float*>(p->d_grid);
+        rc.scale = 1.0f;
+        rc.tw = p->d_tw;
+        p->ops->plane_c2r(rc, st);
+        count_launch(2);
+        return;
+    }
     p->ops->rows_r2c(r, st);
     ColArgs c{};
     c.axis = 0;
@@ -1320,11 +1342,13 @@ lc_status lc_plan_wait(lc_plan* p, uint64_t ticket) {
     cudaError_t e;
     if (ticket == 0) {
         e = cudaStreamSynchronize(p->stream);
+    } else if (ticket <= p->done_upto) {
+        return LC_OK;
     } else {
-        // a stage re-used by a later ticket has an event that completes later
-        // still: waiting on it is correct, only later than needed
-        const int k = (int)((ticket - 1) % 2);
-        e = cudaEventSynchronize(p->ev_copied[k]);
+        // the ticket's own event; once kTicketEvents later tickets have been
+        // issued it stands for a later copy, which completes after this one
+        e = cudaEventSynchronize(p->ev_ticket[(ticket - 1) % lc_plan::kTicketEvents]);
+        if (e == cudaSuccess && ticket > p->done_upto) p->done_upto = ticket;
     }
     return e == cudaSuccess ? LC_OK : cuda_fail(p, e);
 }
@@ -1335,8 +1359,10 @@ lc_status lc_plan_poll(lc_plan* p, uint64_t ticket, int* done) {
     *done = 0;
     cudaError_t e;
     if (ticket == 0) e = cudaStreamQuery(p->stream);
-    else e = cudaEventQuery(p->ev_copied[(ticket - 1) % 2]);
+    else if (ticket <= p->done_upto) e = cudaSuccess;
+    else e = cudaEventQuery(p->ev_ticket[(ticket - 1) % lc_plan::kTicketEvents]);
     if (e == cudaSuccess) {
+        if (ticket > p->done_upto) p->done_upto = ticket;
         *done = 1;
         return LC_OK;
     }
@@ -1358,6 +1384,8 @@ static cudaError_t async_stage(lc_plan* p, int& k) {
         if (!p->ev_computed[i]) e = cudaEventCreateWithFlags(&p->ev_computed[i], cudaEventDisableTiming);
         if (e == cudaSuccess && !p->ev_copied[i]) e = cudaEventCreateWithFlags(&p->ev_copied[i], cudaEventDisableTiming);
     }
+    for (int i = 0; i < lc_plan::kTicketEvents && e == cudaSuccess; ++i)
+        if (!p->ev_ticket[i]) e = cudaEventCreateWithFlags(&p->ev_ticket[i], cudaEventDisableTiming);
     if (e == cudaSuccess && !p->d_out_async[k]) e = dalloc(p, &p->d_out_async[k], (size_t)N3);
     if (e == cudaSuccess && p->stage_ticket[k]) e = cudaStreamWaitEvent(p->stream, p->ev_copied[k], 0);
     return e;
@@ -1511,6 +1539,8 @@ static lc_status field_impl(lc_plan* p, int step, float* out, int instant, uint6
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(out, dout, sizeof(float) * N3, cudaMemcpyDeviceToHost, p->copy_stream);
         if (e == cudaSuccess) e = cudaEventRecord(p->ev_copied[stage], p->copy_stream);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(p->ev_ticket[p->tickets % lc_plan::kTicketEvents], p->copy_stream);
         if (e == cudaSuccess) {
             *ticket = ++p->tickets;
             p->stage_ticket[stage] = *ticket;

@@ -1335,6 +1335,259 @@ __global__ void __launch_bounds__(plane_threads_of(N)) k_plane_c2r(RowC2RArgs a)
 }
 
 // ------------------------------------------------------------------------
+// Plane kernels with the transforms in registers (N = R1 G: R1 = 16, or 12
+// at N = 96 and 192).  A length-N transform is an R1-point DFT per residue
+// q < G over x[q + G p], the twiddle W_N^(q k1), and a G-point DFT per k1
+// over q, giving X[k1 + R1 k2].  Forward, z: a group of G lanes takes one
+// pair of z rows straight from global memory (lane q holds z[q + G p]),
+// exchanges once between the two stages through the pair's own two rows of
+// the plane buffer, unpacks the two real rows' half spectra there and
+// writes them as rows 2u, 2u + 1 of the plane [y][k] (row stride PS).  y:
+// item (column c, residue q) runs the first stage in place on rows q + G p;
+// after one barrier item (c, k1) runs the second and writes Y[k1 + R1 k2]
+// straight to global memory.  This moves about a third of the shared-memory
+// bytes of the staged plane kernels (no staging of the input, no
+// Stockham stage round trips).
+template <int N> __host__ __device__ constexpr bool plane_lanes_ok() {
+    return N == 32 || N == 64 || N == 96 || N == 128 || N == 192;
+}
+template <int N> __host__ __device__ constexpr int plane_lanes_r1() { return (N == 96 || N == 192) ? 12 : 16; }
+template <int N> __host__ __device__ constexpr int plane_lanes_threads() {
+    return N == 32 ? 288 : (N == 64 || N == 128) ? 544 : 608;
+}
+// Row stride (float2): at least H, room for a pair's exchange in two rows
+// (R1 (G + 1) skewed, or Z in natural order, N + 2), and 4 mod 8, so that
+// the unpack stores of a warp's lane groups (rows 2 PS apart) fall on
+// distinct bank pairs.
+template <int N> __host__ __device__ constexpr int plane_lanes_ps() {
+    constexpr int R1 = plane_lanes_r1<N>(), G = N / R1, H = N / 2 + 1;
+    constexpr int EX = R1 * (G + 1) > N + 2 ? R1 * (G + 1) : N + 2;
+    constexpr int NEED = H > (EX + 1) / 2 ? H : (EX + 1) / 2;
+    return NEED + ((12 - NEED % 8) % 8);
+}
+template <int N> __host__ __device__ constexpr size_t plane_lanes_smem_bytes() {
+    return sizeof(float2) * ((size_t)N + (size_t)N * plane_lanes_ps<N>());
+}
+
+template <int N, int IN>
+__global__ void __launch_bounds__(plane_lanes_threads<N>()) k_plane_r2c_lanes(RowR2CArgs a) {
+    constexpr int NT = plane_lanes_threads<N>(), R1 = plane_lanes_r1<N>(), G = N / R1, XS = G + 1;
+    constexpr int H = N / 2 + 1, NRP = nrp_of(N), P = N / 2, PS = plane_lanes_ps<N>(), PW = 32 / G;
+    constexpr int J = (R1 + G - 1) / G, M = (H + G - 1) / G;
+    static_assert(IN == ROW_IN_I64 || IN == ROW_IN_F32, "grid or float input");
+    static_assert(P % PW == 0 && 32 % G == 0, "whole lane groups");
+    extern __shared__ float4 smem_raw[];
+    float2* tw = reinterpret_cast<float2*>(smem_raw);
+    float2* pl = tw + N;
+    const int x = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane / G, q = lane % G;
+    for (int i = threadIdx.x; i < N; i += NT) tw[i] = a.tw[i];
+    float scale = 1.0f;
+    if constexpr (IN == ROW_IN_I64) {
+        const double S = a.slot_S[a.slot];
+        const long long tot = a.slot_total[a.slot];
+        scale = a.bf16 ? (tot > 0 ? (float)(1.0 / (double)tot) : 0.0f) : (float)S;
+    }
+    __syncthreads();
+    for (int u0 = warp * PW; u0 < P; u0 += (NT / 32) * PW) {
+        const int u = u0 + grp;
+        float2* ex = pl + (2 * u) * PS; // this pair's two rows
+        const long long ra = ((long long)x * N + 2 * u) * N, rb = ra + N;
+        float2 v[16];
+        if constexpr (IN == ROW_IN_I64) {
+            long long xa[R1], xb[R1];
+#pragma unroll
+            for (int p = 0; p < R1; ++p) {
+                xa[p] = a.grid[ra + q + G * p];
+                xb[p] = a.grid[rb + q + G * p];
+            }
+#pragma unroll
+            for (int p = 0; p < R1; ++p) v[p] = make_float2(__ll2float_rn(xa[p]) * scale, __ll2float_rn(xb[p]) * scale);
+        } else {
+#pragma unroll
+            for (int p = 0; p < R1; ++p) v[p] = make_float2(a.fin[ra + q + G * p], a.fin[rb + q + G * p]);
+        }
+        dft<R1, -1>(v);
+#pragma unroll
+        for (int k1 = 1; k1 < R1; ++k1) v[k1] = cmul(v[k1], tw[q * k1]);
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) ex[k1 * XS + q] = v[k1];
+        __syncwarp();
+        float2 z[J * G];
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const int k1 = q + G * j;
+            if (k1 < R1) {
+                float2 w[G];
+#pragma unroll
+                for (int r = 0; r < G; ++r) w[r] = ex[k1 * XS + r];
+                dft<G, -1>(w);
+#pragma unroll
+                for (int k2 = 0; k2 < G; ++k2) z[j * G + k2] = w[k2];
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const int k1 = q + G * j;
+            if (k1 < R1) {
+#pragma unroll
+                for (int k2 = 0; k2 < G; ++k2) ex[k1 + R1 * k2] = z[j * G + k2]; // Z in natural order
+            }
+        }
+        __syncwarp();
+        // X_a = (Z_k + conj Z_{N-k}) / 2, X_b = (Z_k - conj Z_{N-k}) / (2 i)
+        float2 ua[M], ub[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const int k = q + G * m;
+            if (k < H) {
+                const float2 zk = ex[k], zn = ex[k == 0 ? 0 : N - k];
+                ua[m] = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
+                ub[m] = make_float2(0.5f * (zk.y + zn.y), 0.5f * (zn.x - zk.x));
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const int k = q + G * m;
+            if (k < H) {
+                ex[k] = ua[m];      // row 2u
+                ex[PS + k] = ub[m]; // row 2u + 1
+            }
+        }
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < H * G; it += NT) {
+        const int c = it % H, r = it / H;
+        float2 v[16];
+#pragma unroll
+        for (int p = 0; p < R1; ++p) v[p] = pl[(r + G * p) * PS + c];
+        dft<R1, -1>(v);
+#pragma unroll
+        for (int k1 = 1; k1 < R1; ++k1) v[k1] = cmul(v[k1], tw[r * k1]);
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) pl[(k1 * G + r) * PS + c] = v[k1]; // the rows it read
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < H * R1; it += NT) {
+        const int c = it % H, k1 = it / H;
+        float2 w[G];
+#pragma unroll
+        for (int r = 0; r < G; ++r) w[r] = pl[(k1 * G + r) * PS + c];
+        dft<G, -1>(w);
+#pragma unroll
+        for (int k2 = 0; k2 < G; ++k2) a.dst[((long long)x * N + (k1 + R1 * k2)) * NRP + c] = w[k2];
+    }
+}
+
+// Inverse of k_plane_r2c_lanes for one x-plane: y inverse with item (c, r)
+// taking its R1 inputs straight from global memory, the second stage in
+// place (its outputs Y[k1 + R1 k2] land on the rows k1 G + k2 it read, so
+// no item overwrites another's input), then the z inverse per row pair
+// (real rows 2u, 2u + 1 as one complex transform, Hermitian-extended), the
+// pair's exchange on the two plane rows that held its input, and the
+// results (times `scale`) written from registers.
+template <int N>
+__global__ void __launch_bounds__(plane_lanes_threads<N>()) k_plane_c2r_lanes(RowC2RArgs a) {
+    constexpr int NT = plane_lanes_threads<N>(), R1 = plane_lanes_r1<N>(), G = N / R1, XS = G + 1;
+    constexpr int H = N / 2 + 1, NRP = nrp_of(N), P = N / 2, PS = plane_lanes_ps<N>(), PW = 32 / G;
+    constexpr int J = (R1 + G - 1) / G;
+    static_assert(P % PW == 0 && 32 % G == 0, "whole lane groups");
+    extern __shared__ float4 smem_raw[];
+    float2* tw = reinterpret_cast<float2*>(smem_raw);
+    float2* pl = tw + N;
+    const int x = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane / G, q = lane % G;
+    for (int i = threadIdx.x; i < N; i += NT) tw[i] = a.tw[i];
+    __syncthreads();
+    for (int it = threadIdx.x; it < H * G; it += NT) {
+        const int c = it % H, r = it / H;
+        float2 v[16];
+#pragma unroll
+        for (int p = 0; p < R1; ++p) v[p] = a.src[((long long)x * N + (r + G * p)) * NRP + c];
+        dft<R1, 1>(v);
+#pragma unroll
+        for (int k1 = 1; k1 < R1; ++k1) {
+            float2 w = tw[r * k1];
+            w.y = -w.y;
+            v[k1] = cmul(v[k1], w);
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) pl[(k1 * G + r) * PS + c] = v[k1];
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < H * R1; it += NT) {
+        const int c = it % H, k1 = it / H;
+        float2 w[G];
+#pragma unroll
+        for (int r = 0; r < G; ++r) w[r] = pl[(k1 * G + r) * PS + c];
+        dft<G, 1>(w);
+#pragma unroll
+        for (int k2 = 0; k2 < G; ++k2) pl[(k1 * G + k2) * PS + c] = w[k2]; // Y[k1 + R1 k2]
+    }
+    __syncthreads();
+    for (int u0 = warp * PW; u0 < P; u0 += (NT / 32) * PW) {
+        const int u = u0 + grp;
+        // the plane rows of y = 2u and 2u + 1
+        float2* xa = pl + (((2 * u) % R1) * G + (2 * u) / R1) * PS;
+        float2* xb = pl + (((2 * u + 1) % R1) * G + (2 * u + 1) / R1) * PS;
+        // Z_n = X_a(n) + i X_b(n), with X(N - n) = conj X(n) beyond N/2
+        float2 v[16];
+#pragma unroll
+        for (int p = 0; p < R1; ++p) {
+            const int n = q + G * p;
+            if (n < H) {
+                float2 A = xa[n], B = xb[n];
+                if (n == 0 || n == N / 2) {
+                    A.y = 0.f;
+                    B.y = 0.f;
+                }
+                v[p] = make_float2(A.x - B.y, A.y + B.x);
+            } else {
+                const float2 A = xa[N - n], B = xb[N - n];
+                v[p] = make_float2(A.x + B.y, B.x - A.y);
+            }
+        }
+        __syncwarp(); // every lane of the group has read the pair's rows
+        dft<R1, 1>(v);
+#pragma unroll
+        for (int k1 = 1; k1 < R1; ++k1) {
+            float2 w = tw[q * k1];
+            w.y = -w.y;
+            v[k1] = cmul(v[k1], w);
+        }
+        // exchange on the pair's two rows: element e at xa[e] (e < PS) or xb[e - PS]
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) {
+            const int e = k1 * XS + q;
+            (e < PS ? xa[e] : xb[e - PS]) = v[k1];
+        }
+        __syncwarp();
+        float* oa = a.out + ((long long)x * N + 2 * u) * N;
+        float* ob = oa + N;
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const int k1 = q + G * j;
+            if (k1 < R1) {
+                float2 w[G];
+#pragma unroll
+                for (int r = 0; r < G; ++r) {
+                    const int e = k1 * XS + r;
+                    w[r] = e < PS ? xa[e] : xb[e - PS];
+                }
+                dft<G, 1>(w);
+#pragma unroll
+                for (int k2 = 0; k2 < G; ++k2) {
+                    oa[k1 + R1 * k2] = w[k2].x * a.scale;
+                    ob[k1 + R1 * k2] = w[k2].y * a.scale;
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------
 // Host-side launchers for one N.
 struct MacArgs;
 struct FftOps {
@@ -1404,15 +1657,18 @@ template <int N> struct Launch {
     }
     static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
     // the column-pass variant in use (FFT_COLS_*)
+    // (grids with plane kernels: FFT_COLS_STAGES = the staged plane kernels,
+    // FFT_COLS_LANES = k_plane_r2c_lanes / k_plane_c2r_lanes)
     static int& variant() {
-        static int v = cols_lanes_ok<N>() ? FFT_COLS_LANES : FFT_COLS_STAGES;
+        static int v = (cols_lanes_ok<N>() || plane_lanes_ok<N>()) ? FFT_COLS_LANES : FFT_COLS_STAGES;
         return v;
     }
     static int variants_built() {
         return (1 << FFT_COLS_STAGES) |
                (cols_lanes_ok<N>()
                     ? (1 << FFT_COLS_LANES) | (1 << FFT_COLS_LANES3) | (1 << FFT_COLS_TMA) | (1 << FFT_COLS_TMA4)
-                    : 0);
+                    : 0) |
+               (plane_lanes_ok<N>() ? (1 << FFT_COLS_LANES) : 0);
     }
     static void set_variant(int v) {
         if (v >= 0 && v < FFT_NVAR && (variants_built() >> v & 1)) variant() = v;
@@ -1555,6 +1811,12 @@ template <int N> struct Launch {
             LC_ATTR((k_plane_r2c<N, ROW_IN_WEDGE>), ps);
             LC_ATTR((k_plane_c2r<N>), ps);
         }
+        if constexpr (plane_lanes_ok<N>()) {
+            const int pls = (int)plane_lanes_smem_bytes<N>();
+            LC_ATTR((k_plane_r2c_lanes<N, ROW_IN_I64>), pls);
+            LC_ATTR((k_plane_r2c_lanes<N, ROW_IN_F32>), pls);
+            LC_ATTR((k_plane_c2r_lanes<N>), pls);
+        }
 #undef LC_ATTR
         return e;
     }
@@ -1562,13 +1824,30 @@ template <int N> struct Launch {
         if constexpr (plane_ok<N>()) {
             const size_t sm = plane_smem_bytes<N>();
             constexpr int NT = plane_threads_of(N);
+            if constexpr (plane_lanes_ok<N>()) {
+                if (lanes_form() && a.in_mode != ROW_IN_WEDGE) {
+                    constexpr int NL = plane_lanes_threads<N>();
+                    const size_t sl = plane_lanes_smem_bytes<N>();
+                    if (a.in_mode == ROW_IN_I64) launch_k(k_plane_r2c_lanes<N, ROW_IN_I64>, N, NL, sl, st, a);
+                    else launch_k(k_plane_r2c_lanes<N, ROW_IN_F32>, N, NL, sl, st, a);
+                    return;
+                }
+            }
             if (a.in_mode == ROW_IN_I64) launch_k(k_plane_r2c<N, ROW_IN_I64>, N, NT, sm, st, a);
             else if (a.in_mode == ROW_IN_F32) launch_k(k_plane_r2c<N, ROW_IN_F32>, N, NT, sm, st, a);
             else launch_k(k_plane_r2c<N, ROW_IN_WEDGE>, N, NT, sm, st, a);
         }
     }
     static void plane_c2r(const RowC2RArgs& a, cudaStream_t st) {
-        if constexpr (plane_ok<N>()) launch_k(k_plane_c2r<N>, N, plane_threads_of(N), plane_smem_bytes<N>(), st, a);
+        if constexpr (plane_ok<N>()) {
+            if constexpr (plane_lanes_ok<N>()) {
+                if (lanes_form()) {
+                    launch_k(k_plane_c2r_lanes<N>, N, plane_lanes_threads<N>(), plane_lanes_smem_bytes<N>(), st, a);
+                    return;
+                }
+            }
+            launch_k(k_plane_c2r<N>, N, plane_threads_of(N), plane_smem_bytes<N>(), st, a);
+        }
     }
     static constexpr bool kRowsPl = N >= 256;
     template <class Kern> static int occ_ctas(Kern k, size_t smem) {

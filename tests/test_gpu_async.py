@@ -2,6 +2,8 @@
 and its device-to-host copy are enqueued, the copy overlapping the next
 steps; lc_plan_wait makes the output readable.  Fields equal the waiting
 call's, with pinned and pageable host buffers, across stage reuse."""
+import time
+
 import numpy as np
 import pytest
 
@@ -103,5 +105,40 @@ def test_page_locked_host_inputs():
         with pytest.raises(lc.LCError) as e:
             b.push(0, torch.from_numpy(w.cat.active(3)[0]).pin_memory(), bad)
         assert e.value.status == lc.LC_ERR_INVALID_ARG
+    a.close()
+    b.close()
+
+
+def test_poll_completes_each_ticket_in_order_over_many_tickets():
+    # more tickets than the stages and than the per-ticket event ring: each
+    # ticket reports done once its own copy has finished, completions are
+    # monotone in ticket order, and every output equals the waiting call's
+    w = synth.small(n=64, box=90.0, n_steps=24, n_src=200, seed=2720, clustered=True)
+    a = lc.Plan.from_workload(w)
+    b = lc.Plan.from_workload(w)
+    nbuf = 5
+    pinned = [torch.empty((w.n,) * 3, dtype=torch.float32).pin_memory() for _ in range(nbuf)]
+    tickets, want = [], []
+    for s in range(24):
+        pos, lum = w.cat.active(s)
+        a.push(s, pos, lum)
+        want.append(a.field(s, np.empty((w.n,) * 3, dtype=np.float32)))
+        if s >= nbuf:  # the buffer is free again once its ticket is done
+            t_end = time.monotonic() + 60.0
+            while not b.poll(tickets[s - nbuf]):
+                assert time.monotonic() < t_end, "ticket never completed"
+            got = pinned[(s - nbuf) % nbuf].numpy()
+            ref = want[s - nbuf]
+            assert np.allclose(got, ref, rtol=1e-6, atol=1e-6 * np.abs(ref).max()), s - nbuf
+        b.push(s, pos, lum)
+        tickets.append(b.field_async(s, pinned[s % nbuf]))
+        # newest first: a ticket seen done implies every earlier ticket done
+        done = [b.poll(t) for t in reversed(tickets)][::-1]
+        assert all(done[i] or not done[i + 1] for i in range(len(done) - 1)), done
+    b.wait(tickets[-1])
+    assert all(b.poll(t) for t in tickets)
+    for s in range(24 - nbuf, 24):
+        ref = want[s]
+        assert np.allclose(pinned[s % nbuf].numpy(), ref, rtol=1e-6, atol=1e-6 * np.abs(ref).max()), s
     a.close()
     b.close()

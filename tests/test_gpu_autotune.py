@@ -178,3 +178,61 @@ def test_fft_pass_forms_give_oracle_fields():
             assert rel <= FP32_L2, (v, rel)
     finally:
         lc.fft_set_variant(256, before)
+
+
+@pytest.mark.parametrize("n", [16, 32, 64, 96, 128, 192])
+def test_plane_forms_against_numpy_and_each_other(n):
+    # grids with plane kernels (z + y per x-plane in shared memory): the
+    # staged plane kernels and the register (lanes) ones against numpy's FP64
+    # transform, and the round trip; 16^3 has the staged form only
+    before = lc.fft_variant(n)
+    rng = np.random.default_rng(n + 11)
+    x = rng.standard_normal((n, n, n)).astype(np.float32)
+    x[3, 5, 7] += 50.0  # a bright cell, so the spectrum is not flat
+    xt = torch.from_numpy(x).cuda()
+    ref = np.fft.rfftn(x.astype(np.float64))
+    forms = [lc.FFT_STAGES] + ([lc.FFT_LANES] if n >= 32 else [])
+    res = {}
+    try:
+        for v in forms:
+            lc.fft_set_variant(n, v)
+            assert lc.fft_variant(n) == v
+            X = lc.fft_r2c(xt)
+            Xn = X.cpu().numpy().astype(np.complex128)
+            err = np.linalg.norm(Xn - ref) / np.linalg.norm(ref)
+            assert err < 2e-6, (v, err)
+            back = lc.fft_c2r(X).cpu().numpy()
+            assert np.abs(back - x).max() < 1e-5 * np.abs(x).max(), v
+            # the inverse on a spectrum with non-Hermitian DC / Nyquist imaginary parts ignores them
+            Y = X.clone()
+            Y[0, 0, 0] += 3j
+            Y[0, 0, n // 2] += 2j
+            back2 = lc.fft_c2r(Y).cpu().numpy()
+            assert np.abs(back2 - x).max() < 1e-5 * np.abs(x).max(), v
+            res[v] = Xn
+    finally:
+        if before >= 0:
+            lc.fft_set_variant(n, before)
+    if len(forms) == 2:
+        d = np.linalg.norm(res[lc.FFT_STAGES] - res[lc.FFT_LANES]) / np.linalg.norm(ref)
+        assert d < 2e-6, d
+
+
+@pytest.mark.parametrize("n,hist", [(64, synth.HISTORY_FP32), (128, synth.HISTORY_FP32), (96, synth.HISTORY_BF16),
+                                    (192, synth.HISTORY_BF16)])
+def test_plane_forms_give_oracle_fields(n, hist):
+    w = synth.small(n=n, box=0.78125 * n, n_steps=6, n_src=250, subsamples=2, clustered=True, seed=1900 + n,
+                    history=hist)
+    P = oracle.Problem.from_workload(w)
+    cells = synth.sample_cells(1901 + n, w.n, 2000)
+    ref = oracle.field_for(P, w.cat, 5, cells=cells)
+    before = lc.fft_variant(n)
+    got = {}
+    try:
+        for v in (lc.FFT_STAGES, lc.FFT_LANES):
+            lc.fft_set_variant(n, v)
+            got[v] = _fields(w, range(6), {5})[5].reshape(-1)[cells].astype(np.float64)
+            rel = np.linalg.norm(got[v] - ref) / np.linalg.norm(ref)
+            assert rel <= (FP32_L2 if hist == synth.HISTORY_FP32 else BF16_L2), (v, rel)
+    finally:
+        lc.fft_set_variant(n, before)
