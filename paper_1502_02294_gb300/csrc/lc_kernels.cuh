@@ -290,13 +290,11 @@ __global__ void __launch_bounds__(col_threads_of(N)) k_cols(ColArgs a) {
         const int nv = s_nv;
         const long long tbase = (long long)tile * a.n_ring * TILE;
         // shells outer, the tile's elements inner: PER independent ring loads
-        // (and Ghat loads) in flight per thread per shell
-        for (int v = 0; v < nv; ++v) {
+        // (and Ghat loads) in flight per thread per shell, and the next
+        // shell's loads issued before this shell's FMAs (same order of sums)
+        auto fetch = [&](int v, float2 (&f)[PER], float (&gv)[PER]) {
             const long long off = s_off[v];
             const int jv = s_j[v];
-            const float D = s_D[v];
-            float2 f[PER];
-            float gv[PER];
 #pragma unroll
             for (int i = 0; i < PER; ++i) {
                 if (TILE % NT == 0 || threadIdx.x + i * NT < TILE) {
@@ -304,13 +302,28 @@ __global__ void __launch_bounds__(col_threads_of(N)) k_cols(ColArgs a) {
                     if constexpr (IN == COL_IN_MAC_F32) f[i] = reinterpret_cast<const float2*>(a.ring)[ri];
                     else f[i] = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(a.ring)[ri]);
                     gv[i] = __ldg(g[i] + jv);
+                } else {
+                    f[i] = make_float2(0.f, 0.f);
+                    gv[i] = 0.f;
                 }
             }
+        };
+        float2 f[PER], fn[PER];
+        float gv[PER], gn[PER];
+        if (nv > 0) fetch(0, f, gv);
+        for (int v = 0; v < nv; ++v) {
+            if (v + 1 < nv) fetch(v + 1, fn, gn);
+            const float D = s_D[v];
 #pragma unroll
             for (int i = 0; i < PER; ++i) {
                 const float w = gv[i] * D;
                 val[i].x = fmaf(w, f[i].x, val[i].x);
                 val[i].y = fmaf(w, f[i].y, val[i].y);
+            }
+#pragma unroll
+            for (int i = 0; i < PER; ++i) {
+                f[i] = fn[i];
+                gv[i] = gn[i];
             }
         }
         if (dc_tile && threadIdx.x == 0) val[0] = make_float2((float)s_dc, 0.0f);
