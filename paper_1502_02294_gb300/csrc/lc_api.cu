@@ -1545,8 +1545,22 @@ static lc_status field_impl(lc_plan* p, int step, float* out, int instant, uint6
         // run meanwhile on the plan's stream
         e = cudaEventRecord(p->ev_computed[stage], st);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(p->copy_stream, p->ev_computed[stage], 0);
-        if (e == cudaSuccess)
+        // LC_D2H=sm: the copy is a kernel on the copy stream writing through
+        // the page-locked buffer's device view (SM stores over the host
+        // link), else a copy-engine transfer
+        static const bool sm_copy = [] {
+            const char* v = getenv("LC_D2H");
+            return v && !strcmp(v, "sm");
+        }();
+        void* hv = sm_copy ? pinned_device_view(out) : nullptr;
+        if (e == cudaSuccess && hv && (reinterpret_cast<uintptr_t>(hv) & 15) == 0) {
+            launch_copy_out(N3 / 4, reinterpret_cast<const float4*>(dout), reinterpret_cast<float4*>(hv),
+                            sm_count(), p->copy_stream);
+            count_launch(1);
+            e = cudaGetLastError();
+        } else if (e == cudaSuccess) {
             e = cudaMemcpyAsync(out, dout, sizeof(float) * N3, cudaMemcpyDeviceToHost, p->copy_stream);
+        }
         if (e == cudaSuccess) e = cudaEventRecord(p->ev_copied[stage], p->copy_stream);
         if (e == cudaSuccess)
             e = cudaEventRecord(p->ev_ticket[p->tickets % lc_plan::kTicketEvents], p->copy_stream);
