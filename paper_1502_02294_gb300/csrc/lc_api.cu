@@ -240,7 +240,6 @@ struct lc_plan {
     float2* d_tw = nullptr;
     ColsMaps maps; // tensor maps of d_work for the TMA column passes
     int* d_err = nullptr;
-    unsigned* d_bar = nullptr; // grid-barrier counter pair of the cooperative near kernel
     unsigned long long* d_maxbits = nullptr;
     double* d_pos = nullptr;
     double* d_lum = nullptr;
@@ -439,7 +438,6 @@ void free_all(lc_plan* p) {
     cudaFree(p->d_slot_total);
     cudaFree(p->d_tw);
     cudaFree(p->d_err);
-    cudaFree(p->d_bar);
     cudaFree(p->d_maxbits);
     cudaFree(p->d_pos);
     cudaFree(p->d_lum);
@@ -1166,8 +1164,7 @@ lc_status lc_plan_create(int n, double box_mpc, const lc_cosmology* cosmo, const
               dalloc(p, (char**)&p->d_ring, hb * (size_t)p->ring_slot * p->n_ring) == cudaSuccess &&
               dalloc(p, &p->d_slot_step, p->n_ring) == cudaSuccess && dalloc(p, &p->d_slot_S, p->n_ring) == cudaSuccess &&
               dalloc(p, &p->d_slot_total, p->n_ring) == cudaSuccess && dalloc(p, &p->d_tw, n) == cudaSuccess &&
-              dalloc(p, &p->d_err, 1) == cudaSuccess && dalloc(p, &p->d_maxbits, 1) == cudaSuccess &&
-              dalloc(p, &p->d_bar, 2) == cudaSuccess;
+              dalloc(p, &p->d_err, 1) == cudaSuccess && dalloc(p, &p->d_maxbits, 1) == cudaSuccess;
     if (!ok) {
         free_all(p);
         delete p;
@@ -1189,7 +1186,6 @@ lc_status lc_plan_create(int n, double box_mpc, const lc_cosmology* cosmo, const
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_slot_total, 0, sizeof(long long) * p->n_ring, p->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_slot_S, 0, sizeof(double) * p->n_ring, p->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_err, 0, sizeof(int), p->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_bar, 0, 2 * sizeof(unsigned), p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) {
         free_all(p);
@@ -1487,13 +1483,8 @@ static lc_status field_impl(lc_plan* p, int step, float* out, int instant, uint6
         }
         if (p->near_on && p->near_n > 0) {
             // innermost shell's near cube, summed exactly in FP64 and folded in
-            // scatter + fold in one cooperative launch where the list is small
-            const int fused = p->near_pm ? 0 : near_fused_ctas(p->near_n);
-            Phase ph(p, LC_PHASE_NEAR, fused ? 1 : 2);
-            if (fused) {
-                launch_near_fused(p->d_src_cell, p->d_src_q, p->near_n, p->N, T.gnear, p->d_slot_S, nslot, p->U,
-                                  p->d_near, dout, p->d_grid, p->d_bar, p->d_err, fused, st);
-            } else if (p->near_pm) {
+            Phase ph(p, LC_PHASE_NEAR, 2);
+            if (p->near_pm) {
                 NearPmArgs na{};
                 na.cell = p->d_src_cell;
                 na.q = p->d_src_q;
@@ -1530,7 +1521,7 @@ static lc_status field_impl(lc_plan* p, int step, float* out, int instant, uint6
                 launch_near_scatter(p->d_src_cell, p->d_src_q, p->near_n, p->N, T.gnear, p->d_slot_S, nslot, p->U,
                                     p->d_near, st);
             }
-            if (!fused) launch_near_fold(p->d_src_cell, p->d_src_q, p->near_n, p->N, p->d_near, dout, p->d_grid, st);
+            launch_near_fold(p->d_src_cell, p->d_src_q, p->near_n, p->N, p->d_near, dout, p->d_grid, st);
             p->grid_dirty = false; // the fold cleared the deposit cells
         }
         e = cudaGetLastError();
@@ -1738,7 +1729,6 @@ lc_status lc_plan_check(lc_plan* p) {
     if (e != cudaSuccess) return cuda_fail(p, e);
     if (err) {
         cudaMemset(p->d_err, 0, sizeof(int));
-        if (err & 16) cudaMemset(p->d_bar, 0, 2 * sizeof(unsigned)); // a barrier gave up: restart its count
         return LC_ERR_DEVICE_CHECK;
     }
     return LC_OK;

@@ -360,74 +360,6 @@ __global__ void __launch_bounds__(256) k_near_fold(const long long* __restrict__
     if (v != 0.0) out[t] = (float)((double)out[t] + v);
 }
 
-// Grid-wide barrier of a cooperative launch (every CTA resident), for thread
-// 0 of each CTA after a __syncthreads: bar[0] counts arrivals, bar[1] is the
-// generation the last arrival advances (it also resets the count for the
-// next launch).  The wait is bounded: about 2^22 polls, then 0 is returned.
-__device__ __forceinline__ int grid_barrier(unsigned* bar, unsigned nblocks) {
-    volatile unsigned* vb = bar;
-    const unsigned gen = vb[1];
-    __threadfence();
-    if (atomicAdd(&bar[0], 1u) == nblocks - 1) {
-        atomicExch(&bar[0], 0u);
-        __threadfence();
-        atomicAdd(&bar[1], 1u);
-        return 1;
-    }
-    for (int i = 0; i < (1 << 22); ++i) {
-        if (vb[1] != gen) {
-            __threadfence();
-            return 1;
-        }
-        __nanosleep(64);
-    }
-    return 0;
-}
-
-// The near field of the innermost shell in one cooperative launch: the
-// scatter of k_near_scatter, a grid-wide barrier, the fold of k_near_fold,
-// each over the (entry, cube cell) pairs in grid-stride loops.  Same sums in
-// the same precision as the two kernels.  A barrier that times out sets bit
-// 16 of the error word and its CTA skips the fold.
-__global__ void __launch_bounds__(256) k_near_fused(const long long* __restrict__ cell,
-                                                    const long long* __restrict__ q, long long n, int N,
-                                                    const double* __restrict__ gnear, const double* __restrict__ slot_S,
-                                                    int slot, double U, double* __restrict__ acc,
-                                                    float* __restrict__ out, long long* __restrict__ grid,
-                                                    unsigned* bar, int* err) {
-    const long long total = n * kNearCube;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    for (long long idx = i0; idx < total; idx += stride) {
-        const long long s = idx / kNearCube;
-        const int m = (int)(idx % kNearCube);
-        const long long qs = q[s];
-        if (qs == 0) continue;
-        int dx, dy, dz;
-        const long long t = near_target(cell[s], m, N, dx, dy, dz);
-        atomicAdd(acc + t, U * slot_S[slot] * (double)qs * gnear[near_wedge(dx, dy, dz)]);
-    }
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        s_ok = grid_barrier(bar, gridDim.x);
-        if (!s_ok) atomicOr(err, 16);
-    }
-    __syncthreads();
-    if (!s_ok) return;
-    for (long long idx = i0; idx < total; idx += stride) {
-        const long long s = idx / kNearCube;
-        const int m = (int)(idx % kNearCube);
-        if (q[s] == 0) continue;
-        if (grid && m == kNearCube / 2) grid[cell[s]] = 0;
-        int dx, dy, dz;
-        const long long t = near_target(cell[s], m, N, dx, dy, dz);
-        const double v = __longlong_as_double(
-            (long long)atomicExch(reinterpret_cast<unsigned long long*>(acc + t), 0ULL));
-        if (v != 0.0) out[t] = (float)((double)out[t] + v);
-    }
-}
-
 // Sub-cell near field (particle-mesh hybrid of the Discussion): one thread
 // per (source, target cell of its near cube).  The target's value is the s^3
 // sub-sample average of g around the source's own position, over the periodic
@@ -566,50 +498,6 @@ void launch_near_fold(const long long* cell, const long long* q, long long n, in
     const long long total = n * kNearCube;
     if (total <= 0) return;
     launch_k(k_near_fold, (unsigned)((total + 255) / 256), 256, 0, st, cell, q, n, N, acc, out, grid);
-}
-
-int near_fused_ctas(long long n) {
-    // CTAs of the cooperative near kernel, or 0 where it is not used: more
-    // than four grid-stride rounds over one CTA per SM (a cooperative grid
-    // waits until all its CTAs fit beside the other streams' kernels, so it
-    // is kept to one small CTA per SM), or no cooperative launch here
-    static int sms = 0, coop = -1;
-    if (coop < 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-            cudaGetLastError();
-            coop = 0;
-        }
-        int occ = 0;
-        if (coop && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_near_fused, 256, 0) != cudaSuccess ||
-                     occ < 2)) {
-            cudaGetLastError();
-            coop = 0;
-        }
-    }
-    const long long total = n * kNearCube;
-    const long long cap = sms;
-    if (!coop || total <= 0 || total > 4 * cap * 256) return 0;
-    const long long want = (total + 255) / 256;
-    return (int)(want < cap ? want : cap);
-}
-
-void launch_near_fused(const long long* cell, const long long* q, long long n, int N, const double* gnear,
-                       const double* slot_S, int slot, double U, double* acc, float* out, long long* grid,
-                       unsigned* bar, int* err, int ctas, cudaStream_t st) {
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)ctas);
-    cfg.blockDim = dim3(256);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = st;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, k_near_fused, cell, q, n, N, gnear, slot_S, slot, U, acc, out, grid, bar, err);
 }
 
 // Zero the deposit cells of a near-field list (entries with a non-zero share).

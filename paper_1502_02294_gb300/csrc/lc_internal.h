@@ -121,14 +121,6 @@ void launch_near_scatter(const long long* cell, const long long* q, long long n,
 // deposit grid, once the transforms have read it)
 void launch_near_fold(const long long* cell, const long long* q, long long n, int N, double* acc, float* out,
                       long long* grid, cudaStream_t st);
-// scatter and fold in one cooperative launch of `ctas` CTAs (a bounded
-// grid-wide barrier between them, counter pair `bar`, zero-initialised; a
-// timed-out barrier sets bit 16 of *err); near_fused_ctas(n) gives the grid,
-// 0 where the two-kernel form is used
-int near_fused_ctas(long long n);
-void launch_near_fused(const long long* cell, const long long* q, long long n, int N, const double* gnear,
-                       const double* slot_S, int slot, double U, double* acc, float* out, long long* grid,
-                       unsigned* bar, int* err, int ctas, cudaStream_t st);
 // zero grid[cell[i]] for the n entries of a near-field list with q[i] != 0
 void launch_cells_clear(const long long* cell, const long long* q, long long n, long long* grid, cudaStream_t st);
 
