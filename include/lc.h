@@ -186,7 +186,9 @@ lc_status lc_retarded_field(lc_plan* plan, int step, float* out);
  * rules), but with a host `out` the call returns once the work and the
  * device-to-host copy are enqueued, and *ticket (> 0) names that copy.  The
  * copy runs on a copy stream of the plan, out of one of two device stages,
- * so the next steps' pushes and fields compute while it drains; `out` holds
+ * so the next steps' pushes and fields compute while it drains (into
+ * page-locked memory by a small copy kernel writing through the buffer's
+ * device view; LC_D2H=ce in the environment uses the copy engine); `out` holds
  * the field once lc_plan_wait(plan, *ticket) returns, and must stay valid
  * until then (page-locked host memory makes the copy asynchronous; with
  * pageable memory the call itself waits for the copy).  With a device `out`

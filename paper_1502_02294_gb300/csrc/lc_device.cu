@@ -548,8 +548,18 @@ __global__ void __launch_bounds__(256) k_fdiff(long long n, const float* __restr
 // Device -> page-locked host copy by the SMs (16-byte stores through the
 // host mapping of the buffer), for the waiting host output path.
 __global__ void __launch_bounds__(256) k_copy_out(long long n4, const float4* __restrict__ src, float4* dst) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x)
-        dst[i] = src[i];
+    // four loads in flight per thread before the stores (a small grid copies
+    // at the host link's rate only with enough bytes outstanding)
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < n4; i += 4 * stride) {
+        float4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = src[i + u * stride];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) dst[i + u * stride] = v[u];
+    }
+    for (; i < n4; i += stride) dst[i] = src[i];
 }
 
 void launch_copy_out(long long n4, const float4* src, float4* dst, int ctas, cudaStream_t st) {
