@@ -1539,9 +1539,10 @@ static lc_status field_impl(lc_plan* p, int step, float* out, int instant, uint6
         // page-locked and 16-byte aligned: a kernel on the copy stream writes
         // it through the buffer's device view (SM stores over the host link;
         // with several plans serving at once this kept up better than the
-        // copy engines: c5 end to end 345 against 231 fields/s), with a small
-        // grid so that the copy holds few SM slots.  LC_D2H=ce: always the
-        // copy engine.  LC_D2H_CTAS: the copy kernel's CTAs.
+        // copy engines), with a small grid so that the copy holds few SM
+        // slots: serving c5 end to end, 231 fields/s by the copy engine,
+        // 340 with 152 CTAs, 378 with 38, 414 with 16.  LC_D2H=ce: always the
+        // copy engine.  LC_D2H_CTAS: the copy kernel's CTAs (default 16).
         static const bool sm_copy = [] {
             const char* v = getenv("LC_D2H");
             return !(v && !strcmp(v, "ce"));
@@ -1549,7 +1550,7 @@ static lc_status field_impl(lc_plan* p, int step, float* out, int instant, uint6
         static const int copy_ctas = [] {
             const char* v = getenv("LC_D2H_CTAS");
             const int c = v ? atoi(v) : 0;
-            return c > 0 ? c : sm_count() / 4;
+            return c > 0 ? c : 16;
         }();
         void* hv = sm_copy ? pinned_device_view(out) : nullptr;
         if (e == cudaSuccess && hv && (reinterpret_cast<uintptr_t>(hv) & 15) == 0) {
