@@ -310,6 +310,11 @@ struct lc_plan {
     // zeroed (by the near fold of the step's field, or before the next
     // deposit when no field ran), never the whole grid
     bool grid_dirty = false;
+    // inside lc_graph_create, whose field follows its push at once: the push
+    // may leave its x pass into the ring to the field's gather MAC
+    // (fuse_x), which then owes it for ring slot x_deferred
+    bool fuse_x = false;
+    int x_deferred = -1;
     int last_pushed = -1;
     bool failed = false;
     // per-phase event timing
@@ -555,6 +560,14 @@ void launch_mac(lc_plan* p, const lc_plan::Table& T, int step, int instant, int 
     c.gstride = T.gstride;
     c.instant = instant;
     c.tw = p->d_tw;
+    if (p->x_deferred >= 0 && variant == MAC_GATHER && !instant) {
+        // the push's x pass of the newest slice, done in this kernel
+        c.in_mode = bf ? COL_IN_MAC_BF16_X : COL_IN_MAC_F32_X;
+        c.src = p->d_work;
+        c.ring_out = p->d_ring;
+        c.wslot = p->x_deferred;
+        p->x_deferred = -1;
+    }
     auto mac_fn = variant == MAC_WS    ? (bf ? p->ops->mac_ws_bf16 : p->ops->mac_ws_f32)
                   : variant == MAC_WS2 ? (bf ? p->ops->mac_ws2_bf16 : p->ops->mac_ws2_f32)
                                        : (bf ? p->ops->mac_bf16 : p->ops->mac_f32);
@@ -1313,7 +1326,13 @@ lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos
     }
     c.n_ring = p->n_ring;
     c.wslot = slot;
-    {
+    // leave the x pass to the field's gather MAC when that field follows in
+    // the same capture (grids with plane kernels, whose x pass the fused
+    // kernel repeats bit for bit)
+    const lc_plan::Table& Tn = p->tables[step];
+    if (p->fuse_x && p->capturing && p->ops->plane_r2c && Tn.ghat && Tn.A > 0 && Tn.mac_variant == MAC_GATHER) {
+        p->x_deferred = slot;
+    } else {
         Phase ph(p, LC_PHASE_FWD_X_RING, 1);
         p->maps.set(c, p->d_err);
         p->ops->cols(c, st);
@@ -1942,8 +1961,12 @@ lc_status lc_graph_create(lc_plan* p, int step, int64_t n_src, const double* pos
     e = cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal);
     lc_status rs = LC_OK;
     if (e == cudaSuccess) {
+        p->fuse_x = true;
         rs = lc_push_sources(p, step, n_src, pos, lum);
         if (rs == LC_OK) rs = lc_retarded_field(p, step, out);
+        p->fuse_x = false;
+        if (rs == LC_OK && p->x_deferred >= 0) rs = LC_ERR_INVALID_ARG; // the field did not take the x pass
+        p->x_deferred = -1;
         cudaError_t e2 = cudaStreamEndCapture(cap_stream, &graph);
         if (e == cudaSuccess) e = e2;
     }

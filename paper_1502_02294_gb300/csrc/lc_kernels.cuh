@@ -20,7 +20,11 @@
 namespace lc {
 
 enum { ROW_IN_I64 = 0, ROW_IN_F32 = 1, ROW_IN_WEDGE = 2 };
-enum { COL_IN_PLAIN = 0, COL_IN_MAC_F32 = 1, COL_IN_MAC_BF16 = 2 };
+// COL_IN_MAC_*_X: the shell MAC whose newest slice (lookback 0) is this
+// tile of the y-transformed spectrum `src`, forward x-transformed in the
+// same kernel and written to its ring slot (`ring_out`, slot `wslot`) on the
+// way, with the arithmetic of the plain x pass into the ring
+enum { COL_IN_PLAIN = 0, COL_IN_MAC_F32 = 1, COL_IN_MAC_BF16 = 2, COL_IN_MAC_F32_X = 3, COL_IN_MAC_BF16_X = 4 };
 // COL_OUT_BF16 / COL_OUT_RING_F32 write one slot of the history ring, whose
 // layout is [tile][slot][N x CW elements]: the history of an x-pass tile over
 // all slots is one contiguous run, read as a stream by the shell MAC
@@ -62,6 +66,7 @@ struct ColArgs {
     int gstride;              // row stride of the Ghat table (A rounded up to 8)
     int instant;              // 1: every shell uses the observing step's slice (Eq. 18)
     int tile0;                // first tile of this launch (tiles before it are skipped)
+    void* ring_out;           // COL_IN_MAC_*_X: the ring the newest slice is written to
     // wedge extract (forward x-pass of a Green's function)
     float* wedge_out;
     int wedge_A, wedge_j;     // wedge_A: row stride of the table written
@@ -225,6 +230,8 @@ __global__ void __launch_bounds__(kThreads) k_rows_r2c(RowR2CArgs a, int nblocks
 // CW Nyquist columns of CW lines).  NT = N * CW / 8 threads, 8 elements each.
 template <int N, int DIR, int IN, int OUT>
 __global__ void __launch_bounds__(col_threads_of(N)) k_cols(ColArgs a) {
+    constexpr bool BFR = IN == COL_IN_MAC_BF16 || IN == COL_IN_MAC_BF16_X; // BF16 ring
+    constexpr bool FWDX = IN == COL_IN_MAC_F32_X || IN == COL_IN_MAC_BF16_X;
     constexpr int NT = col_threads_of(N);
     constexpr int CW = cw_of(N), BP = odd_pad(CW), NRP = nrp_of(N), M = N / 2, NCH = M / CW;
     constexpr int TILE = N * CW, PER = (TILE + NT - 1) / NT;
@@ -270,8 +277,8 @@ __global__ void __launch_bounds__(col_threads_of(N)) k_cols(ColArgs a) {
         const bool dc_tile = (a.axis == 1) && !nyq && line == 0 && chunk == 0;
         int* s_slot = reinterpret_cast<int*>(s_D + kMaxShells);
         if (threadIdx.x < 32)
-            mac_slot_list(a.A, a.step, a.n_ring, a.slot_step, a.slot_total, a.slot_S, a.g0,
-                          IN == COL_IN_MAC_BF16, s_slot, s_j, s_D, &s_nv, &s_dc, a.instant);
+            mac_slot_list(a.A, a.step, a.n_ring, a.slot_step, a.slot_total, a.slot_S, a.g0, BFR, s_slot, s_j, s_D,
+                          &s_nv, &s_dc, a.instant);
         __syncthreads();
         for (int v = threadIdx.x; v < s_nv; v += NT) s_off[v] = (long long)s_slot[v] * TILE;
         for (int i = threadIdx.x; i < N; i += NT) tw[i] = a.tw[i];
@@ -287,6 +294,37 @@ __global__ void __launch_bounds__(col_threads_of(N)) k_cols(ColArgs a) {
             val[i] = make_float2(0.f, 0.f);
         }
         __syncthreads();
+        float2 fx[FWDX ? PER : 1];
+        if constexpr (FWDX) {
+            // the newest slice: the forward x transform of this tile of
+            // `src`, stored to its ring slot exactly as the plain x pass
+            // into the ring stores it, and kept in registers for lookback 0
+#pragma unroll
+            for (int i = 0; i < PER; ++i) {
+                const int idx = threadIdx.x + i * NT;
+                if (TILE % NT == 0 || idx < TILE) buf[(idx / CW) * BP + (idx % CW)] = a.src[addr[i]];
+            }
+            __syncthreads();
+            fft_smem<N, -1, CW, BP, NT>(buf, tw);
+            const long long wbase = ((long long)tile * a.n_ring + a.wslot) * TILE;
+#pragma unroll
+            for (int i = 0; i < PER; ++i) {
+                const int idx = threadIdx.x + i * NT;
+                fx[i] = make_float2(0.f, 0.f);
+                if (TILE % NT == 0 || idx < TILE) {
+                    const float2 v = buf[(idx / CW) * BP + (idx % CW)];
+                    if constexpr (BFR) {
+                        const __nv_bfloat162 b = __floats2bfloat162_rn(v.x, v.y);
+                        reinterpret_cast<__nv_bfloat162*>(a.ring_out)[wbase + idx] = b;
+                        fx[i] = __bfloat1622float2(b);
+                    } else {
+                        reinterpret_cast<float2*>(a.ring_out)[wbase + idx] = v;
+                        fx[i] = v;
+                    }
+                }
+            }
+            __syncthreads(); // buf is free again for the inverse transform
+        }
         const int nv = s_nv;
         const long long tbase = (long long)tile * a.n_ring * TILE;
         // shells outer, the tile's elements inner: PER independent ring loads
@@ -295,11 +333,13 @@ __global__ void __launch_bounds__(col_threads_of(N)) k_cols(ColArgs a) {
         auto fetch = [&](int v, float2 (&f)[PER], float (&gv)[PER]) {
             const long long off = s_off[v];
             const int jv = s_j[v];
+            const bool own = FWDX && jv == 0; // the newest slice, already in registers
 #pragma unroll
             for (int i = 0; i < PER; ++i) {
                 if (TILE % NT == 0 || threadIdx.x + i * NT < TILE) {
                     const long long ri = off + tbase + threadIdx.x + i * NT; // tile-major ring slot
-                    if constexpr (IN == COL_IN_MAC_F32) f[i] = reinterpret_cast<const float2*>(a.ring)[ri];
+                    if (own) f[i] = fx[FWDX ? i : 0];
+                    else if constexpr (!BFR) f[i] = reinterpret_cast<const float2*>(a.ring)[ri];
                     else f[i] = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(a.ring)[ri]);
                     gv[i] = __ldg(g[i] + jv);
                 } else {
@@ -1817,6 +1857,10 @@ template <int N> struct Launch {
         }
         LC_ATTR((k_cols<N, 1, COL_IN_MAC_F32, COL_OUT_PLAIN>), cs);
         LC_ATTR((k_cols<N, 1, COL_IN_MAC_BF16, COL_OUT_PLAIN>), cs);
+        if constexpr (!kColsPl) {
+            LC_ATTR((k_cols<N, 1, COL_IN_MAC_F32_X, COL_OUT_PLAIN>), cs);
+            LC_ATTR((k_cols<N, 1, COL_IN_MAC_BF16_X, COL_OUT_PLAIN>), cs);
+        }
         if constexpr (plane_ok<N>()) {
             const int ps = (int)plane_smem_bytes<N>();
             LC_ATTR((k_plane_r2c<N, ROW_IN_I64>), ps);
@@ -1955,7 +1999,13 @@ template <int N> struct Launch {
         } else {
             if (a.in_mode == COL_IN_PLAIN) cols_plain<1, COL_OUT_PLAIN>(a, ntiles, st);
             else if (a.in_mode == COL_IN_MAC_F32) launch_k(k_cols<N, 1, COL_IN_MAC_F32, COL_OUT_PLAIN>, g, kThreads, sm, st, a);
-            else launch_k(k_cols<N, 1, COL_IN_MAC_BF16, COL_OUT_PLAIN>, g, kThreads, sm, st, a);
+            else if (a.in_mode == COL_IN_MAC_BF16) launch_k(k_cols<N, 1, COL_IN_MAC_BF16, COL_OUT_PLAIN>, g, kThreads, sm, st, a);
+            else if constexpr (!kColsPl) {
+                // with the forward x pass of the newest slice (grids whose
+                // plain x pass is k_cols_pp, whose arithmetic it repeats)
+                if (a.in_mode == COL_IN_MAC_F32_X) launch_k(k_cols<N, 1, COL_IN_MAC_F32_X, COL_OUT_PLAIN>, g, kThreads, sm, st, a);
+                else launch_k(k_cols<N, 1, COL_IN_MAC_BF16_X, COL_OUT_PLAIN>, g, kThreads, sm, st, a);
+            }
         }
     }
 };
