@@ -264,12 +264,13 @@ def max_over_ranks(x, device):
     return float(t.item())
 
 
-def fft_choices():
-    """The FFT pass form in use per grid size (autotuned): {N: name}."""
+def fft_choices(ns):
+    """The FFT pass form in use for each grid size in ns (autotuned when the
+    first plan of that size was created): {N: name}."""
     import paper_1502_02294_gb300 as lc
 
     names = {lc.FFT_STAGES: "stages", lc.FFT_LANES: "lanes", lc.FFT_LANES3: "lanes3", lc.FFT_TMA: "tma", lc.FFT_TMA4: "tma4"}
-    return {n: names.get(lc.fft_variant(n), "-") for n in lc.SUPPORTED_N if n >= 256}
+    return {int(n): names.get(lc.fft_variant(int(n)), "-") for n in sorted(set(ns))}
 
 
 def config_of(workload, w=None, extra=None):
@@ -405,6 +406,29 @@ def run_batched(args):
             p.field(w.steps.n_shell + k, o)
         e2e_t += time.perf_counter() - tic
         h2d += sum(hi[w.steps.n_shell + k][0].nbytes + hi[w.steps.n_shell + k][1].nbytes for w, hi in zip(ws, host_in))
+    # error_vs_fp64 and cpu_baseline: the batch graph's first window step of
+    # the three smallest instances against the FP64 oracle on sampled cells
+    err, cpu = None, None
+    if not args.no_cpu_baseline:
+        import oracle
+
+        refill()
+        graphs[0].launch(stream)
+        torch.cuda.synchronize()
+        picks = sorted(range(len(ws)), key=lambda i: (ws[i].n, i))[:3]
+        rows, times, spent_all = [], [], 0.0
+        for i in picks:
+            w = ws[i]
+            s = w.steps.n_shell
+            rate, spent, desc, samples = oracle_sample(w, [s], cells_per_step=2048, seed=400 + i)
+            J = outs[i].cpu().numpy().reshape(-1)
+            rows.append(sample_errors(f"instance {i} ({w.n}^3, {w.steps.n_shell} shells) step {s}", J, samples[s]))
+            times.append(1.0 / rate)
+            spent_all += spent
+        err = error_summary(rows, 0)
+        cpu = {"value": len(times) / float(np.sum(times)), "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+               "sample": f"instances {picks} (the three smallest grids), their first timed step each: " + desc,
+               "seconds": round(spent_all, 2)}
     for g in graphs:
         g.close()
     for p in plans:
@@ -416,7 +440,7 @@ def run_batched(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": config_of("c4", extra={"instances": n_inst, "grids": [w.n for w in ws],
                                          "shells": [w.steps.n_shell for w in ws]}),
-        "details": {"timed_window_steps": window,
+        "details": {"timed_window_steps": window, "fft_passes": fft_choices([w.n for w in ws]),
                     "l2": f"flushed between timed steps ({args.flush_mb} MB write outside the events)",
                     "inputs": "device-resident"},
         "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99))},
@@ -426,7 +450,7 @@ def run_batched(args):
         "clocks": clocks,
         "e2e": {"value": n_inst * args.steps / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(h2d // args.steps),
                 "d2h_bytes_per_step": int(sum(4 * w.n ** 3 for w in ws))},
-        "gpu_launches": int(launches), "cpu_baseline": None, "error_vs_fp64": None,
+        "gpu_launches": int(launches), "cpu_baseline": cpu, "error_vs_fp64": err,
         "launch": "one batch CUDA graph per step: 16 parallel branches (one per instance)",
         "instances_one_after_another": {"fields_per_s": n_inst * args.steps / T_seq,
                                          "form": "one step graph per instance, launched in turn on one stream"},
@@ -625,7 +649,7 @@ def run_serving(args):
         "config": config_of("c5", extra={"grids": grids, "shells": shells, "requests_per_sim": K}),
         "details": {"hbm_budget_bytes": budget, "admitted_at_once": len(admitted), "slots_per_sim": 4,
                     "stream_priorities": "equal" if args.equal_priorities else "by grid size (small first)",
-                    "fft_passes": fft_choices(),
+                    "fft_passes": fft_choices(grids),
                     "mac_kernel": {k: v for k, v in lc.autotune_report().items() if k.startswith("mac")},
                     "l2": "no flush: every request streams its simulation's history ring (0.55-26 GB, far above "
                           "the 129 MB L2) from HBM",
@@ -988,7 +1012,7 @@ def run_single(args, w, variant, quick=False):
             "config": config_of(args.workload, w, variant),
             "details": {"timed_window": [t0, T], "ring_slots": plan.n_ring,
                         "mac_kernel": dict(sorted(mac_choice.items(), key=lambda kv: int(kv[0][1:]))),
-                        "fft_passes": fft_choices(),
+                        "fft_passes": fft_choices([w.n]),
                         "l2": f"flushed between timed steps ({args.flush_mb} MB write outside the events)",
                         "inputs": "device-resident"},
             "cell_shell_mac_per_s": world * mac_cells / t_max,

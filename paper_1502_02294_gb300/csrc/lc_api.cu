@@ -593,6 +593,63 @@ bool mac_built(const lc_plan* p, int variant) {
 
 int mac_kernels(const lc_plan* p, int variant) { return variant == MAC_BULK && mac_built(p, variant) ? 2 : 1; }
 
+// The autotuners' timing: a transient buffer of twice the L2 size whose
+// memset before each timed launch evicts the launch's inputs, as the other
+// passes of a step do (without it, grids whose data fits in L2 were timed
+// warm and the choice flipped from process to process).
+struct TuneFlush {
+    void* buf = nullptr;
+    size_t bytes = 0;
+    TuneFlush() {
+        int dev = 0, l2 = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess)
+            l2 = 0;
+        bytes = 2 * (size_t)l2;
+        if (bytes && cudaMalloc(&buf, bytes) != cudaSuccess) buf = nullptr;
+        cudaGetLastError();
+    }
+    ~TuneFlush() {
+        if (buf) cudaFree(buf);
+    }
+    TuneFlush(const TuneFlush&) = delete;
+    TuneFlush& operator=(const TuneFlush&) = delete;
+};
+
+// Median time of `launch` (ms) over kTuneReps launches, each after an L2
+// flush and between its own pair of events, after one warm-up; -1 on error.
+constexpr int kTuneReps = 7;
+template <class F> double tune_time(cudaStream_t st, const TuneFlush& fl, F&& launch) {
+    cudaEvent_t a[kTuneReps] = {}, b[kTuneReps] = {};
+    bool ok = true;
+    for (int r = 0; ok && r < kTuneReps; ++r)
+        ok = cudaEventCreate(&a[r]) == cudaSuccess && cudaEventCreate(&b[r]) == cudaSuccess;
+    double med = -1.0;
+    if (ok) {
+        launch();
+        for (int r = 0; r < kTuneReps; ++r) {
+            if (fl.buf) cudaMemsetAsync(fl.buf, 0, fl.bytes, st);
+            cudaEventRecord(a[r], st);
+            launch();
+            cudaEventRecord(b[r], st);
+        }
+        if (cudaEventSynchronize(b[kTuneReps - 1]) == cudaSuccess) {
+            float t[kTuneReps];
+            for (int r = 0; r < kTuneReps; ++r) {
+                t[r] = 0.f;
+                cudaEventElapsedTime(&t[r], a[r], b[r]);
+            }
+            std::sort(t, t + kTuneReps);
+            med = t[kTuneReps / 2];
+        }
+    }
+    for (int r = 0; r < kTuneReps; ++r) {
+        if (a[r]) cudaEventDestroy(a[r]);
+        if (b[r]) cudaEventDestroy(b[r]);
+    }
+    cudaGetLastError();
+    return med;
+}
+
 // Pick the MAC variant for a table (plan time: may synchronise).
 int choose_mac_variant(lc_plan* p, const lc_plan::Table& T, int s) {
     const bool bf = p->history == LC_HISTORY_BF16;
@@ -608,7 +665,7 @@ int choose_mac_variant(lc_plan* p, const lc_plan::Table& T, int s) {
     cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
     cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
     char kb[128];
-    snprintf(kb, sizeof kb, "mac%d/sm%d%d/N%d/%s/A%d", MAC_NVAR, major, minor, p->N, bf ? "bf16" : "fp32", T.A);
+    snprintf(kb, sizeof kb, "mac%dc/sm%d%d/N%d/%s/A%d", MAC_NVAR, major, minor, p->N, bf ? "bf16" : "fp32", T.A);
     const std::string key(kb);
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
@@ -628,41 +685,23 @@ int choose_mac_variant(lc_plan* p, const lc_plan::Table& T, int s) {
     std::vector<long long> ht(p->n_ring, 1);
     for (int j = 0; j < T.A && s - j >= 0; ++j) hs[(s - j) % p->n_ring] = s - j;
     cudaStream_t st = p->stream;
-    constexpr int kReps = 5; // timed launches per variant, each between its own events
-    cudaEvent_t ev[kReps + 1] = {};
     double ms[MAC_NVAR];
     for (int v = 0; v < MAC_NVAR; ++v) ms[v] = -1.0;
     bool ok = cudaMemcpy(p->d_tune_step, hs.data(), sizeof(int) * p->n_ring, cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(p->d_tune_S, hS.data(), sizeof(double) * p->n_ring, cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(p->d_tune_total, ht.data(), sizeof(long long) * p->n_ring, cudaMemcpyHostToDevice) == cudaSuccess;
-    for (int r = 0; ok && r <= kReps; ++r) ok = cudaEventCreate(&ev[r]) == cudaSuccess;
     if (!ok) {
-        for (auto e : ev)
-            if (e) cudaEventDestroy(e);
         cudaGetLastError();
         return MAC_GATHER;
     }
+    TuneFlush fl;
     int best = MAC_GATHER;
     for (int v = 0; v < MAC_NVAR; ++v) {
         if (!mac_built(p, v)) continue;
-        launch_mac(p, T, s, 0, v, p->d_tune_step, p->d_tune_S, p->d_tune_total, st); // warm-up
-        cudaEventRecord(ev[0], st);
-        for (int r = 0; r < kReps; ++r) {
-            launch_mac(p, T, s, 0, v, p->d_tune_step, p->d_tune_S, p->d_tune_total, st);
-            cudaEventRecord(ev[r + 1], st);
-        }
-        cudaEventSynchronize(ev[kReps]);
-        float t[kReps];
-        for (int r = 0; r < kReps; ++r) {
-            t[r] = 0.f;
-            cudaEventElapsedTime(&t[r], ev[r], ev[r + 1]);
-        }
-        std::sort(t, t + kReps);
-        ms[v] = t[kReps / 2]; // median launch
-        count_launch((unsigned long long)(kReps + 1) * mac_kernels(p, v));
-        if (ms[v] < ms[best] || ms[best] < 0) best = v;
+        ms[v] = tune_time(st, fl, [&] { launch_mac(p, T, s, 0, v, p->d_tune_step, p->d_tune_S, p->d_tune_total, st); });
+        count_launch((unsigned long long)(kTuneReps + 1) * mac_kernels(p, v));
+        if (ms[v] >= 0 && (ms[v] < ms[best] || ms[best] < 0)) best = v;
     }
-    for (auto e : ev) cudaEventDestroy(e);
     if (cudaGetLastError() != cudaSuccess) return MAC_GATHER;
     std::lock_guard<std::mutex> g(g_tune_mu);
     tune_store(key, best, ms, MAC_NVAR);
@@ -775,7 +814,7 @@ void choose_fft_variant(lc_plan* p) {
     cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
     cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
     char kb[96];
-    snprintf(kb, sizeof kb, "fft%d/sm%d%d/N%d", FFT_NVAR, major, minor, p->N);
+    snprintf(kb, sizeof kb, "fft%dc/sm%d%d/N%d", FFT_NVAR, major, minor, p->N);
     const std::string key(kb);
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
@@ -787,34 +826,16 @@ void choose_fft_variant(lc_plan* p) {
         }
     }
     cudaStream_t st = p->stream;
-    constexpr int kReps = 5;
-    cudaEvent_t ev[kReps + 1] = {};
-    bool ok = true;
-    for (int r = 0; ok && r <= kReps; ++r) ok = cudaEventCreate(&ev[r]) == cudaSuccess;
     double ms[FFT_NVAR > MAC_NVAR ? FFT_NVAR : MAC_NVAR];
     for (auto& m : ms) m = -1.0;
     int best = ops->cols_variant();
-    for (int v = 0; ok && v < FFT_NVAR; ++v) {
+    TuneFlush fl;
+    for (int v = 0; v < FFT_NVAR; ++v) {
         if (!(built >> v & 1)) continue;
         ops->set_cols_variant(v);
-        fft_step_passes(p, st); // warm-up
-        cudaEventRecord(ev[0], st);
-        for (int r = 0; r < kReps; ++r) {
-            fft_step_passes(p, st);
-            cudaEventRecord(ev[r + 1], st);
-        }
-        cudaEventSynchronize(ev[kReps]);
-        float t[kReps];
-        for (int r = 0; r < kReps; ++r) {
-            t[r] = 0.f;
-            cudaEventElapsedTime(&t[r], ev[r], ev[r + 1]);
-        }
-        std::sort(t, t + kReps);
-        ms[v] = t[kReps / 2];
-        if (ms[best] < 0 || ms[v] < ms[best]) best = v;
+        ms[v] = tune_time(st, fl, [&] { fft_step_passes(p, st); });
+        if (ms[v] >= 0 && (ms[best] < 0 || ms[v] < ms[best])) best = v;
     }
-    for (auto e : ev)
-        if (e) cudaEventDestroy(e);
     ops->set_cols_variant(best);
     // the grid's memory held float outputs: clear it for the first deposit
     cudaMemsetAsync(p->d_grid, 0, sizeof(long long) * (size_t)p->N * p->N * p->N, st);
