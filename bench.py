@@ -704,14 +704,15 @@ def run_serving(args):
 
 
 # DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum) of the
-# shell-MAC phase per step, from the captures summarised in profiles/, valid
-# only for the MAC kernel sources they were taken with (hash below: the
-# warp-specialised and bulk kernels, the gather pass and its slot list); c3 is
-# the c3s capture (32 slices) with its reads scaled to 128 slices.
+# shell-MAC launch, from the captures summarised in profiles/, valid only for
+# the kernel sources they were taken with: the warp-specialised kernels
+# (all of lc_mac.cuh; the kernel the c3 and served 512^3 lines run).  c3 is the
+# c3s capture (32 slices) with its reads scaled to 128 slices.  The 128^3
+# line has none: its steps mix three MAC kernels, and a capture over a whole
+# window of launches is beyond what this pool's profiling rules allow.
+WS_SOURCES = "260d34c3405dd767"
 MAC_TRAFFIC = {
-    "c2": {"sources": "731331f0d508e08e", "bytes": 38.472e6,
-           "from": "profiles/c2_dram_traffic.md (64-step window, all MAC-phase launches)"},
-    "c3": {"sources": "731331f0d508e08e", "bytes": 4 * 1.192879e9 + 73.619e6,
+    "c3": {"sources": WS_SOURCES, "bytes": 4 * 1.192879e9 + 73.619e6,
            "from": "profiles/k_mac_ws_256_bf16_pair.md (c3s, reads x 128/32)"},
 }
 
@@ -719,30 +720,17 @@ MAC_TRAFFIC = {
 # the served 512^3 MAC launch (96 slices, BF16, paired kernel): DRAM traffic
 # scaled from the c5s capture (16 slices: reads x 96/16, writes as captured)
 # and the launch's algorithmic bytes N_k (4 A + 8) + 4 W A
-MAC512_TRAFFIC = {"sources": "731331f0d508e08e", "bytes": 4.877360555e9 * 96 / 16 + 0.598957994e9,
+MAC512_TRAFFIC = {"sources": WS_SOURCES, "bytes": 4.877360555e9 * 96 / 16 + 0.598957994e9,
                   "algorithmic": 67371008 * (4 * 96 + 8) + 4 * 2862209 * 96,
                   "from": "profiles/k_mac_ws_512_bf16_pair.md"}
 
 
-def _function_text(src, head):
-    """The text of the function whose definition line contains `head`, from
-    the start of that line to the closing brace at the start of a line."""
-    i = src.rfind("\n", 0, src.index(head)) + 1
-    return src[i:src.index("\n}\n", i) + 3]
-
-
 def mac_sources_hash():
+    """Hash of the warp-specialised MAC kernels' sources (lc_mac.cuh)."""
     import hashlib
 
-    d = os.path.join(ROOT, "paper_1502_02294_gb300", "csrc")
-    h = hashlib.sha256()
-    with open(os.path.join(d, "lc_mac.cuh"), "rb") as fh:
-        h.update(fh.read())
-    with open(os.path.join(d, "lc_kernels.cuh")) as fh:
-        k = fh.read()
-    h.update(_function_text(k, "__device__ __forceinline__ void mac_slot_list(").encode())
-    h.update(_function_text(k, " k_cols(ColArgs a) {").encode())
-    return h.hexdigest()[:16]
+    with open(os.path.join(ROOT, "paper_1502_02294_gb300", "csrc", "lc_mac.cuh"), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
 def mac_traffic(workload):

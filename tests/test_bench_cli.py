@@ -45,3 +45,6 @@ def test_mac_source_hash_finds_the_kernel_texts():
         assert os.path.exists(os.path.join(ROOT, t["from"].split(" ")[0]))
     t = bench.MAC512_TRAFFIC
     assert t["bytes"] > t["algorithmic"] > 0 and os.path.exists(os.path.join(ROOT, t["from"]))
+    # the captures belong to the kernels as they stand: a change to them
+    # must come with new captures (and a new hash), else `traffic` goes null
+    assert t["sources"] == h and all(x["sources"] == h for x in bench.MAC_TRAFFIC.values())
