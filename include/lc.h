@@ -370,7 +370,8 @@ uint64_t lc_kernel_launches(void);
  * over every tile, one tile per CTA (ws) or the tiles of lines q and N - q
  * together (ws2).  Each plan times every kernel built for its grid on its own
  * buffers when it first builds a table for a new (device, N, history, active
- * slices) combination and keeps the fastest.  Choices are shared by all plans
+ * slices) combination (seven launches, each after an L2 flush) and keeps the
+ * one with the lowest median.  Choices are shared by all plans
  * of the process and persisted to the file named by the environment variable
  * LC_AUTOTUNE_CACHE if set; LC_MAC_VARIANT=gather|bulk|ws|ws2 forces one
  * kernel where it is built.  This writes the current choices ("key variant"
@@ -385,9 +386,13 @@ int lc_autotune_report(char* buf, int size);
  * LC_FFT_LANES (tiles copied by 16-byte asynchronous copies into four
  * stages, one CTA per SM), LC_FFT_LANES3 (three stages, two CTAs per SM),
  * LC_FFT_TMA (tiles moved by tensor-map TMA, three stages, two CTAs per SM)
- * and LC_FFT_TMA4 (TMA, four stages, one CTA per SM).
+ * and LC_FFT_TMA4 (TMA, four stages, one CTA per SM).  Grids with plane
+ * kernels (N = 32 ... 192: z and y per x-plane in one kernel) have two:
+ * LC_FFT_STAGES (staged plane kernels) and LC_FFT_LANES (the transforms in
+ * registers, one shared-memory exchange per axis); 8 and 16 have one.
  * The first plan created for a grid size times every form on its own
- * buffers (forward and inverse passes of one step) and keeps the fastest
+ * buffers (forward and inverse passes of one step, each launch after an L2
+ * flush, median of seven) and keeps the fastest
  * for the rest of the process (the choice is listed by lc_autotune_report
  * and persisted with the shell-MAC choices);
  * LC_FFT_VARIANT=stages|lanes|lanes3|tma|tma4 forces one.
