@@ -1294,14 +1294,12 @@ lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos
     SlotMeta m{slot, step, p->d_slot_step, p->d_slot_S, p->d_slot_total};
     const long long N = p->N;
     {
-        Phase ph(p, LC_PHASE_DEPOSIT, n_src > 0 ? 2 : 1);
+        Phase ph(p, LC_PHASE_DEPOSIT, n_src <= kSmallDepositSources ? 1 : 2);
         if (memset_before_deposit(p)) e = cudaMemsetAsync(p->d_grid, 0, sizeof(long long) * N * N * N, st);
         if (e != cudaSuccess) return cuda_fail(p, e);
-        launch_src_prep(dpos, dlum, n_src, p->d_maxbits, p->d_err, m, st);
-        if (n_src > 0)
-            launch_deposit(dpos, dlum, n_src, p->N, p->l, p->deposit, p->d_maxbits, p->d_grid, m, p->d_err, st,
-                           p->near_on ? p->d_src_cell : nullptr, p->near_on ? p->d_src_q : nullptr,
-                           p->near_pm ? p->d_src_off : nullptr);
+        launch_slice_deposit(dpos, dlum, n_src, p->N, p->l, p->deposit, p->d_maxbits, p->d_grid, m, p->d_err, st,
+                             p->near_on ? p->d_src_cell : nullptr, p->near_on ? p->d_src_q : nullptr,
+                             p->near_pm ? p->d_src_off : nullptr);
     }
     p->near_n = near_entries(p, n_src);
     if (n_src > 0) p->grid_dirty = true;
@@ -2229,9 +2227,7 @@ lc_status lc_deposit_grid(int n, double box, int deposit, int64_t n_src, const d
     if (e == cudaSuccess) e = cudaMemsetAsync(derr, 0, sizeof(int), st);
     SlotMeta m{0, 0, dstep, dS, dtot};
     if (e == cudaSuccess) {
-        launch_src_prep(dpos, dlum, n_src, dmax, derr, m, st);
-        if (n_src > 0) launch_deposit(dpos, dlum, n_src, n, box / n, deposit, dmax, dgrid, m, derr, st);
-        count_launch(n_src > 0 ? 2 : 1);
+        count_launch(launch_slice_deposit(dpos, dlum, n_src, n, box / n, deposit, dmax, dgrid, m, derr, st));
         e = cudaGetLastError();
     }
     long long tot = 0;
