@@ -112,6 +112,18 @@ __device__ __forceinline__ void split_share(long long q, double f, long long& lo
     lo = q - h;
 }
 
+// The target cell of displacement m of the 5^3 near cube around cell c
+// (periodic), with the displacement.
+__device__ __forceinline__ long long near_target(long long c, int m, int N, int& dx, int& dy, int& dz) {
+    dx = m / (kNearSide * kNearSide) - kNearR;
+    dy = (m / kNearSide) % kNearSide - kNearR;
+    dz = m % kNearSide - kNearR;
+    const long long NN = (long long)N * N;
+    const int ix = (int)(c / NN), iy = (int)((c / N) % N), iz = (int)(c % N);
+    const int tx = (ix + dx + N) % N, ty = (iy + dy + N) % N, tz = (iz + dz + N) % N;
+    return ((long long)tx * N + ty) * N + tz;
+}
+
 // The fixed-point unit S of a slice (a power of two: n * lmax < 2^62 S) and
 // 1/S where that is a normal number (0 otherwise: divide by S instead).
 // L / S for a power of two S is the exact L 2^(62-E) rounded once, so the
@@ -231,7 +243,8 @@ template <int CIC>
 __global__ void __launch_bounds__(256)
     k_deposit_small(const double* __restrict__ pos, const double* __restrict__ lum, long long n, int N, double l,
                     long long* __restrict__ grid, SlotMeta m, int* err, long long* __restrict__ cell_out,
-                    long long* __restrict__ q_out, double* __restrict__ off_out) {
+                    long long* __restrict__ q_out, double* __restrict__ off_out, const double* __restrict__ gnear,
+                    double U, double* __restrict__ acc) {
     __shared__ unsigned long long s_max[8];
     __shared__ long long s_tot[8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -265,6 +278,24 @@ __global__ void __launch_bounds__(256)
     const long long i = (long long)blockIdx.x * kSmallPerCta + threadIdx.x;
     if (threadIdx.x < kSmallPerCta && i < n)
         deposit_source<CIC>(i, pos, lum, N, l, S, invS, grid, err, cell_out, q_out, off_out);
+    if (gnear && cell_out) {
+        // the innermost shell's near cubes of this CTA's sources into the
+        // FP64 accumulator, as k_near_scatter does (the entries were written
+        // above by this CTA's first threads)
+        constexpr int E = CIC ? 8 : 1;
+        __syncthreads();
+        const long long e0 = (long long)blockIdx.x * kSmallPerCta * E;
+        const long long e1 = min(n, (long long)(blockIdx.x + 1) * kSmallPerCta) * E;
+        for (long long it = threadIdx.x; it < (e1 - e0) * kNearCube; it += blockDim.x) {
+            const long long e = e0 + it / kNearCube;
+            const int mm = (int)(it % kNearCube);
+            const long long qs = q_out[e];
+            if (qs == 0) continue;
+            int dx, dy, dz;
+            const long long t = near_target(cell_out[e], mm, N, dx, dy, dz);
+            atomicAdd(acc + t, U * S * (double)qs * gnear[near_wedge(dx, dy, dz)]);
+        }
+    }
 }
 
 // wedge index -> sorted triple a <= b <= c
@@ -391,15 +422,6 @@ __global__ void k_near_prep(const double* gw0, const double* scale0, double* gne
     *g0_far -= sum;
 }
 
-__device__ __forceinline__ long long near_target(long long c, int m, int N, int& dx, int& dy, int& dz) {
-    dx = m / (kNearSide * kNearSide) - kNearR;
-    dy = (m / kNearSide) % kNearSide - kNearR;
-    dz = m % kNearSide - kNearR;
-    const long long NN = (long long)N * N;
-    const int ix = (int)(c / NN), iy = (int)((c / N) % N), iz = (int)(c % N);
-    const int tx = (ix + dx + N) % N, ty = (iy + dy + N) % N, tz = (iz + dz + N) % N;
-    return ((long long)tx * N + ty) * N + tz;
-}
 
 __global__ void __launch_bounds__(256) k_near_scatter(const long long* __restrict__ cell, const long long* __restrict__ q,
                                                       long long n, int N, const double* __restrict__ gnear,
@@ -612,15 +634,16 @@ void launch_deposit(const double* pos, const double* lum, long long n, int N, do
 
 int launch_slice_deposit(const double* pos, const double* lum, long long n, int N, double l, int deposit,
                          unsigned long long* maxbits, long long* grid, SlotMeta m, int* err, cudaStream_t st,
-                         long long* cell_out, long long* q_out, double* off_out) {
+                         long long* cell_out, long long* q_out, double* off_out, const double* gnear, double U,
+                         double* acc) {
     if (n <= kSmallDeposit) {
         const unsigned blocks = (unsigned)(n > 0 ? (n + kSmallPerCta - 1) / kSmallPerCta : 1);
         if (deposit == LC_DEPOSIT_CIC)
             launch_k(k_deposit_small<1>, blocks, 256, 0, st, pos, lum, n, N, l, grid, m, err, cell_out, q_out,
-                     (double*)nullptr);
+                     (double*)nullptr, gnear, U, acc);
         else
             launch_k(k_deposit_small<0>, blocks, 256, 0, st, pos, lum, n, N, l, grid, m, err, cell_out, q_out,
-                     off_out);
+                     off_out, gnear, U, acc);
         return 1;
     }
     launch_src_prep(pos, lum, n, maxbits, err, m, st);
