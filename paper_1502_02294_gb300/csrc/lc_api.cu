@@ -315,9 +315,6 @@ struct lc_plan {
     // (fuse_x), which then owes it for ring slot x_deferred
     bool fuse_x = false;
     int x_deferred = -1;
-    // the push's deposit kernel has already scattered the near field of the
-    // innermost shell (step graphs on plane grids); the field only folds it
-    bool near_scattered = false;
     int last_pushed = -1;
     bool failed = false;
     // per-phase event timing
@@ -1296,21 +1293,15 @@ lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos
     const int slot = step % p->n_ring;
     SlotMeta m{slot, step, p->d_slot_step, p->d_slot_S, p->d_slot_total};
     const long long N = p->N;
-    // in a step graph on a plane grid, the deposit kernel also scatters the
-    // innermost shell's near field (the field that follows folds it inside
-    // its inverse plane kernel)
     const lc_plan::Table& Tn = p->tables[step];
-    const bool scatter_here = p->fuse_x && p->capturing && p->near_on && !p->near_pm && p->ops->plane_c2r &&
-                              n_src > 0 && n_src <= kSmallDepositSources && Tn.ghat && Tn.A > 0 && Tn.gnear;
     {
         Phase ph(p, LC_PHASE_DEPOSIT, n_src <= kSmallDepositSources ? 1 : 2);
         if (memset_before_deposit(p)) e = cudaMemsetAsync(p->d_grid, 0, sizeof(long long) * N * N * N, st);
         if (e != cudaSuccess) return cuda_fail(p, e);
         launch_slice_deposit(dpos, dlum, n_src, p->N, p->l, p->deposit, p->d_maxbits, p->d_grid, m, p->d_err, st,
                              p->near_on ? p->d_src_cell : nullptr, p->near_on ? p->d_src_q : nullptr,
-                             p->near_pm ? p->d_src_off : nullptr, scatter_here ? Tn.gnear : nullptr, p->U, p->d_near);
+                             p->near_pm ? p->d_src_off : nullptr);
     }
-    p->near_scattered = scatter_here;
     p->near_n = near_entries(p, n_src);
     if (n_src > 0) p->grid_dirty = true;
     RowR2CArgs r{};
@@ -1515,16 +1506,14 @@ static lc_status field_impl(lc_plan* p, int step, float* out, int instant, uint6
         r.scale = (float)(p->U / (double)N3);
         r.tw = p->d_tw;
         const int nslot = step % p->n_ring;
-        // plane grids: the near field is folded inside the inverse plane
-        // kernel, after its scatter (done by the deposit in a step graph,
-        // else here)
+        // plane grids: the near field is scattered first and folded inside
+        // the inverse plane kernel, by the CTA of each target plane
         const bool fold_in_plane = p->ops->plane_c2r && p->near_on && !p->near_pm && p->near_n > 0 && !instant;
-        if (fold_in_plane && !p->near_scattered) {
+        if (fold_in_plane) {
             Phase ph(p, LC_PHASE_NEAR, 1);
             launch_near_scatter(p->d_src_cell, p->d_src_q, p->near_n, p->N, T.gnear, p->d_slot_S, nslot, p->U,
                                 p->d_near, st);
         }
-        p->near_scattered = false;
         if (p->ops->plane_c2r) {
             // y and z together, one CTA per x-plane
             if (fold_in_plane) {
@@ -2014,7 +2003,6 @@ lc_status lc_graph_create(lc_plan* p, int step, int64_t n_src, const double* pos
         p->fuse_x = false;
         if (rs == LC_OK && p->x_deferred >= 0) rs = LC_ERR_INVALID_ARG; // the field did not take the x pass
         p->x_deferred = -1;
-        p->near_scattered = false;
         cudaError_t e2 = cudaStreamEndCapture(cap_stream, &graph);
         if (e == cudaSuccess) e = e2;
     }

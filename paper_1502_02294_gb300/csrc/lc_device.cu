@@ -231,46 +231,62 @@ __global__ void __launch_bounds__(256)
 }
 
 // Small lists (n <= kSmallDeposit) in one launch: every CTA (256 threads)
-// scans all n sources itself for the maximum luminosity (as k_src_prep) and
-// the exact integer total (as the deposit's sum), so no CTA depends on
-// another, then deposits its own kSmallPerCta sources with its first
-// threads; CTA 0 writes the slot's step, unit and total.  The same integers
-// as k_src_prep + k_deposit.
+// reads all n sources itself, at most kSmallPer per thread, all loads in
+// flight at once and kept in registers, for the maximum luminosity (as
+// k_src_prep) and the exact integer total (as the deposit's sum), so no CTA
+// depends on another; then it deposits its own kSmallPerCta sources with
+// its first threads, and CTA 0 writes the slot's step, unit and total.  The
+// same integers as k_src_prep + k_deposit.
 constexpr long long kSmallDeposit = kSmallDepositSources;
-constexpr int kSmallPerCta = 32;
+constexpr int kSmallThreads = 256, kSmallPer = (int)(kSmallDeposit / kSmallThreads), kSmallPerCta = 32;
 
 template <int CIC>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kSmallThreads)
     k_deposit_small(const double* __restrict__ pos, const double* __restrict__ lum, long long n, int N, double l,
                     long long* __restrict__ grid, SlotMeta m, int* err, long long* __restrict__ cell_out,
-                    long long* __restrict__ q_out, double* __restrict__ off_out, const double* __restrict__ gnear,
-                    double U, double* __restrict__ acc) {
-    __shared__ unsigned long long s_max[8];
-    __shared__ long long s_tot[8];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+                    long long* __restrict__ q_out, double* __restrict__ off_out) {
+    static_assert(kSmallPer * kSmallThreads == kSmallDeposit, "the list fits the registers of one CTA");
+    __shared__ unsigned long long s_max[kSmallThreads / 32];
+    __shared__ long long s_tot[kSmallThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double Lv[kSmallPer];
+    bool okv[kSmallPer];
     unsigned long long mx = 0;
-    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
-        const unsigned long long B = (unsigned long long)__double_as_longlong(lum[i]);
-        if (B < 0x7ff0000000000000ULL) mx = max(mx, B); // finite, >= 0 (and -0 counts as 0)
+#pragma unroll
+    for (int k = 0; k < kSmallPer; ++k) {
+        const long long i = threadIdx.x + (long long)k * kSmallThreads;
+        Lv[k] = 0.0;
+        okv[k] = false;
+        if (i < n) {
+            Lv[k] = lum[i];
+            okv[k] = source_ok(Lv[k], pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kSmallPer; ++k) {
+        const long long i = threadIdx.x + (long long)k * kSmallThreads;
+        const unsigned long long B = (unsigned long long)__double_as_longlong(Lv[k]);
+        if (i < n && B < 0x7ff0000000000000ULL) mx = max(mx, B); // finite, >= 0 (and -0 counts as 0)
     }
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (lane == 0) s_max[warp] = mx;
     __syncthreads();
     mx = 0;
-    for (int w = 0; w < nw; ++w) mx = max(mx, s_max[w]);
+#pragma unroll
+    for (int w = 0; w < kSmallThreads / 32; ++w) mx = max(mx, s_max[w]);
     double S, invS;
     fixed_unit(n, mx, S, invS);
     long long tot = 0;
-    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
-        const double L = lum[i];
-        if (source_ok(L, pos[3 * i], pos[3 * i + 1], pos[3 * i + 2])) tot += quantise(L, S, invS);
-    }
+#pragma unroll
+    for (int k = 0; k < kSmallPer; ++k)
+        if (okv[k]) tot += quantise(Lv[k], S, invS);
     for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
     if (lane == 0) s_tot[warp] = tot;
     __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         long long t = 0;
-        for (int w = 0; w < nw; ++w) t += s_tot[w];
+#pragma unroll
+        for (int w = 0; w < kSmallThreads / 32; ++w) t += s_tot[w];
         m.slot_step[m.slot] = m.step;
         m.slot_total[m.slot] = t;
         m.slot_S[m.slot] = S;
@@ -278,24 +294,6 @@ __global__ void __launch_bounds__(256)
     const long long i = (long long)blockIdx.x * kSmallPerCta + threadIdx.x;
     if (threadIdx.x < kSmallPerCta && i < n)
         deposit_source<CIC>(i, pos, lum, N, l, S, invS, grid, err, cell_out, q_out, off_out);
-    if (gnear && cell_out) {
-        // the innermost shell's near cubes of this CTA's sources into the
-        // FP64 accumulator, as k_near_scatter does (the entries were written
-        // above by this CTA's first threads)
-        constexpr int E = CIC ? 8 : 1;
-        __syncthreads();
-        const long long e0 = (long long)blockIdx.x * kSmallPerCta * E;
-        const long long e1 = min(n, (long long)(blockIdx.x + 1) * kSmallPerCta) * E;
-        for (long long it = threadIdx.x; it < (e1 - e0) * kNearCube; it += blockDim.x) {
-            const long long e = e0 + it / kNearCube;
-            const int mm = (int)(it % kNearCube);
-            const long long qs = q_out[e];
-            if (qs == 0) continue;
-            int dx, dy, dz;
-            const long long t = near_target(cell_out[e], mm, N, dx, dy, dz);
-            atomicAdd(acc + t, U * S * (double)qs * gnear[near_wedge(dx, dy, dz)]);
-        }
-    }
 }
 
 // wedge index -> sorted triple a <= b <= c
@@ -634,16 +632,15 @@ void launch_deposit(const double* pos, const double* lum, long long n, int N, do
 
 int launch_slice_deposit(const double* pos, const double* lum, long long n, int N, double l, int deposit,
                          unsigned long long* maxbits, long long* grid, SlotMeta m, int* err, cudaStream_t st,
-                         long long* cell_out, long long* q_out, double* off_out, const double* gnear, double U,
-                         double* acc) {
+                         long long* cell_out, long long* q_out, double* off_out) {
     if (n <= kSmallDeposit) {
         const unsigned blocks = (unsigned)(n > 0 ? (n + kSmallPerCta - 1) / kSmallPerCta : 1);
         if (deposit == LC_DEPOSIT_CIC)
-            launch_k(k_deposit_small<1>, blocks, 256, 0, st, pos, lum, n, N, l, grid, m, err, cell_out, q_out,
-                     (double*)nullptr, gnear, U, acc);
+            launch_k(k_deposit_small<1>, blocks, kSmallThreads, 0, st, pos, lum, n, N, l, grid, m, err, cell_out,
+                     q_out, (double*)nullptr);
         else
-            launch_k(k_deposit_small<0>, blocks, 256, 0, st, pos, lum, n, N, l, grid, m, err, cell_out, q_out,
-                     off_out, gnear, U, acc);
+            launch_k(k_deposit_small<0>, blocks, kSmallThreads, 0, st, pos, lum, n, N, l, grid, m, err, cell_out,
+                     q_out, off_out);
         return 1;
     }
     launch_src_prep(pos, lum, n, maxbits, err, m, st);
