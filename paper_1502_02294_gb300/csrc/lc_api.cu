@@ -1293,14 +1293,15 @@ lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos
     const int slot = step % p->n_ring;
     SlotMeta m{slot, step, p->d_slot_step, p->d_slot_S, p->d_slot_total};
     const long long N = p->N;
-    const lc_plan::Table& Tn = p->tables[step];
     {
-        Phase ph(p, LC_PHASE_DEPOSIT, n_src <= kSmallDepositSources ? 1 : 2);
+        Phase ph(p, LC_PHASE_DEPOSIT, n_src > 0 ? 2 : 1);
         if (memset_before_deposit(p)) e = cudaMemsetAsync(p->d_grid, 0, sizeof(long long) * N * N * N, st);
         if (e != cudaSuccess) return cuda_fail(p, e);
-        launch_slice_deposit(dpos, dlum, n_src, p->N, p->l, p->deposit, p->d_maxbits, p->d_grid, m, p->d_err, st,
-                             p->near_on ? p->d_src_cell : nullptr, p->near_on ? p->d_src_q : nullptr,
-                             p->near_pm ? p->d_src_off : nullptr);
+        launch_src_prep(dpos, dlum, n_src, p->d_maxbits, p->d_err, m, st);
+        if (n_src > 0)
+            launch_deposit(dpos, dlum, n_src, p->N, p->l, p->deposit, p->d_maxbits, p->d_grid, m, p->d_err, st,
+                           p->near_on ? p->d_src_cell : nullptr, p->near_on ? p->d_src_q : nullptr,
+                           p->near_pm ? p->d_src_off : nullptr);
     }
     p->near_n = near_entries(p, n_src);
     if (n_src > 0) p->grid_dirty = true;
@@ -1349,6 +1350,7 @@ lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos
     // leave the x pass to the field's gather MAC when that field follows in
     // the same capture (grids with plane kernels, whose x pass the fused
     // kernel repeats bit for bit)
+    const lc_plan::Table& Tn = p->tables[step];
     if (p->fuse_x && p->capturing && p->ops->plane_r2c && Tn.ghat && Tn.A > 0 && Tn.mac_variant == MAC_GATHER) {
         p->x_deferred = slot;
     } else {
@@ -1506,26 +1508,10 @@ static lc_status field_impl(lc_plan* p, int step, float* out, int instant, uint6
         r.scale = (float)(p->U / (double)N3);
         r.tw = p->d_tw;
         const int nslot = step % p->n_ring;
-        // plane grids: the near field is scattered first and folded inside
-        // the inverse plane kernel, by the CTA of each target plane
-        const bool fold_in_plane = p->ops->plane_c2r && p->near_on && !p->near_pm && p->near_n > 0 && !instant;
-        if (fold_in_plane) {
-            Phase ph(p, LC_PHASE_NEAR, 1);
-            launch_near_scatter(p->d_src_cell, p->d_src_q, p->near_n, p->N, T.gnear, p->d_slot_S, nslot, p->U,
-                                p->d_near, st);
-        }
         if (p->ops->plane_c2r) {
             // y and z together, one CTA per x-plane
-            if (fold_in_plane) {
-                r.near_cell = p->d_src_cell;
-                r.near_q = p->d_src_q;
-                r.near_n = p->near_n;
-                r.near_acc = p->d_near;
-                r.near_grid = p->d_grid;
-            }
             Phase ph(p, LC_PHASE_C2R_Z, 1);
             p->ops->plane_c2r(r, st);
-            if (fold_in_plane) p->grid_dirty = false; // the fold cleared the deposit cells
         } else {
             {
                 Phase ph(p, LC_PHASE_INV_Y, 1);
@@ -1535,7 +1521,7 @@ static lc_status field_impl(lc_plan* p, int step, float* out, int instant, uint6
             Phase ph(p, LC_PHASE_C2R_Z, 1);
             p->ops->rows_c2r(r, st);
         }
-        if (p->near_on && p->near_n > 0 && !fold_in_plane) {
+        if (p->near_on && p->near_n > 0) {
             // innermost shell's near cube, summed exactly in FP64 and folded in
             Phase ph(p, LC_PHASE_NEAR, 2);
             if (p->near_pm) {
@@ -2243,7 +2229,9 @@ lc_status lc_deposit_grid(int n, double box, int deposit, int64_t n_src, const d
     if (e == cudaSuccess) e = cudaMemsetAsync(derr, 0, sizeof(int), st);
     SlotMeta m{0, 0, dstep, dS, dtot};
     if (e == cudaSuccess) {
-        count_launch(launch_slice_deposit(dpos, dlum, n_src, n, box / n, deposit, dmax, dgrid, m, derr, st));
+        launch_src_prep(dpos, dlum, n_src, dmax, derr, m, st);
+        if (n_src > 0) launch_deposit(dpos, dlum, n_src, n, box / n, deposit, dmax, dgrid, m, derr, st);
+        count_launch(n_src > 0 ? 2 : 1);
         e = cudaGetLastError();
     }
     long long tot = 0;

@@ -112,114 +112,76 @@ __device__ __forceinline__ void split_share(long long q, double f, long long& lo
     lo = q - h;
 }
 
-// The target cell of displacement m of the 5^3 near cube around cell c
-// (periodic), with the displacement.
-__device__ __forceinline__ long long near_target(long long c, int m, int N, int& dx, int& dy, int& dz) {
-    dx = m / (kNearSide * kNearSide) - kNearR;
-    dy = (m / kNearSide) % kNearSide - kNearR;
-    dz = m % kNearSide - kNearR;
-    const long long NN = (long long)N * N;
-    const int ix = (int)(c / NN), iy = (int)((c / N) % N), iz = (int)(c % N);
-    const int tx = (ix + dx + N) % N, ty = (iy + dy + N) % N, tz = (iz + dz + N) % N;
-    return ((long long)tx * N + ty) * N + tz;
-}
-
-// The fixed-point unit S of a slice (a power of two: n * lmax < 2^62 S) and
-// 1/S where that is a normal number (0 otherwise: divide by S instead).
-// L / S for a power of two S is the exact L 2^(62-E) rounded once, so the
-// product with 1/S is the same double.
-__device__ __forceinline__ void fixed_unit(long long n, unsigned long long maxbits, double& S, double& invS) {
-    const double lmax = __longlong_as_double((long long)maxbits);
-    S = 1.0;
-    invS = 1.0;
-    if (lmax > 0.0) {
-        int E;
-        frexp(__dmul_rn((double)n, lmax), &E);
-        S = ldexp(1.0, E - 62);
-        invS = (E - 62 > -1022 && E - 62 < 1022) ? ldexp(1.0, 62 - E) : 0.0;
-    }
-}
-
-__device__ __forceinline__ long long quantise(double L, double S, double invS) {
-    return llrint(invS != 0.0 ? __dmul_rn(L, invS) : __ddiv_rn(L, S));
-}
-
-__device__ __forceinline__ bool source_ok(double L, double x, double y, double z) {
-    return finite_d(L) && L >= 0.0 && finite_d(x) && finite_d(y) && finite_d(z);
-}
-
-// Deposit source i with unit S: the grid atomics and the near-field list
-// entries (NGP: one cell; CIC: the 8 shares, split along x, then y, then z);
-// returns its integer charge q (0 for a source left out as invalid, which
-// sets *err).
-template <int CIC>
-__device__ __forceinline__ long long deposit_source(long long i, const double* __restrict__ pos,
-                                                    const double* __restrict__ lum, int N, double l, double S,
-                                                    double invS, long long* __restrict__ grid, int* err,
-                                                    long long* __restrict__ cell_out, long long* __restrict__ q_out,
-                                                    double* __restrict__ off_out) {
-    long long q = 0;
-    const double L = lum[i];
-    const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
-    const bool ok = source_ok(L, x, y, z);
-    if (!ok) atomicOr(err, 1); // an invalid source is left out and reported
-    if constexpr (CIC) {
-        long long cx[2] = {0, 0}, cy[2] = {0, 0}, cz[2] = {0, 0};
-        long long sh[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        if (ok) {
-            q = quantise(L, S, invS);
-            double fx, fy, fz;
-            cic_axis(x, l, N, cx[0], cx[1], fx);
-            cic_axis(y, l, N, cy[0], cy[1], fy);
-            cic_axis(z, l, N, cz[0], cz[1], fz);
-            long long qx[2], qxy[4];
-            split_share(q, fx, qx[0], qx[1]);
-            for (int a = 0; a < 2; ++a) split_share(qx[a], fy, qxy[2 * a], qxy[2 * a + 1]);
-            for (int ab = 0; ab < 4; ++ab) split_share(qxy[ab], fz, sh[2 * ab], sh[2 * ab + 1]);
-        }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const long long c = (cx[k >> 2] * N + cy[(k >> 1) & 1]) * N + cz[k & 1];
-            if (sh[k]) atomicAdd(reinterpret_cast<unsigned long long*>(grid + c), (unsigned long long)sh[k]);
-            if (cell_out) {
-                cell_out[8 * i + k] = c;
-                q_out[8 * i + k] = sh[k];
-            }
-        }
-    } else {
-        long long c = 0;
-        if (ok) {
-            q = quantise(L, S, invS);
-            c = (ngp_cell(x, l, N) * N + ngp_cell(y, l, N)) * N + ngp_cell(z, l, N);
-            if (q) atomicAdd(reinterpret_cast<unsigned long long*>(grid + c), (unsigned long long)q);
-        }
-        if (cell_out) {
-            cell_out[i] = c;
-            q_out[i] = q;
-        }
-    }
-    if (off_out) {
-        // the source relative to its cell centre, in [-l/2, l/2) per axis
-        const double p3[3] = {x, y, z};
-        for (int d = 0; d < 3; ++d) {
-            const double t = p3[d] / l + 0.5;
-            off_out[3 * i + d] = finite_d(t) ? (t - floor(t) - 0.5) * l : 0.0;
-        }
-    }
-    return q;
-}
-
 template <int CIC>
 __global__ void __launch_bounds__(256)
     k_deposit(const double* __restrict__ pos, const double* __restrict__ lum, long long n, int N, double l,
               const unsigned long long* __restrict__ maxbits, long long* __restrict__ grid, SlotMeta m, int* err,
               long long* __restrict__ cell_out, long long* __restrict__ q_out, double* __restrict__ off_out) {
     __shared__ long long s_sum[8];
-    double S, invS;
-    fixed_unit(n, *maxbits, S, invS);
+    const double lmax = __longlong_as_double((long long)*maxbits);
+    double S = 1.0, invS = 1.0;
+    if (lmax > 0.0) {
+        int E;
+        frexp(__dmul_rn((double)n, lmax), &E);
+        S = ldexp(1.0, E - 62);
+        // L / S for a power of two S is the exact L 2^(62-E) rounded once, so
+        // the product with 1/S is the same double whenever 1/S is a normal
+        // number (E - 62 within the normal exponent range both ways)
+        invS = (E - 62 > -1022 && E - 62 < 1022) ? ldexp(1.0, 62 - E) : 0.0;
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) m.slot_S[m.slot] = S;
+    long long q = 0;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    long long q = i < n ? deposit_source<CIC>(i, pos, lum, N, l, S, invS, grid, err, cell_out, q_out, off_out) : 0;
+    if (i < n) {
+        const double L = lum[i];
+        const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+        const bool ok = finite_d(L) && L >= 0.0 && finite_d(x) && finite_d(y) && finite_d(z);
+        if (!ok) atomicOr(err, 1); // an invalid source is left out and reported
+        if constexpr (CIC) {
+            long long cx[2] = {0, 0}, cy[2] = {0, 0}, cz[2] = {0, 0};
+            long long sh[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            if (ok) {
+                q = llrint(invS != 0.0 ? __dmul_rn(L, invS) : __ddiv_rn(L, S));
+                double fx, fy, fz;
+                cic_axis(x, l, N, cx[0], cx[1], fx);
+                cic_axis(y, l, N, cy[0], cy[1], fy);
+                cic_axis(z, l, N, cz[0], cz[1], fz);
+                // split along x, then each part along y, then each of those along z
+                long long qx[2], qxy[4];
+                split_share(q, fx, qx[0], qx[1]);
+                for (int a = 0; a < 2; ++a) split_share(qx[a], fy, qxy[2 * a], qxy[2 * a + 1]);
+                for (int ab = 0; ab < 4; ++ab) split_share(qxy[ab], fz, sh[2 * ab], sh[2 * ab + 1]);
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const long long c = (cx[k >> 2] * N + cy[(k >> 1) & 1]) * N + cz[k & 1];
+                if (sh[k]) atomicAdd(reinterpret_cast<unsigned long long*>(grid + c), (unsigned long long)sh[k]);
+                if (cell_out) {
+                    cell_out[8 * i + k] = c;
+                    q_out[8 * i + k] = sh[k];
+                }
+            }
+        } else {
+            long long c = 0;
+            if (ok) {
+                q = llrint(invS != 0.0 ? __dmul_rn(L, invS) : __ddiv_rn(L, S));
+                c = (ngp_cell(x, l, N) * N + ngp_cell(y, l, N)) * N + ngp_cell(z, l, N);
+                if (q) atomicAdd(reinterpret_cast<unsigned long long*>(grid + c), (unsigned long long)q);
+            }
+            if (cell_out) {
+                cell_out[i] = c;
+                q_out[i] = q;
+            }
+        }
+        if (off_out) {
+            // the source relative to its cell centre, in [-l/2, l/2) per axis
+            const double p3[3] = {x, y, z};
+            for (int d = 0; d < 3; ++d) {
+                const double t = p3[d] / l + 0.5;
+                off_out[3 * i + d] = finite_d(t) ? (t - floor(t) - 0.5) * l : 0.0;
+            }
+        }
+    }
     for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
     if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = q;
     __syncthreads();
@@ -228,72 +190,6 @@ __global__ void __launch_bounds__(256)
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_sum[w];
         if (t) atomicAdd(reinterpret_cast<unsigned long long*>(m.slot_total + m.slot), (unsigned long long)t);
     }
-}
-
-// Small lists (n <= kSmallDeposit) in one launch: every CTA (256 threads)
-// reads all n sources itself, at most kSmallPer per thread, all loads in
-// flight at once and kept in registers, for the maximum luminosity (as
-// k_src_prep) and the exact integer total (as the deposit's sum), so no CTA
-// depends on another; then it deposits its own kSmallPerCta sources with
-// its first threads, and CTA 0 writes the slot's step, unit and total.  The
-// same integers as k_src_prep + k_deposit.
-constexpr long long kSmallDeposit = kSmallDepositSources;
-constexpr int kSmallThreads = 256, kSmallPer = (int)(kSmallDeposit / kSmallThreads), kSmallPerCta = 32;
-
-template <int CIC>
-__global__ void __launch_bounds__(kSmallThreads)
-    k_deposit_small(const double* __restrict__ pos, const double* __restrict__ lum, long long n, int N, double l,
-                    long long* __restrict__ grid, SlotMeta m, int* err, long long* __restrict__ cell_out,
-                    long long* __restrict__ q_out, double* __restrict__ off_out) {
-    static_assert(kSmallPer * kSmallThreads == kSmallDeposit, "the list fits the registers of one CTA");
-    __shared__ unsigned long long s_max[kSmallThreads / 32];
-    __shared__ long long s_tot[kSmallThreads / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double Lv[kSmallPer];
-    bool okv[kSmallPer];
-    unsigned long long mx = 0;
-#pragma unroll
-    for (int k = 0; k < kSmallPer; ++k) {
-        const long long i = threadIdx.x + (long long)k * kSmallThreads;
-        Lv[k] = 0.0;
-        okv[k] = false;
-        if (i < n) {
-            Lv[k] = lum[i];
-            okv[k] = source_ok(Lv[k], pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]);
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < kSmallPer; ++k) {
-        const long long i = threadIdx.x + (long long)k * kSmallThreads;
-        const unsigned long long B = (unsigned long long)__double_as_longlong(Lv[k]);
-        if (i < n && B < 0x7ff0000000000000ULL) mx = max(mx, B); // finite, >= 0 (and -0 counts as 0)
-    }
-    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) s_max[warp] = mx;
-    __syncthreads();
-    mx = 0;
-#pragma unroll
-    for (int w = 0; w < kSmallThreads / 32; ++w) mx = max(mx, s_max[w]);
-    double S, invS;
-    fixed_unit(n, mx, S, invS);
-    long long tot = 0;
-#pragma unroll
-    for (int k = 0; k < kSmallPer; ++k)
-        if (okv[k]) tot += quantise(Lv[k], S, invS);
-    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-    if (lane == 0) s_tot[warp] = tot;
-    __syncthreads();
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        long long t = 0;
-#pragma unroll
-        for (int w = 0; w < kSmallThreads / 32; ++w) t += s_tot[w];
-        m.slot_step[m.slot] = m.step;
-        m.slot_total[m.slot] = t;
-        m.slot_S[m.slot] = S;
-    }
-    const long long i = (long long)blockIdx.x * kSmallPerCta + threadIdx.x;
-    if (threadIdx.x < kSmallPerCta && i < n)
-        deposit_source<CIC>(i, pos, lum, N, l, S, invS, grid, err, cell_out, q_out, off_out);
 }
 
 // wedge index -> sorted triple a <= b <= c
@@ -420,6 +316,15 @@ __global__ void k_near_prep(const double* gw0, const double* scale0, double* gne
     *g0_far -= sum;
 }
 
+__device__ __forceinline__ long long near_target(long long c, int m, int N, int& dx, int& dy, int& dz) {
+    dx = m / (kNearSide * kNearSide) - kNearR;
+    dy = (m / kNearSide) % kNearSide - kNearR;
+    dz = m % kNearSide - kNearR;
+    const long long NN = (long long)N * N;
+    const int ix = (int)(c / NN), iy = (int)((c / N) % N), iz = (int)(c % N);
+    const int tx = (ix + dx + N) % N, ty = (iy + dy + N) % N, tz = (iz + dz + N) % N;
+    return ((long long)tx * N + ty) * N + tz;
+}
 
 __global__ void __launch_bounds__(256) k_near_scatter(const long long* __restrict__ cell, const long long* __restrict__ q,
                                                       long long n, int N, const double* __restrict__ gnear,
@@ -628,24 +533,6 @@ void launch_deposit(const double* pos, const double* lum, long long n, int N, do
     else
         launch_k(k_deposit<0>, (unsigned)blocks, tb, 0, st, pos, lum, n, N, l, maxbits, grid, m, err, cell_out, q_out,
                  off_out);
-}
-
-int launch_slice_deposit(const double* pos, const double* lum, long long n, int N, double l, int deposit,
-                         unsigned long long* maxbits, long long* grid, SlotMeta m, int* err, cudaStream_t st,
-                         long long* cell_out, long long* q_out, double* off_out) {
-    if (n <= kSmallDeposit) {
-        const unsigned blocks = (unsigned)(n > 0 ? (n + kSmallPerCta - 1) / kSmallPerCta : 1);
-        if (deposit == LC_DEPOSIT_CIC)
-            launch_k(k_deposit_small<1>, blocks, kSmallThreads, 0, st, pos, lum, n, N, l, grid, m, err, cell_out,
-                     q_out, (double*)nullptr);
-        else
-            launch_k(k_deposit_small<0>, blocks, kSmallThreads, 0, st, pos, lum, n, N, l, grid, m, err, cell_out,
-                     q_out, off_out);
-        return 1;
-    }
-    launch_src_prep(pos, lum, n, maxbits, err, m, st);
-    launch_deposit(pos, lum, n, N, l, deposit, maxbits, grid, m, err, st, cell_out, q_out, off_out);
-    return 2;
 }
 
 // f_diff = (J_instant - J) / J, the difference taken and divided in FP64 and

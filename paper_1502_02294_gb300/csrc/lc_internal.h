@@ -74,15 +74,6 @@ void launch_src_prep(const double* pos, const double* lum, long long n, unsigned
 void launch_deposit(const double* pos, const double* lum, long long n, int N, double l, int deposit,
                     const unsigned long long* maxbits, long long* grid, SlotMeta m, int* err, cudaStream_t st,
                     long long* cell_out = nullptr, long long* q_out = nullptr, double* off_out = nullptr);
-// Lists up to this long are deposited in one launch (launch_slice_deposit).
-constexpr long long kSmallDepositSources = 2048;
-// The whole slice: source check, fixed-point unit, slot metadata and deposit.
-// Up to 2,048 sources in one launch (each CTA scans every source for the unit
-// and the total itself), else launch_src_prep + launch_deposit; returns the
-// number of kernels launched.
-int launch_slice_deposit(const double* pos, const double* lum, long long n, int N, double l, int deposit,
-                         unsigned long long* maxbits, long long* grid, SlotMeta m, int* err, cudaStream_t st,
-                         long long* cell_out = nullptr, long long* q_out = nullptr, double* off_out = nullptr);
 
 // Near field of the innermost shell (displacements |d|_inf <= R), which the
 // FFT path leaves out: gnear holds the shell's FP64 values on the wedge prefix

@@ -84,55 +84,7 @@ struct RowC2RArgs {
     float* out;
     float scale;
     const float2* tw;
-    // plane kernels: fold the innermost shell's near field (already
-    // scattered into near_acc) into the CTA's own plane of `out` after its
-    // stores, and clear the entries' deposit cells there (near_n = 0: none)
-    const long long* near_cell;
-    const long long* near_q;
-    long long near_n;
-    double* near_acc;
-    long long* near_grid;
 };
-
-// The near-field fold of one x-plane, run by a plane kernel's CTA after it
-// has stored the plane (its own stores are visible to it after a barrier):
-// the near-list entries whose 5^3 cube meets plane x are compacted into
-// shared memory (in chunks of `cap`), then each of their 25 cells in the
-// plane takes the whole FP64 sum the scatter left there (atomic exchange,
-// so overlapping cubes add it once) into out with one rounding; an entry
-// whose centre lies in the plane also clears its deposit cell.
-template <int N, int NT>
-__device__ __forceinline__ void near_fold_plane(const RowC2RArgs& a, int x, int* s_list, int cap) {
-    constexpr int R = kNearR, SIDE = 2 * R + 1;
-    constexpr long long NN = (long long)N * N;
-    __shared__ int s_cnt;
-    for (long long base = 0; base < a.near_n; base += cap) {
-        const long long end = base + cap < a.near_n ? base + cap : a.near_n;
-        __syncthreads(); // the plane's stores (first chunk), or the previous chunk's work, are done
-        if (threadIdx.x == 0) s_cnt = 0;
-        __syncthreads();
-        for (long long e = base + threadIdx.x; e < end; e += NT) {
-            if (a.near_q[e] == 0) continue;
-            int dx = x - (int)(a.near_cell[e] / NN);
-            dx = dx > N / 2 ? dx - N : (dx < -N / 2 ? dx + N : dx);
-            if (dx >= -R && dx <= R) s_list[atomicAdd(&s_cnt, 1)] = (int)(e - base);
-        }
-        __syncthreads();
-        const int cnt = s_cnt;
-        for (int it = threadIdx.x; it < cnt * SIDE * SIDE; it += NT) {
-            const long long e = base + s_list[it / (SIDE * SIDE)];
-            const int o = it % (SIDE * SIDE), dy = o / SIDE - R, dz = o % SIDE - R;
-            const long long c = a.near_cell[e];
-            const int cy = (int)((c / N) % N), cz = (int)(c % N);
-            const int ty = (cy + dy + N) % N, tz = (cz + dz + N) % N;
-            const long long t = (long long)x * NN + (long long)ty * N + tz;
-            if (dy == 0 && dz == 0 && (int)(c / NN) == x && a.near_grid) a.near_grid[c] = 0;
-            const double v = __longlong_as_double(
-                (long long)atomicExch(reinterpret_cast<unsigned long long*>(a.near_acc + t), 0ULL));
-            if (v != 0.0) a.out[t] = (float)((double)a.out[t] + v);
-        }
-    }
-}
 
 constexpr int kMaxShells = 1024;
 
@@ -1433,10 +1385,6 @@ __global__ void __launch_bounds__(plane_threads_of(N)) k_plane_c2r(RowC2RArgs a)
         const float2 w = pl[t * H + (y >> 1)];
         a.out[((long long)x * N + y) * N + t] = ((y & 1) ? w.y : w.x) * a.scale;
     }
-    if (a.near_n > 0) {
-        __syncthreads(); // the plane buffer is free for the entry list
-        near_fold_plane<N, NT>(a, x, reinterpret_cast<int*>(pl), (int)(2 * (size_t)N * H));
-    }
 }
 
 // ------------------------------------------------------------------------
@@ -1689,10 +1637,6 @@ __global__ void __launch_bounds__(plane_lanes_threads<N>()) k_plane_c2r_lanes(Ro
                 }
             }
         }
-    }
-    if (a.near_n > 0) {
-        __syncthreads(); // every pair's exchange is done: the plane buffer is free for the entry list
-        near_fold_plane<N, NT>(a, x, reinterpret_cast<int*>(pl), 2 * N * PS);
     }
 }
 
