@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(kThreads) k_rows_r2c(RowR2CArgs a, int nblocks
 // y or x pass over one N x CW tile (CW consecutive r-columns of one line, or
 // CW Nyquist columns of CW lines).  NT = N * CW / 8 threads, 8 elements each.
 template <int N, int DIR, int IN, int OUT>
-__global__ void __launch_bounds__(col_threads_of(N)) k_cols(ColArgs a) {
+__global__ void __launch_bounds__(col_threads_of(N), (N <= 128 ? 3 : 1)) k_cols(ColArgs a) {
     constexpr bool BFR = IN == COL_IN_MAC_BF16 || IN == COL_IN_MAC_BF16_X; // BF16 ring
     constexpr bool FWDX = IN == COL_IN_MAC_F32_X || IN == COL_IN_MAC_BF16_X;
     constexpr int NT = col_threads_of(N);
