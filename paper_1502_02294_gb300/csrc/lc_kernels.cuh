@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(kThreads) k_rows_r2c(RowR2CArgs a, int nblocks
 // y or x pass over one N x CW tile (CW consecutive r-columns of one line, or
 // CW Nyquist columns of CW lines).  NT = N * CW / 8 threads, 8 elements each.
 template <int N, int DIR, int IN, int OUT>
-__global__ void __launch_bounds__(col_threads_of(N), (N <= 128 ? 3 : 1)) k_cols(ColArgs a) {
+__global__ void __launch_bounds__(col_threads_of(N)) k_cols(ColArgs a) {
     constexpr bool BFR = IN == COL_IN_MAC_BF16 || IN == COL_IN_MAC_BF16_X; // BF16 ring
     constexpr bool FWDX = IN == COL_IN_MAC_F32_X || IN == COL_IN_MAC_BF16_X;
     constexpr int NT = col_threads_of(N);
@@ -1580,8 +1580,13 @@ __global__ void __launch_bounds__(plane_lanes_threads<N>()) k_plane_c2r_lanes(Ro
         for (int k2 = 0; k2 < G; ++k2) pl[(k1 * G + k2) * PS + c] = w[k2]; // Y[k1 + R1 k2]
     }
     __syncthreads();
+    static_assert(R1 % 2 == 0 && P == G * (R1 / 2), "pairs as (residue, block)");
     for (int u0 = warp * PW; u0 < P; u0 += (NT / 32) * PW) {
-        const int u = u0 + grp;
+        // group T takes pair u = (T mod G) R1/2 + T / G: the lane groups of a
+        // warp then read plane rows one apart (rows (y mod R1) G + y / R1), not
+        // 16 apart, which would put all of them on the same banks
+        const int T = u0 + grp;
+        const int u = (T % G) * (R1 / 2) + T / G;
         // the plane rows of y = 2u and 2u + 1
         float2* xa = pl + (((2 * u) % R1) * G + (2 * u) / R1) * PS;
         float2* xb = pl + (((2 * u + 1) % R1) * G + (2 * u + 1) / R1) * PS;
