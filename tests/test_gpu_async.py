@@ -142,3 +142,38 @@ def test_poll_completes_each_ticket_in_order_over_many_tickets():
         assert np.allclose(pinned[s % nbuf].numpy(), ref, rtol=1e-6, atol=1e-6 * np.abs(ref).max()), s
     a.close()
     b.close()
+
+
+def test_copy_engine_path_equals_copy_kernel_path():
+    # page-locked outputs go through a small copy kernel by default and
+    # through the copy engine with LC_D2H=ce (read once per process): a
+    # child process with each setting gives the same bytes (no near split,
+    # whose FP64 atomics may sum in another order in another process)
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = (
+        "import sys, numpy as np, torch, paper_1502_02294_gb300 as lc, synth\n"
+        "w = synth.small(n=32, box=60.0, n_steps=6, n_src=120, seed=2721, clustered=True)\n"
+        "p = lc.Plan.from_workload(w, near_mode=lc.NEAR_NONE)\n"
+        "outs = [torch.empty((32,) * 3, dtype=torch.float32).pin_memory() for _ in range(6)]\n"
+        "ts = []\n"
+        "for s in range(6):\n"
+        "    pos, lum = w.cat.active(s)\n"
+        "    p.push(s, pos, lum)\n"
+        "    ts.append(p.field_async(s, outs[s]))\n"
+        "p.wait(ts[-1])\n"
+        "np.save(sys.argv[1], np.stack([o.numpy() for o in outs]))\n")
+    import tempfile
+
+    res = {}
+    with tempfile.TemporaryDirectory() as d:
+        for mode in ("sm", "ce"):
+            env = dict(os.environ, LC_D2H=mode, PYTHONPATH=root)
+            path = os.path.join(d, f"{mode}.npy")
+            subprocess.run([sys.executable, "-c", code, path], check=True, env=env, cwd=root, timeout=600)
+            res[mode] = np.load(path)
+    assert np.isfinite(res["sm"]).all() and np.abs(res["sm"]).max() > 0
+    assert np.array_equal(res["sm"], res["ce"])
