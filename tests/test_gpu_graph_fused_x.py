@@ -4,6 +4,8 @@ slice's tile, stores it to its ring slot and uses it as lookback 0.  Graph
 replays over many steps (each step reading ring slots the fused kernel
 wrote) equal the eager push + field bit for bit, FP32 and BF16 history, and
 the fields match the FP64 oracle."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -28,13 +30,15 @@ def ulp32(x):
     return np.exp2(np.floor(np.log2(np.maximum(a, np.finfo(np.float32).tiny))) - 23)
 
 
-@pytest.mark.parametrize("n,hist", [(32, synth.HISTORY_FP32), (64, synth.HISTORY_BF16), (128, synth.HISTORY_FP32),
-                                    (96, synth.HISTORY_BF16)])
+@pytest.mark.parametrize("n,hist,dep", [(32, synth.HISTORY_FP32, lc.DEPOSIT_NGP), (64, synth.HISTORY_BF16, lc.DEPOSIT_NGP),
+                                        (128, synth.HISTORY_FP32, lc.DEPOSIT_NGP), (96, synth.HISTORY_BF16, lc.DEPOSIT_NGP),
+                                        (64, synth.HISTORY_FP32, lc.DEPOSIT_CIC)])
 @pytest.mark.parametrize("near", [lc.NEAR_NONE, lc.NEAR_NGP])
-def test_graph_with_fused_x_pass_equals_eager(monkeypatch, n, hist, near):
+def test_graph_with_fused_x_pass_equals_eager(monkeypatch, n, hist, dep, near):
     monkeypatch.setenv("LC_MAC_VARIANT", "gather")
     steps = 8
     w = synth.small(n=n, box=0.78125 * n, n_steps=steps, n_src=200, seed=4100 + n, clustered=True, history=hist)
+    w = dataclasses.replace(w, deposit=dep)
     eager = lc.Plan.from_workload(w, near_mode=near)
     graph = lc.Plan.from_workload(w, near_mode=near)
     graph.prepare(0, steps)
