@@ -1401,6 +1401,21 @@ __global__ void __launch_bounds__(plane_threads_of(N)) k_plane_c2r(RowC2RArgs a)
 // straight to global memory.  This moves about a third of the shared-memory
 // bytes of the staged plane kernels (no staging of the input, no
 // Stockham stage round trips).
+// Item `it` of a y stage over the H = N/2 + 1 columns and `rows` rows: the
+// N/2 regular columns first, row by row (whole warps per row from N = 64,
+// so a warp's accesses stay in one row), then the Nyquist column (c = N/2).
+template <int N>
+__device__ __forceinline__ void plane_item(int it, int rows, int& c, int& r) {
+    constexpr int M = N / 2;
+    if (it < M * rows) {
+        c = it % M;
+        r = it / M;
+    } else {
+        c = M;
+        r = it - M * rows;
+    }
+}
+
 template <int N> __host__ __device__ constexpr bool plane_lanes_ok() {
     return N == 32 || N == 64 || N == 96 || N == 128 || N == 192;
 }
@@ -1512,7 +1527,8 @@ __global__ void __launch_bounds__(plane_lanes_threads<N>()) k_plane_r2c_lanes(Ro
     }
     __syncthreads();
     for (int it = threadIdx.x; it < H * G; it += NT) {
-        const int c = it % H, r = it / H;
+        int c, r;
+        plane_item<N>(it, G, c, r);
         float2 v[16];
 #pragma unroll
         for (int p = 0; p < R1; ++p) v[p] = pl[(r + G * p) * PS + c];
@@ -1524,7 +1540,8 @@ __global__ void __launch_bounds__(plane_lanes_threads<N>()) k_plane_r2c_lanes(Ro
     }
     __syncthreads();
     for (int it = threadIdx.x; it < H * R1; it += NT) {
-        const int c = it % H, k1 = it / H;
+        int c, k1;
+        plane_item<N>(it, R1, c, k1);
         float2 w[G];
 #pragma unroll
         for (int r = 0; r < G; ++r) w[r] = pl[(k1 * G + r) * PS + c];
@@ -1555,7 +1572,8 @@ __global__ void __launch_bounds__(plane_lanes_threads<N>()) k_plane_c2r_lanes(Ro
     for (int i = threadIdx.x; i < N; i += NT) tw[i] = a.tw[i];
     __syncthreads();
     for (int it = threadIdx.x; it < H * G; it += NT) {
-        const int c = it % H, r = it / H;
+        int c, r;
+        plane_item<N>(it, G, c, r);
         float2 v[16];
 #pragma unroll
         for (int p = 0; p < R1; ++p) v[p] = a.src[((long long)x * N + (r + G * p)) * NRP + c];
@@ -1571,7 +1589,8 @@ __global__ void __launch_bounds__(plane_lanes_threads<N>()) k_plane_c2r_lanes(Ro
     }
     __syncthreads();
     for (int it = threadIdx.x; it < H * R1; it += NT) {
-        const int c = it % H, k1 = it / H;
+        int c, k1;
+        plane_item<N>(it, R1, c, k1);
         float2 w[G];
 #pragma unroll
         for (int r = 0; r < G; ++r) w[r] = pl[(k1 * G + r) * PS + c];
