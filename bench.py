@@ -662,7 +662,13 @@ def run_serving(args):
                        "poisson_p50_without_admission_wait": pois["p50_ms_without_admission_wait"],
                        "poisson_p99_without_admission_wait": pois["p99_ms_without_admission_wait"],
                        "poisson_service_p50": pois["service_p50_ms"], "poisson_service_p99": pois["service_p99_ms"],
-                       "poisson_by_grid": pois["by_grid"]},
+                       "poisson_by_grid": pois["by_grid"],
+                       # the mix spans about 20x in service time (128^3 to 512^3), so the
+                       # overall p99/p50 compares different request sizes; per grid size:
+                       "poisson_p99_over_p50_by_grid": {n: (g["p99_ms"] / g["p50_ms"]) if g["p50_ms"] else None
+                                                        for n, g in pois["by_grid"].items()},
+                       "poisson_p99_over_p50_by_grid_max": max((g["p99_ms"] / g["p50_ms"])
+                                                               for g in pois["by_grid"].values() if g["p50_ms"])},
         "poisson_fields_per_s": pois["fields_per_s"],
         "plain_fp32_one_instance": {"fields_per_s": plain_rate, "seconds": plain_s,
                                     "served_over_plain": value / world / plain_rate,
