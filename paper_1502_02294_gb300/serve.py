@@ -91,8 +91,8 @@ class Server:
     tables (lc_plan_set_table_budget), building later ones when their step
     is served.  retain: keep simulations admitted after their last request
     (rewind() then serves the same steps again).  priorities: each
-    simulation's stream gets a CUDA stream priority by grid size (the
-    highest up to 192^3, the middle one at 256^3, the lowest above), so short
+    simulation's stream gets a CUDA stream priority by grid size (four
+    tiers: up to 192^3, 256^3, 384^3, larger), so short
     requests of small grids are not queued behind the blocks of large ones;
     False gives every stream the default priority."""
 
@@ -142,7 +142,10 @@ class Server:
         lo, hi = self.torch.cuda.Stream.priority_range() if hasattr(self.torch.cuda.Stream, "priority_range") \
             else (0, -1)
         n = sim.workload.n
-        prio = hi if n <= 192 else (lo + hi) // 2 if n <= 256 else lo
+        # four tiers by grid size, i.e. by service time: up to 192^3, 256^3,
+        # 384^3, larger (CUDA: the lower number is the higher priority)
+        tier = 0 if n <= 192 else 1 if n <= 256 else 2 if n <= 384 else 3
+        prio = hi + int(round((lo - hi) * tier / 3))
         return self.torch.cuda.Stream(priority=prio)
 
     def _admit(self):
