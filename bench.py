@@ -60,6 +60,8 @@ WORKLOADS = {
             "BF16 history (profiling size of the c3 path)"),
     "c5s": ("512^3 grid, 400 Mpc box, 16 equal-conformal-time shells, 24 steps, 4e4 clustered sources, BF16 history "
             "(profiling size of the served 512^3 path)"),
+    "c5m": ("384^3 grid, 300 Mpc box, 16 equal-conformal-time shells, 24 steps, 3e4 clustered sources, BF16 history "
+            "(profiling size of the served 384^3 path)"),
     "c4": ("16 uneven instances (grids 64..256 cycled, 32..128 shells, 1e3..1e5 clustered sources, 0.78 Mpc "
            "cells), FP32, all instances' step in one CUDA graph replay (parallel branches)"),
 }
@@ -746,7 +748,7 @@ def mac_traffic(workload):
     return t["bytes"], t["from"]
 
 
-DEFAULT_STEPS = {"c1": 2048, "c2": 2048, "c3": 64, "c3s": 32, "c5s": 16, "c4": 32, "c5": 20}
+DEFAULT_STEPS = {"c1": 2048, "c2": 2048, "c3": 64, "c3s": 32, "c5s": 16, "c5m": 16, "c4": 32, "c5": 20}
 
 
 # ---------------------------------------------------------------- single instance (c1, c2, c3, c3s)
@@ -1103,7 +1105,7 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     import synth
 
-    w = synth.config(args.workload) if args.workload in ("c1", "c2", "c3", "c3s", "c5s") else None
+    w = synth.config(args.workload) if args.workload in ("c1", "c2", "c3", "c3s", "c5s", "c5m") else None
     variant = {}
     if w is not None:
         if args.kernel == "exp":

@@ -182,6 +182,13 @@ def config(name: str) -> Workload:
         cat = make_catalogue(SEED_BASE + 78, 40_000, 400.0, 24, clustered=True,
                              n_centres=400, sigma=2.0)
         return Workload("c5s", 512, 400.0, 0.31, 0.68, st, 4, HISTORY_BF16, cat)
+    if name == "c5m":
+        # the 384^3 BF16 path of the serving set at a profiling size: 16
+        # equal-conformal-time shells (ring ~1.8 GB), 24 steps, 3e4 clustered sources
+        st = StepSpec(STEPS_EQUAL_TAU, 24, z_end=15.0, n_shell=16)
+        cat = make_catalogue(SEED_BASE + 79, 30_000, 300.0, 24, clustered=True,
+                             n_centres=300, sigma=2.0)
+        return Workload("c5m", 384, 300.0, 0.31, 0.68, st, 4, HISTORY_BF16, cat)
     raise KeyError(name)
 
 
