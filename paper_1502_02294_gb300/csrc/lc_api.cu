@@ -241,6 +241,10 @@ struct lc_plan {
     ColsMaps maps; // tensor maps of d_work for the TMA column passes
     int* d_err = nullptr;
     unsigned long long* d_maxbits = nullptr;
+    // push counter and, per grid row, the counter of its last deposit (the
+    // z pass skips rows without a share of the current push)
+    unsigned* d_stamp = nullptr;
+    unsigned* d_rowstamp = nullptr;
     double* d_pos = nullptr;
     double* d_lum = nullptr;
     long long src_cap = 0;
@@ -444,6 +448,8 @@ void free_all(lc_plan* p) {
     cudaFree(p->d_tw);
     cudaFree(p->d_err);
     cudaFree(p->d_maxbits);
+    cudaFree(p->d_stamp);
+    cudaFree(p->d_rowstamp);
     cudaFree(p->d_pos);
     cudaFree(p->d_lum);
     cudaFree(p->d_out_stage);
@@ -1128,7 +1134,7 @@ lc_status lc_plan_estimate(int n, const lc_steps* steps, const lc_cosmology* cos
     const long long nrp = nrp_of(n), spec = (long long)n * n * nrp, slot = (long long)n * n * (n / 2 + 1);
     const long long hb = steps->history == LC_HISTORY_BF16 ? 4 : 8;
     const long long W = (long long)(n / 2 + 1) * (n / 2 + 2) * (n / 2 + 3) / 6;
-    if (base_bytes) *base_bytes = (size_t)(8LL * n * n * n + 8 * spec + hb * slot * ring + 4LL * n * n * n);
+    if (base_bytes) *base_bytes = (size_t)(8LL * n * n * n + 8 * spec + hb * slot * ring + 4LL * n * n * n + 4LL * n * n);
     if (table_bytes_per_step) *table_bytes_per_step = (size_t)(4 * W * ring + 8 * ring);
     return LC_OK;
 }
@@ -1198,7 +1204,8 @@ lc_status lc_plan_create(int n, double box_mpc, const lc_cosmology* cosmo, const
               dalloc(p, (char**)&p->d_ring, hb * (size_t)p->ring_slot * p->n_ring) == cudaSuccess &&
               dalloc(p, &p->d_slot_step, p->n_ring) == cudaSuccess && dalloc(p, &p->d_slot_S, p->n_ring) == cudaSuccess &&
               dalloc(p, &p->d_slot_total, p->n_ring) == cudaSuccess && dalloc(p, &p->d_tw, n) == cudaSuccess &&
-              dalloc(p, &p->d_err, 1) == cudaSuccess && dalloc(p, &p->d_maxbits, 1) == cudaSuccess;
+              dalloc(p, &p->d_err, 1) == cudaSuccess && dalloc(p, &p->d_maxbits, 1) == cudaSuccess &&
+              dalloc(p, &p->d_stamp, 1) == cudaSuccess && dalloc(p, &p->d_rowstamp, (size_t)n * n) == cudaSuccess;
     if (!ok) {
         free_all(p);
         delete p;
@@ -1220,6 +1227,8 @@ lc_status lc_plan_create(int n, double box_mpc, const lc_cosmology* cosmo, const
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_slot_total, 0, sizeof(long long) * p->n_ring, p->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_slot_S, 0, sizeof(double) * p->n_ring, p->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_err, 0, sizeof(int), p->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_stamp, 0, sizeof(unsigned), p->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_rowstamp, 0, sizeof(unsigned) * (size_t)n * n, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) {
         free_all(p);
@@ -1291,7 +1300,13 @@ lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos
     if (!p->capturing) clear_grid_cells(p, st);
     if (lc_status r = ensure_near(p, near_entries(p, n_src)); r != LC_OK) return r;
     const int slot = step % p->n_ring;
-    SlotMeta m{slot, step, p->d_slot_step, p->d_slot_S, p->d_slot_total};
+    // LC_ROW_STAMPS=0: the z pass reads every row of the grid
+    static const bool row_stamps = [] {
+        const char* v = getenv("LC_ROW_STAMPS");
+        return !(v && !strcmp(v, "0"));
+    }();
+    SlotMeta m{slot, step, p->d_slot_step, p->d_slot_S, p->d_slot_total, row_stamps ? p->d_stamp : nullptr,
+               row_stamps ? p->d_rowstamp : nullptr};
     const long long N = p->N;
     {
         Phase ph(p, LC_PHASE_DEPOSIT, n_src > 0 ? 2 : 1);
@@ -1314,6 +1329,8 @@ lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos
     r.slot = slot;
     r.bf16 = p->history == LC_HISTORY_BF16;
     r.zero_in = zeroed_by_r2c(p) ? 1 : 0;
+    r.rowstamp = m.rowstamp;
+    r.stamp = m.stamp;
     r.dst = p->d_work;
     r.tw = p->d_tw;
     ColArgs c{};
@@ -1508,8 +1525,26 @@ static lc_status field_impl(lc_plan* p, int step, float* out, int instant, uint6
         r.scale = (float)(p->U / (double)N3);
         r.tw = p->d_tw;
         const int nslot = step % p->n_ring;
+        const bool near_list = p->near_on && p->near_n > 0 && !p->near_pm;
+        NearScatter ns{p->d_src_cell, p->d_src_q, p->near_n, T.gnear, p->d_slot_S, nslot, p->U, p->d_near, 0};
+        bool near_done = false;
         if (p->ops->plane_c2r) {
-            // y and z together, one CTA per x-plane
+            // y and z together, one CTA per x-plane; a short near-field list
+            // runs on extra CTAs of the same launch, on the SMs that the N
+            // planes leave idle, instead of a launch of its own.
+            // LC_NEAR_CTAS=0: always the separate launch
+            static const bool fuse_near = [] {
+                const char* v = getenv("LC_NEAR_CTAS");
+                return !(v && !strcmp(v, "0"));
+            }();
+            if (near_list && fuse_near) {
+                const int c = p->ops->plane_near_ctas(p->near_n * kNearCube, sm_count());
+                if (c > 0) {
+                    r.near = ns;
+                    r.near.ctas = c;
+                    near_done = true;
+                }
+            }
             Phase ph(p, LC_PHASE_C2R_Z, 1);
             p->ops->plane_c2r(r, st);
         } else {
@@ -1523,7 +1558,7 @@ static lc_status field_impl(lc_plan* p, int step, float* out, int instant, uint6
         }
         if (p->near_on && p->near_n > 0) {
             // innermost shell's near cube, summed exactly in FP64 and folded in
-            Phase ph(p, LC_PHASE_NEAR, 2);
+            Phase ph(p, LC_PHASE_NEAR, near_done ? 1 : 2);
             if (p->near_pm) {
                 NearPmArgs na{};
                 na.cell = p->d_src_cell;
@@ -1557,9 +1592,8 @@ static lc_status field_impl(lc_plan* p, int step, float* out, int instant, uint6
                 na.slot = nslot;
                 na.U_out = p->U;
                 launch_near_pm(na, p->d_near, st);
-            } else {
-                launch_near_scatter(p->d_src_cell, p->d_src_q, p->near_n, p->N, T.gnear, p->d_slot_S, nslot, p->U,
-                                    p->d_near, st);
+            } else if (!near_done) {
+                launch_near_scatter(ns, p->N, st);
             }
             launch_near_fold(p->d_src_cell, p->d_src_q, p->near_n, p->N, p->d_near, dout, p->d_grid, st);
             p->grid_dirty = false; // the fold cleared the deposit cells

@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(kPrepThreads)
         m.slot_step[m.slot] = m.step;
         m.slot_total[m.slot] = 0;
         m.slot_S[m.slot] = 1.0; // replaced by the deposit's unit when there are sources
+        if (m.stamp) *m.stamp += 1u;
     }
 }
 
@@ -130,6 +131,8 @@ __global__ void __launch_bounds__(256)
         invS = (E - 62 > -1022 && E - 62 < 1022) ? ldexp(1.0, 62 - E) : 0.0;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) m.slot_S[m.slot] = S;
+    // this push's value of the counter, stored for every row deposited into
+    const unsigned stamp = m.rowstamp ? *m.stamp : 0u;
     long long q = 0;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
@@ -155,7 +158,10 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 const long long c = (cx[k >> 2] * N + cy[(k >> 1) & 1]) * N + cz[k & 1];
-                if (sh[k]) atomicAdd(reinterpret_cast<unsigned long long*>(grid + c), (unsigned long long)sh[k]);
+                if (sh[k]) {
+                    atomicAdd(reinterpret_cast<unsigned long long*>(grid + c), (unsigned long long)sh[k]);
+                    if (m.rowstamp) m.rowstamp[c / N] = stamp;
+                }
                 if (cell_out) {
                     cell_out[8 * i + k] = c;
                     q_out[8 * i + k] = sh[k];
@@ -166,7 +172,10 @@ __global__ void __launch_bounds__(256)
             if (ok) {
                 q = llrint(invS != 0.0 ? __dmul_rn(L, invS) : __ddiv_rn(L, S));
                 c = (ngp_cell(x, l, N) * N + ngp_cell(y, l, N)) * N + ngp_cell(z, l, N);
-                if (q) atomicAdd(reinterpret_cast<unsigned long long*>(grid + c), (unsigned long long)q);
+                if (q) {
+                    atomicAdd(reinterpret_cast<unsigned long long*>(grid + c), (unsigned long long)q);
+                    if (m.rowstamp) m.rowstamp[c / N] = stamp;
+                }
             }
             if (cell_out) {
                 cell_out[i] = c;
@@ -316,29 +325,10 @@ __global__ void k_near_prep(const double* gw0, const double* scale0, double* gne
     *g0_far -= sum;
 }
 
-__device__ __forceinline__ long long near_target(long long c, int m, int N, int& dx, int& dy, int& dz) {
-    dx = m / (kNearSide * kNearSide) - kNearR;
-    dy = (m / kNearSide) % kNearSide - kNearR;
-    dz = m % kNearSide - kNearR;
-    const long long NN = (long long)N * N;
-    const int ix = (int)(c / NN), iy = (int)((c / N) % N), iz = (int)(c % N);
-    const int tx = (ix + dx + N) % N, ty = (iy + dy + N) % N, tz = (iz + dz + N) % N;
-    return ((long long)tx * N + ty) * N + tz;
-}
-
-__global__ void __launch_bounds__(256) k_near_scatter(const long long* __restrict__ cell, const long long* __restrict__ q,
-                                                      long long n, int N, const double* __restrict__ gnear,
-                                                      const double* __restrict__ slot_S, int slot, double U,
-                                                      double* __restrict__ acc) {
+__global__ void __launch_bounds__(256) k_near_scatter(NearScatter a, int N) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n * kNearCube) return;
-    const long long s = idx / kNearCube;
-    const int m = (int)(idx % kNearCube);
-    const long long qs = q[s];
-    if (qs == 0) return;
-    int dx, dy, dz;
-    const long long t = near_target(cell[s], m, N, dx, dy, dz);
-    atomicAdd(acc + t, U * slot_S[slot] * (double)qs * gnear[near_wedge(dx, dy, dz)]);
+    if (idx >= a.n * kNearCube) return;
+    near_scatter_item(a, N, idx);
 }
 
 __global__ void __launch_bounds__(256) k_near_fold(const long long* __restrict__ cell, const long long* __restrict__ q,
@@ -486,11 +476,10 @@ void launch_near_prep(const double* gw0, const double* scale0, double* gnear, do
     k_near_prep<<<1, 1, 0, st>>>(gw0, scale0, gnear, g0_far);
 }
 
-void launch_near_scatter(const long long* cell, const long long* q, long long n, int N, const double* gnear,
-                         const double* slot_S, int slot, double U, double* acc, cudaStream_t st) {
-    const long long total = n * kNearCube;
+void launch_near_scatter(const NearScatter& a, int N, cudaStream_t st) {
+    const long long total = a.n * kNearCube;
     if (total <= 0) return;
-    launch_k(k_near_scatter, (unsigned)((total + 255) / 256), 256, 0, st, cell, q, n, N, gnear, slot_S, slot, U, acc);
+    launch_k(k_near_scatter, (unsigned)((total + 255) / 256), 256, 0, st, a, N);
 }
 
 void launch_near_fold(const long long* cell, const long long* q, long long n, int N, double* acc, float* out,

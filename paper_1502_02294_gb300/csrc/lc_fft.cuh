@@ -37,6 +37,43 @@ __host__ __device__ __forceinline__ int near_wedge(int dx, int dy, int dz) {
     return c * (c + 1) * (c + 2) / 6 + b * (b + 1) / 2 + a;
 }
 
+// Near-field list of one push: per deposited source its cell and its integer
+// share q; the innermost shell's near cube around each is summed exactly in
+// FP64 into `acc` (one item per (source, cube cell), kNearCube per source).
+struct NearScatter {
+    const long long* cell;
+    const long long* q;
+    long long n;             // sources in the list
+    const double* gnear;     // the innermost shell's near wedge (f_0 folded in)
+    const double* slot_S;    // per-slot fixed-point unit
+    int slot;
+    double U;                // output unit
+    double* acc;             // N^3 FP64 accumulator, zero where not yet folded
+    int ctas;                // extra CTAs of a plane kernel that run the list (0: none)
+};
+
+// Item idx = s * kNearCube + m: source s, displacement m of its near cube
+// (x slowest), target cell wrapped periodically on the N^3 grid.
+__device__ __forceinline__ long long near_target(long long c, int m, int N, int& dx, int& dy, int& dz) {
+    dx = m / (kNearSide * kNearSide) - kNearR;
+    dy = (m / kNearSide) % kNearSide - kNearR;
+    dz = m % kNearSide - kNearR;
+    const long long NN = (long long)N * N;
+    const int ix = (int)(c / NN), iy = (int)((c / N) % N), iz = (int)(c % N);
+    const int tx = (ix + dx + N) % N, ty = (iy + dy + N) % N, tz = (iz + dz + N) % N;
+    return ((long long)tx * N + ty) * N + tz;
+}
+
+__device__ __forceinline__ void near_scatter_item(const NearScatter& a, int N, long long idx) {
+    const long long s = idx / kNearCube;
+    const int m = (int)(idx % kNearCube);
+    const long long qs = a.q[s];
+    if (qs == 0) return;
+    int dx, dy, dz;
+    const long long t = near_target(a.cell[s], m, N, dx, dy, dz);
+    atomicAdd(a.acc + t, a.U * a.slot_S[a.slot] * (double)qs * a.gnear[near_wedge(dx, dy, dz)]);
+}
+
 // Launch through cudaLaunchKernelEx (one launch path for every per-step
 // kernel; no launch attributes).
 template <typename... KArgs, typename... Args>

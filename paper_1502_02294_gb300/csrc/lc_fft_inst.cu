@@ -45,5 +45,6 @@ const FftOps LC_CAT(fft_ops_, LC_N) = {LC_N,
                                       LC_N * Launch<LC_N>::NCH,
                                       &Launch<LC_N>::variants_built,
                                       &Launch<LC_N>::set_variant,
-                                      &Launch<LC_N>::get_variant};
+                                      &Launch<LC_N>::get_variant,
+                                      &Launch<LC_N>::plane_near_ctas};
 } // namespace lc

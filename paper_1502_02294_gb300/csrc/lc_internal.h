@@ -59,18 +59,25 @@ struct SlotMeta {
     int* slot_step;
     double* slot_S;
     long long* slot_total;
+    // optional (nullptr: none): the push counter, advanced by the source
+    // check, and per grid row (x N + y) the counter value of the last push
+    // that deposited into it, so that the z pass can skip rows left all zero
+    unsigned* stamp;
+    unsigned* rowstamp;
 };
 // Checks the luminosities (finite, >= 0; a bad one sets *err) and records the
-// bits of their maximum; marks the slot (step, total = 0).
+// bits of their maximum; marks the slot (step, total = 0) and advances the
+// push counter.
 void launch_src_prep(const double* pos, const double* lum, long long n, unsigned long long* maxbits, int* err,
                      SlotMeta m, cudaStream_t st);
 // Fixed-point deposit (LC_DEPOSIT_NGP or LC_DEPOSIT_CIC) into grid (int64,
 // pre-zeroed), total into slot_total; a source with a non-finite position or
 // luminosity, or a negative one, is left out and sets *err.  cell_out / q_out
 // (may be null): the flat cell index and integer share of each of a source's
-// cells (1 for NGP, 8 for CIC, at [k * n_src ... ] no: at [cells * i + k]),
-// kept for the near-field correction of the innermost shell; off_out (NGP
-// only): each source's position relative to its cell centre.
+// cells (1 for NGP, 8 for CIC, at [cells * i + k]), kept for the near-field
+// correction of the innermost shell; off_out (NGP only): each source's
+// position relative to its cell centre.  With m.rowstamp, every row that
+// receives a non-zero share is stamped with the push counter.
 void launch_deposit(const double* pos, const double* lum, long long n, int N, double l, int deposit,
                     const unsigned long long* maxbits, long long* grid, SlotMeta m, int* err, cudaStream_t st,
                     long long* cell_out = nullptr, long long* q_out = nullptr, double* off_out = nullptr);
@@ -114,8 +121,9 @@ void launch_copy_out(long long n4, const float4* src, float4* dst, int ctas, cud
 void launch_gsum(long long W, int A, int gstride, const float* ghat, const double* g0, float* gsum, double* g0sum,
                  cudaStream_t st);
 // scatter U * S * q * G(d) into the FP64 accumulator for every source and d
-void launch_near_scatter(const long long* cell, const long long* q, long long n, int N, const double* gnear,
-                         const double* slot_S, int slot, double U, double* acc, cudaStream_t st);
+// (NearScatter: the list and its factors, defined with the kernels)
+struct NearScatter;
+void launch_near_scatter(const NearScatter& a, int N, cudaStream_t st);
 // fold the accumulator into out (one rounding per cell) and clear it; with a
 // grid, also zero each entry's own deposit cell there (the sparse clear of the
 // deposit grid, once the transforms have read it)

@@ -39,6 +39,12 @@ struct RowR2CArgs {
     int slot;
     int bf16;                 // ROW_IN_I64: 1 -> values / (S * total), else * S
     int zero_in;              // ROW_IN_I64: leave the grid all zero for the next deposit
+    // ROW_IN_I64, optional (nullptr: every row read): per row (x N + y) the
+    // push counter of its last deposit, and the counter (*stamp); a row whose
+    // value differs holds no share of this push and is all zero, so the lanes
+    // forms of the z pass skip its loads and transform (its half spectrum is 0)
+    const unsigned* rowstamp;
+    const unsigned* stamp;
     const float* fin;         // ROW_IN_F32
     const double* gw;         // ROW_IN_WEDGE: wedge values of one shell (FP64)
     const double* gscale;     // ROW_IN_WEDGE: that shell's normalisation factor
@@ -84,7 +90,18 @@ struct RowC2RArgs {
     float* out;
     float scale;
     const float2* tw;
+    // plane kernels: the near-field list, run by near.ctas CTAs launched
+    // after the N plane CTAs, on SMs the planes leave idle (0: none)
+    NearScatter near;
 };
+
+// The CTAs of a plane kernel beyond its N planes walk the near-field list.
+template <int N, int NT>
+__device__ __forceinline__ void plane_near_ctas(const NearScatter& a) {
+    const long long total = a.n * kNearCube;
+    for (long long i = (long long)(blockIdx.x - N) * NT + threadIdx.x; i < total; i += (long long)a.ctas * NT)
+        near_scatter_item(a, N, i);
+}
 
 constexpr int kMaxShells = 1024;
 
@@ -922,11 +939,13 @@ __global__ void __launch_bounds__(kRowsLanesThreads, 2) k_rows_r2c_lanes(RowR2CA
     float2* ex = tw + N + (warp * PW + grp) * EX;
     for (int i = threadIdx.x; i < N; i += kRowsLanesThreads) tw[i] = a.tw[i];
     float scale = 1.0f;
+    unsigned cur = 0;
     if constexpr (IN == ROW_IN_I64) {
         const double Su = a.slot_S[a.slot];
         const long long tot = a.slot_total[a.slot];
         // as k_rows_r2c: S per unit (FP32 history), 1 / total (BF16 history)
         scale = a.bf16 ? (tot > 0 ? (float)(1.0 / (double)tot) : 0.0f) : (float)Su;
+        if (a.rowstamp) cur = *a.stamp;
     }
     __syncthreads();
     const long long nwarps = (long long)gridDim.x * (kRowsLanesThreads / 32);
@@ -935,6 +954,24 @@ __global__ void __launch_bounds__(kRowsLanesThreads, 2) k_rows_r2c_lanes(RowR2CA
         const long long ra = 2 * rp * N, rb = ra + N;
         float2 v[16];
         if constexpr (IN == ROW_IN_I64) {
+            if (a.rowstamp) {
+                // the warp's 2 PW rows (2 u PW ... 2 u PW + 2 PW - 1 < 2 npairs);
+                // none with a share of this push: zero half spectra, no loads
+                const bool mine = lane < 2 * PW && a.rowstamp[2 * u * PW + lane] == cur;
+                if (!__any_sync(0xffffffffu, mine)) {
+                    float2* da = a.dst + (2 * rp) * NRP;
+                    float2* db = da + NRP;
+#pragma unroll
+                    for (int m = 0; m < (H + G - 1) / G; ++m) {
+                        const int k = q + G * m;
+                        if (k < H) {
+                            da[k] = make_float2(0.f, 0.f);
+                            db[k] = make_float2(0.f, 0.f);
+                        }
+                    }
+                    continue;
+                }
+            }
             long long xa[R1], xb[R1];
 #pragma unroll
             for (int p = 0; p < R1; ++p) {
@@ -1334,6 +1371,10 @@ __global__ void __launch_bounds__(plane_threads_of(N)) k_plane_c2r(RowC2RArgs a)
     constexpr int NT = plane_threads_of(N), H = N / 2 + 1, NRP = nrp_of(N), P = N / 2;
     constexpr int LD = N * H, LPER = (LD + NT - 1) / NT;
     constexpr int UN = P * H, UPER = (UN + NT - 1) / NT;
+    if (blockIdx.x >= N) {
+        plane_near_ctas<N, NT>(a.near);
+        return;
+    }
     extern __shared__ float4 smem_raw[];
     float2* tw = reinterpret_cast<float2*>(smem_raw);
     float2* pl = tw + N;
@@ -1451,10 +1492,12 @@ __global__ void __launch_bounds__(plane_lanes_threads<N>()) k_plane_r2c_lanes(Ro
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane / G, q = lane % G;
     for (int i = threadIdx.x; i < N; i += NT) tw[i] = a.tw[i];
     float scale = 1.0f;
+    unsigned cur = 0;
     if constexpr (IN == ROW_IN_I64) {
         const double S = a.slot_S[a.slot];
         const long long tot = a.slot_total[a.slot];
         scale = a.bf16 ? (tot > 0 ? (float)(1.0 / (double)tot) : 0.0f) : (float)S;
+        if (a.rowstamp) cur = *a.stamp;
     }
     __syncthreads();
     for (int u0 = warp * PW; u0 < P; u0 += (NT / 32) * PW) {
@@ -1463,6 +1506,22 @@ __global__ void __launch_bounds__(plane_lanes_threads<N>()) k_plane_r2c_lanes(Ro
         const long long ra = ((long long)x * N + 2 * u) * N, rb = ra + N;
         float2 v[16];
         if constexpr (IN == ROW_IN_I64) {
+            if (a.rowstamp) {
+                // rows without a share of this push: zero half spectra, when
+                // all of the warp's pairs are such (the warp stays converged)
+                const unsigned* rs = a.rowstamp + (long long)x * N + 2 * u;
+                if (!__any_sync(0xffffffffu, rs[0] == cur || rs[1] == cur)) {
+#pragma unroll
+                    for (int m = 0; m < M; ++m) {
+                        const int k = q + G * m;
+                        if (k < H) {
+                            ex[k] = make_float2(0.f, 0.f);
+                            ex[PS + k] = make_float2(0.f, 0.f);
+                        }
+                    }
+                    continue;
+                }
+            }
             long long xa[R1], xb[R1];
 #pragma unroll
             for (int p = 0; p < R1; ++p) {
@@ -1564,6 +1623,10 @@ __global__ void __launch_bounds__(plane_lanes_threads<N>()) k_plane_c2r_lanes(Ro
     constexpr int H = N / 2 + 1, NRP = nrp_of(N), P = N / 2, PS = plane_lanes_ps<N>(), PW = 32 / G;
     constexpr int J = (R1 + G - 1) / G;
     static_assert(P % PW == 0 && 32 % G == 0, "whole lane groups");
+    if (blockIdx.x >= N) {
+        plane_near_ctas<N, NT>(a.near);
+        return;
+    }
     extern __shared__ float4 smem_raw[];
     float2* tw = reinterpret_cast<float2*>(smem_raw);
     float2* pl = tw + N;
@@ -1695,6 +1758,9 @@ struct FftOps {
     int (*cols_variants)();          // bit mask of the variants built for this N
     void (*set_cols_variant)(int);
     int (*cols_variant)();
+    // extra CTAs of plane_c2r for a near-field list of `items` items on a GPU
+    // of nsm SMs (0: run the list in a launch of its own)
+    int (*plane_near_ctas)(long long items, int nsm);
 };
 enum { FFT_COLS_STAGES = 0, FFT_COLS_LANES = 1, FFT_COLS_LANES3 = 2, FFT_COLS_TMA = 3, FFT_COLS_TMA4 = 4, FFT_NVAR = 5 };
 
@@ -1923,12 +1989,29 @@ template <int N> struct Launch {
         if constexpr (plane_ok<N>()) {
             if constexpr (plane_lanes_ok<N>()) {
                 if (lanes_form()) {
-                    launch_k(k_plane_c2r_lanes<N>, N, plane_lanes_threads<N>(), plane_lanes_smem_bytes<N>(), st, a);
+                    launch_k(k_plane_c2r_lanes<N>, N + a.near.ctas, plane_lanes_threads<N>(), plane_lanes_smem_bytes<N>(),
+                             st, a);
                     return;
                 }
             }
-            launch_k(k_plane_c2r<N>, N, plane_threads_of(N), plane_smem_bytes<N>(), st, a);
+            launch_k(k_plane_c2r<N>, N + a.near.ctas, plane_threads_of(N), plane_smem_bytes<N>(), st, a);
         }
+    }
+    // The near-field list on the SMs the N plane CTAs (one per SM) leave idle
+    // in their last wave, about one item a thread, if that leaves at most
+    // N / 16 items a thread: the planes' own time grows with N, and the list
+    // should end within it.
+    static int plane_near_ctas(long long items, int nsm) {
+        if constexpr (plane_ok<N>()) {
+            int nt = plane_threads_of(N);
+            if constexpr (plane_lanes_ok<N>())
+                if (lanes_form()) nt = plane_lanes_threads<N>();
+            const int idle = (nsm > 0 && N % nsm) ? nsm - N % nsm : 0;
+            if (idle == 0 || items <= 0) return 0;
+            const long long want = (items + nt - 1) / nt, c = want < idle ? want : idle;
+            return items <= c * nt * (N / 16) ? (int)c : 0;
+        }
+        return 0;
     }
     static constexpr bool kRowsPl = N >= 256;
     template <class Kern> static int occ_ctas(Kern k, size_t smem) {
