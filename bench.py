@@ -271,7 +271,8 @@ def fft_choices(ns):
     first plan of that size was created): {N: name}."""
     import paper_1502_02294_gb300 as lc
 
-    names = {lc.FFT_STAGES: "stages", lc.FFT_LANES: "lanes", lc.FFT_LANES3: "lanes3", lc.FFT_TMA: "tma", lc.FFT_TMA4: "tma4"}
+    names = {lc.FFT_STAGES: "stages", lc.FFT_LANES: "lanes", lc.FFT_LANES3: "lanes3", lc.FFT_TMA: "tma", lc.FFT_TMA4: "tma4",
+             lc.FFT_PLANE4: "plane4"}
     return {int(n): names.get(lc.fft_variant(int(n)), "-") for n in sorted(set(ns))}
 
 

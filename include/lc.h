@@ -381,7 +381,7 @@ int lc_autotune_report(char* buf, int size);
 
 /* The FFT passes of Eq. 12 along y and x (and along z) come in five kernel
  * forms for N = 256, 384 and 512: LC_FFT_STAGES, block-wide Stockham radix stages
- * in shared memory (every N), and three forms with one lane per tile column
+ * in shared memory (every N), and four forms with one lane per tile column
  * (a lane group per row pair along z), the 16-point DFTs in registers and a
  * single shared-memory exchange between the two radix stages:
  * LC_FFT_LANES (tiles copied by 16-byte asynchronous copies into four
@@ -391,17 +391,29 @@ int lc_autotune_report(char* buf, int size);
  * kernels (N = 32 ... 192: z and y per x-plane in one kernel) have two:
  * LC_FFT_STAGES (staged plane kernels) and LC_FFT_LANES (the transforms in
  * registers, one shared-memory exchange per axis); 8 and 16 have one.
+ * N = 256 has a sixth, LC_FFT_PLANE4: the z and y passes of a step in one
+ * kernel each way, an x-plane per cluster of four CTAs (two per SM), each
+ * holding a quarter of the plane's columns (the z pass of its quarter of
+ * the rows stores into every CTA's shared memory), the x passes as
+ * LC_FFT_LANES.
  * The first plan created for a grid size times every form on its own
  * buffers (forward and inverse passes of one step, each launch after an L2
  * flush, median of seven) and keeps the fastest
  * for the rest of the process (the choice is listed by lc_autotune_report
  * and persisted with the shell-MAC choices);
- * LC_FFT_VARIANT=stages|lanes|lanes3|tma|tma4 forces one.
+ * LC_FFT_VARIANT=stages|lanes|lanes3|tma|tma4|plane4 forces one.
  * lc_fft_set_variant(n, v) forces v for grid size n from now on (later plans
  * and stand-alone calls; a table already built keeps its values), and
  * lc_fft_variant(n) returns the form in use (-1: n not supported).
  * LC_ERR_UNSUPPORTED_SIZE if n has no such form. */
-enum { LC_FFT_STAGES = 0, LC_FFT_LANES = 1, LC_FFT_LANES3 = 2, LC_FFT_TMA = 3, LC_FFT_TMA4 = 4 };
+enum {
+    LC_FFT_STAGES = 0,
+    LC_FFT_LANES = 1,
+    LC_FFT_LANES3 = 2,
+    LC_FFT_TMA = 3,
+    LC_FFT_TMA4 = 4,
+    LC_FFT_PLANE4 = 5
+};
 lc_status lc_fft_set_variant(int n, int variant);
 int lc_fft_variant(int n);
 

@@ -45,11 +45,11 @@ def autotune_report() -> dict:
     return out
 
 
-FFT_STAGES, FFT_LANES, FFT_LANES3, FFT_TMA, FFT_TMA4 = 0, 1, 2, 3, 4  # FFT pass forms (lc_fft_set_variant)
+FFT_STAGES, FFT_LANES, FFT_LANES3, FFT_TMA, FFT_TMA4, FFT_PLANE4 = 0, 1, 2, 3, 4, 5  # FFT pass forms
 
 
 def fft_set_variant(n: int, variant: int):
-    """Force the FFT pass form for grid size n (one of FFT_STAGES ... FFT_TMA4)."""
+    """Force the FFT pass form for grid size n (one of FFT_STAGES ... FFT_PLANE4)."""
     _check(_lib().lc_fft_set_variant(int(n), int(variant)), "lc_fft_set_variant")
 
 

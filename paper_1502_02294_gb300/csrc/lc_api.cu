@@ -420,6 +420,12 @@ lc_status cuda_fail(lc_plan* p, cudaError_t e) {
     return e == cudaErrorMemoryAllocation ? LC_ERR_OOM : LC_ERR_CUDA;
 }
 
+// z and y of a step's transforms by plane kernels (one launch each way): for
+// grids up to 192^3 always, at 256^3 in the four-CTA cluster form when chosen
+static bool plane_step(const lc_plan* p) { return p->ops->plane_r2c && p->ops->plane_on(); }
+// the Green's function tables through plane kernels (one CTA per plane only)
+static bool plane_table(const lc_plan* p) { return p->ops->plane_r2c && !p->ops->plane_clustered; }
+
 template <class T> cudaError_t dalloc(lc_plan* p, T** ptr, size_t count) {
     *ptr = nullptr;
     if (count == 0) count = 1;
@@ -714,7 +720,7 @@ int choose_mac_variant(lc_plan* p, const lc_plan::Table& T, int s) {
     return best;
 }
 
-const char* const kFftNames[FFT_NVAR] = {"stages", "lanes", "lanes3", "tma", "tma4"};
+const char* const kFftNames[FFT_NVAR] = {"stages", "lanes", "lanes3", "tma", "tma4", "plane4"};
 
 // One step's FFT passes on the plan's own buffers (forward from the int64
 // grid into ring slot 0, inverse from the work spectrum into the grid's
@@ -722,6 +728,7 @@ const char* const kFftNames[FFT_NVAR] = {"stages", "lanes", "lanes3", "tma", "tm
 // it again afterwards.
 void fft_step_passes(lc_plan* p, cudaStream_t st) {
     const long long N = p->N;
+    const bool pl = plane_step(p);
     RowR2CArgs r{};
     r.in_mode = ROW_IN_I64;
     r.nrows = N * N;
@@ -730,24 +737,15 @@ void fft_step_passes(lc_plan* p, cudaStream_t st) {
     r.slot_total = p->d_slot_total;
     r.slot = 0;
     r.bf16 = p->history == LC_HISTORY_BF16;
-    r.zero_in = 1;
+    r.zero_in = N >= 256 ? 1 : 0;
     r.dst = p->d_work;
     r.tw = p->d_tw;
-    if (p->ops->plane_r2c) {
-        // grids with plane kernels: only the z + y passes depend on the form
-        r.zero_in = 0;
-        p->ops->plane_r2c(r, st);
-        RowC2RArgs rc{};
-        rc.nrows = N * N;
-        rc.src = p->d_work;
-        rc.out = reinterpret_cast<float*>(p->d_grid);
-        rc.scale = 1.0f;
-        rc.tw = p->d_tw;
-        p->ops->plane_c2r(rc, st);
-        count_launch(2);
-        return;
-    }
-    p->ops->rows_r2c(r, st);
+    RowC2RArgs rc{};
+    rc.nrows = N * N;
+    rc.src = p->d_work;
+    rc.out = reinterpret_cast<float*>(p->d_grid);
+    rc.scale = 1.0f;
+    rc.tw = p->d_tw;
     ColArgs c{};
     c.axis = 0;
     c.dir = -1;
@@ -756,8 +754,20 @@ void fft_step_passes(lc_plan* p, cudaStream_t st) {
     c.src = p->d_work;
     c.dst = p->d_work;
     c.tw = p->d_tw;
-    p->maps.set(c, p->d_err);
-    p->ops->cols(c, st);
+    if (pl && !p->ops->plane_clustered) {
+        // grids with one CTA per plane: only the z + y passes depend on the form
+        p->ops->plane_r2c(r, st);
+        p->ops->plane_c2r(rc, st);
+        count_launch(2);
+        return;
+    }
+    if (pl) {
+        p->ops->plane_r2c(r, st);
+    } else {
+        p->ops->rows_r2c(r, st);
+        p->maps.set(c, p->d_err);
+        p->ops->cols(c, st);
+    }
     c.axis = 1;
     if (p->history == LC_HISTORY_BF16) {
         c.out_mode = COL_OUT_BF16;
@@ -770,6 +780,11 @@ void fft_step_passes(lc_plan* p, cudaStream_t st) {
     c.wslot = 0;
     p->maps.set(c, p->d_err);
     p->ops->cols(c, st);
+    if (pl) {
+        p->ops->plane_c2r(rc, st);
+        count_launch(3);
+        return;
+    }
     ColArgs ci{};
     ci.axis = 0;
     ci.dir = 1;
@@ -780,12 +795,6 @@ void fft_step_passes(lc_plan* p, cudaStream_t st) {
     ci.tw = p->d_tw;
     p->maps.set(ci, p->d_err);
     p->ops->cols(ci, st);
-    RowC2RArgs rc{};
-    rc.nrows = N * N;
-    rc.src = p->d_work;
-    rc.out = reinterpret_cast<float*>(p->d_grid);
-    rc.scale = 1.0f;
-    rc.tw = p->d_tw;
     p->ops->rows_c2r(rc, st);
     count_launch(5);
 }
@@ -1018,7 +1027,7 @@ lc_status build_table(lc_plan* p, int s) {
     launch_rgf_accum(ra, st);
     launch_rgf_norm(p->N, p->W, A, p->d_gw, p->d_I, p->l * p->l * p->l, p->normalise, p->d_scale, T.g0, st);
     if (p->near_on) launch_near_prep(p->d_gw, p->d_scale, T.gnear, T.g0, st);
-    count_launch(2 + (p->ops->plane_r2c ? 2ULL : 3ULL) * A + (p->near_on ? 1 : 0));
+    count_launch(2 + (plane_table(p) ? 2ULL : 3ULL) * A + (p->near_on ? 1 : 0));
     for (int j = 0; j < A; ++j) {
         RowR2CArgs r{};
         r.in_mode = ROW_IN_WEDGE;
@@ -1036,7 +1045,7 @@ lc_status build_table(lc_plan* p, int s) {
         c.src = p->d_work;
         c.dst = p->d_work;
         c.tw = p->d_tw;
-        if (p->ops->plane_r2c) {
+        if (plane_table(p)) {
             p->ops->plane_r2c(r, st);
         } else {
             p->ops->rows_r2c(r, st);
@@ -1268,7 +1277,7 @@ lc_status lc_plan_prepare(lc_plan* p, int b, int e) {
 // only the cells the push deposited into (sparse clear); without one, the
 // staged z pass of N >= 256 zeroes every block it reads, and smaller grids
 // (plane kernels) are cleared by a memset before each deposit.
-static bool zeroed_by_r2c(const lc_plan* p) { return !p->near_on && p->N >= 256 && !p->ops->plane_r2c; }
+static bool zeroed_by_r2c(const lc_plan* p) { return !p->near_on && p->N >= 256; }
 static bool memset_before_deposit(const lc_plan* p) { return !p->near_on && !zeroed_by_r2c(p); }
 
 lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos, const double* lum) {
@@ -1341,8 +1350,8 @@ lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos
     c.src = p->d_work;
     c.dst = p->d_work;
     c.tw = p->d_tw;
-    if (p->ops->plane_r2c) {
-        // z and y together, one CTA per x-plane
+    if (plane_step(p)) {
+        // z and y together, one CTA (or a cluster of four) per x-plane
         Phase ph(p, LC_PHASE_R2C_Z, 1);
         p->ops->plane_r2c(r, st);
     } else {
@@ -1368,7 +1377,7 @@ lc_status lc_push_sources(lc_plan* p, int step, int64_t n_src, const double* pos
     // the same capture (grids with plane kernels, whose x pass the fused
     // kernel repeats bit for bit)
     const lc_plan::Table& Tn = p->tables[step];
-    if (p->fuse_x && p->capturing && p->ops->plane_r2c && Tn.ghat && Tn.A > 0 && Tn.mac_variant == MAC_GATHER) {
+    if (p->fuse_x && p->capturing && plane_table(p) && Tn.ghat && Tn.A > 0 && Tn.mac_variant == MAC_GATHER) {
         p->x_deferred = slot;
     } else {
         Phase ph(p, LC_PHASE_FWD_X_RING, 1);
@@ -1528,10 +1537,10 @@ static lc_status field_impl(lc_plan* p, int step, float* out, int instant, uint6
         const bool near_list = p->near_on && p->near_n > 0 && !p->near_pm;
         NearScatter ns{p->d_src_cell, p->d_src_q, p->near_n, T.gnear, p->d_slot_S, nslot, p->U, p->d_near, 0};
         bool near_done = false;
-        if (p->ops->plane_c2r) {
-            // y and z together, one CTA per x-plane; a short near-field list
-            // runs on extra CTAs of the same launch, on the SMs that the N
-            // planes leave idle, instead of a launch of its own.
+        if (plane_step(p)) {
+            // y and z together, one CTA (or a cluster of four) per x-plane; a
+            // short near-field list runs on extra CTAs of the same launch, on
+            // the SMs that the planes leave idle, instead of a launch of its own.
             // LC_NEAR_CTAS=0: always the separate launch
             static const bool fuse_near = [] {
                 const char* v = getenv("LC_NEAR_CTAS");
@@ -2328,7 +2337,8 @@ lc_status lc_fft_r2c(int n, const float* in, float* out_complex, void* stream) {
     c.tw = tw;
     ColsMaps maps;
     maps.make(work, n);
-    if (ops->plane_r2c) {
+    const bool pl = ops->plane_r2c && ops->plane_on();
+    if (pl) {
         ops->plane_r2c(ra, st);
     } else {
         ops->rows_r2c(ra, st);
@@ -2338,7 +2348,7 @@ lc_status lc_fft_r2c(int n, const float* in, float* out_complex, void* stream) {
     c.axis = 1;
     maps.set(c, nullptr);
     ops->cols(c, st);
-    count_launch(ops->plane_r2c ? 2 : 3);
+    count_launch(pl ? 2 : 3);
     const int h = n / 2 + 1;
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
@@ -2381,13 +2391,14 @@ lc_status lc_fft_c2r(int n, const float* in_complex, float* out, float scale, vo
         ra.out = out;
         ra.scale = scale;
         ra.tw = tw;
-        if (ops->plane_c2r) {
+        const bool pl = ops->plane_c2r && ops->plane_on();
+        if (pl) {
             ops->plane_c2r(ra, st);
         } else {
             ops->cols(c, st);
             ops->rows_c2r(ra, st);
         }
-        count_launch(ops->plane_c2r ? 2 : 3);
+        count_launch(pl ? 2 : 3);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -34,8 +34,8 @@ const FftOps LC_CAT(fft_ops_, LC_N) = {LC_N,
                                       &Launch<LC_N>::rows_r2c,
                                       &Launch<LC_N>::cols,
                                       &Launch<LC_N>::rows_c2r,
-                                      plane_ok<LC_N>() ? &Launch<LC_N>::plane_r2c : nullptr,
-                                      plane_ok<LC_N>() ? &Launch<LC_N>::plane_c2r : nullptr,
+                                      (plane_ok<LC_N>() || plane_cl_ok<LC_N>()) ? &Launch<LC_N>::plane_r2c : nullptr,
+                                      (plane_ok<LC_N>() || plane_cl_ok<LC_N>()) ? &Launch<LC_N>::plane_c2r : nullptr,
                                       MacCfg<LC_N, false>::OK ? &mac_f32 : nullptr,
                                       MacCfg<LC_N, true>::OK ? &mac_bf16 : nullptr,
                                       MacWsCfg<LC_N, false, false>::OK ? &mac_ws_f32 : nullptr,
@@ -46,5 +46,7 @@ const FftOps LC_CAT(fft_ops_, LC_N) = {LC_N,
                                       &Launch<LC_N>::variants_built,
                                       &Launch<LC_N>::set_variant,
                                       &Launch<LC_N>::get_variant,
-                                      &Launch<LC_N>::plane_near_ctas};
+                                      &Launch<LC_N>::plane_near_ctas,
+                                      &Launch<LC_N>::plane_on,
+                                      plane_cl_ok<LC_N>()};
 } // namespace lc

@@ -95,11 +95,12 @@ struct RowC2RArgs {
     NearScatter near;
 };
 
-// The CTAs of a plane kernel beyond its N planes walk the near-field list.
-template <int N, int NT>
+// The CTAs of a plane kernel from block FIRST on (past its planes) walk the
+// near-field list of the N^3 grid.
+template <int N, int NT, int FIRST = N>
 __device__ __forceinline__ void plane_near_ctas(const NearScatter& a) {
     const long long total = a.n * kNearCube;
-    for (long long i = (long long)(blockIdx.x - N) * NT + threadIdx.x; i < total; i += (long long)a.ctas * NT)
+    for (long long i = (long long)(blockIdx.x - FIRST) * NT + threadIdx.x; i < total; i += (long long)a.ctas * NT)
         near_scatter_item(a, N, i);
 }
 
@@ -1728,6 +1729,274 @@ __global__ void __launch_bounds__(plane_lanes_threads<N>()) k_plane_c2r_lanes(Ro
 }
 
 // ------------------------------------------------------------------------
+// N = 256: z and y per x-plane on a cluster of C = 4 CTAs.  The 256 x 129
+// half plane (264 KB) does not fit one CTA's shared memory, so each x-plane
+// goes to a cluster, and the z pass, the y pass and the transposition
+// between them stay on chip.  Rank c keeps the y-pass columns kz in
+// [CW c, CW c + CW) (CW = N / 2C; rank 0 also the Nyquist column N/2) of all
+// N rows in a buffer B[y][PS].
+//   forward: rank c transforms rows y in [R c, R c + R) (R = N / C) along z,
+//     a row pair per lane group as k_rows_r2c_lanes, and stores each
+//     unpacked value in the buffer of the rank that owns its kz, its own or a
+//     peer's (distributed shared memory); after the cluster barrier it runs
+//     the y pass of its columns as k_plane_r2c_lanes (R1 = G = 16) and writes
+//     them out.
+//   inverse: rank c runs the y pass of its columns from global memory, the
+//     result Y[k1 + 16 k2] on buffer row 16 k1 + k2; after the cluster
+//     barrier it transforms rows [R c, R c + R) along z as k_rows_c2r_lanes,
+//     reading each kz from the buffer that holds it, and a second barrier
+//     keeps every buffer until the peers have read it.
+// Two 288-thread CTAs per SM (112 KB of shared memory each), so that one
+// CTA's transfers overlap the other's arithmetic.  (A cluster of two, one
+// 544-thread CTA per SM with 215 KB, was slower: the inverse 72.7 against
+// 64.3 us a step at 256^3.)
+template <int N> __host__ __device__ constexpr bool plane_cl_ok() { return N == 256; }
+constexpr int kPlaneClC = 4, kPlaneClThreads = 288;
+template <int N> __host__ __device__ constexpr int plane_cl_ps() { return N / (2 * kPlaneClC) + 4; }
+template <int N> __host__ __device__ constexpr size_t plane_cl_smem_bytes() {
+    return sizeof(float2) * ((size_t)N + (size_t)N * plane_cl_ps<N>() +
+                             (size_t)(kPlaneClThreads / (N / lanes_r1<N>(0))) * rows_lanes_ex<N>());
+}
+// the rank holding column k of the half spectrum (CW columns a rank, the
+// Nyquist column N/2 = C CW on rank 0), its column index there, and back
+__device__ __forceinline__ int plane_cl_owner(int k, int CW, int C) { return k == C * CW ? 0 : k / CW; }
+__device__ __forceinline__ int plane_cl_col(int k, int CW, int C) { return k == C * CW ? CW : k % CW; }
+__device__ __forceinline__ int plane_cl_kz(int rank, int c, int CW, int C) { return c == CW ? C * CW : rank * CW + c; }
+// item `it` of a y stage over a rank's columns (CW regular ones, row by row,
+// then rank 0's Nyquist column c = CW)
+__device__ __forceinline__ void plane_cl_item(int it, int rows, int CW, int& c, int& r) {
+    if (it < CW * rows) {
+        c = it % CW;
+        r = it / CW;
+    } else {
+        c = CW;
+        r = it - CW * rows;
+    }
+}
+// store v at float2 index idx of rank o's buffer (sB: this CTA's buffer as a
+// shared::cta address)
+__device__ __forceinline__ void plane_cl_put(float2* B, unsigned sB, int rank, int o, int idx, float2 v) {
+    if (o == rank) B[idx] = v;
+    else cluster_st(cluster_map(sB + 8u * (unsigned)idx, (unsigned)o), v);
+}
+__device__ __forceinline__ float2 plane_cl_get(const float2* B, unsigned sB, int rank, int o, int idx) {
+    return o == rank ? B[idx] : cluster_ld(cluster_map(sB + 8u * (unsigned)idx, (unsigned)o));
+}
+
+template <int N, int IN>
+__global__ void __cluster_dims__(kPlaneClC, 1, 1) __launch_bounds__(kPlaneClThreads, 2) k_plane_cl_r2c(RowR2CArgs a) {
+    constexpr int C = kPlaneClC, NT = kPlaneClThreads, R1 = lanes_r1<N>(0), G = N / R1, PW = 32 / G, H = N / 2 + 1;
+    constexpr int NRP = nrp_of(N), PS = plane_cl_ps<N>(), EX = rows_lanes_ex<N>(), CW = N / (2 * C), R = N / C;
+    static_assert(R1 == 16 && G == 16 && PW == 2, "16 x 16 rows, two row pairs per warp");
+    static_assert(IN == ROW_IN_I64 || IN == ROW_IN_F32, "grid or float input");
+    extern __shared__ float4 smem_raw[];
+    float2* tw = reinterpret_cast<float2*>(smem_raw);
+    float2* B = tw + N;
+    const unsigned sB = smem_u32(B);
+    const int rank = (int)cluster_rank(), x = blockIdx.x / C;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane / G, q = lane % G;
+    float2* ex = B + N * PS + (warp * PW + grp) * EX;
+    for (int i = threadIdx.x; i < N; i += NT) tw[i] = a.tw[i];
+    float scale = 1.0f;
+    unsigned cur = 0;
+    if constexpr (IN == ROW_IN_I64) {
+        const double S = a.slot_S[a.slot];
+        const long long tot = a.slot_total[a.slot];
+        scale = a.bf16 ? (tot > 0 ? (float)(1.0 / (double)tot) : 0.0f) : (float)S;
+        if (a.rowstamp) cur = *a.stamp;
+    }
+    cluster_sync(); // the peers run (their buffers may be written) and the twiddles are in place
+    for (int u0 = warp * PW; u0 < R / 2; u0 += (NT / 32) * PW) {
+        const int ya = R * rank + 2 * (u0 + grp), yb = ya + 1;
+        const long long ra = ((long long)x * N + ya) * N, rb = ra + N;
+        bool zero = false;
+        if constexpr (IN == ROW_IN_I64) {
+            if (a.rowstamp) {
+                // no row of the warp's two pairs holds a share of this push
+                const unsigned* rs = a.rowstamp + (long long)x * N + ya;
+                zero = !__any_sync(0xffffffffu, rs[0] == cur || rs[1] == cur);
+            }
+        }
+        if (zero) {
+#pragma unroll
+            for (int m = 0; m < (H + G - 1) / G; ++m) {
+                const int k = q + G * m;
+                if (k < H) {
+                    const int o = plane_cl_owner(k, CW, C), c = plane_cl_col(k, CW, C);
+                    plane_cl_put(B, sB, rank, o, ya * PS + c, make_float2(0.f, 0.f));
+                    plane_cl_put(B, sB, rank, o, yb * PS + c, make_float2(0.f, 0.f));
+                }
+            }
+            continue;
+        }
+        float2 v[16];
+        if constexpr (IN == ROW_IN_I64) {
+            long long xa[R1], xb[R1];
+#pragma unroll
+            for (int p = 0; p < R1; ++p) {
+                xa[p] = a.grid[ra + q + G * p];
+                xb[p] = a.grid[rb + q + G * p];
+            }
+            if (a.zero_in) {
+                long long* g = const_cast<long long*>(a.grid);
+#pragma unroll
+                for (int p = 0; p < R1; ++p) {
+                    g[ra + q + G * p] = 0;
+                    g[rb + q + G * p] = 0;
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < R1; ++p) v[p] = make_float2(__ll2float_rn(xa[p]) * scale, __ll2float_rn(xb[p]) * scale);
+        } else {
+#pragma unroll
+            for (int p = 0; p < R1; ++p) v[p] = make_float2(a.fin[ra + q + G * p], a.fin[rb + q + G * p]);
+        }
+        int t0, ts;
+        fft_row_lanes<N, -1>(v, ex, tw, q, t0, ts); // G = 16: every lane active, Z[t0 + ts k] = v[k]
+#pragma unroll
+        for (int k = 0; k < 16; ++k) ex[t0 + ts * k] = v[k];
+        __syncwarp();
+        // X_a = (Z_k + conj Z_{N-k}) / 2, X_b = (Z_k - conj Z_{N-k}) / (2 i), to the owner of column k
+#pragma unroll
+        for (int m = 0; m < (H + G - 1) / G; ++m) {
+            const int k = q + G * m;
+            if (k < H) {
+                const float2 zk = ex[k], zn = ex[k == 0 ? 0 : N - k];
+                const int o = plane_cl_owner(k, CW, C), c = plane_cl_col(k, CW, C);
+                plane_cl_put(B, sB, rank, o, ya * PS + c, make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y)));
+                plane_cl_put(B, sB, rank, o, yb * PS + c, make_float2(0.5f * (zk.y + zn.y), 0.5f * (zn.x - zk.x)));
+            }
+        }
+        __syncwarp(); // the exchange buffer is free for the next pair
+    }
+    cluster_sync(); // all N rows of this rank's columns are in its buffer
+    const int NC = rank ? CW : CW + 1;
+    for (int it = threadIdx.x; it < NC * G; it += NT) {
+        int c, r;
+        plane_cl_item(it, G, CW, c, r);
+        float2 v[16];
+#pragma unroll
+        for (int p = 0; p < R1; ++p) v[p] = B[(r + G * p) * PS + c];
+        dft<R1, -1>(v);
+#pragma unroll
+        for (int k1 = 1; k1 < R1; ++k1) v[k1] = cmul(v[k1], tw[r * k1]);
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) B[(k1 * G + r) * PS + c] = v[k1]; // the rows it read
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < NC * R1; it += NT) {
+        int c, k1;
+        plane_cl_item(it, R1, CW, c, k1);
+        float2 w[G];
+#pragma unroll
+        for (int r = 0; r < G; ++r) w[r] = B[(k1 * G + r) * PS + c];
+        dft<G, -1>(w);
+        const int kz = plane_cl_kz(rank, c, CW, C);
+#pragma unroll
+        for (int k2 = 0; k2 < G; ++k2) a.dst[((long long)x * N + (k1 + R1 * k2)) * NRP + kz] = w[k2];
+    }
+}
+
+template <int N>
+__global__ void __cluster_dims__(kPlaneClC, 1, 1) __launch_bounds__(kPlaneClThreads, 2) k_plane_cl_c2r(RowC2RArgs a) {
+    constexpr int C = kPlaneClC, NT = kPlaneClThreads, R1 = lanes_r1<N>(0), G = N / R1, PW = 32 / G, H = N / 2 + 1;
+    constexpr int NRP = nrp_of(N), PS = plane_cl_ps<N>(), EX = rows_lanes_ex<N>(), CW = N / (2 * C), R = N / C;
+    static_assert(R1 == 16 && G == 16 && PW == 2, "16 x 16 rows, two row pairs per warp");
+    static_assert(2 * H <= EX, "both half spectra fit the exchange buffer");
+    if (blockIdx.x >= C * N) {
+        // whole clusters past the planes: the near-field list (no cluster barrier)
+        plane_near_ctas<N, NT, C * N>(a.near);
+        return;
+    }
+    extern __shared__ float4 smem_raw[];
+    float2* tw = reinterpret_cast<float2*>(smem_raw);
+    float2* B = tw + N;
+    const unsigned sB = smem_u32(B);
+    const int rank = (int)cluster_rank(), x = blockIdx.x / C;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane / G, q = lane % G;
+    float2* ex = B + N * PS + (warp * PW + grp) * EX;
+    for (int i = threadIdx.x; i < N; i += NT) tw[i] = a.tw[i];
+    __syncthreads();
+    const int NC = rank ? CW : CW + 1;
+    for (int it = threadIdx.x; it < NC * G; it += NT) {
+        int c, r;
+        plane_cl_item(it, G, CW, c, r);
+        const int kz = plane_cl_kz(rank, c, CW, C);
+        float2 v[16];
+#pragma unroll
+        for (int p = 0; p < R1; ++p) v[p] = a.src[((long long)x * N + (r + G * p)) * NRP + kz];
+        dft<R1, 1>(v);
+#pragma unroll
+        for (int k1 = 1; k1 < R1; ++k1) {
+            float2 w = tw[r * k1];
+            w.y = -w.y;
+            v[k1] = cmul(v[k1], w);
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) B[(k1 * G + r) * PS + c] = v[k1];
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < NC * R1; it += NT) {
+        int c, k1;
+        plane_cl_item(it, R1, CW, c, k1);
+        float2 w[G];
+#pragma unroll
+        for (int r = 0; r < G; ++r) w[r] = B[(k1 * G + r) * PS + c];
+        dft<G, 1>(w);
+#pragma unroll
+        for (int k2 = 0; k2 < G; ++k2) B[(k1 * G + k2) * PS + c] = w[k2]; // Y[k1 + R1 k2]
+    }
+    cluster_sync(); // every rank's y results are visible in the cluster
+    for (int u0 = warp * PW; u0 < R / 2; u0 += (NT / 32) * PW) {
+        const int ya = R * rank + 2 * (u0 + grp), yb = ya + 1;
+        // buffer rows of y = k1 + R1 k2: G k1 + k2
+        const int ba = (ya % R1) * G + ya / R1, bb = (yb % R1) * G + yb / R1;
+        float2* xa = ex;
+        float2* xb = ex + H;
+#pragma unroll
+        for (int m = 0; m < (H + G - 1) / G; ++m) {
+            const int k = q + G * m;
+            if (k < H) {
+                const int o = plane_cl_owner(k, CW, C), c = plane_cl_col(k, CW, C);
+                float2 A = plane_cl_get(B, sB, rank, o, ba * PS + c);
+                float2 Bv = plane_cl_get(B, sB, rank, o, bb * PS + c);
+                if (k == 0 || k == N / 2) {
+                    A.y = 0.f;
+                    Bv.y = 0.f;
+                }
+                xa[k] = A;
+                xb[k] = Bv;
+            }
+        }
+        __syncwarp();
+        // Z_n = X_a(n) + i X_b(n), with the Hermitian extension X(N - k) = conj X(k)
+        float2 v[16];
+#pragma unroll
+        for (int p = 0; p < R1; ++p) {
+            const int n = q + G * p;
+            if (n < H) {
+                const float2 A = xa[n], Bv = xb[n];
+                v[p] = make_float2(A.x - Bv.y, A.y + Bv.x);
+            } else {
+                const float2 A = xa[N - n], Bv = xb[N - n];
+                v[p] = make_float2(A.x + Bv.y, Bv.x - A.y);
+            }
+        }
+        __syncwarp();
+        int t0, ts;
+        fft_row_lanes<N, 1>(v, ex, tw, q, t0, ts);
+        float* oa = a.out + ((long long)x * N + ya) * N;
+        float* ob = oa + N;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            oa[t0 + ts * k] = v[k].x * a.scale;
+            ob[t0 + ts * k] = v[k].y * a.scale;
+        }
+    }
+    cluster_sync(); // the peers have read this rank's buffer
+}
+
+// ------------------------------------------------------------------------
 // Host-side launchers for one N.
 struct MacArgs;
 struct FftOps {
@@ -1761,8 +2030,24 @@ struct FftOps {
     // extra CTAs of plane_c2r for a near-field list of `items` items on a GPU
     // of nsm SMs (0: run the list in a launch of its own)
     int (*plane_near_ctas)(long long items, int nsm);
+    // whether the per-step transforms take plane_r2c / plane_c2r now (always
+    // where plane_r2c exists for one CTA per plane; for N = 256 with the
+    // FFT_PLANE4 form); plane_clustered: a cluster of CTAs per plane
+    // (N = 256), whose plane kernels take grid or float input only
+    bool (*plane_on)();
+    bool plane_clustered;
 };
-enum { FFT_COLS_STAGES = 0, FFT_COLS_LANES = 1, FFT_COLS_LANES3 = 2, FFT_COLS_TMA = 3, FFT_COLS_TMA4 = 4, FFT_NVAR = 5 };
+// FFT_PLANE4 (N = 256): z and y per x-plane on a cluster of four CTAs
+// (k_plane_cl_r2c / k_plane_cl_c2r), the x passes in the FFT_COLS_LANES form
+enum {
+    FFT_COLS_STAGES = 0,
+    FFT_COLS_LANES = 1,
+    FFT_COLS_LANES3 = 2,
+    FFT_COLS_TMA = 3,
+    FFT_COLS_TMA4 = 4,
+    FFT_PLANE4 = 5,
+    FFT_NVAR = 6
+};
 
 template <int N> struct Launch {
     static constexpr int CW = cw_of(N), NCH = (N / 2) / CW;
@@ -1811,7 +2096,13 @@ template <int N> struct Launch {
                (cols_lanes_ok<N>()
                     ? (1 << FFT_COLS_LANES) | (1 << FFT_COLS_LANES3) | (1 << FFT_COLS_TMA) | (1 << FFT_COLS_TMA4)
                     : 0) |
-               (plane_lanes_ok<N>() ? (1 << FFT_COLS_LANES) : 0);
+               (plane_lanes_ok<N>() ? (1 << FFT_COLS_LANES) : 0) |
+               (plane_cl_ok<N>() ? (1 << FFT_PLANE4) : 0);
+    }
+    static bool plane_on() {
+        if constexpr (plane_ok<N>()) return true;
+        else if constexpr (plane_cl_ok<N>()) return variant() == FFT_PLANE4;
+        else return false;
     }
     static void set_variant(int v) {
         if (v >= 0 && v < FFT_NVAR && (variants_built() >> v & 1)) variant() = v;
@@ -1964,6 +2255,12 @@ template <int N> struct Launch {
             LC_ATTR((k_plane_r2c_lanes<N, ROW_IN_F32>), pls);
             LC_ATTR((k_plane_c2r_lanes<N>), pls);
         }
+        if constexpr (plane_cl_ok<N>()) {
+            const int pc = (int)plane_cl_smem_bytes<N>();
+            LC_ATTR((k_plane_cl_r2c<N, ROW_IN_I64>), pc);
+            LC_ATTR((k_plane_cl_r2c<N, ROW_IN_F32>), pc);
+            LC_ATTR((k_plane_cl_c2r<N>), pc);
+        }
 #undef LC_ATTR
         return e;
     }
@@ -1983,6 +2280,13 @@ template <int N> struct Launch {
             if (a.in_mode == ROW_IN_I64) launch_k(k_plane_r2c<N, ROW_IN_I64>, N, NT, sm, st, a);
             else if (a.in_mode == ROW_IN_F32) launch_k(k_plane_r2c<N, ROW_IN_F32>, N, NT, sm, st, a);
             else launch_k(k_plane_r2c<N, ROW_IN_WEDGE>, N, NT, sm, st, a);
+        } else if constexpr (plane_cl_ok<N>()) {
+            // a cluster per x-plane; grid or float input only
+            constexpr size_t sm = plane_cl_smem_bytes<N>();
+            if (a.in_mode == ROW_IN_I64)
+                launch_k(k_plane_cl_r2c<N, ROW_IN_I64>, kPlaneClC * N, kPlaneClThreads, sm, st, a);
+            else if (a.in_mode == ROW_IN_F32)
+                launch_k(k_plane_cl_r2c<N, ROW_IN_F32>, kPlaneClC * N, kPlaneClThreads, sm, st, a);
         }
     }
     static void plane_c2r(const RowC2RArgs& a, cudaStream_t st) {
@@ -1995,23 +2299,37 @@ template <int N> struct Launch {
                 }
             }
             launch_k(k_plane_c2r<N>, N + a.near.ctas, plane_threads_of(N), plane_smem_bytes<N>(), st, a);
+        } else if constexpr (plane_cl_ok<N>()) {
+            // near.ctas is a multiple of the cluster size: whole clusters
+            launch_k(k_plane_cl_c2r<N>, kPlaneClC * N + a.near.ctas, kPlaneClThreads, plane_cl_smem_bytes<N>(), st, a);
         }
     }
     // The near-field list on the SMs the N plane CTAs (one per SM) leave idle
     // in their last wave, about one item a thread, if that leaves at most
     // N / 16 items a thread: the planes' own time grows with N, and the list
     // should end within it.
+    // With a cluster per plane, the list takes whole clusters.
     static int plane_near_ctas(long long items, int nsm) {
+        int nt = 0, planes = 0, unit = 1, slots = nsm;
         if constexpr (plane_ok<N>()) {
-            int nt = plane_threads_of(N);
+            nt = plane_threads_of(N);
             if constexpr (plane_lanes_ok<N>())
                 if (lanes_form()) nt = plane_lanes_threads<N>();
-            const int idle = (nsm > 0 && N % nsm) ? nsm - N % nsm : 0;
-            if (idle == 0 || items <= 0) return 0;
-            const long long want = (items + nt - 1) / nt, c = want < idle ? want : idle;
-            return items <= c * nt * (N / 16) ? (int)c : 0;
+            planes = N;
+        } else if constexpr (plane_cl_ok<N>()) {
+            unit = kPlaneClC;
+            nt = kPlaneClThreads;
+            planes = kPlaneClC * N;
+            slots = 2 * nsm; // two CTAs resident per SM
         }
-        return 0;
+        if (planes == 0 || nsm <= 0 || items <= 0) return 0;
+        int idle = (planes % slots) ? slots - planes % slots : 0;
+        idle -= idle % unit;
+        if (idle == 0) return 0;
+        long long want = (items + nt - 1) / nt;
+        want += (unit - want % unit) % unit;
+        const long long c = want < idle ? want : idle;
+        return items <= c * nt * (N / 16) ? (int)c : 0;
     }
     static constexpr bool kRowsPl = N >= 256;
     template <class Kern> static int occ_ctas(Kern k, size_t smem) {

@@ -131,7 +131,8 @@ extern "C" lc_status lc_fft_r2c_static(int n, const float* in, float* out_comple
     c.src = work;
     c.dst = work;
     c.tw = tw;
-    if (ops->plane_r2c) {
+    const bool pl = ops->plane_r2c && ops->plane_on();
+    if (pl) {
         ops->plane_r2c(ra, st);
     } else {
         ops->rows_r2c(ra, st);
@@ -141,7 +142,7 @@ extern "C" lc_status lc_fft_r2c_static(int n, const float* in, float* out_comple
     ops->cols(c, st);
     const int h = n / 2 + 1;
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) count_launch(ops->plane_r2c ? 3 : 4); // twiddles + the transform's passes
+    if (e == cudaSuccess) count_launch(pl ? 3 : 4); // twiddles + the transform's passes
     if (e == cudaSuccess)
         e = cudaMemcpy2DAsync(out_complex, sizeof(float2) * h, work, sizeof(float2) * nrp_of(n), sizeof(float2) * h,
                               (size_t)n * n, cudaMemcpyDeviceToDevice, st);

@@ -138,8 +138,10 @@ def test_fft_pass_forms_against_numpy_and_each_other(n):
     xt = torch.from_numpy(x).cuda()
     ref = np.fft.rfftn(x.astype(np.float64))
     res = {}
+    forms = (lc.FFT_STAGES, lc.FFT_LANES, lc.FFT_LANES3, lc.FFT_TMA, lc.FFT_TMA4) + (
+        (lc.FFT_PLANE4,) if n == 256 else ())
     try:
-        for v in (lc.FFT_STAGES, lc.FFT_LANES, lc.FFT_LANES3, lc.FFT_TMA, lc.FFT_TMA4):
+        for v in forms:
             lc.fft_set_variant(n, v)
             assert lc.fft_variant(n) == v
             X = lc.fft_r2c(xt)
@@ -151,7 +153,7 @@ def test_fft_pass_forms_against_numpy_and_each_other(n):
             res[v] = Xn
     finally:
         lc.fft_set_variant(n, before)
-    for v in (lc.FFT_LANES, lc.FFT_LANES3, lc.FFT_TMA, lc.FFT_TMA4):
+    for v in forms[1:]:
         d = np.linalg.norm(res[lc.FFT_STAGES] - res[v]) / np.linalg.norm(ref)
         assert d < 2e-6, (v, d)
     # the same arithmetic under other tile schedules and copy engines
@@ -171,7 +173,7 @@ def test_fft_pass_forms_give_oracle_fields():
     ref = oracle.field_for(P, w.cat, 7, cells=cells)
     before = lc.fft_variant(256)
     try:
-        for v in (lc.FFT_STAGES, lc.FFT_LANES, lc.FFT_LANES3, lc.FFT_TMA, lc.FFT_TMA4):
+        for v in (lc.FFT_STAGES, lc.FFT_LANES, lc.FFT_LANES3, lc.FFT_TMA, lc.FFT_TMA4, lc.FFT_PLANE4):
             lc.fft_set_variant(256, v)
             got = _fields(w, range(8), {7})[7].reshape(-1)[cells].astype(np.float64)
             rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)

@@ -1,7 +1,8 @@
 """The innermost shell's near-field scatter on extra CTAs of the inverse plane
-kernel (grids up to 192^3, short lists) against its own launch: the same
-fields, one launch fewer per field.  LC_NEAR_CTAS is read once per process,
-so each setting runs in a child process."""
+kernel (grids up to 192^3, and 256^3 with the four-CTA cluster plane kernels;
+short lists) against its own launch: the same fields, one launch fewer per
+field.  LC_NEAR_CTAS and LC_FFT_VARIANT are read once per process, so each
+setting runs in a child process."""
 import os
 import subprocess
 import sys
@@ -22,6 +23,8 @@ CHILD = (
     "elif name == 'c2cic':\n"
     "    import dataclasses\n"
     "    w = dataclasses.replace(synth.config('c2'), deposit=1)\n"
+    "elif name == 'g256p4':\n"
+    "    w = synth.small(n=256, box=200.0, n_steps=steps, n_src=600, seed=4411, clustered=True)\n"
     "else:\n"
     "    w = synth.small(n=192, box=150.0, n_steps=steps, n_src=600, seed=4409, clustered=True)\n"
     "p = lc.Plan.from_workload(w)\n"
@@ -39,6 +42,8 @@ def _run(name, steps, fuse, d):
     env = dict(os.environ, PYTHONPATH=ROOT)
     if not fuse:
         env["LC_NEAR_CTAS"] = "0"
+    if name.endswith("p4"):
+        env["LC_FFT_VARIANT"] = "plane4"
     path = os.path.join(d, f"{name}_{int(fuse)}.npz")
     subprocess.run([sys.executable, "-c", CHILD, path, name, str(steps)], check=True, env=env, cwd=ROOT,
                    timeout=900)
@@ -46,10 +51,12 @@ def _run(name, steps, fuse, d):
     return r["f"], r["k"]
 
 
-@pytest.mark.parametrize("name,steps,fused", [("c2", 6, True), ("g192", 4, True), ("c2cic", 4, False)])
+@pytest.mark.parametrize("name,steps,fused", [("c2", 6, True), ("g192", 4, True), ("g256p4", 4, True),
+                                              ("c2cic", 4, False)])
 def test_near_on_plane_ctas_equals_own_launch(name, steps, fused):
     # c2: 142-418 sources a step at 128^3 (24 idle SMs); 192^3: the extra
-    # CTAs follow the 40 planes of the second wave; c2 with cloud in cell:
+    # CTAs follow the 40 planes of the second wave; 256^3 with the cluster
+    # plane kernels: whole clusters after the plane CTAs; c2 with cloud in cell:
     # 8 entries a source, beyond the short-list bound, so both runs launch
     # the scatter on its own
     with tempfile.TemporaryDirectory() as d:

@@ -39,17 +39,20 @@ def _run(name, steps, stamps, d):
     env = dict(os.environ, PYTHONPATH=ROOT)
     if not stamps:
         env["LC_ROW_STAMPS"] = "0"
+    if name.endswith("p4"):
+        env["LC_FFT_VARIANT"] = "plane4"
     path = os.path.join(d, f"{name}_{int(stamps)}.npy")
     subprocess.run([sys.executable, "-c", CHILD, path, name, str(steps)], check=True, env=env, cwd=ROOT,
                    timeout=900)
     return np.load(path)
 
 
-@pytest.mark.parametrize("name,steps", [("c2", 6), ("cic64", 5), ("bf16_256", 3)])
+@pytest.mark.parametrize("name,steps", [("c2", 6), ("cic64", 5), ("bf16_256", 3), ("bf16_256p4", 3)])
 def test_sparse_z_pass_equals_dense(name, steps):
     # c2: 128^3 plane kernels, FP32 history; 64^3 cloud in cell (up to four
-    # rows a source); 256^3 BF16 history through the row pass, which also
-    # clears the grid rows it reads
+    # rows a source); 256^3 BF16 history through the autotuned form and
+    # through the four-CTA cluster plane kernels, which also clear the grid
+    # rows they read
     with tempfile.TemporaryDirectory() as d:
         a = _run(name, steps, True, d)
         b = _run(name, steps, False, d)
