@@ -342,7 +342,11 @@ lc_status lc_batch_graph_destroy(lc_batch_graph* graph);
 /* --- tracing ------------------------------------------------------------------ */
 
 /* Phases of one step, each timed with a pair of CUDA events on the plan's
- * stream when timing is enabled. */
+ * stream when timing is enabled.  Where plane kernels do z and y together
+ * (N <= 192, and 256 in the cluster form), LC_PHASE_R2C_Z and LC_PHASE_C2R_Z
+ * hold both passes and the y phases stay empty; where a short near-field list
+ * runs on extra CTAs of the inverse plane kernel, its scatter counts in
+ * LC_PHASE_C2R_Z and LC_PHASE_NEAR holds the fold alone. */
 enum {
     LC_PHASE_DEPOSIT = 0,    /* zero grid + source checks + fixed-point deposit */
     LC_PHASE_R2C_Z = 1,      /* z rows, real -> complex (int64 prologue) */
