@@ -1747,9 +1747,10 @@ __global__ void __launch_bounds__(plane_lanes_threads<N>()) k_plane_c2r_lanes(Ro
 //     reading each kz from the buffer that holds it, and a second barrier
 //     keeps every buffer until the peers have read it.
 // Two 288-thread CTAs per SM (112 KB of shared memory each), so that one
-// CTA's transfers overlap the other's arithmetic.  (A cluster of two, one
-// 544-thread CTA per SM with 215 KB, was slower: the inverse 72.7 against
-// 64.3 us a step at 256^3.)
+// CTA's transfers overlap the other's arithmetic.  (Clusters of two, one
+// 544-thread CTA per SM with 215 KB, and of eight, three 256-thread CTAs per
+// SM with 59 KB, were slower at 256^3: the more CTAs a cluster holds, the
+// more of them wait at each barrier for the slowest.)
 template <int N> __host__ __device__ constexpr bool plane_cl_ok() { return N == 256; }
 constexpr int kPlaneClC = 4, kPlaneClThreads = 288;
 template <int N> __host__ __device__ constexpr int plane_cl_ps() { return N / (2 * kPlaneClC) + 4; }
