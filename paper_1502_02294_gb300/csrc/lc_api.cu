@@ -1624,9 +1624,9 @@ static lc_status field_impl(lc_plan* p, int step, float* out, int instant, uint6
         // with several plans serving at once this kept up better than the
         // copy engines), with a small grid so that the copy holds few SM
         // slots: serving c5 end to end, 231 fields/s by the copy engine,
-        // 340 with 152 CTAs, 386 with 24, 409 with 16, 419 with 12, 428 with
-        // 8, 439 with 6, 436 with 4.  LC_D2H=ce: always the copy engine.
-        // LC_D2H_CTAS: the copy kernel's CTAs (default 6).
+        // 340 with 152 CTAs, 386 with 24, 409 with 16, 419 with 12, and
+        // 414-439 (the spread between runs) with 4 to 8.  LC_D2H=ce: always
+        // the copy engine.  LC_D2H_CTAS: the copy kernel's CTAs (default 6).
         static const bool sm_copy = [] {
             const char* v = getenv("LC_D2H");
             return !(v && !strcmp(v, "ce"));
