@@ -948,9 +948,14 @@ __global__ void __launch_bounds__(kRowsLanesThreads, 2) k_rows_r2c_lanes(RowR2CA
         scale = a.bf16 ? (tot > 0 ? (float)(1.0 / (double)tot) : 0.0f) : (float)Su;
         if (a.rowstamp) cur = *a.stamp;
     }
-    __syncthreads();
     const long long nwarps = (long long)gridDim.x * (kRowsLanesThreads / 32);
-    for (long long u = (long long)blockIdx.x * (kRowsLanesThreads / 32) + warp; u * PW < npairs; u += nwarps) {
+    long long u = (long long)blockIdx.x * (kRowsLanesThreads / 32) + warp;
+    // the row stamps of a warp's rows, loaded one iteration ahead (lane l < 2 PW: row 2 u PW + l)
+    unsigned stamp_next = 0;
+    if constexpr (IN == ROW_IN_I64)
+        if (a.rowstamp && lane < 2 * PW && u * PW < npairs) stamp_next = a.rowstamp[2 * u * PW + lane];
+    __syncthreads();
+    for (; u * PW < npairs; u += nwarps) {
         const long long rp = u * PW + grp; // npairs is a multiple of PW: every group of the warp has a pair
         const long long ra = 2 * rp * N, rb = ra + N;
         float2 v[16];
@@ -958,7 +963,9 @@ __global__ void __launch_bounds__(kRowsLanesThreads, 2) k_rows_r2c_lanes(RowR2CA
             if (a.rowstamp) {
                 // the warp's 2 PW rows (2 u PW ... 2 u PW + 2 PW - 1 < 2 npairs);
                 // none with a share of this push: zero half spectra, no loads
-                const bool mine = lane < 2 * PW && a.rowstamp[2 * u * PW + lane] == cur;
+                const bool mine = lane < 2 * PW && stamp_next == cur;
+                const long long un = u + nwarps;
+                stamp_next = (lane < 2 * PW && un * PW < npairs) ? a.rowstamp[2 * un * PW + lane] : 0u;
                 if (!__any_sync(0xffffffffu, mine)) {
                     float2* da = a.dst + (2 * rp) * NRP;
                     float2* db = da + NRP;
@@ -1500,6 +1507,15 @@ __global__ void __launch_bounds__(plane_lanes_threads<N>()) k_plane_r2c_lanes(Ro
         scale = a.bf16 ? (tot > 0 ? (float)(1.0 / (double)tot) : 0.0f) : (float)S;
         if (a.rowstamp) cur = *a.stamp;
     }
+    // the stamps of this group's rows 2u, 2u + 1, loaded one pair ahead
+    unsigned sa = 0, sb = 0;
+    if constexpr (IN == ROW_IN_I64) {
+        const int u = warp * PW + grp;
+        if (a.rowstamp && u < P) {
+            sa = a.rowstamp[(long long)x * N + 2 * u];
+            sb = a.rowstamp[(long long)x * N + 2 * u + 1];
+        }
+    }
     __syncthreads();
     for (int u0 = warp * PW; u0 < P; u0 += (NT / 32) * PW) {
         const int u = u0 + grp;
@@ -1510,8 +1526,11 @@ __global__ void __launch_bounds__(plane_lanes_threads<N>()) k_plane_r2c_lanes(Ro
             if (a.rowstamp) {
                 // rows without a share of this push: zero half spectra, when
                 // all of the warp's pairs are such (the warp stays converged)
-                const unsigned* rs = a.rowstamp + (long long)x * N + 2 * u;
-                if (!__any_sync(0xffffffffu, rs[0] == cur || rs[1] == cur)) {
+                const bool mine = sa == cur || sb == cur;
+                const int un = u + (NT / 32) * PW;
+                sa = un < P ? a.rowstamp[(long long)x * N + 2 * un] : 0u;
+                sb = un < P ? a.rowstamp[(long long)x * N + 2 * un + 1] : 0u;
+                if (!__any_sync(0xffffffffu, mine)) {
 #pragma unroll
                     for (int m = 0; m < M; ++m) {
                         const int k = q + G * m;
@@ -1806,6 +1825,15 @@ __global__ void __cluster_dims__(kPlaneClC, 1, 1) __launch_bounds__(kPlaneClThre
         scale = a.bf16 ? (tot > 0 ? (float)(1.0 / (double)tot) : 0.0f) : (float)S;
         if (a.rowstamp) cur = *a.stamp;
     }
+    // the stamps of this group's rows, loaded one pair ahead
+    unsigned sa = 0, sb = 0;
+    if constexpr (IN == ROW_IN_I64) {
+        const int ya = R * rank + 2 * (warp * PW + grp);
+        if (a.rowstamp && warp * PW < R / 2) {
+            sa = a.rowstamp[(long long)x * N + ya];
+            sb = a.rowstamp[(long long)x * N + ya + 1];
+        }
+    }
     cluster_sync(); // the peers run (their buffers may be written) and the twiddles are in place
     for (int u0 = warp * PW; u0 < R / 2; u0 += (NT / 32) * PW) {
         const int ya = R * rank + 2 * (u0 + grp), yb = ya + 1;
@@ -1814,8 +1842,11 @@ __global__ void __cluster_dims__(kPlaneClC, 1, 1) __launch_bounds__(kPlaneClThre
         if constexpr (IN == ROW_IN_I64) {
             if (a.rowstamp) {
                 // no row of the warp's two pairs holds a share of this push
-                const unsigned* rs = a.rowstamp + (long long)x * N + ya;
-                zero = !__any_sync(0xffffffffu, rs[0] == cur || rs[1] == cur);
+                const bool mine = sa == cur || sb == cur;
+                const int un = u0 + (NT / 32) * PW, yn = R * rank + 2 * (un + grp);
+                sa = un < R / 2 ? a.rowstamp[(long long)x * N + yn] : 0u;
+                sb = un < R / 2 ? a.rowstamp[(long long)x * N + yn + 1] : 0u;
+                zero = !__any_sync(0xffffffffu, mine);
             }
         }
         if (zero) {
