@@ -93,8 +93,8 @@ enum { LC_KERNEL_LW = 0, LC_KERNEL_EXP = 1 };
  *                    the mesh: each target cell gets the s^3 sub-sample average
  *                    of g around the source (over the periodic images, inside
  *                    the innermost shell and the horizon) times the shell's
- *                    normalisation factor.  Needs the FP32 history and the NGP
- *                    deposit;
+ *                    normalisation factor.  Needs the NGP deposit (either
+ *                    history);
  *   LC_NEAR_NONE:    no split: the innermost shell goes through the FFT path
  *                    whole (no per-source near-field work). */
 enum { LC_NEAR_NGP = 0, LC_NEAR_SUBCELL = 1, LC_NEAR_NONE = 2 };

@@ -507,7 +507,6 @@ bool valid_steps(const lc_steps* st) {
     if (st->kernel != LC_KERNEL_LW && st->kernel != LC_KERNEL_EXP) return false;
     if (st->near_mode != LC_NEAR_NGP && st->near_mode != LC_NEAR_SUBCELL && st->near_mode != LC_NEAR_NONE)
         return false;
-    if (st->near_mode == LC_NEAR_SUBCELL && st->history != LC_HISTORY_FP32) return false;
     if (st->kernel == LC_KERNEL_EXP && !(st->kernel_length > 0.0 && isfinite(st->kernel_length) &&
                                          st->kernel_rmax > 0.0 && isfinite(st->kernel_rmax)))
         return false;

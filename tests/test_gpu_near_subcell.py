@@ -68,7 +68,7 @@ def test_sources_on_cell_centres_give_the_ngp_field():
     assert rel <= FP32_L2 and mx <= FP32_MAX, (rel, mx)
 
 
-def test_subcell_checkpoint_and_bf16_refused():
+def test_subcell_checkpoint():
     w = synth.small(n=32, box=60.0, n_steps=6, n_src=100, subsamples=4, seed=3303)
     a = lc.Plan.from_workload(w, near_mode=lc.NEAR_SUBCELL)
     for s in range(4):
@@ -86,6 +86,22 @@ def test_subcell_checkpoint_and_bf16_refused():
         c.load(buf)
     for p in (a, b, c):
         p.close()
-    wb = synth.small(n=16, box=40.0, n_steps=4, history=synth.HISTORY_BF16)
-    with pytest.raises(lc.LCError):
-        lc.Plan.from_workload(wb, near_mode=lc.NEAR_SUBCELL)
+
+
+def test_subcell_near_field_bf16_history():
+    # the sub-cell near cube is summed in FP64 from the sources' positions
+    # whatever the history format: with the BF16 history the field meets the
+    # BF16 bound against the FP64 oracle, and stays close to the FP32-history
+    # field of the same mode
+    w = synth.small(n=32, box=60.0, n_steps=8, n_src=150, subsamples=4, seed=3304, z_start=16.0, z_end=15.0,
+                    history=synth.HISTORY_BF16)
+    P = oracle.Problem.from_workload(w)
+    got = _fields(w, range(8), {3, 7}, lc.NEAR_SUBCELL)
+    w32 = synth.small(n=32, box=60.0, n_steps=8, n_src=150, subsamples=4, seed=3304, z_start=16.0, z_end=15.0)
+    f32 = _fields(w32, range(8), {3, 7}, lc.NEAR_SUBCELL)
+    for s, J in got.items():
+        ref = oracle.hybrid_field_for(P, w.cat, s)
+        rel = np.linalg.norm(J.astype(np.float64) - ref) / np.linalg.norm(ref)
+        assert rel <= 5e-3, (s, rel)
+        d = np.linalg.norm(J.astype(np.float64) - f32[s]) / np.linalg.norm(f32[s])
+        assert d <= 5e-3, (s, d)
