@@ -188,7 +188,7 @@ lc_status lc_retarded_field(lc_plan* plan, int step, float* out);
  * copy runs on a copy stream of the plan, out of one of two device stages,
  * so the next steps' pushes and fields compute while it drains (into
  * page-locked memory by a small copy kernel writing through the buffer's
- * device view, LC_D2H_CTAS CTAs, default 6; LC_D2H=ce in the environment
+ * device view, LC_D2H_CTAS CTAs, default 8; LC_D2H=ce in the environment
  * uses the copy engine); `out` holds
  * the field once lc_plan_wait(plan, *ticket) returns, and must stay valid
  * until then (page-locked host memory makes the copy asynchronous; with

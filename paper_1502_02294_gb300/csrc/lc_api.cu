@@ -1624,8 +1624,8 @@ static lc_status field_impl(lc_plan* p, int step, float* out, int instant, uint6
         // copy engines), with a small grid so that the copy holds few SM
         // slots: serving c5 end to end, 231 fields/s by the copy engine,
         // 340 with 152 CTAs, 386 with 24, 409 with 16, 419 with 12, and
-        // 414-439 (the spread between runs) with 4 to 8.  LC_D2H=ce: always
-        // the copy engine.  LC_D2H_CTAS: the copy kernel's CTAs (default 6).
+        // 402-439 (the spread between runs) with 4 to 8.  LC_D2H=ce: always
+        // the copy engine.  LC_D2H_CTAS: the copy kernel's CTAs (default 8).
         static const bool sm_copy = [] {
             const char* v = getenv("LC_D2H");
             return !(v && !strcmp(v, "ce"));
@@ -1633,7 +1633,7 @@ static lc_status field_impl(lc_plan* p, int step, float* out, int instant, uint6
         static const int copy_ctas = [] {
             const char* v = getenv("LC_D2H_CTAS");
             const int c = v ? atoi(v) : 0;
-            return c > 0 ? c : 6;
+            return c > 0 ? c : 8;
         }();
         void* hv = sm_copy ? pinned_device_view(out) : nullptr;
         if (e == cudaSuccess && hv && (reinterpret_cast<uintptr_t>(hv) & 15) == 0) {
