@@ -1274,8 +1274,9 @@ lc_status lc_plan_prepare(lc_plan* p, int b, int e) {
 
 // How the deposit grid is cleared between pushes: with a near-field list,
 // only the cells the push deposited into (sparse clear); without one, the
-// staged z pass of N >= 256 zeroes every block it reads, and smaller grids
-// (plane kernels) are cleared by a memset before each deposit.
+// z pass of N >= 256 zeroes what it reads (with row stamps, the stamped rows,
+// which hold every non-zero cell), and smaller grids (plane kernels) are
+// cleared by a memset before each deposit.
 static bool zeroed_by_r2c(const lc_plan* p) { return !p->near_on && p->N >= 256; }
 static bool memset_before_deposit(const lc_plan* p) { return !p->near_on && !zeroed_by_r2c(p); }
 
